@@ -1,0 +1,141 @@
+"""Pins of the oracle's equations of state (Sec. III, Eqs. 15-27) against
+facts that do not come from the oracle's own formulas:
+
+* Eq. 3, p0 = rho psi' - psi, ties the printed psi and mu to the separately
+  printed p0 (Eqs. 16, 19, 22, 25);
+* psi' is the derivative of psi (Eq. 8 with the gradient term dropped),
+  checked by finite differences;
+* closed-form critical points: van der Waals T_c = 8a/(27bR), rho_c = 1/(3b),
+  Z_c = 3/8; Redlich-Kwong family Z_c = 1/3 and b rho_c = 2^(1/3) - 1;
+  Peng-Robinson textbook constants Omega_a = 0.45724, Omega_b = 0.07780,
+  Z_c = 0.3074; Carnahan-Starling-van der Waals Z_c = 0.3590;
+* alpha(T_c) = 1 for PR and RKS.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from oracle import thermo
+
+EOS_SETS = [  # (kind, a, b): Sec. III parameter sets; vdW as in the configs
+    ("vdw", 9 / 49, 2 / 21),
+    ("cs", 1.0, 4.0),
+    ("pr", 2 / 49, 2 / 21),
+    ("rks", 2 / 49, 2 / 21),
+]
+
+
+def _eos(kind, a, b, Tr=0.85, omega=0.344):
+    return thermo.make_eos(kind, a, b, 1.0, Tr, omega)
+
+
+@pytest.mark.parametrize("kind,a,b", EOS_SETS)
+@pytest.mark.parametrize("Tr", [0.6, 0.85, 1.1])
+def test_pressure_identity_eq3(kind, a, b, Tr):
+    e = _eos(kind, a, b, Tr)
+    top = thermo.rho_max(kind, b)
+    rho = np.linspace(0.002, 0.95, 200) * top
+    psi, mu, p0 = e.eval(rho)
+    scale = np.abs(rho * mu) + np.abs(psi) + np.abs(p0)
+    assert np.max(np.abs(rho * mu - psi - p0) / scale) < 1e-13
+
+
+@pytest.mark.parametrize("kind,a,b", EOS_SETS)
+def test_mu_is_derivative_of_psi(kind, a, b):
+    e = _eos(kind, a, b)
+    top = thermo.rho_max(kind, b)
+    rho = np.linspace(0.01, 0.9, 60) * top
+    h = 2e-3 * np.minimum(rho, top - rho)
+    d = (-e.psi(rho + 2 * h) + 8 * e.psi(rho + h) - 8 * e.psi(rho - h)
+         + e.psi(rho - 2 * h)) / (12 * h)
+    mu = e.mu(rho)
+    assert np.max(np.abs(d - mu) / (np.abs(mu) + np.abs(e.p0(rho) / rho))) \
+        < 1e-8
+
+
+def test_vdw_critical_point_closed_form():
+    for a, b, R in [(9 / 49, 2 / 21, 1.0), (1.0, 0.5, 2.0)]:
+        Tc, rc = thermo.critical_point("vdw", a, b, R)
+        assert Tc == pytest.approx(8 * a / (27 * b * R), rel=1e-13)
+        assert rc == pytest.approx(1 / (3 * b), rel=1e-13)
+        pc = oracle.Eos("vdw", a, b, R, Tc).p0(rc)
+        assert pc == pytest.approx(a / (27 * b * b), rel=1e-12)
+
+
+@pytest.mark.parametrize("kind,a,b,Zc,tol", [
+    ("vdw", 9 / 49, 2 / 21, 3 / 8, 1e-12),
+    ("rks", 2 / 49, 2 / 21, 1 / 3, 1e-12),
+    ("pr", 2 / 49, 2 / 21, 0.3074, 2e-4),
+    ("cs", 1.0, 4.0, 0.3590, 2e-4),
+])
+def test_critical_compressibility(kind, a, b, Zc, tol):
+    Tc, rc = thermo.critical_point(kind, a, b)
+    pc = oracle.Eos(kind, a, b, 1.0, Tc, 1.0).p0(rc)
+    assert pc / (rc * Tc) == pytest.approx(Zc, rel=tol)
+
+
+def test_redlich_kwong_critical_density_closed_form():
+    _, rc = thermo.critical_point("rks", 2 / 49, 2 / 21)
+    assert (2 / 21) * rc == pytest.approx(2 ** (1 / 3) - 1, rel=1e-12)
+
+
+@pytest.mark.parametrize("kind,omega_a,omega_b", [
+    ("pr", 0.45724, 0.07780), ("rks", 0.42748, 0.08664)])
+def test_cubic_eos_textbook_constants(kind, omega_a, omega_b):
+    a, b = 2 / 49, 2 / 21
+    Tc, rc = thermo.critical_point(kind, a, b)
+    pc = oracle.Eos(kind, a, b, 1.0, Tc, 1.0).p0(rc)
+    assert a * pc / Tc ** 2 == pytest.approx(omega_a, rel=2e-4)
+    assert b * pc / Tc == pytest.approx(omega_b, rel=2e-4)
+
+
+@pytest.mark.parametrize("kind,a,b", EOS_SETS)
+def test_critical_point_is_inflection_of_printed_p0(kind, a, b):
+    Tc, rc = thermo.critical_point(kind, a, b)
+    e = oracle.Eos(kind, a, b, 1.0, Tc, 1.0)
+    h = 1e-3 * rc
+    p = [float(e.p0(rc + k * h)) for k in (-2, -1, 0, 1, 2)]
+    d1 = (p[0] - 8 * p[1] + 8 * p[3] - p[4]) / (12 * h)
+    d2 = (-p[0] + 16 * p[1] - 30 * p[2] + 16 * p[3] - p[4]) / (12 * h * h)
+    d3 = (-p[0] + 2 * p[1] - 2 * p[3] + p[4]) / (2 * h ** 3)
+    # d1 and d2 vanish; d3 sets the scale of what "vanish" means
+    assert abs(d1) * rc < 1e-7 * abs(d3) * rc ** 3
+    assert abs(d2) * rc ** 2 < 1e-5 * abs(d3) * rc ** 3
+
+
+@pytest.mark.parametrize("kind,a,b", EOS_SETS)
+def test_dp0_drho_matches_finite_difference(kind, a, b):
+    e = _eos(kind, a, b, 0.8)
+    top = thermo.rho_max(kind, b)
+    for r in np.linspace(0.02, 0.9, 15) * top:
+        h = 1e-5 * min(r, top - r)
+        fd = float(e.p0(r + h) - e.p0(r - h)) / (2 * h)
+        an = thermo.dp0_drho(e.kind, e.a, e.b, e.R, e.T, e.alpha, r)
+        scale = abs(float(e.p0(r))) / r + e.R * e.T
+        assert an == pytest.approx(fd, rel=1e-6, abs=1e-7 * scale)
+
+
+def test_alpha_is_one_at_critical_and_decreases_with_temperature():
+    for kind in ("pr", "rks"):
+        for omega in (0.344, 0.011):
+            assert thermo.alpha_of(kind, 1.0, omega) == 1.0
+            assert thermo.alpha_of(kind, 0.8, omega) > 1.0
+            assert thermo.alpha_of(kind, 1.2, omega) < 1.0
+    assert thermo.alpha_of("vdw", 0.7, 0.3) == 1.0
+    # PR, omega = 0.344: m = 0.37464 + 1.54226 w - 0.26992 w^2 (Eq. 22 text)
+    m = 0.37464 + 1.54226 * 0.344 - 0.26992 * 0.344 ** 2
+    assert thermo.alpha_of("pr", 0.81, 0.344) == pytest.approx(
+        (1 + m * 0.1) ** 2, rel=1e-15)
+
+
+def test_critical_point_scales_with_parameters():
+    # p0(rho; a, b, R, T) = (a/b^2) P(b rho; R T b / a): T_c ~ a/(b R),
+    # rho_c ~ 1/b for every EOS of the paper.
+    for kind in ("cs", "pr", "rks"):
+        T1, r1 = thermo.critical_point(kind, 1.0, 1.0, 1.0)
+        T2, r2 = thermo.critical_point(kind, 3.0, 0.5, 2.0)
+        assert T2 == pytest.approx(T1 * 3.0 / (0.5 * 2.0), rel=1e-12)
+        assert r2 == pytest.approx(r1 / 0.5, rel=1e-12)
+    assert math.isfinite(thermo.critical_point("cs", 1, 4)[0])

@@ -1,0 +1,169 @@
+"""Physics pins of the whole oracle step: what the paper and square-gradient
+theory fix about converged states.
+
+* Flat interface at the paper's own parameters (RKS, T_r = 0.8, kappa = 0.01,
+  tau = 1.3, Sec. V): coexistence densities close to the Maxwell
+  construction (Sec. III, Fig. 1: "excellent agreement").
+* Static drops (Carnahan-Starling, kappa = 0.5): the Laplace pressure jump
+  Delta p r equals the square-gradient tension sigma of Eq. 1.
+* Wetting (Sec. IV-V): at mu_s = mu_coex the wall is neutral (theta = 90
+  degrees) and theta rises almost linearly with mu_s (Fig. 3).
+* Fig. 2: the paper's printed (CP, theta) pairs for RKS (tests/golden).
+* Galilean invariance (Sec. II): a slab given a uniform velocity keeps its
+  profile and is carried by that velocity.
+"""
+import math
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from oracle import observables as ob
+from oracle import thermo
+from paper_1611_00907_gb300 import inputs
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _read_golden(name):
+    rows = []
+    with open(os.path.join(GOLDEN, name)) as fh:
+        for line in fh:
+            line = line.split("#", 1)[0].strip()
+            if line:
+                rows.append([float(v) for v in line.split()])
+    return np.array(rows)
+
+
+def test_flat_interface_matches_maxwell_at_paper_parameters(oracle_threads):
+    e = thermo.make_eos("rks", 2 / 49, 2 / 21, 1.0, 0.8, 0.344)
+    rv, rl, _, _ = thermo.maxwell(e)
+    nx, ny = 4, 128
+    L = oracle.Lattice(nx, ny, e, 1.3, 0.01)
+    L.init_equilibrium(inputs.slab(nx, ny, rl, rv, width=2.0))
+    L.step(6000)
+    hi, lo = ob.slab_bulk(L.moments()["rho"])
+    assert hi == pytest.approx(rl, rel=1e-2)
+    assert lo == pytest.approx(rv, rel=5e-2)
+    # density ratio above 30, as the paper's large-ratio claim needs
+    assert hi / lo > 30
+
+
+def test_flat_interface_converges_and_keeps_mass(oracle_threads):
+    # The configuration of the 64 x 64 Carnahan-Starling slab: converged
+    # bulk densities change by < 1e-7 per 1000 steps and mass is conserved.
+    e = thermo.make_eos("cs", 1.0, 4.0, 1.0, 0.85)
+    rv, rl, _, _ = thermo.maxwell(e)
+    L = oracle.Lattice(4, 64, e, 1.0, 0.5)
+    L.init_equilibrium(inputs.slab(4, 64, rl, rv, 4.0))
+    m0 = L.density().sum()
+    L.step(4000)
+    a = ob.slab_bulk(L.moments()["rho"])
+    L.step(1000)
+    b = ob.slab_bulk(L.moments()["rho"])
+    assert abs(a[0] - b[0]) < 1e-7 and abs(a[1] - b[1]) < 1e-7
+    assert abs(L.density().sum() - m0) / m0 < 1e-12   # round-off only
+    # liquid within 2 % of Maxwell; vapour is depleted (lattice forcing
+    # error at this interface width) but stays within a factor 0.6..1
+    assert b[0] == pytest.approx(rl, rel=2e-2)
+    assert 0.6 * rv < b[1] < rv
+
+
+def test_laplace_law(oracle_threads):
+    e = thermo.make_eos("cs", 1.0, 4.0, 1.0, 0.85)
+    rv, rl, _, _ = thermo.maxwell(e)
+    sigma = thermo.surface_tension(e, 0.5)
+    n = 64
+    pts = []
+    for r in (14, 20):
+        L = oracle.Lattice(n, n, e, 1.0, 0.5)
+        L.init_equilibrium(inputs.drop(n, n, r, rl, rv, 4.0))
+        L.step(5000)
+        dp, req = ob.laplace_jump(e, L.moments()["rho"])
+        pts.append((1 / req, dp))
+        assert dp * req == pytest.approx(sigma, rel=5e-2)
+    (x1, y1), (x2, y2) = pts
+    slope = (y2 - y1) / (x2 - x1)
+    assert slope == pytest.approx(sigma, rel=8e-2)
+
+
+def _wall_angle(e, rv, rl, mu_s, nx=128, ny=64, r=24, steps=6000):
+    L = oracle.Lattice(nx, ny, e, 1.0, 0.5, walls=True, mu_bottom=mu_s)
+    L.init_equilibrium(inputs.wall_drop(nx, ny, r, rl, rv, 4.0))
+    L.step(steps)
+    return ob.contact_angle(L.moments()["rho"], rl, rv)[0]
+
+
+def test_contact_angle_neutral_and_linear_in_surface_mu(oracle_threads):
+    e = thermo.make_eos("cs", 1.0, 4.0, 1.0, 0.85)
+    rv, rl, mc, _ = thermo.maxwell(e)
+    dmu = np.array([-0.03, 0.0, 0.03])
+    th = np.array([_wall_angle(e, rv, rl, mc + d) for d in dmu])
+    assert th[1] == pytest.approx(90.0, abs=1.5)
+    assert np.all(np.diff(th) > 5.0)           # hydrophobic as mu_s grows
+    # near-linear (Sec. V, Fig. 3): the midpoint sits on the chord
+    assert th[1] == pytest.approx(0.5 * (th[0] + th[2]), abs=1.0)
+
+
+@pytest.mark.parametrize("row", [1, 3])
+def test_fig2_contact_angles_rks(row, oracle_threads):
+    # Fig. 2 setup at half linear size (Dx = 250, Dy = 100, drop radius 25):
+    # RKS, T_r = 0.8, kappa = 0.01, tau = 1.3.  The paper reads its angles
+    # off images; +-6 degrees covers that and the halved resolution.
+    gold = _read_golden("fig2_contact_angles.txt")
+    e = thermo.make_eos("rks", 2 / 49, 2 / 21, 1.0, 0.8, 0.344)
+    rv, rl, _, _ = thermo.maxwell(e)
+    for cp, theta in gold[[row]]:
+        L = oracle.Lattice(250, 100, e, 1.3, 0.01, walls=True, mu_bottom=cp)
+        L.init_equilibrium(inputs.wall_drop(250, 100, 25, rl, rv, 2.0))
+        L.step(4000)
+        got = ob.contact_angle(L.moments()["rho"], rl, rv)[0]
+        assert got == pytest.approx(theta, abs=6.0), (cp, got, theta)
+
+
+def _centroid(r):
+    n = r.size
+    ph = np.angle(np.sum((r - r.min()) * np.exp(2j * np.pi * np.arange(n) /
+                                                  n)))
+    return ph * n / (2 * np.pi)
+
+
+def test_galilean_invariance_of_a_moving_slab(oracle_threads):
+    e = thermo.make_eos("cs", 1.0, 4.0, 1.0, 0.85)
+    rv, rl, _, _ = thermo.maxwell(e)
+    nx, ny, U = 128, 4, 0.02
+    A = oracle.Lattice(nx, ny, e, 1.0, 0.5)
+    A.init_equilibrium(inputs.slab(nx, ny, rl, rv, 4.0, axis="x"))
+    A.step(3000)
+    r0 = A.moments()["rho"]
+    B = oracle.Lattice(nx, ny, e, 1.0, 0.5)
+    B.init_equilibrium(r0, np.full((ny, nx), U), None)
+    T = 1600
+    B.step(T)
+    r1 = B.moments()["rho"][0]
+    shift = (_centroid(r1) - _centroid(r0[0])) % nx
+    assert shift == pytest.approx(U * T, rel=2e-2)
+    k = np.fft.fftfreq(nx) * 2 * np.pi
+    back = np.real(np.fft.ifft(np.fft.fft(r1) * np.exp(1j * k * shift)))
+    assert np.max(np.abs(back - r0[0])) < 0.03 * (rl - rv)
+    assert r1.max() == pytest.approx(r0.max(), rel=1e-2)
+    assert r1.min() == pytest.approx(r0.min(), rel=1e-2)
+    assert math.isfinite(float(r1.sum()))
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("row", [0, 2, 4, 5])
+def test_fig2_contact_angles_rks_remaining(row, oracle_threads):
+    # The other four (CP, theta) pairs of Fig. 2, same half-size setup.  At
+    # CP = 0.15 and 0.18 the half-size drop lifts off (180 degrees); the
+    # paper's full-size drop shows 160 and 180 degrees.
+    gold = _read_golden("fig2_contact_angles.txt")
+    e = thermo.make_eos("rks", 2 / 49, 2 / 21, 1.0, 0.8, 0.344)
+    rv, rl, _, _ = thermo.maxwell(e)
+    cp, theta = gold[row]
+    L = oracle.Lattice(250, 100, e, 1.3, 0.01, walls=True, mu_bottom=cp)
+    L.init_equilibrium(inputs.wall_drop(250, 100, 25, rl, rv, 2.0))
+    L.step(6000)
+    got = ob.contact_angle(L.moments()["rho"], rl, rv)[0]
+    assert got == pytest.approx(theta, abs=6.0 if theta < 150 else 21.0)
