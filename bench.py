@@ -1,0 +1,381 @@
+"""Throughput benchmark of the fused chemical-potential LBM step.
+
+Workload: a 4096 x 4096 periodic D2Q9 lattice, Carnahan-Starling EOS (a = 1,
+b = 4, R = 1) at T_r = 0.85, kappa = 0.5, tau = 1, spinodal decomposition
+from rho_c (1 + 0.01 xi), xi ~ U[-1, 1) with seed 1.  The FP32 state is
+0.6 GB, far above the 129 MB L2, so no flush is needed between steps.
+
+One line of JSON on stdout (rank 0).  `value` is MLUPS (million lattice
+updates per second) of the FP32 step over all ranks; `roofline` relates the
+step kernel's algorithmic bytes (9 populations read and written: 72 B per
+update in FP32) to the measured HBM copy bandwidth.  `fp64` repeats the
+measurement with FP64 storage and arithmetic.  `e2e` runs the same steps
+through the public API from host memory (initial field uploaded, a global
+FP64 reduction read back every `check_every` steps, final density read back).
+`cpu_baseline` times the CPU oracle on a bounded sample of the same workload.
+
+--impl reference times the CPU oracle (FP64, all host cores) on the same
+workload and metric.
+"""
+import argparse
+import hashlib
+import json
+import os
+import re
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+N_SIDE = 4096
+EOS_ARGS = dict(eos="cs", a=1.0, b=4.0, R=1.0, Tr=0.85, tau=1.0, kappa=0.5)
+BYTES_PER_LU = {"f64": 144, "f32": 72, "f32_offset": 72, "f16_offset": 36}
+FALLBACK_HBM_GBS = 6800.0
+KERNEL_SOURCES = ["paper_1611_00907_gb300/csrc/step.cu",
+                  "paper_1611_00907_gb300/csrc/device_common.cuh",
+                  "paper_1611_00907_gb300/csrc/cplbm_internal.h"]
+
+
+def workload_config(n=N_SIDE):
+    return {"workload": "cs_spinodal_%dx%d" % (n, n), "nx": n, "ny": n,
+            "eos": "carnahan-starling a=1 b=4 R=1", "T_over_Tc": 0.85,
+            "kappa": 0.5, "tau": 1.0, "init": "rho_c(1+0.01*U[-1,1)), seed 1",
+            "boundary": "periodic", "l2": "working set > L2 (no flush)"}
+
+
+def initial_rho(n=N_SIDE):
+    from paper_1611_00907_gb300 import eos_critical, inputs
+    _, rc = eos_critical("cs", 1.0, 4.0, 1.0)
+    return inputs.spinodal_noise(n, n, rc, 0.01, seed=1)
+
+
+# ---------------------------------------------------------------------------
+# Peaks, traffic record, clocks
+# ---------------------------------------------------------------------------
+def hbm_peak():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as fh:
+            d = json.load(fh)
+        for k in ("hbm_gbs", "hbm_GBs", "hbm_copy_gbs"):
+            if k in d:
+                return float(d[k]), "measured"
+    except (OSError, ValueError):
+        pass
+    return FALLBACK_HBM_GBS, "fallback"
+
+
+def kernel_hash():
+    h = hashlib.sha256()
+    for rel in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, rel), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def recorded_traffic(precision, n_side=N_SIDE):
+    """DRAM bytes per step-kernel launch from the committed ncu summary,
+    scaled to the bench lattice, or None when the kernel changed since."""
+    path = os.path.join(ROOT, "profiles", "step_kernel_%s.md" % precision)
+    try:
+        text = open(path).read()
+    except OSError:
+        return None
+    m = re.search(r"traffic_bytes_per_node:\s*([0-9.eE+-]+)", text)
+    hm = re.search(r"kernel_sources_sha256_16:\s*([0-9a-f]+)", text)
+    if not m or not hm or hm.group(1) != kernel_hash():
+        return None
+    return float(m.group(1)) * n_side * n_side
+
+
+class ClockSampler:
+    """nvidia-smi sampling of SM clocks and throttle reasons while running."""
+
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,"
+             "clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+             "clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,"
+             "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index=0):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index),
+                 "--query-gpu=" + self.QUERY, "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=subprocess.PIPE,
+                stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *exc):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+            self.t.join(timeout=2)
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown",
+                 "sw_power_cap"]
+        for line in self.lines:
+            p = [x.strip() for x in line.split(",")]
+            if len(p) < 9:
+                continue
+            try:
+                sm.append(float(p[1]))
+                mx.append(float(p[2]))
+            except ValueError:
+                continue
+            for name, v in zip(names, p[5:9]):
+                if v.lower() == "active":
+                    reasons.add(name)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [],
+                    "samples": 0}
+        sm.sort()
+        return {"sm_mhz": sm[len(sm) // 2], "sm_max_mhz": max(mx),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------
+# GPU measurement
+# ---------------------------------------------------------------------------
+def time_steps(sim, steps, warmup):
+    """Device time (ms) of `steps` launches of the step kernel, measured with
+    CUDA events on the library's stream, after `warmup` steps."""
+    import torch
+    stream = torch.cuda.current_stream()
+    sim.step(warmup)
+    torch.cuda.synchronize()
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    t0.record(stream)
+    sim.step(steps)
+    t1.record(stream)
+    torch.cuda.synchronize()
+    return t0.elapsed_time(t1)
+
+
+def measure_gpu(precision, steps, warmup, rho):
+    import torch
+    from paper_1611_00907_gb300 import Simulation
+    n = rho.shape[0]
+    rho_dev = torch.tensor(rho, device="cuda")
+    sim = Simulation(n, n, precision=precision,
+                     rho_ref=0.15 if "offset" in precision else 0.0,
+                     **EOS_ARGS)
+    with sim:
+        sim.init(rho_dev)
+        del rho_dev
+        ms = time_steps(sim, steps, warmup)
+    return ms
+
+
+def measure_e2e(precision, steps, warmup, rho, check_every):
+    """Same steps through the public API with host buffers."""
+    import numpy as np
+    import torch
+    from paper_1611_00907_gb300 import Simulation
+    n = rho.shape[0]
+    host_rho = torch.from_numpy(np.ascontiguousarray(rho)).pin_memory()
+    out = torch.empty((n, n), dtype=torch.float64).pin_memory()
+    sim = Simulation(n, n, precision=precision, **EOS_ARGS)
+    with sim:
+        sim.init(host_rho.numpy()).step(warmup)
+        sim.reduce()
+        sim.moments()          # staging buffers allocated before timing
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        sim.init(host_rho.numpy())
+        reads = 0
+        for k in range(0, steps, check_every):
+            sim.step(min(check_every, steps - k))
+            sim.reduce()
+            reads += 1
+        m = sim.moments()
+        out.numpy()[...] = m["rho"]
+        dt = time.perf_counter() - t
+    field = n * n * 8
+    return {"value": n * n * steps / dt / 1e6, "unit": "MLUPS",
+            "h2d_bytes_per_step": field / steps,
+            "d2h_bytes_per_step": (4 * field + 32 * reads) / steps,
+            "seconds": dt, "check_every": check_every}
+
+
+def cpu_baseline(budget_s=15.0):
+    """The oracle as it stands (FP64 C) on a 512 x 512 sample of the same
+    workload, all host cores."""
+    import oracle
+    from oracle import thermo
+    from paper_1611_00907_gb300 import inputs
+    cores = os.cpu_count() or 1
+    oracle.set_threads(cores)
+    n = 512
+    e = thermo.make_eos("cs", 1.0, 4.0, 1.0, 0.85)
+    _, rc = thermo.critical_point("cs", 1.0, 4.0)
+    L = oracle.Lattice(n, n, e, 1.0, 0.5)
+    L.init_equilibrium(inputs.spinodal_noise(n, n, rc, 0.01, seed=1))
+    L.step(2)
+    steps, t = 0, time.perf_counter()
+    while time.perf_counter() - t < budget_s:
+        L.step(5)
+        steps += 5
+    dt = time.perf_counter() - t
+    oracle.set_threads(1)
+    return {"value": n * n * steps / dt / 1e6, "unit": "MLUPS",
+            "cores": cores, "kind": "oracle",
+            "sample": "%dx%d CS spinodal, %d steps, FP64 C oracle" % (
+                n, n, steps)}
+
+
+def roofline(precision, ms_per_step, n_nodes, n_side=N_SIDE):
+    peak, src = hbm_peak()
+    achieved = BYTES_PER_LU[precision] * n_nodes / (ms_per_step * 1e-3) / 1e9
+    traffic = recorded_traffic(precision, n_side)
+    return {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak,
+            "unit": "GB/s", "frac": round(achieved / peak, 4),
+            "traffic": traffic, "peak_source": src,
+            "bytes_per_update": BYTES_PER_LU[precision]}
+
+
+# ---------------------------------------------------------------------------
+def dist_setup():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        backend = "nccl" if torch.cuda.is_available() else "gloo"
+        dist.init_process_group(backend)
+        if torch.cuda.is_available():
+            torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    return rank, world
+
+
+def max_over_ranks(value, world):
+    """Largest value over all ranks (the job's wall time)."""
+    if world == 1:
+        return value
+    import torch
+    import torch.distributed as dist
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([value], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return 0
+    base = cpu_baseline(budget_s=max(5.0, min(60.0, 2.0 * args.steps)))
+    line = {"impl": "reference", "metric": "MLUPS", "value": base["value"],
+            "unit": "MLUPS", "n_gpus": args.gpus, "steps": args.steps,
+            "warmup": args.warmup, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": workload_config(),
+            "cpu_baseline": base,
+            "e2e": {"value": base["value"], "unit": "MLUPS",
+                    "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=2000)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", default="cuda", choices=["cuda", "reference"])
+    ap.add_argument("--precision", default="f32",
+                    choices=["f32", "f32_offset", "f16_offset", "f64"])
+    ap.add_argument("--fp64-steps", type=int, default=200)
+    ap.add_argument("--check-every", type=int, default=100)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--n", type=int, default=N_SIDE,
+                    help="lattice side (profiling runs use smaller cases)")
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+    rank, world = dist_setup()
+    if args.impl == "reference":
+        return run_reference(args, rank, world)
+
+    import torch
+    if not torch.cuda.is_available():
+        print(json.dumps({"error": "no CUDA device"}))
+        return 1
+    import __graft_entry__
+    __graft_entry__.build()
+    rho = initial_rho(args.n)
+    n_nodes = rho.size
+
+    barrier(world)
+    with ClockSampler(int(os.environ.get("LOCAL_RANK", "0"))) as clocks:
+        ms = measure_gpu(args.precision, args.steps, args.warmup, rho)
+    ms = max_over_ranks(ms, world)
+    ms_step = ms / args.steps
+    value = world * n_nodes * args.steps / (ms * 1e-3) / 1e6
+
+    fp64 = None
+    if args.fp64_steps > 0:
+        fp64_ms = measure_gpu("f64", args.fp64_steps, 3, rho) / args.fp64_steps
+        fp64_ms = max_over_ranks(fp64_ms, world)
+        fp64 = {"value": world * n_nodes / (fp64_ms * 1e-3) / 1e6,
+                "unit": "MLUPS", "ms_per_step": fp64_ms,
+                "steps": args.fp64_steps,
+                "roofline": roofline("f64", fp64_ms, n_nodes, args.n)}
+
+    e2e = None
+    if not args.no_e2e:
+        e2e = measure_e2e(args.precision, args.steps, args.warmup, rho,
+                          args.check_every)
+        e2e["value"] = world * e2e["value"]
+
+    base = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        base = cpu_baseline()
+
+    if rank == 0:
+        line = {"metric": "MLUPS", "value": round(value, 1), "unit": "MLUPS",
+                "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+                "ms_per_step": ms_step, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None,
+                "dtype": args.precision, "data": "synthetic",
+                "config": workload_config(args.n),
+                "roofline": roofline(args.precision, ms_step, n_nodes, args.n),
+                "fp64": fp64, "e2e": e2e, "cpu_baseline": base,
+                "gpu_launches": args.steps, "clocks": clocks.summary()}
+        print(json.dumps(line))
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,167 @@
+/*
+ * cplbm: chemical-potential lattice Boltzmann method for nonideal fluids on
+ * one GPU (sm_103a), after Wen, Zhou, He, Zhang, Fang, arXiv 1611.00907.
+ *
+ * C ABI of the D2Q9 time step.  One call of lbm_step advances the
+ * distributions by the paper's update:
+ *   density             rho = sum_i f_i                        (Sec. II)
+ *   solid-row density    weighted average of Eq. 28              (Sec. IV)
+ *   chemical potential   mu = psi'(rho) - kappa lap(rho)         (Eq. 8; psi'
+ *                        from Eq. 18 vdW, Eq. 21 RK/RKS, Eq. 24 PR,
+ *                        Eq. 27 CS); solid rows carry the surface value
+ *                        (Sec. IV, Sec. V)
+ *   nonideal force       F = -rho grad(mu) + grad(cs^2 rho)      (Eq. 12)
+ *   collision            BGK, Eq. 13, towards Eq. 14 with the equilibrium
+ *                        velocity u + tau F / rho                (Sec. II)
+ *   streaming            with halfway bounce-back on solid rows  (Sec. IV)
+ * Gradients and Laplacians are the isotropic D2Q9 stencils
+ *   grad(phi) = 3 sum_i w_i phi(x + e_i) e_i,
+ *   lap(phi)  = 6 sum_i w_i (phi(x + e_i) - phi(x)).
+ *
+ * Conventions.
+ *  - Fields passed in or out are double, row-major [ny][nx], node (x, y) at
+ *    index y * nx + x, lattice directions e_0 = (0,0), e_1..4 = (1,0),
+ *    (0,1), (-1,0), (0,-1), e_5..8 = (1,1), (-1,1), (-1,-1), (1,-1).
+ *  - x is always periodic.  walls == 0: y periodic.  walls == 1: rows y = 0
+ *    and y = ny - 1 are solid; fluid rows are 1..ny-2.
+ *  - The caller owns every buffer it passes; the library never keeps a
+ *    caller pointer past the call.  `on_device` != 0 means the pointer is
+ *    device memory of the context's GPU, else host memory.
+ *  - Every function returns a status and never aborts or throws.  After an
+ *    error, lbm_last_error() describes it.  Calls on one context are not
+ *    thread-safe; separate contexts are independent.
+ *  - Work is queued on the context's CUDA stream.  lbm_step returns without
+ *    waiting; lbm_moments, lbm_reduce, lbm_get_populations and the state
+ *    calls wait for the stream.
+ */
+#ifndef CPLBM_H
+#define CPLBM_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct lbm_ctx lbm_ctx;
+
+typedef enum {
+    LBM_OK = 0,
+    LBM_ERR_ARG = -1,     /* invalid argument or configuration */
+    LBM_ERR_CUDA = -2,    /* a CUDA runtime call failed */
+    LBM_ERR_OOM = -3,     /* device or host allocation failed */
+    LBM_ERR_NUMERIC = -4, /* non-finite value found by lbm_reduce */
+    LBM_ERR_STATE = -5    /* call out of order (e.g. step before init) */
+} lbm_status;
+
+typedef enum {
+    LBM_EOS_VDW = 0, /* van der Waals, Eqs. 16-18 */
+    LBM_EOS_CS = 1,  /* Carnahan-Starling, Eqs. 25-27 */
+    LBM_EOS_PR = 2,  /* Peng-Robinson, Eqs. 22-24 */
+    LBM_EOS_RKS = 3  /* Redlich-Kwong-Soave, Eqs. 19-21 */
+} lbm_eos;
+
+/* Storage and arithmetic of the distributions.
+ *  LBM_F64:        FP64 storage and arithmetic.
+ *  LBM_F32:        FP32 storage and arithmetic.
+ *  LBM_F32_OFFSET: FP32 arithmetic; each f_i is stored as f_i - w_i rho_ref
+ *                  and the density as rho - rho_ref.
+ *  LBM_F16_OFFSET: FP32 arithmetic; offsets stored as FP16, density as FP32.
+ * The global reductions of lbm_reduce always accumulate in FP64. */
+typedef enum {
+    LBM_F64 = 0,
+    LBM_F32 = 1,
+    LBM_F32_OFFSET = 2,
+    LBM_F16_OFFSET = 3
+} lbm_precision;
+
+typedef struct {
+    int nx, ny;     /* lattice size, solid rows included; nx >= 5, ny >= 5 */
+    int walls;      /* 0 periodic in y, 1 solid rows y = 0 and y = ny - 1 */
+    double tau;     /* BGK relaxation time (Eq. 13), > 0.5 */
+    double kappa;   /* square-gradient coefficient (Eq. 1, Eq. 8), >= 0 */
+    double rho_ref; /* reference density of the offset precisions */
+    int precision;  /* lbm_precision */
+    void *stream;   /* cudaStream_t to queue work on; NULL: legacy stream */
+    int device;     /* CUDA device ordinal */
+} lbm_config;
+
+/* Allocate a context and its device state for cfg.  *out receives the
+ * context (NULL on error).  Device memory per lattice node: 8 distributions
+ * in the storage type plus three densities. */
+lbm_status lbm_create(const lbm_config *cfg, lbm_ctx **out);
+
+/* Select the equation of state (Sec. III): a, b, R as in Eqs. 16, 19, 22,
+ * 25; T = T_over_Tc * T_c, where T_c is the EOS's critical temperature with
+ * alpha = 1, found by the library; omega is the acentric factor of the
+ * alpha(T) of PR (Eq. 22 text) and RKS (Eq. 19 text) and is ignored by vdW
+ * and CS.  Must be called before lbm_init. */
+lbm_status lbm_set_eos(lbm_ctx *ctx, int eos, double a, double b, double R,
+                       double T_over_Tc, double omega);
+
+/* Surface chemical potentials of the solid rows (Sec. IV, Sec. V).  The
+ * bottom row y = 0 carries mu_bottom.  top_mode 0: the top row copies the
+ * chemical potential of its fluid neighbour (Sec. V); top_mode 1: it
+ * carries mu_top.  Ignored when walls == 0.  Default: 0, mode 0. */
+lbm_status lbm_set_wall_mu(lbm_ctx *ctx, double mu_bottom, int top_mode,
+                           double mu_top);
+
+/* Set the state to equilibrium populations f_i = f_i^eq(rho, u) (Eq. 14)
+ * at every fluid node, and the step counter to 0.  rho must be positive and
+ * below the EOS's repulsive pole at fluid nodes; ux and uy may be NULL
+ * (zero velocity).  Values on solid rows are ignored. */
+lbm_status lbm_init(lbm_ctx *ctx, const double *rho, const double *ux,
+                    const double *uy, int on_device);
+
+/* Queue nsteps (>= 0) time steps.  Returns without waiting for the GPU. */
+lbm_status lbm_step(lbm_ctx *ctx, int nsteps);
+
+/* Macroscopic fields of the current state: rho (solid rows: Eq. 28), the
+ * fluid velocity v = u + F / (2 rho) (Sec. II; zero on solid rows) and mu
+ * (solid rows: the wall values the step uses).  Any pointer may be NULL. */
+lbm_status lbm_moments(lbm_ctx *ctx, double *rho, double *vx, double *vy,
+                       double *mu, int on_device);
+
+/* Distributions of the current state in natural order, FP64
+ * [9][ny][nx] (solid rows zero). */
+lbm_status lbm_get_populations(lbm_ctx *ctx, double *f, int on_device);
+
+/* FP64 global reductions over fluid nodes: out[0] = sum rho,
+ * out[1], out[2] = sum rho v, out[3] = max |rho - rho at the previous
+ * lbm_reduce call| (the first call after lbm_init reports the change since
+ * the initial state).  LBM_ERR_NUMERIC if a non-finite value is found.
+ * out is host memory. */
+lbm_status lbm_reduce(lbm_ctx *ctx, double out[4]);
+
+/* Checkpoint: the raw device state (distributions, current density, step
+ * parity) copied to or from host memory, for a bitwise resume in the same
+ * precision and geometry.  lbm_state_size() gives the byte count. */
+size_t lbm_state_size(const lbm_ctx *ctx);
+lbm_status lbm_get_state(lbm_ctx *ctx, void *buf, size_t bytes);
+lbm_status lbm_set_state(lbm_ctx *ctx, const void *buf, size_t bytes);
+
+/* Steps taken since lbm_init or lbm_set_state's saved counter. */
+long long lbm_step_count(const lbm_ctx *ctx);
+
+/* Absolute temperature, alpha(T) and critical point of the selected EOS. */
+lbm_status lbm_eos_info(const lbm_ctx *ctx, double *T, double *alpha,
+                        double *Tc, double *rhoc);
+
+/* Critical point (T_c, rho_c) of an EOS with alpha = 1: both the first and
+ * the second density derivative of p0 vanish (Sec. III's reduced
+ * variables).  Host-only helper. */
+lbm_status lbm_eos_critical(int eos, double a, double b, double R,
+                            double *Tc, double *rhoc);
+
+/* Release the context and its device memory.  NULL is ignored. */
+void lbm_destroy(lbm_ctx *ctx);
+
+/* Message of the last error on ctx (or of the last failed lbm_create or
+ * lbm_eos_critical when ctx is NULL).  Never NULL. */
+const char *lbm_last_error(const lbm_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* CPLBM_H */

@@ -1,0 +1,187 @@
+"""GB300 implementation of the chemical-potential lattice Boltzmann method
+for nonideal fluids (Wen et al., arXiv 1611.00907).
+
+The numerical work runs in libcplbm.so (CUDA, sm_103a) behind the C ABI of
+include/cplbm.h; this module only marshals arguments.  PyTorch is used for
+device buffers and the CUDA stream when the caller passes CUDA tensors.
+"""
+import ctypes as C
+
+import numpy as np
+
+from . import _lib
+from ._lib import EOS, PRECISION, LbmError, check
+
+__all__ = ["Simulation", "LbmError", "eos_critical", "EOS", "PRECISION"]
+
+
+def eos_critical(eos, a, b, R=1.0):
+    """(T_c, rho_c) of an EOS with alpha = 1, from the library."""
+    lib = _lib.load()
+    Tc, rc = C.c_double(), C.c_double()
+    check(lib.lbm_eos_critical(EOS[eos] if isinstance(eos, str) else int(eos),
+                               float(a), float(b), float(R), C.byref(Tc),
+                               C.byref(rc)))
+    return Tc.value, rc.value
+
+
+def _is_torch(x):
+    return type(x).__module__.startswith("torch")
+
+
+def _arg(x, n):
+    """(pointer, on_device, keepalive) for a [ny][nx] float64 field."""
+    if x is None:
+        return None, None, None
+    if _is_torch(x):
+        import torch
+        if x.dtype != torch.float64 or not x.is_contiguous() or x.numel() != n:
+            raise ValueError("device fields must be contiguous float64 [ny, nx]")
+        return x.data_ptr(), 1 if x.is_cuda else 0, x
+    a = np.ascontiguousarray(x, dtype=np.float64)
+    if a.size != n:
+        raise ValueError("field has %d values, expected %d" % (a.size, n))
+    return a.ctypes.data, 0, a
+
+
+class Simulation:
+    """One D2Q9 lattice on one GPU.
+
+    Parameters follow the paper: eos in {'vdw', 'cs', 'pr', 'rks'} with a, b,
+    R (Sec. III), reduced temperature Tr = T / T_c, acentric factor omega
+    (PR, RKS), relaxation time tau (Eq. 13), kappa (Eq. 8).  walls=True puts
+    solid rows at y = 0 and y = ny - 1 with surface chemical potential
+    mu_bottom (top: copies its neighbour, top_mode=0, or mu_top, top_mode=1).
+    precision in {'f64', 'f32', 'f32_offset', 'f16_offset'}; rho_ref is the
+    reference density of the offset storages.
+    """
+
+    def __init__(self, nx, ny, eos="cs", a=1.0, b=4.0, R=1.0, Tr=0.85,
+                 omega=0.344, tau=1.0, kappa=0.5, walls=False,
+                 precision="f64", rho_ref=0.0, mu_bottom=0.0, top_mode=0,
+                 mu_top=0.0, device=0, stream=None):
+        self._lib = _lib.load()
+        self.nx, self.ny, self.walls = int(nx), int(ny), bool(walls)
+        self.precision = precision
+        self.device = int(device)
+        if stream is None:
+            try:
+                import torch
+                if torch.cuda.is_available():
+                    stream = torch.cuda.current_stream(self.device).cuda_stream
+            except ImportError:
+                stream = None
+        cfg = _lib.LbmConfig(self.nx, self.ny, int(self.walls), float(tau),
+                             float(kappa), float(rho_ref), PRECISION[precision],
+                             C.c_void_p(stream) if stream else None,
+                             self.device)
+        ctx = C.c_void_p()
+        check(self._lib.lbm_create(C.byref(cfg), C.byref(ctx)))
+        self._ctx = ctx
+        try:
+            check(self._lib.lbm_set_eos(ctx, EOS[eos], float(a), float(b),
+                                        float(R), float(Tr), float(omega)),
+                  ctx)
+            check(self._lib.lbm_set_wall_mu(ctx, float(mu_bottom),
+                                            int(top_mode), float(mu_top)), ctx)
+        except Exception:
+            self.close()
+            raise
+
+    # ------------------------------------------------------------------
+    def close(self):
+        if getattr(self, "_ctx", None):
+            self._lib.lbm_destroy(self._ctx)
+            self._ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    @property
+    def n(self):
+        return self.nx * self.ny
+
+    def _check(self, status):
+        return check(status, self._ctx)
+
+    # ------------------------------------------------------------------
+    def set_wall_mu(self, mu_bottom, top_mode=0, mu_top=0.0):
+        self._check(self._lib.lbm_set_wall_mu(self._ctx, float(mu_bottom),
+                                              int(top_mode), float(mu_top)))
+
+    def init(self, rho, ux=None, uy=None):
+        """Equilibrium state (Eq. 14) from [ny, nx] float64 fields given as
+        numpy arrays (host) or CUDA tensors (device)."""
+        pr, dr, kr = _arg(rho, self.n)
+        px, dx, kx = _arg(ux, self.n)
+        py, dy, ky = _arg(uy, self.n)
+        kinds = {d for d in (dr, dx, dy) if d is not None}
+        if len(kinds) != 1:
+            raise ValueError("rho, ux, uy must all be host or all device")
+        self._check(self._lib.lbm_init(self._ctx, pr, px, py, dr))
+        del kr, kx, ky
+        return self
+
+    def step(self, n=1):
+        self._check(self._lib.lbm_step(self._ctx, int(n)))
+        return self
+
+    @property
+    def step_count(self):
+        return int(self._lib.lbm_step_count(self._ctx))
+
+    def eos_info(self):
+        """dict(T, alpha, Tc, rhoc) of the selected EOS."""
+        v = [C.c_double() for _ in range(4)]
+        self._check(self._lib.lbm_eos_info(self._ctx, *[C.byref(x) for x in v]))
+        return dict(zip(("T", "alpha", "Tc", "rhoc"), (x.value for x in v)))
+
+    def moments(self, device=False):
+        """dict of rho, vx, vy, mu [ny, nx] float64: numpy arrays, or CUDA
+        tensors when device=True."""
+        if device:
+            import torch
+            out = {k: torch.empty((self.ny, self.nx), dtype=torch.float64,
+                                  device="cuda:%d" % self.device)
+                   for k in ("rho", "vx", "vy", "mu")}
+            ptr = [out[k].data_ptr() for k in ("rho", "vx", "vy", "mu")]
+            self._check(self._lib.lbm_moments(self._ctx, *ptr, 1))
+            return out
+        out = {k: np.empty((self.ny, self.nx)) for k in ("rho", "vx", "vy",
+                                                          "mu")}
+        ptr = [out[k].ctypes.data for k in ("rho", "vx", "vy", "mu")]
+        self._check(self._lib.lbm_moments(self._ctx, *ptr, 0))
+        return out
+
+    def populations(self):
+        """Natural-order FP64 distributions [9, ny, nx] (numpy)."""
+        f = np.empty((9, self.ny, self.nx))
+        self._check(self._lib.lbm_get_populations(self._ctx, f.ctypes.data, 0))
+        return f
+
+    def reduce(self):
+        """(mass, momentum x, momentum y, max |rho - rho at last call|)."""
+        out = (C.c_double * 4)()
+        self._check(self._lib.lbm_reduce(self._ctx, out))
+        return tuple(out)
+
+    def get_state(self):
+        n = self._lib.lbm_state_size(self._ctx)
+        buf = np.empty(n, dtype=np.uint8)
+        self._check(self._lib.lbm_get_state(self._ctx, buf.ctypes.data, n))
+        return buf
+
+    def set_state(self, buf):
+        buf = np.ascontiguousarray(buf, dtype=np.uint8)
+        self._check(self._lib.lbm_set_state(self._ctx, buf.ctypes.data,
+                                            buf.size))
+        return self

@@ -1,0 +1,549 @@
+// C ABI of the cplbm library (include/cplbm.h): context and device memory,
+// argument checks, EOS set-up and the host side of every call.
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+
+#include "../../include/cplbm.h"
+#include "cplbm_internal.h"
+
+using namespace cplbm;
+
+struct lbm_ctx {
+    Lattice L{};
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    long long t = 0;
+    bool eos_set = false, initialized = false;
+    double T = 0, alpha = 1, Tc = 0, rhoc = 0;
+    double *d_red = nullptr;   // 4 reduction slots
+    int *d_bad = nullptr;      // error counter
+    double *d_prev = nullptr;  // density snapshot of lbm_reduce [ny][nx]
+    double *d_tmp = nullptr;   // staging for host-side field transfers
+    size_t tmp_bytes = 0;
+    std::string err;
+};
+
+static thread_local std::string g_err;
+
+namespace {
+
+lbm_status fail(lbm_ctx *c, lbm_status s, const char *fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    (c ? c->err : g_err) = buf;
+    return s;
+}
+
+#define CUDA_TRY(c, call)                                                    \
+    do {                                                                     \
+        cudaError_t e_ = (call);                                             \
+        if (e_ != cudaSuccess)                                               \
+            return fail((c), e_ == cudaErrorMemoryAllocation ? LBM_ERR_OOM   \
+                                                             : LBM_ERR_CUDA, \
+                        "%s: %s", #call, cudaGetErrorString(e_));            \
+    } while (0)
+
+// ---------------------------------------------------------------------------
+// Thermodynamics on the host.  p0(rho) of Eqs. 16, 19, 22, 25 is evaluated
+// on second-order forward-mode dual numbers, which carry p0, dp0/drho and
+// d2p0/drho2 through the printed formula exactly (to rounding).
+// ---------------------------------------------------------------------------
+struct D2 {
+    double v, d, dd;
+};
+D2 operator+(D2 a, D2 b) { return {a.v + b.v, a.d + b.d, a.dd + b.dd}; }
+D2 operator-(D2 a, D2 b) { return {a.v - b.v, a.d - b.d, a.dd - b.dd}; }
+D2 operator*(D2 a, D2 b)
+{
+    return {a.v * b.v, a.d * b.v + a.v * b.d,
+            a.dd * b.v + 2 * a.d * b.d + a.v * b.dd};
+}
+D2 recip(D2 b)
+{
+    const double i = 1.0 / b.v;
+    return {i, -b.d * i * i, 2 * b.d * b.d * i * i * i - b.dd * i * i};
+}
+D2 operator/(D2 a, D2 b) { return a * recip(b); }
+D2 cst(double c) { return {c, 0, 0}; }
+
+// p0 with temperature factor RT and attraction aa (a alpha).
+D2 p0_dual(int kind, double aa, double b, double RT, D2 rho)
+{
+    const D2 one = cst(1), br = cst(b) * rho;
+    switch (kind) {
+    case EOS_VDW:
+        return cst(RT) * rho / (one - br) - cst(aa) * rho * rho;
+    case EOS_RKS:
+        return cst(RT) * rho / (one - br) - cst(aa) * rho * rho / (one + br);
+    case EOS_PR:
+        return cst(RT) * rho / (one - br) -
+               cst(aa) * rho * rho / (one + cst(2) * br - br * br);
+    default: {  // CS
+        const D2 h = cst(0.25) * br;
+        const D2 q = one - h;
+        return cst(RT) * rho * (one + h + h * h - h * h * h) / (q * q * q) -
+               cst(aa) * rho * rho;
+    }
+    }
+}
+
+double pole(int kind, double b) { return (kind == EOS_CS ? 4.0 : 1.0) / b; }
+
+// Critical point with alpha = 1.  p0 = T A(rho) - B(rho): A from
+// p0(RT = R, aa = 0), B from -p0(RT = 0, aa = a).  Where p0' = p0'' = 0,
+// T = B'/A' = B''/A'', so rho_c is the root of B' A'' - B'' A' (one sign
+// change on (0, pole)); bisection to the last bit.
+bool critical(int kind, double a, double b, double R, double *Tc, double *rc)
+{
+    auto g = [&](double r, double *T) {
+        const D2 A = p0_dual(kind, 0.0, b, R, D2{r, 1, 0});
+        const D2 B = p0_dual(kind, a, b, 0.0, D2{r, 1, 0});
+        const double A1 = A.d, A2 = A.dd, B1 = -B.d, B2 = -B.dd;
+        if (T) *T = B1 / A1;
+        return B1 * A2 - B2 * A1;
+    };
+    double lo = 1e-9 * pole(kind, b), hi = (1 - 1e-9) * pole(kind, b);
+    double glo = g(lo, nullptr), ghi = g(hi, nullptr);
+    if (!(glo * ghi < 0)) return false;
+    for (int it = 0; it < 2000; ++it) {
+        const double mid = 0.5 * (lo + hi);
+        if (mid <= lo || mid >= hi) break;
+        const double gm = g(mid, nullptr);
+        if ((gm < 0) == (glo < 0)) { lo = mid; glo = gm; } else { hi = mid; }
+    }
+    *rc = 0.5 * (lo + hi);
+    g(*rc, Tc);
+    return std::isfinite(*Tc) && *Tc > 0;
+}
+
+// alpha(T) of PR (text under Eq. 22) and RKS (text under Eq. 19).
+double alpha_of(int kind, double Tr, double omega)
+{
+    double m;
+    if (kind == EOS_PR) m = 0.37464 + 1.54226 * omega - 0.26992 * omega * omega;
+    else if (kind == EOS_RKS) m = 0.480 + 1.574 * omega - 0.176 * omega * omega;
+    else return 1.0;
+    const double s = 1.0 + m * (1.0 - std::sqrt(Tr));
+    return s * s;
+}
+
+lbm_status ensure_tmp(lbm_ctx *c, size_t bytes)
+{
+    if (c->tmp_bytes >= bytes) return LBM_OK;
+    if (c->d_tmp) cudaFree(c->d_tmp);
+    c->d_tmp = nullptr;
+    c->tmp_bytes = 0;
+    CUDA_TRY(c, cudaMalloc(&c->d_tmp, bytes));
+    c->tmp_bytes = bytes;
+    return LBM_OK;
+}
+
+size_t ring_elems(const Lattice &L)
+{
+    const size_t a = (size_t)L.nyf * L.pitch, b = (size_t)L.pitch * L.nyf_pad;
+    return a > b ? a : b;
+}
+
+void free_all(lbm_ctx *c)
+{
+    Lattice &L = c->L;
+    cudaFree(L.pops);
+    for (int k = 0; k < 2; ++k) {
+        cudaFree(L.rho[k]);
+        for (int r = 0; r < R_COUNT; ++r) cudaFree(L.ring[k][r]);
+    }
+    cudaFree(c->d_red);
+    cudaFree(c->d_bad);
+    cudaFree(c->d_prev);
+    cudaFree(c->d_tmp);
+}
+
+struct StateHeader {
+    char magic[8];  // "CPLBMST1"
+    int nx, ny, walls, precision;
+    long long t;
+};
+
+}  // namespace
+
+extern "C" {
+
+lbm_status lbm_create(const lbm_config *cfg, lbm_ctx **out)
+{
+    if (out) *out = nullptr;
+    if (!cfg || !out) return fail(nullptr, LBM_ERR_ARG, "null argument");
+    if (cfg->nx < 5 || cfg->ny < 5)
+        return fail(nullptr, LBM_ERR_ARG, "nx and ny must be >= 5 (got %d, %d)",
+                    cfg->nx, cfg->ny);
+    if (cfg->walls != 0 && cfg->walls != 1)
+        return fail(nullptr, LBM_ERR_ARG, "walls must be 0 or 1");
+    if (cfg->walls && cfg->ny < 7)
+        return fail(nullptr, LBM_ERR_ARG, "walls need ny >= 7");
+    if (!(cfg->tau > 0.5) || !std::isfinite(cfg->tau))
+        return fail(nullptr, LBM_ERR_ARG, "tau must be > 0.5 (got %g)", cfg->tau);
+    if (!(cfg->kappa >= 0) || !std::isfinite(cfg->kappa))
+        return fail(nullptr, LBM_ERR_ARG, "kappa must be >= 0");
+    if (cfg->precision < LBM_F64 || cfg->precision > LBM_F16_OFFSET)
+        return fail(nullptr, LBM_ERR_ARG, "unknown precision %d", cfg->precision);
+    if (!std::isfinite(cfg->rho_ref))
+        return fail(nullptr, LBM_ERR_ARG, "rho_ref must be finite");
+    if ((long long)cfg->nx * cfg->ny > (1LL << 31))
+        return fail(nullptr, LBM_ERR_ARG, "lattice larger than 2^31 nodes");
+
+    lbm_ctx *c = new (std::nothrow) lbm_ctx();
+    if (!c) return fail(nullptr, LBM_ERR_OOM, "host allocation failed");
+    c->device = cfg->device;
+    c->stream = (cudaStream_t)cfg->stream;
+    cudaError_t e = cudaSetDevice(cfg->device);
+    if (e != cudaSuccess) {
+        delete c;
+        return fail(nullptr, LBM_ERR_CUDA, "cudaSetDevice(%d): %s", cfg->device,
+                    cudaGetErrorString(e));
+    }
+    Lattice &L = c->L;
+    L.nx = cfg->nx;
+    L.ny = cfg->ny;
+    L.walls = cfg->walls;
+    L.nyf = cfg->walls ? cfg->ny - 2 : cfg->ny;
+    L.pitch = (cfg->nx + 31) / 32 * 32;
+    L.nyf_pad = (L.nyf + 31) / 32 * 32;
+    L.plane = (long long)L.nyf * L.pitch;
+    L.tau = cfg->tau;
+    L.kappa = cfg->kappa;
+    L.rho_ref = (cfg->precision == LBM_F32_OFFSET ||
+                 cfg->precision == LBM_F16_OFFSET) ? cfg->rho_ref : 0.0;
+    L.precision = cfg->precision;
+    L.top_mode = 0;
+
+    const size_t pb = pop_bytes(L.precision), rb = rho_bytes(L.precision);
+    const size_t nring = ring_elems(L);
+    lbm_status st = LBM_OK;
+    auto alloc = [&](void **p, size_t bytes) {
+        if (st != LBM_OK) return;
+        cudaError_t ea = cudaMalloc(p, bytes);
+        if (ea != cudaSuccess) {
+            *p = nullptr;
+            st = fail(nullptr, LBM_ERR_OOM, "cudaMalloc(%zu): %s", bytes,
+                      cudaGetErrorString(ea));
+        }
+    };
+    alloc(&L.pops, 8 * (size_t)L.plane * pb);
+    for (int k = 0; k < 2; ++k) {
+        alloc(&L.rho[k], (size_t)L.plane * rb);
+        for (int r = 0; r < R_COUNT; ++r) alloc(&L.ring[k][r], nring * rb);
+    }
+    alloc((void **)&c->d_red, 4 * sizeof(double));
+    alloc((void **)&c->d_bad, sizeof(int));
+    alloc((void **)&c->d_prev, (size_t)L.nx * L.ny * sizeof(double));
+    if (st != LBM_OK) {
+        free_all(c);
+        delete c;
+        return st;
+    }
+    *out = c;
+    return LBM_OK;
+}
+
+lbm_status lbm_eos_critical(int eos, double a, double b, double R, double *Tc,
+                            double *rhoc)
+{
+    if (!Tc || !rhoc) return fail(nullptr, LBM_ERR_ARG, "null output");
+    if (eos < LBM_EOS_VDW || eos > LBM_EOS_RKS)
+        return fail(nullptr, LBM_ERR_ARG, "unknown EOS %d", eos);
+    if (!(a > 0 && b > 0 && R > 0))
+        return fail(nullptr, LBM_ERR_ARG, "a, b, R must be positive");
+    if (!critical(eos, a, b, R, Tc, rhoc))
+        return fail(nullptr, LBM_ERR_NUMERIC, "critical point not found");
+    return LBM_OK;
+}
+
+lbm_status lbm_set_eos(lbm_ctx *c, int eos, double a, double b, double R,
+                       double T_over_Tc, double omega)
+{
+    if (!c) return fail(nullptr, LBM_ERR_ARG, "null context");
+    if (eos < LBM_EOS_VDW || eos > LBM_EOS_RKS)
+        return fail(c, LBM_ERR_ARG, "unknown EOS %d", eos);
+    if (!(a > 0 && b > 0 && R > 0))
+        return fail(c, LBM_ERR_ARG, "a, b, R must be positive");
+    if (!(T_over_Tc > 0) || !std::isfinite(T_over_Tc) || !std::isfinite(omega))
+        return fail(c, LBM_ERR_ARG, "T_over_Tc must be positive and finite");
+    double Tc, rc;
+    if (!critical(eos, a, b, R, &Tc, &rc))
+        return fail(c, LBM_ERR_NUMERIC, "critical point not found");
+    c->Tc = Tc;
+    c->rhoc = rc;
+    c->T = T_over_Tc * Tc;
+    c->alpha = alpha_of(eos, T_over_Tc, omega);
+    EosParams &E = c->L.eos;
+    E.kind = eos;
+    E.a = a;
+    E.b = b;
+    E.RT = R * c->T;
+    E.aalpha = a * c->alpha;
+    c->eos_set = true;
+    return LBM_OK;
+}
+
+lbm_status lbm_eos_info(const lbm_ctx *c, double *T, double *alpha,
+                        double *Tc, double *rhoc)
+{
+    if (!c) return fail(nullptr, LBM_ERR_ARG, "null context");
+    if (!c->eos_set)
+        return fail(const_cast<lbm_ctx *>(c), LBM_ERR_STATE, "EOS not set");
+    if (T) *T = c->T;
+    if (alpha) *alpha = c->alpha;
+    if (Tc) *Tc = c->Tc;
+    if (rhoc) *rhoc = c->rhoc;
+    return LBM_OK;
+}
+
+lbm_status lbm_set_wall_mu(lbm_ctx *c, double mu_bottom, int top_mode,
+                           double mu_top)
+{
+    if (!c) return fail(nullptr, LBM_ERR_ARG, "null context");
+    if (top_mode != 0 && top_mode != 1)
+        return fail(c, LBM_ERR_ARG, "top_mode must be 0 or 1");
+    if (!std::isfinite(mu_bottom) || !std::isfinite(mu_top))
+        return fail(c, LBM_ERR_ARG, "surface chemical potentials must be finite");
+    c->L.mu_bottom = mu_bottom;
+    c->L.top_mode = top_mode;
+    c->L.mu_top = mu_top;
+    return LBM_OK;
+}
+
+lbm_status lbm_init(lbm_ctx *c, const double *rho, const double *ux,
+                    const double *uy, int on_device)
+{
+    if (!c) return fail(nullptr, LBM_ERR_ARG, "null context");
+    if (!rho) return fail(c, LBM_ERR_ARG, "rho is required");
+    if (!c->eos_set) return fail(c, LBM_ERR_STATE, "lbm_set_eos must come first");
+    CUDA_TRY(c, cudaSetDevice(c->device));
+    Lattice &L = c->L;
+    const size_t field = (size_t)L.nx * L.ny * sizeof(double);
+    const double *drho = rho, *dux = ux, *duy = uy;
+    if (!on_device) {
+        lbm_status s = ensure_tmp(c, 3 * field);
+        if (s != LBM_OK) return s;
+        double *t0 = c->d_tmp, *t1 = t0 + (size_t)L.nx * L.ny,
+               *t2 = t1 + (size_t)L.nx * L.ny;
+        CUDA_TRY(c, cudaMemcpyAsync(t0, rho, field, cudaMemcpyHostToDevice, c->stream));
+        drho = t0;
+        dux = duy = nullptr;
+        if (ux) {
+            CUDA_TRY(c, cudaMemcpyAsync(t1, ux, field, cudaMemcpyHostToDevice, c->stream));
+            dux = t1;
+        }
+        if (uy) {
+            CUDA_TRY(c, cudaMemcpyAsync(t2, uy, field, cudaMemcpyHostToDevice, c->stream));
+            duy = t2;
+        }
+    }
+    const size_t rb = rho_bytes(L.precision), nring = ring_elems(L);
+    for (int k = 0; k < 2; ++k) {
+        CUDA_TRY(c, cudaMemsetAsync(L.rho[k], 0, (size_t)L.plane * rb, c->stream));
+        for (int r = 0; r < R_COUNT; ++r)
+            CUDA_TRY(c, cudaMemsetAsync(L.ring[k][r], 0, nring * rb, c->stream));
+    }
+    CUDA_TRY(c, cudaMemsetAsync(c->d_bad, 0, sizeof(int), c->stream));
+    CUDA_TRY(c, launch_init(L, drho, dux, duy, c->d_bad, c->stream));
+    // the reduction snapshot starts at the initial density
+    CUDA_TRY(c, cudaMemsetAsync(c->d_prev, 0, field, c->stream));
+    CUDA_TRY(c, launch_macro(L, 0, 0, c->d_prev, nullptr, nullptr, nullptr,
+                             nullptr, nullptr, nullptr, c->stream));
+    int bad = 0;
+    CUDA_TRY(c, cudaMemcpyAsync(&bad, c->d_bad, sizeof(int), cudaMemcpyDeviceToHost,
+                                c->stream));
+    CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+    c->t = 0;
+    if (bad) {
+        c->initialized = false;
+        return fail(c, LBM_ERR_ARG,
+                    "%d fluid node(s) with density outside (0, %g) or non-finite "
+                    "velocity", bad, pole(L.eos.kind, L.eos.b));
+    }
+    c->initialized = true;
+    return LBM_OK;
+}
+
+lbm_status lbm_step(lbm_ctx *c, int nsteps)
+{
+    if (!c) return fail(nullptr, LBM_ERR_ARG, "null context");
+    if (nsteps < 0) return fail(c, LBM_ERR_ARG, "nsteps must be >= 0");
+    if (!c->initialized) return fail(c, LBM_ERR_STATE, "lbm_init must come first");
+    CUDA_TRY(c, cudaSetDevice(c->device));
+    for (int k = 0; k < nsteps; ++k) {
+        const int p = (int)(c->t & 1);
+        CUDA_TRY(c, launch_step(c->L, p, p, c->stream));
+        ++c->t;
+    }
+    return LBM_OK;
+}
+
+lbm_status lbm_moments(lbm_ctx *c, double *rho, double *vx, double *vy,
+                       double *mu, int on_device)
+{
+    if (!c) return fail(nullptr, LBM_ERR_ARG, "null context");
+    if (!c->initialized) return fail(c, LBM_ERR_STATE, "lbm_init must come first");
+    CUDA_TRY(c, cudaSetDevice(c->device));
+    Lattice &L = c->L;
+    const int p = (int)(c->t & 1);
+    const size_t n = (size_t)L.nx * L.ny, field = n * sizeof(double);
+    if (on_device) {
+        CUDA_TRY(c, launch_macro(L, p, p, rho, vx, vy, mu, nullptr, nullptr,
+                                 nullptr, c->stream));
+        CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+        return LBM_OK;
+    }
+    lbm_status s = ensure_tmp(c, 4 * field);
+    if (s != LBM_OK) return s;
+    double *d[4] = {c->d_tmp, c->d_tmp + n, c->d_tmp + 2 * n, c->d_tmp + 3 * n};
+    double *h[4] = {rho, vx, vy, mu};
+    CUDA_TRY(c, launch_macro(L, p, p, rho ? d[0] : nullptr, vx ? d[1] : nullptr,
+                             vy ? d[2] : nullptr, mu ? d[3] : nullptr, nullptr,
+                             nullptr, nullptr, c->stream));
+    for (int k = 0; k < 4; ++k)
+        if (h[k])
+            CUDA_TRY(c, cudaMemcpyAsync(h[k], d[k], field, cudaMemcpyDeviceToHost,
+                                        c->stream));
+    CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+    return LBM_OK;
+}
+
+lbm_status lbm_get_populations(lbm_ctx *c, double *f, int on_device)
+{
+    if (!c) return fail(nullptr, LBM_ERR_ARG, "null context");
+    if (!f) return fail(c, LBM_ERR_ARG, "null output");
+    if (!c->initialized) return fail(c, LBM_ERR_STATE, "lbm_init must come first");
+    CUDA_TRY(c, cudaSetDevice(c->device));
+    Lattice &L = c->L;
+    const int p = (int)(c->t & 1);
+    const size_t bytes = 9 * (size_t)L.nx * L.ny * sizeof(double);
+    double *dst = f;
+    if (!on_device) {
+        lbm_status s = ensure_tmp(c, bytes);
+        if (s != LBM_OK) return s;
+        dst = c->d_tmp;
+    }
+    CUDA_TRY(c, cudaMemsetAsync(dst, 0, bytes, c->stream));
+    CUDA_TRY(c, launch_populations(L, p, p, dst, c->stream));
+    if (!on_device)
+        CUDA_TRY(c, cudaMemcpyAsync(f, dst, bytes, cudaMemcpyDeviceToHost, c->stream));
+    CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+    return LBM_OK;
+}
+
+lbm_status lbm_reduce(lbm_ctx *c, double out[4])
+{
+    if (!c) return fail(nullptr, LBM_ERR_ARG, "null context");
+    if (!out) return fail(c, LBM_ERR_ARG, "null output");
+    if (!c->initialized) return fail(c, LBM_ERR_STATE, "lbm_init must come first");
+    CUDA_TRY(c, cudaSetDevice(c->device));
+    const int p = (int)(c->t & 1);
+    CUDA_TRY(c, cudaMemsetAsync(c->d_red, 0, 4 * sizeof(double), c->stream));
+    CUDA_TRY(c, cudaMemsetAsync(c->d_bad, 0, sizeof(int), c->stream));
+    CUDA_TRY(c, launch_macro(c->L, p, p, nullptr, nullptr, nullptr, nullptr,
+                             c->d_red, c->d_prev, c->d_bad, c->stream));
+    double h[4];
+    int bad = 0;
+    CUDA_TRY(c, cudaMemcpyAsync(h, c->d_red, sizeof h, cudaMemcpyDeviceToHost,
+                                c->stream));
+    CUDA_TRY(c, cudaMemcpyAsync(&bad, c->d_bad, sizeof(int), cudaMemcpyDeviceToHost,
+                                c->stream));
+    CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+    for (int k = 0; k < 4; ++k) out[k] = h[k];
+    if (bad)
+        return fail(c, LBM_ERR_NUMERIC, "%d fluid node(s) with non-finite "
+                    "density or momentum", bad);
+    return LBM_OK;
+}
+
+size_t lbm_state_size(const lbm_ctx *c)
+{
+    if (!c) return 0;
+    const Lattice &L = c->L;
+    return sizeof(StateHeader) + 8 * (size_t)L.plane * pop_bytes(L.precision) +
+           (size_t)L.plane * rho_bytes(L.precision);
+}
+
+lbm_status lbm_get_state(lbm_ctx *c, void *buf, size_t bytes)
+{
+    if (!c) return fail(nullptr, LBM_ERR_ARG, "null context");
+    if (!buf || bytes < lbm_state_size(c))
+        return fail(c, LBM_ERR_ARG, "buffer smaller than lbm_state_size()");
+    if (!c->initialized) return fail(c, LBM_ERR_STATE, "lbm_init must come first");
+    CUDA_TRY(c, cudaSetDevice(c->device));
+    Lattice &L = c->L;
+    const int p = (int)(c->t & 1);
+    StateHeader h{};
+    memcpy(h.magic, "CPLBMST1", 8);
+    h.nx = L.nx; h.ny = L.ny; h.walls = L.walls; h.precision = L.precision;
+    h.t = c->t;
+    char *o = (char *)buf;
+    memcpy(o, &h, sizeof h);
+    o += sizeof h;
+    const size_t pbytes = 8 * (size_t)L.plane * pop_bytes(L.precision);
+    const size_t rbytes = (size_t)L.plane * rho_bytes(L.precision);
+    // the next-step density buffer is free between steps: gather into it
+    CUDA_TRY(c, launch_gather_rho(L, p, L.rho[p ^ 1], c->stream));
+    CUDA_TRY(c, cudaMemcpyAsync(o, L.pops, pbytes, cudaMemcpyDeviceToHost, c->stream));
+    CUDA_TRY(c, cudaMemcpyAsync(o + pbytes, L.rho[p ^ 1], rbytes,
+                                cudaMemcpyDeviceToHost, c->stream));
+    CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+    return LBM_OK;
+}
+
+lbm_status lbm_set_state(lbm_ctx *c, const void *buf, size_t bytes)
+{
+    if (!c) return fail(nullptr, LBM_ERR_ARG, "null context");
+    if (!buf || bytes < lbm_state_size(c))
+        return fail(c, LBM_ERR_ARG, "buffer smaller than lbm_state_size()");
+    if (!c->eos_set) return fail(c, LBM_ERR_STATE, "lbm_set_eos must come first");
+    StateHeader h;
+    memcpy(&h, buf, sizeof h);
+    Lattice &L = c->L;
+    if (memcmp(h.magic, "CPLBMST1", 8) != 0 || h.nx != L.nx || h.ny != L.ny ||
+        h.walls != L.walls || h.precision != L.precision || h.t < 0)
+        return fail(c, LBM_ERR_ARG, "state does not match this context");
+    CUDA_TRY(c, cudaSetDevice(c->device));
+    const char *in = (const char *)buf + sizeof h;
+    const size_t pbytes = 8 * (size_t)L.plane * pop_bytes(L.precision);
+    const size_t rbytes = (size_t)L.plane * rho_bytes(L.precision);
+    const int p = (int)(h.t & 1);
+    const size_t nring = ring_elems(L);
+    for (int k = 0; k < 2; ++k)
+        for (int r = 0; r < R_COUNT; ++r)
+            CUDA_TRY(c, cudaMemsetAsync(L.ring[k][r], 0, nring * rho_bytes(L.precision),
+                                        c->stream));
+    CUDA_TRY(c, cudaMemcpyAsync(L.pops, in, pbytes, cudaMemcpyHostToDevice, c->stream));
+    CUDA_TRY(c, cudaMemcpyAsync(L.rho[p], in + pbytes, rbytes,
+                                cudaMemcpyHostToDevice, c->stream));
+    CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+    c->t = h.t;
+    c->initialized = true;
+    return LBM_OK;
+}
+
+long long lbm_step_count(const lbm_ctx *c) { return c ? c->t : -1; }
+
+void lbm_destroy(lbm_ctx *c)
+{
+    if (!c) return;
+    cudaSetDevice(c->device);
+    free_all(c);
+    delete c;
+}
+
+const char *lbm_last_error(const lbm_ctx *c)
+{
+    return c ? c->err.c_str() : g_err.c_str();
+}
+
+}  // extern "C"

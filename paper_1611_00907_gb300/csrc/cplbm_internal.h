@@ -1,0 +1,97 @@
+// Internal declarations shared by the host side (capi.cu) and the kernels
+// (step.cu, fields.cu) of the cplbm library.  Nothing here is public ABI.
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+
+#include <cuda_runtime.h>
+
+namespace cplbm {
+
+enum Precision { P_F64 = 0, P_F32 = 1, P_F32_OFF = 2, P_F16_OFF = 3 };
+enum EosKind { EOS_VDW = 0, EOS_CS = 1, EOS_PR = 2, EOS_RKS = 3 };
+
+// Tile of the fused step: TILE_X x TILE_Y fluid nodes per CTA.
+constexpr int TILE_X = 64;
+constexpr int TILE_Y = 16;
+constexpr int STEP_THREADS = 256;
+
+// Classes of partial density sums that cross a tile boundary, named by the
+// direction from the receiving node's tile to the tile that wrote them.
+enum Ring { R_L = 0, R_R, R_B, R_T, R_BL, R_BR, R_TL, R_TR, R_COUNT };
+
+// EOS constants in the arithmetic type of a kernel.  Each kernel converts
+// the double values held by the context.
+struct EosParams {
+    int kind;
+    double a, b, RT;   // RT = R * T
+    double aalpha;     // a * alpha(T) (PR, RKS); a otherwise
+};
+
+// Geometry, storage and physics of one lattice as the kernels see it.
+//
+// Device layout (all row pitches are `pitch` elements, pitch >= nx):
+//  pops   [8][nyf][pitch]   moving populations f_1..f_8 in the AA-pattern
+//                           in-place order (see step.cu), storage type;
+//  rho[k] [nyf][pitch]      k = 0, 1: density of the current / next step
+//                           (offset precisions: rho - rho_ref), where a
+//                           node on a tile's edge holds only the part
+//                           summed inside its own tile;
+//  ring[k][c]               k = 0, 1: the partial sums of class c written
+//                           by the neighbouring tile.  Classes L and R are
+//                           stored column-major [pitch][nyf_pad] so a tile
+//                           column is contiguous; the others row-major.
+// nyf is the number of fluid rows: ny - 2 with walls, ny otherwise; fluid
+// row r is lattice row r + 1 with walls.
+struct Lattice {
+    void *pops;
+    void *rho[2];
+    void *ring[2][R_COUNT];
+    int nx, ny, nyf, pitch, nyf_pad;
+    int walls;
+    long long plane;     // nyf * pitch
+    double tau, kappa, rho_ref;
+    EosParams eos;
+    double mu_bottom, mu_top;
+    int top_mode;
+    int precision;
+};
+
+// Sizes of the storage types per precision.
+inline size_t pop_bytes(int prec)
+{
+    return prec == P_F64 ? 8 : prec == P_F16_OFF ? 2 : 4;
+}
+inline size_t rho_bytes(int prec) { return prec == P_F64 ? 8 : 4; }
+
+// Launchers (step.cu).  `cur` selects rho[cur] / ring[cur] as the current
+// density and `parity` the AA phase of the step being taken.
+cudaError_t launch_step(const Lattice &L, int parity, int cur,
+                        cudaStream_t s);
+
+// fields.cu
+// Equilibrium initial state from double fields [ny][nx] on the device:
+// fills pops (parity 0 order) and rho[0]/ring[0]; counts invalid densities
+// into *bad (device int, zeroed by the caller).
+cudaError_t launch_init(const Lattice &L, const double *rho, const double *ux,
+                        const double *uy, int *bad, cudaStream_t s);
+
+// Macroscopic fields of the state (any output may be NULL; [ny][nx]), and
+// optional FP64 reductions into red[0..3] (sum rho, sum rho vx, sum rho vy,
+// max |rho - prev| as ordered bits) with `prev` the snapshot density
+// [ny][nx] that is then updated; nonfinite counts into *bad.
+cudaError_t launch_macro(const Lattice &L, int parity, int cur, double *rho,
+                         double *vx, double *vy, double *mu, double *red,
+                         double *prev, int *bad, cudaStream_t s);
+
+// Natural-order FP64 populations [9][ny][nx].
+cudaError_t launch_populations(const Lattice &L, int parity, int cur,
+                               double *f, cudaStream_t s);
+
+// Re-sum the current density of every node into rho[dst] (all nodes full,
+// ring classes zero): used when restoring a checkpoint.
+cudaError_t launch_gather_rho(const Lattice &L, int cur, void *dst,
+                              cudaStream_t s);
+
+}  // namespace cplbm

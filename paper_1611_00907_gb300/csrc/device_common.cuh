@@ -1,0 +1,308 @@
+// Device building blocks of the chemical-potential LBM step (arXiv
+// 1611.00907): D2Q9 lattice, storage types, the EOS chemical potentials,
+// the AA-pattern addressing and the tile loaders shared by the fused step
+// kernel and the field kernels.
+#pragma once
+
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+
+#include "cplbm_internal.h"
+
+namespace cplbm {
+
+// ---------------------------------------------------------------------------
+// D2Q9 lattice (Eq. 13-14).  e_0 = (0,0); e_1..4 = (1,0),(0,1),(-1,0),(0,-1);
+// e_5..8 = (1,1),(-1,1),(-1,-1),(1,-1).
+// ---------------------------------------------------------------------------
+__host__ __device__ constexpr int ex(int i)
+{
+    return (i == 1 || i == 5 || i == 8) ? 1 : (i == 3 || i == 6 || i == 7) ? -1 : 0;
+}
+__host__ __device__ constexpr int ey(int i)
+{
+    return (i == 2 || i == 5 || i == 6) ? 1 : (i == 4 || i == 7 || i == 8) ? -1 : 0;
+}
+__host__ __device__ constexpr int opp(int i)
+{
+    return i == 0 ? 0 : (i <= 4 ? ((i + 1) % 4) + 1 : ((i - 3) % 4) + 5);
+}
+static_assert(opp(1) == 3 && opp(2) == 4 && opp(3) == 1 && opp(4) == 2, "");
+static_assert(opp(5) == 7 && opp(6) == 8 && opp(7) == 5 && opp(8) == 6, "");
+
+template <class T>
+__host__ __device__ constexpr T wgt(int i)
+{
+    return i == 0 ? T(4) / T(9) : (i <= 4 ? T(1) / T(9) : T(1) / T(36));
+}
+
+// ---------------------------------------------------------------------------
+// Storage variants: population storage type, density storage type, the
+// arithmetic type, and whether values are stored as offsets from the
+// reference state (f_i - w_i rho_ref, rho - rho_ref).
+// ---------------------------------------------------------------------------
+struct SF64 {
+    using pop_t = double; using rho_t = double; using real = double;
+    static constexpr bool offset = false;
+};
+struct SF32 {
+    using pop_t = float; using rho_t = float; using real = float;
+    static constexpr bool offset = false;
+};
+struct SF32Off {
+    using pop_t = float; using rho_t = float; using real = float;
+    static constexpr bool offset = true;
+};
+struct SF16Off {
+    using pop_t = __half; using rho_t = float; using real = float;
+    static constexpr bool offset = true;
+};
+
+template <class T> __device__ __forceinline__ float to_f(T v) { return (float)v; }
+__device__ __forceinline__ double ld_real(const double *p) { return *p; }
+__device__ __forceinline__ float ld_real(const float *p) { return *p; }
+__device__ __forceinline__ float ld_real(const __half *p) { return __half2float(*p); }
+__device__ __forceinline__ void st_real(double *p, double v) { *p = v; }
+__device__ __forceinline__ void st_real(float *p, float v) { *p = v; }
+__device__ __forceinline__ void st_real(__half *p, float v) { *p = __float2half_rn(v); }
+
+// ---------------------------------------------------------------------------
+// Bulk chemical potential psi'(rho): Eq. 18 (vdW), Eq. 21 (RK/RKS), Eq. 24
+// (PR), Eq. 27 (CS) without the -kappa lap(rho) term.
+// ---------------------------------------------------------------------------
+template <class T>
+struct EosT {
+    int kind;
+    T a, b, RT, aalpha, quarter_b, pr_c, pr_s2m1, pr_s2p1, rks_c;
+    __host__ __device__ explicit EosT(const EosParams &e)
+        : kind(e.kind), a(T(e.a)), b(T(e.b)), RT(T(e.RT)), aalpha(T(e.aalpha)),
+          quarter_b(T(0.25 * e.b)),
+          pr_c(T(e.aalpha / (2.0 * 1.4142135623730951 * e.b))),
+          pr_s2m1(T(0.41421356237309515)), pr_s2p1(T(2.414213562373095)),
+          rks_c(T(e.aalpha / e.b)) {}
+};
+
+template <class T>
+__device__ __forceinline__ T mu_bulk(const EosT<T> &e, T rho)
+{
+    switch (e.kind) {
+    case EOS_VDW: {
+        const T q = T(1) - e.b * rho;
+        return e.RT * (log(rho / q) + T(1) / q) - T(2) * e.a * rho;
+    }
+    case EOS_CS: {
+        const T h = e.quarter_b * rho;
+        const T q = T(1) - h;
+        return e.RT * ((T(3) - h) / (q * q * q) + log(rho) + T(1)) -
+               T(2) * e.a * rho;
+    }
+    case EOS_PR: {
+        const T br = e.b * rho;
+        const T q = T(1) - br;
+        return e.RT * log(rho / q) -
+               e.pr_c * log((e.pr_s2m1 + br) / (e.pr_s2p1 - br)) + e.RT / q -
+               e.aalpha * rho / (T(1) + T(2) * br - br * br);
+    }
+    default: {  // EOS_RKS
+        const T br = e.b * rho;
+        const T q = T(1) - br;
+        return e.RT * log(rho / q) + e.RT / q - e.rks_c * log(T(1) + br) -
+               e.aalpha * rho / (T(1) + br);
+    }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Addressing.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ int wrapi(int v, int n)
+{
+    return v < 0 ? v + n : (v >= n ? v - n : v);
+}
+
+// Index of population i (1..8) of fluid node (x, r) in the pops array.
+__device__ __forceinline__ long long pidx(const Lattice &L, int i, int r, int x)
+{
+    return (long long)(i - 1) * L.plane + (long long)r * L.pitch + x;
+}
+__device__ __forceinline__ long long fidx(const Lattice &L, int r, int x)
+{
+    return (long long)r * L.pitch + x;
+}
+// Column-major index used by the L / R ring classes.
+__device__ __forceinline__ long long cidx(const Lattice &L, int r, int x)
+{
+    return (long long)x * L.nyf_pad + r;
+}
+
+// Row r + dy of a fluid node; with walls, -1 / nyf mean the solid rows.
+__device__ __forceinline__ bool row_is_solid(const Lattice &L, int r)
+{
+    return L.walls && (r < 0 || r >= L.nyf);
+}
+__device__ __forceinline__ int row_wrap(const Lattice &L, int r)
+{
+    return L.walls ? r : wrapi(r, L.nyf);
+}
+
+// AA pattern (in place).  Even step: node x reads f_i from its own slot i
+// and writes f*_i into its own slot opp(i).  Odd step: node x reads f_i from
+// slot opp(i) of x - e_i and writes f*_i into slot i of x + e_i.  Every slot
+// a node reads is one it writes, so no two nodes touch the same slot in a
+// step.  Halfway bounce-back (Sec. IV): on an odd step, a population whose
+// source x - e_i is solid is read from slot i of x itself, where the even
+// step left f*_opp(i); a population whose target x + e_i is solid is written
+// to slot opp(i) of x, where the next even step reads it.
+__device__ __forceinline__ long long aa_read_index(const Lattice &L, int parity,
+                                                   int i, int r, int x)
+{
+    if (parity == 0) return pidx(L, i, r, x);
+    const int rs = r - ey(i);
+    if (row_is_solid(L, rs)) return pidx(L, i, r, x);
+    return pidx(L, opp(i), row_wrap(L, rs), wrapi(x - ex(i), L.nx));
+}
+__device__ __forceinline__ long long aa_write_index(const Lattice &L,
+                                                    int parity, int i, int r,
+                                                    int x)
+{
+    if (parity == 0) return pidx(L, opp(i), r, x);
+    const int rt = r + ey(i);
+    if (row_is_solid(L, rt)) return pidx(L, opp(i), r, x);
+    return pidx(L, i, row_wrap(L, rt), wrapi(x + ex(i), L.nx));
+}
+
+// ---------------------------------------------------------------------------
+// Density of the current step at fluid node (x, r): the tile-local sum in
+// rho[cur] plus the partial sums written by neighbouring tiles for nodes on
+// the edge of their tile (see launch_step).  The result is absolute
+// density, also for offset storage.
+// ---------------------------------------------------------------------------
+template <class S>
+__device__ __forceinline__ typename S::real load_rho(const Lattice &L, int cur,
+                                                     int r, int x)
+{
+    using rt = typename S::rho_t;
+    using real = typename S::real;
+    const rt *R = (const rt *)L.rho[cur];
+    real v = (real)R[fidx(L, r, x)];
+    const int bx = x / TILE_X, by = r / TILE_Y;
+    const int lx = x - bx * TILE_X, ly = r - by * TILE_Y;
+    const int wx = min(TILE_X, L.nx - bx * TILE_X);
+    const int wy = min(TILE_Y, L.nyf - by * TILE_Y);
+    const bool left = lx == 0, right = lx == wx - 1;
+    const bool below = ly == 0 && !(L.walls && r == 0);
+    const bool above = ly == wy - 1 && !(L.walls && r == L.nyf - 1);
+    if (left | right | below | above) {
+        rt *const *ring = (rt *const *)L.ring[cur];
+        if (left) v += (real)ring[R_L][cidx(L, r, x)];
+        if (right) v += (real)ring[R_R][cidx(L, r, x)];
+        if (below) {
+            v += (real)ring[R_B][fidx(L, r, x)];
+            if (left) v += (real)ring[R_BL][fidx(L, r, x)];
+            if (right) v += (real)ring[R_BR][fidx(L, r, x)];
+        }
+        if (above) {
+            v += (real)ring[R_T][fidx(L, r, x)];
+            if (left) v += (real)ring[R_TL][fidx(L, r, x)];
+            if (right) v += (real)ring[R_TR][fidx(L, r, x)];
+        }
+    }
+    if (S::offset) v += (real)L.rho_ref;
+    return v;
+}
+
+// Fill s_rho[(TY + 4) x (TX + 4)] with the density of the tile at (X0, Y0)
+// and a halo of two nodes; solid rows get the Eq. 28 average of the
+// adjacent fluid row (the top row mirrors it from row nyf - 1).
+template <class S, int TX, int TY>
+__device__ void load_rho_tile(const Lattice &L, int cur, int X0, int Y0,
+                              typename S::real *s_rho)
+{
+    using real = typename S::real;
+    constexpr int W = TX + 4, H = TY + 4;
+    const int wx = min(TX, L.nx - X0), wy = min(TY, L.nyf - Y0);
+    for (int k = threadIdx.x; k < W * H; k += blockDim.x) {
+        const int lx = k % W, ly = k / W;
+        if (lx > wx + 3 || ly > wy + 3) {  // beyond a ragged tile's halo
+            s_rho[k] = real(0);
+            continue;
+        }
+        // X0 - 2 <= x < X0 + wx + 2 <= nx + 2: one wrap suffices (nx >= 5)
+        const int x = wrapi(X0 + lx - 2, L.nx);
+        const int r = Y0 + ly - 2;
+        real v;
+        if (!L.walls) {
+            v = load_rho<S>(L, cur, wrapi(r, L.nyf), x);
+        } else if (r >= 0 && r < L.nyf) {
+            v = load_rho<S>(L, cur, r, x);
+        } else if (r == -1 || r == L.nyf) {
+            // Eq. 28: rho(x, wall) = 2/3 rho(x, 1) + 1/6 rho(x-1, 1) + 1/6 rho(x+1, 1)
+            const int rf = r < 0 ? 0 : L.nyf - 1;
+            v = real(2) / real(3) * load_rho<S>(L, cur, rf, x) +
+                real(1) / real(6) * load_rho<S>(L, cur, rf, wrapi(x - 1, L.nx)) +
+                real(1) / real(6) * load_rho<S>(L, cur, rf, wrapi(x + 1, L.nx));
+        } else {
+            v = real(0);  // beyond a wall: never read
+        }
+        s_rho[k] = v;
+    }
+}
+
+// Isotropic D2Q9 Laplacian and gradient on a shared-memory tile of row
+// width W at linear index c.
+template <class T, int W>
+__device__ __forceinline__ T lap9(const T *s, int c)
+{
+    const T axial = s[c + 1] + s[c - 1] + s[c + W] + s[c - W];
+    const T diag = s[c + W + 1] + s[c + W - 1] + s[c - W + 1] + s[c - W - 1];
+    return (T(4) * axial + diag - T(20) * s[c]) / T(6);
+}
+template <class T, int W>
+__device__ __forceinline__ void grad9(const T *s, int c, T &gx, T &gy)
+{
+    // 3 sum_i w_i phi(x + e_i) e_i = [4 (E - W) + (NE - NW + SE - SW)] / 12
+    const T ne = s[c + W + 1], nw = s[c + W - 1];
+    const T se = s[c - W + 1], sw = s[c - W - 1];
+    gx = (T(4) * (s[c + 1] - s[c - 1]) + (ne - nw) + (se - sw)) / T(12);
+    gy = (T(4) * (s[c + W] - s[c - W]) + (ne + nw) - (se + sw)) / T(12);
+}
+
+// Fill s_mu[(TY + 2) x (TX + 2)] with mu on the tile and a one-node halo
+// (Eq. 8); solid rows carry the surface values (Sec. IV, V).
+template <class S, int TX, int TY>
+__device__ void mu_tile(const Lattice &L, int X0, int Y0,
+                        const typename S::real *s_rho, typename S::real *s_mu)
+{
+    using real = typename S::real;
+    constexpr int W = TX + 2, H = TY + 2, WR = TX + 4;
+    const EosT<real> eos(L.eos);
+    const real kappa = (real)L.kappa;
+    const int wx = min(TX, L.nx - X0), wy = min(TY, L.nyf - Y0);
+    for (int k = threadIdx.x; k < W * H; k += blockDim.x) {
+        const int lx = k % W, ly = k / W;
+        if (lx > wx + 1 || ly > wy + 1) {  // beyond a ragged tile's halo
+            s_mu[k] = real(0);
+            continue;
+        }
+        const int r = Y0 + ly - 1;
+        const int c = (ly + 1) * WR + lx + 1;  // same node in s_rho
+        real m;
+        if (L.walls && r == -1) {
+            m = (real)L.mu_bottom;
+        } else if (L.walls && r == L.nyf) {
+            if (L.top_mode == 0) {
+                const int cb = c - WR;  // fluid neighbour below (row nyf-1)
+                m = mu_bulk(eos, s_rho[cb]) - kappa * lap9<real, WR>(s_rho, cb);
+            } else {
+                m = (real)L.mu_top;
+            }
+        } else if (L.walls && (r < -1 || r > L.nyf)) {
+            m = real(0);
+        } else {
+            m = mu_bulk(eos, s_rho[c]) - kappa * lap9<real, WR>(s_rho, c);
+        }
+        s_mu[k] = m;
+    }
+}
+
+}  // namespace cplbm

@@ -1,0 +1,234 @@
+"""Parity of the CUDA step with the FP64 CPU oracle, through the C ABI.
+
+FP64: one step to 1e-13 and 1000 steps to 1e-10 relative per field (rho, v,
+mu and all nine populations), on sizes that span several 64 x 16 tiles with
+ragged last tiles, one-node-wide last tiles, the minimum sizes, periodic and
+walled geometries and every EOS.  Full size (4096 x 4096, the throughput
+workload): one step of sampled nodes against the oracle run on a periodic
+patch around each sample (a node's next state depends on its 7 x 7
+neighbourhood only), and exact mass conservation.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from oracle import thermo
+from paper_1611_00907_gb300 import LbmError, Simulation, inputs
+
+pytestmark = pytest.mark.gpu
+
+# (kind, a, b, Tr, kappa, tau): the paper's parameter sets (Sec. III, V);
+# kappa scaled to the EOS's density range so runs stay stable.
+EOS_CASES = {
+    "cs": ("cs", 1.0, 4.0, 0.85, 0.5, 1.0),
+    "vdw": ("vdw", 9 / 49, 2 / 21, 0.85, 0.01, 1.0),
+    "pr": ("pr", 2 / 49, 2 / 21, 0.85, 0.01, 1.3),
+    "rks": ("rks", 2 / 49, 2 / 21, 0.8, 0.01, 1.3),
+}
+
+
+def _setup(case, nx, ny, walls, mu_shift=0.01, precision="f64", rho_ref=0.0,
+           geometry="drop", top_mode=0, mu_top=0.0):
+    kind, a, b, Tr, kappa, tau = EOS_CASES[case]
+    e = thermo.make_eos(kind, a, b, 1.0, Tr, 0.344)
+    rv, rl, mc, _ = thermo.maxwell(e)
+    width = 4.0 if kind == "cs" else 2.0
+    r = max(2.0, min(nx, ny) / 4)
+    if walls:
+        rho = inputs.wall_drop(nx, ny, r, rl, rv, width)
+    elif geometry == "slab":
+        rho = inputs.slab(nx, ny, rl, rv, width)
+    else:
+        rho = inputs.drop(nx, ny, r, rl, rv, width)
+    sim = Simulation(nx, ny, kind, a, b, 1.0, Tr, omega=0.344, tau=tau,
+                     kappa=kappa, walls=walls, precision=precision,
+                     rho_ref=rho_ref, mu_bottom=mc + mu_shift,
+                     top_mode=top_mode, mu_top=mu_top)
+    ref = oracle.Lattice(nx, ny, e, tau, kappa, walls=walls,
+                         mu_bottom=mc + mu_shift, top_mode=top_mode,
+                         mu_top=mu_top)
+    return sim, ref, rho
+
+
+def _rel(got, want):
+    scale = np.abs(want).max()
+    return np.abs(got - want).max() / (scale if scale > 0 else 1.0)
+
+
+def _compare(sim, ref, tol):
+    g, w = sim.moments(), ref.moments()
+    for k in ("rho", "mu", "vx", "vy"):
+        assert _rel(g[k], w[k]) < tol, (k, _rel(g[k], w[k]))
+    fg, fw = sim.populations(), ref.f
+    for i in range(9):
+        assert _rel(fg[i], fw[i]) < tol, ("f", i, _rel(fg[i], fw[i]))
+
+
+SIZES = [(9, 7), (70, 21), (131, 37), (65, 17), (5, 5), (64, 16), (200, 9)]
+
+
+@pytest.mark.parametrize("case", list(EOS_CASES))
+@pytest.mark.parametrize("walls", [False, True])
+@pytest.mark.parametrize("size", SIZES)
+def test_one_step_fp64(case, walls, size):
+    nx, ny = size
+    if walls and ny < 7:
+        ny = 7
+    sim, ref, rho = _setup(case, nx, ny, walls)
+    with sim:
+        sim.init(rho)
+        ref.init_equilibrium(rho)
+        _compare(sim, ref, 1e-13)
+        sim.step(1)
+        ref.step(1)
+        _compare(sim, ref, 1e-13)
+        sim.step(1)      # odd parity of the in-place pattern
+        ref.step(1)
+        _compare(sim, ref, 1e-13)
+
+
+@pytest.mark.parametrize("case,walls,size", [
+    ("cs", False, (64, 64)),      # the 64 x 64 slab/drop configuration
+    ("cs", True, (131, 37)),
+    ("rks", True, (97, 40)),
+    ("pr", False, (70, 33)),
+    ("vdw", True, (65, 18)),
+])
+def test_1000_steps_fp64(case, walls, size, oracle_threads):
+    nx, ny = size
+    sim, ref, rho = _setup(case, nx, ny, walls)
+    with sim:
+        sim.init(rho).step(1000)
+        ref.init_equilibrium(rho).step(1000)
+        _compare(sim, ref, 1e-10)
+
+
+def test_top_wall_with_given_value():
+    sim, ref, rho = _setup("cs", 70, 21, True, top_mode=1, mu_top=0.004)
+    with sim:
+        sim.init(rho).step(25)
+        ref.init_equilibrium(rho).step(25)
+        _compare(sim, ref, 1e-12)
+
+
+def test_initial_velocity_field():
+    nx, ny = 70, 21
+    sim, ref, rho = _setup("cs", nx, ny, False)
+    rng = np.random.default_rng(5)
+    ux = 0.02 * rng.uniform(-1, 1, (ny, nx))
+    uy = 0.02 * rng.uniform(-1, 1, (ny, nx))
+    with sim:
+        sim.init(rho, ux, uy).step(30)
+        ref.init_equilibrium(rho, ux, uy).step(30)
+        _compare(sim, ref, 1e-12)
+
+
+def test_device_tensors_in_and_out():
+    torch = pytest.importorskip("torch")
+    nx, ny = 70, 21
+    sim, ref, rho = _setup("cs", nx, ny, False)
+    with sim:
+        sim.init(torch.tensor(rho, device="cuda")).step(5)
+        ref.init_equilibrium(rho).step(5)
+        got = sim.moments(device=True)
+        assert got["rho"].is_cuda
+        assert _rel(got["rho"].cpu().numpy(), ref.moments()["rho"]) < 1e-13
+
+
+def test_mass_conservation_and_reduce():
+    sim, ref, rho = _setup("cs", 131, 37, True)
+    with sim:
+        sim.init(rho)
+        m0, px, py, d0 = sim.reduce()
+        assert m0 == pytest.approx(ref.init_equilibrium(rho).density()[1:-1]
+                                   .sum(), rel=1e-14)
+        assert d0 == 0.0
+        sim.step(500)
+        m1, _, _, d1 = sim.reduce()
+        assert abs(m1 - m0) / m0 < 1e-13
+        assert d1 > 0.0
+        _, _, _, d2 = sim.reduce()
+        assert d2 == 0.0           # no step since the last call
+
+
+def test_checkpoint_resume_is_bitwise():
+    sim, _, rho = _setup("cs", 131, 37, True)
+    with sim:
+        sim.init(rho).step(37)     # odd step count
+        state = sim.get_state()
+        sim.step(13)
+        a = sim.populations()
+    sim2, _, _ = _setup("cs", 131, 37, True)
+    with sim2:
+        sim2.set_state(state)
+        assert sim2.step_count == 37
+        sim2.step(13)
+        b = sim2.populations()
+    assert np.array_equal(a, b)
+
+
+def test_zero_steps_and_uniform_fixed_point():
+    nx, ny = 70, 21
+    sim, _, _ = _setup("cs", nx, ny, False)
+    with sim:
+        rho = np.full((ny, nx), 0.2)
+        sim.init(rho, np.full((ny, nx), 0.03), np.full((ny, nx), -0.01))
+        f0 = sim.populations()
+        sim.step(0)
+        assert np.array_equal(sim.populations(), f0)
+        sim.step(20)
+        assert np.abs(sim.populations() - f0).max() < 1e-15
+
+
+def test_invalid_init_is_rejected_without_fault():
+    sim, _, rho = _setup("cs", 70, 21, False)
+    with sim:
+        bad = rho.copy()
+        bad[3, 4] = 1.5            # beyond the CS pole 4/b = 1
+        with pytest.raises(LbmError) as ei:
+            sim.init(bad)
+        assert "density" in str(ei.value)
+        with pytest.raises(LbmError):
+            sim.step(1)            # not initialised
+        sim.init(rho).step(2)      # the context stays usable
+
+
+def _patch_step(e, tau, kappa, fpatch):
+    """One oracle step on a periodic patch; returns the centre node."""
+    n = fpatch.shape[1]
+    L = oracle.Lattice(n, n, e, tau, kappa)
+    L.f = np.ascontiguousarray(fpatch)
+    L.step(1)
+    return L.f[:, n // 2, n // 2]
+
+
+@pytest.mark.parametrize("precision,tol", [("f64", 1e-13), ("f32", 2e-6)])
+def test_full_size_sampled_one_step(precision, tol):
+    # The throughput workload: 4096 x 4096 Carnahan-Starling spinodal
+    # decomposition at T_r = 0.85 from rho_c (1 + 0.01 xi).
+    n = 4096
+    e = thermo.make_eos("cs", 1.0, 4.0, 1.0, 0.85)
+    _, rc = thermo.critical_point("cs", 1.0, 4.0)
+    rho = inputs.spinodal_noise(n, n, rc, 0.01, seed=1)
+    sim = Simulation(n, n, "cs", 1.0, 4.0, 1.0, 0.85, tau=1.0, kappa=0.5,
+                     precision=precision)
+    with sim:
+        sim.init(rho).step(3)
+        f0 = sim.populations()
+        m0 = sim.reduce()[0]
+        sim.step(1)
+        f1 = sim.populations()
+        rng = np.random.default_rng(7)
+        pts = [(0, 0), (n - 1, n - 1), (63, 15), (64, 16), (4095, 16),
+               (2047, 2048)] + [tuple(p) for p in rng.integers(0, n, (20, 2))]
+        h = 6
+        for (y, x) in pts:
+            ys = np.arange(y - h, y + h + 1) % n
+            xs = np.arange(x - h, x + h + 1) % n
+            patch = f0[:, ys][:, :, xs]
+            want = _patch_step(e, 1.0, 0.5, patch)
+            got = f1[:, y, x]
+            assert np.abs(got - want).max() / np.abs(want).max() < tol, (y, x)
+        sim.step(96)
+        m1 = sim.reduce()[0]
+        assert abs(m1 - m0) / m0 < (1e-13 if precision == "f64" else 1e-5)
