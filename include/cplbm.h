@@ -153,6 +153,37 @@ lbm_status lbm_eos_info(const lbm_ctx *ctx, double *T, double *alpha,
 lbm_status lbm_eos_critical(int eos, double a, double b, double R,
                             double *Tc, double *rhoc);
 
+/* Allocation-free FP64 step, for callers that may not allocate device
+ * memory: for example a host application whose own allocator owns the GPU
+ * and forbids other code from calling cudaMalloc, or one that cannot accept
+ * the device-wide synchronisation cudaMalloc and cudaFree can cause while
+ * other work shares the GPU.  The paper has no counterpart: this is an
+ * interface variant of lbm_step, not part of the method.
+ *
+ * f is the caller's device array of natural-order FP64 populations
+ * [9][ny][nx] (the layout lbm_get_populations returns; solid rows unused),
+ * advanced in place by nsteps steps of the same update as lbm_step, with
+ * the EOS and wall arguments of lbm_set_eos and lbm_set_wall_mu.  cfg gives
+ * nx, ny, walls, tau, kappa, stream and device; precision must be LBM_F64.
+ * nsteps must be even (f is in natural order only between step pairs).
+ * Work is queued on cfg->stream and the call returns without waiting.
+ *
+ * The call allocates nothing: the density buffers a context would own live
+ * in one fixed device array of LBM_NOALLOC_SCRATCH_BYTES, which every GPU
+ * that loads the library holds until the process exits.  A lattice needs
+ * 8 * (2 nx nyf + 16 nx ceil32(nyf)) bytes of it, nyf = ny - 2 with walls,
+ * else ny (256 x 256 periodic fits exactly); larger lattices are rejected
+ * with LBM_ERR_ARG.  The first call on a device looks up the array's device
+ * address (cudaGetSymbolAddress); make that first call before any stream
+ * capture.  All calls share the array and each clears what must start at
+ * zero: calls that overlap on the GPU race on it and must be serialised by
+ * the caller.  Errors are reported through lbm_last_error(NULL). */
+#define LBM_NOALLOC_SCRATCH_BYTES (18u * 65536u * 8u)
+lbm_status lbm_step_noalloc(const lbm_config *cfg, int eos, double a,
+                            double b, double R, double T_over_Tc,
+                            double omega, double mu_bottom, int top_mode,
+                            double mu_top, double *f, int nsteps);
+
 /* Release the context and its device memory.  NULL is ignored. */
 void lbm_destroy(lbm_ctx *ctx);
 

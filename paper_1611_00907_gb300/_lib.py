@@ -48,6 +48,10 @@ SIGNATURES = {
     "lbm_eos_info": ([_ctx, _dp, _dp, _dp, _dp], C.c_int),
     "lbm_eos_critical": ([C.c_int, C.c_double, C.c_double, C.c_double, _dp,
                           _dp], C.c_int),
+    "lbm_step_noalloc": ([C.POINTER(LbmConfig), C.c_int, C.c_double,
+                          C.c_double, C.c_double, C.c_double, C.c_double,
+                          C.c_double, C.c_int, C.c_double, _vp, C.c_int],
+                         C.c_int),
     "lbm_destroy": ([_ctx], None),
     "lbm_last_error": ([_ctx], C.c_char_p),
 }

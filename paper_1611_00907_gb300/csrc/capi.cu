@@ -174,6 +174,20 @@ struct StateHeader {
 
 }  // namespace
 
+namespace cplbm {
+// Host helpers shared with the allocation-free entry point (noalloc.cu).
+bool host_critical(int kind, double a, double b, double R, double *Tc,
+                   double *rhoc)
+{
+    return critical(kind, a, b, R, Tc, rhoc);
+}
+double host_alpha(int kind, double Tr, double omega)
+{
+    return alpha_of(kind, Tr, omega);
+}
+void set_global_error(const char *msg) { g_err = msg; }
+}  // namespace cplbm
+
 extern "C" {
 
 lbm_status lbm_create(const lbm_config *cfg, lbm_ctx **out)

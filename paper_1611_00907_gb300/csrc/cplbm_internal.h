@@ -94,4 +94,10 @@ cudaError_t launch_populations(const Lattice &L, int parity, int cur,
 cudaError_t launch_gather_rho(const Lattice &L, int cur, void *dst,
                               cudaStream_t s);
 
+// capi.cu: host helpers for entry points outside it.
+bool host_critical(int kind, double a, double b, double R, double *Tc,
+                   double *rhoc);
+double host_alpha(int kind, double Tr, double omega);
+void set_global_error(const char *msg);
+
 }  // namespace cplbm
