@@ -175,7 +175,7 @@ def time_steps(sim, steps, warmup):
     return t0.elapsed_time(t1)
 
 
-def measure_gpu(precision, steps, warmup, rho):
+def measure_gpu(precision, steps, warmup, rho, tile=None):
     import torch
     from paper_1611_00907_gb300 import Simulation
     n = rho.shape[0]
@@ -184,6 +184,8 @@ def measure_gpu(precision, steps, warmup, rho):
                      rho_ref=0.15 if "offset" in precision else 0.0,
                      **EOS_ARGS)
     with sim:
+        if tile:
+            sim.set_tile(*tile)
         sim.init(rho_dev)
         del rho_dev
         ms = time_steps(sim, steps, warmup)
@@ -319,6 +321,8 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--n", type=int, default=N_SIDE,
                     help="lattice side (profiling runs use smaller cases)")
+    ap.add_argument("--tile", default=None,
+                    help="step tile shape TXxTY (default: the library's)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     rank, world = dist_setup()
@@ -333,10 +337,11 @@ def main():
     __graft_entry__.build()
     rho = initial_rho(args.n)
     n_nodes = rho.size
+    tile = tuple(int(v) for v in args.tile.split("x")) if args.tile else None
 
     barrier(world)
     with ClockSampler(int(os.environ.get("LOCAL_RANK", "0"))) as clocks:
-        ms = measure_gpu(args.precision, args.steps, args.warmup, rho)
+        ms = measure_gpu(args.precision, args.steps, args.warmup, rho, tile)
     ms = max_over_ranks(ms, world)
     ms_step = ms / args.steps
     value = world * n_nodes * args.steps / (ms * 1e-3) / 1e6

@@ -106,6 +106,13 @@ lbm_status lbm_set_eos(lbm_ctx *ctx, int eos, double a, double b, double R,
 lbm_status lbm_set_wall_mu(lbm_ctx *ctx, double mu_bottom, int top_mode,
                            double mu_top);
 
+/* Tile shape of the fused step kernel: tx x ty fluid nodes per CTA, one of
+ * 32x16, 32x24, 32x32, 64x16 (LBM_ERR_ARG otherwise).  The shape changes
+ * speed only, not results.  May be called at any time; the default depends
+ * on the precision. */
+lbm_status lbm_set_tile(lbm_ctx *ctx, int tx, int ty);
+lbm_status lbm_get_tile(const lbm_ctx *ctx, int *tx, int *ty);
+
 /* Set the state to equilibrium populations f_i = f_i^eq(rho, u) (Eq. 14)
  * at every fluid node, and the step counter to 0.  rho must be positive and
  * below the EOS's repulsive pole at fluid nodes; ux and uy may be NULL

@@ -118,6 +118,17 @@ class Simulation:
         self._check(self._lib.lbm_set_wall_mu(self._ctx, float(mu_bottom),
                                               int(top_mode), float(mu_top)))
 
+    def set_tile(self, tx, ty):
+        """Tile shape of the step kernel (speed only; results unchanged)."""
+        self._check(self._lib.lbm_set_tile(self._ctx, int(tx), int(ty)))
+        return self
+
+    @property
+    def tile(self):
+        tx, ty = C.c_int(), C.c_int()
+        self._check(self._lib.lbm_get_tile(self._ctx, C.byref(tx), C.byref(ty)))
+        return tx.value, ty.value
+
     def init(self, rho, ux=None, uy=None):
         """Equilibrium state (Eq. 14) from [ny, nx] float64 fields given as
         numpy arrays (host) or CUDA tensors (device)."""

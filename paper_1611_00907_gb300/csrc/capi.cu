@@ -236,6 +236,7 @@ lbm_status lbm_create(const lbm_config *cfg, lbm_ctx **out)
                  cfg->precision == LBM_F16_OFFSET) ? cfg->rho_ref : 0.0;
     L.precision = cfg->precision;
     L.top_mode = 0;
+    step_default_shape(L.precision, &L.tx, &L.ty);
 
     const size_t pb = pop_bytes(L.precision), rb = rho_bytes(L.precision);
     const size_t nring = ring_elems(L);
@@ -316,6 +317,39 @@ lbm_status lbm_eos_info(const lbm_ctx *c, double *T, double *alpha,
     if (alpha) *alpha = c->alpha;
     if (Tc) *Tc = c->Tc;
     if (rhoc) *rhoc = c->rhoc;
+    return LBM_OK;
+}
+
+lbm_status lbm_set_tile(lbm_ctx *c, int tx, int ty)
+{
+    if (!c) return fail(nullptr, LBM_ERR_ARG, "null context");
+    if (!step_shape_supported(c->L.precision, tx, ty))
+        return fail(c, LBM_ERR_ARG, "no step kernel for tile %d x %d", tx, ty);
+    if (c->initialized && (tx != c->L.tx || ty != c->L.ty)) {
+        // The tile grid defines how the current density is split between
+        // rho and the partial sums: gather it whole before switching.
+        CUDA_TRY(c, cudaSetDevice(c->device));
+        Lattice &L = c->L;
+        const int p = (int)(c->t & 1);
+        CUDA_TRY(c, launch_gather_rho(L, p, L.rho[p ^ 1], c->stream));
+        const size_t rb = rho_bytes(L.precision), nring = ring_elems(L);
+        for (int k = 0; k < 2; ++k)
+            for (int r = 0; r < R_COUNT; ++r)
+                CUDA_TRY(c, cudaMemsetAsync(L.ring[k][r], 0, nring * rb, c->stream));
+        CUDA_TRY(c, cudaMemcpyAsync(L.rho[p], L.rho[p ^ 1], (size_t)L.plane * rb,
+                                    cudaMemcpyDeviceToDevice, c->stream));
+        CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+    }
+    c->L.tx = tx;
+    c->L.ty = ty;
+    return LBM_OK;
+}
+
+lbm_status lbm_get_tile(const lbm_ctx *c, int *tx, int *ty)
+{
+    if (!c || !tx || !ty) return fail(nullptr, LBM_ERR_ARG, "null argument");
+    *tx = c->L.tx;
+    *ty = c->L.ty;
     return LBM_OK;
 }
 

@@ -12,9 +12,13 @@ namespace cplbm {
 enum Precision { P_F64 = 0, P_F32 = 1, P_F32_OFF = 2, P_F16_OFF = 3 };
 enum EosKind { EOS_VDW = 0, EOS_CS = 1, EOS_PR = 2, EOS_RKS = 3 };
 
-// Tile of the fused step: TILE_X x TILE_Y fluid nodes per CTA.
-constexpr int TILE_X = 64;
-constexpr int TILE_Y = 16;
+// Tile of the field kernels (moments, reductions): independent of the step.
+constexpr int FIELD_TILE_X = 64;
+constexpr int FIELD_TILE_Y = 16;
+// Threads of a step CTA.  The step's tile shape (tx x ty fluid nodes per
+// CTA) is a property of the lattice: it also fixes the grid on which the
+// step hands the next density over (see step.cu), so every kernel that reads
+// the density uses the lattice's tx, ty.
 constexpr int STEP_THREADS = 256;
 
 // Classes of partial density sums that cross a tile boundary, named by the
@@ -49,6 +53,7 @@ struct Lattice {
     void *rho[2];
     void *ring[2][R_COUNT];
     int nx, ny, nyf, pitch, nyf_pad;
+    int tx, ty;          // step tile shape
     int walls;
     long long plane;     // nyf * pitch
     double tau, kappa, rho_ref;
@@ -69,6 +74,10 @@ inline size_t rho_bytes(int prec) { return prec == P_F64 ? 8 : 4; }
 // density and `parity` the AA phase of the step being taken.
 cudaError_t launch_step(const Lattice &L, int parity, int cur,
                         cudaStream_t s);
+// Whether the step has a kernel for tile shape tx x ty in precision prec,
+// and the default shape of a precision.
+bool step_shape_supported(int prec, int tx, int ty);
+void step_default_shape(int prec, int *tx, int *ty);
 
 // fields.cu
 // Equilibrium initial state from double fields [ny][nx] on the device:

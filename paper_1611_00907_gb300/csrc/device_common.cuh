@@ -82,34 +82,70 @@ struct EosT {
           rks_c(T(e.aalpha / e.b)) {}
 };
 
+// Division and logarithm of the arithmetic type: the FP32 kernels use the
+// fast hardware forms (__fdividef, __logf), whose few-ulp errors sit far
+// below the FP32 storage error; FP64 keeps IEEE division and log().
+__device__ __forceinline__ float fdiv(float a, float b) { return __fdividef(a, b); }
+__device__ __forceinline__ double fdiv(double a, double b) { return a / b; }
+__device__ __forceinline__ float flog(float x) { return __logf(x); }
+__device__ __forceinline__ double flog(double x) { return log(x); }
+
 template <class T>
 __device__ __forceinline__ T mu_bulk(const EosT<T> &e, T rho)
 {
     switch (e.kind) {
     case EOS_VDW: {
-        const T q = T(1) - e.b * rho;
-        return e.RT * (log(rho / q) + T(1) / q) - T(2) * e.a * rho;
+        const T iq = fdiv(T(1), T(1) - e.b * rho);
+        return e.RT * (flog(rho * iq) + iq) - T(2) * e.a * rho;
     }
     case EOS_CS: {
         const T h = e.quarter_b * rho;
-        const T q = T(1) - h;
-        return e.RT * ((T(3) - h) / (q * q * q) + log(rho) + T(1)) -
+        const T iq = fdiv(T(1), T(1) - h);
+        return e.RT * ((T(3) - h) * (iq * iq * iq) + flog(rho) + T(1)) -
                T(2) * e.a * rho;
     }
     case EOS_PR: {
         const T br = e.b * rho;
-        const T q = T(1) - br;
-        return e.RT * log(rho / q) -
-               e.pr_c * log((e.pr_s2m1 + br) / (e.pr_s2p1 - br)) + e.RT / q -
-               e.aalpha * rho / (T(1) + T(2) * br - br * br);
+        const T iq = fdiv(T(1), T(1) - br);
+        return e.RT * flog(rho * iq) -
+               e.pr_c * flog(fdiv(e.pr_s2m1 + br, e.pr_s2p1 - br)) +
+               e.RT * iq - fdiv(e.aalpha * rho, T(1) + T(2) * br - br * br);
     }
     default: {  // EOS_RKS
         const T br = e.b * rho;
-        const T q = T(1) - br;
-        return e.RT * log(rho / q) + e.RT / q - e.rks_c * log(T(1) + br) -
-               e.aalpha * rho / (T(1) + br);
+        const T iq = fdiv(T(1), T(1) - br);
+        return e.RT * (flog(rho * iq) + iq) - e.rks_c * flog(T(1) + br) -
+               fdiv(e.aalpha * rho, T(1) + br);
     }
     }
+}
+
+// ---------------------------------------------------------------------------
+// Asynchronous global -> shared copies of single elements (sm_80+ cp.async).
+// A thread's copies become visible to that thread after cp_async_wait_all.
+// ---------------------------------------------------------------------------
+template <int BYTES>
+__device__ __forceinline__ void cp_async(void *smem, const void *gmem)
+{
+    static_assert(BYTES == 4 || BYTES == 8 || BYTES == 16, "cp.async size");
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], %2;\n" ::"r"(s),
+                 "l"(gmem), "n"(BYTES)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async_commit()
+{
+    asm volatile("cp.async.commit_group;\n" ::: "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all()
+{
+    asm volatile("cp.async.wait_all;\n" ::: "memory");
+}
+// Wait until at most N of the thread's most recent copy groups are pending.
+template <int N>
+__device__ __forceinline__ void cp_async_wait_group()
+{
+    asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
 }
 
 // ---------------------------------------------------------------------------
@@ -172,23 +208,24 @@ __device__ __forceinline__ long long aa_write_index(const Lattice &L,
 }
 
 // ---------------------------------------------------------------------------
-// Density of the current step at fluid node (x, r): the tile-local sum in
-// rho[cur] plus the partial sums written by neighbouring tiles for nodes on
-// the edge of their tile (see launch_step).  The result is absolute
-// density, also for offset storage.
+// Density of the current step at fluid node (x, r) in stored form (offset
+// precisions: rho - rho_ref): the tile-local sum in rho[cur] plus the
+// partial sums written by neighbouring tiles for nodes on the edge of their
+// tile (see step.cu), always added in this order.
 // ---------------------------------------------------------------------------
 template <class S>
-__device__ __forceinline__ typename S::real load_rho(const Lattice &L, int cur,
-                                                     int r, int x)
+__device__ __forceinline__ typename S::real load_rho_stored(const Lattice &L,
+                                                            int cur, int r,
+                                                            int x)
 {
     using rt = typename S::rho_t;
     using real = typename S::real;
     const rt *R = (const rt *)L.rho[cur];
     real v = (real)R[fidx(L, r, x)];
-    const int bx = x / TILE_X, by = r / TILE_Y;
-    const int lx = x - bx * TILE_X, ly = r - by * TILE_Y;
-    const int wx = min(TILE_X, L.nx - bx * TILE_X);
-    const int wy = min(TILE_Y, L.nyf - by * TILE_Y);
+    const int bx = x / L.tx, by = r / L.ty;
+    const int lx = x - bx * L.tx, ly = r - by * L.ty;
+    const int wx = min(L.tx, L.nx - bx * L.tx);
+    const int wy = min(L.ty, L.nyf - by * L.ty);
     const bool left = lx == 0, right = lx == wx - 1;
     const bool below = ly == 0 && !(L.walls && r == 0);
     const bool above = ly == wy - 1 && !(L.walls && r == L.nyf - 1);
@@ -207,13 +244,22 @@ __device__ __forceinline__ typename S::real load_rho(const Lattice &L, int cur,
             if (right) v += (real)ring[R_TR][fidx(L, r, x)];
         }
     }
-    if (S::offset) v += (real)L.rho_ref;
     return v;
 }
 
-// Fill s_rho[(TY + 4) x (TX + 4)] with the density of the tile at (X0, Y0)
-// and a halo of two nodes; solid rows get the Eq. 28 average of the
-// adjacent fluid row (the top row mirrors it from row nyf - 1).
+// Absolute density.
+template <class S>
+__device__ __forceinline__ typename S::real load_rho(const Lattice &L, int cur,
+                                                     int r, int x)
+{
+    using real = typename S::real;
+    const real v = load_rho_stored<S>(L, cur, r, x);
+    return S::offset ? v + (real)L.rho_ref : v;
+}
+
+// Fill s_rho[(TY + 4) x (TX + 4)] with the stored-form density of the tile
+// at (X0, Y0) and a halo of two nodes; solid rows get the Eq. 28 average of
+// the adjacent fluid row (the top row mirrors it from row nyf - 1).
 template <class S, int TX, int TY>
 __device__ void load_rho_tile(const Lattice &L, int cur, int X0, int Y0,
                               typename S::real *s_rho)
@@ -232,15 +278,16 @@ __device__ void load_rho_tile(const Lattice &L, int cur, int X0, int Y0,
         const int r = Y0 + ly - 2;
         real v;
         if (!L.walls) {
-            v = load_rho<S>(L, cur, wrapi(r, L.nyf), x);
+            v = load_rho_stored<S>(L, cur, wrapi(r, L.nyf), x);
         } else if (r >= 0 && r < L.nyf) {
-            v = load_rho<S>(L, cur, r, x);
+            v = load_rho_stored<S>(L, cur, r, x);
         } else if (r == -1 || r == L.nyf) {
             // Eq. 28: rho(x, wall) = 2/3 rho(x, 1) + 1/6 rho(x-1, 1) + 1/6 rho(x+1, 1)
+            // (the weights sum to one, so the stored form averages the same)
             const int rf = r < 0 ? 0 : L.nyf - 1;
-            v = real(2) / real(3) * load_rho<S>(L, cur, rf, x) +
-                real(1) / real(6) * load_rho<S>(L, cur, rf, wrapi(x - 1, L.nx)) +
-                real(1) / real(6) * load_rho<S>(L, cur, rf, wrapi(x + 1, L.nx));
+            v = real(2.0 / 3.0) * load_rho_stored<S>(L, cur, rf, x) +
+                real(1.0 / 6.0) * load_rho_stored<S>(L, cur, rf, wrapi(x - 1, L.nx)) +
+                real(1.0 / 6.0) * load_rho_stored<S>(L, cur, rf, wrapi(x + 1, L.nx));
         } else {
             v = real(0);  // beyond a wall: never read
         }
@@ -255,7 +302,7 @@ __device__ __forceinline__ T lap9(const T *s, int c)
 {
     const T axial = s[c + 1] + s[c - 1] + s[c + W] + s[c - W];
     const T diag = s[c + W + 1] + s[c + W - 1] + s[c - W + 1] + s[c - W - 1];
-    return (T(4) * axial + diag - T(20) * s[c]) / T(6);
+    return (T(4) * axial + diag - T(20) * s[c]) * T(1.0 / 6.0);
 }
 template <class T, int W>
 __device__ __forceinline__ void grad9(const T *s, int c, T &gx, T &gy)
@@ -263,12 +310,13 @@ __device__ __forceinline__ void grad9(const T *s, int c, T &gx, T &gy)
     // 3 sum_i w_i phi(x + e_i) e_i = [4 (E - W) + (NE - NW + SE - SW)] / 12
     const T ne = s[c + W + 1], nw = s[c + W - 1];
     const T se = s[c - W + 1], sw = s[c - W - 1];
-    gx = (T(4) * (s[c + 1] - s[c - 1]) + (ne - nw) + (se - sw)) / T(12);
-    gy = (T(4) * (s[c + W] - s[c - W]) + (ne + nw) - (se + sw)) / T(12);
+    gx = (T(4) * (s[c + 1] - s[c - 1]) + (ne - nw) + (se - sw)) * T(1.0 / 12.0);
+    gy = (T(4) * (s[c + W] - s[c - W]) + (ne + nw) - (se + sw)) * T(1.0 / 12.0);
 }
 
 // Fill s_mu[(TY + 2) x (TX + 2)] with mu on the tile and a one-node halo
-// (Eq. 8); solid rows carry the surface values (Sec. IV, V).
+// (Eq. 8) from the stored-form densities in s_rho; solid rows carry the
+// surface values (Sec. IV, V).
 template <class S, int TX, int TY>
 __device__ void mu_tile(const Lattice &L, int X0, int Y0,
                         const typename S::real *s_rho, typename S::real *s_mu)
@@ -277,6 +325,7 @@ __device__ void mu_tile(const Lattice &L, int X0, int Y0,
     constexpr int W = TX + 2, H = TY + 2, WR = TX + 4;
     const EosT<real> eos(L.eos);
     const real kappa = (real)L.kappa;
+    const real ref = S::offset ? (real)L.rho_ref : real(0);
     const int wx = min(TX, L.nx - X0), wy = min(TY, L.nyf - Y0);
     for (int k = threadIdx.x; k < W * H; k += blockDim.x) {
         const int lx = k % W, ly = k / W;
@@ -292,14 +341,14 @@ __device__ void mu_tile(const Lattice &L, int X0, int Y0,
         } else if (L.walls && r == L.nyf) {
             if (L.top_mode == 0) {
                 const int cb = c - WR;  // fluid neighbour below (row nyf-1)
-                m = mu_bulk(eos, s_rho[cb]) - kappa * lap9<real, WR>(s_rho, cb);
+                m = mu_bulk(eos, s_rho[cb] + ref) - kappa * lap9<real, WR>(s_rho, cb);
             } else {
                 m = (real)L.mu_top;
             }
         } else if (L.walls && (r < -1 || r > L.nyf)) {
             m = real(0);
         } else {
-            m = mu_bulk(eos, s_rho[c]) - kappa * lap9<real, WR>(s_rho, c);
+            m = mu_bulk(eos, s_rho[c] + ref) - kappa * lap9<real, WR>(s_rho, c);
         }
         s_mu[k] = m;
     }

@@ -75,6 +75,7 @@ __global__ void macro_kernel(const Lattice L, int parity, int cur,
     const real rho_ref = S::offset ? (real)L.rho_ref : real(0);
     const pop_t *A = (const pop_t *)L.pops;
     double acc_m = 0.0, acc_x = 0.0, acc_y = 0.0, acc_d = 0.0;
+    // s_rho holds the stored form; rho_ref makes it absolute
     int nbad = 0;
     for (int n = threadIdx.x; n < TX * TY; n += blockDim.x) {
         const int lx = n % TX, ly = n / TX;
@@ -85,7 +86,7 @@ __global__ void macro_kernel(const Lattice L, int parity, int cur,
 #pragma unroll
         for (int i = 1; i < 9; ++i)
             f[i] = ld_real(A + aa_read_index(L, parity, i, r, x));
-        const real rho = s_rho[cr];
+        const real rho = s_rho[cr] + rho_ref;
         real gmx, gmy, grx, gry;
         grad9<real, WM>(s_mu, cm, gmx, gmy);
         grad9<real, WR>(s_rho, cr, grx, gry);
@@ -112,7 +113,6 @@ __global__ void macro_kernel(const Lattice L, int parity, int cur,
                 prev[g] = (double)rho;
             }
         }
-        (void)rho_ref;
     }
     // Solid rows: rho by Eq. 28 and the wall mu from the shared tiles.
     if (L.walls && (o_rho || o_mu || o_vx || o_vy)) {
@@ -120,14 +120,14 @@ __global__ void macro_kernel(const Lattice L, int parity, int cur,
             const int x = X0 + lx;
             if (Y0 == 0) {
                 const long long g = x;
-                if (o_rho) o_rho[g] = (double)s_rho[1 * WR + lx + 2];
+                if (o_rho) o_rho[g] = (double)(s_rho[1 * WR + lx + 2] + rho_ref);
                 if (o_mu) o_mu[g] = (double)s_mu[0 * WM + lx + 1];
                 if (o_vx) o_vx[g] = 0.0;
                 if (o_vy) o_vy[g] = 0.0;
             }
             if (Y0 + wy == L.nyf) {
                 const long long g = (long long)(L.ny - 1) * L.nx + x;
-                if (o_rho) o_rho[g] = (double)s_rho[(wy + 2) * WR + lx + 2];
+                if (o_rho) o_rho[g] = (double)(s_rho[(wy + 2) * WR + lx + 2] + rho_ref);
                 if (o_mu) o_mu[g] = (double)s_mu[(wy + 1) * WM + lx + 1];
                 if (o_vx) o_vx[g] = 0.0;
                 if (o_vy) o_vy[g] = 0.0;
@@ -194,13 +194,10 @@ template <class S>
 __global__ void gather_rho_kernel(const Lattice L, int cur, void *dst)
 {
     using rho_t = typename S::rho_t;
-    using real = typename S::real;
     const long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (n >= (long long)L.nx * L.nyf) return;
     const int x = (int)(n % L.nx), r = (int)(n / L.nx);
-    real v = load_rho<S>(L, cur, r, x);
-    if (S::offset) v -= (real)L.rho_ref;
-    ((rho_t *)dst)[fidx(L, r, x)] = (rho_t)v;
+    ((rho_t *)dst)[fidx(L, r, x)] = (rho_t)load_rho_stored<S>(L, cur, r, x);
 }
 
 // ---------------------------------------------------------------------------
@@ -228,7 +225,7 @@ static cudaError_t launch_macro_t(const Lattice &L, int parity, int cur,
                                   int *bad, cudaStream_t s)
 {
     using real = typename S::real;
-    constexpr int TX = TILE_X, TY = TILE_Y;
+    constexpr int TX = FIELD_TILE_X, TY = FIELD_TILE_Y;
     const size_t smem =
         sizeof(real) * ((TY + 4) * (TX + 4) + (TY + 2) * (TX + 2));
     dim3 grid((L.nx + TX - 1) / TX, (L.nyf + TY - 1) / TY);

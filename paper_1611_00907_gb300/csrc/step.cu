@@ -18,153 +18,488 @@
 // partial-sum buffers ring[next][class], class = direction from the ring
 // node's own tile to this one.  Each entry has exactly one writer, so the
 // hand-over needs no atomics and no clearing, and the next step adds the
-// parts in a fixed order (load_rho): results do not depend on scheduling.
+// parts in a fixed order (load_rho_stored): results do not depend on
+// scheduling.
+//
+// Memory pipeline.  Every global load a CTA needs is issued at its start as
+// an asynchronous copy into shared memory (cp.async): the density halo and
+// the partial sums first, then the eight populations of each node, which
+// land in the planes of the post-collision buffer the node later overwrites.
+// The chemical potential is computed while the populations are in flight.
+//
+// Two code paths share this structure.  Tiles whose halo and ring touch no
+// domain edge and whose neighbours are full tiles (nearly all of a large
+// lattice) take the interior path: constant address offsets, no periodic
+// wrap, no wall tests, asynchronous density loads.  All other tiles take
+// the general path.  Both add the same terms in the same order, so a node's
+// values do not depend on which path a tile took.
 #include "device_common.cuh"
 
 namespace cplbm {
 
+// Shared-memory carve-up of one CTA.
+template <class real, int TX, int TY>
+struct StepSmem {
+    static constexpr int WR = TX + 4, HR = TY + 4;   // rho + 2-node halo
+    static constexpr int WM = TX + 2, HM = TY + 2;   // mu + 1-node halo
+    static constexpr int NPOST = 8 * TX * TY;        // f*_1..8 of the tile
+    static constexpr int NRING = 4 * HR + 4 * WR + 16;  // staged partial sums
+    static constexpr size_t bytes =
+        sizeof(real) * (WR * HR + WM * HM + NPOST + NRING);
+};
+
+// In an interior tile's density halo the tile grid's edges sit at fixed
+// columns (1, 2, TX + 1, TX + 2) and rows (1, 2, TY + 1, TY + 2).  Columns 2
+// and TX + 2 are left edges of their tile (class L), 1 and TX + 1 right
+// edges (R); rows 2 and TY + 2 are bottom edges (B), 1 and TY + 1 top edges.
+template <int T>
+__device__ __forceinline__ int edge_col(int ci)
+{
+    return ci == 0 ? 1 : ci == 1 ? 2 : ci == 2 ? T + 1 : T + 2;
+}
+__device__ __forceinline__ bool col_is_left(int ci) { return ci & 1; }
+__device__ __forceinline__ bool row_is_below(int ri) { return ri & 1; }
+template <int T>
+__device__ __forceinline__ int col_index(int l)
+{
+    return l == 1 ? 0 : l == 2 ? 1 : l == T + 1 ? 2 : l == T + 2 ? 3 : -1;
+}
+
+// Issue the asynchronous loads of an interior tile's stored density and of
+// the partial sums its halo needs.
 template <class S, int TX, int TY, int NT>
-__global__ void __launch_bounds__(NT)
-    step_kernel(const Lattice L, int parity, int cur)
+__device__ __forceinline__ void issue_rho_interior(const Lattice &L, int cur,
+                                                   int X0, int Y0,
+                                                   typename S::real *s_rho,
+                                                   typename S::real *s_ring)
+{
+    using real = typename S::real;
+    using rt = typename S::rho_t;
+    static_assert(sizeof(rt) == sizeof(real), "density staged as stored");
+    using SM = StepSmem<real, TX, TY>;
+    constexpr int WR = SM::WR, HR = SM::HR;
+    const rt *R = (const rt *)L.rho[cur];
+    rt *const *ring = (rt *const *)L.ring[cur];
+    for (int k = threadIdx.x; k < WR * HR; k += NT) {
+        const int lx = k % WR, ly = k / WR;
+        const long long fi = (long long)(Y0 + ly - 2) * L.pitch + X0 + lx - 2;
+        cp_async<sizeof(rt)>(&s_rho[k], R + fi);
+    }
+    for (int p = threadIdx.x; p < SM::NRING; p += NT) {
+        int c, lx, ly;
+        if (p < 4 * HR) {  // edge columns: class L or R, column-major storage
+            const int ci = p / HR;
+            ly = p % HR;
+            lx = edge_col<TX>(ci);
+            c = col_is_left(ci) ? R_L : R_R;
+        } else if (p < 4 * HR + 4 * WR) {  // edge rows: class B or T
+            const int q = p - 4 * HR, ri = q / WR;
+            lx = q % WR;
+            ly = edge_col<TY>(ri);
+            c = row_is_below(ri) ? R_B : R_T;
+        } else {  // the 16 crossings: corner classes
+            const int q = p - 4 * HR - 4 * WR, ci = q / 4, ri = q % 4;
+            lx = edge_col<TX>(ci);
+            ly = edge_col<TY>(ri);
+            c = row_is_below(ri) ? (col_is_left(ci) ? R_BL : R_BR)
+                                 : (col_is_left(ci) ? R_TL : R_TR);
+        }
+        const int x = X0 + lx - 2, r = Y0 + ly - 2;
+        const long long idx =
+            (c == R_L || c == R_R) ? cidx(L, r, x) : fidx(L, r, x);
+        cp_async<sizeof(rt)>(&s_ring[p], ring[c] + idx);
+    }
+}
+
+// Add the staged partial sums to the halo's edge nodes, in the order of
+// load_rho_stored.
+template <class S, int TX, int TY, int NT>
+__device__ __forceinline__ void combine_rho_interior(typename S::real *s_rho,
+                                                     const typename S::real *s_ring)
+{
+    using real = typename S::real;
+    using SM = StepSmem<real, TX, TY>;
+    constexpr int WR = SM::WR, HR = SM::HR;
+    for (int q = threadIdx.x; q < 4 * HR + 4 * WR; q += NT) {
+        int lx, ly;
+        if (q < 4 * HR) {
+            lx = edge_col<TX>(q / HR);
+            ly = q % HR;
+        } else {
+            const int t = q - 4 * HR;
+            lx = t % WR;
+            ly = edge_col<TY>(t / WR);
+            if (col_index<TX>(lx) >= 0) continue;  // done by its column entry
+        }
+        const int ci = col_index<TX>(lx), ri = col_index<TY>(ly);
+        const bool lr = ci >= 0, ba = ri >= 0;
+        real v = s_rho[ly * WR + lx];
+        if (lr) v += s_ring[ci * HR + ly];
+        if (ba) {
+            v += s_ring[4 * HR + ri * WR + lx];
+            if (lr) v += s_ring[4 * HR + 4 * WR + ci * 4 + ri];
+        }
+        s_rho[ly * WR + lx] = v;
+    }
+}
+
+template <class S, int TX, int TY, int NT>
+__device__ __forceinline__ void mu_interior(const Lattice &L,
+                                            const typename S::real *s_rho,
+                                            typename S::real *s_mu)
+{
+    using real = typename S::real;
+    constexpr int W = TX + 2, H = TY + 2, WR = TX + 4;
+    const EosT<real> eos(L.eos);
+    const real kappa = (real)L.kappa;
+    const real ref = S::offset ? (real)L.rho_ref : real(0);
+    for (int k = threadIdx.x; k < W * H; k += NT) {
+        const int lx = k % W, ly = k / W;
+        const int c = (ly + 1) * WR + lx + 1;
+        s_mu[k] = mu_bulk(eos, s_rho[c] + ref) - kappa * lap9<real, WR>(s_rho, c);
+    }
+}
+
+// BGK collision of one node with the velocity-shift forcing.  f[1..8] are
+// the node's stored populations, drho its stored density (rho - rho_ref)
+// and rho the absolute one; fp[0..8] receive the post-collision values in
+// stored form.
+template <class real>
+__device__ __forceinline__ void collide(const real *f, real drho, real rho,
+                                        real Fx, real Fy, real tau, real omega,
+                                        real *fp)
+{
+    real sum = real(0);
+#pragma unroll
+    for (int i = 1; i < 9; ++i) sum += f[i];
+    const real f0 = drho - sum;
+    // u = sum f_i e_i / rho; u_eq = u + tau F / rho (Sec. II)
+    const real jx = (f[1] - f[3]) + (f[5] - f[7]) + (f[8] - f[6]);
+    const real jy = (f[2] - f[4]) + (f[5] - f[7]) + (f[6] - f[8]);
+    const real inv_rho = fdiv(real(1), rho);
+    const real ux = (jx + tau * Fx) * inv_rho;
+    const real uy = (jy + tau * Fy) * inv_rho;
+    const real usq = real(1.5) * (ux * ux + uy * uy);
+    // Eq. 14 in stored form: f_eq - w_i rho_ref = w_i (drho + rho P_i(u)),
+    // P_i = 3 e.u + 4.5 (e.u)^2 - 1.5 u^2; opposite directions share the
+    // even part of P.
+    const real w0 = real(4.0 / 9.0), w1 = real(1.0 / 9.0), w5 = real(1.0 / 36.0);
+    fp[0] = f0 + omega * (w0 * (drho - rho * usq) - f0);
+    {
+        const real ex2 = real(4.5) * ux * ux - usq, ey2 = real(4.5) * uy * uy - usq;
+        const real ax = w1 * (drho + rho * ex2), bx = w1 * rho * real(3) * ux;
+        const real ay = w1 * (drho + rho * ey2), by = w1 * rho * real(3) * uy;
+        fp[1] = f[1] + omega * ((ax + bx) - f[1]);
+        fp[3] = f[3] + omega * ((ax - bx) - f[3]);
+        fp[2] = f[2] + omega * ((ay + by) - f[2]);
+        fp[4] = f[4] + omega * ((ay - by) - f[4]);
+    }
+    {
+        const real sp = ux + uy, sm = ux - uy;
+        const real ep = real(4.5) * sp * sp - usq, em = real(4.5) * sm * sm - usq;
+        const real a5 = w5 * (drho + rho * ep), b5 = w5 * rho * real(3) * sp;
+        const real a8 = w5 * (drho + rho * em), b8 = w5 * rho * real(3) * sm;
+        fp[5] = f[5] + omega * ((a5 + b5) - f[5]);
+        fp[7] = f[7] + omega * ((a5 - b5) - f[7]);
+        fp[8] = f[8] + omega * ((a8 + b8) - f[8]);
+        fp[6] = f[6] + omega * ((a8 - b8) - f[6]);
+    }
+}
+
+// Index of f*_i (i = 1..8) of tile node (lx, ly) in s_post.
+template <int TX, int TY>
+__device__ __forceinline__ int post_idx(int i, int ly, int lx)
+{
+    return ((i - 1) * TY + ly) * TX + lx;
+}
+
+// Partial density at position (ox, oy) of the tile or its ring from the
+// tile's post-collision populations, with the general checks.  self0 is
+// f*_0 of the node when the position is inside the tile.
+template <class real, int TX, int TY>
+__device__ __forceinline__ real handover_sum(const Lattice &L, const real *s_post,
+                                             int ox, int oy, int wx, int wy,
+                                             int r, bool inside, real self0)
+{
+    real s = inside ? self0 : real(0);
+#pragma unroll
+    for (int i = 1; i < 9; ++i) {
+        const int sx = ox - ex(i), sy = oy - ey(i);
+        if (inside && L.walls && row_is_solid(L, r - ey(i))) {
+            // bounce-back: f*_opp(i) of this node comes back as f_i
+            s += s_post[post_idx<TX, TY>(opp(i), oy, ox)];
+        } else if (sx >= 0 && sx < wx && sy >= 0 && sy < wy) {
+            s += s_post[post_idx<TX, TY>(i, sy, sx)];
+        }
+    }
+    return s;
+}
+
+__device__ __forceinline__ int ring_class(int ox, int oy, int wx, int wy)
+{
+    if (ox < 0) return oy < 0 ? R_TR : (oy >= wy ? R_BR : R_R);
+    if (ox >= wx) return oy < 0 ? R_TL : (oy >= wy ? R_BL : R_L);
+    return oy < 0 ? R_T : R_B;
+}
+
+// Ring position p (0 .. 2 (wx + wy) + 3) of a wx x wy tile, walking the
+// bottom row, the top row, then the left and right columns.
+__device__ __forceinline__ void ring_position(int p, int wx, int wy, int &ox,
+                                              int &oy)
+{
+    if (p < wx + 2) { ox = p - 1; oy = -1; return; }
+    p -= wx + 2;
+    if (p < wx + 2) { ox = p - 1; oy = wy; return; }
+    p -= wx + 2;
+    if (p < wy) { ox = -1; oy = p; return; }
+    ox = wx; oy = p - wy;
+}
+
+template <class S, int TX, int TY, int NT, int PARITY, bool INTERIOR>
+__device__ __forceinline__ void step_tile(const Lattice &L, int cur, int X0,
+                                          int Y0, unsigned char *smem_raw)
 {
     using real = typename S::real;
     using pop_t = typename S::pop_t;
     using rho_t = typename S::rho_t;
-    constexpr int WR = TX + 4;       // s_rho row width
-    constexpr int WM = TX + 2;       // s_mu row width
-    constexpr int NODES = TX * TY;
-    constexpr int PER = NODES / NT;  // nodes per thread
-    static_assert(NODES % NT == 0, "tile must split evenly over threads");
-
-    extern __shared__ unsigned char smem_raw[];
+    using SM = StepSmem<real, TX, TY>;
+    constexpr int WR = SM::WR, WM = SM::WM;
+    constexpr int PER = TX * TY / NT;
+    constexpr int DY = NT / TX;  // rows between a thread's nodes
+    static_assert((TX * TY) % NT == 0 && NT % TX == 0, "thread mapping");
     real *s_rho = reinterpret_cast<real *>(smem_raw);
-    real *s_mu = s_rho + (TY + 4) * WR;
-    real *s_post = s_mu + (TY + 2) * WM;  // [9][TY][TX] post-collision
+    real *s_mu = s_rho + SM::WR * SM::HR;
+    real *s_post = s_mu + SM::WM * SM::HM;  // [8][TY][TX]
+    real *s_ring = s_post + SM::NPOST;
 
-    const int X0 = blockIdx.x * TX, Y0 = blockIdx.y * TY;
-    const int wx = min(TX, L.nx - X0), wy = min(TY, L.nyf - Y0);
+    const int wx = INTERIOR ? TX : min(TX, L.nx - X0);
+    const int wy = INTERIOR ? TY : min(TY, L.nyf - Y0);
     const int nxt = cur ^ 1;
-
-    load_rho_tile<S, TX, TY>(L, cur, X0, Y0, s_rho);
-    __syncthreads();
-    mu_tile<S, TX, TY>(L, X0, Y0, s_rho, s_mu);
-    __syncthreads();
-
-    const real omega = real(1) / (real)L.tau;
-    const real tau = (real)L.tau;
-    const real rho_ref = S::offset ? (real)L.rho_ref : real(0);
     pop_t *A = (pop_t *)L.pops;
+    const int lx = threadIdx.x % TX, ly0 = threadIdx.x / TX;
+    // Storage and arithmetic of the same width: populations are staged
+    // asynchronously (FP16 storage is loaded directly instead).
+    constexpr bool ASYNC = sizeof(pop_t) == sizeof(real);
 
+    // per-direction offsets of the in-place pattern (interior tiles)
+    long long roff[9], woff[9];
+#pragma unroll
+    for (int i = 1; i < 9; ++i) {
+        if (PARITY == 0) {
+            roff[i] = (long long)(i - 1) * L.plane;
+            woff[i] = (long long)(opp(i) - 1) * L.plane;
+        } else {
+            roff[i] = (long long)(opp(i) - 1) * L.plane -
+                      (long long)ey(i) * L.pitch - ex(i);
+            woff[i] = (long long)(i - 1) * L.plane +
+                      (long long)ey(i) * L.pitch + ex(i);
+        }
+    }
+
+    // 1. Issue the loads: density (interior tiles), then the populations.
+    if (INTERIOR) {
+        issue_rho_interior<S, TX, TY, NT>(L, cur, X0, Y0, s_rho, s_ring);
+        cp_async_commit();
+    }
+    if constexpr (ASYNC) {
+#pragma unroll
+        for (int k = 0; k < PER; ++k) {
+            const int ly = ly0 + k * DY;
+            if (!INTERIOR && (lx >= wx || ly >= wy)) continue;
+            const int x = X0 + lx, r = Y0 + ly;
+            const long long base = (long long)r * L.pitch + x;
+#pragma unroll
+            for (int i = 1; i < 9; ++i) {
+                const pop_t *src = INTERIOR
+                    ? A + base + roff[i]
+                    : A + aa_read_index(L, PARITY, i, r, x);
+                cp_async<sizeof(pop_t)>(&s_post[post_idx<TX, TY>(i, ly, lx)], src);
+            }
+        }
+        cp_async_commit();
+    }
+
+    // 2. Density with halo, then mu on the tile and a one-node halo.
+    if (INTERIOR) {
+        if constexpr (ASYNC) cp_async_wait_group<1>();  // density group only
+        else cp_async_wait_all();
+        __syncthreads();
+        combine_rho_interior<S, TX, TY, NT>(s_rho, s_ring);
+        __syncthreads();
+        mu_interior<S, TX, TY, NT>(L, s_rho, s_mu);
+    } else {
+        load_rho_tile<S, TX, TY>(L, cur, X0, Y0, s_rho);
+        __syncthreads();
+        mu_tile<S, TX, TY>(L, X0, Y0, s_rho, s_mu);
+    }
+    __syncthreads();
+
+    // 3. Force, collision, in-place streaming.
+    const real tau = (real)L.tau;
+    const real omega = real(1) / tau;
+    const real rho_ref = S::offset ? (real)L.rho_ref : real(0);
+    if constexpr (ASYNC) cp_async_wait_all();
+    real self0[PER];
 #pragma unroll
     for (int k = 0; k < PER; ++k) {
-        const int n = threadIdx.x + k * NT;
-        const int lx = n % TX, ly = n / TX;
-        if (lx >= wx || ly >= wy) continue;
+        self0[k] = real(0);
+        const int ly = ly0 + k * DY;
+        if (!INTERIOR && (lx >= wx || ly >= wy)) continue;
         const int x = X0 + lx, r = Y0 + ly;
-
-        // stored values (offset form for offset precisions)
+        const long long base = (long long)r * L.pitch + x;
         real f[9];
-        real sum = real(0);
+        if constexpr (ASYNC) {
 #pragma unroll
-        for (int i = 1; i < 9; ++i) {
-            f[i] = ld_real(A + aa_read_index(L, parity, i, r, x));
-            sum += f[i];
+            for (int i = 1; i < 9; ++i) f[i] = s_post[post_idx<TX, TY>(i, ly, lx)];
+        } else if (INTERIOR) {
+#pragma unroll
+            for (int i = 1; i < 9; ++i) f[i] = ld_real(A + base + roff[i]);
+        } else {
+#pragma unroll
+            for (int i = 1; i < 9; ++i)
+                f[i] = ld_real(A + aa_read_index(L, PARITY, i, r, x));
         }
         const int cr = (ly + 2) * WR + lx + 2, cm = (ly + 1) * WM + lx + 1;
-        const real rho = s_rho[cr];
-        f[0] = (rho - rho_ref) - sum;
-
+        const real drho = s_rho[cr];
+        const real rho = drho + rho_ref;
         // Eq. 12: F = -rho grad(mu) + grad(cs^2 rho)
         real gmx, gmy, grx, gry;
         grad9<real, WM>(s_mu, cm, gmx, gmy);
         grad9<real, WR>(s_rho, cr, grx, gry);
-        const real Fx = -rho * gmx + grx / real(3);
-        const real Fy = -rho * gmy + gry / real(3);
-
-        // u = sum f_i e_i / rho; u_eq = u + tau F / rho (Sec. II)
-        const real jx = f[1] - f[3] + f[5] - f[6] - f[7] + f[8];
-        const real jy = f[2] - f[4] + f[5] + f[6] - f[7] - f[8];
-        const real inv_rho = real(1) / rho;
-        const real ux = (jx + tau * Fx) * inv_rho;
-        const real uy = (jy + tau * Fy) * inv_rho;
-        const real usq = real(1.5) * (ux * ux + uy * uy);
-
-        // BGK towards Eq. 14 (offset form: f_eq - w_i rho_ref)
+        const real Fx = grx * real(1.0 / 3.0) - rho * gmx;
+        const real Fy = gry * real(1.0 / 3.0) - rho * gmy;
+        real fp[9];
+        collide<real>(f, drho, rho, Fx, Fy, tau, omega, fp);
+        self0[k] = fp[0];
 #pragma unroll
-        for (int i = 0; i < 9; ++i) {
-            const real eu = real(ex(i)) * ux + real(ey(i)) * uy;
-            const real poly = real(3) * eu + real(4.5) * eu * eu - usq;
-            const real feq = wgt<real>(i) * ((rho - rho_ref) + rho * poly);
-            const real fp = f[i] + omega * (feq - f[i]);
-            s_post[(i * TY + ly) * TX + lx] = fp;
-            if (i > 0) st_real(A + aa_write_index(L, parity, i, r, x), fp);
+        for (int i = 1; i < 9; ++i) s_post[post_idx<TX, TY>(i, ly, lx)] = fp[i];
+        if (INTERIOR) {
+#pragma unroll
+            for (int i = 1; i < 9; ++i) st_real(A + base + woff[i], fp[i]);
+        } else {
+#pragma unroll
+            for (int i = 1; i < 9; ++i)
+                st_real(A + aa_write_index(L, PARITY, i, r, x), fp[i]);
         }
     }
     __syncthreads();
 
-    // Density hand-over: every node of the tile and of its one-node ring
-    // receives the post-collision populations streaming to it from the tile.
+    // 4. Density hand-over, tile nodes: the thread's own nodes.
     rho_t *Rn = (rho_t *)L.rho[nxt];
     rho_t *const *ring = (rho_t *const *)L.ring[nxt];
-    constexpr int WO = TX + 2, HO = TY + 2;
-    for (int k = threadIdx.x; k < WO * HO; k += NT) {
-        const int ox = k % WO - 1, oy = k / WO - 1;
-        if (ox > wx || oy > wy) continue;
-        const int r = Y0 + oy;
-        if (L.walls && (r < 0 || r >= L.nyf)) continue;  // solid: no density
-        const bool in_x = ox >= 0 && ox < wx, in_y = oy >= 0 && oy < wy;
-        const bool inside = in_x && in_y;
-        real s = real(0);
-        bool any = false;
 #pragma unroll
-        for (int i = 0; i < 9; ++i) {
-            const int sx = ox - ex(i), sy = oy - ey(i);
-            if (i > 0 && inside && L.walls &&
-                row_is_solid(L, r - ey(i))) {
-                // bounce-back: f*_opp(i) of this node comes back as f_i
-                s += s_post[(opp(i) * TY + oy) * TX + ox];
-                any = true;
-            } else if (sx >= 0 && sx < wx && sy >= 0 && sy < wy) {
-                s += s_post[(i * TY + sy) * TX + sx];
-                any = true;
-            }
-        }
-        if (!any) continue;
-        const int x = wrapi(X0 + ox, L.nx);
-        const int rw = row_wrap(L, r);
-        if (inside) {
-            Rn[fidx(L, rw, x)] = (rho_t)s;
+    for (int k = 0; k < PER; ++k) {
+        const int ly = ly0 + k * DY;
+        if (!INTERIOR && (lx >= wx || ly >= wy)) continue;
+        const int r = Y0 + ly;
+        real s;
+        const bool deep = lx >= 1 && lx <= wx - 2 && ly >= 1 && ly <= wy - 2 &&
+                          (INTERIOR || !L.walls || (r >= 1 && r <= L.nyf - 2));
+        if (deep) {  // all nine sources inside the tile
+            s = self0[k];
+#pragma unroll
+            for (int i = 1; i < 9; ++i)
+                s += s_post[post_idx<TX, TY>(i, ly - ey(i), lx - ex(i))];
         } else {
-            int c;
-            if (ox < 0) c = oy < 0 ? R_TR : (oy >= wy ? R_BR : R_R);
-            else if (ox >= wx) c = oy < 0 ? R_TL : (oy >= wy ? R_BL : R_L);
-            else c = oy < 0 ? R_T : R_B;
-            const long long idx =
-                (c == R_L || c == R_R) ? cidx(L, rw, x) : fidx(L, rw, x);
-            ring[c][idx] = (rho_t)s;
+            s = handover_sum<real, TX, TY>(L, s_post, lx, ly, wx, wy, r, true,
+                                           self0[k]);
         }
+        Rn[(long long)r * L.pitch + X0 + lx] = (rho_t)s;
+    }
+    // Ring around the tile: partial sums for the neighbouring tiles.
+    const int nring = 2 * (wx + wy) + 4;
+    for (int p = threadIdx.x; p < nring; p += NT) {
+        int ox, oy;
+        ring_position(p, wx, wy, ox, oy);
+        const int r = Y0 + oy;
+        if (!INTERIOR && L.walls && (r < 0 || r >= L.nyf)) continue;
+        const real s = handover_sum<real, TX, TY>(L, s_post, ox, oy, wx, wy, r,
+                                                  false, real(0));
+        const int x = INTERIOR ? X0 + ox : wrapi(X0 + ox, L.nx);
+        const int rw = INTERIOR ? r : row_wrap(L, r);
+        const int c = ring_class(ox, oy, wx, wy);
+        const long long idx =
+            (c == R_L || c == R_R) ? cidx(L, rw, x) : fidx(L, rw, x);
+        ring[c][idx] = (rho_t)s;
     }
 }
+
+template <class S, int TX, int TY, int NT, int PARITY>
+__global__ void __launch_bounds__(NT)
+    step_kernel(const Lattice L, int cur, int xlo, int xhi, int ylo, int yhi)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int bx = blockIdx.x, by = blockIdx.y;
+    const int X0 = bx * TX, Y0 = by * TY;
+    const bool interior = bx >= xlo && bx <= xhi && by >= ylo && by <= yhi;
+    if (interior)
+        step_tile<S, TX, TY, NT, PARITY, true>(L, cur, X0, Y0, smem_raw);
+    else
+        step_tile<S, TX, TY, NT, PARITY, false>(L, cur, X0, Y0, smem_raw);
+}
+
+template <class S, int TX, int TY>
+static cudaError_t launch_shape(const Lattice &L, int parity, int cur,
+                                cudaStream_t s)
+{
+    using real = typename S::real;
+    constexpr int NT = STEP_THREADS;
+    const size_t smem = StepSmem<real, TX, TY>::bytes;
+    auto k0 = step_kernel<S, TX, TY, NT, 0>;
+    auto k1 = step_kernel<S, TX, TY, NT, 1>;
+    static int configured = -1;  // device the attribute was set on
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (configured != dev) {
+        e = cudaFuncSetAttribute(k0, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)smem);
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(
+                k1, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        configured = dev;
+    }
+    // Interior tiles: the tile and its eight neighbours are full tiles and
+    // the halo and ring need no wrap and meet no solid row.
+    const int ntx = (L.nx + TX - 1) / TX, nty = (L.nyf + TY - 1) / TY;
+    const int nfx = L.nx / TX, nfy = L.nyf / TY;  // full tiles per direction
+    dim3 grid(ntx, nty);
+    if (parity == 0)
+        k0<<<grid, NT, smem, s>>>(L, cur, 1, nfx - 2, 1, nfy - 2);
+    else
+        k1<<<grid, NT, smem, s>>>(L, cur, 1, nfx - 2, 1, nfy - 2);
+    return cudaGetLastError();
+}
+
+// Tile shapes with a compiled kernel (all precisions).
+#define CPLBM_STEP_SHAPES(X) X(32, 16) X(32, 24) X(32, 32) X(64, 16)
 
 template <class S>
 static cudaError_t launch_step_t(const Lattice &L, int parity, int cur,
                                  cudaStream_t s)
 {
-    using real = typename S::real;
-    constexpr int TX = TILE_X, TY = TILE_Y, NT = STEP_THREADS;
-    const size_t smem = sizeof(real) * ((TY + 4) * (TX + 4) +
-                                        (TY + 2) * (TX + 2) + 9 * TY * TX);
-    auto kern = step_kernel<S, TX, TY, NT>;
-    static bool configured = false;  // per template instance
-    if (!configured) {
-        cudaError_t e = cudaFuncSetAttribute(
-            kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-        configured = true;
-    }
-    dim3 grid((L.nx + TX - 1) / TX, (L.nyf + TY - 1) / TY);
-    kern<<<grid, NT, smem, s>>>(L, parity, cur);
-    return cudaGetLastError();
+#define CPLBM_CASE(a, b)                                           \
+    if (L.tx == a && L.ty == b)                                    \
+        return launch_shape<S, a, b>(L, parity, cur, s);
+    CPLBM_STEP_SHAPES(CPLBM_CASE)
+#undef CPLBM_CASE
+    return cudaErrorInvalidValue;
+}
+
+bool step_shape_supported(int prec, int tx, int ty)
+{
+    (void)prec;
+#define CPLBM_CASE(a, b) if (tx == a && ty == b) return true;
+    CPLBM_STEP_SHAPES(CPLBM_CASE)
+#undef CPLBM_CASE
+    return false;
+}
+
+void step_default_shape(int prec, int *tx, int *ty)
+{
+    *tx = 32;
+    *ty = prec == P_F64 ? 16 : 24;
 }
 
 cudaError_t launch_step(const Lattice &L, int parity, int cur, cudaStream_t s)

@@ -103,6 +103,35 @@ def test_1000_steps_fp64(case, walls, size, oracle_threads):
         _compare(sim, ref, 1e-10)
 
 
+@pytest.mark.parametrize("tile", [(32, 16), (32, 24), (32, 32), (64, 16)])
+@pytest.mark.parametrize("precision,tol,steps", [("f64", 1e-12, 60),
+                                                 ("f32", 3e-5, 60)])
+def test_every_tile_shape(tile, precision, tol, steps):
+    # 200 x 90 with walls: interior tiles, ragged edge tiles, both parities
+    sim, ref, rho = _setup("cs", 200, 90, True, precision=precision)
+    with sim:
+        sim.set_tile(*tile)
+        assert sim.tile == tile
+        sim.init(rho).step(steps)
+        ref.init_equilibrium(rho).step(steps)
+        g, w = sim.moments(), ref.moments()
+        for k in ("rho", "mu", "vx", "vy"):
+            assert _rel(g[k], w[k]) < tol, (k, _rel(g[k], w[k]))
+
+
+def test_tile_switch_mid_run():
+    sim, ref, rho = _setup("cs", 200, 90, False)
+    with sim:
+        sim.set_tile(64, 16)
+        sim.init(rho).step(31)
+        sim.set_tile(32, 24)        # re-splits the current density
+        sim.step(30)
+        ref.init_equilibrium(rho).step(61)
+        _compare(sim, ref, 1e-12)
+        with pytest.raises(LbmError):
+            sim.set_tile(48, 16)
+
+
 def test_top_wall_with_given_value():
     sim, ref, rho = _setup("cs", 70, 21, True, top_mode=1, mu_top=0.004)
     with sim:
