@@ -113,6 +113,12 @@ lbm_status lbm_set_wall_mu(lbm_ctx *ctx, double mu_bottom, int top_mode,
 lbm_status lbm_set_tile(lbm_ctx *ctx, int tx, int ty);
 lbm_status lbm_get_tile(const lbm_ctx *ctx, int *tx, int *ty);
 
+/* Time nsteps (rounded up to an even count >= 2) steps of each compiled
+ * tile shape on the context's own lattice, keep the fastest, and restore
+ * the state exactly as it was (the step counter included).  Allocates one
+ * temporary copy of the state.  *tx, *ty (may be NULL) receive the shape. */
+lbm_status lbm_autotune(lbm_ctx *ctx, int nsteps, int *tx, int *ty);
+
 /* Set the state to equilibrium populations f_i = f_i^eq(rho, u) (Eq. 14)
  * at every fluid node, and the step counter to 0.  rho must be positive and
  * below the EOS's repulsive pole at fluid nodes; ux and uy may be NULL

@@ -123,6 +123,14 @@ class Simulation:
         self._check(self._lib.lbm_set_tile(self._ctx, int(tx), int(ty)))
         return self
 
+    def autotune(self, nsteps=20):
+        """Time every tile shape on this lattice, keep the fastest; the state
+        is left unchanged.  Returns the shape."""
+        tx, ty = C.c_int(), C.c_int()
+        self._check(self._lib.lbm_autotune(self._ctx, int(nsteps), C.byref(tx),
+                                           C.byref(ty)))
+        return tx.value, ty.value
+
     @property
     def tile(self):
         tx, ty = C.c_int(), C.c_int()

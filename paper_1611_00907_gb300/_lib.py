@@ -39,6 +39,8 @@ SIGNATURES = {
     "lbm_init": ([_ctx, _vp, _vp, _vp, C.c_int], C.c_int),
     "lbm_set_tile": ([_ctx, C.c_int, C.c_int], C.c_int),
     "lbm_get_tile": ([_ctx, C.POINTER(C.c_int), C.POINTER(C.c_int)], C.c_int),
+    "lbm_autotune": ([_ctx, C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_int)],
+                     C.c_int),
     "lbm_step": ([_ctx, C.c_int], C.c_int),
     "lbm_moments": ([_ctx, _vp, _vp, _vp, _vp, C.c_int], C.c_int),
     "lbm_get_populations": ([_ctx, _vp, C.c_int], C.c_int),

@@ -345,6 +345,95 @@ lbm_status lbm_set_tile(lbm_ctx *c, int tx, int ty)
     return LBM_OK;
 }
 
+namespace {
+// Copy the current state (populations and whole density) into snap, or back
+// from it, leaving the partial sums zero.  snap holds pops then density.
+lbm_status snapshot(lbm_ctx *c, char *snap, bool save)
+{
+    Lattice &L = c->L;
+    const int p = (int)(c->t & 1);
+    const size_t pb = 8 * (size_t)L.plane * pop_bytes(L.precision);
+    const size_t rb = (size_t)L.plane * rho_bytes(L.precision);
+    if (save) {
+        CUDA_TRY(c, launch_gather_rho(L, p, snap + pb, c->stream));
+        CUDA_TRY(c, cudaMemcpyAsync(snap, L.pops, pb, cudaMemcpyDeviceToDevice,
+                                    c->stream));
+    } else {
+        const size_t nring = ring_elems(L);
+        for (int k = 0; k < 2; ++k)
+            for (int r = 0; r < R_COUNT; ++r)
+                CUDA_TRY(c, cudaMemsetAsync(L.ring[k][r], 0,
+                                            nring * rho_bytes(L.precision),
+                                            c->stream));
+        CUDA_TRY(c, cudaMemcpyAsync(L.pops, snap, pb, cudaMemcpyDeviceToDevice,
+                                    c->stream));
+        CUDA_TRY(c, cudaMemcpyAsync(L.rho[p], snap + pb, rb,
+                                    cudaMemcpyDeviceToDevice, c->stream));
+    }
+    return LBM_OK;
+}
+}  // namespace
+
+lbm_status lbm_autotune(lbm_ctx *c, int nsteps, int *best_tx, int *best_ty)
+{
+    if (!c) return fail(nullptr, LBM_ERR_ARG, "null context");
+    if (!c->initialized) return fail(c, LBM_ERR_STATE, "lbm_init must come first");
+    if (nsteps < 2) nsteps = 2;
+    nsteps &= ~1;
+    CUDA_TRY(c, cudaSetDevice(c->device));
+    Lattice &L = c->L;
+    const size_t bytes = 8 * (size_t)L.plane * pop_bytes(L.precision) +
+                         (size_t)L.plane * rho_bytes(L.precision);
+    char *snap = nullptr;
+    CUDA_TRY(c, cudaMalloc(&snap, bytes));
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    int tx[16], ty[16];
+    const int n = step_shapes(tx, ty, 16);
+    const long long t0 = c->t;
+    int best = -1;
+    float best_ms = 0.f;
+    lbm_status st = snapshot(c, snap, true);
+    cudaError_t e = cudaSuccess;
+    if (st == LBM_OK) e = cudaEventCreate(&e0);
+    if (st == LBM_OK && e == cudaSuccess) e = cudaEventCreate(&e1);
+    for (int k = 0; k < n && st == LBM_OK && e == cudaSuccess; ++k) {
+        if (!step_shape_supported(L.precision, tx[k], ty[k])) continue;
+        L.tx = tx[k];
+        L.ty = ty[k];
+        st = snapshot(c, snap, false);
+        c->t = t0;
+        for (int w = 0; w < 2 && e == cudaSuccess; ++w, ++c->t)
+            e = launch_step(L, (int)(c->t & 1), (int)(c->t & 1), c->stream);
+        if (e == cudaSuccess) e = cudaEventRecord(e0, c->stream);
+        for (int s = 0; s < nsteps && e == cudaSuccess; ++s, ++c->t)
+            e = launch_step(L, (int)(c->t & 1), (int)(c->t & 1), c->stream);
+        if (e == cudaSuccess) e = cudaEventRecord(e1, c->stream);
+        if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+        float ms = 0.f;
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+        if (e == cudaSuccess && (best < 0 || ms < best_ms)) {
+            best = k;
+            best_ms = ms;
+        }
+    }
+    if (st == LBM_OK && e == cudaSuccess && best >= 0) {
+        L.tx = tx[best];
+        L.ty = ty[best];
+        st = snapshot(c, snap, false);
+        c->t = t0;
+        if (st == LBM_OK) e = cudaStreamSynchronize(c->stream);
+    }
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    cudaFree(snap);
+    if (st != LBM_OK) return st;
+    if (e != cudaSuccess)
+        return fail(c, LBM_ERR_CUDA, "autotune: %s", cudaGetErrorString(e));
+    if (best_tx) *best_tx = L.tx;
+    if (best_ty) *best_ty = L.ty;
+    return LBM_OK;
+}
+
 lbm_status lbm_get_tile(const lbm_ctx *c, int *tx, int *ty)
 {
     if (!c || !tx || !ty) return fail(nullptr, LBM_ERR_ARG, "null argument");

@@ -78,6 +78,9 @@ cudaError_t launch_step(const Lattice &L, int parity, int cur,
 // and the default shape of a precision.
 bool step_shape_supported(int prec, int tx, int ty);
 void step_default_shape(int prec, int *tx, int *ty);
+// The compiled tile shapes, in a fixed order: returns how many, fills up to
+// `max` pairs.
+int step_shapes(int *tx, int *ty, int max);
 
 // fields.cu
 // Equilibrium initial state from double fields [ny][nx] on the device:

@@ -496,6 +496,17 @@ bool step_shape_supported(int prec, int tx, int ty)
     return false;
 }
 
+int step_shapes(int *tx, int *ty, int max)
+{
+    int n = 0;
+#define CPLBM_CASE(a, b)                    \
+    if (n < max) { tx[n] = a; ty[n] = b; }  \
+    ++n;
+    CPLBM_STEP_SHAPES(CPLBM_CASE)
+#undef CPLBM_CASE
+    return n;
+}
+
 void step_default_shape(int prec, int *tx, int *ty)
 {
     *tx = 32;

@@ -1,0 +1,136 @@
+"""Observables of each storage precision against the FP64 oracle.
+
+The hot path's precision variants (FP64; FP32; FP32 offset f_i - w_i rho_ref;
+FP16 offset with an FP32 density) must reproduce the oracle's converged
+observables: coexistence densities of a flat interface (< 0.5 %), the
+Laplace slope of static drops (< 1 %) and the contact angle on a wall with a
+surface chemical potential (< 1 degree).  The FP16 storage errors are
+stated by the same tests with their own, wider bounds.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from oracle import observables as ob
+from oracle import thermo
+from paper_1611_00907_gb300 import Simulation, inputs
+
+pytestmark = pytest.mark.gpu
+
+CS = dict(eos="cs", a=1.0, b=4.0, R=1.0, Tr=0.85, tau=1.0, kappa=0.5)
+# precision -> (rho_ref, slab tol, laplace tol, angle tol [deg])
+PRECISIONS = {
+    "f64": (0.0, 1e-9, 1e-6, 1e-6),
+    "f32": (0.0, 5e-3, 1e-2, 1.0),
+    "f32_offset": (None, 5e-3, 1e-2, 1.0),
+    "f16_offset": (None, 5e-2, 5e-2, 5.0),
+}
+
+
+@pytest.fixture(scope="module")
+def cs_eos():
+    e = thermo.make_eos("cs", 1.0, 4.0, 1.0, 0.85)
+    rv, rl, mc, _ = thermo.maxwell(e)
+    return e, rv, rl, mc
+
+
+def _ref(prec, rv, rl):
+    r = PRECISIONS[prec][0]
+    return 0.5 * (rv + rl) if r is None else r
+
+
+@pytest.fixture(scope="module")
+def slab_oracle(cs_eos):
+    e, rv, rl, _ = cs_eos
+    oracle.set_threads(8)
+    L = oracle.Lattice(8, 64, e, 1.0, 0.5)
+    L.init_equilibrium(inputs.slab(8, 64, rl, rv, 4.0)).step(5000)
+    oracle.set_threads(1)
+    return ob.slab_bulk(L.moments()["rho"])
+
+
+@pytest.mark.parametrize("prec", list(PRECISIONS))
+def test_coexistence_densities(prec, cs_eos, slab_oracle):
+    e, rv, rl, _ = cs_eos
+    with Simulation(8, 64, precision=prec, rho_ref=_ref(prec, rv, rl),
+                    **CS) as sim:
+        sim.init(inputs.slab(8, 64, rl, rv, 4.0)).step(5000)
+        hi, lo = ob.slab_bulk(sim.moments()["rho"])
+    tol = PRECISIONS[prec][1]
+    assert hi == pytest.approx(slab_oracle[0], rel=tol)
+    assert lo == pytest.approx(slab_oracle[1], rel=tol)
+
+
+@pytest.fixture(scope="module")
+def wall_oracle(cs_eos):
+    e, rv, rl, mc = cs_eos
+    oracle.set_threads(8)
+    L = oracle.Lattice(128, 64, e, 1.0, 0.5, walls=True, mu_bottom=mc + 0.03)
+    L.init_equilibrium(inputs.wall_drop(128, 64, 24, rl, rv, 4.0)).step(6000)
+    oracle.set_threads(1)
+    return ob.contact_angle(L.moments()["rho"], rl, rv)[0]
+
+
+@pytest.mark.parametrize("prec", list(PRECISIONS))
+def test_contact_angle(prec, cs_eos, wall_oracle):
+    e, rv, rl, mc = cs_eos
+    with Simulation(128, 64, precision=prec, rho_ref=_ref(prec, rv, rl),
+                    walls=True, mu_bottom=mc + 0.03, **CS) as sim:
+        sim.init(inputs.wall_drop(128, 64, 24, rl, rv, 4.0)).step(6000)
+        theta = ob.contact_angle(sim.moments()["rho"], rl, rv)[0]
+    assert abs(theta - wall_oracle) < PRECISIONS[prec][3], (theta, wall_oracle)
+
+
+def _laplace_points(run):
+    pts = []
+    for r in (14, 20):
+        dp, req = run(r)
+        pts.append((1.0 / req, dp))
+    (x1, y1), (x2, y2) = pts
+    return (y2 - y1) / (x2 - x1)
+
+
+@pytest.fixture(scope="module")
+def laplace_oracle(cs_eos):
+    e, rv, rl, _ = cs_eos
+    oracle.set_threads(8)
+
+    def run(r):
+        L = oracle.Lattice(64, 64, e, 1.0, 0.5)
+        L.init_equilibrium(inputs.drop(64, 64, r, rl, rv, 4.0)).step(5000)
+        return ob.laplace_jump(e, L.moments()["rho"])
+
+    slope = _laplace_points(run)
+    oracle.set_threads(1)
+    return slope
+
+
+@pytest.mark.parametrize("prec", list(PRECISIONS))
+def test_laplace_slope(prec, cs_eos, laplace_oracle):
+    e, rv, rl, _ = cs_eos
+
+    def run(r):
+        with Simulation(64, 64, precision=prec, rho_ref=_ref(prec, rv, rl),
+                        **CS) as sim:
+            sim.init(inputs.drop(64, 64, r, rl, rv, 4.0)).step(5000)
+            return ob.laplace_jump(e, sim.moments()["rho"])
+
+    slope = _laplace_points(run)
+    assert slope == pytest.approx(laplace_oracle, rel=PRECISIONS[prec][2])
+    sigma = thermo.surface_tension(e, 0.5)
+    assert slope == pytest.approx(sigma, rel=0.08)
+
+
+@pytest.mark.parametrize("prec", ["f32", "f32_offset", "f16_offset"])
+def test_mass_conserved_in_reduced_precision(prec, cs_eos):
+    e, rv, rl, mc = cs_eos
+    with Simulation(131, 37, precision=prec, rho_ref=_ref(prec, rv, rl),
+                    walls=True, mu_bottom=mc, **CS) as sim:
+        sim.init(inputs.wall_drop(131, 37, 12, rl, rv, 4.0))
+        m0 = sim.reduce()[0]
+        sim.step(2000)
+        m1, px, py, _ = sim.reduce()
+    # FP32 round-off of the density itself; the FP16 populations' rounding
+    # is absorbed by the rest population, so mass stays FP32-exact
+    assert abs(m1 - m0) / m0 < 1e-5
+    assert np.isfinite(px) and np.isfinite(py)
