@@ -3,6 +3,7 @@
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <new>
 #include <string>
@@ -24,6 +25,9 @@ struct lbm_ctx {
     double *d_prev = nullptr;  // density snapshot of lbm_reduce [ny][nx]
     double *d_tmp = nullptr;   // staging for host-side field transfers
     size_t tmp_bytes = 0;
+    int *d_err = nullptr;      // kernel error flags (Lattice::err)
+    TmaMaps maps{};            // tensor maps of the TMA interior path
+    bool use_tma = true;
     std::string err;
 };
 
@@ -164,6 +168,29 @@ void free_all(lbm_ctx *c)
     cudaFree(c->d_bad);
     cudaFree(c->d_prev);
     cudaFree(c->d_tmp);
+    cudaFree(c->d_err);
+}
+
+// Tensor maps for the current tile shape (the TMA path is skipped when they
+// cannot be built, e.g. for FP16 storage).
+void refresh_maps(lbm_ctx *c)
+{
+    char msg[256];
+    c->maps.valid = 0;
+    if (c->use_tma) build_tma_maps(c->L, &c->maps, msg, sizeof msg);
+}
+
+// Kernel error flags: a bounded wait inside a kernel gave up.
+lbm_status check_kernel_flags(lbm_ctx *c)
+{
+    int flags = 0;
+    CUDA_TRY(c, cudaMemcpy(&flags, c->d_err, sizeof(int), cudaMemcpyDeviceToHost));
+    if (flags) {
+        CUDA_TRY(c, cudaMemset(c->d_err, 0, sizeof(int)));
+        return fail(c, LBM_ERR_CUDA, "a step kernel's wait for its data timed out "
+                    "(flags %d); the affected tiles were not updated", flags);
+    }
+    return LBM_OK;
 }
 
 struct StateHeader {
@@ -258,11 +285,18 @@ lbm_status lbm_create(const lbm_config *cfg, lbm_ctx **out)
     alloc((void **)&c->d_red, 4 * sizeof(double));
     alloc((void **)&c->d_bad, sizeof(int));
     alloc((void **)&c->d_prev, (size_t)L.nx * L.ny * sizeof(double));
+    alloc((void **)&c->d_err, sizeof(int));
+    if (st == LBM_OK && cudaMemset(c->d_err, 0, sizeof(int)) != cudaSuccess)
+        st = fail(nullptr, LBM_ERR_CUDA, "cudaMemset failed");
     if (st != LBM_OK) {
         free_all(c);
         delete c;
         return st;
     }
+    L.err = c->d_err;
+    const char *no_tma = getenv("CPLBM_NO_TMA");
+    c->use_tma = !(no_tma && no_tma[0] == '1');
+    refresh_maps(c);
     *out = c;
     return LBM_OK;
 }
@@ -342,6 +376,7 @@ lbm_status lbm_set_tile(lbm_ctx *c, int tx, int ty)
     }
     c->L.tx = tx;
     c->L.ty = ty;
+    refresh_maps(c);
     return LBM_OK;
 }
 
@@ -400,13 +435,16 @@ lbm_status lbm_autotune(lbm_ctx *c, int nsteps, int *best_tx, int *best_ty)
         if (!step_shape_supported(L.precision, tx[k], ty[k])) continue;
         L.tx = tx[k];
         L.ty = ty[k];
+        refresh_maps(c);
         st = snapshot(c, snap, false);
         c->t = t0;
         for (int w = 0; w < 2 && e == cudaSuccess; ++w, ++c->t)
-            e = launch_step(L, (int)(c->t & 1), (int)(c->t & 1), c->stream);
+            e = launch_step(L, (int)(c->t & 1), (int)(c->t & 1), c->stream,
+                            &c->maps);
         if (e == cudaSuccess) e = cudaEventRecord(e0, c->stream);
         for (int s = 0; s < nsteps && e == cudaSuccess; ++s, ++c->t)
-            e = launch_step(L, (int)(c->t & 1), (int)(c->t & 1), c->stream);
+            e = launch_step(L, (int)(c->t & 1), (int)(c->t & 1), c->stream,
+                            &c->maps);
         if (e == cudaSuccess) e = cudaEventRecord(e1, c->stream);
         if (e == cudaSuccess) e = cudaEventSynchronize(e1);
         float ms = 0.f;
@@ -419,6 +457,7 @@ lbm_status lbm_autotune(lbm_ctx *c, int nsteps, int *best_tx, int *best_ty)
     if (st == LBM_OK && e == cudaSuccess && best >= 0) {
         L.tx = tx[best];
         L.ty = ty[best];
+        refresh_maps(c);
         st = snapshot(c, snap, false);
         c->t = t0;
         if (st == LBM_OK) e = cudaStreamSynchronize(c->stream);
@@ -518,7 +557,7 @@ lbm_status lbm_step(lbm_ctx *c, int nsteps)
     CUDA_TRY(c, cudaSetDevice(c->device));
     for (int k = 0; k < nsteps; ++k) {
         const int p = (int)(c->t & 1);
-        CUDA_TRY(c, launch_step(c->L, p, p, c->stream));
+        CUDA_TRY(c, launch_step(c->L, p, p, c->stream, &c->maps));
         ++c->t;
     }
     return LBM_OK;
@@ -537,6 +576,10 @@ lbm_status lbm_moments(lbm_ctx *c, double *rho, double *vx, double *vy,
         CUDA_TRY(c, launch_macro(L, p, p, rho, vx, vy, mu, nullptr, nullptr,
                                  nullptr, c->stream));
         CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+    {
+        lbm_status fs = check_kernel_flags(c);
+        if (fs != LBM_OK) return fs;
+    }
         return LBM_OK;
     }
     lbm_status s = ensure_tmp(c, 4 * field);
@@ -551,6 +594,10 @@ lbm_status lbm_moments(lbm_ctx *c, double *rho, double *vx, double *vy,
             CUDA_TRY(c, cudaMemcpyAsync(h[k], d[k], field, cudaMemcpyDeviceToHost,
                                         c->stream));
     CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+    {
+        lbm_status fs = check_kernel_flags(c);
+        if (fs != LBM_OK) return fs;
+    }
     return LBM_OK;
 }
 
@@ -574,6 +621,10 @@ lbm_status lbm_get_populations(lbm_ctx *c, double *f, int on_device)
     if (!on_device)
         CUDA_TRY(c, cudaMemcpyAsync(f, dst, bytes, cudaMemcpyDeviceToHost, c->stream));
     CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+    {
+        lbm_status fs = check_kernel_flags(c);
+        if (fs != LBM_OK) return fs;
+    }
     return LBM_OK;
 }
 
@@ -595,6 +646,10 @@ lbm_status lbm_reduce(lbm_ctx *c, double out[4])
     CUDA_TRY(c, cudaMemcpyAsync(&bad, c->d_bad, sizeof(int), cudaMemcpyDeviceToHost,
                                 c->stream));
     CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+    {
+        lbm_status fs = check_kernel_flags(c);
+        if (fs != LBM_OK) return fs;
+    }
     for (int k = 0; k < 4; ++k) out[k] = h[k];
     if (bad)
         return fail(c, LBM_ERR_NUMERIC, "%d fluid node(s) with non-finite "

@@ -5,6 +5,7 @@
 #include <cstddef>
 #include <cstdint>
 
+#include <cuda.h>  // CUtensorMap (tensor-map descriptors only)
 #include <cuda_runtime.h>
 
 namespace cplbm {
@@ -61,7 +62,25 @@ struct Lattice {
     double mu_bottom, mu_top;
     int top_mode;
     int precision;
+    int *err;            // device flag: a bounded wait in a kernel gave up
 };
+
+// Tensor-map descriptors for the TMA loads of the step's interior tiles:
+// the population array (3-D: x, fluid row, plane) and the two density
+// buffers (2-D), with boxes sized for the tile shape (tx, ty).
+struct TmaMaps {
+    CUtensorMap pops;
+    CUtensorMap rho[2];
+    int valid;
+    int tx, ty;
+};
+
+// tma.cu: build the maps for lattice L and its current tile shape; false
+// (with a message) when the layout does not allow TMA.
+bool build_tma_maps(const Lattice &L, TmaMaps *m, char *err, size_t errlen);
+
+// Bits of Lattice::err.
+enum { ERR_WAIT_TIMEOUT = 1 };
 
 // Sizes of the storage types per precision.
 inline size_t pop_bytes(int prec)
@@ -73,7 +92,7 @@ inline size_t rho_bytes(int prec) { return prec == P_F64 ? 8 : 4; }
 // Launchers (step.cu).  `cur` selects rho[cur] / ring[cur] as the current
 // density and `parity` the AA phase of the step being taken.
 cudaError_t launch_step(const Lattice &L, int parity, int cur,
-                        cudaStream_t s);
+                        cudaStream_t s, const TmaMaps *maps = nullptr);
 // Whether the step has a kernel for tile shape tx x ty in precision prec,
 // and the default shape of a precision.
 bool step_shape_supported(int prec, int tx, int ty);

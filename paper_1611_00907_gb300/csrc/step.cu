@@ -161,18 +161,14 @@ __device__ __forceinline__ void mu_interior(const Lattice &L,
 }
 
 // BGK collision of one node with the velocity-shift forcing.  f[1..8] are
-// the node's stored populations, drho its stored density (rho - rho_ref)
-// and rho the absolute one; fp[0..8] receive the post-collision values in
-// stored form.
+// the node's stored populations (f_0 = drho - sum f_i is implicit), drho
+// its stored density (rho - rho_ref) and rho the absolute one; fp[0..8]
+// receive the post-collision values in stored form.
 template <class real>
 __device__ __forceinline__ void collide(const real *f, real drho, real rho,
                                         real Fx, real Fy, real tau, real omega,
                                         real *fp)
 {
-    real sum = real(0);
-#pragma unroll
-    for (int i = 1; i < 9; ++i) sum += f[i];
-    const real f0 = drho - sum;
     // u = sum f_i e_i / rho; u_eq = u + tau F / rho (Sec. II)
     const real jx = (f[1] - f[3]) + (f[5] - f[7]) + (f[8] - f[6]);
     const real jy = (f[2] - f[4]) + (f[5] - f[7]) + (f[6] - f[8]);
@@ -183,8 +179,7 @@ __device__ __forceinline__ void collide(const real *f, real drho, real rho,
     // Eq. 14 in stored form: f_eq - w_i rho_ref = w_i (drho + rho P_i(u)),
     // P_i = 3 e.u + 4.5 (e.u)^2 - 1.5 u^2; opposite directions share the
     // even part of P.
-    const real w0 = real(4.0 / 9.0), w1 = real(1.0 / 9.0), w5 = real(1.0 / 36.0);
-    fp[0] = f0 + omega * (w0 * (drho - rho * usq) - f0);
+    const real w1 = real(1.0 / 9.0), w5 = real(1.0 / 36.0);
     {
         const real ex2 = real(4.5) * ux * ux - usq, ey2 = real(4.5) * uy * uy - usq;
         const real ax = w1 * (drho + rho * ex2), bx = w1 * rho * real(3) * ux;
@@ -204,6 +199,12 @@ __device__ __forceinline__ void collide(const real *f, real drho, real rho,
         fp[8] = f[8] + omega * ((a8 + b8) - f[8]);
         fp[6] = f[6] + omega * ((a8 - b8) - f[6]);
     }
+    // The rest population takes what the moving ones leave of the density:
+    // in exact arithmetic this equals f_0 + omega (f_0^eq - f_0) with
+    // f_0 = drho - sum_{i>0} f_i, and it keeps the collision's mass exact
+    // instead of biased by the rounding of f_eq.
+    fp[0] = drho - (((fp[1] + fp[2]) + (fp[3] + fp[4])) +
+                    ((fp[5] + fp[6]) + (fp[7] + fp[8])));
 }
 
 // Index of f*_i (i = 1..8) of tile node (lx, ly) in s_post.
@@ -424,14 +425,306 @@ __device__ __forceinline__ void step_tile(const Lattice &L, int cur, int X0,
     }
 }
 
+// ---------------------------------------------------------------------------
+// Interior tiles with TMA.  One thread issues nine tensor copies per tile:
+// the density halo (a (TX + 8) x (TY + 4) box from x = X0 - 4, the nearest
+// 16-byte-aligned column) and, per direction, the (TX + 8) x TY box of the
+// plane and rows that direction is read from in this step's AA order.  They
+// complete on one mbarrier; the partial sums of the halo's edge nodes come by
+// per-element cp.async.  Staged rows have pitch RP = TX + 8 with the tile's
+// column 0 at offset 4, and the post-collision values later overwrite the
+// staged populations in the same layout.  Lanes map to x (TX = 32) and each
+// warp owns PER consecutive rows, so a thread's stencil windows overlap and
+// are loaded once.
+// ---------------------------------------------------------------------------
+template <class real, int TX, int TY>
+struct TmaSmem {
+    static constexpr int RP = TX + 8;
+    static constexpr int PLANE = TY * RP;
+    static constexpr int NRHO = (TY + 4) * RP;
+    static constexpr int MP = TX + 2, MH = TY + 2;
+    static constexpr int NRING = StepSmem<real, TX, TY>::NRING;
+    static constexpr int NMU = MP * MH;
+    static constexpr size_t bar_offset =
+        (sizeof(real) * (8 * PLANE + NRHO + NRING + NMU) + 15) / 16 * 16;
+    static constexpr size_t bytes = bar_offset + 16;
+    static constexpr unsigned tx_bytes = sizeof(real) * (8 * PLANE + NRHO);
+};
+
+// Partial density of position (ox, oy) from post-collision values staged
+// with row pitch P and column offset OFF (general checks, as handover_sum).
+template <class real, int TY, int P, int OFF>
+__device__ __forceinline__ real handover_sum_staged(const Lattice &L,
+                                                    const real *s_post, int ox,
+                                                    int oy, int wx, int wy, int r,
+                                                    bool inside, real self0)
+{
+    real s = inside ? self0 : real(0);
+#pragma unroll
+    for (int i = 1; i < 9; ++i) {
+        const int sx = ox - ex(i), sy = oy - ey(i);
+        if (inside && L.walls && row_is_solid(L, r - ey(i))) {
+            s += s_post[((opp(i) - 1) * TY + oy) * P + ox + OFF];
+        } else if (sx >= 0 && sx < wx && sy >= 0 && sy < wy) {
+            s += s_post[((i - 1) * TY + sy) * P + sx + OFF];
+        }
+    }
+    return s;
+}
+
+// Gradient of the isotropic stencil from a 3 x 3 window w[row][col] (row 0
+// below, col 0 left), same arithmetic as grad9.
+template <class T>
+__device__ __forceinline__ void grad_w(const T (&w)[3][3], T &gx, T &gy)
+{
+    const T ne = w[2][2], nw = w[2][0], se = w[0][2], sw = w[0][0];
+    gx = (T(4) * (w[1][2] - w[1][0]) + (ne - nw) + (se - sw)) * T(1.0 / 12.0);
+    gy = (T(4) * (w[2][1] - w[0][1]) + (ne + nw) - (se + sw)) * T(1.0 / 12.0);
+}
+
+template <class S, int TX, int TY, int NT, int PARITY>
+__device__ __forceinline__ void step_tile_tma(const Lattice &L, int cur, int X0,
+                                              int Y0, unsigned char *smem_raw,
+                                              const TmaMaps &maps)
+{
+    using real = typename S::real;
+    using pop_t = typename S::pop_t;
+    using rho_t = typename S::rho_t;
+    using TS = TmaSmem<real, TX, TY>;
+    static_assert(TX == 32, "lanes map to x");
+    static_assert(sizeof(pop_t) == sizeof(real), "populations staged as stored");
+    constexpr int NW = NT / 32, PER = TY / NW;
+    static_assert(PER * NW == TY, "warps own whole row blocks");
+    constexpr int RP = TS::RP, PLANE = TS::PLANE, MP = TS::MP, MH = TS::MH;
+    constexpr int WR = TX + 4, HR = TY + 4;  // halo geometry of the ring staging
+    real *s_pin = reinterpret_cast<real *>(smem_raw);  // [8][TY][RP]
+    real *s_rho = s_pin + 8 * PLANE;                     // [TY + 4][RP]
+    real *s_ring = s_rho + TS::NRHO;
+    real *s_mu = s_ring + TS::NRING;                     // [MH][MP]
+    unsigned long long *bar =
+        reinterpret_cast<unsigned long long *>(smem_raw + TS::bar_offset);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int nxt = cur ^ 1;
+
+    // 1. Loads.  Density halo and populations by TMA (thread 0), partial
+    //    sums by cp.async (all threads).
+    if (threadIdx.x == 0) mbar_init(bar, 1);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        mbar_expect_tx(bar, TS::tx_bytes);
+        tma_load_2d(s_rho, &maps.rho[cur], X0 - 4, Y0 - 2, bar);
+#pragma unroll
+        for (int i = 1; i < 9; ++i) {
+            const int plane = PARITY == 0 ? i - 1 : opp(i) - 1;
+            const int y0 = PARITY == 0 ? Y0 : Y0 - ey(i);
+            tma_load_3d(s_pin + (i - 1) * PLANE, &maps.pops, X0 - 4, y0, plane, bar);
+        }
+    }
+    {
+        using rt = rho_t;
+        rt *const *ring = (rt *const *)L.ring[cur];
+        for (int p = threadIdx.x; p < TS::NRING; p += NT) {
+            int c, lx, ly;
+            if (p < 4 * HR) {
+                const int ci = p / HR;
+                ly = p % HR;
+                lx = edge_col<TX>(ci);
+                c = col_is_left(ci) ? R_L : R_R;
+            } else if (p < 4 * HR + 4 * WR) {
+                const int q = p - 4 * HR, ri = q / WR;
+                lx = q % WR;
+                ly = edge_col<TY>(ri);
+                c = row_is_below(ri) ? R_B : R_T;
+            } else {
+                const int q = p - 4 * HR - 4 * WR, ci = q / 4, ri = q % 4;
+                lx = edge_col<TX>(ci);
+                ly = edge_col<TY>(ri);
+                c = row_is_below(ri) ? (col_is_left(ci) ? R_BL : R_BR)
+                                     : (col_is_left(ci) ? R_TL : R_TR);
+            }
+            const int x = X0 + lx - 2, r = Y0 + ly - 2;
+            const long long idx =
+                (c == R_L || c == R_R) ? cidx(L, r, x) : fidx(L, r, x);
+            cp_async<sizeof(rt)>(&s_ring[p], ring[c] + idx);
+        }
+        cp_async_commit();
+    }
+    cp_async_wait_all();
+    const bool ok = mbar_wait(bar, 0, 2000000000LL);  // ~1 s at 2 GHz
+    if (__syncthreads_or(!ok)) {
+        // the copies did not land in time: flag it, give the copies another
+        // bounded wait so none is left writing into this block's memory,
+        // and leave the tile untouched
+        if (threadIdx.x == 0 && L.err) atomicOr(L.err, ERR_WAIT_TIMEOUT);
+        mbar_wait(bar, 0, 2000000000LL);
+        __syncthreads();
+        return;
+    }
+
+    // 2. Partial sums into the halo's tile-edge nodes (order of
+    //    load_rho_stored).  Halo (lx, ly) of the (TX + 4)-wide convention is
+    //    staged row ly, column lx + 2.
+    for (int q = threadIdx.x; q < 4 * HR + 4 * WR; q += NT) {
+        int lx, ly;
+        if (q < 4 * HR) {
+            lx = edge_col<TX>(q / HR);
+            ly = q % HR;
+        } else {
+            const int t = q - 4 * HR;
+            lx = t % WR;
+            ly = edge_col<TY>(t / WR);
+            if (col_index<TX>(lx) >= 0) continue;
+        }
+        const int ci = col_index<TX>(lx), ri = col_index<TY>(ly);
+        real v = s_rho[ly * RP + lx + 2];
+        if (ci >= 0) v += s_ring[ci * HR + ly];
+        if (ri >= 0) {
+            v += s_ring[4 * HR + ri * WR + lx];
+            if (ci >= 0) v += s_ring[4 * HR + 4 * WR + ci * 4 + ri];
+        }
+        s_rho[ly * RP + lx + 2] = v;
+    }
+    __syncthreads();
+
+    // 3. mu at (a, b), a in [0, TX + 2) <-> x = X0 - 1 + a, b in [0, TY + 2)
+    //    <-> r = Y0 - 1 + b; its density sits at staged (b + 1, a + 3).
+    {
+        const EosT<real> eos(L.eos);
+        const real kappa = (real)L.kappa;
+        const real ref = S::offset ? (real)L.rho_ref : real(0);
+        for (int b = warp; b < MH; b += NW) {  // columns 1..TX, one per lane
+            const int a = lane + 1, c = (b + 1) * RP + a + 3;
+            s_mu[b * MP + a] =
+                mu_bulk(eos, s_rho[c] + ref) - kappa * lap9<real, RP>(s_rho, c);
+        }
+        for (int t = threadIdx.x; t < 2 * MH; t += NT) {  // columns 0, TX + 1
+            const int a = (t & 1) ? TX + 1 : 0, b = t >> 1;
+            const int c = (b + 1) * RP + a + 3;
+            s_mu[b * MP + a] =
+                mu_bulk(eos, s_rho[c] + ref) - kappa * lap9<real, RP>(s_rho, c);
+        }
+    }
+    __syncthreads();
+
+    // 4. Force, collision, in-place streaming of the thread's PER nodes at
+    //    rows ly0 .. ly0 + PER - 1, column lx.  A node's post-collision
+    //    values overwrite staged slots that only lanes of the same row (the
+    //    same warp) read, so a warp barrier between reading a row and
+    //    writing it suffices.  Stencil windows roll down the rows.
+    const int lx = lane, ly0 = warp * PER;
+    const real tau = (real)L.tau;
+    const real omega = real(1) / tau;
+    const real rho_ref = S::offset ? (real)L.rho_ref : real(0);
+    pop_t *A = (pop_t *)L.pops;
+    long long woff[9];
+#pragma unroll
+    for (int i = 1; i < 9; ++i)
+        woff[i] = PARITY == 0 ? (long long)(opp(i) - 1) * L.plane
+                              : (long long)(i - 1) * L.plane +
+                                    (long long)ey(i) * L.pitch + ex(i);
+    // density window: staged rows ly + 1 .. ly + 3; mu: rows ly .. ly + 2
+    real wr[3][3], wm[3][3];
+#pragma unroll
+    for (int j = 0; j < 2; ++j)
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+            wr[j][d] = s_rho[(ly0 + 1 + j) * RP + lx + 3 + d];
+            wm[j][d] = s_mu[(ly0 + j) * MP + lx + d];
+        }
+    real self0[PER];
+#pragma unroll
+    for (int k = 0; k < PER; ++k) {
+        const int ly = ly0 + k, r = Y0 + ly, x = X0 + lx;
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+            wr[2][d] = s_rho[(ly + 3) * RP + lx + 3 + d];
+            wm[2][d] = s_mu[(ly + 2) * MP + lx + d];
+        }
+        real f[9];
+#pragma unroll
+        for (int i = 1; i < 9; ++i)
+            f[i] = s_pin[(i - 1) * PLANE + ly * RP + lx + 4 -
+                         (PARITY == 0 ? 0 : ex(i))];
+        __syncwarp();
+        const real drho = wr[1][1];
+        const real rho = drho + rho_ref;
+        real gmx, gmy, grx, gry;
+        grad_w(wm, gmx, gmy);
+        grad_w(wr, grx, gry);
+        const real Fx = grx * real(1.0 / 3.0) - rho * gmx;
+        const real Fy = gry * real(1.0 / 3.0) - rho * gmy;
+        real fp[9];
+        collide<real>(f, drho, rho, Fx, Fy, tau, omega, fp);
+        self0[k] = fp[0];
+        const long long base = (long long)r * L.pitch + x;
+#pragma unroll
+        for (int i = 1; i < 9; ++i) {
+            s_pin[(i - 1) * PLANE + ly * RP + lx + 4] = fp[i];
+            st_real(A + base + woff[i], fp[i]);
+        }
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+            wr[0][d] = wr[1][d]; wr[1][d] = wr[2][d];
+            wm[0][d] = wm[1][d]; wm[1][d] = wm[2][d];
+        }
+    }
+    __syncthreads();
+
+    // 5. Density hand-over (see the file comment).
+    rho_t *Rn = (rho_t *)L.rho[nxt];
+    rho_t *const *ring = (rho_t *const *)L.ring[nxt];
+#pragma unroll
+    for (int k = 0; k < PER; ++k) {
+        const int ly = ly0 + k, r = Y0 + ly;
+        real s;
+        if (lx >= 1 && lx <= TX - 2 && ly >= 1 && ly <= TY - 2) {
+            s = self0[k];
+#pragma unroll
+            for (int i = 1; i < 9; ++i)
+                s += s_pin[((i - 1) * TY + ly - ey(i)) * RP + lx + 4 - ex(i)];
+        } else {
+            s = handover_sum_staged<real, TY, RP, 4>(L, s_pin, lx, ly, TX, TY, r,
+                                                     true, self0[k]);
+        }
+        Rn[(long long)r * L.pitch + X0 + lx] = (rho_t)s;
+    }
+    constexpr int NRP = 2 * (TX + TY) + 4;
+    for (int p = threadIdx.x; p < NRP; p += NT) {
+        int ox, oy;
+        ring_position(p, TX, TY, ox, oy);
+        const int r = Y0 + oy, x = X0 + ox;
+        const real s = handover_sum_staged<real, TY, RP, 4>(
+            L, s_pin, ox, oy, TX, TY, r, false, real(0));
+        const int c = ring_class(ox, oy, TX, TY);
+        const long long idx =
+            (c == R_L || c == R_R) ? cidx(L, r, x) : fidx(L, r, x);
+        ring[c][idx] = (rho_t)s;
+    }
+}
+
+// Whether a (precision, tile) pair has the TMA interior path.
+template <class S, int TX, int TY, int NT>
+struct HasTma {
+    static constexpr bool value = TX == 32 && (TY % (NT / 32)) == 0 &&
+                                  sizeof(typename S::pop_t) ==
+                                      sizeof(typename S::real);
+};
+
 template <class S, int TX, int TY, int NT, int PARITY>
 __global__ void __launch_bounds__(NT)
-    step_kernel(const Lattice L, int cur, int xlo, int xhi, int ylo, int yhi)
+    step_kernel(const Lattice L, int cur, int xlo, int xhi, int ylo, int yhi,
+                const __grid_constant__ TmaMaps maps)
 {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
+    extern __shared__ __align__(128) unsigned char smem_raw[];
     const int bx = blockIdx.x, by = blockIdx.y;
     const int X0 = bx * TX, Y0 = by * TY;
     const bool interior = bx >= xlo && bx <= xhi && by >= ylo && by <= yhi;
+    if constexpr (HasTma<S, TX, TY, NT>::value) {
+        if (interior && maps.valid) {
+            step_tile_tma<S, TX, TY, NT, PARITY>(L, cur, X0, Y0, smem_raw, maps);
+            return;
+        }
+    }
     if (interior)
         step_tile<S, TX, TY, NT, PARITY, true>(L, cur, X0, Y0, smem_raw);
     else
@@ -440,11 +733,16 @@ __global__ void __launch_bounds__(NT)
 
 template <class S, int TX, int TY>
 static cudaError_t launch_shape(const Lattice &L, int parity, int cur,
-                                cudaStream_t s)
+                                cudaStream_t s, const TmaMaps *maps)
 {
     using real = typename S::real;
     constexpr int NT = STEP_THREADS;
-    const size_t smem = StepSmem<real, TX, TY>::bytes;
+    const size_t smem_v4 = StepSmem<real, TX, TY>::bytes;
+    const size_t smem_tma = HasTma<S, TX, TY, NT>::value
+                                ? TmaSmem<real, TX, TY>::bytes : 0;
+    const size_t smem = smem_v4 > smem_tma ? smem_v4 : smem_tma;
+    TmaMaps m{};
+    if (maps && maps->valid && maps->tx == TX && maps->ty == TY) m = *maps;
     auto k0 = step_kernel<S, TX, TY, NT, 0>;
     auto k1 = step_kernel<S, TX, TY, NT, 1>;
     static int configured = -1;  // device the attribute was set on
@@ -466,9 +764,9 @@ static cudaError_t launch_shape(const Lattice &L, int parity, int cur,
     const int nfx = L.nx / TX, nfy = L.nyf / TY;  // full tiles per direction
     dim3 grid(ntx, nty);
     if (parity == 0)
-        k0<<<grid, NT, smem, s>>>(L, cur, 1, nfx - 2, 1, nfy - 2);
+        k0<<<grid, NT, smem, s>>>(L, cur, 1, nfx - 2, 1, nfy - 2, m);
     else
-        k1<<<grid, NT, smem, s>>>(L, cur, 1, nfx - 2, 1, nfy - 2);
+        k1<<<grid, NT, smem, s>>>(L, cur, 1, nfx - 2, 1, nfy - 2, m);
     return cudaGetLastError();
 }
 
@@ -477,11 +775,11 @@ static cudaError_t launch_shape(const Lattice &L, int parity, int cur,
 
 template <class S>
 static cudaError_t launch_step_t(const Lattice &L, int parity, int cur,
-                                 cudaStream_t s)
+                                 cudaStream_t s, const TmaMaps *maps)
 {
 #define CPLBM_CASE(a, b)                                           \
     if (L.tx == a && L.ty == b)                                    \
-        return launch_shape<S, a, b>(L, parity, cur, s);
+        return launch_shape<S, a, b>(L, parity, cur, s, maps);
     CPLBM_STEP_SHAPES(CPLBM_CASE)
 #undef CPLBM_CASE
     return cudaErrorInvalidValue;
@@ -509,17 +807,20 @@ int step_shapes(int *tx, int *ty, int max)
 
 void step_default_shape(int prec, int *tx, int *ty)
 {
+    // fastest measured on GB300 for the 4096^2 workload (lbm_autotune picks
+    // per lattice)
     *tx = 32;
-    *ty = prec == P_F64 ? 16 : 24;
+    *ty = prec == P_F64 ? 16 : (prec == P_F16_OFF ? 24 : 32);
 }
 
-cudaError_t launch_step(const Lattice &L, int parity, int cur, cudaStream_t s)
+cudaError_t launch_step(const Lattice &L, int parity, int cur, cudaStream_t s,
+                        const TmaMaps *maps)
 {
     switch (L.precision) {
-    case P_F64: return launch_step_t<SF64>(L, parity, cur, s);
-    case P_F32: return launch_step_t<SF32>(L, parity, cur, s);
-    case P_F32_OFF: return launch_step_t<SF32Off>(L, parity, cur, s);
-    case P_F16_OFF: return launch_step_t<SF16Off>(L, parity, cur, s);
+    case P_F64: return launch_step_t<SF64>(L, parity, cur, s, maps);
+    case P_F32: return launch_step_t<SF32>(L, parity, cur, s, maps);
+    case P_F32_OFF: return launch_step_t<SF32Off>(L, parity, cur, s, maps);
+    case P_F16_OFF: return launch_step_t<SF16Off>(L, parity, cur, s, maps);
     }
     return cudaErrorInvalidValue;
 }

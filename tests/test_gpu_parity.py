@@ -132,6 +132,20 @@ def test_tile_switch_mid_run():
             sim.set_tile(48, 16)
 
 
+def test_autotune_keeps_the_state():
+    sim, ref, rho = _setup("cs", 200, 90, True)
+    with sim:
+        sim.init(rho).step(7)
+        before = sim.populations()
+        shape = sim.autotune(4)
+        assert shape == sim.tile
+        assert sim.step_count == 7
+        assert np.array_equal(sim.populations(), before)
+        sim.step(13)
+        ref.init_equilibrium(rho).step(20)
+        _compare(sim, ref, 1e-12)
+
+
 def test_top_wall_with_given_value():
     sim, ref, rho = _setup("cs", 70, 21, True, top_mode=1, mu_top=0.004)
     with sim:
