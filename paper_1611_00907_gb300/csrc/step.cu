@@ -432,10 +432,19 @@ __device__ __forceinline__ void step_tile(const Lattice &L, int cur, int X0,
 // plane and rows that direction is read from in this step's AA order.  They
 // complete on one mbarrier; the partial sums of the halo's edge nodes come by
 // per-element cp.async.  Staged rows have pitch RP = TX + 8 with the tile's
-// column 0 at offset 4, and the post-collision values later overwrite the
-// staged populations in the same layout.  Lanes map to x (TX = 32) and each
-// warp owns PER consecutive rows, so a thread's stencil windows overlap and
-// are loaded once.
+// column 0 at offset 4.
+//
+// Lanes map to x (TX = 32) and each warp owns PER consecutive rows, walked
+// bottom to top.  Stencil windows roll with the rows, and the density
+// hand-over is done in registers: a node's next density is
+//   same(k) + up(k - 1) + down(k + 1),
+// same = f*_0 + f*_1 from the left lane + f*_3 from the right lane,
+// up   = f*_2 + f*_5 from the left + f*_6 from the right (to the row above),
+// down = f*_4 + f*_8 from the left + f*_7 from the right (to the row below),
+// with lane neighbours by warp shuffles.  Only each warp's first "down" and
+// last "up" cross to the neighbouring warp, through shared memory.  Lane 0
+// and lane 31 carry the same sums for the tile's left and right ring
+// columns; the first and last warps write the bottom and top ring rows.
 // ---------------------------------------------------------------------------
 template <class real, int TX, int TY>
 struct TmaSmem {
@@ -445,32 +454,12 @@ struct TmaSmem {
     static constexpr int MP = TX + 2, MH = TY + 2;
     static constexpr int NRING = StepSmem<real, TX, TY>::NRING;
     static constexpr int NMU = MP * MH;
+    static constexpr int NXCH = 2 * (STEP_THREADS / 32) * (TX + 2);
     static constexpr size_t bar_offset =
-        (sizeof(real) * (8 * PLANE + NRHO + NRING + NMU) + 15) / 16 * 16;
+        (sizeof(real) * (8 * PLANE + NRHO + NRING + NMU + NXCH) + 15) / 16 * 16;
     static constexpr size_t bytes = bar_offset + 16;
     static constexpr unsigned tx_bytes = sizeof(real) * (8 * PLANE + NRHO);
 };
-
-// Partial density of position (ox, oy) from post-collision values staged
-// with row pitch P and column offset OFF (general checks, as handover_sum).
-template <class real, int TY, int P, int OFF>
-__device__ __forceinline__ real handover_sum_staged(const Lattice &L,
-                                                    const real *s_post, int ox,
-                                                    int oy, int wx, int wy, int r,
-                                                    bool inside, real self0)
-{
-    real s = inside ? self0 : real(0);
-#pragma unroll
-    for (int i = 1; i < 9; ++i) {
-        const int sx = ox - ex(i), sy = oy - ey(i);
-        if (inside && L.walls && row_is_solid(L, r - ey(i))) {
-            s += s_post[((opp(i) - 1) * TY + oy) * P + ox + OFF];
-        } else if (sx >= 0 && sx < wx && sy >= 0 && sy < wy) {
-            s += s_post[((i - 1) * TY + sy) * P + sx + OFF];
-        }
-    }
-    return s;
-}
 
 // Gradient of the isotropic stencil from a 3 x 3 window w[row][col] (row 0
 // below, col 0 left), same arithmetic as grad9.
@@ -480,6 +469,14 @@ __device__ __forceinline__ void grad_w(const T (&w)[3][3], T &gx, T &gy)
     const T ne = w[2][2], nw = w[2][0], se = w[0][2], sw = w[0][0];
     gx = (T(4) * (w[1][2] - w[1][0]) + (ne - nw) + (se - sw)) * T(1.0 / 12.0);
     gy = (T(4) * (w[2][1] - w[0][1]) + (ne + nw) - (se + sw)) * T(1.0 / 12.0);
+}
+// Laplacian of the isotropic stencil from a 3 x 3 window, as lap9.
+template <class T>
+__device__ __forceinline__ T lap_w(const T (&w)[3][3])
+{
+    const T axial = w[1][2] + w[1][0] + w[2][1] + w[0][1];
+    const T diag = w[2][2] + w[2][0] + w[0][2] + w[0][0];
+    return (T(4) * axial + diag - T(20) * w[1][1]) * T(1.0 / 6.0);
 }
 
 template <class S, int TX, int TY, int NT, int PARITY>
@@ -494,13 +491,16 @@ __device__ __forceinline__ void step_tile_tma(const Lattice &L, int cur, int X0,
     static_assert(TX == 32, "lanes map to x");
     static_assert(sizeof(pop_t) == sizeof(real), "populations staged as stored");
     constexpr int NW = NT / 32, PER = TY / NW;
-    static_assert(PER * NW == TY, "warps own whole row blocks");
+    static_assert(PER * NW == TY && PER >= 2, "warps own whole row blocks");
     constexpr int RP = TS::RP, PLANE = TS::PLANE, MP = TS::MP, MH = TS::MH;
     constexpr int WR = TX + 4, HR = TY + 4;  // halo geometry of the ring staging
+    constexpr int XW = TX + 2;               // exchange slots per warp
     real *s_pin = reinterpret_cast<real *>(smem_raw);  // [8][TY][RP]
     real *s_rho = s_pin + 8 * PLANE;                     // [TY + 4][RP]
     real *s_ring = s_rho + TS::NRHO;
     real *s_mu = s_ring + TS::NRING;                     // [MH][MP]
+    real *s_up = s_mu + TS::NMU;                         // [NW][XW]
+    real *s_down = s_up + NW * XW;                       // [NW][XW]
     unsigned long long *bar =
         reinterpret_cast<unsigned long long *>(smem_raw + TS::bar_offset);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -588,41 +588,53 @@ __device__ __forceinline__ void step_tile_tma(const Lattice &L, int cur, int X0,
 
     // 3. mu at (a, b), a in [0, TX + 2) <-> x = X0 - 1 + a, b in [0, TY + 2)
     //    <-> r = Y0 - 1 + b; its density sits at staged (b + 1, a + 3).
+    //    Columns 1..TX: lane a - 1, each warp a run of consecutive rows with
+    //    a rolling 3 x 3 window; columns 0 and TX + 1 separately.
     {
         const EosT<real> eos(L.eos);
         const real kappa = (real)L.kappa;
         const real ref = S::offset ? (real)L.rho_ref : real(0);
-        for (int b = warp; b < MH; b += NW) {  // columns 1..TX, one per lane
-            const int a = lane + 1, c = (b + 1) * RP + a + 3;
-            s_mu[b * MP + a] =
-                mu_bulk(eos, s_rho[c] + ref) - kappa * lap9<real, RP>(s_rho, c);
+        const int b0 = (warp * MH) / NW, b1 = ((warp + 1) * MH) / NW;
+        const int a = lane + 1;
+        real w[3][3];
+#pragma unroll
+        for (int j = 0; j < 2; ++j)
+#pragma unroll
+            for (int d = 0; d < 3; ++d) w[j][d] = s_rho[(b0 + j) * RP + a + 2 + d];
+        for (int b = b0; b < b1; ++b) {
+#pragma unroll
+            for (int d = 0; d < 3; ++d) w[2][d] = s_rho[(b + 2) * RP + a + 2 + d];
+            s_mu[b * MP + a] = mu_bulk(eos, w[1][1] + ref) - kappa * lap_w(w);
+#pragma unroll
+            for (int d = 0; d < 3; ++d) {
+                w[0][d] = w[1][d];
+                w[1][d] = w[2][d];
+            }
         }
-        for (int t = threadIdx.x; t < 2 * MH; t += NT) {  // columns 0, TX + 1
-            const int a = (t & 1) ? TX + 1 : 0, b = t >> 1;
-            const int c = (b + 1) * RP + a + 3;
-            s_mu[b * MP + a] =
+        for (int t = threadIdx.x; t < 2 * MH; t += NT) {
+            const int ae = (t & 1) ? TX + 1 : 0, b = t >> 1;
+            const int c = (b + 1) * RP + ae + 3;
+            s_mu[b * MP + ae] =
                 mu_bulk(eos, s_rho[c] + ref) - kappa * lap9<real, RP>(s_rho, c);
         }
     }
     __syncthreads();
 
-    // 4. Force, collision, in-place streaming of the thread's PER nodes at
-    //    rows ly0 .. ly0 + PER - 1, column lx.  A node's post-collision
-    //    values overwrite staged slots that only lanes of the same row (the
-    //    same warp) read, so a warp barrier between reading a row and
-    //    writing it suffices.  Stencil windows roll down the rows.
+    // 4. Force, collision, in-place streaming and the register hand-over for
+    //    the thread's PER nodes at rows ly0 .. ly0 + PER - 1, column lx.
     const int lx = lane, ly0 = warp * PER;
     const real tau = (real)L.tau;
     const real omega = real(1) / tau;
     const real rho_ref = S::offset ? (real)L.rho_ref : real(0);
     pop_t *A = (pop_t *)L.pops;
-    long long woff[9];
+    rho_t *Rn = (rho_t *)L.rho[nxt];
+    rho_t *const *ring = (rho_t *const *)L.ring[nxt];
+    int woff[9];  // 32-bit: the TMA maps exist only when 8 planes fit
 #pragma unroll
     for (int i = 1; i < 9; ++i)
-        woff[i] = PARITY == 0 ? (long long)(opp(i) - 1) * L.plane
-                              : (long long)(i - 1) * L.plane +
-                                    (long long)ey(i) * L.pitch + ex(i);
-    // density window: staged rows ly + 1 .. ly + 3; mu: rows ly .. ly + 2
+        woff[i] = PARITY == 0 ? (opp(i) - 1) * (int)L.plane
+                              : (i - 1) * (int)L.plane + ey(i) * L.pitch + ex(i);
+    const bool has_l = lane > 0, has_r = lane < 31;
     real wr[3][3], wm[3][3];
 #pragma unroll
     for (int j = 0; j < 2; ++j)
@@ -631,10 +643,19 @@ __device__ __forceinline__ void step_tile_tma(const Lattice &L, int cur, int X0,
             wr[j][d] = s_rho[(ly0 + 1 + j) * RP + lx + 3 + d];
             wm[j][d] = s_mu[(ly0 + j) * MP + lx + d];
         }
-    real self0[PER];
+    // Rolling hand-over.  pend: row k - 1 without its "down" part;
+    // first: row 0 of the warp without the warp below's "up"; *_c: the same
+    // for the ring column a lane 0 / lane 31 feeds.
+    real pend = real(0), up_prev = real(0), first = real(0);
+    real pend_c = real(0), up_prev_c = real(0), first_c = real(0);
+    const int slot_c = TX + (lane == 31);        // exchange slot of a column
+    const int xc = lane == 0 ? X0 - 1 : X0 + TX;  // ring column of the lane
+    const int cls_c = lane == 0 ? R_R : R_L;
+    const bool col_lane = lane == 0 || lane == 31;
+    pop_t *Arow = A + (long long)(Y0 + ly0) * L.pitch + X0 + lx;
 #pragma unroll
     for (int k = 0; k < PER; ++k) {
-        const int ly = ly0 + k, r = Y0 + ly, x = X0 + lx;
+        const int ly = ly0 + k;
 #pragma unroll
         for (int d = 0; d < 3; ++d) {
             wr[2][d] = s_rho[(ly + 3) * RP + lx + 3 + d];
@@ -645,7 +666,6 @@ __device__ __forceinline__ void step_tile_tma(const Lattice &L, int cur, int X0,
         for (int i = 1; i < 9; ++i)
             f[i] = s_pin[(i - 1) * PLANE + ly * RP + lx + 4 -
                          (PARITY == 0 ? 0 : ex(i))];
-        __syncwarp();
         const real drho = wr[1][1];
         const real rho = drho + rho_ref;
         real gmx, gmy, grx, gry;
@@ -655,50 +675,85 @@ __device__ __forceinline__ void step_tile_tma(const Lattice &L, int cur, int X0,
         const real Fy = gry * real(1.0 / 3.0) - rho * gmy;
         real fp[9];
         collide<real>(f, drho, rho, Fx, Fy, tau, omega, fp);
-        self0[k] = fp[0];
-        const long long base = (long long)r * L.pitch + x;
 #pragma unroll
-        for (int i = 1; i < 9; ++i) {
-            s_pin[(i - 1) * PLANE + ly * RP + lx + 4] = fp[i];
-            st_real(A + base + woff[i], fp[i]);
+        for (int i = 1; i < 9; ++i) st_real(Arow + woff[i], fp[i]);
+        Arow += L.pitch;
+
+        // lane-neighbour parts of the hand-over
+        const real f1l = __shfl_up_sync(0xffffffffu, fp[1], 1);
+        const real f5l = __shfl_up_sync(0xffffffffu, fp[5], 1);
+        const real f8l = __shfl_up_sync(0xffffffffu, fp[8], 1);
+        const real f3r = __shfl_down_sync(0xffffffffu, fp[3], 1);
+        const real f6r = __shfl_down_sync(0xffffffffu, fp[6], 1);
+        const real f7r = __shfl_down_sync(0xffffffffu, fp[7], 1);
+        const real same = fp[0] + (has_l ? f1l : real(0)) + (has_r ? f3r : real(0));
+        const real up = fp[2] + (has_l ? f5l : real(0)) + (has_r ? f6r : real(0));
+        const real down = fp[4] + (has_l ? f8l : real(0)) + (has_r ? f7r : real(0));
+        // ring columns: lane 0 feeds x = X0 - 1 (f*_3; f*_6 up; f*_7 down),
+        // lane 31 feeds x = X0 + TX (f*_1; f*_5 up; f*_8 down)
+        const real same_c = lane == 0 ? fp[3] : fp[1];
+        const real up_c = lane == 0 ? fp[6] : fp[5];
+        const real down_c = lane == 0 ? fp[7] : fp[8];
+        if (k == 0) {
+            // this row's "down" belongs to the warp below (or the ring row
+            // under the tile)
+            s_down[warp * XW + lane] = down;
+            if (col_lane) s_down[warp * XW + slot_c] = down_c;
+            pend = same;
+            pend_c = same_c;
+        } else {
+            const real done = pend + down;        // row ly - 1
+            const real done_c = pend_c + down_c;
+            if (k == 1) {
+                first = done;
+                first_c = done_c;
+            } else {
+                Rn[(long long)(Y0 + ly - 1) * L.pitch + X0 + lx] = (rho_t)done;
+                if (col_lane) ring[cls_c][cidx(L, Y0 + ly - 1, xc)] = (rho_t)done_c;
+            }
+            pend = same + up_prev;
+            pend_c = same_c + up_prev_c;
         }
+        up_prev = up;
+        up_prev_c = up_c;
 #pragma unroll
         for (int d = 0; d < 3; ++d) {
             wr[0][d] = wr[1][d]; wr[1][d] = wr[2][d];
             wm[0][d] = wm[1][d]; wm[1][d] = wm[2][d];
         }
     }
+    // up_prev: the warp's last-row "up", for the warp above (or the ring
+    // row over the tile).
+    s_up[warp * XW + lane] = up_prev;
+    if (col_lane) s_up[warp * XW + slot_c] = up_prev_c;
     __syncthreads();
-
-    // 5. Density hand-over (see the file comment).
-    rho_t *Rn = (rho_t *)L.rho[nxt];
-    rho_t *const *ring = (rho_t *const *)L.ring[nxt];
-#pragma unroll
-    for (int k = 0; k < PER; ++k) {
-        const int ly = ly0 + k, r = Y0 + ly;
-        real s;
-        if (lx >= 1 && lx <= TX - 2 && ly >= 1 && ly <= TY - 2) {
-            s = self0[k];
-#pragma unroll
-            for (int i = 1; i < 9; ++i)
-                s += s_pin[((i - 1) * TY + ly - ey(i)) * RP + lx + 4 - ex(i)];
-        } else {
-            s = handover_sum_staged<real, TY, RP, 4>(L, s_pin, lx, ly, TX, TY, r,
-                                                     true, self0[k]);
+    {
+        // last row: add the warp above's first-row "down"
+        real top = pend, top_c = pend_c;
+        if (warp + 1 < NW) {
+            top += s_down[(warp + 1) * XW + lane];
+            top_c += s_down[(warp + 1) * XW + slot_c];
         }
-        Rn[(long long)r * L.pitch + X0 + lx] = (rho_t)s;
+        Rn[(long long)(Y0 + ly0 + PER - 1) * L.pitch + X0 + lx] = (rho_t)top;
+        if (col_lane) ring[cls_c][cidx(L, Y0 + ly0 + PER - 1, xc)] = (rho_t)top_c;
+        // first row: add the warp below's last-row "up"
+        if (warp > 0) {
+            first += s_up[(warp - 1) * XW + lane];
+            first_c += s_up[(warp - 1) * XW + slot_c];
+        }
+        Rn[(long long)(Y0 + ly0) * L.pitch + X0 + lx] = (rho_t)first;
+        if (col_lane) ring[cls_c][cidx(L, Y0 + ly0, xc)] = (rho_t)first_c;
     }
-    constexpr int NRP = 2 * (TX + TY) + 4;
-    for (int p = threadIdx.x; p < NRP; p += NT) {
-        int ox, oy;
-        ring_position(p, TX, TY, ox, oy);
-        const int r = Y0 + oy, x = X0 + ox;
-        const real s = handover_sum_staged<real, TY, RP, 4>(
-            L, s_pin, ox, oy, TX, TY, r, false, real(0));
-        const int c = ring_class(ox, oy, TX, TY);
-        const long long idx =
-            (c == R_L || c == R_R) ? cidx(L, r, x) : fidx(L, r, x);
-        ring[c][idx] = (rho_t)s;
+    // ring rows below and above the tile, with their corners
+    if (warp == 0) {
+        ring[R_T][fidx(L, Y0 - 1, X0 + lx)] = (rho_t)s_down[lane];
+        if (lane == 0) ring[R_TR][fidx(L, Y0 - 1, X0 - 1)] = (rho_t)s_down[TX];
+        if (lane == 31) ring[R_TL][fidx(L, Y0 - 1, X0 + TX)] = (rho_t)s_down[TX + 1];
+    }
+    if (warp == NW - 1) {
+        ring[R_B][fidx(L, Y0 + TY, X0 + lx)] = (rho_t)up_prev;
+        if (lane == 0) ring[R_BR][fidx(L, Y0 + TY, X0 - 1)] = (rho_t)up_prev_c;
+        if (lane == 31) ring[R_BL][fidx(L, Y0 + TY, X0 + TX)] = (rho_t)up_prev_c;
     }
 }
 

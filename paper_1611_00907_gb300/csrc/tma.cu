@@ -38,6 +38,11 @@ bool build_tma_maps(const Lattice &L, TmaMaps *m, char *err, size_t errlen)
     const CUtensorMapDataType dt = L.precision == P_F64
                                        ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64
                                        : CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
+    if (8LL * L.plane + 2LL * L.pitch >= 2147483647LL) {
+        // the TMA path addresses the planes with 32-bit offsets
+        snprintf(err, errlen, "lattice too large for 32-bit plane offsets");
+        return false;
+    }
     if ((L.pitch * es) % 16 || (L.plane * es) % 16 || L.tx != 32) {
         snprintf(err, errlen, "layout not TMA-aligned (pitch %d, tile %dx%d)",
                  L.pitch, L.tx, L.ty);

@@ -104,11 +104,14 @@ def test_1000_steps_fp64(case, walls, size, oracle_threads):
 
 
 @pytest.mark.parametrize("tile", [(32, 16), (32, 24), (32, 32), (64, 16)])
+# FP32: mu = psi'(rho) - kappa lap(rho) cancels terms ~100x its size, so
+# eps_32 ~ 6e-8 becomes ~1e-5 relative per evaluation and grows over steps.
 @pytest.mark.parametrize("precision,tol,steps", [("f64", 1e-12, 60),
-                                                 ("f32", 3e-5, 60)])
+                                                 ("f32", 1e-4, 60)])
 def test_every_tile_shape(tile, precision, tol, steps):
-    # 200 x 90 with walls: interior tiles, ragged edge tiles, both parities
-    sim, ref, rho = _setup("cs", 200, 90, True, precision=precision)
+    # 230 x 140 with walls: interior tiles (TMA path for 32-wide tiles),
+    # ragged edge tiles, both parities
+    sim, ref, rho = _setup("cs", 230, 140, True, precision=precision)
     with sim:
         sim.set_tile(*tile)
         assert sim.tile == tile
@@ -117,6 +120,19 @@ def test_every_tile_shape(tile, precision, tol, steps):
         g, w = sim.moments(), ref.moments()
         for k in ("rho", "mu", "vx", "vy"):
             assert _rel(g[k], w[k]) < tol, (k, _rel(g[k], w[k]))
+
+
+@pytest.mark.parametrize("tile", [(32, 16), (32, 24), (32, 32), (64, 16)])
+@pytest.mark.parametrize("walls,size", [(True, (260, 200)), (False, (224, 165))])
+def test_interior_tiles_many_steps_fp64(tile, walls, size, oracle_threads):
+    # lattices with several rows and columns of interior tiles, 400 steps
+    nx, ny = size
+    sim, ref, rho = _setup("cs", nx, ny, walls)
+    with sim:
+        sim.set_tile(*tile)
+        sim.init(rho).step(400)
+        ref.init_equilibrium(rho).step(400)
+        _compare(sim, ref, 1e-11)
 
 
 def test_tile_switch_mid_run():
