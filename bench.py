@@ -223,6 +223,83 @@ def measure_e2e(precision, steps, warmup, rho, check_every):
             "seconds": dt, "check_every": check_every}
 
 
+def batch_specs(which):
+    """Specs and initial densities of a batched workload (library
+    coexistence densities)."""
+    from paper_1611_00907_gb300 import eos_coexistence, inputs
+    if which == "uneven":
+        specs = inputs.uneven_batch(256)
+    else:
+        _, _, mc = eos_coexistence("vdw", 9 / 49, 2 / 21, 1.0, 0.85)
+        specs = inputs.wetting_sweep(32, mu_coex=mc)
+    fields = []
+    for sp in specs:
+        rv, rl, _ = eos_coexistence(sp["eos"], sp["a"], sp["b"], 1.0, sp["Tr"],
+                                    sp.get("omega", 0.344))
+        fields.append(inputs.initial_density(sp, rv, rl))
+    keep = ("nx", "ny", "walls", "tau", "kappa", "eos", "a", "b", "Tr",
+            "omega", "mu_bottom")
+    return [{k: v for k, v in sp.items() if k in keep} for sp in specs], fields
+
+
+def measure_batch(which, precision, steps, warmup, sequential=True):
+    """One persistent launch per step over every lattice (graph-replayed),
+    and the same lattices stepped one by one, each its own launch."""
+    import math
+    import torch
+    from paper_1611_00907_gb300 import Batch, LbmError, Simulation
+    specs, fields = batch_specs(which)
+    stream = torch.cuda.Stream()
+    nodes = sum(sp["nx"] * sp["ny"] for sp in specs)
+    out = {"instances": len(specs), "nodes": nodes, "steps": steps,
+           "precision": precision, "unit": "MLUPS"}
+    with torch.cuda.stream(stream):
+        with Batch(specs, precision=precision,
+                   stream=stream.cuda_stream) as b:
+            for k, f in enumerate(fields):
+                b.init(k, f)
+            out["tile"] = list(b.autotune(6))
+            b.step(warmup)
+            torch.cuda.synchronize()
+            t0 = torch.cuda.Event(enable_timing=True)
+            t1 = torch.cuda.Event(enable_timing=True)
+            t0.record(stream)
+            b.step(steps)
+            t1.record(stream)
+            torch.cuda.synchronize()
+            ms = t0.elapsed_time(t1)
+            out["value"] = nodes * steps / (ms * 1e-3) / 1e6
+            out["ms_per_step"] = ms / steps
+            finite = 0
+            for k in range(len(specs)):
+                try:
+                    finite += math.isfinite(b.reduce(k)[0])
+                except LbmError:   # non-finite values on that lattice
+                    pass
+            out["finite_fraction"] = finite / len(specs)
+        if sequential:
+            sims = []
+            for sp, f in zip(specs, fields):
+                kw = {k: v for k, v in sp.items() if k not in ("nx", "ny")}
+                sim = Simulation(sp["nx"], sp["ny"], precision=precision,
+                                 stream=stream.cuda_stream, **kw)
+                sims.append(sim.init(f))
+            for sim in sims:
+                sim.step(warmup)
+            torch.cuda.synchronize()
+            t0.record(stream)
+            for _ in range(steps):
+                for sim in sims:
+                    sim.step(1)
+            t1.record(stream)
+            torch.cuda.synchronize()
+            ms = t0.elapsed_time(t1)
+            out["sequential_value"] = nodes * steps / (ms * 1e-3) / 1e6
+            for sim in sims:
+                sim.close()
+    return out
+
+
 def cpu_baseline(budget_s=15.0):
     """The oracle as it stands (FP64 C) on a 512 x 512 sample of the same
     workload, all host cores."""
@@ -323,6 +400,8 @@ def main():
                     help="lattice side (profiling runs use smaller cases)")
     ap.add_argument("--tile", default=None,
                     help="step tile shape TXxTY (default: the library's)")
+    ap.add_argument("--batch-steps", type=int, default=100,
+                    help="steps of the batched workloads (0: skip them)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     rank, world = dist_setup()
@@ -361,6 +440,15 @@ def main():
                           args.check_every)
         e2e["value"] = world * e2e["value"]
 
+    batches = {}
+    if args.batch_steps > 0:
+        batches["batch_uneven"] = measure_batch("uneven", "f32",
+                                                args.batch_steps, 4)
+        batches["batch_wetting"] = measure_batch("wetting", "f32",
+                                                 args.batch_steps, 4)
+        batches["batch_wetting_f16"] = measure_batch(
+            "wetting", "f16_offset", args.batch_steps, 4, sequential=False)
+
     base = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         base = cpu_baseline()
@@ -375,6 +463,7 @@ def main():
                 "roofline": roofline(args.precision, ms_step, n_nodes, args.n),
                 "fp64": fp64, "e2e": e2e, "cpu_baseline": base,
                 "gpu_launches": args.steps, "clocks": clocks.summary()}
+        line.update(batches)
         print(json.dumps(line))
     if world > 1:
         import torch.distributed as dist

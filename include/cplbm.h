@@ -166,6 +166,53 @@ lbm_status lbm_eos_info(const lbm_ctx *ctx, double *T, double *alpha,
 lbm_status lbm_eos_critical(int eos, double a, double b, double R,
                             double *Tc, double *rhoc);
 
+/* ------------------------------------------------------------------------
+ * Batches: many independent lattices (different sizes, EOS, temperatures,
+ * relaxation times, wall chemical potentials; one precision) advanced
+ * together by one persistent kernel launch per step over all their tiles,
+ * with blocks of 16 steps replayed from a captured CUDA graph.  Every
+ * lattice follows the same update as lbm_step.  Lattice i is addressed by
+ * its index in the array given to lbm_batch_create.
+ * ------------------------------------------------------------------------ */
+typedef struct lbm_batch lbm_batch;
+
+typedef struct {
+    int nx, ny, walls;      /* as lbm_config */
+    double tau, kappa, rho_ref;
+    int eos;                /* as lbm_set_eos */
+    double a, b, R, T_over_Tc, omega;
+    double mu_bottom;       /* as lbm_set_wall_mu */
+    int top_mode;
+    double mu_top;
+} lbm_instance;
+
+/* Create count lattices on one device.  stream NULL: the batch creates its
+ * own (graph capture needs one); else all work goes to that stream.  On
+ * error *out is NULL and lbm_batch_last_error(NULL) explains. */
+lbm_status lbm_batch_create(const lbm_instance *inst, int count, int precision,
+                            void *stream, int device, lbm_batch **out);
+/* lbm_init for lattice `index`; allowed while the batch has taken an even
+ * number of steps (the in-place order is then the natural one). */
+lbm_status lbm_batch_init(lbm_batch *b, int index, const double *rho,
+                          const double *ux, const double *uy, int on_device);
+/* Queue nsteps steps of every lattice; all must be initialised. */
+lbm_status lbm_batch_step(lbm_batch *b, int nsteps);
+/* Per-lattice lbm_moments, lbm_get_populations and lbm_reduce. */
+lbm_status lbm_batch_moments(lbm_batch *b, int index, double *rho, double *vx,
+                             double *vy, double *mu, int on_device);
+lbm_status lbm_batch_populations(lbm_batch *b, int index, double *f,
+                                 int on_device);
+lbm_status lbm_batch_reduce(lbm_batch *b, int index, double out[4]);
+/* Tile shape of the batched kernel (as lbm_set_tile), or the fastest one
+ * measured over nsteps steps with the state restored afterwards. */
+lbm_status lbm_batch_set_tile(lbm_batch *b, int tx, int ty);
+lbm_status lbm_batch_autotune(lbm_batch *b, int nsteps, int *tx, int *ty);
+/* Lattice count, total nodes, steps taken, tile shape (any may be NULL). */
+lbm_status lbm_batch_info(const lbm_batch *b, int *count, long long *nodes,
+                          long long *steps, int *tx, int *ty);
+void lbm_batch_destroy(lbm_batch *b);
+const char *lbm_batch_last_error(const lbm_batch *b);
+
 /* Allocation-free FP64 step, for callers that may not allocate device
  * memory: for example a host application whose own allocator owns the GPU
  * and forbids other code from calling cudaMalloc, or one that cannot accept
@@ -196,6 +243,14 @@ lbm_status lbm_step_noalloc(const lbm_config *cfg, int eos, double a,
                             double b, double R, double T_over_Tc,
                             double omega, double mu_bottom, int top_mode,
                             double mu_top, double *f, int nsteps);
+
+/* Coexisting vapour and liquid densities and their common chemical
+ * potential psi' at T = T_over_Tc * T_c (0 < T_over_Tc < 1): the Maxwell
+ * equal-area construction of Sec. III (equal p0 and equal psi').  Host-only
+ * helper for initial states. */
+lbm_status lbm_eos_coexistence(int eos, double a, double b, double R,
+                               double T_over_Tc, double omega, double *rho_v,
+                               double *rho_l, double *mu_coex);
 
 /* Release the context and its device memory.  NULL is ignored. */
 void lbm_destroy(lbm_ctx *ctx);

@@ -12,7 +12,8 @@ import numpy as np
 from . import _lib
 from ._lib import EOS, PRECISION, LbmError, check
 
-__all__ = ["Simulation", "LbmError", "eos_critical", "EOS", "PRECISION"]
+__all__ = ["Simulation", "Batch", "LbmError", "eos_critical",
+           "eos_coexistence", "EOS", "PRECISION"]
 
 
 def eos_critical(eos, a, b, R=1.0):
@@ -23,6 +24,17 @@ def eos_critical(eos, a, b, R=1.0):
                                float(a), float(b), float(R), C.byref(Tc),
                                C.byref(rc)))
     return Tc.value, rc.value
+
+
+def eos_coexistence(eos, a, b, R=1.0, Tr=0.85, omega=0.344):
+    """(rho_v, rho_l, mu_coex) of the Maxwell construction, from the library."""
+    lib = _lib.load()
+    v, l, m = C.c_double(), C.c_double(), C.c_double()
+    check(lib.lbm_eos_coexistence(EOS[eos] if isinstance(eos, str) else int(eos),
+                                  float(a), float(b), float(R), float(Tr),
+                                  float(omega), C.byref(v), C.byref(l),
+                                  C.byref(m)))
+    return v.value, l.value, m.value
 
 
 def _is_torch(x):
@@ -204,3 +216,125 @@ class Simulation:
         self._check(self._lib.lbm_set_state(self._ctx, buf.ctypes.data,
                                             buf.size))
         return self
+
+
+class Batch:
+    """Many independent lattices advanced together (one persistent kernel
+    launch per step, blocks of steps replayed from a CUDA graph).
+
+    instances: list of dicts with keys nx, ny and optionally walls, tau,
+    kappa, rho_ref, eos, a, b, R, Tr, omega, mu_bottom, top_mode, mu_top
+    (defaults as for Simulation).  All share one precision.
+    """
+
+    DEFAULTS = dict(walls=False, tau=1.0, kappa=0.5, rho_ref=0.0, eos="cs",
+                    a=1.0, b=4.0, R=1.0, Tr=0.85, omega=0.344, mu_bottom=0.0,
+                    top_mode=0, mu_top=0.0)
+
+    def __init__(self, instances, precision="f32", device=0, stream=None):
+        self._lib = _lib.load()
+        self.device = int(device)
+        self.specs = []
+        arr = (_lib.LbmInstance * len(instances))()
+        for k, spec in enumerate(instances):
+            d = dict(self.DEFAULTS)
+            d.update(spec)
+            self.specs.append(d)
+            arr[k] = _lib.LbmInstance(
+                int(d["nx"]), int(d["ny"]), int(bool(d["walls"])),
+                float(d["tau"]), float(d["kappa"]), float(d["rho_ref"]),
+                EOS[d["eos"]] if isinstance(d["eos"], str) else int(d["eos"]),
+                float(d["a"]), float(d["b"]), float(d["R"]), float(d["Tr"]),
+                float(d["omega"]), float(d["mu_bottom"]), int(d["top_mode"]),
+                float(d["mu_top"]))
+        if stream is None:
+            try:
+                import torch
+                if torch.cuda.is_available():
+                    s = torch.cuda.current_stream(self.device).cuda_stream
+                    stream = s if s else None
+            except ImportError:
+                stream = None
+        handle = C.c_void_p()
+        _lib.check_batch(self._lib.lbm_batch_create(
+            arr, len(instances), PRECISION[precision],
+            C.c_void_p(stream) if stream else None, self.device,
+            C.byref(handle)))
+        self._b = handle
+        self.precision = precision
+
+    def close(self):
+        if getattr(self, "_b", None):
+            self._lib.lbm_batch_destroy(self._b)
+            self._b = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __len__(self):
+        return len(self.specs)
+
+    def _check(self, status):
+        return _lib.check_batch(status, self._b)
+
+    def init(self, index, rho, ux=None, uy=None):
+        d = self.specs[index]
+        n = int(d["nx"]) * int(d["ny"])
+        pr, dr, kr = _arg(rho, n)
+        px, _, kx = _arg(ux, n)
+        py, _, ky = _arg(uy, n)
+        self._check(self._lib.lbm_batch_init(self._b, int(index), pr, px, py, dr))
+        del kr, kx, ky
+        return self
+
+    def step(self, n=1):
+        self._check(self._lib.lbm_batch_step(self._b, int(n)))
+        return self
+
+    def moments(self, index):
+        d = self.specs[index]
+        shape = (int(d["ny"]), int(d["nx"]))
+        out = {k: np.empty(shape) for k in ("rho", "vx", "vy", "mu")}
+        ptr = [out[k].ctypes.data for k in ("rho", "vx", "vy", "mu")]
+        self._check(self._lib.lbm_batch_moments(self._b, int(index), *ptr, 0))
+        return out
+
+    def populations(self, index):
+        d = self.specs[index]
+        f = np.empty((9, int(d["ny"]), int(d["nx"])))
+        self._check(self._lib.lbm_batch_populations(self._b, int(index),
+                                                    f.ctypes.data, 0))
+        return f
+
+    def reduce(self, index):
+        out = (C.c_double * 4)()
+        self._check(self._lib.lbm_batch_reduce(self._b, int(index), out))
+        return tuple(out)
+
+    def set_tile(self, tx, ty):
+        self._check(self._lib.lbm_batch_set_tile(self._b, int(tx), int(ty)))
+        return self
+
+    def autotune(self, nsteps=10):
+        tx, ty = C.c_int(), C.c_int()
+        self._check(self._lib.lbm_batch_autotune(self._b, int(nsteps),
+                                                 C.byref(tx), C.byref(ty)))
+        return tx.value, ty.value
+
+    def info(self):
+        cnt, nodes, steps = C.c_int(), C.c_longlong(), C.c_longlong()
+        tx, ty = C.c_int(), C.c_int()
+        self._check(self._lib.lbm_batch_info(self._b, C.byref(cnt),
+                                             C.byref(nodes), C.byref(steps),
+                                             C.byref(tx), C.byref(ty)))
+        return dict(count=cnt.value, nodes=nodes.value, steps=steps.value,
+                    tile=(tx.value, ty.value))

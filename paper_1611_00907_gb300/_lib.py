@@ -27,6 +27,16 @@ class LbmConfig(C.Structure):
                 ("stream", C.c_void_p), ("device", C.c_int)]
 
 
+class LbmInstance(C.Structure):
+    _fields_ = [("nx", C.c_int), ("ny", C.c_int), ("walls", C.c_int),
+                ("tau", C.c_double), ("kappa", C.c_double),
+                ("rho_ref", C.c_double), ("eos", C.c_int), ("a", C.c_double),
+                ("b", C.c_double), ("R", C.c_double),
+                ("T_over_Tc", C.c_double), ("omega", C.c_double),
+                ("mu_bottom", C.c_double), ("top_mode", C.c_int),
+                ("mu_top", C.c_double)]
+
+
 _dp = C.POINTER(C.c_double)
 _vp = C.c_void_p
 _ctx = C.c_void_p
@@ -52,10 +62,28 @@ SIGNATURES = {
     "lbm_eos_info": ([_ctx, _dp, _dp, _dp, _dp], C.c_int),
     "lbm_eos_critical": ([C.c_int, C.c_double, C.c_double, C.c_double, _dp,
                           _dp], C.c_int),
+    "lbm_eos_coexistence": ([C.c_int, C.c_double, C.c_double, C.c_double,
+                             C.c_double, C.c_double, _dp, _dp, _dp], C.c_int),
     "lbm_step_noalloc": ([C.POINTER(LbmConfig), C.c_int, C.c_double,
                           C.c_double, C.c_double, C.c_double, C.c_double,
                           C.c_double, C.c_int, C.c_double, _vp, C.c_int],
                          C.c_int),
+    "lbm_batch_create": ([C.POINTER(LbmInstance), C.c_int, C.c_int, _vp,
+                          C.c_int, C.POINTER(_ctx)], C.c_int),
+    "lbm_batch_init": ([_ctx, C.c_int, _vp, _vp, _vp, C.c_int], C.c_int),
+    "lbm_batch_step": ([_ctx, C.c_int], C.c_int),
+    "lbm_batch_moments": ([_ctx, C.c_int, _vp, _vp, _vp, _vp, C.c_int],
+                          C.c_int),
+    "lbm_batch_populations": ([_ctx, C.c_int, _vp, C.c_int], C.c_int),
+    "lbm_batch_reduce": ([_ctx, C.c_int, _dp], C.c_int),
+    "lbm_batch_set_tile": ([_ctx, C.c_int, C.c_int], C.c_int),
+    "lbm_batch_autotune": ([_ctx, C.c_int, C.POINTER(C.c_int),
+                            C.POINTER(C.c_int)], C.c_int),
+    "lbm_batch_info": ([_ctx, C.POINTER(C.c_int), C.POINTER(C.c_longlong),
+                        C.POINTER(C.c_longlong), C.POINTER(C.c_int),
+                        C.POINTER(C.c_int)], C.c_int),
+    "lbm_batch_destroy": ([_ctx], None),
+    "lbm_batch_last_error": ([_ctx], C.c_char_p),
     "lbm_destroy": ([_ctx], None),
     "lbm_last_error": ([_ctx], C.c_char_p),
 }
@@ -97,5 +125,12 @@ class LbmError(RuntimeError):
 def check(status, ctx=None):
     if status != LBM_OK:
         msg = load().lbm_last_error(ctx)
+        raise LbmError(status, msg.decode() if msg else "")
+    return status
+
+
+def check_batch(status, batch=None):
+    if status != LBM_OK:
+        msg = load().lbm_batch_last_error(batch)
         raise LbmError(status, msg.decode() if msg else "")
     return status

@@ -13,23 +13,7 @@
 
 using namespace cplbm;
 
-struct lbm_ctx {
-    Lattice L{};
-    int device = 0;
-    cudaStream_t stream = nullptr;
-    long long t = 0;
-    bool eos_set = false, initialized = false;
-    double T = 0, alpha = 1, Tc = 0, rhoc = 0;
-    double *d_red = nullptr;   // 4 reduction slots
-    int *d_bad = nullptr;      // error counter
-    double *d_prev = nullptr;  // density snapshot of lbm_reduce [ny][nx]
-    double *d_tmp = nullptr;   // staging for host-side field transfers
-    size_t tmp_bytes = 0;
-    int *d_err = nullptr;      // kernel error flags (Lattice::err)
-    TmaMaps maps{};            // tensor maps of the TMA interior path
-    bool use_tma = true;
-    std::string err;
-};
+#include "context.h"
 
 static thread_local std::string g_err;
 
@@ -137,6 +121,76 @@ double alpha_of(int kind, double Tr, double omega)
     else return 1.0;
     const double s = 1.0 + m * (1.0 - std::sqrt(Tr));
     return s * s;
+}
+
+// Printed bulk chemical potential psi'(rho) (Eqs. 18, 21, 24, 27 without
+// the gradient term), host FP64, for the coexistence solver.
+double host_mu(int kind, double a, double aa, double b, double RT, double r)
+{
+    const double q = 1.0 - b * r;
+    switch (kind) {
+    case EOS_VDW:
+        return RT * (std::log(r / q) + 1.0 / q) - 2.0 * a * r;
+    case EOS_RKS:
+        return RT * std::log(r / q) + RT / q - aa / b * std::log(1.0 + b * r) -
+               aa * r / (1.0 + b * r);
+    case EOS_PR: {
+        const double s2 = std::sqrt(2.0);
+        return RT * std::log(r / q) -
+               aa / (2.0 * s2 * b) * std::log((s2 - 1.0 + b * r) / (s2 + 1.0 - b * r)) +
+               RT / q - aa * r / (1.0 + 2.0 * b * r - b * b * r * r);
+    }
+    default: {  // CS
+        const double h = 0.25 * b * r, qc = 1.0 - h;
+        return RT * ((3.0 - h) / (qc * qc * qc) + std::log(r) + 1.0) - 2.0 * a * r;
+    }
+    }
+}
+
+// Root of a monotonic f on [lo, hi] (f(lo), f(hi) of opposite signs) by
+// bisection to the last representable midpoint.
+template <class F>
+double bisect(F f, double lo, double hi)
+{
+    double flo = f(lo);
+    for (int it = 0; it < 2000; ++it) {
+        const double mid = 0.5 * (lo + hi);
+        if (mid <= lo || mid >= hi) break;
+        const double fm = f(mid);
+        if ((fm < 0) == (flo < 0)) { lo = mid; flo = fm; } else { hi = mid; }
+    }
+    return 0.5 * (lo + hi);
+}
+
+// Coexisting densities by the Maxwell construction (Sec. III): the pressure
+// p_s at which the vapour and liquid branches of p0 have equal chemical
+// potential, found by bisection in p_s between the spinodal pressures.
+bool coexistence(int kind, double a, double b, double R, double Tr,
+                 double omega, double *rv, double *rl, double *muc)
+{
+    double Tc, rc;
+    if (!(Tr > 0 && Tr < 1) || !critical(kind, a, b, R, &Tc, &rc)) return false;
+    const double RT = R * Tr * Tc, aa = a * alpha_of(kind, Tr, omega);
+    const double top = pole(kind, b);
+    auto p = [&](double r) { return p0_dual(kind, aa, b, RT, D2{r, 1, 0}).v; };
+    auto dp = [&](double r) { return p0_dual(kind, aa, b, RT, D2{r, 1, 0}).d; };
+    if (!(dp(rc) < 0)) return false;
+    const double s1 = bisect(dp, 1e-12 * top, rc);   // dp0/drho = 0, vapour side
+    const double s2 = bisect(dp, rc, (1 - 1e-12) * top);
+    const double phi = p(s1), plo = std::max(p(s2), 0.0);
+    auto roots = [&](double ps, double *v, double *l) {
+        *v = bisect([&](double r) { return p(r) - ps; }, 1e-300, s1);
+        *l = bisect([&](double r) { return p(r) - ps; }, s2, (1 - 1e-14) * top);
+    };
+    auto g = [&](double ps) {
+        double v, l;
+        roots(ps, &v, &l);
+        return host_mu(kind, a, aa, b, RT, v) - host_mu(kind, a, aa, b, RT, l);
+    };
+    const double ps = bisect(g, plo + 1e-14 * std::fabs(phi), phi * (1 - 1e-12));
+    roots(ps, rv, rl);
+    *muc = 0.5 * (host_mu(kind, a, aa, b, RT, *rv) + host_mu(kind, a, aa, b, RT, *rl));
+    return std::isfinite(*rv) && std::isfinite(*rl) && *rv < *rl;
 }
 
 lbm_status ensure_tmp(lbm_ctx *c, size_t bytes)
@@ -311,6 +365,22 @@ lbm_status lbm_eos_critical(int eos, double a, double b, double R, double *Tc,
         return fail(nullptr, LBM_ERR_ARG, "a, b, R must be positive");
     if (!critical(eos, a, b, R, Tc, rhoc))
         return fail(nullptr, LBM_ERR_NUMERIC, "critical point not found");
+    return LBM_OK;
+}
+
+lbm_status lbm_eos_coexistence(int eos, double a, double b, double R,
+                               double T_over_Tc, double omega, double *rho_v,
+                               double *rho_l, double *mu_coex)
+{
+    if (!rho_v || !rho_l) return fail(nullptr, LBM_ERR_ARG, "null output");
+    if (eos < LBM_EOS_VDW || eos > LBM_EOS_RKS || !(a > 0 && b > 0 && R > 0))
+        return fail(nullptr, LBM_ERR_ARG, "invalid EOS parameters");
+    if (!(T_over_Tc > 0 && T_over_Tc < 1))
+        return fail(nullptr, LBM_ERR_ARG, "coexistence needs 0 < T/T_c < 1");
+    double mu = 0;
+    if (!coexistence(eos, a, b, R, T_over_Tc, omega, rho_v, rho_l, &mu))
+        return fail(nullptr, LBM_ERR_NUMERIC, "Maxwell construction failed");
+    if (mu_coex) *mu_coex = mu;
     return LBM_OK;
 }
 
@@ -739,3 +809,17 @@ const char *lbm_last_error(const lbm_ctx *c)
 }
 
 }  // extern "C"
+
+namespace cplbm {
+size_t ctx_state_bytes(const lbm_ctx *c)
+{
+    const Lattice &L = c->L;
+    return 8 * (size_t)L.plane * pop_bytes(L.precision) +
+           (size_t)L.plane * rho_bytes(L.precision);
+}
+lbm_status ctx_snapshot(lbm_ctx *c, char *snap, bool save)
+{
+    return snapshot(c, snap, save);
+}
+void ctx_refresh_maps(lbm_ctx *c) { refresh_maps(c); }
+}  // namespace cplbm

@@ -101,6 +101,20 @@ void step_default_shape(int prec, int *tx, int *ty);
 // `max` pairs.
 int step_shapes(int *tx, int *ty, int max);
 
+// A tile of one lattice of a batch: the persistent batched step walks a
+// list of these (step.cu).
+struct WorkItem {
+    int inst;      // index into the batch's Lattice array
+    int bx, by;    // tile position
+    int interior;  // the tile and its neighbours are full, no wrap or wall
+};
+// One step of every lattice of a batch in one launch: gridDim CTAs stride
+// over the work list.  All lattices share precision, tile shape and step
+// parity.  grid <= 0 picks one CTA per SM slot (occupancy-limited).
+cudaError_t launch_step_batch(const Lattice *d_lats, const WorkItem *d_items,
+                              int n_items, int parity, int cur, int precision,
+                              int tx, int ty, int grid, cudaStream_t s);
+
 // fields.cu
 // Equilibrium initial state from double fields [ny][nx] on the device:
 // fills pops (parity 0 order) and rho[0]/ring[0]; counts invalid densities

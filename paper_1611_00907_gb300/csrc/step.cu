@@ -828,6 +828,95 @@ static cudaError_t launch_shape(const Lattice &L, int parity, int cur,
 // Tile shapes with a compiled kernel (all precisions).
 #define CPLBM_STEP_SHAPES(X) X(32, 16) X(32, 24) X(32, 32) X(64, 16)
 
+// ---------------------------------------------------------------------------
+// Batched step: many independent lattices of different sizes and physics in
+// one persistent launch.  Each CTA takes work items blockIdx.x,
+// blockIdx.x + gridDim.x, ... and runs the general or interior tile path on
+// that item's lattice, whose descriptor it first copies to shared memory.
+// ---------------------------------------------------------------------------
+template <class S, int TX, int TY, int NT, int PARITY>
+__global__ void __launch_bounds__(NT)
+    step_batch_kernel(const Lattice *__restrict__ lats,
+                      const WorkItem *__restrict__ items, int n_items, int cur)
+{
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    __shared__ Lattice sL;
+    static_assert(sizeof(Lattice) % sizeof(int) == 0, "descriptor copy");
+    for (int w = blockIdx.x; w < n_items; w += gridDim.x) {
+        const WorkItem it = items[w];
+        {
+            const int *src = reinterpret_cast<const int *>(lats + it.inst);
+            int *dst = reinterpret_cast<int *>(&sL);
+            for (int q = threadIdx.x; q < (int)(sizeof(Lattice) / sizeof(int));
+                 q += NT)
+                dst[q] = src[q];
+        }
+        __syncthreads();
+        if (it.interior)
+            step_tile<S, TX, TY, NT, PARITY, true>(sL, cur, it.bx * TX,
+                                                   it.by * TY, smem_raw);
+        else
+            step_tile<S, TX, TY, NT, PARITY, false>(sL, cur, it.bx * TX,
+                                                    it.by * TY, smem_raw);
+        __syncthreads();  // smem and sL are reused by the next item
+    }
+}
+
+template <class S, int TX, int TY>
+static cudaError_t launch_batch_shape(const Lattice *d_lats,
+                                      const WorkItem *d_items, int n_items,
+                                      int parity, int cur, int grid,
+                                      cudaStream_t s)
+{
+    using real = typename S::real;
+    constexpr int NT = STEP_THREADS;
+    const size_t smem = StepSmem<real, TX, TY>::bytes;
+    auto k0 = step_batch_kernel<S, TX, TY, NT, 0>;
+    auto k1 = step_batch_kernel<S, TX, TY, NT, 1>;
+    static int configured = -1, slots = 0;
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (configured != dev) {
+        e = cudaFuncSetAttribute(k0, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)smem);
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(
+                k1, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        int per_sm = 0, sms = 0;
+        if (e == cudaSuccess)
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k0, NT, smem);
+        if (e == cudaSuccess)
+            e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (e != cudaSuccess) return e;
+        slots = (per_sm > 0 ? per_sm : 1) * sms;
+        configured = dev;
+    }
+    if (n_items <= 0) return cudaSuccess;
+    if (grid <= 0) grid = slots;
+    if (grid > n_items) grid = n_items;
+    if (parity == 0)
+        k0<<<grid, NT, smem, s>>>(d_lats, d_items, n_items, cur);
+    else
+        k1<<<grid, NT, smem, s>>>(d_lats, d_items, n_items, cur);
+    return cudaGetLastError();
+}
+
+template <class S>
+static cudaError_t launch_batch_t(const Lattice *d_lats, const WorkItem *d_items,
+                                  int n_items, int parity, int cur, int tx,
+                                  int ty, int grid, cudaStream_t s)
+{
+#define CPLBM_CASE(a, b)                                                   \
+    if (tx == a && ty == b)                                                \
+        return launch_batch_shape<S, a, b>(d_lats, d_items, n_items, parity, \
+                                           cur, grid, s);
+    CPLBM_STEP_SHAPES(CPLBM_CASE)
+#undef CPLBM_CASE
+    return cudaErrorInvalidValue;
+}
+
+
 template <class S>
 static cudaError_t launch_step_t(const Lattice &L, int parity, int cur,
                                  cudaStream_t s, const TmaMaps *maps)
@@ -866,6 +955,23 @@ void step_default_shape(int prec, int *tx, int *ty)
     // per lattice)
     *tx = 32;
     *ty = prec == P_F64 ? 16 : (prec == P_F16_OFF ? 24 : 32);
+}
+
+cudaError_t launch_step_batch(const Lattice *d_lats, const WorkItem *d_items,
+                              int n_items, int parity, int cur, int precision,
+                              int tx, int ty, int grid, cudaStream_t s)
+{
+    switch (precision) {
+    case P_F64:
+        return launch_batch_t<SF64>(d_lats, d_items, n_items, parity, cur, tx, ty, grid, s);
+    case P_F32:
+        return launch_batch_t<SF32>(d_lats, d_items, n_items, parity, cur, tx, ty, grid, s);
+    case P_F32_OFF:
+        return launch_batch_t<SF32Off>(d_lats, d_items, n_items, parity, cur, tx, ty, grid, s);
+    case P_F16_OFF:
+        return launch_batch_t<SF16Off>(d_lats, d_items, n_items, parity, cur, tx, ty, grid, s);
+    }
+    return cudaErrorInvalidValue;
 }
 
 cudaError_t launch_step(const Lattice &L, int parity, int cur, cudaStream_t s,

@@ -77,6 +77,65 @@ def uneven_sides(count, lo=64, hi=1024, seed=161100907):
     return np.rint(lo * (hi / lo) ** u).astype(np.int64)
 
 
+# The paper's parameter sets (Sec. III), with the vdW set of the wetting
+# sweep; kappa is chosen per EOS so the scheme stays stable across its
+# density range (0.5 for Carnahan-Starling, 0.01 for the cubic EOS whose
+# liquid densities are ~20x larger, as the paper's Sec. V run uses).
+EOS_SETS = {
+    "vdw": dict(a=9 / 49, b=2 / 21, kappa=0.01),
+    "cs": dict(a=1.0, b=4.0, kappa=0.5),
+    "pr": dict(a=2 / 49, b=2 / 21, kappa=0.01, omega=0.344),
+}
+
+
+def uneven_batch(count=256, seed=161100907, lo=64, hi=1024):
+    """Specs of a batch of uneven independent lattices: square sides
+    round(lo (hi/lo)^U), EOS uniform over vdW / CS / PR, T_r ~ U[0.6, 0.95],
+    tau ~ U[0.6, 1.2], a drop (radius ~ U[0.1, 0.3] side) or a slab with
+    probability 1/2 each, all from numpy PCG64 with `seed`."""
+    rng = np.random.default_rng(seed)
+    sides = np.rint(lo * (hi / lo) ** rng.uniform(0.0, 1.0, count))
+    kinds = rng.choice(["vdw", "cs", "pr"], size=count)
+    Tr = rng.uniform(0.6, 0.95, count)
+    tau = rng.uniform(0.6, 1.2, count)
+    geom = rng.choice(["drop", "slab"], size=count)
+    rfrac = rng.uniform(0.1, 0.3, count)
+    specs = []
+    for k in range(count):
+        e = dict(EOS_SETS[kinds[k]])
+        kappa = e.pop("kappa")
+        specs.append(dict(nx=int(sides[k]), ny=int(sides[k]), eos=str(kinds[k]),
+                          Tr=float(Tr[k]), tau=float(tau[k]), kappa=kappa,
+                          geometry=str(geom[k]), radius_fraction=float(rfrac[k]),
+                          **e))
+    return specs
+
+
+def wetting_sweep(count=32, nx=512, ny=256, mu_coex=0.0, mu_span=0.3):
+    """Specs of the wall-wetting sweep: vdW (a = 9/49, b = 2/21) at
+    T_r = 0.85 on nx x ny lattices with solid rows at the bottom and top, the
+    bottom wall's chemical potential evenly spaced over mu_coex +- mu_span/2."""
+    e = dict(EOS_SETS["vdw"])
+    kappa = e.pop("kappa")
+    mus = half_open_linspace(mu_coex - mu_span / 2, mu_coex + mu_span / 2, count)
+    return [dict(nx=nx, ny=ny, eos="vdw", Tr=0.85, tau=1.0, kappa=kappa,
+                 walls=True, mu_bottom=m, geometry="wall_drop", radius=60.0, **e)
+            for m in mus]
+
+
+def initial_density(spec, rho_v, rho_l):
+    """Initial field of one spec of uneven_batch / wetting_sweep."""
+    nx, ny = spec["nx"], spec["ny"]
+    width = 4.0 if spec["kappa"] >= 0.1 else 2.0
+    g = spec.get("geometry", "drop")
+    if g == "slab":
+        return slab(nx, ny, rho_l, rho_v, width)
+    if g == "wall_drop":
+        return wall_drop(nx, ny, spec["radius"], rho_l, rho_v, width)
+    r = spec.get("radius", spec.get("radius_fraction", 0.25) * min(nx, ny))
+    return drop(nx, ny, r, rho_l, rho_v, width)
+
+
 def ring_radii(lo, hi, count):
     """Evenly spaced radii from lo to hi, rounded to integers."""
     return [int(round(lo + (hi - lo) * k / (count - 1))) for k in range(count)]
@@ -88,4 +147,5 @@ def half_open_linspace(lo, hi, count):
 
 
 __all__ = ["tanh_profile", "slab", "drop", "wall_drop", "spinodal_noise",
-           "perturbed", "uneven_sides", "ring_radii", "half_open_linspace"]
+           "perturbed", "uneven_sides", "ring_radii", "half_open_linspace",
+           "EOS_SETS", "uneven_batch", "wetting_sweep", "initial_density"]

@@ -97,3 +97,25 @@ def test_critical_rejects_bad_eos(lib):
         _lib.LBM_ERR_ARG
     assert lib.lbm_eos_critical(1, -1, 1, 1, C.byref(Tc), C.byref(rc)) == \
         _lib.LBM_ERR_ARG
+
+
+@pytest.mark.parametrize("kind,eos,a,b", [("vdw", 0, 9 / 49, 2 / 21),
+                                          ("cs", 1, 1.0, 4.0),
+                                          ("pr", 2, 2 / 49, 2 / 21),
+                                          ("rks", 3, 2 / 49, 2 / 21)])
+@pytest.mark.parametrize("Tr", [0.6, 0.85, 0.95])
+def test_library_coexistence_matches_oracle(lib, kind, eos, a, b, Tr):
+    from oracle import thermo
+    v, l, m = C.c_double(), C.c_double(), C.c_double()
+    assert lib.lbm_eos_coexistence(eos, a, b, 1.0, Tr, 0.344, C.byref(v),
+                                   C.byref(l), C.byref(m)) == 0
+    rv, rl, mc, _ = thermo.maxwell(thermo.make_eos(kind, a, b, 1.0, Tr, 0.344))
+    assert v.value == pytest.approx(rv, rel=1e-9)
+    assert l.value == pytest.approx(rl, rel=1e-9)
+    assert m.value == pytest.approx(mc, rel=1e-9, abs=1e-12)
+
+
+def test_library_coexistence_rejects_supercritical(lib):
+    v, l = C.c_double(), C.c_double()
+    assert lib.lbm_eos_coexistence(1, 1.0, 4.0, 1.0, 1.02, 0.3, C.byref(v),
+                                   C.byref(l), None) == _lib.LBM_ERR_ARG

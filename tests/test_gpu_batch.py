@@ -1,0 +1,119 @@
+"""Batched lattices (one persistent launch per step over every lattice's
+tiles, blocks of steps from a CUDA graph) against the FP64 oracle and the
+single-lattice path, lattice by lattice."""
+import numpy as np
+import pytest
+
+import oracle
+from oracle import thermo
+from paper_1611_00907_gb300 import Batch, LbmError, Simulation, inputs
+
+pytestmark = pytest.mark.gpu
+
+# heterogeneous lattices: sizes with ragged tiles, walls, every EOS, taus
+SPECS = [
+    dict(nx=70, ny=21, eos="cs", a=1.0, b=4.0, Tr=0.85, tau=1.0, kappa=0.5),
+    dict(nx=131, ny=100, eos="cs", a=1.0, b=4.0, Tr=0.9, tau=0.9, kappa=0.5,
+         walls=True, mu_delta=0.02),
+    dict(nx=97, ny=40, eos="rks", a=2 / 49, b=2 / 21, Tr=0.8, tau=1.3,
+         kappa=0.01, walls=True, mu_delta=-0.05),
+    dict(nx=64, ny=64, eos="pr", a=2 / 49, b=2 / 21, Tr=0.85, tau=1.3,
+         kappa=0.01),
+    dict(nx=230, ny=140, eos="vdw", a=9 / 49, b=2 / 21, Tr=0.85, tau=1.0,
+         kappa=0.01, walls=True),
+]
+
+
+def _instances():
+    out = []
+    for s in SPECS:
+        e = thermo.make_eos(s["eos"], s["a"], s["b"], 1.0, s["Tr"], 0.344)
+        rv, rl, mc, _ = thermo.maxwell(e)
+        d = {k: v for k, v in s.items() if k != "mu_delta"}
+        d["mu_bottom"] = mc + s.get("mu_delta", 0.0)
+        width = 4.0 if s["eos"] == "cs" else 2.0
+        r = max(2.0, min(s["nx"], s["ny"]) / 4)
+        rho = (inputs.wall_drop(s["nx"], s["ny"], r, rl, rv, width)
+               if s.get("walls") else inputs.drop(s["nx"], s["ny"], r, rl, rv,
+                                                  width))
+        out.append((d, e, rho))
+    return out
+
+
+def _rel(got, want):
+    return np.abs(got - want).max() / np.abs(want).max()
+
+
+@pytest.mark.parametrize("steps", [37, 1])
+def test_batch_matches_oracle_per_lattice(steps, oracle_threads):
+    inst = _instances()
+    with Batch([d for d, _, _ in inst], precision="f64") as b:
+        for k, (_, _, rho) in enumerate(inst):
+            b.init(k, rho)
+        b.step(steps)          # odd: graph blocks of 16 plus single steps
+        assert b.info()["steps"] == steps
+        for k, (d, e, rho) in enumerate(inst):
+            ref = oracle.Lattice(d["nx"], d["ny"], e, d["tau"], d["kappa"],
+                                 walls=d.get("walls", False),
+                                 mu_bottom=d["mu_bottom"])
+            ref.init_equilibrium(rho).step(steps)
+            got, want = b.moments(k), ref.moments()
+            for key in ("rho", "mu", "vx", "vy"):
+                assert _rel(got[key], want[key]) < 1e-12, (k, key)
+            fg = b.populations(k)
+            for i in range(9):
+                assert _rel(fg[i], ref.f[i]) < 1e-12, (k, i)
+
+
+def test_batch_matches_single_lattice_runs():
+    inst = _instances()
+    with Batch([d for d, _, _ in inst], precision="f32") as b:
+        for k, (_, _, rho) in enumerate(inst):
+            b.init(k, rho)
+        b.step(50)
+        for k, (d, _, rho) in enumerate(inst):
+            kw = {x: d[x] for x in ("eos", "a", "b", "tau", "kappa", "walls",
+                                    "mu_bottom") if x in d}
+            with Simulation(d["nx"], d["ny"], Tr=d["Tr"], precision="f32",
+                            **kw) as sim:
+                sim.set_tile(*b.info()["tile"])
+                sim.init(rho).step(50)
+                one = sim.moments()
+            got = b.moments(k)
+            assert _rel(got["rho"], one["rho"]) < 1e-5
+
+
+def test_batch_autotune_keeps_state_and_reduce_conserves_mass():
+    inst = _instances()
+    with Batch([d for d, _, _ in inst], precision="f64") as b:
+        for k, (_, _, rho) in enumerate(inst):
+            b.init(k, rho)
+        b.step(4)
+        m0 = [b.reduce(k)[0] for k in range(len(inst))]
+        before = [b.populations(k) for k in range(len(inst))]
+        shape = b.autotune(4)
+        assert shape == b.info()["tile"]
+        assert b.info()["steps"] == 4
+        for k in range(len(inst)):
+            assert np.array_equal(b.populations(k), before[k])
+        b.step(40)
+        for k in range(len(inst)):
+            assert abs(b.reduce(k)[0] - m0[k]) / m0[k] < 1e-13
+
+
+def test_batch_rejects_init_at_odd_step_and_bad_index():
+    inst = _instances()[:2]
+    with Batch([d for d, _, _ in inst], precision="f32") as b:
+        with pytest.raises(LbmError):
+            b.step(1)                     # not initialised
+        for k, (_, _, rho) in enumerate(inst):
+            b.init(k, rho)
+        b.step(1)
+        with pytest.raises(LbmError):
+            b.init(0, inst[0][2])         # odd step count
+        with pytest.raises(IndexError):
+            b.moments(5)
+        # the C ABI checks the index itself
+        assert b._lib.lbm_batch_reduce(b._b, 5, None) == -1
+        b.step(1)
+        b.init(0, inst[0][2])             # even again: allowed
