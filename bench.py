@@ -35,7 +35,7 @@ N_SIDE = 4096
 EOS_ARGS = dict(eos="cs", a=1.0, b=4.0, R=1.0, Tr=0.85, tau=1.0, kappa=0.5)
 BYTES_PER_LU = {"f64": 144, "f32": 72, "f32_offset": 72, "f16_offset": 36}
 FALLBACK_HBM_GBS = 6800.0
-KERNEL_SOURCES = ["paper_1611_00907_gb300/csrc/step.cu",
+KERNEL_SOURCES = ["paper_1611_00907_gb300/csrc/step_impl.cuh",
                   "paper_1611_00907_gb300/csrc/device_common.cuh",
                   "paper_1611_00907_gb300/csrc/cplbm_internal.h"]
 
@@ -175,15 +175,28 @@ def time_steps(sim, steps, warmup):
     return t0.elapsed_time(t1)
 
 
-def measure_gpu(precision, steps, warmup, rho, tile=None):
+def measure_gpu(precision, steps, warmup, rho, tile=None, no_tma=False,
+                force_model=None):
     import torch
     from paper_1611_00907_gb300 import Simulation
     n = rho.shape[0]
     rho_dev = torch.tensor(rho, device="cuda")
-    sim = Simulation(n, n, precision=precision,
-                     rho_ref=0.15 if "offset" in precision else 0.0,
-                     **EOS_ARGS)
+    old = os.environ.get("CPLBM_NO_TMA")
+    if no_tma:
+        os.environ["CPLBM_NO_TMA"] = "1"
+    try:
+        sim = Simulation(n, n, precision=precision,
+                         rho_ref=0.15 if "offset" in precision else 0.0,
+                         **EOS_ARGS)
+    finally:
+        if no_tma:
+            if old is None:
+                os.environ.pop("CPLBM_NO_TMA")
+            else:
+                os.environ["CPLBM_NO_TMA"] = old
     with sim:
+        if force_model:
+            sim.set_force_model(force_model)
         if tile:
             sim.set_tile(*tile)
         sim.init(rho_dev)
@@ -402,6 +415,8 @@ def main():
                     help="step tile shape TXxTY (default: the library's)")
     ap.add_argument("--batch-steps", type=int, default=100,
                     help="steps of the batched workloads (0: skip them)")
+    ap.add_argument("--pt-steps", type=int, default=200,
+                    help="steps of the pressure-tensor comparison (0: skip)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     rank, world = dist_setup()
@@ -440,6 +455,22 @@ def main():
                           args.check_every)
         e2e["value"] = world * e2e["value"]
 
+    # The paper's efficiency claim (Sec. II, VI): the chemical-potential force
+    # against the pressure-tensor force it replaces, same kernel structure
+    # (general tile paths, no TMA), same lattice and tile.
+    pt = None
+    if args.pt_steps > 0:
+        pt = {}
+        for prec, tile in (("f32", (32, 32)), ("f64", (32, 16))):
+            k = args.pt_steps if prec == "f32" else max(2, args.pt_steps // 10)
+            cp_ms = measure_gpu(prec, k, 3, rho, tile, no_tma=True) / k
+            pt_ms = measure_gpu(prec, k, 3, rho, None, no_tma=True,
+                                force_model="pressure_tensor") / k
+            pt[prec] = {"chemical_potential_mlups": n_nodes / (cp_ms * 1e-3) / 1e6,
+                        "pressure_tensor_mlups": n_nodes / (pt_ms * 1e-3) / 1e6,
+                        "speedup": pt_ms / cp_ms, "tile": list(tile),
+                        "steps": k}
+
     batches = {}
     if args.batch_steps > 0:
         batches["batch_uneven"] = measure_batch("uneven", "f32",
@@ -464,6 +495,8 @@ def main():
                 "fp64": fp64, "e2e": e2e, "cpu_baseline": base,
                 "gpu_launches": args.steps, "clocks": clocks.summary()}
         line.update(batches)
+        if pt:
+            line["pressure_tensor_vs_chemical_potential"] = pt
         print(json.dumps(line))
     if world > 1:
         import torch.distributed as dist

@@ -119,6 +119,14 @@ lbm_status lbm_get_tile(const lbm_ctx *ctx, int *tx, int *ty);
  * temporary copy of the state.  *tx, *ty (may be NULL) receive the shape. */
 lbm_status lbm_autotune(lbm_ctx *ctx, int nsteps, int *tx, int *ty);
 
+/* Force model of lbm_step.  0 (default): the chemical-potential force of
+ * Eq. 12.  1: the pressure-tensor force it replaces, F = -div(P) +
+ * grad(cs^2 rho) with P of Eq. 9 (Eq. 5), same stencils - a baseline for
+ * measuring the cost the method avoids; periodic lattices, LBM_F64 or
+ * LBM_F32, fixed tile shape (set by this call).  lbm_moments reports v and
+ * mu with the chemical-potential definitions in both models. */
+lbm_status lbm_set_force_model(lbm_ctx *ctx, int model);
+
 /* Set the state to equilibrium populations f_i = f_i^eq(rho, u) (Eq. 14)
  * at every fluid node, and the step counter to 0.  rho must be positive and
  * below the EOS's repulsive pole at fluid nodes; ux and uy may be NULL

@@ -68,6 +68,8 @@ def lib():
              None),
             ("orc_stream", [pp, dp, dp], None),
             ("orc_step", [pp, dp, C.c_int], C.c_int),
+            ("orc_step_pressure_tensor", [pp, dp, C.c_int], C.c_int),
+            ("orc_force_pressure_tensor", [pp, dp, dp, dp], None),
             ("orc_moments", [pp, dp, dp, dp, dp, dp, dp, dp], C.c_int),
             ("orc_init_equilibrium", [pp, dp, dp, dp, dp], None),
             ("orc_set_threads", [C.c_int], None),
@@ -175,6 +177,24 @@ class Lattice:
         if rc != 0:
             raise MemoryError("oracle step: allocation failed")
         return self
+
+    def step_pressure_tensor(self, n=1):
+        """n steps with the pressure-tensor force of Eq. 5 (periodic only)."""
+        p = self.params()
+        rc = lib().orc_step_pressure_tensor(C.byref(p), _ptr(self.f), int(n))
+        if rc == -2:
+            raise ValueError("the pressure-tensor form has no wall rule")
+        if rc != 0:
+            raise MemoryError("oracle step: allocation failed")
+        return self
+
+    def force_pressure_tensor(self, rho):
+        rho = np.ascontiguousarray(rho, dtype=np.float64)
+        Fx, Fy = self.field(), self.field()
+        p = self.params()
+        lib().orc_force_pressure_tensor(C.byref(p), _ptr(rho), _ptr(Fx),
+                                        _ptr(Fy))
+        return Fx, Fy
 
     def moments(self):
         """dict of rho, vx, vy, mu, Fx, Fy ([ny, nx] each)."""

@@ -298,6 +298,51 @@ void orc_force(const orc_params *p, const double *rho, const double *mu,
         }
 }
 
+/* Nonideal force from the pressure tensor instead (Eq. 5 with Eq. 9), the
+ * form the method replaces: P = [p0 - kappa rho lap(rho) - kappa/2 |grad
+ * rho|^2] I + kappa grad(rho) grad(rho), F = -div(P) + grad(cs^2 rho), with
+ * the same isotropic stencils for every derivative.  Periodic lattices only
+ * (the paper gives no wall rule for this form).  rho must hold the density
+ * at every node. */
+void orc_force_pressure_tensor(const orc_params *p, const double *rho,
+                               double *Fx, double *Fy)
+{
+    const long N = (long)p->nx * p->ny;
+    double *pxx = malloc(sizeof(double) * N);
+    double *pxy = malloc(sizeof(double) * N);
+    double *pyy = malloc(sizeof(double) * N);
+    if (!pxx || !pxy || !pyy) {
+        free(pxx); free(pxy); free(pyy);
+        for (long n = 0; n < N; ++n) Fx[n] = Fy[n] = NAN;
+        return;
+    }
+    for (int y = 0; y < p->ny; ++y)
+        for (int x = 0; x < p->nx; ++x) {
+            const long n = (long)y * p->nx + x;
+            double gx, gy;
+            orc_gradient_at(p, rho, x, y, &gx, &gy);
+            const double lap = orc_laplacian_at(p, rho, x, y);
+            const double iso = orc_p0(&p->eos, rho[n]) -
+                               p->kappa * rho[n] * lap -
+                               0.5 * p->kappa * (gx * gx + gy * gy);
+            pxx[n] = iso + p->kappa * gx * gx;
+            pyy[n] = iso + p->kappa * gy * gy;
+            pxy[n] = p->kappa * gx * gy;
+        }
+    for (int y = 0; y < p->ny; ++y)
+        for (int x = 0; x < p->nx; ++x) {
+            const long n = (long)y * p->nx + x;
+            double dxx, dxy_x, dxy_y, dyy, rx, ry, unused;
+            orc_gradient_at(p, pxx, x, y, &dxx, &unused);
+            orc_gradient_at(p, pxy, x, y, &dxy_x, &dxy_y);
+            orc_gradient_at(p, pyy, x, y, &unused, &dyy);
+            orc_gradient_at(p, rho, x, y, &rx, &ry);
+            Fx[n] = -(dxx + dxy_y) + CS2 * rx;
+            Fy[n] = -(dxy_x + dyy) + CS2 * ry;
+        }
+    free(pxx); free(pxy); free(pyy);
+}
+
 /* Second-order equilibrium of Eq. 14 for density rho and velocity (ux, uy). */
 void orc_equilibrium(double rho, double ux, double uy, double *feq)
 {
@@ -364,8 +409,23 @@ static void fields(const orc_params *p, const double *f, double *rho,
     orc_force(p, rho, mu, Fx, Fy);
 }
 
+static int step_impl(const orc_params *p, double *f, int nsteps, int model);
+
 /* Advance f by nsteps time steps.  Returns 0, or -1 on allocation failure. */
 int orc_step(const orc_params *p, double *f, int nsteps)
+{
+    return step_impl(p, f, nsteps, 0);
+}
+
+/* The same step with the pressure-tensor force (Eq. 5); periodic only.
+ * Returns -2 for a lattice with walls. */
+int orc_step_pressure_tensor(const orc_params *p, double *f, int nsteps)
+{
+    if (p->walls) return -2;
+    return step_impl(p, f, nsteps, 1);
+}
+
+static int step_impl(const orc_params *p, double *f, int nsteps, int model)
 {
     const long N = (long)p->nx * p->ny;
     double *rho = malloc(sizeof(double) * N);
@@ -377,7 +437,12 @@ int orc_step(const orc_params *p, double *f, int nsteps)
     int rc = 0;
     if (!rho || !mu || !Fx || !Fy || !fpost || !fnext) { rc = -1; goto out; }
     for (int s = 0; s < nsteps; ++s) {
-        fields(p, f, rho, mu, Fx, Fy);
+        if (model == 0) {
+            fields(p, f, rho, mu, Fx, Fy);
+        } else {
+            orc_density(p, f, rho);
+            orc_force_pressure_tensor(p, rho, Fx, Fy);
+        }
 #pragma omp parallel for num_threads(g_threads)
         for (int y = 0; y < p->ny; ++y) {
             if (is_solid_row(p, y)) continue;

@@ -130,6 +130,13 @@ class Simulation:
         self._check(self._lib.lbm_set_wall_mu(self._ctx, float(mu_bottom),
                                               int(top_mode), float(mu_top)))
 
+    def set_force_model(self, model):
+        """'chemical_potential' (Eq. 12, default) or 'pressure_tensor' (the
+        Eq. 5 baseline: periodic, f32 / f64)."""
+        m = {"chemical_potential": 0, "pressure_tensor": 1}[model]
+        self._check(self._lib.lbm_set_force_model(self._ctx, m))
+        return self
+
     def set_tile(self, tx, ty):
         """Tile shape of the step kernel (speed only; results unchanged)."""
         self._check(self._lib.lbm_set_tile(self._ctx, int(tx), int(ty)))

@@ -48,6 +48,7 @@ SIGNATURES = {
     "lbm_set_wall_mu": ([_ctx, C.c_double, C.c_int, C.c_double], C.c_int),
     "lbm_init": ([_ctx, _vp, _vp, _vp, C.c_int], C.c_int),
     "lbm_set_tile": ([_ctx, C.c_int, C.c_int], C.c_int),
+    "lbm_set_force_model": ([_ctx, C.c_int], C.c_int),
     "lbm_get_tile": ([_ctx, C.POINTER(C.c_int), C.POINTER(C.c_int)], C.c_int),
     "lbm_autotune": ([_ctx, C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_int)],
                      C.c_int),

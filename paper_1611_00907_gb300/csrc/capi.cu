@@ -429,6 +429,13 @@ lbm_status lbm_set_tile(lbm_ctx *c, int tx, int ty)
     if (!c) return fail(nullptr, LBM_ERR_ARG, "null context");
     if (!step_shape_supported(c->L.precision, tx, ty))
         return fail(c, LBM_ERR_ARG, "no step kernel for tile %d x %d", tx, ty);
+    if (c->force_model == 1) {
+        int px, py;
+        pt_shape(c->L.precision, &px, &py);
+        if (tx != px || ty != py)
+            return fail(c, LBM_ERR_ARG, "the pressure-tensor baseline runs on "
+                        "tiles %d x %d only", px, py);
+    }
     if (c->initialized && (tx != c->L.tx || ty != c->L.ty)) {
         // The tile grid defines how the current density is split between
         // rho and the partial sums: gather it whole before switching.
@@ -543,6 +550,28 @@ lbm_status lbm_autotune(lbm_ctx *c, int nsteps, int *best_tx, int *best_ty)
     return LBM_OK;
 }
 
+lbm_status lbm_set_force_model(lbm_ctx *c, int model)
+{
+    if (!c) return fail(nullptr, LBM_ERR_ARG, "null context");
+    if (model == 0) {
+        c->force_model = 0;
+        return LBM_OK;
+    }
+    if (model != 1) return fail(c, LBM_ERR_ARG, "unknown force model %d", model);
+    if (c->L.walls)
+        return fail(c, LBM_ERR_ARG, "the pressure-tensor force has no wall rule "
+                    "(Sec. IV defines the chemical-potential one)");
+    if (c->L.precision != LBM_F64 && c->L.precision != LBM_F32)
+        return fail(c, LBM_ERR_ARG, "the pressure-tensor baseline runs in "
+                    "LBM_F64 or LBM_F32");
+    int tx, ty;
+    pt_shape(c->L.precision, &tx, &ty);
+    lbm_status st = lbm_set_tile(c, tx, ty);
+    if (st != LBM_OK) return st;
+    c->force_model = 1;
+    return LBM_OK;
+}
+
 lbm_status lbm_get_tile(const lbm_ctx *c, int *tx, int *ty)
 {
     if (!c || !tx || !ty) return fail(nullptr, LBM_ERR_ARG, "null argument");
@@ -627,7 +656,10 @@ lbm_status lbm_step(lbm_ctx *c, int nsteps)
     CUDA_TRY(c, cudaSetDevice(c->device));
     for (int k = 0; k < nsteps; ++k) {
         const int p = (int)(c->t & 1);
-        CUDA_TRY(c, launch_step(c->L, p, p, c->stream, &c->maps));
+        if (c->force_model == 1)
+            CUDA_TRY(c, launch_step_pt(c->L, p, p, c->stream));
+        else
+            CUDA_TRY(c, launch_step(c->L, p, p, c->stream, &c->maps));
         ++c->t;
     }
     return LBM_OK;

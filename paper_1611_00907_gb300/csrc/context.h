@@ -23,6 +23,7 @@ struct lbm_ctx {
     int *d_err = nullptr;      // kernel error flags (Lattice::err)
     cplbm::TmaMaps maps{};            // tensor maps of the TMA interior path
     bool use_tma = true;
+    int force_model = 0;       // 0 chemical potential (Eq. 12), 1 Eq. 5
     std::string err;
 };
 

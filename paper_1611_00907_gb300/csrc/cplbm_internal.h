@@ -101,6 +101,11 @@ void step_default_shape(int prec, int *tx, int *ty);
 // `max` pairs.
 int step_shapes(int *tx, int *ty, int max);
 
+// Baseline step with the pressure-tensor force (Eq. 5): FP32 (tile 32x32)
+// and FP64 (32x16), periodic lattices; pt_shape gives the tile it needs.
+cudaError_t launch_step_pt(const Lattice &L, int parity, int cur, cudaStream_t s);
+void pt_shape(int prec, int *tx, int *ty);
+
 // A tile of one lattice of a batch: the persistent batched step walks a
 // list of these (step.cu).
 struct WorkItem {

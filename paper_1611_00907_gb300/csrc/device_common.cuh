@@ -120,6 +120,28 @@ __device__ __forceinline__ T mu_bulk(const EosT<T> &e, T rho)
     }
 }
 
+// Equation of state p0(rho): Eq. 16 (vdW), Eq. 19 (RK/RKS), Eq. 22 (PR),
+// Eq. 25 (CS).  Used only by the pressure-tensor force of Eq. 5.
+template <class T>
+__device__ __forceinline__ T p0_bulk(const EosT<T> &e, T rho)
+{
+    const T br = e.b * rho;
+    switch (e.kind) {
+    case EOS_VDW:
+        return fdiv(rho * e.RT, T(1) - br) - e.a * rho * rho;
+    case EOS_CS: {
+        const T h = e.quarter_b * rho, q = T(1) - h;
+        return fdiv(rho * e.RT * (T(1) + h + h * h - h * h * h), q * q * q) -
+               e.a * rho * rho;
+    }
+    case EOS_PR:
+        return fdiv(rho * e.RT, T(1) - br) -
+               fdiv(e.aalpha * rho * rho, T(1) + T(2) * br - br * br);
+    default:  // EOS_RKS
+        return fdiv(rho * e.RT, T(1) - br) - fdiv(e.aalpha * rho * rho, T(1) + br);
+    }
+}
+
 // ---------------------------------------------------------------------------
 // Asynchronous global -> shared copies of single elements (sm_80+ cp.async).
 // A thread's copies become visible to that thread after cp_async_wait_all.

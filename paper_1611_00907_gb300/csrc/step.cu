@@ -1,933 +1,27 @@
-// Fused time step of the chemical-potential lattice Boltzmann method (arXiv
-// 1611.00907): one kernel launch per step does density, Eq. 28 wall density,
-// chemical potential (Eq. 8), nonideal force (Eq. 12), BGK collision with
-// the velocity-shift forcing (Eq. 13-14, Sec. II) and streaming with halfway
-// bounce-back (Sec. IV), in place (AA pattern).
-//
-// State.  The eight moving populations live in one array, updated in place
-// in the AA order (device_common.cuh).  The rest population f_0 is not
-// stored: the density field replaces it (f_0 = rho - sum_{i>0} f_i), so
-// each node moves 8 populations plus one density in and out per step, the
-// same 9 + 9 values as a plain in-place D2Q9 step.
-//
-// Density hand-over.  Every CTA owns a TX x TY tile.  After the collision it
-// has all post-collision populations of its tile in shared memory and sums,
-// for every node of the tile and of the one-node ring around it, the
-// populations that stream there from inside the tile (bounce-back returns
-// included).  A tile node's sum goes to rho[next]; the ring sums go to the
-// partial-sum buffers ring[next][class], class = direction from the ring
-// node's own tile to this one.  Each entry has exactly one writer, so the
-// hand-over needs no atomics and no clearing, and the next step adds the
-// parts in a fixed order (load_rho_stored): results do not depend on
-// scheduling.
-//
-// Memory pipeline.  Every global load a CTA needs is issued at its start as
-// an asynchronous copy into shared memory (cp.async): the density halo and
-// the partial sums first, then the eight populations of each node, which
-// land in the planes of the post-collision buffer the node later overwrites.
-// The chemical potential is computed while the populations are in flight.
-//
-// Two code paths share this structure.  Tiles whose halo and ring touch no
-// domain edge and whose neighbours are full tiles (nearly all of a large
-// lattice) take the interior path: constant address offsets, no periodic
-// wrap, no wall tests, asynchronous density loads.  All other tiles take
-// the general path.  Both add the same terms in the same order, so a node's
-// values do not depend on which path a tile took.
-#include "device_common.cuh"
+// Fused time step: dispatch to the per-precision kernels (step_<precision>.cu,
+// templates in step_impl.cuh) and the table of compiled tile shapes.
+#include "cplbm_internal.h"
 
 namespace cplbm {
 
-// Shared-memory carve-up of one CTA.
-template <class real, int TX, int TY>
-struct StepSmem {
-    static constexpr int WR = TX + 4, HR = TY + 4;   // rho + 2-node halo
-    static constexpr int WM = TX + 2, HM = TY + 2;   // mu + 1-node halo
-    static constexpr int NPOST = 8 * TX * TY;        // f*_1..8 of the tile
-    static constexpr int NRING = 4 * HR + 4 * WR + 16;  // staged partial sums
-    static constexpr size_t bytes =
-        sizeof(real) * (WR * HR + WM * HM + NPOST + NRING);
-};
+#define CPLBM_PREC_DECL(tag)                                                   \
+    cudaError_t launch_step_##tag(const Lattice &L, int parity, int cur,       \
+                                  cudaStream_t s, const TmaMaps *maps);        \
+    cudaError_t launch_batch_##tag(const Lattice *d_lats,                      \
+                                   const WorkItem *d_items, int n_items,      \
+                                   int parity, int cur, int tx, int ty,       \
+                                   int grid, cudaStream_t s);
+CPLBM_PREC_DECL(f64)
+CPLBM_PREC_DECL(f32)
+CPLBM_PREC_DECL(f32off)
+CPLBM_PREC_DECL(f16off)
+#undef CPLBM_PREC_DECL
+cudaError_t launch_pt_f64(const Lattice &L, int parity, int cur, cudaStream_t s);
+cudaError_t launch_pt_f32(const Lattice &L, int parity, int cur, cudaStream_t s);
 
-// In an interior tile's density halo the tile grid's edges sit at fixed
-// columns (1, 2, TX + 1, TX + 2) and rows (1, 2, TY + 1, TY + 2).  Columns 2
-// and TX + 2 are left edges of their tile (class L), 1 and TX + 1 right
-// edges (R); rows 2 and TY + 2 are bottom edges (B), 1 and TY + 1 top edges.
-template <int T>
-__device__ __forceinline__ int edge_col(int ci)
-{
-    return ci == 0 ? 1 : ci == 1 ? 2 : ci == 2 ? T + 1 : T + 2;
-}
-__device__ __forceinline__ bool col_is_left(int ci) { return ci & 1; }
-__device__ __forceinline__ bool row_is_below(int ri) { return ri & 1; }
-template <int T>
-__device__ __forceinline__ int col_index(int l)
-{
-    return l == 1 ? 0 : l == 2 ? 1 : l == T + 1 ? 2 : l == T + 2 ? 3 : -1;
-}
-
-// Issue the asynchronous loads of an interior tile's stored density and of
-// the partial sums its halo needs.
-template <class S, int TX, int TY, int NT>
-__device__ __forceinline__ void issue_rho_interior(const Lattice &L, int cur,
-                                                   int X0, int Y0,
-                                                   typename S::real *s_rho,
-                                                   typename S::real *s_ring)
-{
-    using real = typename S::real;
-    using rt = typename S::rho_t;
-    static_assert(sizeof(rt) == sizeof(real), "density staged as stored");
-    using SM = StepSmem<real, TX, TY>;
-    constexpr int WR = SM::WR, HR = SM::HR;
-    const rt *R = (const rt *)L.rho[cur];
-    rt *const *ring = (rt *const *)L.ring[cur];
-    for (int k = threadIdx.x; k < WR * HR; k += NT) {
-        const int lx = k % WR, ly = k / WR;
-        const long long fi = (long long)(Y0 + ly - 2) * L.pitch + X0 + lx - 2;
-        cp_async<sizeof(rt)>(&s_rho[k], R + fi);
-    }
-    for (int p = threadIdx.x; p < SM::NRING; p += NT) {
-        int c, lx, ly;
-        if (p < 4 * HR) {  // edge columns: class L or R, column-major storage
-            const int ci = p / HR;
-            ly = p % HR;
-            lx = edge_col<TX>(ci);
-            c = col_is_left(ci) ? R_L : R_R;
-        } else if (p < 4 * HR + 4 * WR) {  // edge rows: class B or T
-            const int q = p - 4 * HR, ri = q / WR;
-            lx = q % WR;
-            ly = edge_col<TY>(ri);
-            c = row_is_below(ri) ? R_B : R_T;
-        } else {  // the 16 crossings: corner classes
-            const int q = p - 4 * HR - 4 * WR, ci = q / 4, ri = q % 4;
-            lx = edge_col<TX>(ci);
-            ly = edge_col<TY>(ri);
-            c = row_is_below(ri) ? (col_is_left(ci) ? R_BL : R_BR)
-                                 : (col_is_left(ci) ? R_TL : R_TR);
-        }
-        const int x = X0 + lx - 2, r = Y0 + ly - 2;
-        const long long idx =
-            (c == R_L || c == R_R) ? cidx(L, r, x) : fidx(L, r, x);
-        cp_async<sizeof(rt)>(&s_ring[p], ring[c] + idx);
-    }
-}
-
-// Add the staged partial sums to the halo's edge nodes, in the order of
-// load_rho_stored.
-template <class S, int TX, int TY, int NT>
-__device__ __forceinline__ void combine_rho_interior(typename S::real *s_rho,
-                                                     const typename S::real *s_ring)
-{
-    using real = typename S::real;
-    using SM = StepSmem<real, TX, TY>;
-    constexpr int WR = SM::WR, HR = SM::HR;
-    for (int q = threadIdx.x; q < 4 * HR + 4 * WR; q += NT) {
-        int lx, ly;
-        if (q < 4 * HR) {
-            lx = edge_col<TX>(q / HR);
-            ly = q % HR;
-        } else {
-            const int t = q - 4 * HR;
-            lx = t % WR;
-            ly = edge_col<TY>(t / WR);
-            if (col_index<TX>(lx) >= 0) continue;  // done by its column entry
-        }
-        const int ci = col_index<TX>(lx), ri = col_index<TY>(ly);
-        const bool lr = ci >= 0, ba = ri >= 0;
-        real v = s_rho[ly * WR + lx];
-        if (lr) v += s_ring[ci * HR + ly];
-        if (ba) {
-            v += s_ring[4 * HR + ri * WR + lx];
-            if (lr) v += s_ring[4 * HR + 4 * WR + ci * 4 + ri];
-        }
-        s_rho[ly * WR + lx] = v;
-    }
-}
-
-template <class S, int TX, int TY, int NT>
-__device__ __forceinline__ void mu_interior(const Lattice &L,
-                                            const typename S::real *s_rho,
-                                            typename S::real *s_mu)
-{
-    using real = typename S::real;
-    constexpr int W = TX + 2, H = TY + 2, WR = TX + 4;
-    const EosT<real> eos(L.eos);
-    const real kappa = (real)L.kappa;
-    const real ref = S::offset ? (real)L.rho_ref : real(0);
-    for (int k = threadIdx.x; k < W * H; k += NT) {
-        const int lx = k % W, ly = k / W;
-        const int c = (ly + 1) * WR + lx + 1;
-        s_mu[k] = mu_bulk(eos, s_rho[c] + ref) - kappa * lap9<real, WR>(s_rho, c);
-    }
-}
-
-// BGK collision of one node with the velocity-shift forcing.  f[1..8] are
-// the node's stored populations (f_0 = drho - sum f_i is implicit), drho
-// its stored density (rho - rho_ref) and rho the absolute one; fp[0..8]
-// receive the post-collision values in stored form.
-template <class real>
-__device__ __forceinline__ void collide(const real *f, real drho, real rho,
-                                        real Fx, real Fy, real tau, real omega,
-                                        real *fp)
-{
-    // u = sum f_i e_i / rho; u_eq = u + tau F / rho (Sec. II)
-    const real jx = (f[1] - f[3]) + (f[5] - f[7]) + (f[8] - f[6]);
-    const real jy = (f[2] - f[4]) + (f[5] - f[7]) + (f[6] - f[8]);
-    const real inv_rho = fdiv(real(1), rho);
-    const real ux = (jx + tau * Fx) * inv_rho;
-    const real uy = (jy + tau * Fy) * inv_rho;
-    const real usq = real(1.5) * (ux * ux + uy * uy);
-    // Eq. 14 in stored form: f_eq - w_i rho_ref = w_i (drho + rho P_i(u)),
-    // P_i = 3 e.u + 4.5 (e.u)^2 - 1.5 u^2; opposite directions share the
-    // even part of P.
-    const real w1 = real(1.0 / 9.0), w5 = real(1.0 / 36.0);
-    {
-        const real ex2 = real(4.5) * ux * ux - usq, ey2 = real(4.5) * uy * uy - usq;
-        const real ax = w1 * (drho + rho * ex2), bx = w1 * rho * real(3) * ux;
-        const real ay = w1 * (drho + rho * ey2), by = w1 * rho * real(3) * uy;
-        fp[1] = f[1] + omega * ((ax + bx) - f[1]);
-        fp[3] = f[3] + omega * ((ax - bx) - f[3]);
-        fp[2] = f[2] + omega * ((ay + by) - f[2]);
-        fp[4] = f[4] + omega * ((ay - by) - f[4]);
-    }
-    {
-        const real sp = ux + uy, sm = ux - uy;
-        const real ep = real(4.5) * sp * sp - usq, em = real(4.5) * sm * sm - usq;
-        const real a5 = w5 * (drho + rho * ep), b5 = w5 * rho * real(3) * sp;
-        const real a8 = w5 * (drho + rho * em), b8 = w5 * rho * real(3) * sm;
-        fp[5] = f[5] + omega * ((a5 + b5) - f[5]);
-        fp[7] = f[7] + omega * ((a5 - b5) - f[7]);
-        fp[8] = f[8] + omega * ((a8 + b8) - f[8]);
-        fp[6] = f[6] + omega * ((a8 - b8) - f[6]);
-    }
-    // The rest population takes what the moving ones leave of the density:
-    // in exact arithmetic this equals f_0 + omega (f_0^eq - f_0) with
-    // f_0 = drho - sum_{i>0} f_i, and it keeps the collision's mass exact
-    // instead of biased by the rounding of f_eq.
-    fp[0] = drho - (((fp[1] + fp[2]) + (fp[3] + fp[4])) +
-                    ((fp[5] + fp[6]) + (fp[7] + fp[8])));
-}
-
-// Index of f*_i (i = 1..8) of tile node (lx, ly) in s_post.
-template <int TX, int TY>
-__device__ __forceinline__ int post_idx(int i, int ly, int lx)
-{
-    return ((i - 1) * TY + ly) * TX + lx;
-}
-
-// Partial density at position (ox, oy) of the tile or its ring from the
-// tile's post-collision populations, with the general checks.  self0 is
-// f*_0 of the node when the position is inside the tile.
-template <class real, int TX, int TY>
-__device__ __forceinline__ real handover_sum(const Lattice &L, const real *s_post,
-                                             int ox, int oy, int wx, int wy,
-                                             int r, bool inside, real self0)
-{
-    real s = inside ? self0 : real(0);
-#pragma unroll
-    for (int i = 1; i < 9; ++i) {
-        const int sx = ox - ex(i), sy = oy - ey(i);
-        if (inside && L.walls && row_is_solid(L, r - ey(i))) {
-            // bounce-back: f*_opp(i) of this node comes back as f_i
-            s += s_post[post_idx<TX, TY>(opp(i), oy, ox)];
-        } else if (sx >= 0 && sx < wx && sy >= 0 && sy < wy) {
-            s += s_post[post_idx<TX, TY>(i, sy, sx)];
-        }
-    }
-    return s;
-}
-
-__device__ __forceinline__ int ring_class(int ox, int oy, int wx, int wy)
-{
-    if (ox < 0) return oy < 0 ? R_TR : (oy >= wy ? R_BR : R_R);
-    if (ox >= wx) return oy < 0 ? R_TL : (oy >= wy ? R_BL : R_L);
-    return oy < 0 ? R_T : R_B;
-}
-
-// Ring position p (0 .. 2 (wx + wy) + 3) of a wx x wy tile, walking the
-// bottom row, the top row, then the left and right columns.
-__device__ __forceinline__ void ring_position(int p, int wx, int wy, int &ox,
-                                              int &oy)
-{
-    if (p < wx + 2) { ox = p - 1; oy = -1; return; }
-    p -= wx + 2;
-    if (p < wx + 2) { ox = p - 1; oy = wy; return; }
-    p -= wx + 2;
-    if (p < wy) { ox = -1; oy = p; return; }
-    ox = wx; oy = p - wy;
-}
-
-template <class S, int TX, int TY, int NT, int PARITY, bool INTERIOR>
-__device__ __forceinline__ void step_tile(const Lattice &L, int cur, int X0,
-                                          int Y0, unsigned char *smem_raw)
-{
-    using real = typename S::real;
-    using pop_t = typename S::pop_t;
-    using rho_t = typename S::rho_t;
-    using SM = StepSmem<real, TX, TY>;
-    constexpr int WR = SM::WR, WM = SM::WM;
-    constexpr int PER = TX * TY / NT;
-    constexpr int DY = NT / TX;  // rows between a thread's nodes
-    static_assert((TX * TY) % NT == 0 && NT % TX == 0, "thread mapping");
-    real *s_rho = reinterpret_cast<real *>(smem_raw);
-    real *s_mu = s_rho + SM::WR * SM::HR;
-    real *s_post = s_mu + SM::WM * SM::HM;  // [8][TY][TX]
-    real *s_ring = s_post + SM::NPOST;
-
-    const int wx = INTERIOR ? TX : min(TX, L.nx - X0);
-    const int wy = INTERIOR ? TY : min(TY, L.nyf - Y0);
-    const int nxt = cur ^ 1;
-    pop_t *A = (pop_t *)L.pops;
-    const int lx = threadIdx.x % TX, ly0 = threadIdx.x / TX;
-    // Storage and arithmetic of the same width: populations are staged
-    // asynchronously (FP16 storage is loaded directly instead).
-    constexpr bool ASYNC = sizeof(pop_t) == sizeof(real);
-
-    // per-direction offsets of the in-place pattern (interior tiles)
-    long long roff[9], woff[9];
-#pragma unroll
-    for (int i = 1; i < 9; ++i) {
-        if (PARITY == 0) {
-            roff[i] = (long long)(i - 1) * L.plane;
-            woff[i] = (long long)(opp(i) - 1) * L.plane;
-        } else {
-            roff[i] = (long long)(opp(i) - 1) * L.plane -
-                      (long long)ey(i) * L.pitch - ex(i);
-            woff[i] = (long long)(i - 1) * L.plane +
-                      (long long)ey(i) * L.pitch + ex(i);
-        }
-    }
-
-    // 1. Issue the loads: density (interior tiles), then the populations.
-    if (INTERIOR) {
-        issue_rho_interior<S, TX, TY, NT>(L, cur, X0, Y0, s_rho, s_ring);
-        cp_async_commit();
-    }
-    if constexpr (ASYNC) {
-#pragma unroll
-        for (int k = 0; k < PER; ++k) {
-            const int ly = ly0 + k * DY;
-            if (!INTERIOR && (lx >= wx || ly >= wy)) continue;
-            const int x = X0 + lx, r = Y0 + ly;
-            const long long base = (long long)r * L.pitch + x;
-#pragma unroll
-            for (int i = 1; i < 9; ++i) {
-                const pop_t *src = INTERIOR
-                    ? A + base + roff[i]
-                    : A + aa_read_index(L, PARITY, i, r, x);
-                cp_async<sizeof(pop_t)>(&s_post[post_idx<TX, TY>(i, ly, lx)], src);
-            }
-        }
-        cp_async_commit();
-    }
-
-    // 2. Density with halo, then mu on the tile and a one-node halo.
-    if (INTERIOR) {
-        if constexpr (ASYNC) cp_async_wait_group<1>();  // density group only
-        else cp_async_wait_all();
-        __syncthreads();
-        combine_rho_interior<S, TX, TY, NT>(s_rho, s_ring);
-        __syncthreads();
-        mu_interior<S, TX, TY, NT>(L, s_rho, s_mu);
-    } else {
-        load_rho_tile<S, TX, TY>(L, cur, X0, Y0, s_rho);
-        __syncthreads();
-        mu_tile<S, TX, TY>(L, X0, Y0, s_rho, s_mu);
-    }
-    __syncthreads();
-
-    // 3. Force, collision, in-place streaming.
-    const real tau = (real)L.tau;
-    const real omega = real(1) / tau;
-    const real rho_ref = S::offset ? (real)L.rho_ref : real(0);
-    if constexpr (ASYNC) cp_async_wait_all();
-    real self0[PER];
-#pragma unroll
-    for (int k = 0; k < PER; ++k) {
-        self0[k] = real(0);
-        const int ly = ly0 + k * DY;
-        if (!INTERIOR && (lx >= wx || ly >= wy)) continue;
-        const int x = X0 + lx, r = Y0 + ly;
-        const long long base = (long long)r * L.pitch + x;
-        real f[9];
-        if constexpr (ASYNC) {
-#pragma unroll
-            for (int i = 1; i < 9; ++i) f[i] = s_post[post_idx<TX, TY>(i, ly, lx)];
-        } else if (INTERIOR) {
-#pragma unroll
-            for (int i = 1; i < 9; ++i) f[i] = ld_real(A + base + roff[i]);
-        } else {
-#pragma unroll
-            for (int i = 1; i < 9; ++i)
-                f[i] = ld_real(A + aa_read_index(L, PARITY, i, r, x));
-        }
-        const int cr = (ly + 2) * WR + lx + 2, cm = (ly + 1) * WM + lx + 1;
-        const real drho = s_rho[cr];
-        const real rho = drho + rho_ref;
-        // Eq. 12: F = -rho grad(mu) + grad(cs^2 rho)
-        real gmx, gmy, grx, gry;
-        grad9<real, WM>(s_mu, cm, gmx, gmy);
-        grad9<real, WR>(s_rho, cr, grx, gry);
-        const real Fx = grx * real(1.0 / 3.0) - rho * gmx;
-        const real Fy = gry * real(1.0 / 3.0) - rho * gmy;
-        real fp[9];
-        collide<real>(f, drho, rho, Fx, Fy, tau, omega, fp);
-        self0[k] = fp[0];
-#pragma unroll
-        for (int i = 1; i < 9; ++i) s_post[post_idx<TX, TY>(i, ly, lx)] = fp[i];
-        if (INTERIOR) {
-#pragma unroll
-            for (int i = 1; i < 9; ++i) st_real(A + base + woff[i], fp[i]);
-        } else {
-#pragma unroll
-            for (int i = 1; i < 9; ++i)
-                st_real(A + aa_write_index(L, PARITY, i, r, x), fp[i]);
-        }
-    }
-    __syncthreads();
-
-    // 4. Density hand-over, tile nodes: the thread's own nodes.
-    rho_t *Rn = (rho_t *)L.rho[nxt];
-    rho_t *const *ring = (rho_t *const *)L.ring[nxt];
-#pragma unroll
-    for (int k = 0; k < PER; ++k) {
-        const int ly = ly0 + k * DY;
-        if (!INTERIOR && (lx >= wx || ly >= wy)) continue;
-        const int r = Y0 + ly;
-        real s;
-        const bool deep = lx >= 1 && lx <= wx - 2 && ly >= 1 && ly <= wy - 2 &&
-                          (INTERIOR || !L.walls || (r >= 1 && r <= L.nyf - 2));
-        if (deep) {  // all nine sources inside the tile
-            s = self0[k];
-#pragma unroll
-            for (int i = 1; i < 9; ++i)
-                s += s_post[post_idx<TX, TY>(i, ly - ey(i), lx - ex(i))];
-        } else {
-            s = handover_sum<real, TX, TY>(L, s_post, lx, ly, wx, wy, r, true,
-                                           self0[k]);
-        }
-        Rn[(long long)r * L.pitch + X0 + lx] = (rho_t)s;
-    }
-    // Ring around the tile: partial sums for the neighbouring tiles.
-    const int nring = 2 * (wx + wy) + 4;
-    for (int p = threadIdx.x; p < nring; p += NT) {
-        int ox, oy;
-        ring_position(p, wx, wy, ox, oy);
-        const int r = Y0 + oy;
-        if (!INTERIOR && L.walls && (r < 0 || r >= L.nyf)) continue;
-        const real s = handover_sum<real, TX, TY>(L, s_post, ox, oy, wx, wy, r,
-                                                  false, real(0));
-        const int x = INTERIOR ? X0 + ox : wrapi(X0 + ox, L.nx);
-        const int rw = INTERIOR ? r : row_wrap(L, r);
-        const int c = ring_class(ox, oy, wx, wy);
-        const long long idx =
-            (c == R_L || c == R_R) ? cidx(L, rw, x) : fidx(L, rw, x);
-        ring[c][idx] = (rho_t)s;
-    }
-}
-
-// ---------------------------------------------------------------------------
-// Interior tiles with TMA.  One thread issues nine tensor copies per tile:
-// the density halo (a (TX + 8) x (TY + 4) box from x = X0 - 4, the nearest
-// 16-byte-aligned column) and, per direction, the (TX + 8) x TY box of the
-// plane and rows that direction is read from in this step's AA order.  They
-// complete on one mbarrier; the partial sums of the halo's edge nodes come by
-// per-element cp.async.  Staged rows have pitch RP = TX + 8 with the tile's
-// column 0 at offset 4.
-//
-// Lanes map to x (TX = 32) and each warp owns PER consecutive rows, walked
-// bottom to top.  Stencil windows roll with the rows, and the density
-// hand-over is done in registers: a node's next density is
-//   same(k) + up(k - 1) + down(k + 1),
-// same = f*_0 + f*_1 from the left lane + f*_3 from the right lane,
-// up   = f*_2 + f*_5 from the left + f*_6 from the right (to the row above),
-// down = f*_4 + f*_8 from the left + f*_7 from the right (to the row below),
-// with lane neighbours by warp shuffles.  Only each warp's first "down" and
-// last "up" cross to the neighbouring warp, through shared memory.  Lane 0
-// and lane 31 carry the same sums for the tile's left and right ring
-// columns; the first and last warps write the bottom and top ring rows.
-// ---------------------------------------------------------------------------
-template <class real, int TX, int TY>
-struct TmaSmem {
-    static constexpr int RP = TX + 8;
-    static constexpr int PLANE = TY * RP;
-    static constexpr int NRHO = (TY + 4) * RP;
-    static constexpr int MP = TX + 2, MH = TY + 2;
-    static constexpr int NRING = StepSmem<real, TX, TY>::NRING;
-    static constexpr int NMU = MP * MH;
-    static constexpr int NXCH = 2 * (STEP_THREADS / 32) * (TX + 2);
-    static constexpr size_t bar_offset =
-        (sizeof(real) * (8 * PLANE + NRHO + NRING + NMU + NXCH) + 15) / 16 * 16;
-    static constexpr size_t bytes = bar_offset + 16;
-    static constexpr unsigned tx_bytes = sizeof(real) * (8 * PLANE + NRHO);
-};
-
-// Gradient of the isotropic stencil from a 3 x 3 window w[row][col] (row 0
-// below, col 0 left), same arithmetic as grad9.
-template <class T>
-__device__ __forceinline__ void grad_w(const T (&w)[3][3], T &gx, T &gy)
-{
-    const T ne = w[2][2], nw = w[2][0], se = w[0][2], sw = w[0][0];
-    gx = (T(4) * (w[1][2] - w[1][0]) + (ne - nw) + (se - sw)) * T(1.0 / 12.0);
-    gy = (T(4) * (w[2][1] - w[0][1]) + (ne + nw) - (se + sw)) * T(1.0 / 12.0);
-}
-// Laplacian of the isotropic stencil from a 3 x 3 window, as lap9.
-template <class T>
-__device__ __forceinline__ T lap_w(const T (&w)[3][3])
-{
-    const T axial = w[1][2] + w[1][0] + w[2][1] + w[0][1];
-    const T diag = w[2][2] + w[2][0] + w[0][2] + w[0][0];
-    return (T(4) * axial + diag - T(20) * w[1][1]) * T(1.0 / 6.0);
-}
-
-template <class S, int TX, int TY, int NT, int PARITY>
-__device__ __forceinline__ void step_tile_tma(const Lattice &L, int cur, int X0,
-                                              int Y0, unsigned char *smem_raw,
-                                              const TmaMaps &maps)
-{
-    using real = typename S::real;
-    using pop_t = typename S::pop_t;
-    using rho_t = typename S::rho_t;
-    using TS = TmaSmem<real, TX, TY>;
-    static_assert(TX == 32, "lanes map to x");
-    static_assert(sizeof(pop_t) == sizeof(real), "populations staged as stored");
-    constexpr int NW = NT / 32, PER = TY / NW;
-    static_assert(PER * NW == TY && PER >= 2, "warps own whole row blocks");
-    constexpr int RP = TS::RP, PLANE = TS::PLANE, MP = TS::MP, MH = TS::MH;
-    constexpr int WR = TX + 4, HR = TY + 4;  // halo geometry of the ring staging
-    constexpr int XW = TX + 2;               // exchange slots per warp
-    real *s_pin = reinterpret_cast<real *>(smem_raw);  // [8][TY][RP]
-    real *s_rho = s_pin + 8 * PLANE;                     // [TY + 4][RP]
-    real *s_ring = s_rho + TS::NRHO;
-    real *s_mu = s_ring + TS::NRING;                     // [MH][MP]
-    real *s_up = s_mu + TS::NMU;                         // [NW][XW]
-    real *s_down = s_up + NW * XW;                       // [NW][XW]
-    unsigned long long *bar =
-        reinterpret_cast<unsigned long long *>(smem_raw + TS::bar_offset);
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int nxt = cur ^ 1;
-
-    // 1. Loads.  Density halo and populations by TMA (thread 0), partial
-    //    sums by cp.async (all threads).
-    if (threadIdx.x == 0) mbar_init(bar, 1);
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        mbar_expect_tx(bar, TS::tx_bytes);
-        tma_load_2d(s_rho, &maps.rho[cur], X0 - 4, Y0 - 2, bar);
-#pragma unroll
-        for (int i = 1; i < 9; ++i) {
-            const int plane = PARITY == 0 ? i - 1 : opp(i) - 1;
-            const int y0 = PARITY == 0 ? Y0 : Y0 - ey(i);
-            tma_load_3d(s_pin + (i - 1) * PLANE, &maps.pops, X0 - 4, y0, plane, bar);
-        }
-    }
-    {
-        using rt = rho_t;
-        rt *const *ring = (rt *const *)L.ring[cur];
-        for (int p = threadIdx.x; p < TS::NRING; p += NT) {
-            int c, lx, ly;
-            if (p < 4 * HR) {
-                const int ci = p / HR;
-                ly = p % HR;
-                lx = edge_col<TX>(ci);
-                c = col_is_left(ci) ? R_L : R_R;
-            } else if (p < 4 * HR + 4 * WR) {
-                const int q = p - 4 * HR, ri = q / WR;
-                lx = q % WR;
-                ly = edge_col<TY>(ri);
-                c = row_is_below(ri) ? R_B : R_T;
-            } else {
-                const int q = p - 4 * HR - 4 * WR, ci = q / 4, ri = q % 4;
-                lx = edge_col<TX>(ci);
-                ly = edge_col<TY>(ri);
-                c = row_is_below(ri) ? (col_is_left(ci) ? R_BL : R_BR)
-                                     : (col_is_left(ci) ? R_TL : R_TR);
-            }
-            const int x = X0 + lx - 2, r = Y0 + ly - 2;
-            const long long idx =
-                (c == R_L || c == R_R) ? cidx(L, r, x) : fidx(L, r, x);
-            cp_async<sizeof(rt)>(&s_ring[p], ring[c] + idx);
-        }
-        cp_async_commit();
-    }
-    cp_async_wait_all();
-    const bool ok = mbar_wait(bar, 0, 2000000000LL);  // ~1 s at 2 GHz
-    if (__syncthreads_or(!ok)) {
-        // the copies did not land in time: flag it, give the copies another
-        // bounded wait so none is left writing into this block's memory,
-        // and leave the tile untouched
-        if (threadIdx.x == 0 && L.err) atomicOr(L.err, ERR_WAIT_TIMEOUT);
-        mbar_wait(bar, 0, 2000000000LL);
-        __syncthreads();
-        return;
-    }
-
-    // 2. Partial sums into the halo's tile-edge nodes (order of
-    //    load_rho_stored).  Halo (lx, ly) of the (TX + 4)-wide convention is
-    //    staged row ly, column lx + 2.
-    for (int q = threadIdx.x; q < 4 * HR + 4 * WR; q += NT) {
-        int lx, ly;
-        if (q < 4 * HR) {
-            lx = edge_col<TX>(q / HR);
-            ly = q % HR;
-        } else {
-            const int t = q - 4 * HR;
-            lx = t % WR;
-            ly = edge_col<TY>(t / WR);
-            if (col_index<TX>(lx) >= 0) continue;
-        }
-        const int ci = col_index<TX>(lx), ri = col_index<TY>(ly);
-        real v = s_rho[ly * RP + lx + 2];
-        if (ci >= 0) v += s_ring[ci * HR + ly];
-        if (ri >= 0) {
-            v += s_ring[4 * HR + ri * WR + lx];
-            if (ci >= 0) v += s_ring[4 * HR + 4 * WR + ci * 4 + ri];
-        }
-        s_rho[ly * RP + lx + 2] = v;
-    }
-    __syncthreads();
-
-    // 3. mu at (a, b), a in [0, TX + 2) <-> x = X0 - 1 + a, b in [0, TY + 2)
-    //    <-> r = Y0 - 1 + b; its density sits at staged (b + 1, a + 3).
-    //    Columns 1..TX: lane a - 1, each warp a run of consecutive rows with
-    //    a rolling 3 x 3 window; columns 0 and TX + 1 separately.
-    {
-        const EosT<real> eos(L.eos);
-        const real kappa = (real)L.kappa;
-        const real ref = S::offset ? (real)L.rho_ref : real(0);
-        const int b0 = (warp * MH) / NW, b1 = ((warp + 1) * MH) / NW;
-        const int a = lane + 1;
-        real w[3][3];
-#pragma unroll
-        for (int j = 0; j < 2; ++j)
-#pragma unroll
-            for (int d = 0; d < 3; ++d) w[j][d] = s_rho[(b0 + j) * RP + a + 2 + d];
-        for (int b = b0; b < b1; ++b) {
-#pragma unroll
-            for (int d = 0; d < 3; ++d) w[2][d] = s_rho[(b + 2) * RP + a + 2 + d];
-            s_mu[b * MP + a] = mu_bulk(eos, w[1][1] + ref) - kappa * lap_w(w);
-#pragma unroll
-            for (int d = 0; d < 3; ++d) {
-                w[0][d] = w[1][d];
-                w[1][d] = w[2][d];
-            }
-        }
-        for (int t = threadIdx.x; t < 2 * MH; t += NT) {
-            const int ae = (t & 1) ? TX + 1 : 0, b = t >> 1;
-            const int c = (b + 1) * RP + ae + 3;
-            s_mu[b * MP + ae] =
-                mu_bulk(eos, s_rho[c] + ref) - kappa * lap9<real, RP>(s_rho, c);
-        }
-    }
-    __syncthreads();
-
-    // 4. Force, collision, in-place streaming and the register hand-over for
-    //    the thread's PER nodes at rows ly0 .. ly0 + PER - 1, column lx.
-    const int lx = lane, ly0 = warp * PER;
-    const real tau = (real)L.tau;
-    const real omega = real(1) / tau;
-    const real rho_ref = S::offset ? (real)L.rho_ref : real(0);
-    pop_t *A = (pop_t *)L.pops;
-    rho_t *Rn = (rho_t *)L.rho[nxt];
-    rho_t *const *ring = (rho_t *const *)L.ring[nxt];
-    int woff[9];  // 32-bit: the TMA maps exist only when 8 planes fit
-#pragma unroll
-    for (int i = 1; i < 9; ++i)
-        woff[i] = PARITY == 0 ? (opp(i) - 1) * (int)L.plane
-                              : (i - 1) * (int)L.plane + ey(i) * L.pitch + ex(i);
-    const bool has_l = lane > 0, has_r = lane < 31;
-    real wr[3][3], wm[3][3];
-#pragma unroll
-    for (int j = 0; j < 2; ++j)
-#pragma unroll
-        for (int d = 0; d < 3; ++d) {
-            wr[j][d] = s_rho[(ly0 + 1 + j) * RP + lx + 3 + d];
-            wm[j][d] = s_mu[(ly0 + j) * MP + lx + d];
-        }
-    // Rolling hand-over.  pend: row k - 1 without its "down" part;
-    // first: row 0 of the warp without the warp below's "up"; *_c: the same
-    // for the ring column a lane 0 / lane 31 feeds.
-    real pend = real(0), up_prev = real(0), first = real(0);
-    real pend_c = real(0), up_prev_c = real(0), first_c = real(0);
-    const int slot_c = TX + (lane == 31);        // exchange slot of a column
-    const int xc = lane == 0 ? X0 - 1 : X0 + TX;  // ring column of the lane
-    const int cls_c = lane == 0 ? R_R : R_L;
-    const bool col_lane = lane == 0 || lane == 31;
-    pop_t *Arow = A + (long long)(Y0 + ly0) * L.pitch + X0 + lx;
-#pragma unroll
-    for (int k = 0; k < PER; ++k) {
-        const int ly = ly0 + k;
-#pragma unroll
-        for (int d = 0; d < 3; ++d) {
-            wr[2][d] = s_rho[(ly + 3) * RP + lx + 3 + d];
-            wm[2][d] = s_mu[(ly + 2) * MP + lx + d];
-        }
-        real f[9];
-#pragma unroll
-        for (int i = 1; i < 9; ++i)
-            f[i] = s_pin[(i - 1) * PLANE + ly * RP + lx + 4 -
-                         (PARITY == 0 ? 0 : ex(i))];
-        const real drho = wr[1][1];
-        const real rho = drho + rho_ref;
-        real gmx, gmy, grx, gry;
-        grad_w(wm, gmx, gmy);
-        grad_w(wr, grx, gry);
-        const real Fx = grx * real(1.0 / 3.0) - rho * gmx;
-        const real Fy = gry * real(1.0 / 3.0) - rho * gmy;
-        real fp[9];
-        collide<real>(f, drho, rho, Fx, Fy, tau, omega, fp);
-#pragma unroll
-        for (int i = 1; i < 9; ++i) st_real(Arow + woff[i], fp[i]);
-        Arow += L.pitch;
-
-        // lane-neighbour parts of the hand-over
-        const real f1l = __shfl_up_sync(0xffffffffu, fp[1], 1);
-        const real f5l = __shfl_up_sync(0xffffffffu, fp[5], 1);
-        const real f8l = __shfl_up_sync(0xffffffffu, fp[8], 1);
-        const real f3r = __shfl_down_sync(0xffffffffu, fp[3], 1);
-        const real f6r = __shfl_down_sync(0xffffffffu, fp[6], 1);
-        const real f7r = __shfl_down_sync(0xffffffffu, fp[7], 1);
-        const real same = fp[0] + (has_l ? f1l : real(0)) + (has_r ? f3r : real(0));
-        const real up = fp[2] + (has_l ? f5l : real(0)) + (has_r ? f6r : real(0));
-        const real down = fp[4] + (has_l ? f8l : real(0)) + (has_r ? f7r : real(0));
-        // ring columns: lane 0 feeds x = X0 - 1 (f*_3; f*_6 up; f*_7 down),
-        // lane 31 feeds x = X0 + TX (f*_1; f*_5 up; f*_8 down)
-        const real same_c = lane == 0 ? fp[3] : fp[1];
-        const real up_c = lane == 0 ? fp[6] : fp[5];
-        const real down_c = lane == 0 ? fp[7] : fp[8];
-        if (k == 0) {
-            // this row's "down" belongs to the warp below (or the ring row
-            // under the tile)
-            s_down[warp * XW + lane] = down;
-            if (col_lane) s_down[warp * XW + slot_c] = down_c;
-            pend = same;
-            pend_c = same_c;
-        } else {
-            const real done = pend + down;        // row ly - 1
-            const real done_c = pend_c + down_c;
-            if (k == 1) {
-                first = done;
-                first_c = done_c;
-            } else {
-                Rn[(long long)(Y0 + ly - 1) * L.pitch + X0 + lx] = (rho_t)done;
-                if (col_lane) ring[cls_c][cidx(L, Y0 + ly - 1, xc)] = (rho_t)done_c;
-            }
-            pend = same + up_prev;
-            pend_c = same_c + up_prev_c;
-        }
-        up_prev = up;
-        up_prev_c = up_c;
-#pragma unroll
-        for (int d = 0; d < 3; ++d) {
-            wr[0][d] = wr[1][d]; wr[1][d] = wr[2][d];
-            wm[0][d] = wm[1][d]; wm[1][d] = wm[2][d];
-        }
-    }
-    // up_prev: the warp's last-row "up", for the warp above (or the ring
-    // row over the tile).
-    s_up[warp * XW + lane] = up_prev;
-    if (col_lane) s_up[warp * XW + slot_c] = up_prev_c;
-    __syncthreads();
-    {
-        // last row: add the warp above's first-row "down"
-        real top = pend, top_c = pend_c;
-        if (warp + 1 < NW) {
-            top += s_down[(warp + 1) * XW + lane];
-            top_c += s_down[(warp + 1) * XW + slot_c];
-        }
-        Rn[(long long)(Y0 + ly0 + PER - 1) * L.pitch + X0 + lx] = (rho_t)top;
-        if (col_lane) ring[cls_c][cidx(L, Y0 + ly0 + PER - 1, xc)] = (rho_t)top_c;
-        // first row: add the warp below's last-row "up"
-        if (warp > 0) {
-            first += s_up[(warp - 1) * XW + lane];
-            first_c += s_up[(warp - 1) * XW + slot_c];
-        }
-        Rn[(long long)(Y0 + ly0) * L.pitch + X0 + lx] = (rho_t)first;
-        if (col_lane) ring[cls_c][cidx(L, Y0 + ly0, xc)] = (rho_t)first_c;
-    }
-    // ring rows below and above the tile, with their corners
-    if (warp == 0) {
-        ring[R_T][fidx(L, Y0 - 1, X0 + lx)] = (rho_t)s_down[lane];
-        if (lane == 0) ring[R_TR][fidx(L, Y0 - 1, X0 - 1)] = (rho_t)s_down[TX];
-        if (lane == 31) ring[R_TL][fidx(L, Y0 - 1, X0 + TX)] = (rho_t)s_down[TX + 1];
-    }
-    if (warp == NW - 1) {
-        ring[R_B][fidx(L, Y0 + TY, X0 + lx)] = (rho_t)up_prev;
-        if (lane == 0) ring[R_BR][fidx(L, Y0 + TY, X0 - 1)] = (rho_t)up_prev_c;
-        if (lane == 31) ring[R_BL][fidx(L, Y0 + TY, X0 + TX)] = (rho_t)up_prev_c;
-    }
-}
-
-// Whether a (precision, tile) pair has the TMA interior path.
-template <class S, int TX, int TY, int NT>
-struct HasTma {
-    static constexpr bool value = TX == 32 && (TY % (NT / 32)) == 0 &&
-                                  sizeof(typename S::pop_t) ==
-                                      sizeof(typename S::real);
-};
-
-template <class S, int TX, int TY, int NT, int PARITY>
-__global__ void __launch_bounds__(NT)
-    step_kernel(const Lattice L, int cur, int xlo, int xhi, int ylo, int yhi,
-                const __grid_constant__ TmaMaps maps)
-{
-    extern __shared__ __align__(128) unsigned char smem_raw[];
-    const int bx = blockIdx.x, by = blockIdx.y;
-    const int X0 = bx * TX, Y0 = by * TY;
-    const bool interior = bx >= xlo && bx <= xhi && by >= ylo && by <= yhi;
-    if constexpr (HasTma<S, TX, TY, NT>::value) {
-        if (interior && maps.valid) {
-            step_tile_tma<S, TX, TY, NT, PARITY>(L, cur, X0, Y0, smem_raw, maps);
-            return;
-        }
-    }
-    if (interior)
-        step_tile<S, TX, TY, NT, PARITY, true>(L, cur, X0, Y0, smem_raw);
-    else
-        step_tile<S, TX, TY, NT, PARITY, false>(L, cur, X0, Y0, smem_raw);
-}
-
-template <class S, int TX, int TY>
-static cudaError_t launch_shape(const Lattice &L, int parity, int cur,
-                                cudaStream_t s, const TmaMaps *maps)
-{
-    using real = typename S::real;
-    constexpr int NT = STEP_THREADS;
-    const size_t smem_v4 = StepSmem<real, TX, TY>::bytes;
-    const size_t smem_tma = HasTma<S, TX, TY, NT>::value
-                                ? TmaSmem<real, TX, TY>::bytes : 0;
-    const size_t smem = smem_v4 > smem_tma ? smem_v4 : smem_tma;
-    TmaMaps m{};
-    if (maps && maps->valid && maps->tx == TX && maps->ty == TY) m = *maps;
-    auto k0 = step_kernel<S, TX, TY, NT, 0>;
-    auto k1 = step_kernel<S, TX, TY, NT, 1>;
-    static int configured = -1;  // device the attribute was set on
-    int dev = 0;
-    cudaError_t e = cudaGetDevice(&dev);
-    if (e != cudaSuccess) return e;
-    if (configured != dev) {
-        e = cudaFuncSetAttribute(k0, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)smem);
-        if (e == cudaSuccess)
-            e = cudaFuncSetAttribute(
-                k1, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-        configured = dev;
-    }
-    // Interior tiles: the tile and its eight neighbours are full tiles and
-    // the halo and ring need no wrap and meet no solid row.
-    const int ntx = (L.nx + TX - 1) / TX, nty = (L.nyf + TY - 1) / TY;
-    const int nfx = L.nx / TX, nfy = L.nyf / TY;  // full tiles per direction
-    dim3 grid(ntx, nty);
-    if (parity == 0)
-        k0<<<grid, NT, smem, s>>>(L, cur, 1, nfx - 2, 1, nfy - 2, m);
-    else
-        k1<<<grid, NT, smem, s>>>(L, cur, 1, nfx - 2, 1, nfy - 2, m);
-    return cudaGetLastError();
-}
-
-// Tile shapes with a compiled kernel (all precisions).
+// Tile shapes with a compiled kernel (all precisions; same list in
+// step_impl.cuh).
 #define CPLBM_STEP_SHAPES(X) X(32, 16) X(32, 24) X(32, 32) X(64, 16)
-
-// ---------------------------------------------------------------------------
-// Batched step: many independent lattices of different sizes and physics in
-// one persistent launch.  Each CTA takes work items blockIdx.x,
-// blockIdx.x + gridDim.x, ... and runs the general or interior tile path on
-// that item's lattice, whose descriptor it first copies to shared memory.
-// ---------------------------------------------------------------------------
-template <class S, int TX, int TY, int NT, int PARITY>
-__global__ void __launch_bounds__(NT)
-    step_batch_kernel(const Lattice *__restrict__ lats,
-                      const WorkItem *__restrict__ items, int n_items, int cur)
-{
-    extern __shared__ __align__(128) unsigned char smem_raw[];
-    __shared__ Lattice sL;
-    static_assert(sizeof(Lattice) % sizeof(int) == 0, "descriptor copy");
-    for (int w = blockIdx.x; w < n_items; w += gridDim.x) {
-        const WorkItem it = items[w];
-        {
-            const int *src = reinterpret_cast<const int *>(lats + it.inst);
-            int *dst = reinterpret_cast<int *>(&sL);
-            for (int q = threadIdx.x; q < (int)(sizeof(Lattice) / sizeof(int));
-                 q += NT)
-                dst[q] = src[q];
-        }
-        __syncthreads();
-        if (it.interior)
-            step_tile<S, TX, TY, NT, PARITY, true>(sL, cur, it.bx * TX,
-                                                   it.by * TY, smem_raw);
-        else
-            step_tile<S, TX, TY, NT, PARITY, false>(sL, cur, it.bx * TX,
-                                                    it.by * TY, smem_raw);
-        __syncthreads();  // smem and sL are reused by the next item
-    }
-}
-
-template <class S, int TX, int TY>
-static cudaError_t launch_batch_shape(const Lattice *d_lats,
-                                      const WorkItem *d_items, int n_items,
-                                      int parity, int cur, int grid,
-                                      cudaStream_t s)
-{
-    using real = typename S::real;
-    constexpr int NT = STEP_THREADS;
-    const size_t smem = StepSmem<real, TX, TY>::bytes;
-    auto k0 = step_batch_kernel<S, TX, TY, NT, 0>;
-    auto k1 = step_batch_kernel<S, TX, TY, NT, 1>;
-    static int configured = -1, slots = 0;
-    int dev = 0;
-    cudaError_t e = cudaGetDevice(&dev);
-    if (e != cudaSuccess) return e;
-    if (configured != dev) {
-        e = cudaFuncSetAttribute(k0, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)smem);
-        if (e == cudaSuccess)
-            e = cudaFuncSetAttribute(
-                k1, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        int per_sm = 0, sms = 0;
-        if (e == cudaSuccess)
-            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k0, NT, smem);
-        if (e == cudaSuccess)
-            e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        if (e != cudaSuccess) return e;
-        slots = (per_sm > 0 ? per_sm : 1) * sms;
-        configured = dev;
-    }
-    if (n_items <= 0) return cudaSuccess;
-    if (grid <= 0) grid = slots;
-    if (grid > n_items) grid = n_items;
-    if (parity == 0)
-        k0<<<grid, NT, smem, s>>>(d_lats, d_items, n_items, cur);
-    else
-        k1<<<grid, NT, smem, s>>>(d_lats, d_items, n_items, cur);
-    return cudaGetLastError();
-}
-
-template <class S>
-static cudaError_t launch_batch_t(const Lattice *d_lats, const WorkItem *d_items,
-                                  int n_items, int parity, int cur, int tx,
-                                  int ty, int grid, cudaStream_t s)
-{
-#define CPLBM_CASE(a, b)                                                   \
-    if (tx == a && ty == b)                                                \
-        return launch_batch_shape<S, a, b>(d_lats, d_items, n_items, parity, \
-                                           cur, grid, s);
-    CPLBM_STEP_SHAPES(CPLBM_CASE)
-#undef CPLBM_CASE
-    return cudaErrorInvalidValue;
-}
-
-
-template <class S>
-static cudaError_t launch_step_t(const Lattice &L, int parity, int cur,
-                                 cudaStream_t s, const TmaMaps *maps)
-{
-#define CPLBM_CASE(a, b)                                           \
-    if (L.tx == a && L.ty == b)                                    \
-        return launch_shape<S, a, b>(L, parity, cur, s, maps);
-    CPLBM_STEP_SHAPES(CPLBM_CASE)
-#undef CPLBM_CASE
-    return cudaErrorInvalidValue;
-}
 
 bool step_shape_supported(int prec, int tx, int ty)
 {
@@ -957,19 +51,33 @@ void step_default_shape(int prec, int *tx, int *ty)
     *ty = prec == P_F64 ? 16 : (prec == P_F16_OFF ? 24 : 32);
 }
 
+void pt_shape(int prec, int *tx, int *ty)
+{
+    *tx = 32;
+    *ty = prec == P_F64 ? 16 : 32;
+}
+
+cudaError_t launch_step_pt(const Lattice &L, int parity, int cur, cudaStream_t s)
+{
+    if (L.walls) return cudaErrorInvalidValue;
+    if (L.precision == P_F64 && L.tx == 32 && L.ty == 16)
+        return launch_pt_f64(L, parity, cur, s);
+    if (L.precision == P_F32 && L.tx == 32 && L.ty == 32)
+        return launch_pt_f32(L, parity, cur, s);
+    return cudaErrorInvalidValue;
+}
+
 cudaError_t launch_step_batch(const Lattice *d_lats, const WorkItem *d_items,
                               int n_items, int parity, int cur, int precision,
                               int tx, int ty, int grid, cudaStream_t s)
 {
     switch (precision) {
-    case P_F64:
-        return launch_batch_t<SF64>(d_lats, d_items, n_items, parity, cur, tx, ty, grid, s);
-    case P_F32:
-        return launch_batch_t<SF32>(d_lats, d_items, n_items, parity, cur, tx, ty, grid, s);
+    case P_F64: return launch_batch_f64(d_lats, d_items, n_items, parity, cur, tx, ty, grid, s);
+    case P_F32: return launch_batch_f32(d_lats, d_items, n_items, parity, cur, tx, ty, grid, s);
     case P_F32_OFF:
-        return launch_batch_t<SF32Off>(d_lats, d_items, n_items, parity, cur, tx, ty, grid, s);
+        return launch_batch_f32off(d_lats, d_items, n_items, parity, cur, tx, ty, grid, s);
     case P_F16_OFF:
-        return launch_batch_t<SF16Off>(d_lats, d_items, n_items, parity, cur, tx, ty, grid, s);
+        return launch_batch_f16off(d_lats, d_items, n_items, parity, cur, tx, ty, grid, s);
     }
     return cudaErrorInvalidValue;
 }
@@ -978,10 +86,10 @@ cudaError_t launch_step(const Lattice &L, int parity, int cur, cudaStream_t s,
                         const TmaMaps *maps)
 {
     switch (L.precision) {
-    case P_F64: return launch_step_t<SF64>(L, parity, cur, s, maps);
-    case P_F32: return launch_step_t<SF32>(L, parity, cur, s, maps);
-    case P_F32_OFF: return launch_step_t<SF32Off>(L, parity, cur, s, maps);
-    case P_F16_OFF: return launch_step_t<SF16Off>(L, parity, cur, s, maps);
+    case P_F64: return launch_step_f64(L, parity, cur, s, maps);
+    case P_F32: return launch_step_f32(L, parity, cur, s, maps);
+    case P_F32_OFF: return launch_step_f32off(L, parity, cur, s, maps);
+    case P_F16_OFF: return launch_step_f16off(L, parity, cur, s, maps);
     }
     return cudaErrorInvalidValue;
 }

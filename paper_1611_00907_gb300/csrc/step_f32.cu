@@ -1,0 +1,26 @@
+// Step kernels of one storage precision (SF32); the templates live in
+// step_impl.cuh and the dispatch in step.cu.  One translation unit per
+// precision keeps the build parallel.
+#include "step_impl.cuh"
+
+namespace cplbm {
+
+cudaError_t launch_step_f32(const Lattice &L, int parity, int cur,
+                            cudaStream_t s, const TmaMaps *maps)
+{
+    return launch_step_t<SF32>(L, parity, cur, s, maps);
+}
+
+cudaError_t launch_batch_f32(const Lattice *d_lats, const WorkItem *d_items,
+                             int n_items, int parity, int cur, int tx, int ty,
+                             int grid, cudaStream_t s)
+{
+    return launch_batch_t<SF32>(d_lats, d_items, n_items, parity, cur, tx, ty, grid, s);
+}
+
+cudaError_t launch_pt_f32(const Lattice &L, int parity, int cur, cudaStream_t s)
+{
+    return launch_pt_shape<SF32, 32, 32>(L, parity, cur, s);
+}
+
+}  // namespace cplbm

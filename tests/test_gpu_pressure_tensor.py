@@ -1,0 +1,64 @@
+"""The pressure-tensor baseline (Eq. 5 with Eq. 9) on the GPU against the
+oracle's pressure-tensor step, and its argument checks."""
+import numpy as np
+import pytest
+
+import oracle
+from oracle import thermo
+from paper_1611_00907_gb300 import LbmError, Simulation, inputs
+
+pytestmark = pytest.mark.gpu
+
+
+def _case(nx, ny, precision):
+    e = thermo.make_eos("cs", 1.0, 4.0, 1.0, 0.85)
+    rv, rl, _, _ = thermo.maxwell(e)
+    rho = inputs.drop(nx, ny, min(nx, ny) / 4, rl, rv, 4.0)
+    sim = Simulation(nx, ny, "cs", 1.0, 4.0, 1.0, 0.85, tau=1.0, kappa=0.5,
+                     precision=precision)
+    ref = oracle.Lattice(nx, ny, e, 1.0, 0.5)
+    return sim, ref, rho
+
+
+def _rel(a, b):
+    return np.abs(a - b).max() / np.abs(b).max()
+
+
+@pytest.mark.parametrize("size", [(70, 21), (224, 165), (5, 5)])
+@pytest.mark.parametrize("steps", [1, 2, 200])
+def test_pressure_tensor_step_matches_oracle_fp64(size, steps, oracle_threads):
+    sim, ref, rho = _case(*size, "f64")
+    with sim:
+        sim.set_force_model("pressure_tensor")
+        sim.init(rho).step(steps)
+        ref.init_equilibrium(rho).step_pressure_tensor(steps)
+        f = sim.populations()
+        for i in range(9):
+            assert _rel(f[i], ref.f[i]) < 1e-12, i
+
+
+def test_pressure_tensor_fp32(oracle_threads):
+    sim, ref, rho = _case(224, 165, "f32")
+    with sim:
+        sim.set_force_model("pressure_tensor")
+        sim.init(rho).step(50)
+        ref.init_equilibrium(rho).step_pressure_tensor(50)
+        assert _rel(sim.moments()["rho"], ref.moments()["rho"]) < 1e-5
+
+
+def test_pressure_tensor_arguments():
+    e = thermo.make_eos("cs", 1.0, 4.0, 1.0, 0.85)
+    rv, rl, _, _ = thermo.maxwell(e)
+    with Simulation(70, 21, walls=True) as sim:
+        with pytest.raises(LbmError):
+            sim.set_force_model("pressure_tensor")
+    with Simulation(70, 21, precision="f16_offset", rho_ref=0.15) as sim:
+        with pytest.raises(LbmError):
+            sim.set_force_model("pressure_tensor")
+    with Simulation(70, 21, precision="f64") as sim:
+        sim.set_force_model("pressure_tensor")
+        with pytest.raises(LbmError):
+            sim.set_tile(64, 16)
+        sim.init(inputs.drop(70, 21, 5, rl, rv)).step(3)
+        sim.set_force_model("chemical_potential")
+        sim.step(3)
