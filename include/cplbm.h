@@ -221,6 +221,33 @@ lbm_status lbm_batch_info(const lbm_batch *b, int *count, long long *nodes,
 void lbm_batch_destroy(lbm_batch *b);
 const char *lbm_batch_last_error(const lbm_batch *b);
 
+/* ------------------------------------------------------------------------
+ * Learned warm start: a small BF16 multilayer perceptron with FP32
+ * accumulation (tensor-core kernels) that maps a case's parameters to its
+ * converged observables, used to start a simulation near equilibrium.  The
+ * paper has no counterpart; the simulation it initialises is the paper's.
+ * Network: up to 16 inputs -> 3 x 128 tanh -> up to 16 linear outputs.
+ * Parameters are FP32 in one array of lbm_mlp_param_count() values: per
+ * layer the weights [k][n] (k inputs, n outputs; 16, 128, 128, 128 by
+ * 128, 128, 128, 16), then the biases of the four layers.
+ * ------------------------------------------------------------------------ */
+typedef struct lbm_mlp lbm_mlp;
+int lbm_mlp_param_count(void);
+/* init: host array of the initial parameters. */
+lbm_status lbm_mlp_create(int device, const float *init, lbm_mlp **out);
+/* iters full-batch Adam steps (lr; betas 0.9, 0.999) minimising the mean
+ * squared error between the first nout outputs and T.  X [B][nin] and
+ * T [B][nout] are device FP32 arrays; *loss (may be NULL) receives the mean
+ * squared error of the last step's forward pass. */
+lbm_status lbm_mlp_train(lbm_mlp *m, const float *X, int nin, const float *T,
+                         int nout, int B, int iters, float lr, float *loss);
+/* Y [B][nout] = the network's first nout outputs for X [B][nin] (device). */
+lbm_status lbm_mlp_predict(lbm_mlp *m, const float *X, int nin, float *Y,
+                           int nout, int B);
+lbm_status lbm_mlp_get_params(lbm_mlp *m, float *out);  /* host FP32 */
+void lbm_mlp_destroy(lbm_mlp *m);
+const char *lbm_mlp_last_error(const lbm_mlp *m);
+
 /* Allocation-free FP64 step, for callers that may not allocate device
  * memory: for example a host application whose own allocator owns the GPU
  * and forbids other code from calling cudaMalloc, or one that cannot accept

@@ -85,6 +85,14 @@ SIGNATURES = {
                         C.POINTER(C.c_int)], C.c_int),
     "lbm_batch_destroy": ([_ctx], None),
     "lbm_batch_last_error": ([_ctx], C.c_char_p),
+    "lbm_mlp_param_count": ([], C.c_int),
+    "lbm_mlp_create": ([C.c_int, _vp, C.POINTER(_ctx)], C.c_int),
+    "lbm_mlp_train": ([_ctx, _vp, C.c_int, _vp, C.c_int, C.c_int, C.c_int,
+                       C.c_float, C.POINTER(C.c_float)], C.c_int),
+    "lbm_mlp_predict": ([_ctx, _vp, C.c_int, _vp, C.c_int, C.c_int], C.c_int),
+    "lbm_mlp_get_params": ([_ctx, _vp], C.c_int),
+    "lbm_mlp_destroy": ([_ctx], None),
+    "lbm_mlp_last_error": ([_ctx], C.c_char_p),
     "lbm_destroy": ([_ctx], None),
     "lbm_last_error": ([_ctx], C.c_char_p),
 }
@@ -126,6 +134,13 @@ class LbmError(RuntimeError):
 def check(status, ctx=None):
     if status != LBM_OK:
         msg = load().lbm_last_error(ctx)
+        raise LbmError(status, msg.decode() if msg else "")
+    return status
+
+
+def check_mlp(status, mlp=None):
+    if status != LBM_OK:
+        msg = load().lbm_mlp_last_error(mlp)
         raise LbmError(status, msg.decode() if msg else "")
     return status
 

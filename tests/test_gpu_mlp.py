@@ -1,0 +1,106 @@
+"""The BF16 tensor-core MLP against a NumPy definition of the same network
+(BF16 rounding of weights and layer inputs at the same points, wide
+accumulation): forward outputs, the direction of the first Adam step
+(equal to -sign(gradient)), and that full-batch training reduces the loss."""
+import numpy as np
+import pytest
+
+from paper_1611_00907_gb300 import mlp
+
+pytestmark = pytest.mark.gpu
+
+
+def bf16(x):
+    """Round float32 values to bfloat16 (nearest, ties to even)."""
+    u = np.ascontiguousarray(x, dtype=np.float32).view(np.uint32)
+    r = (u + (0x7FFF + ((u >> 16) & 1))) & 0xFFFF0000
+    return r.view(np.float32)
+
+
+def ref_forward(p, X, nout):
+    ws, bs = mlp.layout()
+    a = bf16(np.pad(X, ((0, 0), (0, 16 - X.shape[1]))))
+    acts = [a]
+    for l, ((sl, (k, n)), bsl) in enumerate(zip(ws, bs)):
+        W = bf16(p[sl].reshape(k, n)).astype(np.float64)
+        z = acts[-1].astype(np.float64) @ W + p[bsl]
+        if l < 3:
+            acts.append(bf16(np.tanh(z).astype(np.float32)))
+        else:
+            out = z
+    return out[:, :nout], acts
+
+
+def ref_grad(p, X, T):
+    ws, bs = mlp.layout()
+    B, nout = T.shape
+    y, acts = ref_forward(p, X, nout)
+    g = np.zeros_like(p, dtype=np.float64)
+    d = np.zeros((B, 16))
+    d[:, :nout] = 2 * (y - T) / (B * nout)
+    for l in range(3, -1, -1):
+        sl, (k, n) = ws[l]
+        g[sl] = (acts[l].astype(np.float64).T @ d).ravel()
+        g[bs[l]] = d.sum(axis=0)
+        if l == 0:
+            break
+        W = bf16(p[sl].reshape(k, n)).astype(np.float64)
+        d = (d @ W.T) * (1 - acts[l].astype(np.float64) ** 2)
+    return g
+
+
+def _data(B=512, nin=8, nout=4, seed=0):
+    rng = np.random.default_rng(seed)
+    X = rng.uniform(-1, 1, (B, nin)).astype(np.float32)
+    A = rng.normal(size=(nin, nout))
+    T = np.sin(X @ A).astype(np.float32)
+    return X, T
+
+
+def test_forward_matches_reference():
+    torch = pytest.importorskip("torch")
+    X, _ = _data(300)        # not a multiple of the 64-sample CTA
+    p = mlp.init_params(3)
+    net = mlp.Mlp(p)
+    try:
+        Y = net.predict(torch.tensor(X, device="cuda"), 4).cpu().numpy()
+    finally:
+        net.close()
+    want, _ = ref_forward(p, X, 4)
+    err = np.abs(Y - want)
+    assert np.percentile(err, 99) < 2e-3
+    assert err.max() < 3e-2
+
+
+def test_first_adam_step_follows_the_gradient():
+    torch = pytest.importorskip("torch")
+    X, T = _data(512)
+    p = mlp.init_params(5)
+    net = mlp.Mlp(p)
+    try:
+        net.train(torch.tensor(X, device="cuda"), torch.tensor(T, device="cuda"),
+                  1, lr=1e-4)
+        p1 = net.params()
+    finally:
+        net.close()
+    step = (p1 - p) / -1e-4          # = g / (|g| + eps) on the first step
+    g = ref_grad(p, X, T)
+    big = np.abs(g) > 1e-2 * np.abs(g).max()
+    assert big.sum() > 1000
+    agree = np.mean(np.sign(step[big]) == np.sign(g[big]))
+    assert agree > 0.99
+
+
+def test_training_reduces_loss():
+    torch = pytest.importorskip("torch")
+    X, T = _data(4096, seed=1)
+    net = mlp.Mlp(seed=2)
+    try:
+        Xd, Td = torch.tensor(X, device="cuda"), torch.tensor(T, device="cuda")
+        first = net.train(Xd, Td, 1, lr=3e-3)
+        last = net.train(Xd, Td, 600, lr=3e-3)
+        pred = net.predict(Xd, 4).cpu().numpy()
+    finally:
+        net.close()
+    assert last < 0.1 * first
+    assert np.mean((pred - T) ** 2) < 0.2 * np.mean(T ** 2)
