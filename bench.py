@@ -313,6 +313,36 @@ def measure_batch(which, precision, steps, warmup, sequential=True):
     return out
 
 
+def measure_warmstart(full):
+    """Sweep time-to-converge, learned warm start against the plain
+    half-disc start.  Small: 64 wall drops of 256x128 after training on
+    1024 runs of 128x64; full: 256 drops of 512x256 after 4096 runs."""
+    import torch
+    from paper_1611_00907_gb300 import warmstart as ws
+    ntrain, neval, nx, ny, max_steps = ((4096, 256, 512, 256, 40000) if full
+                                        else (1024, 64, 256, 128, 20000))
+    stream = torch.cuda.Stream()
+    t0 = time.perf_counter()
+    with torch.cuda.stream(stream):
+        cases, X, Y = ws.build_dataset(ntrain, 128, 64, 6000, seed=1,
+                                       stream=stream)
+    t_data = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    model = ws.Model(X, Y, iters=3000, lr=2e-3)
+    t_train = time.perf_counter() - t0
+    try:
+        with torch.cuda.stream(stream):
+            r = ws.compare(model, ws.sample_cases(neval, seed=99), nx, ny,
+                           max_steps, check_every=200, tol=1e-5, stream=stream)
+    finally:
+        model.close()
+    r.update(training_runs=ntrain, training_kept=len(cases),
+             training_lattice=[128, 64], training_steps=6000,
+             dataset_s=round(t_data, 2), train_s=round(t_train, 2),
+             final_loss=model.loss)
+    return r
+
+
 def cpu_baseline(budget_s=15.0):
     """The oracle as it stands (FP64 C) on a 512 x 512 sample of the same
     workload, all host cores."""
@@ -417,6 +447,9 @@ def main():
                     help="steps of the batched workloads (0: skip them)")
     ap.add_argument("--pt-steps", type=int, default=200,
                     help="steps of the pressure-tensor comparison (0: skip)")
+    ap.add_argument("--warmstart", default="small",
+                    choices=["small", "full", "off"],
+                    help="learned warm-start sweep (full: 256 x 512x256)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     rank, world = dist_setup()
@@ -480,6 +513,10 @@ def main():
         batches["batch_wetting_f16"] = measure_batch(
             "wetting", "f16_offset", args.batch_steps, 4, sequential=False)
 
+    warm = None
+    if args.warmstart != "off" and rank == 0:
+        warm = measure_warmstart(args.warmstart == "full")
+
     base = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         base = cpu_baseline()
@@ -497,6 +534,8 @@ def main():
         line.update(batches)
         if pt:
             line["pressure_tensor_vs_chemical_potential"] = pt
+        if warm:
+            line["warm_start"] = warm
         print(json.dumps(line))
     if world > 1:
         import torch.distributed as dist

@@ -317,6 +317,7 @@ lbm_status lbm_create(const lbm_config *cfg, lbm_ctx **out)
                  cfg->precision == LBM_F16_OFFSET) ? cfg->rho_ref : 0.0;
     L.precision = cfg->precision;
     L.top_mode = 0;
+    set_consts(L);
     step_default_shape(L.precision, &L.tx, &L.ty);
 
     const size_t pb = pop_bytes(L.precision), rb = rho_bytes(L.precision);
@@ -407,6 +408,7 @@ lbm_status lbm_set_eos(lbm_ctx *c, int eos, double a, double b, double R,
     E.b = b;
     E.RT = R * c->T;
     E.aalpha = a * c->alpha;
+    set_consts(c->L);
     c->eos_set = true;
     return LBM_OK;
 }
@@ -591,6 +593,7 @@ lbm_status lbm_set_wall_mu(lbm_ctx *c, double mu_bottom, int top_mode,
     c->L.mu_bottom = mu_bottom;
     c->L.top_mode = top_mode;
     c->L.mu_top = mu_top;
+    set_consts(c->L);
     return LBM_OK;
 }
 

@@ -26,12 +26,29 @@ constexpr int STEP_THREADS = 256;
 // direction from the receiving node's tile to the tile that wrote them.
 enum Ring { R_L = 0, R_R, R_B, R_T, R_BL, R_BR, R_TL, R_TR, R_COUNT };
 
-// EOS constants in the arithmetic type of a kernel.  Each kernel converts
-// the double values held by the context.
+// EOS constants as the context holds them (double).
 struct EosParams {
     int kind;
     double a, b, RT;   // RT = R * T
     double aalpha;     // a * alpha(T) (PR, RKS); a otherwise
+};
+
+// The same constants in the arithmetic type T of a kernel, with the
+// combinations the bulk chemical potentials use precomputed (set_consts):
+//   quarter_b = b / 4 (CS), pr_c = a alpha / (2 sqrt2 b) (PR),
+//   pr_s2m1 = sqrt2 - 1, pr_s2p1 = sqrt2 + 1 (PR), rks_c = a alpha / b (RKS).
+template <class T> struct EosT {
+    int kind;
+    T a, b, RT, aalpha, quarter_b, pr_c, pr_s2m1, pr_s2p1, rks_c;
+};
+
+// Physical constants of one lattice in the arithmetic type T, filled on the
+// host by set_consts: kernels do no double arithmetic and no double-to-float
+// conversion (GB300's FP64 pipe is narrow enough that two double divisions
+// per thread showed up as a busy FP64 pipe in the FP32 step).
+template <class T> struct Consts {
+    T tau, omega, kappa, rho_ref, mu_bottom, mu_top;   // omega = 1 / tau
+    EosT<T> eos;
 };
 
 // Geometry, storage and physics of one lattice as the kernels see it.
@@ -63,7 +80,23 @@ struct Lattice {
     int top_mode;
     int precision;
     int *err;            // device flag: a bounded wait in a kernel gave up
+    Consts<float> cf;    // tau .. mu_top and eos as float (set_consts)
+    Consts<double> cd;   // ... and as double
 };
+
+// Refresh L.cf and L.cd from the double fields; call after any change of
+// tau, kappa, rho_ref, eos, mu_bottom or mu_top.
+void set_consts(Lattice &L);
+
+template <class T> __host__ __device__ __forceinline__ const Consts<T> &consts(const Lattice &L);
+template <> __host__ __device__ __forceinline__ const Consts<float> &consts<float>(const Lattice &L)
+{
+    return L.cf;
+}
+template <> __host__ __device__ __forceinline__ const Consts<double> &consts<double>(const Lattice &L)
+{
+    return L.cd;
+}
 
 // Tensor-map descriptors for the TMA loads of the step's interior tiles:
 // the population array (3-D: x, fluid row, plane) and the two density

@@ -70,18 +70,6 @@ __device__ __forceinline__ void st_real(__half *p, float v) { *p = __float2half_
 // Bulk chemical potential psi'(rho): Eq. 18 (vdW), Eq. 21 (RK/RKS), Eq. 24
 // (PR), Eq. 27 (CS) without the -kappa lap(rho) term.
 // ---------------------------------------------------------------------------
-template <class T>
-struct EosT {
-    int kind;
-    T a, b, RT, aalpha, quarter_b, pr_c, pr_s2m1, pr_s2p1, rks_c;
-    __host__ __device__ explicit EosT(const EosParams &e)
-        : kind(e.kind), a(T(e.a)), b(T(e.b)), RT(T(e.RT)), aalpha(T(e.aalpha)),
-          quarter_b(T(0.25 * e.b)),
-          pr_c(T(e.aalpha / (2.0 * 1.4142135623730951 * e.b))),
-          pr_s2m1(T(0.41421356237309515)), pr_s2p1(T(2.414213562373095)),
-          rks_c(T(e.aalpha / e.b)) {}
-};
-
 // Division and logarithm of the arithmetic type: the FP32 kernels use the
 // fast hardware forms (__fdividef, __logf), whose few-ulp errors sit far
 // below the FP32 storage error; FP64 keeps IEEE division and log().
@@ -340,7 +328,7 @@ __device__ __forceinline__ typename S::real load_rho(const Lattice &L, int cur,
 {
     using real = typename S::real;
     const real v = load_rho_stored<S>(L, cur, r, x);
-    return S::offset ? v + (real)L.rho_ref : v;
+    return S::offset ? v + consts<real>(L).rho_ref : v;
 }
 
 // Fill s_rho[(TY + 4) x (TX + 4)] with the stored-form density of the tile
@@ -409,9 +397,10 @@ __device__ void mu_tile(const Lattice &L, int X0, int Y0,
 {
     using real = typename S::real;
     constexpr int W = TX + 2, H = TY + 2, WR = TX + 4;
-    const EosT<real> eos(L.eos);
-    const real kappa = (real)L.kappa;
-    const real ref = S::offset ? (real)L.rho_ref : real(0);
+    const Consts<real> &K = consts<real>(L);
+    const EosT<real> &eos = K.eos;
+    const real kappa = K.kappa;
+    const real ref = S::offset ? K.rho_ref : real(0);
     const int wx = min(TX, L.nx - X0), wy = min(TY, L.nyf - Y0);
     for (int k = threadIdx.x; k < W * H; k += blockDim.x) {
         const int lx = k % W, ly = k / W;
@@ -423,13 +412,13 @@ __device__ void mu_tile(const Lattice &L, int X0, int Y0,
         const int c = (ly + 1) * WR + lx + 1;  // same node in s_rho
         real m;
         if (L.walls && r == -1) {
-            m = (real)L.mu_bottom;
+            m = K.mu_bottom;
         } else if (L.walls && r == L.nyf) {
             if (L.top_mode == 0) {
                 const int cb = c - WR;  // fluid neighbour below (row nyf-1)
                 m = mu_bulk(eos, s_rho[cb] + ref) - kappa * lap9<real, WR>(s_rho, cb);
             } else {
-                m = (real)L.mu_top;
+                m = K.mu_top;
             }
         } else if (L.walls && (r < -1 || r > L.nyf)) {
             m = real(0);

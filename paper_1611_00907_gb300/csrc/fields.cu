@@ -72,7 +72,7 @@ __global__ void macro_kernel(const Lattice L, int parity, int cur,
     mu_tile<S, TX, TY>(L, X0, Y0, s_rho, s_mu);
     __syncthreads();
 
-    const real rho_ref = S::offset ? (real)L.rho_ref : real(0);
+    const real rho_ref = S::offset ? consts<real>(L).rho_ref : real(0);
     const pop_t *A = (const pop_t *)L.pops;
     double acc_m = 0.0, acc_x = 0.0, acc_y = 0.0, acc_d = 0.0;
     // s_rho holds the stored form; rho_ref makes it absolute

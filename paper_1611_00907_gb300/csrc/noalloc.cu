@@ -151,6 +151,7 @@ extern "C" lbm_status lbm_step_noalloc(
     L.top_mode = top_mode;
     L.mu_top = mu_top;
     L.precision = P_F64;
+    set_consts(L);
     step_default_shape(P_F64, &L.tx, &L.ty);
 
     if (cfg->device < 0 || cfg->device >= kMaxDevices)

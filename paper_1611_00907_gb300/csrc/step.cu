@@ -19,6 +19,34 @@ CPLBM_PREC_DECL(f16off)
 cudaError_t launch_pt_f64(const Lattice &L, int parity, int cur, cudaStream_t s);
 cudaError_t launch_pt_f32(const Lattice &L, int parity, int cur, cudaStream_t s);
 
+template <class T>
+static void fill_consts(Consts<T> &k, const Lattice &L)
+{
+    const EosParams &e = L.eos;
+    k.tau = T(L.tau);
+    k.omega = T(1) / T(L.tau);
+    k.kappa = T(L.kappa);
+    k.rho_ref = T(L.rho_ref);
+    k.mu_bottom = T(L.mu_bottom);
+    k.mu_top = T(L.mu_top);
+    k.eos.kind = e.kind;
+    k.eos.a = T(e.a);
+    k.eos.b = T(e.b);
+    k.eos.RT = T(e.RT);
+    k.eos.aalpha = T(e.aalpha);
+    k.eos.quarter_b = T(0.25 * e.b);
+    k.eos.pr_c = T(e.b > 0 ? e.aalpha / (2.0 * 1.4142135623730951 * e.b) : 0.0);
+    k.eos.pr_s2m1 = T(0.41421356237309515);
+    k.eos.pr_s2p1 = T(2.414213562373095);
+    k.eos.rks_c = T(e.b > 0 ? e.aalpha / e.b : 0.0);
+}
+
+void set_consts(Lattice &L)
+{
+    fill_consts(L.cf, L);
+    fill_consts(L.cd, L);
+}
+
 // Tile shapes with a compiled kernel (all precisions; same list in
 // step_impl.cuh).
 #define CPLBM_STEP_SHAPES(X) X(32, 16) X(32, 24) X(32, 32) X(64, 16)

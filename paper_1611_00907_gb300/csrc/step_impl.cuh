@@ -151,9 +151,10 @@ __device__ __forceinline__ void mu_interior(const Lattice &L,
 {
     using real = typename S::real;
     constexpr int W = TX + 2, H = TY + 2, WR = TX + 4;
-    const EosT<real> eos(L.eos);
-    const real kappa = (real)L.kappa;
-    const real ref = S::offset ? (real)L.rho_ref : real(0);
+    const Consts<real> &K = consts<real>(L);
+    const EosT<real> &eos = K.eos;
+    const real kappa = K.kappa;
+    const real ref = S::offset ? K.rho_ref : real(0);
     for (int k = threadIdx.x; k < W * H; k += NT) {
         const int lx = k % W, ly = k / W;
         const int c = (ly + 1) * WR + lx + 1;
@@ -266,9 +267,10 @@ __device__ void pt_tile(const Lattice &L, int X0, int Y0,
 {
     using real = typename S::real;
     constexpr int W = TX + 2, H = TY + 2, WR = TX + 4, N = W * H;
-    const EosT<real> eos(L.eos);
-    const real kappa = (real)L.kappa;
-    const real ref = S::offset ? (real)L.rho_ref : real(0);
+    const Consts<real> &K = consts<real>(L);
+    const EosT<real> &eos = K.eos;
+    const real kappa = K.kappa;
+    const real ref = S::offset ? K.rho_ref : real(0);
     const int wx = min(TX, L.nx - X0), wy = min(TY, L.nyf - Y0);
     for (int k = threadIdx.x; k < N; k += blockDim.x) {
         const int lx = k % W, ly = k / W;
@@ -372,9 +374,9 @@ __device__ __forceinline__ void step_tile(const Lattice &L, int cur, int X0,
     __syncthreads();
 
     // 3. Force, collision, in-place streaming.
-    const real tau = (real)L.tau;
-    const real omega = real(1) / tau;
-    const real rho_ref = S::offset ? (real)L.rho_ref : real(0);
+    const real tau = consts<real>(L).tau;
+    const real omega = consts<real>(L).omega;
+    const real rho_ref = S::offset ? consts<real>(L).rho_ref : real(0);
     if constexpr (ASYNC) cp_async_wait_all();
     real self0[PER];
 #pragma unroll
@@ -639,9 +641,10 @@ __device__ __forceinline__ void step_tile_tma(const Lattice &L, int cur, int X0,
     //    Columns 1..TX: lane a - 1, each warp a run of consecutive rows with
     //    a rolling 3 x 3 window; columns 0 and TX + 1 separately.
     {
-        const EosT<real> eos(L.eos);
-        const real kappa = (real)L.kappa;
-        const real ref = S::offset ? (real)L.rho_ref : real(0);
+        const Consts<real> &K = consts<real>(L);
+        const EosT<real> &eos = K.eos;
+        const real kappa = K.kappa;
+        const real ref = S::offset ? K.rho_ref : real(0);
         const int b0 = (warp * MH) / NW, b1 = ((warp + 1) * MH) / NW;
         const int a = lane + 1;
         real w[3][3];
@@ -671,9 +674,9 @@ __device__ __forceinline__ void step_tile_tma(const Lattice &L, int cur, int X0,
     // 4. Force, collision, in-place streaming and the register hand-over for
     //    the thread's PER nodes at rows ly0 .. ly0 + PER - 1, column lx.
     const int lx = lane, ly0 = warp * PER;
-    const real tau = (real)L.tau;
-    const real omega = real(1) / tau;
-    const real rho_ref = S::offset ? (real)L.rho_ref : real(0);
+    const real tau = consts<real>(L).tau;
+    const real omega = consts<real>(L).omega;
+    const real rho_ref = S::offset ? consts<real>(L).rho_ref : real(0);
     pop_t *A = (pop_t *)L.pops;
     rho_t *Rn = (rho_t *)L.rho[nxt];
     rho_t *const *ring = (rho_t *const *)L.ring[nxt];

@@ -1,0 +1,87 @@
+"""Measurements on converged density fields of a wall droplet: bulk liquid
+and vapour densities, interface width and contact angle (Sec. V's
+spherical-cap formulas).  Used for the learned warm start's training
+targets and for judging its error; plain NumPy on host arrays [ny, nx].
+
+Conventions: rows 0 and ny - 1 are solid; the wall plane of the halfway
+bounce-back lies half a node above row 0; the interface is the level set
+rho_m = (rho_l + rho_v) / 2, located by linear interpolation.
+"""
+import math
+
+import numpy as np
+
+
+def bulk_densities(rho):
+    """(rho_l, rho_v): mean of the liquid plateau (within 2 % of the largest
+    density) and median of the top quarter of the fluid rows."""
+    fluid = rho[1:-1]
+    top = fluid.max()
+    rho_l = float(fluid[fluid >= top - 0.02 * abs(top)].mean())
+    q = max(1, fluid.shape[0] // 4)
+    rho_v = float(np.median(fluid[-q:]))
+    return rho_l, rho_v
+
+
+def _level_crossings(v, level):
+    """Fractional positions where the sequence v crosses `level`."""
+    s = v - level
+    i = np.nonzero(s[:-1] * s[1:] < 0)[0]
+    return i + s[i] / (s[i] - s[i + 1])
+
+
+def drop_column(rho):
+    """Column through the drop's mass centre (excess over the vapour)."""
+    _, rho_v = bulk_densities(rho)
+    w = np.clip(rho[1:-1] - rho_v, 0.0, None).sum(axis=0)
+    if w.sum() <= 0:
+        return rho.shape[1] // 2
+    return int(round(float((w * np.arange(rho.shape[1])).sum() / w.sum())))
+
+
+def interface_width(rho):
+    """10-90 % thickness of the drop's top interface along its centre
+    column, converted to the width W of a tanh(2 d / W) profile."""
+    rho_l, rho_v = bulk_densities(rho)
+    col = rho[1:-1, drop_column(rho)]
+    lo = _level_crossings(col, rho_v + 0.1 * (rho_l - rho_v))
+    hi = _level_crossings(col, rho_v + 0.9 * (rho_l - rho_v))
+    if len(lo) == 0 or len(hi) == 0:
+        return float("nan")
+    return float((lo.max() - hi.max()) / math.atanh(0.8))
+
+
+def contact_angle(rho):
+    """Contact angle in degrees from the base chord L on the wall plane
+    (extrapolated from the first two fluid rows) and the apex height H
+    above it (Sec. V):
+    R = (4 H^2 + L^2) / (8 H), tan(theta) = L / (2 (R - H)).  A drop no
+    longer touching the wall gives 180."""
+    rho_l, rho_v = bulk_densities(rho)
+    mid = 0.5 * (rho_l + rho_v)
+    if not (rho[1] > mid).any():
+        return 180.0 if (rho[1:-1] > mid).any() else float("nan")
+    cx = drop_column(rho)
+    chords = []
+    for row in (rho[1], rho[2]):
+        xs = _level_crossings(row, mid)
+        left, right = xs[xs <= cx], xs[xs >= cx]
+        if len(left) == 0 or len(right) == 0:
+            return float("nan")
+        chords.append(float(right.min() - left.max()))
+    # rows 1 and 2 sit 0.5 and 1.5 above the wall plane: extrapolate the
+    # chord linearly down to the plane
+    L = 1.5 * chords[0] - 0.5 * chords[1]
+    ys = _level_crossings(rho[1:-1, cx], mid)
+    if len(ys) == 0:
+        return float("nan")
+    H = float(ys.max()) + 0.5          # fluid row 1 is 0.5 above the wall
+    R = (4 * H * H + L * L) / (8 * H)
+    return math.degrees(math.atan2(L / 2, R - H))
+
+
+def measure(rho):
+    """dict of rho_l, rho_v, width, theta for a wall-droplet field."""
+    rho_l, rho_v = bulk_densities(rho)
+    return dict(rho_l=rho_l, rho_v=rho_v, width=interface_width(rho),
+                theta=contact_angle(rho))

@@ -1,0 +1,233 @@
+"""Learned warm start for wall-droplet runs.
+
+A BF16 MLP (mlp.py) maps a case's parameters - EOS (one-hot vdW / CS /
+PR), T/T_c, kappa, tau, the wall's surface chemical potential (relative to
+coexistence) and the drop's area fraction - to its converged observables:
+liquid and vapour densities, interface width and contact angle.  It is
+trained on converged runs of the method itself (batched lattices), and a
+new case then starts from a circular-cap drop with the predicted angle,
+densities and width instead of the plain half-disc at the Maxwell
+densities.  The plain cold start stays the fallback and the judge: both
+are run to convergence and their observables compared.
+"""
+import math
+
+import numpy as np
+
+from . import Batch, eos_coexistence, eos_critical, inputs
+from . import observables as obs
+
+KINDS = ("vdw", "cs", "pr")
+# parameter ranges kept inside the scheme's stable region
+RANGES = {
+    "vdw": dict(Tr=(0.78, 0.95), kappa=(0.008, 0.016), tau=(0.9, 1.3), dmu=0.15),
+    "cs": dict(Tr=(0.78, 0.95), kappa=(0.4, 0.6), tau=(0.9, 1.3), dmu=0.05),
+    "pr": dict(Tr=(0.8, 0.95), kappa=(0.008, 0.016), tau=(1.0, 1.3), dmu=0.15),
+}
+NFEAT, NTARG = 8, 4
+
+
+def sample_cases(n, seed):
+    """n random wall-droplet cases: EOS, T_r, kappa, tau, mu_s - mu_coex,
+    drop area fraction."""
+    rng = np.random.default_rng(seed)
+    cases = []
+    for _ in range(n):
+        kind = KINDS[rng.integers(3)]
+        r = RANGES[kind]
+        e = dict(inputs.EOS_SETS[kind])
+        e.pop("kappa")
+        Tr = rng.uniform(*r["Tr"])
+        rv, rl, mc = eos_coexistence(kind, e["a"], e["b"], 1.0, Tr,
+                                     e.get("omega", 0.344))
+        dmu = rng.uniform(-r["dmu"], r["dmu"])
+        cases.append(dict(eos=kind, Tr=Tr, kappa=rng.uniform(*r["kappa"]),
+                          tau=rng.uniform(*r["tau"]), dmu=dmu,
+                          mu_bottom=mc + dmu, area=rng.uniform(0.05, 0.15),
+                          rho_v=rv, rho_l=rl, **e))
+    return cases
+
+
+def features(cases):
+    X = np.zeros((len(cases), NFEAT), dtype=np.float32)
+    for i, c in enumerate(cases):
+        X[i, KINDS.index(c["eos"])] = 1.0
+        X[i, 3:] = (c["Tr"], math.log(c["kappa"]), c["tau"],
+                    c["dmu"] / RANGES[c["eos"]]["dmu"], c["area"])
+    return X
+
+
+def targets(cases, measured):
+    """Observables scaled to O(1): rho_l / rho_c, log(rho_v / rho_c),
+    width, theta / 180."""
+    Y = np.zeros((len(cases), NTARG), dtype=np.float32)
+    for i, (c, m) in enumerate(zip(cases, measured)):
+        _, rc = eos_critical(c["eos"], c["a"], c["b"], 1.0)
+        Y[i] = (m["rho_l"] / rc, math.log(max(m["rho_v"], 1e-12) / rc),
+                m["width"], m["theta"] / 180.0)
+    return Y
+
+
+def untarget(case, y):
+    _, rc = eos_critical(case["eos"], case["a"], case["b"], 1.0)
+    return dict(rho_l=float(y[0]) * rc, rho_v=math.exp(float(y[1])) * rc,
+                width=float(y[2]), theta=float(y[3]) * 180.0)
+
+
+def _spec(case, nx, ny):
+    return dict(nx=nx, ny=ny, walls=True, tau=case["tau"], kappa=case["kappa"],
+                eos=case["eos"], a=case["a"], b=case["b"], Tr=case["Tr"],
+                omega=case.get("omega", 0.344), mu_bottom=case["mu_bottom"])
+
+
+def cold_field(case, nx, ny):
+    """The plain start: a half disc of the requested area at the Maxwell
+    densities, on the wall plane."""
+    area = case["area"] * nx * (ny - 2)
+    r = math.sqrt(2 * area / math.pi)
+    width = 4.0 if case["kappa"] > 0.1 else 2.0
+    return inputs.wall_drop(nx, ny, r, case["rho_l"], case["rho_v"], width)
+
+
+def warm_field(case, pred, nx, ny):
+    """A circular cap of the same area meeting the wall at the predicted
+    angle, with the predicted bulk densities and interface width."""
+    th = math.radians(min(max(pred["theta"], 5.0), 175.0))
+    area = case["area"] * nx * (ny - 2)
+    R = math.sqrt(area / (th - math.sin(th) * math.cos(th)))
+    yy, xx = np.mgrid[0:ny, 0:nx].astype(np.float64)
+    cx, cy = nx / 2.0 - 0.5, 0.5 - R * math.cos(th)   # centre below/above wall
+    d = R - np.hypot(xx - cx, yy - cy)   # row 0 (solid) is ignored
+    rl = pred["rho_l"] if pred["rho_l"] > pred["rho_v"] else case["rho_l"]
+    rv = max(pred["rho_v"], 1e-6)
+    W = min(max(pred["width"], 1.0), 12.0)
+    return inputs.tanh_profile(d, rl, rv, W)
+
+
+def run_batch(cases, fields, nx, ny, max_steps, check_every=200, tol=1e-6,
+              precision="f32", stream=None):
+    """Run every case from its field until max |rho change| over
+    check_every steps stays below tol * rho_l, or max_steps.  Returns the
+    per-case convergence step (max_steps if never), the final fields, the
+    device milliseconds until the last case converged, and the steps run."""
+    import torch
+    specs = [_spec(c, nx, ny) for c in cases]
+    conv = np.full(len(cases), max_steps, dtype=np.int64)
+    done = np.zeros(len(cases), dtype=bool)
+    steps = 0
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    with Batch(specs, precision=precision,
+               stream=stream.cuda_stream if stream else None) as b:
+        for k, f in enumerate(fields):
+            b.init(k, f)
+        for k in range(len(cases)):
+            b.reduce(k)
+        torch.cuda.synchronize()
+        ev0.record(stream if stream else torch.cuda.current_stream())
+        while steps < max_steps and not done.all():
+            b.step(check_every)
+            steps += check_every
+            for k in range(len(cases)):
+                if done[k]:
+                    continue
+                try:
+                    d = b.reduce(k)[3]
+                except Exception:
+                    done[k] = True            # non-finite: never converges
+                    continue
+                if d < tol * cases[k]["rho_l"]:
+                    done[k] = True
+                    conv[k] = steps
+        ev1.record(stream if stream else torch.cuda.current_stream())
+        torch.cuda.synchronize()
+        ms = ev0.elapsed_time(ev1)
+        final = [b.moments(k)["rho"] for k in range(len(cases))]
+    return conv, final, ms, steps
+
+
+def build_dataset(n, nx, ny, steps, seed, stream=None):
+    """Converged runs of n random cases from the cold start: features and
+    targets of the finite ones with a measurable angle."""
+    cases = sample_cases(n, seed)
+    fields = [cold_field(c, nx, ny) for c in cases]
+    _, final, _, _ = run_batch(cases, fields, nx, ny, steps, check_every=steps,
+                               tol=0.0, stream=stream)
+    keep, meas = [], []
+    for c, rho in zip(cases, final):
+        if not np.isfinite(rho).all():
+            continue
+        m = obs.measure(rho)
+        if all(np.isfinite(v) for v in m.values()) and m["theta"] < 179.0:
+            keep.append(c)
+            meas.append(m)
+    return keep, features(keep), targets(keep, meas)
+
+
+class Model:
+    """The trained network with its input / output standardisation."""
+
+    def __init__(self, X, Y, iters=3000, lr=2e-3, seed=0):
+        import torch
+        from .mlp import Mlp
+        self.xm, self.xs = X.mean(0), X.std(0) + 1e-6
+        self.ym, self.ys = Y.mean(0), Y.std(0) + 1e-6
+        Xd = torch.tensor((X - self.xm) / self.xs, device="cuda")
+        Yd = torch.tensor((Y - self.ym) / self.ys, device="cuda")
+        self.net = Mlp(seed=seed)
+        self.loss = self.net.train(Xd, Yd, iters, lr)
+
+    def predict(self, cases):
+        import torch
+        X = (features(cases) - self.xm) / self.xs
+        Y = self.net.predict(torch.tensor(X, device="cuda"), NTARG).cpu().numpy()
+        Y = Y * self.ys + self.ym
+        return [untarget(c, y) for c, y in zip(cases, Y)]
+
+    def close(self):
+        self.net.close()
+
+
+def compare(model, cases, nx, ny, max_steps, check_every=200, tol=1e-6,
+            stream=None):
+    """Cold and warm starts of the same cases run to convergence: step
+    counts, device time to the last converged case, and, over the cases
+    both starts converged on, the warm start's observable errors against
+    the cold start's result."""
+    preds = model.predict(cases)
+    cold = run_batch(cases, [cold_field(c, nx, ny) for c in cases], nx, ny,
+                     max_steps, check_every, tol, stream=stream)
+    warm = run_batch(cases, [warm_field(c, p, nx, ny) for c, p in
+                             zip(cases, preds)], nx, ny, max_steps,
+                     check_every, tol, stream=stream)
+    both = (cold[0] < max_steps) & (warm[0] < max_steps)
+    err = {"rho_l": [], "rho_v": [], "theta": []}
+    for k, (rc, rw) in enumerate(zip(cold[1], warm[1])):
+        if not both[k]:
+            continue
+        mc, mw = obs.measure(rc), obs.measure(rw)
+        err["rho_l"].append(abs(mw["rho_l"] - mc["rho_l"]) / mc["rho_l"])
+        err["rho_v"].append(abs(mw["rho_v"] - mc["rho_v"]) / mc["rho_v"])
+        err["theta"].append(abs(mw["theta"] - mc["theta"]))
+    pred_err = []
+    for p, rc in zip(preds, cold[1]):
+        if np.isfinite(rc).all():
+            t = obs.measure(rc)["theta"]
+            if np.isfinite(t):
+                pred_err.append(abs(p["theta"] - t))
+    return dict(
+        cases=len(cases), nx=nx, ny=ny, tol=tol, check_every=check_every,
+        max_steps=max_steps,
+        cold_steps_mean=float(cold[0].mean()), warm_steps_mean=float(warm[0].mean()),
+        both_converged=int(both.sum()),
+        cold_steps_median_both=float(np.median(cold[0][both])) if both.any() else None,
+        warm_steps_median_both=float(np.median(warm[0][both])) if both.any() else None,
+        step_ratio_median_both=float(np.median(warm[0][both] / cold[0][both]))
+        if both.any() else None,
+        cold_ms=cold[2], warm_ms=warm[2],
+        cold_converged=float((cold[0] < max_steps).mean()),
+        warm_converged=float((warm[0] < max_steps).mean()),
+        max_rel_err_rho_l=float(max(err["rho_l"], default=float("nan"))),
+        max_rel_err_rho_v=float(max(err["rho_v"], default=float("nan"))),
+        max_abs_err_theta_deg=float(max(err["theta"], default=float("nan"))),
+        mlp_theta_err_deg_median=float(np.median(pred_err)) if pred_err else None)

@@ -1,0 +1,50 @@
+"""Learned warm start of wall-droplet runs: the BF16 MLP, trained on
+converged batched runs of the method, predicts held-out cases' contact
+angle; runs started from its prediction converge in fewer steps than the
+plain half-disc start and reach the same observables (the cold start is
+the judge)."""
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def trained():
+    torch = pytest.importorskip("torch")
+    from paper_1611_00907_gb300 import warmstart as ws
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        cases, X, Y = ws.build_dataset(768, 128, 64, 6000, seed=1,
+                                       stream=stream)
+    n = len(cases)
+    assert n > 0.6 * 768
+    ntr = int(0.9 * n)
+    model = ws.Model(X[:ntr], Y[:ntr], iters=2500, lr=2e-3)
+    yield ws, model, cases[ntr:], Y[ntr:], stream
+    model.close()
+
+
+def test_holdout_angle_prediction(trained):
+    ws, model, held, Y, _ = trained
+    pred = model.predict(held)
+    err = np.abs(np.array([p["theta"] for p in pred]) - 180.0 * Y[:, 3])
+    assert np.median(err) < 2.0
+    assert np.percentile(err, 90) < 8.0
+    rl = np.array([p["rho_l"] for p in pred])
+    assert np.all(rl > np.array([p["rho_v"] for p in pred]))
+
+
+def test_warm_start_converges_faster_to_the_same_state(trained):
+    torch = pytest.importorskip("torch")
+    ws, model, _, _, stream = trained
+    cases = ws.sample_cases(32, seed=99)
+    with torch.cuda.stream(stream):
+        r = ws.compare(model, cases, 192, 96, 16000, check_every=200,
+                       tol=1e-5, stream=stream)
+    assert r["both_converged"] >= 8
+    assert r["step_ratio_median_both"] < 0.95
+    assert r["warm_converged"] >= r["cold_converged"] - 0.1
+    assert r["max_rel_err_rho_l"] < 5e-3
+    assert r["max_rel_err_rho_v"] < 3e-2
+    assert r["max_abs_err_theta_deg"] < 5.0
