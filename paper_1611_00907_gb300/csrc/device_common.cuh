@@ -375,7 +375,7 @@ template <class T, int W>
 __device__ __forceinline__ T lap9(const T *s, int c)
 {
     const T axial = s[c + 1] + s[c - 1] + s[c + W] + s[c - W];
-    const T diag = s[c + W + 1] + s[c + W - 1] + s[c - W + 1] + s[c - W - 1];
+    const T diag = (s[c + W + 1] + s[c + W - 1]) + (s[c - W + 1] + s[c - W - 1]);
     return (T(4) * axial + diag - T(20) * s[c]) * T(1.0 / 6.0);
 }
 template <class T, int W>

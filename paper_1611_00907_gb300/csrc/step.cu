@@ -49,7 +49,7 @@ void set_consts(Lattice &L)
 
 // Tile shapes with a compiled kernel (all precisions; same list in
 // step_impl.cuh).
-#define CPLBM_STEP_SHAPES(X) X(32, 16) X(32, 24) X(32, 32) X(64, 16)
+#define CPLBM_STEP_SHAPES(X) X(32, 16) X(32, 24) X(32, 32) X(64, 16) X(64, 32)
 
 bool step_shape_supported(int prec, int tx, int ty)
 {

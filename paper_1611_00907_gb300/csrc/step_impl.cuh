@@ -478,11 +478,12 @@ __device__ __forceinline__ void step_tile(const Lattice &L, int cur, int X0,
 // ---------------------------------------------------------------------------
 // Interior tiles with TMA.  One thread issues nine tensor copies per tile:
 // the density halo (a (TX + 8) x (TY + 4) box from x = X0 - 4, the nearest
-// 16-byte-aligned column) and, per direction, the (TX + 8) x TY box of the
-// plane and rows that direction is read from in this step's AA order.  They
-// complete on one mbarrier; the partial sums of the halo's edge nodes come by
-// per-element cp.async.  Staged rows have pitch RP = TX + 8 with the tile's
-// column 0 at offset 4.
+// 16-byte-aligned column; staged rows of pitch RP = TX + 8, the tile's
+// column 0 at offset 4) and, per direction, the (TX + 4) x TY box of the
+// plane and rows that direction is read from in this step's AA order
+// (pin_x0 / pin_col below).  They complete on one mbarrier; the partial sums
+// of the halo's edge nodes come by per-element cp.async into a buffer that
+// the warps' exchange slots reuse once the sums are added.
 //
 // Lanes map to x (TX = 32) and each warp owns PER consecutive rows, walked
 // bottom to top.  Stencil windows roll with the rows, and the density
@@ -496,19 +497,54 @@ __device__ __forceinline__ void step_tile(const Lattice &L, int cur, int X0,
 // and lane 31 carry the same sums for the tile's left and right ring
 // columns; the first and last warps write the bottom and top ring rows.
 // ---------------------------------------------------------------------------
+// Population staging of the TMA paths: per direction a (TX + 4) x TY box
+// from x = X0 + pin_x0(i) (X0 - 4 for the directions an odd step reads from
+// x - 1, X0 otherwise: both 16-byte aligned), so that tile column lx of
+// direction i sits at staged column lx + pin_col(i).
+template <int PARITY>
+__device__ __forceinline__ constexpr int pin_x0(int i)
+{
+    return (PARITY == 1 && ex(i) == 1) ? -4 : 0;
+}
+template <int PARITY>
+__device__ __forceinline__ constexpr int pin_col(int i)
+{
+    return PARITY == 0 ? 0 : (ex(i) == 1 ? 3 : (ex(i) == -1 ? 1 : 0));
+}
+
+// All threads: wait (bounded) for barrier k of the tile's copies (0: the
+// density halo, 1: the populations), then a block barrier.  false when any
+// thread gave up: the flag is raised, every copy of the tile is given
+// another bounded wait so none is left writing into this block's shared
+// memory, and the caller leaves the tile untouched.
+__device__ __forceinline__ bool tma_landed(unsigned long long *bar, int k, int *err)
+{
+    const bool ok = mbar_wait(&bar[k], 0, 2000000000LL);  // ~1 s at 2 GHz
+    if (!__syncthreads_or(!ok)) return true;
+    if (threadIdx.x == 0 && err) atomicOr(err, ERR_WAIT_TIMEOUT);
+    mbar_wait(&bar[0], 0, 2000000000LL);
+    mbar_wait(&bar[1], 0, 2000000000LL);
+    __syncthreads();
+    return false;
+}
+
 template <class real, int TX, int TY>
 struct TmaSmem {
-    static constexpr int RP = TX + 8;
-    static constexpr int PLANE = TY * RP;
+    static constexpr int RP = TX + 8;  // density rows
+    static constexpr int PP = TX + 4;  // population rows
+    static constexpr int PLANE = TY * PP;
     static constexpr int NRHO = (TY + 4) * RP;
     static constexpr int MP = TX + 2, MH = TY + 2;
     static constexpr int NRING = StepSmem<real, TX, TY>::NRING;
     static constexpr int NMU = MP * MH;
     static constexpr int NXCH = 2 * (STEP_THREADS / 32) * (TX + 2);
+    static constexpr int NSHARE = NRING > NXCH ? NRING : NXCH;  // ring, then exchange
     static constexpr size_t bar_offset =
-        (sizeof(real) * (8 * PLANE + NRHO + NRING + NMU + NXCH) + 15) / 16 * 16;
+        (sizeof(real) * (8 * PLANE + NRHO + NSHARE + NMU) + 15) / 16 * 16;
     static constexpr size_t bytes = bar_offset + 16;
-    static constexpr unsigned tx_bytes = sizeof(real) * (8 * PLANE + NRHO);
+    static constexpr unsigned tx_rho = sizeof(real) * NRHO;
+    static constexpr unsigned tx_pops = sizeof(real) * 8 * PLANE;
+    static_assert((PLANE * sizeof(real)) % 128 == 0, "TMA destinations");
 };
 
 // Gradient of the isotropic stencil from a 3 x 3 window w[row][col] (row 0
@@ -525,7 +561,7 @@ template <class T>
 __device__ __forceinline__ T lap_w(const T (&w)[3][3])
 {
     const T axial = w[1][2] + w[1][0] + w[2][1] + w[0][1];
-    const T diag = w[2][2] + w[2][0] + w[0][2] + w[0][0];
+    const T diag = (w[2][2] + w[2][0]) + (w[0][2] + w[0][0]);
     return (T(4) * axial + diag - T(20) * w[1][1]) * T(1.0 / 6.0);
 }
 
@@ -542,14 +578,14 @@ __device__ __forceinline__ void step_tile_tma(const Lattice &L, int cur, int X0,
     static_assert(sizeof(pop_t) == sizeof(real), "populations staged as stored");
     constexpr int NW = NT / 32, PER = TY / NW;
     static_assert(PER * NW == TY && PER >= 2, "warps own whole row blocks");
-    constexpr int RP = TS::RP, PLANE = TS::PLANE, MP = TS::MP, MH = TS::MH;
+    constexpr int RP = TS::RP, PP = TS::PP, PLANE = TS::PLANE, MP = TS::MP, MH = TS::MH;
     constexpr int WR = TX + 4, HR = TY + 4;  // halo geometry of the ring staging
     constexpr int XW = TX + 2;               // exchange slots per warp
-    real *s_pin = reinterpret_cast<real *>(smem_raw);  // [8][TY][RP]
+    real *s_pin = reinterpret_cast<real *>(smem_raw);  // [8][TY][PP]
     real *s_rho = s_pin + 8 * PLANE;                     // [TY + 4][RP]
     real *s_ring = s_rho + TS::NRHO;
-    real *s_mu = s_ring + TS::NRING;                     // [MH][MP]
-    real *s_up = s_mu + TS::NMU;                         // [NW][XW]
+    real *s_mu = s_ring + TS::NSHARE;                    // [MH][MP]
+    real *s_up = s_ring;                                 // [NW][XW], after step 2
     real *s_down = s_up + NW * XW;                       // [NW][XW]
     unsigned long long *bar =
         reinterpret_cast<unsigned long long *>(smem_raw + TS::bar_offset);
@@ -558,16 +594,21 @@ __device__ __forceinline__ void step_tile_tma(const Lattice &L, int cur, int X0,
 
     // 1. Loads.  Density halo and populations by TMA (thread 0), partial
     //    sums by cp.async (all threads).
-    if (threadIdx.x == 0) mbar_init(bar, 1);
+    if (threadIdx.x == 0) {
+        mbar_init(&bar[0], 1);
+        mbar_init(&bar[1], 1);
+    }
     __syncthreads();
     if (threadIdx.x == 0) {
-        mbar_expect_tx(bar, TS::tx_bytes);
-        tma_load_2d(s_rho, &maps.rho[cur], X0 - 4, Y0 - 2, bar);
+        mbar_expect_tx(&bar[0], TS::tx_rho);
+        tma_load_2d(s_rho, &maps.rho[cur], X0 - 4, Y0 - 2, &bar[0]);
+        mbar_expect_tx(&bar[1], TS::tx_pops);
 #pragma unroll
         for (int i = 1; i < 9; ++i) {
             const int plane = PARITY == 0 ? i - 1 : opp(i) - 1;
             const int y0 = PARITY == 0 ? Y0 : Y0 - ey(i);
-            tma_load_3d(s_pin + (i - 1) * PLANE, &maps.pops, X0 - 4, y0, plane, bar);
+            tma_load_3d(s_pin + (i - 1) * PLANE, &maps.pops, X0 + pin_x0<PARITY>(i),
+                        y0, plane, &bar[1]);
         }
     }
     {
@@ -600,16 +641,7 @@ __device__ __forceinline__ void step_tile_tma(const Lattice &L, int cur, int X0,
         cp_async_commit();
     }
     cp_async_wait_all();
-    const bool ok = mbar_wait(bar, 0, 2000000000LL);  // ~1 s at 2 GHz
-    if (__syncthreads_or(!ok)) {
-        // the copies did not land in time: flag it, give the copies another
-        // bounded wait so none is left writing into this block's memory,
-        // and leave the tile untouched
-        if (threadIdx.x == 0 && L.err) atomicOr(L.err, ERR_WAIT_TIMEOUT);
-        mbar_wait(bar, 0, 2000000000LL);
-        __syncthreads();
-        return;
-    }
+    if (!tma_landed(bar, 0, L.err)) return;
 
     // 2. Partial sums into the halo's tile-edge nodes (order of
     //    load_rho_stored).  Halo (lx, ly) of the (TX + 4)-wide convention is
@@ -669,7 +701,9 @@ __device__ __forceinline__ void step_tile_tma(const Lattice &L, int cur, int X0,
                 mu_bulk(eos, s_rho[c] + ref) - kappa * lap9<real, RP>(s_rho, c);
         }
     }
-    __syncthreads();
+    // the populations were in flight during steps 2 and 3; the barrier also
+    // publishes s_mu
+    if (!tma_landed(bar, 1, L.err)) return;
 
     // 4. Force, collision, in-place streaming and the register hand-over for
     //    the thread's PER nodes at rows ly0 .. ly0 + PER - 1, column lx.
@@ -715,8 +749,7 @@ __device__ __forceinline__ void step_tile_tma(const Lattice &L, int cur, int X0,
         real f[9];
 #pragma unroll
         for (int i = 1; i < 9; ++i)
-            f[i] = s_pin[(i - 1) * PLANE + ly * RP + lx + 4 -
-                         (PARITY == 0 ? 0 : ex(i))];
+            f[i] = s_pin[(i - 1) * PLANE + ly * PP + lx + pin_col<PARITY>(i)];
         const real drho = wr[1][1];
         const real rho = drho + rho_ref;
         real gmx, gmy, grx, gry;
@@ -808,6 +841,459 @@ __device__ __forceinline__ void step_tile_tma(const Lattice &L, int cur, int X0,
     }
 }
 
+// ---------------------------------------------------------------------------
+// FP32 interior tiles with TMA, two nodes per lane.  Tiles are TX = 64 wide:
+// lane l owns columns 2l and 2l + 1 of each of its warp's PER rows, and the
+// pair's arithmetic runs on packed FP32 pairs (the two-wide FFMA / FADD /
+// FMUL of sm_100 and later), so one instruction serves both nodes.  Loads,
+// partial sums and the density hand-over are those of step_tile_tma; even
+// steps also move the pair's populations as aligned 64-bit words (odd steps
+// read and write the x-shifted directions one node at a time).
+//
+// Stencils on a pair.  For a field v and one row of the pair's window, with
+// (v0, v1) the pair and wl = v(x0 - 1), wr = v(x1 + 1):
+//   C = (v0, v1),  H = W + E = (v1 + wl, wr + v0),  D = E - W = (v1 - wl, wr - v0),
+// and with rows u (above), m and d (below):
+//   grad_x = (4 D_m + D_u + D_d) / 12,   grad_y = (4 (C_u - C_d) + H_u - H_d) / 12,
+//   lap    = (4 (H_m + C_u + C_d) + (H_u + H_d) - 20 C_m) / 6,
+// which are grad_w / lap_w term by term.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ float2 p2(float a) { return make_float2(a, a); }
+__device__ __forceinline__ float2 padd(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 pmul(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 pfma(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+// a - b as b * (-1) + a: the exact difference rounded once, as a subtraction
+__device__ __forceinline__ float2 psub(float2 a, float2 b)
+{
+    return __ffma2_rn(b, make_float2(-1.0f, -1.0f), a);
+}
+__device__ __forceinline__ float2 prcp(float2 v)
+{
+    return make_float2(__fdividef(1.0f, v.x), __fdividef(1.0f, v.y));
+}
+__device__ __forceinline__ float2 pdiv(float2 a, float2 b)
+{
+    return make_float2(__fdividef(a.x, b.x), __fdividef(a.y, b.y));
+}
+__device__ __forceinline__ float2 plog(float2 v)
+{
+    return make_float2(__logf(v.x), __logf(v.y));
+}
+
+// One window row of a field around the pair at s + i (8-byte aligned).
+struct Row2 {
+    float2 c, h, d;
+};
+__device__ __forceinline__ Row2 row2(const float *s, int i)
+{
+    const float2 c = *reinterpret_cast<const float2 *>(s + i);
+    const float wl = s[i - 1], wr = s[i + 2];
+    return {c, make_float2(c.y + wl, wr + c.x), make_float2(c.y - wl, wr - c.x)};
+}
+__device__ __forceinline__ float2 lap2(const Row2 &u, const Row2 &m, const Row2 &d)
+{
+    const float2 axial = padd(padd(m.h, u.c), d.c);
+    const float2 diag = padd(u.h, d.h);
+    return pmul(pfma(p2(-20.0f), m.c, pfma(p2(4.0f), axial, diag)), p2(1.0f / 6.0f));
+}
+__device__ __forceinline__ void grad2(const Row2 &u, const Row2 &m, const Row2 &d,
+                                      float2 &gx, float2 &gy)
+{
+    const float2 c = p2(1.0f / 12.0f), four = p2(4.0f);
+    gx = pmul(padd(pfma(four, m.d, u.d), d.d), c);
+    gy = pmul(psub(pfma(four, psub(u.c, d.c), u.h), d.h), c);
+}
+
+// mu_bulk on a pair of densities.
+__device__ __forceinline__ float2 mu_bulk2(const EosT<float> &e, float2 rho)
+{
+    const float2 one = p2(1.0f), m2a = p2(-2.0f * e.a);
+    switch (e.kind) {
+    case EOS_VDW: {
+        const float2 iq = prcp(psub(one, pmul(p2(e.b), rho)));
+        return pfma(m2a, rho, pmul(p2(e.RT), padd(plog(pmul(rho, iq)), iq)));
+    }
+    case EOS_CS: {
+        const float2 h = pmul(p2(e.quarter_b), rho);
+        const float2 iq = prcp(psub(one, h));
+        const float2 iq3 = pmul(pmul(iq, iq), iq);
+        const float2 s = padd(padd(pmul(psub(p2(3.0f), h), iq3), plog(rho)), one);
+        return pfma(m2a, rho, pmul(p2(e.RT), s));
+    }
+    case EOS_PR: {
+        const float2 br = pmul(p2(e.b), rho);
+        const float2 iq = prcp(psub(one, br));
+        const float2 t1 = pmul(p2(e.RT), plog(pmul(rho, iq)));
+        const float2 t2 = pmul(
+            p2(e.pr_c), plog(pdiv(padd(p2(e.pr_s2m1), br), psub(p2(e.pr_s2p1), br))));
+        const float2 den = psub(pfma(p2(2.0f), br, one), pmul(br, br));
+        return psub(pfma(p2(e.RT), iq, psub(t1, t2)), pdiv(pmul(p2(e.aalpha), rho), den));
+    }
+    default: {  // EOS_RKS
+        const float2 br = pmul(p2(e.b), rho);
+        const float2 iq = prcp(psub(one, br));
+        const float2 t1 = pmul(p2(e.RT), padd(plog(pmul(rho, iq)), iq));
+        const float2 t2 = pmul(p2(e.rks_c), plog(padd(one, br)));
+        return psub(psub(t1, t2), pdiv(pmul(p2(e.aalpha), rho), padd(one, br)));
+    }
+    }
+}
+
+// collide() on a pair of nodes.
+__device__ __forceinline__ void collide2(const float2 *f, float2 drho, float2 rho,
+                                         float2 Fx, float2 Fy, float2 tau,
+                                         float2 omega, float2 *fp)
+{
+    const float2 d57 = psub(f[5], f[7]);
+    const float2 jx = padd(padd(psub(f[1], f[3]), d57), psub(f[8], f[6]));
+    const float2 jy = padd(padd(psub(f[2], f[4]), d57), psub(f[6], f[8]));
+    const float2 inv_rho = prcp(rho);
+    const float2 ux = pmul(pfma(tau, Fx, jx), inv_rho);
+    const float2 uy = pmul(pfma(tau, Fy, jy), inv_rho);
+    const float2 nusq = pmul(p2(-1.5f), pfma(ux, ux, pmul(uy, uy)));  // -1.5 u^2
+    const float2 c45 = p2(4.5f), c3 = p2(3.0f);
+    {
+        const float2 w1 = p2(1.0f / 9.0f);
+        const float2 ex2 = pfma(pmul(c45, ux), ux, nusq);
+        const float2 ey2 = pfma(pmul(c45, uy), uy, nusq);
+        const float2 ax = pmul(w1, pfma(rho, ex2, drho));
+        const float2 ay = pmul(w1, pfma(rho, ey2, drho));
+        const float2 r3 = pmul(pmul(w1, rho), c3);
+        const float2 bx = pmul(r3, ux), by = pmul(r3, uy);
+        fp[1] = pfma(omega, psub(padd(ax, bx), f[1]), f[1]);
+        fp[3] = pfma(omega, psub(psub(ax, bx), f[3]), f[3]);
+        fp[2] = pfma(omega, psub(padd(ay, by), f[2]), f[2]);
+        fp[4] = pfma(omega, psub(psub(ay, by), f[4]), f[4]);
+    }
+    {
+        const float2 w5 = p2(1.0f / 36.0f);
+        const float2 sp = padd(ux, uy), sm = psub(ux, uy);
+        const float2 ep = pfma(pmul(c45, sp), sp, nusq);
+        const float2 em = pfma(pmul(c45, sm), sm, nusq);
+        const float2 a5 = pmul(w5, pfma(rho, ep, drho));
+        const float2 a8 = pmul(w5, pfma(rho, em, drho));
+        const float2 r3 = pmul(pmul(w5, rho), c3);
+        const float2 b5 = pmul(r3, sp), b8 = pmul(r3, sm);
+        fp[5] = pfma(omega, psub(padd(a5, b5), f[5]), f[5]);
+        fp[7] = pfma(omega, psub(psub(a5, b5), f[7]), f[7]);
+        fp[8] = pfma(omega, psub(padd(a8, b8), f[8]), f[8]);
+        fp[6] = pfma(omega, psub(psub(a8, b8), f[6]), f[6]);
+    }
+    fp[0] = psub(drho, padd(padd(padd(fp[1], fp[2]), padd(fp[3], fp[4])),
+                            padd(padd(fp[5], fp[6]), padd(fp[7], fp[8]))));
+}
+
+template <int TX, int TY, int NT>
+struct TmaPairSmem {
+    static constexpr int NW = NT / 32;
+    static constexpr int RP = TX + 8;              // density rows from x = X0 - 4
+    static constexpr int PP = TX + 4;              // population rows (pin_x0)
+    static constexpr int PLANE = TY * PP;
+    static constexpr int NRHO = (TY + 4) * RP;
+    static constexpr int MP = TX + 4, MH = TY + 2;  // mu of halo column a at a + 1
+    static constexpr int NRING = 4 * (TY + 4) + 4 * (TX + 4) + 16;
+    static constexpr int NMU = MP * MH;
+    static constexpr int XW = TX + 2;              // exchange slots per warp
+    static constexpr int NXCH = 2 * NW * XW;
+    static constexpr int NSHARE = NRING > NXCH ? NRING : NXCH;  // ring, then exchange
+    static constexpr size_t bar_offset =
+        (sizeof(float) * (8 * PLANE + NRHO + NSHARE + NMU) + 15) / 16 * 16;
+    static constexpr size_t bytes = bar_offset + 16;
+    static constexpr unsigned tx_rho = sizeof(float) * NRHO;
+    static constexpr unsigned tx_pops = sizeof(float) * 8 * PLANE;
+    static_assert((PLANE * sizeof(float)) % 128 == 0, "TMA destinations");
+    static_assert(NRHO % 2 == 0 && NSHARE % 2 == 0 && NMU % 2 == 0 && XW % 2 == 0 &&
+                      PP % 2 == 0,
+                  "pair-aligned sub-arrays");
+};
+
+template <class S, int TX, int TY, int NT, int PARITY>
+__device__ __forceinline__ void step_tile_tma_pair(const Lattice &L, int cur, int X0,
+                                                   int Y0, unsigned char *smem_raw,
+                                                   const TmaMaps &maps)
+{
+    using rho_t = typename S::rho_t;
+    using TS = TmaPairSmem<TX, TY, NT>;
+    static_assert(TX == 64, "lanes map to x pairs");
+    static_assert(sizeof(typename S::pop_t) == 4 && sizeof(rho_t) == 4, "FP32 storage");
+    constexpr int NW = TS::NW, PER = TY / NW;
+    static_assert(PER * NW == TY && PER >= 2, "warps own whole row blocks");
+    constexpr int RP = TS::RP, PP = TS::PP, PLANE = TS::PLANE, MP = TS::MP, MH = TS::MH;
+    constexpr int XW = TS::XW;
+    constexpr int WR = TX + 4, HR = TY + 4;  // halo geometry of the ring staging
+    float *s_pin = reinterpret_cast<float *>(smem_raw);  // [8][TY][PP]
+    float *s_rho = s_pin + 8 * PLANE;                     // [TY + 4][RP]
+    float *s_ring = s_rho + TS::NRHO;
+    float *s_mu = s_ring + TS::NSHARE;                    // [MH][MP]
+    float *s_up = s_ring;                                 // [NW][XW], after step 2
+    float *s_down = s_up + NW * XW;                       // [NW][XW]
+    unsigned long long *bar =
+        reinterpret_cast<unsigned long long *>(smem_raw + TS::bar_offset);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int nxt = cur ^ 1;
+
+    // 1. Loads: density halo and populations by TMA (thread 0), partial sums
+    //    by cp.async (all threads).
+    if (threadIdx.x == 0) {
+        mbar_init(&bar[0], 1);
+        mbar_init(&bar[1], 1);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        mbar_expect_tx(&bar[0], TS::tx_rho);
+        tma_load_2d(s_rho, &maps.rho[cur], X0 - 4, Y0 - 2, &bar[0]);
+        mbar_expect_tx(&bar[1], TS::tx_pops);
+#pragma unroll
+        for (int i = 1; i < 9; ++i) {
+            const int plane = PARITY == 0 ? i - 1 : opp(i) - 1;
+            const int y0 = PARITY == 0 ? Y0 : Y0 - ey(i);
+            tma_load_3d(s_pin + (i - 1) * PLANE, &maps.pops, X0 + pin_x0<PARITY>(i),
+                        y0, plane, &bar[1]);
+        }
+    }
+    {
+        rho_t *const *ring = (rho_t *const *)L.ring[cur];
+        for (int p = threadIdx.x; p < TS::NRING; p += NT) {
+            int c, lx, ly;
+            if (p < 4 * HR) {
+                const int ci = p / HR;
+                ly = p % HR;
+                lx = edge_col<TX>(ci);
+                c = col_is_left(ci) ? R_L : R_R;
+            } else if (p < 4 * HR + 4 * WR) {
+                const int q = p - 4 * HR, ri = q / WR;
+                lx = q % WR;
+                ly = edge_col<TY>(ri);
+                c = row_is_below(ri) ? R_B : R_T;
+            } else {
+                const int q = p - 4 * HR - 4 * WR, ci = q / 4, ri = q % 4;
+                lx = edge_col<TX>(ci);
+                ly = edge_col<TY>(ri);
+                c = row_is_below(ri) ? (col_is_left(ci) ? R_BL : R_BR)
+                                     : (col_is_left(ci) ? R_TL : R_TR);
+            }
+            const int x = X0 + lx - 2, r = Y0 + ly - 2;
+            const long long idx =
+                (c == R_L || c == R_R) ? cidx(L, r, x) : fidx(L, r, x);
+            cp_async<sizeof(rho_t)>(&s_ring[p], ring[c] + idx);
+        }
+        cp_async_commit();
+    }
+    cp_async_wait_all();
+    if (!tma_landed(bar, 0, L.err)) return;
+
+    // 2. Partial sums into the halo's tile-edge nodes (order of
+    //    load_rho_stored); halo (lx, ly) is staged at row ly, column lx + 2.
+    for (int q = threadIdx.x; q < 4 * HR + 4 * WR; q += NT) {
+        int lx, ly;
+        if (q < 4 * HR) {
+            lx = edge_col<TX>(q / HR);
+            ly = q % HR;
+        } else {
+            const int t = q - 4 * HR;
+            lx = t % WR;
+            ly = edge_col<TY>(t / WR);
+            if (col_index<TX>(lx) >= 0) continue;
+        }
+        const int ci = col_index<TX>(lx), ri = col_index<TY>(ly);
+        float v = s_rho[ly * RP + lx + 2];
+        if (ci >= 0) v += s_ring[ci * HR + ly];
+        if (ri >= 0) {
+            v += s_ring[4 * HR + ri * WR + lx];
+            if (ci >= 0) v += s_ring[4 * HR + 4 * WR + ci * 4 + ri];
+        }
+        s_rho[ly * RP + lx + 2] = v;
+    }
+    __syncthreads();
+
+    // 3. mu at halo column a (x = X0 - 1 + a) and row b (r = Y0 - 1 + b),
+    //    stored at s_mu[b][a + 1]; its density is staged at (b + 1, a + 3).
+    //    Lane l takes the pair a = 2l + 1, 2l + 2 down its warp's rows with a
+    //    rolling window; columns 0 and TX + 1 one node at a time.
+    const Consts<float> &K = consts<float>(L);
+    const float ref = S::offset ? K.rho_ref : 0.0f;
+    const float2 ref2 = p2(ref);
+    {
+        const EosT<float> &eos = K.eos;
+        const float2 mkappa = p2(-K.kappa);
+        const int b0 = (warp * MH) / NW, b1 = ((warp + 1) * MH) / NW;
+        const int c0 = 2 * lane + 4;
+        Row2 d = row2(s_rho, b0 * RP + c0), m = row2(s_rho, (b0 + 1) * RP + c0);
+        for (int b = b0; b < b1; ++b) {
+            const Row2 u = row2(s_rho, (b + 2) * RP + c0);
+            const float2 rho = S::offset ? padd(m.c, ref2) : m.c;
+            *reinterpret_cast<float2 *>(s_mu + b * MP + 2 * lane + 2) =
+                pfma(mkappa, lap2(u, m, d), mu_bulk2(eos, rho));
+            d = m;
+            m = u;
+        }
+        for (int t = threadIdx.x; t < 2 * MH; t += NT) {
+            const int ae = (t & 1) ? TX + 1 : 0, b = t >> 1;
+            const int c = (b + 1) * RP + ae + 3;
+            s_mu[b * MP + ae + 1] =
+                mu_bulk(eos, s_rho[c] + ref) - K.kappa * lap9<float, RP>(s_rho, c);
+        }
+    }
+    // the populations were in flight during steps 2 and 3; the barrier also
+    // publishes s_mu
+    if (!tma_landed(bar, 1, L.err)) return;
+
+    // 4. Force, collision, in-place streaming and the register hand-over for
+    //    the pair at columns x0, x0 + 1 of rows ly0 .. ly0 + PER - 1.
+    const int x0 = 2 * lane, ly0 = warp * PER;
+    const float2 tau = p2(K.tau), omega = p2(K.omega), third = p2(1.0f / 3.0f);
+    float *A = (float *)L.pops;
+    rho_t *Rn = (rho_t *)L.rho[nxt];
+    rho_t *const *ring = (rho_t *const *)L.ring[nxt];
+    int woff[9];  // 32-bit: the TMA maps exist only when 8 planes fit
+#pragma unroll
+    for (int i = 1; i < 9; ++i)
+        woff[i] = PARITY == 0 ? (opp(i) - 1) * (int)L.plane
+                              : (i - 1) * (int)L.plane + ey(i) * L.pitch + ex(i);
+    const bool has_l = lane > 0, has_r = lane < 31;
+    // windows: density of tile row ly at staged row ly + 2, column x0 + 4;
+    // mu of tile row ly at s_mu row ly + 1, column x0 + 2
+    Row2 rd = row2(s_rho, (ly0 + 1) * RP + x0 + 4), rm = row2(s_rho, (ly0 + 2) * RP + x0 + 4);
+    Row2 md = row2(s_mu, ly0 * MP + x0 + 2), mm = row2(s_mu, (ly0 + 1) * MP + x0 + 2);
+    float2 pend = p2(0.0f), up_prev = p2(0.0f), first = p2(0.0f);
+    float pend_c = 0.0f, up_prev_c = 0.0f, first_c = 0.0f;
+    const int slot_c = TX + (lane == 31);        // exchange slot of a column
+    const int xc = lane == 0 ? X0 - 1 : X0 + TX;  // ring column of the lane
+    const int cls_c = lane == 0 ? R_R : R_L;
+    const bool col_lane = lane == 0 || lane == 31;
+    float *Arow = A + (long long)(Y0 + ly0) * L.pitch + X0 + x0;
+#pragma unroll
+    for (int k = 0; k < PER; ++k) {
+        const int ly = ly0 + k;
+        const Row2 ru = row2(s_rho, (ly + 3) * RP + x0 + 4);
+        const Row2 mu = row2(s_mu, (ly + 2) * MP + x0 + 2);
+        float2 f[9];
+#pragma unroll
+        for (int i = 1; i < 9; ++i) {
+            const float *src = s_pin + (i - 1) * PLANE + ly * PP + x0 + pin_col<PARITY>(i);
+            if (PARITY == 0 || ex(i) == 0)
+                f[i] = *reinterpret_cast<const float2 *>(src);
+            else
+                f[i] = make_float2(src[0], src[1]);
+        }
+        const float2 drho = rm.c;
+        const float2 rho = S::offset ? padd(drho, ref2) : drho;
+        float2 grx, gry, gmx, gmy;
+        grad2(ru, rm, rd, grx, gry);
+        grad2(mu, mm, md, gmx, gmy);
+        const float2 Fx = psub(pmul(grx, third), pmul(rho, gmx));
+        const float2 Fy = psub(pmul(gry, third), pmul(rho, gmy));
+        float2 fp[9];
+        collide2(f, drho, rho, Fx, Fy, tau, omega, fp);
+#pragma unroll
+        for (int i = 1; i < 9; ++i) {
+            float *dst = Arow + woff[i];
+            if (PARITY == 0 || ex(i) == 0) {
+                *reinterpret_cast<float2 *>(dst) = fp[i];
+            } else {
+                dst[0] = fp[i].x;
+                dst[1] = fp[i].y;
+            }
+        }
+        Arow += L.pitch;
+
+        // lane-neighbour parts of the hand-over
+        const float f1l = __shfl_up_sync(0xffffffffu, fp[1].y, 1);
+        const float f5l = __shfl_up_sync(0xffffffffu, fp[5].y, 1);
+        const float f8l = __shfl_up_sync(0xffffffffu, fp[8].y, 1);
+        const float f3r = __shfl_down_sync(0xffffffffu, fp[3].x, 1);
+        const float f6r = __shfl_down_sync(0xffffffffu, fp[6].x, 1);
+        const float f7r = __shfl_down_sync(0xffffffffu, fp[7].x, 1);
+        const float2 same = make_float2((fp[0].x + (has_l ? f1l : 0.0f)) + fp[3].y,
+                                        (fp[0].y + fp[1].x) + (has_r ? f3r : 0.0f));
+        const float2 up = make_float2((fp[2].x + (has_l ? f5l : 0.0f)) + fp[6].y,
+                                      (fp[2].y + fp[5].x) + (has_r ? f6r : 0.0f));
+        const float2 down = make_float2((fp[4].x + (has_l ? f8l : 0.0f)) + fp[7].y,
+                                        (fp[4].y + fp[8].x) + (has_r ? f7r : 0.0f));
+        // ring columns: lane 0 feeds x = X0 - 1 (f*_3; f*_6 up; f*_7 down) from
+        // its first node, lane 31 feeds x = X0 + TX (f*_1; f*_5 up; f*_8 down)
+        // from its second
+        const float same_c = lane == 0 ? fp[3].x : fp[1].y;
+        const float up_c = lane == 0 ? fp[6].x : fp[5].y;
+        const float down_c = lane == 0 ? fp[7].x : fp[8].y;
+        if (k == 0) {
+            *reinterpret_cast<float2 *>(s_down + warp * XW + x0) = down;
+            if (col_lane) s_down[warp * XW + slot_c] = down_c;
+            pend = same;
+            pend_c = same_c;
+        } else {
+            const float2 done = padd(pend, down);  // row ly - 1
+            const float done_c = pend_c + down_c;
+            if (k == 1) {
+                first = done;
+                first_c = done_c;
+            } else {
+                *reinterpret_cast<float2 *>(Rn + (long long)(Y0 + ly - 1) * L.pitch +
+                                            X0 + x0) = done;
+                if (col_lane) ring[cls_c][cidx(L, Y0 + ly - 1, xc)] = done_c;
+            }
+            pend = padd(same, up_prev);
+            pend_c = same_c + up_prev_c;
+        }
+        up_prev = up;
+        up_prev_c = up_c;
+        rd = rm;
+        rm = ru;
+        md = mm;
+        mm = mu;
+    }
+    *reinterpret_cast<float2 *>(s_up + warp * XW + x0) = up_prev;
+    if (col_lane) s_up[warp * XW + slot_c] = up_prev_c;
+    __syncthreads();
+    {
+        float2 top = pend;
+        float top_c = pend_c;
+        if (warp + 1 < NW) {
+            top = padd(top, *reinterpret_cast<const float2 *>(s_down + (warp + 1) * XW + x0));
+            top_c += s_down[(warp + 1) * XW + slot_c];
+        }
+        *reinterpret_cast<float2 *>(Rn + (long long)(Y0 + ly0 + PER - 1) * L.pitch + X0 +
+                                    x0) = top;
+        if (col_lane) ring[cls_c][cidx(L, Y0 + ly0 + PER - 1, xc)] = top_c;
+        if (warp > 0) {
+            first = padd(first, *reinterpret_cast<const float2 *>(s_up + (warp - 1) * XW + x0));
+            first_c += s_up[(warp - 1) * XW + slot_c];
+        }
+        *reinterpret_cast<float2 *>(Rn + (long long)(Y0 + ly0) * L.pitch + X0 + x0) = first;
+        if (col_lane) ring[cls_c][cidx(L, Y0 + ly0, xc)] = first_c;
+    }
+    // ring rows below and above the tile, with their corners
+    if (warp == 0) {
+        *reinterpret_cast<float2 *>(ring[R_T] + fidx(L, Y0 - 1, X0 + x0)) =
+            *reinterpret_cast<const float2 *>(s_down + x0);
+        if (lane == 0) ring[R_TR][fidx(L, Y0 - 1, X0 - 1)] = s_down[TX];
+        if (lane == 31) ring[R_TL][fidx(L, Y0 - 1, X0 + TX)] = s_down[TX + 1];
+    }
+    if (warp == NW - 1) {
+        *reinterpret_cast<float2 *>(ring[R_B] + fidx(L, Y0 + TY, X0 + x0)) = up_prev;
+        if (lane == 0) ring[R_BR][fidx(L, Y0 + TY, X0 - 1)] = up_prev_c;
+        if (lane == 31) ring[R_BL][fidx(L, Y0 + TY, X0 + TX)] = up_prev_c;
+    }
+}
+
+// Whether a (precision, tile) pair has the two-nodes-per-lane TMA path, and
+// the CTA size of a shape: four rows per warp on that path.
+template <class S>
+struct IsF32Storage {
+    static constexpr bool value = sizeof(typename S::real) == 4 &&
+                                  sizeof(typename S::pop_t) == 4;
+};
+template <class S, int TX, int TY>
+constexpr int step_threads()
+{
+    return (TX == 64 && IsF32Storage<S>::value) ? 8 * TY : STEP_THREADS;
+}
+template <class S, int TX, int TY, int NT>
+struct HasTmaPair {
+    static constexpr bool value = TX == 64 && IsF32Storage<S>::value &&
+                                  TY % (NT / 32) == 0 && TY / (NT / 32) >= 2;
+};
+
 // Whether a (precision, tile) pair has the TMA interior path.
 template <class S, int TX, int TY, int NT>
 struct HasTma {
@@ -817,7 +1303,7 @@ struct HasTma {
 };
 
 template <class S, int TX, int TY, int NT, int PARITY>
-__global__ void __launch_bounds__(NT)
+__global__ void __launch_bounds__(NT, HasTmaPair<S, TX, TY, NT>::value ? 512 / NT : 0)
     step_kernel(const Lattice L, int cur, int xlo, int xhi, int ylo, int yhi,
                 const __grid_constant__ TmaMaps maps)
 {
@@ -828,6 +1314,12 @@ __global__ void __launch_bounds__(NT)
     if constexpr (HasTma<S, TX, TY, NT>::value) {
         if (interior && maps.valid) {
             step_tile_tma<S, TX, TY, NT, PARITY>(L, cur, X0, Y0, smem_raw, maps);
+            return;
+        }
+    }
+    if constexpr (HasTmaPair<S, TX, TY, NT>::value) {
+        if (interior && maps.valid) {
+            step_tile_tma_pair<S, TX, TY, NT, PARITY>(L, cur, X0, Y0, smem_raw, maps);
             return;
         }
     }
@@ -842,10 +1334,12 @@ static cudaError_t launch_shape(const Lattice &L, int parity, int cur,
                                 cudaStream_t s, const TmaMaps *maps)
 {
     using real = typename S::real;
-    constexpr int NT = STEP_THREADS;
+    constexpr int NT = step_threads<S, TX, TY>();
     const size_t smem_v4 = StepSmem<real, TX, TY>::bytes;
-    const size_t smem_tma = HasTma<S, TX, TY, NT>::value
-                                ? TmaSmem<real, TX, TY>::bytes : 0;
+    size_t smem_tma = 0;
+    if constexpr (HasTma<S, TX, TY, NT>::value) smem_tma = TmaSmem<real, TX, TY>::bytes;
+    if constexpr (HasTmaPair<S, TX, TY, NT>::value)
+        smem_tma = TmaPairSmem<TX, TY, NT>::bytes;
     const size_t smem = smem_v4 > smem_tma ? smem_v4 : smem_tma;
     TmaMaps m{};
     if (maps && maps->valid && maps->tx == TX && maps->ty == TY) m = *maps;
@@ -877,7 +1371,7 @@ static cudaError_t launch_shape(const Lattice &L, int parity, int cur,
 }
 
 // Tile shapes with a compiled kernel (all precisions).
-#define CPLBM_STEP_SHAPES(X) X(32, 16) X(32, 24) X(32, 32) X(64, 16)
+#define CPLBM_STEP_SHAPES(X) X(32, 16) X(32, 24) X(32, 32) X(64, 16) X(64, 32)
 
 // ---------------------------------------------------------------------------
 // Batched step: many independent lattices of different sizes and physics in

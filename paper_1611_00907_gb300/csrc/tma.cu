@@ -43,7 +43,7 @@ bool build_tma_maps(const Lattice &L, TmaMaps *m, char *err, size_t errlen)
         snprintf(err, errlen, "lattice too large for 32-bit plane offsets");
         return false;
     }
-    if ((L.pitch * es) % 16 || (L.plane * es) % 16 || L.tx != 32) {
+    if ((L.pitch * es) % 16 || (L.plane * es) % 16 || (L.tx != 32 && L.tx != 64)) {
         snprintf(err, errlen, "layout not TMA-aligned (pitch %d, tile %dx%d)",
                  L.pitch, L.tx, L.ty);
         return false;
@@ -53,11 +53,13 @@ bool build_tma_maps(const Lattice &L, TmaMaps *m, char *err, size_t errlen)
         snprintf(err, errlen, "cuTensorMapEncodeTiled unavailable");
         return false;
     }
-    const cuuint32_t bx = (cuuint32_t)(L.tx + 8);  // x from X0 - 4, 16-B aligned
+    // density box from x = X0 - 4 (16-B aligned) covering the 2-node halo;
+    // population boxes from X0 - 4 or X0 covering a 1-node shift
+    const cuuint32_t bx = (cuuint32_t)(L.tx + 8), bxp = (cuuint32_t)(L.tx + 4);
     {
         cuuint64_t dims[3] = {(cuuint64_t)L.pitch, (cuuint64_t)L.nyf, 8};
         cuuint64_t strides[2] = {(cuuint64_t)L.pitch * es, (cuuint64_t)L.plane * es};
-        cuuint32_t box[3] = {bx, (cuuint32_t)L.ty, 1};
+        cuuint32_t box[3] = {bxp, (cuuint32_t)L.ty, 1};
         cuuint32_t estr[3] = {1, 1, 1};
         CUresult r = encode(&m->pops, dt, 3, L.pops, dims, strides, box, estr,
                             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,

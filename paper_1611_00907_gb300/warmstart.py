@@ -188,6 +188,10 @@ class Model:
         self.net.close()
 
 
+def _stat(values, fn):
+    return float(fn(np.asarray(values))) if len(values) else float("nan")
+
+
 def compare(model, cases, nx, ny, max_steps, check_every=200, tol=1e-6,
             stream=None):
     """Cold and warm starts of the same cases run to convergence: step
@@ -227,7 +231,12 @@ def compare(model, cases, nx, ny, max_steps, check_every=200, tol=1e-6,
         cold_ms=cold[2], warm_ms=warm[2],
         cold_converged=float((cold[0] < max_steps).mean()),
         warm_converged=float((warm[0] < max_steps).mean()),
-        max_rel_err_rho_l=float(max(err["rho_l"], default=float("nan"))),
-        max_rel_err_rho_v=float(max(err["rho_v"], default=float("nan"))),
-        max_abs_err_theta_deg=float(max(err["theta"], default=float("nan"))),
+        max_rel_err_rho_l=_stat(err["rho_l"], np.max),
+        max_rel_err_rho_v=_stat(err["rho_v"], np.max),
+        max_abs_err_theta_deg=_stat(err["theta"], np.max),
+        median_rel_err_rho_l=_stat(err["rho_l"], np.median),
+        median_rel_err_rho_v=_stat(err["rho_v"], np.median),
+        median_abs_err_theta_deg=_stat(err["theta"], np.median),
+        p90_rel_err_rho_v=_stat(err["rho_v"], lambda v: np.percentile(v, 90)),
+        p90_abs_err_theta_deg=_stat(err["theta"], lambda v: np.percentile(v, 90)),
         mlp_theta_err_deg_median=float(np.median(pred_err)) if pred_err else None)

@@ -103,15 +103,18 @@ def test_1000_steps_fp64(case, walls, size, oracle_threads):
         _compare(sim, ref, 1e-10)
 
 
-@pytest.mark.parametrize("tile", [(32, 16), (32, 24), (32, 32), (64, 16)])
+@pytest.mark.parametrize("tile", [(32, 16), (32, 24), (32, 32), (64, 16), (64, 32)])
 # FP32: mu = psi'(rho) - kappa lap(rho) cancels terms ~100x its size, so
 # eps_32 ~ 6e-8 becomes ~1e-5 relative per evaluation and grows over steps.
 @pytest.mark.parametrize("precision,tol,steps", [("f64", 1e-12, 60),
-                                                 ("f32", 1e-4, 60)])
+                                                 ("f32", 1e-4, 60),
+                                                 ("f32_offset", 1e-4, 60)])
 def test_every_tile_shape(tile, precision, tol, steps):
-    # 230 x 140 with walls: interior tiles (TMA path for 32-wide tiles),
-    # ragged edge tiles, both parities
-    sim, ref, rho = _setup("cs", 230, 140, True, precision=precision)
+    # 230 x 140 with walls: interior tiles (TMA paths), ragged edge tiles,
+    # both parities
+    ref_rho = 0.5 * sum(_coexistence("cs")) if precision == "f32_offset" else 0.0
+    sim, ref, rho = _setup("cs", 230, 140, True, precision=precision,
+                           rho_ref=ref_rho)
     with sim:
         sim.set_tile(*tile)
         assert sim.tile == tile
@@ -122,7 +125,7 @@ def test_every_tile_shape(tile, precision, tol, steps):
             assert _rel(g[k], w[k]) < tol, (k, _rel(g[k], w[k]))
 
 
-@pytest.mark.parametrize("tile", [(32, 16), (32, 24), (32, 32), (64, 16)])
+@pytest.mark.parametrize("tile", [(32, 16), (32, 24), (32, 32), (64, 16), (64, 32)])
 @pytest.mark.parametrize("walls,size", [(True, (260, 200)), (False, (224, 165))])
 def test_interior_tiles_many_steps_fp64(tile, walls, size, oracle_threads):
     # lattices with several rows and columns of interior tiles, 400 steps
@@ -133,6 +136,54 @@ def test_interior_tiles_many_steps_fp64(tile, walls, size, oracle_threads):
         sim.init(rho).step(400)
         ref.init_equilibrium(rho).step(400)
         _compare(sim, ref, 1e-11)
+
+
+def _coexistence(case):
+    kind, a, b, Tr, _, _ = EOS_CASES[case]
+    rv, rl, _, _ = thermo.maxwell(thermo.make_eos(kind, a, b, 1.0, Tr, 0.344))
+    return rv, rl
+
+
+# FP32 interior tiles take the TMA path (32-wide tiles) or the path with two
+# nodes per lane on packed FP32 pairs (64-wide tiles), edge tiles the general
+# path.  Two steps (both parities of the in-place pattern) against the
+# oracle: the density and populations carry FP32 rounding of a few ulp per
+# step, mu (~100x cancellation) and the velocity (small against the
+# populations it is summed from) proportionally more.
+@pytest.mark.parametrize("case", list(EOS_CASES))
+@pytest.mark.parametrize("precision", ["f32", "f32_offset"])
+@pytest.mark.parametrize("tile,walls", [((64, 16), False), ((64, 32), True),
+                                        ((32, 32), False)])
+def test_fp32_paths_two_steps(case, precision, tile, walls):
+    ref_rho = 0.5 * sum(_coexistence(case)) if precision == "f32_offset" else 0.0
+    # 330 x 200: three columns of interior 64-wide tiles, ragged last tiles
+    sim, ref, rho = _setup(case, 330, 200, walls, precision=precision,
+                           rho_ref=ref_rho)
+    with sim:
+        sim.set_tile(*tile)
+        sim.init(rho).step(2)
+        ref.init_equilibrium(rho).step(2)
+        g, w = sim.moments(), ref.moments()
+        assert _rel(g["rho"], w["rho"]) < 2e-6
+        assert _rel(g["mu"], w["mu"]) < 1e-4
+        for k in ("vx", "vy"):
+            assert _rel(g[k], w[k]) < 1e-3, (k, _rel(g[k], w[k]))
+        fg = sim.populations()
+        for i in range(9):
+            assert _rel(fg[i], ref.f[i]) < 5e-6, (i, _rel(fg[i], ref.f[i]))
+
+
+@pytest.mark.parametrize("tile", [(64, 16), (32, 32)])
+def test_fp32_step_is_deterministic(tile):
+    # no atomics on the data path: two runs agree bit for bit
+    out = []
+    for _ in range(2):
+        sim, _, rho = _setup("cs", 330, 200, False, precision="f32")
+        with sim:
+            sim.set_tile(*tile)
+            sim.init(rho).step(31)
+            out.append(sim.populations())
+    assert np.array_equal(out[0], out[1])
 
 
 def test_tile_switch_mid_run():
