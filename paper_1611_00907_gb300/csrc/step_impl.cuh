@@ -1308,7 +1308,10 @@ __global__ void __launch_bounds__(NT, HasTmaPair<S, TX, TY, NT>::value ? 512 / N
                 const __grid_constant__ TmaMaps maps)
 {
     extern __shared__ __align__(128) unsigned char smem_raw[];
-    const int bx = blockIdx.x, by = blockIdx.y;
+    // Odd steps walk the tile grid backwards: the tiles a step writes last,
+    // still in L2, are the first the next step reads.
+    const int bx = PARITY ? gridDim.x - 1 - blockIdx.x : blockIdx.x;
+    const int by = PARITY ? gridDim.y - 1 - blockIdx.y : blockIdx.y;
     const int X0 = bx * TX, Y0 = by * TY;
     const bool interior = bx >= xlo && bx <= xhi && by >= ylo && by <= yhi;
     if constexpr (HasTma<S, TX, TY, NT>::value) {
@@ -1388,7 +1391,8 @@ __global__ void __launch_bounds__(NT)
     __shared__ Lattice sL;
     static_assert(sizeof(Lattice) % sizeof(int) == 0, "descriptor copy");
     for (int w = blockIdx.x; w < n_items; w += gridDim.x) {
-        const WorkItem it = items[w];
+        // odd steps take the work list backwards (see step_kernel)
+        const WorkItem it = items[PARITY ? n_items - 1 - w : w];
         {
             const int *src = reinterpret_cast<const int *>(lats + it.inst);
             int *dst = reinterpret_cast<int *>(&sL);
@@ -1472,7 +1476,8 @@ __global__ void __launch_bounds__(NT)
     step_pt_kernel(const Lattice L, int cur, int xlo, int xhi, int ylo, int yhi)
 {
     extern __shared__ __align__(128) unsigned char smem_raw[];
-    const int bx = blockIdx.x, by = blockIdx.y;
+    const int bx = PARITY ? gridDim.x - 1 - blockIdx.x : blockIdx.x;  // as step_kernel
+    const int by = PARITY ? gridDim.y - 1 - blockIdx.y : blockIdx.y;
     const bool interior = bx >= xlo && bx <= xhi && by >= ylo && by <= yhi;
     if (interior)
         step_tile<S, TX, TY, NT, PARITY, true, true>(L, cur, bx * TX, by * TY,
