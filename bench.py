@@ -250,8 +250,9 @@ def batch_specs(which):
         rv, rl, _ = eos_coexistence(sp["eos"], sp["a"], sp["b"], 1.0, sp["Tr"],
                                     sp.get("omega", 0.344))
         fields.append(inputs.initial_density(sp, rv, rl))
+        sp["rho_ref"] = 0.5 * (rv + rl)   # used by the offset storages only
     keep = ("nx", "ny", "walls", "tau", "kappa", "eos", "a", "b", "Tr",
-            "omega", "mu_bottom")
+            "omega", "mu_bottom", "rho_ref")
     return [{k: v for k, v in sp.items() if k in keep} for sp in specs], fields
 
 
@@ -310,6 +311,114 @@ def measure_batch(which, precision, steps, warmup, sequential=True):
             out["sequential_value"] = nodes * steps / (ms * 1e-3) / 1e6
             for sim in sims:
                 sim.close()
+    return out
+
+
+def _run_batch(specs, fields, precision, steps):
+    """Run a batch `steps` steps from its fields: (device ms, final
+    densities, finite flags)."""
+    import math
+    import torch
+    from paper_1611_00907_gb300 import Batch, LbmError
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        with Batch(specs, precision=precision, stream=stream.cuda_stream) as b:
+            for k, f in enumerate(fields):
+                b.init(k, f)
+            torch.cuda.synchronize()
+            t0 = torch.cuda.Event(enable_timing=True)
+            t1 = torch.cuda.Event(enable_timing=True)
+            t0.record(stream)
+            b.step(steps)
+            t1.record(stream)
+            torch.cuda.synchronize()
+            rhos, finite = [], []
+            for k in range(len(specs)):
+                try:
+                    ok = math.isfinite(b.reduce(k)[0])
+                except LbmError:
+                    ok = False
+                finite.append(ok)
+                rhos.append(b.moments(k)["rho"] if ok else None)
+    return t0.elapsed_time(t1), rhos, finite
+
+
+# (T/T_c, tau) of the Laplace study: at T/T_c = 0.7 the CS drop with
+# kappa = 0.5 holds only with tau = 1.5 (tau = 1 diverges, in the oracle too)
+LAPLACE_T = ((0.7, 1.5), (0.8, 1.0), (0.9, 1.0))
+
+
+def measure_laplace(steps):
+    """Static CS drops (a 1, b 4, kappa 0.5) of radii 16 .. 80 in 256^2
+    periodic boxes at three temperatures, one batch per storage (FP32 offset,
+    FP64): Laplace pressure jump against 1 / R per temperature."""
+    from paper_1611_00907_gb300 import eos_coexistence, eos_pressure, inputs
+    from paper_1611_00907_gb300 import observables as obs
+    radii = inputs.ring_radii(16, 80, 8)
+    specs, fields = [], []
+    for Tr, tau in LAPLACE_T:
+        rv, rl, _ = eos_coexistence("cs", 1.0, 4.0, 1.0, Tr)
+        for r in radii:
+            specs.append(dict(nx=256, ny=256, eos="cs", a=1.0, b=4.0, Tr=Tr,
+                              tau=tau, kappa=0.5, rho_ref=0.5 * (rv + rl)))
+            fields.append(inputs.drop(256, 256, r, rl, rv, 4.0))
+    out = {"lattice": [256, 256], "steps": steps, "radii": radii,
+           "eos": "carnahan-starling a=1 b=4", "kappa": 0.5,
+           "T_over_Tc_tau": [list(v) for v in LAPLACE_T]}
+    for prec in ("f32_offset", "f64"):
+        ms, rhos, finite = _run_batch(specs, fields, prec, steps)
+        res = {"seconds": ms * 1e-3,
+               "mlups": len(specs) * 256 * 256 * steps / (ms * 1e-3) / 1e6,
+               "finite_fraction": sum(finite) / len(finite)}
+        for j, (Tr, _) in enumerate(LAPLACE_T):
+            rv, rl, _ = eos_coexistence("cs", 1.0, 4.0, 1.0, Tr)
+            pts, gone = [], []
+            for k in range(j * len(radii), (j + 1) * len(radii)):
+                if rhos[k] is None:
+                    continue
+                rin, rout = obs.periodic_drop_bulk(rhos[k])
+                if rin - rout < 0.5 * (rl - rv):   # the drop evaporated
+                    gone.append(radii[k - j * len(radii)])
+                    continue
+                dp, R = obs.laplace_jump(
+                    rhos[k], lambda v: eos_pressure("cs", 1.0, 4.0, 1.0, Tr, 0.344, v))
+                pts.append((1.0 / R, dp))
+            fit = obs.line_fit(*zip(*pts)) if len(pts) >= 3 else (None,) * 3
+            res["T%.1f" % Tr] = {"slope": fit[0], "intercept": fit[1],
+                                 "r2": fit[2], "inv_R_dp": pts,
+                                 "evaporated_initial_radii": gone}
+        out[prec] = res
+    out["slope_rel_diff_f32_offset_vs_f64"] = {
+        key: (abs(out["f32_offset"][key]["slope"] / out["f64"][key]["slope"] - 1)
+              if out["f32_offset"][key]["slope"] and out["f64"][key]["slope"]
+              else None)
+        for key in ("T%.1f" % Tr for Tr, _ in LAPLACE_T)}
+    return out
+
+
+def measure_wetting_angles(steps):
+    """The wetting sweep run to `steps` steps in FP32 and in FP16 offset
+    storage: contact angle against the wall's surface chemical potential."""
+    from paper_1611_00907_gb300 import eos_coexistence
+    from paper_1611_00907_gb300 import observables as obs
+    specs, fields = batch_specs("wetting")
+    _, _, mc = eos_coexistence("vdw", 9 / 49, 2 / 21, 1.0, 0.85)
+    out = {"instances": len(specs), "lattice": [specs[0]["nx"], specs[0]["ny"]],
+           "steps": steps,
+           "mu_s_minus_mu_coex": [sp["mu_bottom"] - mc for sp in specs]}
+    for prec in ("f32", "f16_offset"):
+        ms, rhos, finite = _run_batch(specs, fields, prec, steps)
+        th = [obs.contact_angle(r) if r is not None else float("nan") for r in rhos]
+        pts = [(m, t) for m, t in zip(out["mu_s_minus_mu_coex"], th)
+               if 0.0 < t < 180.0]
+        fit = obs.line_fit(*zip(*pts)) if len(pts) >= 3 else (None,) * 3
+        out[prec] = {"seconds": ms * 1e-3, "theta_deg": th,
+                     "finite_fraction": sum(finite) / len(finite),
+                     "dtheta_dmu_s": fit[0], "theta_at_mu_coex": fit[1],
+                     "r2": fit[2]}
+    d = [abs(a - b) for a, b in zip(out["f32"]["theta_deg"], out["f16_offset"]["theta_deg"])
+         if a == a and b == b]
+    out["max_abs_theta_diff_f16_vs_f32_deg"] = max(d) if d else None
     return out
 
 
@@ -479,6 +588,9 @@ def main():
     ap.add_argument("--warmstart", default="small",
                     choices=["small", "full", "off"],
                     help="learned warm-start sweep (full: 256 x 512x256)")
+    ap.add_argument("--physics-steps", type=int, default=20000,
+                    help="steps of the Laplace study; the wetting sweep runs "
+                         "1.5x as many (0: skip both)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     rank, world = dist_setup()
@@ -546,6 +658,12 @@ def main():
     if args.warmstart != "off" and rank == 0:
         warm = measure_warmstart(args.warmstart == "full")
 
+    physics = {}
+    if args.physics_steps > 0 and rank == 0:
+        physics["laplace"] = measure_laplace(args.physics_steps)
+        physics["wetting_angles"] = measure_wetting_angles(
+            3 * args.physics_steps // 2)
+
     base = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         base = cpu_baseline()
@@ -565,6 +683,7 @@ def main():
             line["pressure_tensor_vs_chemical_potential"] = pt
         if warm:
             line["warm_start"] = warm
+        line.update(physics)
         print(json.dumps(line))
     if world > 1:
         import torch.distributed as dist

@@ -203,8 +203,15 @@ lbm_status lbm_batch_create(const lbm_instance *inst, int count, int precision,
  * number of steps (the in-place order is then the natural one). */
 lbm_status lbm_batch_init(lbm_batch *b, int index, const double *rho,
                           const double *ux, const double *uy, int on_device);
-/* Queue nsteps steps of every lattice; all must be initialised. */
+/* Queue nsteps steps of every active lattice; all must be initialised. */
 lbm_status lbm_batch_step(lbm_batch *b, int nsteps);
+/* Take lattice `index` out of the batched launch (active = 0) or put it
+ * back (active = 1).  An inactive lattice keeps its state and step count and
+ * the per-lattice calls below still work on it: a sweep drops the lattices
+ * that have converged so that the launch carries only the rest.  Allowed
+ * after an even number of batch steps (the in-place order is then the
+ * natural one); the next lbm_batch_step re-captures its graph. */
+lbm_status lbm_batch_set_active(lbm_batch *b, int index, int active);
 /* Per-lattice lbm_moments, lbm_get_populations and lbm_reduce. */
 lbm_status lbm_batch_moments(lbm_batch *b, int index, double *rho, double *vx,
                              double *vy, double *mu, int on_device);
@@ -286,6 +293,15 @@ lbm_status lbm_step_noalloc(const lbm_config *cfg, int eos, double a,
 lbm_status lbm_eos_coexistence(int eos, double a, double b, double R,
                                double T_over_Tc, double omega, double *rho_v,
                                double *rho_l, double *mu_coex);
+
+/* Bulk pressure p0 of the EOS at T = T_over_Tc * T_c for n densities:
+ * Eq. 16 (vdW), Eq. 19 (RKS), Eq. 22 (PR), Eq. 25 (CS).  rho[n] in, p[n]
+ * out, host arrays.  Host-only helper for measurements such as the Laplace
+ * pressure jump (Sec. III); a density outside (0, pole of the EOS) gives
+ * LBM_ERR_ARG and leaves p unspecified. */
+lbm_status lbm_eos_pressure(int eos, double a, double b, double R,
+                            double T_over_Tc, double omega, const double *rho,
+                            double *p, size_t n);
 
 /* Release the context and its device memory.  NULL is ignored. */
 void lbm_destroy(lbm_ctx *ctx);

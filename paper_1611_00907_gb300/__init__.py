@@ -13,7 +13,7 @@ from . import _lib
 from ._lib import EOS, PRECISION, LbmError, check
 
 __all__ = ["Simulation", "Batch", "LbmError", "eos_critical",
-           "eos_coexistence", "EOS", "PRECISION"]
+           "eos_coexistence", "eos_pressure", "EOS", "PRECISION"]
 
 
 def eos_critical(eos, a, b, R=1.0):
@@ -35,6 +35,19 @@ def eos_coexistence(eos, a, b, R=1.0, Tr=0.85, omega=0.344):
                                   float(omega), C.byref(v), C.byref(l),
                                   C.byref(m)))
     return v.value, l.value, m.value
+
+
+def eos_pressure(eos, a, b, R=1.0, Tr=0.85, omega=0.344, rho=None):
+    """Bulk pressure p0(rho) of the EOS (array in, array out), from the
+    library."""
+    lib = _lib.load()
+    r = np.ascontiguousarray(rho, dtype=np.float64)
+    p = np.empty_like(r)
+    check(lib.lbm_eos_pressure(EOS[eos] if isinstance(eos, str) else int(eos),
+                               float(a), float(b), float(R), float(Tr),
+                               float(omega), r.ctypes.data, p.ctypes.data,
+                               r.size))
+    return p
 
 
 def _is_torch(x):
@@ -305,6 +318,13 @@ class Batch:
 
     def step(self, n=1):
         self._check(self._lib.lbm_batch_step(self._b, int(n)))
+        return self
+
+    def set_active(self, index, active=True):
+        """Take a lattice out of the launch (or put it back); after an even
+        number of batch steps."""
+        self._check(self._lib.lbm_batch_set_active(self._b, int(index),
+                                                   1 if active else 0))
         return self
 
     def moments(self, index):

@@ -65,6 +65,8 @@ SIGNATURES = {
                           _dp], C.c_int),
     "lbm_eos_coexistence": ([C.c_int, C.c_double, C.c_double, C.c_double,
                              C.c_double, C.c_double, _dp, _dp, _dp], C.c_int),
+    "lbm_eos_pressure": ([C.c_int, C.c_double, C.c_double, C.c_double,
+                          C.c_double, C.c_double, _vp, _vp, C.c_size_t], C.c_int),
     "lbm_step_noalloc": ([C.POINTER(LbmConfig), C.c_int, C.c_double,
                           C.c_double, C.c_double, C.c_double, C.c_double,
                           C.c_double, C.c_int, C.c_double, _vp, C.c_int],
@@ -73,6 +75,7 @@ SIGNATURES = {
                           C.c_int, C.POINTER(_ctx)], C.c_int),
     "lbm_batch_init": ([_ctx, C.c_int, _vp, _vp, _vp, C.c_int], C.c_int),
     "lbm_batch_step": ([_ctx, C.c_int], C.c_int),
+    "lbm_batch_set_active": ([_ctx, C.c_int, C.c_int], C.c_int),
     "lbm_batch_moments": ([_ctx, C.c_int, _vp, _vp, _vp, _vp, C.c_int],
                           C.c_int),
     "lbm_batch_populations": ([_ctx, C.c_int, _vp, C.c_int], C.c_int),

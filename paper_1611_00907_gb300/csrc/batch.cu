@@ -18,6 +18,7 @@ using namespace cplbm;
 
 struct lbm_batch {
     std::vector<lbm_ctx *> inst;
+    std::vector<char> active;  // lattices in the launch
     int precision = 0, device = 0;
     cudaStream_t stream = nullptr;
     bool own_stream = false;
@@ -75,6 +76,7 @@ lbm_status rebuild(lbm_batch *b)
         c->L.ty = b->ty;
         ctx_refresh_maps(c);
         lats.push_back(c->L);
+        if (!b->active[i]) continue;
         const Lattice &L = c->L;
         const int ntx = (L.nx + b->tx - 1) / b->tx, nty = (L.nyf + b->ty - 1) / b->ty;
         const int nfx = L.nx / b->tx, nfy = L.nyf / b->ty;
@@ -195,6 +197,7 @@ lbm_status lbm_batch_create(const lbm_instance *inst, int count, int precision,
             break;
         }
         b->inst.push_back(c);
+        b->active.push_back(1);
         st = lbm_set_eos(c, q.eos, q.a, q.b, q.R, q.T_over_Tc, q.omega);
         if (st == LBM_OK) st = lbm_set_wall_mu(c, q.mu_bottom, q.top_mode, q.mu_top);
         if (st != LBM_OK) bfail(b, st, "lattice %d: %s", i, lbm_last_error(c));
@@ -233,7 +236,8 @@ lbm_status lbm_batch_step(lbm_batch *b, int nsteps)
         if (!b->inst[i]->initialized)
             return bfail(b, LBM_ERR_STATE, "lattice %zu is not initialised", i);
     BCUDA(b, cudaSetDevice(b->device));
-    int left = nsteps;
+    const long long t0 = b->t;
+    int left = b->n_items > 0 ? nsteps : 0;  // nothing to launch: time only
     lbm_status st = LBM_OK;
     if (left > 0 && (b->t & 1)) {
         st = launch_one(b);
@@ -253,8 +257,25 @@ lbm_status lbm_batch_step(lbm_batch *b, int nsteps)
         st = launch_one(b);
         --left;
     }
-    for (lbm_ctx *c : b->inst) c->t = b->t;
+    if (b->n_items == 0) b->t += nsteps;
+    for (size_t i = 0; i < b->inst.size(); ++i)
+        if (b->active[i]) b->inst[i]->t += b->t - t0;
     return st;
+}
+
+lbm_status lbm_batch_set_active(lbm_batch *b, int index, int active)
+{
+    if (!b) return LBM_ERR_ARG;
+    lbm_status st = check_index(b, index);
+    if (st != LBM_OK) return st;
+    if (b->t & 1)
+        return bfail(b, LBM_ERR_STATE, "lattices can leave or join the launch "
+                     "only after an even number of batch steps (now %lld)", b->t);
+    const char want = active ? 1 : 0;
+    if (b->active[index] == want) return LBM_OK;
+    b->active[index] = want;
+    BCUDA(b, cudaSetDevice(b->device));
+    return rebuild(b);
 }
 
 lbm_status lbm_batch_moments(lbm_batch *b, int index, double *rho, double *vx,
@@ -320,6 +341,8 @@ lbm_status lbm_batch_autotune(lbm_batch *b, int nsteps, int *tx, int *ty)
     int sx[16], sy[16];
     const int n = step_shapes(sx, sy, 16);
     const long long t0 = b->t;
+    std::vector<long long> tsave;  // inactive lattices may lag the batch
+    for (lbm_ctx *c : b->inst) tsave.push_back(c->t);
     int best = -1;
     float best_ms = 0.f;
     cudaEvent_t e0 = nullptr, e1 = nullptr;
@@ -333,7 +356,7 @@ lbm_status lbm_batch_autotune(lbm_batch *b, int nsteps, int *tx, int *ty)
         for (size_t i = 0; i < b->inst.size() && s2 == LBM_OK; ++i)
             s2 = ctx_snapshot(b->inst[i], snaps[i], false);
         b->t = t0;
-        for (lbm_ctx *c : b->inst) c->t = t0;
+        for (size_t i = 0; i < b->inst.size(); ++i) b->inst[i]->t = tsave[i];
         return s2;
     };
     for (int k = 0; k < n && st == LBM_OK; ++k) {

@@ -385,6 +385,28 @@ lbm_status lbm_eos_coexistence(int eos, double a, double b, double R,
     return LBM_OK;
 }
 
+lbm_status lbm_eos_pressure(int eos, double a, double b, double R,
+                            double T_over_Tc, double omega, const double *rho,
+                            double *p, size_t n)
+{
+    if ((!rho || !p) && n) return fail(nullptr, LBM_ERR_ARG, "null array");
+    if (eos < LBM_EOS_VDW || eos > LBM_EOS_RKS || !(a > 0 && b > 0 && R > 0))
+        return fail(nullptr, LBM_ERR_ARG, "invalid EOS parameters");
+    if (!(T_over_Tc > 0) || !std::isfinite(T_over_Tc) || !std::isfinite(omega))
+        return fail(nullptr, LBM_ERR_ARG, "T_over_Tc must be positive and finite");
+    double Tc, rc;
+    if (!critical(eos, a, b, R, &Tc, &rc))
+        return fail(nullptr, LBM_ERR_NUMERIC, "critical point not found");
+    const double RT = R * T_over_Tc * Tc, aa = a * alpha_of(eos, T_over_Tc, omega);
+    const double top = pole(eos, b);
+    for (size_t k = 0; k < n; ++k) {
+        if (!(rho[k] > 0 && rho[k] < top))
+            return fail(nullptr, LBM_ERR_ARG, "density %g outside (0, %g)", rho[k], top);
+        p[k] = p0_dual(eos, aa, b, RT, D2{rho[k], 1, 0}).v;
+    }
+    return LBM_OK;
+}
+
 lbm_status lbm_set_eos(lbm_ctx *c, int eos, double a, double b, double R,
                        double T_over_Tc, double omega)
 {

@@ -1,7 +1,8 @@
-"""Measurements on converged density fields of a wall droplet: bulk liquid
-and vapour densities, interface width and contact angle (Sec. V's
-spherical-cap formulas).  Used for the learned warm start's training
-targets and for judging its error; plain NumPy on host arrays [ny, nx].
+"""Measurements on converged density fields: for a wall droplet the bulk
+liquid and vapour densities, interface width and contact angle (Sec. V's
+spherical-cap formulas); for a free droplet in a periodic box the Laplace
+pressure jump and equimolar radius (Sec. III).  Used by the learned warm
+start and the physics reports; plain NumPy on host arrays [ny, nx].
 
 Conventions: rows 0 and ny - 1 are solid; the wall plane of the halfway
 bounce-back lies half a node above row 0; the interface is the level set
@@ -85,3 +86,39 @@ def measure(rho):
     rho_l, rho_v = bulk_densities(rho)
     return dict(rho_l=rho_l, rho_v=rho_v, width=interface_width(rho),
                 theta=contact_angle(rho))
+
+
+def periodic_drop_bulk(rho):
+    """(rho_in, rho_out) of a drop centred in a periodic box: mean of the
+    interior plateau (within 2 % of the density range of the maximum) and
+    median of the box's edge rows and columns, the points farthest from the
+    drop."""
+    lo, hi = float(rho.min()), float(rho.max())
+    rho_in = float(rho[rho >= hi - 0.02 * (hi - lo)].mean())
+    edge = np.concatenate([rho[0], rho[-1], rho[:, 0], rho[:, -1]])
+    return rho_in, float(np.median(edge))
+
+
+def equimolar_radius(rho, rho_in, rho_out):
+    """Radius of the disc that holds the drop's excess mass at the bulk
+    densities: A = sum(rho - rho_out) / (rho_in - rho_out), R = sqrt(A / pi)."""
+    area = float((rho - rho_out).sum()) / (rho_in - rho_out)
+    return math.sqrt(max(area, 0.0) / math.pi)
+
+
+def laplace_jump(rho, pressure):
+    """(Delta p, R) of a static periodic drop: the bulk pressure p0 of the
+    interior density minus that of the far field, and the equimolar radius.
+    pressure maps an array of densities to p0 (the library's EOS)."""
+    rho_in, rho_out = periodic_drop_bulk(rho)
+    p_in, p_out = pressure(np.array([rho_in, rho_out]))
+    return float(p_in - p_out), equimolar_radius(rho, rho_in, rho_out)
+
+
+def line_fit(x, y):
+    """Least-squares y = slope x + intercept: (slope, intercept, r^2)."""
+    x, y = np.asarray(x, float), np.asarray(y, float)
+    slope, icpt = np.polyfit(x, y, 1)
+    res = y - (slope * x + icpt)
+    tot = ((y - y.mean()) ** 2).sum()
+    return float(slope), float(icpt), float(1 - (res ** 2).sum() / tot) if tot > 0 else 1.0

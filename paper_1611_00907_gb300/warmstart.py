@@ -107,9 +107,11 @@ def warm_field(case, pred, nx, ny):
 def run_batch(cases, fields, nx, ny, max_steps, check_every=200, tol=1e-6,
               precision="f32", stream=None):
     """Run every case from its field until max |rho change| over
-    check_every steps stays below tol * rho_l, or max_steps.  Returns the
-    per-case convergence step (max_steps if never), the final fields, the
-    device milliseconds until the last case converged, and the steps run."""
+    check_every steps (even) stays below tol * rho_l, or max_steps; a case
+    that has converged (or gone non-finite) leaves the batched launch.
+    Returns the per-case convergence step (max_steps if never), the final
+    fields, the device milliseconds until the last case converged, and the
+    steps run."""
     import torch
     specs = [_spec(c, nx, ny) for c in cases]
     conv = np.full(len(cases), max_steps, dtype=np.int64)
@@ -135,10 +137,12 @@ def run_batch(cases, fields, nx, ny, max_steps, check_every=200, tol=1e-6,
                     d = b.reduce(k)[3]
                 except Exception:
                     done[k] = True            # non-finite: never converges
+                    b.set_active(k, False)
                     continue
                 if d < tol * cases[k]["rho_l"]:
                     done[k] = True
                     conv[k] = steps
+                    b.set_active(k, False)
         ev1.record(stream if stream else torch.cuda.current_stream())
         torch.cuda.synchronize()
         ms = ev0.elapsed_time(ev1)

@@ -3,6 +3,8 @@ function include/cplbm.h declares; argument validation and the host-side
 critical-point helper work without touching a device."""
 import ctypes as C
 import math
+
+import numpy as np
 import subprocess
 
 import pytest
@@ -119,3 +121,20 @@ def test_library_coexistence_rejects_supercritical(lib):
     v, l = C.c_double(), C.c_double()
     assert lib.lbm_eos_coexistence(1, 1.0, 4.0, 1.0, 1.02, 0.3, C.byref(v),
                                    C.byref(l), None) == _lib.LBM_ERR_ARG
+
+
+@pytest.mark.parametrize("kind,a,b,Tr", [("vdw", 9 / 49, 2 / 21, 0.85),
+                                         ("cs", 1.0, 4.0, 0.85),
+                                         ("pr", 2 / 49, 2 / 21, 0.8),
+                                         ("rks", 2 / 49, 2 / 21, 0.8)])
+def test_library_pressure_matches_oracle(kind, a, b, Tr):
+    from oracle import thermo
+    from paper_1611_00907_gb300 import LbmError, eos_pressure
+    e = thermo.make_eos(kind, a, b, 1.0, Tr, 0.344)
+    rv, rl, _, _ = thermo.maxwell(e)
+    rho = np.linspace(0.5 * rv, 1.2 * rl, 41)
+    got = eos_pressure(kind, a, b, 1.0, Tr, 0.344, rho)
+    want = e.p0(rho)
+    assert np.abs(got - want).max() <= 1e-12 * np.abs(want).max()
+    with pytest.raises(LbmError):
+        eos_pressure(kind, a, b, 1.0, Tr, 0.344, [-0.1])

@@ -117,3 +117,35 @@ def test_batch_rejects_init_at_odd_step_and_bad_index():
         assert b._lib.lbm_batch_reduce(b._b, 5, None) == -1
         b.step(1)
         b.init(0, inst[0][2])             # even again: allowed
+
+
+def test_inactive_lattices_keep_their_state(oracle_threads):
+    # a lattice that leaves the launch is frozen; the others go on; back in
+    # the launch it continues from where it stopped
+    inst = _instances()[:3]
+    with Batch([d for d, _, _ in inst], precision="f64") as b:
+        for k, (_, _, rho) in enumerate(inst):
+            b.init(k, rho)
+        b.step(10)
+        frozen = b.populations(1)
+        b.set_active(1, False)
+        b.step(20)
+        assert np.array_equal(b.populations(1), frozen)
+        b.set_active(0, False)
+        b.set_active(2, False)
+        b.step(6)                          # nothing in the launch
+        b.set_active(1, True)
+        b.set_active(2, True)
+        b.step(1)
+        with pytest.raises(LbmError):
+            b.set_active(0, True)          # odd batch step count
+        b.step(9)
+        for k, steps in ((0, 30), (1, 20), (2, 40)):
+            d, e, rho = inst[k]
+            ref = oracle.Lattice(d["nx"], d["ny"], e, d["tau"], d["kappa"],
+                                 walls=d.get("walls", False),
+                                 mu_bottom=d["mu_bottom"])
+            ref.init_equilibrium(rho).step(steps)
+            got = b.moments(k)
+            for key in ("rho", "mu", "vx", "vy"):
+                assert _rel(got[key], ref.moments()[key]) < 1e-12, (k, key)

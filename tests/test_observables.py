@@ -7,6 +7,7 @@ import math
 import numpy as np
 import pytest
 
+from paper_1611_00907_gb300 import inputs
 from paper_1611_00907_gb300 import observables as obs
 from paper_1611_00907_gb300 import warmstart as ws
 
@@ -55,3 +56,25 @@ def test_drop_column_tracks_the_centre():
     rho = cap(60, 2.0)
     rho = np.roll(rho, 37, axis=1)
     assert abs(obs.drop_column(rho) - (256 + 37)) <= 1
+
+
+def test_equimolar_radius_and_jump_of_a_disc():
+    n = 256
+    yy, xx = np.mgrid[0:n, 0:n]
+    for R in (20.0, 45.0):
+        d = R - np.hypot(xx - n / 2 + 0.5, yy - n / 2 + 0.5)
+        rho = inputs.tanh_profile(d, 0.3, 0.02, 4.0)
+        rin, rout = obs.periodic_drop_bulk(rho)
+        # the plateau band (2 % of the range) takes in the profile's tail
+        assert abs(rin - 0.3) < 1e-3 and abs(rout - 0.02) < 1e-9
+        # a symmetric tanh profile puts the excess mass's edge at d = 0 up
+        # to a curvature correction of order W^2 / R
+        assert abs(obs.equimolar_radius(rho, rin, rout) - R) < 3.0 / R
+        dp, r = obs.laplace_jump(rho, lambda v: 2.0 * v)
+        assert abs(dp - 2.0 * (rin - rout)) < 1e-12 and abs(r - R) < 3.0 / R
+
+
+def test_line_fit_recovers_a_line():
+    x = np.linspace(0.01, 0.1, 8)
+    s, c, r2 = obs.line_fit(x, 3.0 * x - 0.5)
+    assert abs(s - 3.0) < 1e-12 and abs(c + 0.5) < 1e-12 and r2 == pytest.approx(1.0)
