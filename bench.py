@@ -488,6 +488,45 @@ def roofline(precision, ms_per_step, n_nodes, n_side=N_SIDE):
             "bytes_per_update": BYTES_PER_LU[precision]}
 
 
+# GB300's FP64 pipe: 2 thread instructions per SM per clock (ncu's sustained
+# peak of the pipe, 304 per clock over the GPU) x 152 SMs x 2.07 GHz.
+FP64_PIPE_GINST = 2 * 152 * 2.07
+
+
+def recorded_fp64_ops():
+    """FP64-pipe thread instructions per lattice update from the committed
+    ncu summary of the FP64 step, or None when the kernel changed since."""
+    path = os.path.join(ROOT, "profiles", "step_kernel_f64.md")
+    try:
+        text = open(path).read()
+    except OSError:
+        return None
+    m = re.search(r"fp64_pipe_inst_per_node:\s*([0-9.eE+-]+)", text)
+    hm = re.search(r"kernel_sources_sha256_16:\s*([0-9a-f]+)", text)
+    if not m or not hm or hm.group(1) != kernel_hash():
+        return None
+    return float(m.group(1))
+
+
+def roofline_fp64(ms_per_step, n_nodes, n_side=N_SIDE):
+    """The FP64 step is bound by the FP64 pipe: its instructions per update
+    (ncu) over the launch time against the pipe's peak; the HBM figures
+    beside it for reference."""
+    ops = recorded_fp64_ops()
+    hbm = roofline("f64", ms_per_step, n_nodes, n_side)
+    if ops is None:
+        return dict(hbm, bound="alu", achieved=None,
+                    peak=round(FP64_PIPE_GINST, 1), unit="G FP64-pipe inst/s",
+                    frac=None, peak_source="derived", hbm_frac=hbm["frac"])
+    achieved = ops * n_nodes / (ms_per_step * 1e-3) / 1e9
+    return {"bound": "alu", "achieved": round(achieved, 1),
+            "peak": round(FP64_PIPE_GINST, 1), "unit": "G FP64-pipe inst/s",
+            "frac": round(achieved / FP64_PIPE_GINST, 4),
+            "fp64_inst_per_update": ops, "peak_source": "derived",
+            "traffic": hbm["traffic"], "hbm_achieved_gbs": hbm["achieved"],
+            "hbm_frac": hbm["frac"]}
+
+
 # ---------------------------------------------------------------------------
 def dist_setup():
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -621,7 +660,7 @@ def main():
         fp64 = {"value": world * n_nodes / (fp64_ms * 1e-3) / 1e6,
                 "unit": "MLUPS", "ms_per_step": fp64_ms,
                 "steps": args.fp64_steps,
-                "roofline": roofline("f64", fp64_ms, n_nodes, args.n)}
+                "roofline": roofline_fp64(fp64_ms, n_nodes, args.n)}
 
     e2e = None
     if not args.no_e2e:
