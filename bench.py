@@ -422,6 +422,41 @@ def measure_wetting_angles(steps):
     return out
 
 
+# Fig. 1: coexistence curves of flat interfaces against the Maxwell
+# construction (Sec. III, V): (label, EOS, a, b, omega, kappa, tau)
+FIG1_EOS = (("pr_water", "pr", 2 / 49, 2 / 21, 0.344, 0.01, 1.3),
+            ("pr_methane", "pr", 2 / 49, 2 / 21, 0.011, 0.01, 1.3),
+            ("rks_water", "rks", 2 / 49, 2 / 21, 0.344, 0.01, 1.3),
+            ("cs", "cs", 1.0, 4.0, 0.344, 0.5, 1.0))
+FIG1_TR = (0.65, 0.7, 0.75, 0.8, 0.85, 0.9, 0.95)
+
+
+def measure_coexistence_curves(steps):
+    """Flat liquid slabs (32 x 256 periodic, FP64) of every Fig. 1 EOS over
+    a range of temperatures, one batch: bulk densities against the Maxwell
+    construction."""
+    from paper_1611_00907_gb300 import eos_coexistence, inputs
+    from paper_1611_00907_gb300 import observables as obs
+    specs, fields, meta = [], [], []
+    for label, kind, a, b, om, kappa, tau in FIG1_EOS:
+        for Tr in FIG1_TR:
+            rv, rl, _ = eos_coexistence(kind, a, b, 1.0, Tr, om)
+            specs.append(dict(nx=32, ny=256, eos=kind, a=a, b=b, Tr=Tr,
+                              omega=om, kappa=kappa, tau=tau))
+            fields.append(inputs.slab(32, 256, rl, rv, 4.0 if kappa > 0.1 else 2.0))
+            meta.append((label, Tr, rv, rl))
+    ms, rhos, finite = _run_batch(specs, fields, "f64", steps)
+    out = {"lattice": [32, 256], "steps": steps, "precision": "f64",
+           "seconds": ms * 1e-3, "finite_fraction": sum(finite) / len(finite)}
+    for (label, Tr, rv, rl), rho in zip(meta, rhos):
+        row = {"T_over_Tc": Tr, "maxwell": [rv, rl]}
+        if rho is not None:
+            l, v = obs.slab_bulk(rho)
+            row.update(sim=[v, l], rel_err=[v / rv - 1, l / rl - 1])
+        out.setdefault(label, []).append(row)
+    return out
+
+
 def measure_warmstart(full):
     """Sweep time-to-converge, learned warm start against the plain
     half-disc start.  Small: 64 wall drops of 256x128 after training on
@@ -613,6 +648,8 @@ def main():
     ap.add_argument("--precision", default="f32",
                     choices=["f32", "f32_offset", "f16_offset", "f64"])
     ap.add_argument("--fp64-steps", type=int, default=200)
+    ap.add_argument("--fp16-steps", type=int, default=500,
+                    help="steps of the FP16-storage leg (0: skip)")
     ap.add_argument("--check-every", type=int, default=100)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
@@ -662,6 +699,17 @@ def main():
                 "steps": args.fp64_steps,
                 "roofline": roofline_fp64(fp64_ms, n_nodes, args.n)}
 
+    # the FP16-storage variant (FP32 arithmetic, 36 B per update) on the same
+    # lattice
+    fp16 = None
+    if args.fp16_steps > 0:
+        f16_ms = measure_gpu("f16_offset", args.fp16_steps, 3, rho) / args.fp16_steps
+        f16_ms = max_over_ranks(f16_ms, world)
+        fp16 = {"value": world * n_nodes / (f16_ms * 1e-3) / 1e6,
+                "unit": "MLUPS", "ms_per_step": f16_ms,
+                "steps": args.fp16_steps,
+                "roofline": roofline("f16_offset", f16_ms, n_nodes, args.n)}
+
     e2e = None
     if not args.no_e2e:
         e2e = measure_e2e(args.precision, args.steps, args.warmup, rho,
@@ -702,6 +750,8 @@ def main():
         physics["laplace"] = measure_laplace(args.physics_steps)
         physics["wetting_angles"] = measure_wetting_angles(
             3 * args.physics_steps // 2)
+        physics["coexistence_curves"] = measure_coexistence_curves(
+            args.physics_steps)
 
     base = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -715,7 +765,8 @@ def main():
                 "dtype": args.precision, "data": "synthetic",
                 "config": workload_config(args.n),
                 "roofline": roofline(args.precision, ms_step, n_nodes, args.n),
-                "fp64": fp64, "e2e": e2e, "cpu_baseline": base,
+                "fp64": fp64, "fp16_offset": fp16, "e2e": e2e,
+                "cpu_baseline": base,
                 "gpu_launches": args.steps, "clocks": clocks.summary()}
         line.update(batches)
         if pt:

@@ -122,3 +122,14 @@ def line_fit(x, y):
     res = y - (slope * x + icpt)
     tot = ((y - y.mean()) ** 2).sum()
     return float(slope), float(icpt), float(1 - (res ** 2).sum() / tot) if tot > 0 else 1.0
+
+
+def slab_bulk(rho):
+    """(rho_l, rho_v) of a liquid slab centred in a periodic box along y:
+    medians of the x-averaged profile over the central quarter of the rows
+    and over the quarter farthest from the slab (the box edges)."""
+    prof = rho.mean(axis=1)
+    n = prof.size
+    mid = prof[3 * n // 8:5 * n // 8]
+    far = np.concatenate([prof[:n // 8], prof[n - n // 8:]])
+    return float(np.median(mid)), float(np.median(far))

@@ -78,3 +78,9 @@ def test_line_fit_recovers_a_line():
     x = np.linspace(0.01, 0.1, 8)
     s, c, r2 = obs.line_fit(x, 3.0 * x - 0.5)
     assert abs(s - 3.0) < 1e-12 and abs(c + 0.5) < 1e-12 and r2 == pytest.approx(1.0)
+
+
+def test_slab_bulk_reads_the_plateaus():
+    rho = inputs.slab(16, 256, 0.3, 0.02, 4.0)
+    l, v = obs.slab_bulk(rho)
+    assert abs(l - 0.3) < 1e-9 and abs(v - 0.02) < 1e-9
