@@ -73,10 +73,11 @@ int step_shapes(int *tx, int *ty, int max)
 
 void step_default_shape(int prec, int *tx, int *ty)
 {
-    // fastest measured on GB300 for the 4096^2 workload (lbm_autotune picks
-    // per lattice)
+    // fastest measured on GB300 for the 4096^2 workload in every precision
+    // (lbm_autotune picks per lattice)
+    (void)prec;
     *tx = 32;
-    *ty = prec == P_F64 ? 16 : (prec == P_F16_OFF ? 24 : 32);
+    *ty = 32;
 }
 
 void pt_shape(int prec, int *tx, int *ty)

@@ -497,19 +497,20 @@ __device__ __forceinline__ void step_tile(const Lattice &L, int cur, int X0,
 // and lane 31 carry the same sums for the tile's left and right ring
 // columns; the first and last warps write the bottom and top ring rows.
 // ---------------------------------------------------------------------------
-// Population staging of the TMA paths: per direction a (TX + 4) x TY box
-// from x = X0 + pin_x0(i) (X0 - 4 for the directions an odd step reads from
-// x - 1, X0 otherwise: both 16-byte aligned), so that tile column lx of
-// direction i sits at staged column lx + pin_col(i).
-template <int PARITY>
+// Population staging of the TMA paths: per direction a (TX + PX) x TY box,
+// PX = 16 bytes in elements (the step of a TMA x coordinate), from
+// x = X0 + pin_x0(i): X0 - PX for the directions an odd step reads from
+// x - 1, X0 otherwise.  Tile column lx of direction i then sits at staged
+// column lx + pin_col(i).
+template <int PARITY, int PX>
 __device__ __forceinline__ constexpr int pin_x0(int i)
 {
-    return (PARITY == 1 && ex(i) == 1) ? -4 : 0;
+    return (PARITY == 1 && ex(i) == 1) ? -PX : 0;
 }
-template <int PARITY>
+template <int PARITY, int PX>
 __device__ __forceinline__ constexpr int pin_col(int i)
 {
-    return PARITY == 0 ? 0 : (ex(i) == 1 ? 3 : (ex(i) == -1 ? 1 : 0));
+    return PARITY == 0 ? 0 : (ex(i) == 1 ? PX - 1 : (ex(i) == -1 ? 1 : 0));
 }
 
 // All threads: wait (bounded) for barrier k of the tile's copies (0: the
@@ -528,11 +529,18 @@ __device__ __forceinline__ bool tma_landed(unsigned long long *bar, int k, int *
     return false;
 }
 
-template <class real, int TX, int TY>
+// Shared memory of a TMA tile: the staged populations in their storage
+// type, then density, partial sums / exchange slots and mu in the
+// arithmetic type.
+template <class S, int TX, int TY>
 struct TmaSmem {
-    static constexpr int RP = TX + 8;  // density rows
-    static constexpr int PP = TX + 4;  // population rows
+    using real = typename S::real;
+    using pop_t = typename S::pop_t;
+    static constexpr int PX = 16 / sizeof(pop_t);
+    static constexpr int RP = TX + 8;   // density rows (from X0 - 4)
+    static constexpr int PP = TX + PX;  // population rows
     static constexpr int PLANE = TY * PP;
+    static constexpr size_t PIN_BYTES = sizeof(pop_t) * 8 * PLANE;
     static constexpr int NRHO = (TY + 4) * RP;
     static constexpr int MP = TX + 2, MH = TY + 2;
     static constexpr int NRING = StepSmem<real, TX, TY>::NRING;
@@ -540,11 +548,11 @@ struct TmaSmem {
     static constexpr int NXCH = 2 * (STEP_THREADS / 32) * (TX + 2);
     static constexpr int NSHARE = NRING > NXCH ? NRING : NXCH;  // ring, then exchange
     static constexpr size_t bar_offset =
-        (sizeof(real) * (8 * PLANE + NRHO + NSHARE + NMU) + 15) / 16 * 16;
+        (PIN_BYTES + sizeof(real) * (NRHO + NSHARE + NMU) + 15) / 16 * 16;
     static constexpr size_t bytes = bar_offset + 16;
     static constexpr unsigned tx_rho = sizeof(real) * NRHO;
-    static constexpr unsigned tx_pops = sizeof(real) * 8 * PLANE;
-    static_assert((PLANE * sizeof(real)) % 128 == 0, "TMA destinations");
+    static constexpr unsigned tx_pops = PIN_BYTES;
+    static_assert((PLANE * sizeof(pop_t)) % 128 == 0, "TMA destinations");
 };
 
 // Gradient of the isotropic stencil from a 3 x 3 window w[row][col] (row 0
@@ -573,16 +581,15 @@ __device__ __forceinline__ void step_tile_tma(const Lattice &L, int cur, int X0,
     using real = typename S::real;
     using pop_t = typename S::pop_t;
     using rho_t = typename S::rho_t;
-    using TS = TmaSmem<real, TX, TY>;
+    using TS = TmaSmem<S, TX, TY>;
     static_assert(TX == 32, "lanes map to x");
-    static_assert(sizeof(pop_t) == sizeof(real), "populations staged as stored");
     constexpr int NW = NT / 32, PER = TY / NW;
     static_assert(PER * NW == TY && PER >= 2, "warps own whole row blocks");
     constexpr int RP = TS::RP, PP = TS::PP, PLANE = TS::PLANE, MP = TS::MP, MH = TS::MH;
     constexpr int WR = TX + 4, HR = TY + 4;  // halo geometry of the ring staging
     constexpr int XW = TX + 2;               // exchange slots per warp
-    real *s_pin = reinterpret_cast<real *>(smem_raw);  // [8][TY][PP]
-    real *s_rho = s_pin + 8 * PLANE;                     // [TY + 4][RP]
+    pop_t *s_pin = reinterpret_cast<pop_t *>(smem_raw);            // [8][TY][PP]
+    real *s_rho = reinterpret_cast<real *>(smem_raw + TS::PIN_BYTES);  // [TY + 4][RP]
     real *s_ring = s_rho + TS::NRHO;
     real *s_mu = s_ring + TS::NSHARE;                    // [MH][MP]
     real *s_up = s_ring;                                 // [NW][XW], after step 2
@@ -607,8 +614,8 @@ __device__ __forceinline__ void step_tile_tma(const Lattice &L, int cur, int X0,
         for (int i = 1; i < 9; ++i) {
             const int plane = PARITY == 0 ? i - 1 : opp(i) - 1;
             const int y0 = PARITY == 0 ? Y0 : Y0 - ey(i);
-            tma_load_3d(s_pin + (i - 1) * PLANE, &maps.pops, X0 + pin_x0<PARITY>(i),
-                        y0, plane, &bar[1]);
+            tma_load_3d(s_pin + (i - 1) * PLANE, &maps.pops,
+                        X0 + pin_x0<PARITY, TS::PX>(i), y0, plane, &bar[1]);
         }
     }
     {
@@ -749,7 +756,7 @@ __device__ __forceinline__ void step_tile_tma(const Lattice &L, int cur, int X0,
         real f[9];
 #pragma unroll
         for (int i = 1; i < 9; ++i)
-            f[i] = s_pin[(i - 1) * PLANE + ly * PP + lx + pin_col<PARITY>(i)];
+            f[i] = ld_real(s_pin + (i - 1) * PLANE + ly * PP + lx + pin_col<PARITY, TS::PX>(i));
         const real drho = wr[1][1];
         const real rho = drho + rho_ref;
         real gmx, gmy, grx, gry;
@@ -1047,7 +1054,7 @@ __device__ __forceinline__ void step_tile_tma_pair(const Lattice &L, int cur, in
         for (int i = 1; i < 9; ++i) {
             const int plane = PARITY == 0 ? i - 1 : opp(i) - 1;
             const int y0 = PARITY == 0 ? Y0 : Y0 - ey(i);
-            tma_load_3d(s_pin + (i - 1) * PLANE, &maps.pops, X0 + pin_x0<PARITY>(i),
+            tma_load_3d(s_pin + (i - 1) * PLANE, &maps.pops, X0 + pin_x0<PARITY, 4>(i),
                         y0, plane, &bar[1]);
         }
     }
@@ -1170,7 +1177,7 @@ __device__ __forceinline__ void step_tile_tma_pair(const Lattice &L, int cur, in
         float2 f[9];
 #pragma unroll
         for (int i = 1; i < 9; ++i) {
-            const float *src = s_pin + (i - 1) * PLANE + ly * PP + x0 + pin_col<PARITY>(i);
+            const float *src = s_pin + (i - 1) * PLANE + ly * PP + x0 + pin_col<PARITY, 4>(i);
             if (PARITY == 0 || ex(i) == 0)
                 f[i] = *reinterpret_cast<const float2 *>(src);
             else
@@ -1297,9 +1304,7 @@ struct HasTmaPair {
 // Whether a (precision, tile) pair has the TMA interior path.
 template <class S, int TX, int TY, int NT>
 struct HasTma {
-    static constexpr bool value = TX == 32 && (TY % (NT / 32)) == 0 &&
-                                  sizeof(typename S::pop_t) ==
-                                      sizeof(typename S::real);
+    static constexpr bool value = TX == 32 && (TY % (NT / 32)) == 0;
 };
 
 template <class S, int TX, int TY, int NT, int PARITY>
@@ -1340,7 +1345,7 @@ static cudaError_t launch_shape(const Lattice &L, int parity, int cur,
     constexpr int NT = step_threads<S, TX, TY>();
     const size_t smem_v4 = StepSmem<real, TX, TY>::bytes;
     size_t smem_tma = 0;
-    if constexpr (HasTma<S, TX, TY, NT>::value) smem_tma = TmaSmem<real, TX, TY>::bytes;
+    if constexpr (HasTma<S, TX, TY, NT>::value) smem_tma = TmaSmem<S, TX, TY>::bytes;
     if constexpr (HasTmaPair<S, TX, TY, NT>::value)
         smem_tma = TmaPairSmem<TX, TY, NT>::bytes;
     const size_t smem = smem_v4 > smem_tma ? smem_v4 : smem_tma;

@@ -342,3 +342,33 @@ def test_full_size_sampled_one_step(precision, tol):
         sim.step(96)
         m1 = sim.reduce()[0]
         assert abs(m1 - m0) / m0 < (1e-13 if precision == "f64" else 1e-5)
+
+
+@pytest.mark.parametrize("tile", [(32, 16), (32, 24), (32, 32)])
+def test_fp16_storage_tma_path(tile, monkeypatch):
+    # FP16 storage: interior tiles stage the half populations by TMA; the
+    # same lattice with every tile on the general path (no tensor maps)
+    # does the same FP32 arithmetic on the same half inputs.  The two paths
+    # sum the density hand-over in different orders, and an FP32 last-bit
+    # difference flips the half rounding of a stored g_i = f_i - w_i rho_ref
+    # now and then: one such flip moves rho by ~3e-5 of its largest value.
+    rv, rl = _coexistence("cs")
+    runs = []
+    for no_tma in (False, True):
+        if no_tma:
+            monkeypatch.setenv("CPLBM_NO_TMA", "1")
+        sim, ref, rho = _setup("cs", 330, 200, False, precision="f16_offset",
+                               rho_ref=0.5 * (rv + rl))
+        with sim:
+            sim.set_tile(*tile)
+            sim.init(rho).step(21)
+            runs.append(sim.moments())
+    ref.init_equilibrium(rho).step(21)
+    want = ref.moments()
+    # mu = psi'(rho) - kappa lap(rho) cancels terms ~100x its size, so the
+    # same density differences show ~100x larger in mu
+    for k, tol in (("rho", 5e-4), ("mu", 3e-2)):
+        assert _rel(runs[0][k], runs[1][k]) < tol, (k, _rel(runs[0][k], runs[1][k]))
+    # half populations (eps 4.9e-4 on g_i) against the FP64 oracle
+    for run in runs:
+        assert _rel(run["rho"], want["rho"]) < 2e-3

