@@ -204,10 +204,28 @@ lbm_status ensure_tmp(lbm_ctx *c, size_t bytes)
     return LBM_OK;
 }
 
-size_t ring_elems(const Lattice &L)
+// Elements of the compact partial-sum buffer of class c (ring_index): one
+// column per tile column (L, R), one row per tile row (B, T), one entry per
+// tile (corners), counted for the smallest compiled tile, 32 x 16, so that
+// every tile shape fits.
+size_t ring_elems(const Lattice &L, int c)
 {
-    const size_t a = (size_t)L.nyf * L.pitch, b = (size_t)L.pitch * L.nyf_pad;
-    return a > b ? a : b;
+    const size_t ncx = ((size_t)L.nx + 31) / 32, ncy = ((size_t)L.nyf + 15) / 16;
+    if (c == R_L || c == R_R) return ncx * L.nyf_pad;
+    if (c == R_B || c == R_T) return ncy * L.pitch;
+    return ncy * ncx;
+}
+
+// Queue the zeroing of both generations of partial sums.
+cudaError_t clear_rings(const Lattice &L, cudaStream_t s)
+{
+    const size_t rb = rho_bytes(L.precision);
+    for (int k = 0; k < 2; ++k)
+        for (int r = 0; r < R_COUNT; ++r) {
+            cudaError_t e = cudaMemsetAsync(L.ring[k][r], 0, ring_elems(L, r) * rb, s);
+            if (e != cudaSuccess) return e;
+        }
+    return cudaSuccess;
 }
 
 void free_all(lbm_ctx *c)
@@ -321,7 +339,6 @@ lbm_status lbm_create(const lbm_config *cfg, lbm_ctx **out)
     step_default_shape(L.precision, &L.tx, &L.ty);
 
     const size_t pb = pop_bytes(L.precision), rb = rho_bytes(L.precision);
-    const size_t nring = ring_elems(L);
     lbm_status st = LBM_OK;
     auto alloc = [&](void **p, size_t bytes) {
         if (st != LBM_OK) return;
@@ -335,7 +352,7 @@ lbm_status lbm_create(const lbm_config *cfg, lbm_ctx **out)
     alloc(&L.pops, 8 * (size_t)L.plane * pb);
     for (int k = 0; k < 2; ++k) {
         alloc(&L.rho[k], (size_t)L.plane * rb);
-        for (int r = 0; r < R_COUNT; ++r) alloc(&L.ring[k][r], nring * rb);
+        for (int r = 0; r < R_COUNT; ++r) alloc(&L.ring[k][r], ring_elems(L, r) * rb);
     }
     alloc((void **)&c->d_red, 4 * sizeof(double));
     alloc((void **)&c->d_bad, sizeof(int));
@@ -467,10 +484,8 @@ lbm_status lbm_set_tile(lbm_ctx *c, int tx, int ty)
         Lattice &L = c->L;
         const int p = (int)(c->t & 1);
         CUDA_TRY(c, launch_gather_rho(L, p, L.rho[p ^ 1], c->stream));
-        const size_t rb = rho_bytes(L.precision), nring = ring_elems(L);
-        for (int k = 0; k < 2; ++k)
-            for (int r = 0; r < R_COUNT; ++r)
-                CUDA_TRY(c, cudaMemsetAsync(L.ring[k][r], 0, nring * rb, c->stream));
+        const size_t rb = rho_bytes(L.precision);
+        CUDA_TRY(c, clear_rings(L, c->stream));
         CUDA_TRY(c, cudaMemcpyAsync(L.rho[p], L.rho[p ^ 1], (size_t)L.plane * rb,
                                     cudaMemcpyDeviceToDevice, c->stream));
         CUDA_TRY(c, cudaStreamSynchronize(c->stream));
@@ -495,12 +510,7 @@ lbm_status snapshot(lbm_ctx *c, char *snap, bool save)
         CUDA_TRY(c, cudaMemcpyAsync(snap, L.pops, pb, cudaMemcpyDeviceToDevice,
                                     c->stream));
     } else {
-        const size_t nring = ring_elems(L);
-        for (int k = 0; k < 2; ++k)
-            for (int r = 0; r < R_COUNT; ++r)
-                CUDA_TRY(c, cudaMemsetAsync(L.ring[k][r], 0,
-                                            nring * rho_bytes(L.precision),
-                                            c->stream));
+        CUDA_TRY(c, clear_rings(L, c->stream));
         CUDA_TRY(c, cudaMemcpyAsync(L.pops, snap, pb, cudaMemcpyDeviceToDevice,
                                     c->stream));
         CUDA_TRY(c, cudaMemcpyAsync(L.rho[p], snap + pb, rb,
@@ -646,12 +656,10 @@ lbm_status lbm_init(lbm_ctx *c, const double *rho, const double *ux,
             duy = t2;
         }
     }
-    const size_t rb = rho_bytes(L.precision), nring = ring_elems(L);
-    for (int k = 0; k < 2; ++k) {
+    const size_t rb = rho_bytes(L.precision);
+    for (int k = 0; k < 2; ++k)
         CUDA_TRY(c, cudaMemsetAsync(L.rho[k], 0, (size_t)L.plane * rb, c->stream));
-        for (int r = 0; r < R_COUNT; ++r)
-            CUDA_TRY(c, cudaMemsetAsync(L.ring[k][r], 0, nring * rb, c->stream));
-    }
+    CUDA_TRY(c, clear_rings(L, c->stream));
     CUDA_TRY(c, cudaMemsetAsync(c->d_bad, 0, sizeof(int), c->stream));
     CUDA_TRY(c, launch_init(L, drho, dux, duy, c->d_bad, c->stream));
     // the reduction snapshot starts at the initial density
@@ -836,11 +844,7 @@ lbm_status lbm_set_state(lbm_ctx *c, const void *buf, size_t bytes)
     const size_t pbytes = 8 * (size_t)L.plane * pop_bytes(L.precision);
     const size_t rbytes = (size_t)L.plane * rho_bytes(L.precision);
     const int p = (int)(h.t & 1);
-    const size_t nring = ring_elems(L);
-    for (int k = 0; k < 2; ++k)
-        for (int r = 0; r < R_COUNT; ++r)
-            CUDA_TRY(c, cudaMemsetAsync(L.ring[k][r], 0, nring * rho_bytes(L.precision),
-                                        c->stream));
+    CUDA_TRY(c, clear_rings(L, c->stream));
     CUDA_TRY(c, cudaMemcpyAsync(L.pops, in, pbytes, cudaMemcpyHostToDevice, c->stream));
     CUDA_TRY(c, cudaMemcpyAsync(L.rho[p], in + pbytes, rbytes,
                                 cudaMemcpyHostToDevice, c->stream));

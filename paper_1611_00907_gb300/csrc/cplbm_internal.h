@@ -61,9 +61,15 @@ template <class T> struct Consts {
 //                           node on a tile's edge holds only the part
 //                           summed inside its own tile;
 //  ring[k][c]               k = 0, 1: the partial sums of class c written
-//                           by the neighbouring tile.  Classes L and R are
-//                           stored column-major [pitch][nyf_pad] so a tile
-//                           column is contiguous; the others row-major.
+//                           by the neighbouring tile, compact: a class
+//                           holds one entry per tile along the axis it
+//                           crosses (ring_index in device_common.cuh).
+//                           L, R: [ceil(nx / 32)][nyf_pad], one column per
+//                           tile column; B, T: [ceil(nyf / 16)][pitch], one
+//                           row per tile row; corners: [ceil(nyf / 16)]
+//                           [ceil(nx / 32)].  The strides fit the smallest
+//                           compiled tile (32 x 16), so every tile shape
+//                           uses the same buffers.
 // nyf is the number of fluid rows: ny - 2 with walls, ny otherwise; fluid
 // row r is lattice row r + 1 with walls.
 struct Lattice {

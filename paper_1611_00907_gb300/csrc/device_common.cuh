@@ -239,10 +239,15 @@ __device__ __forceinline__ long long fidx(const Lattice &L, int r, int x)
 {
     return (long long)r * L.pitch + x;
 }
-// Column-major index used by the L / R ring classes.
-__device__ __forceinline__ long long cidx(const Lattice &L, int r, int x)
+// Index of the partial sum of class c for the receiving node (r, x), whose
+// tile is (bx, by): classes L and R keep one column per tile column, B and
+// T one row per tile row, the corners one entry per tile.
+__device__ __forceinline__ long long ring_index(const Lattice &L, int c, int bx,
+                                                int by, int r, int x)
 {
-    return (long long)x * L.nyf_pad + r;
+    if (c == R_L || c == R_R) return (long long)bx * L.nyf_pad + r;
+    if (c == R_B || c == R_T) return (long long)by * L.pitch + x;
+    return (long long)by * ((L.nx + 31) >> 5) + bx;
 }
 
 // Row r + dy of a fluid node; with walls, -1 / nyf mean the solid rows.
@@ -305,17 +310,18 @@ __device__ __forceinline__ typename S::real load_rho_stored(const Lattice &L,
     const bool above = ly == wy - 1 && !(L.walls && r == L.nyf - 1);
     if (left | right | below | above) {
         rt *const *ring = (rt *const *)L.ring[cur];
-        if (left) v += (real)ring[R_L][cidx(L, r, x)];
-        if (right) v += (real)ring[R_R][cidx(L, r, x)];
+        auto at = [&](int c) { return ring[c][ring_index(L, c, bx, by, r, x)]; };
+        if (left) v += (real)at(R_L);
+        if (right) v += (real)at(R_R);
         if (below) {
-            v += (real)ring[R_B][fidx(L, r, x)];
-            if (left) v += (real)ring[R_BL][fidx(L, r, x)];
-            if (right) v += (real)ring[R_BR][fidx(L, r, x)];
+            v += (real)at(R_B);
+            if (left) v += (real)at(R_BL);
+            if (right) v += (real)at(R_BR);
         }
         if (above) {
-            v += (real)ring[R_T][fidx(L, r, x)];
-            if (left) v += (real)ring[R_TL][fidx(L, r, x)];
-            if (right) v += (real)ring[R_TR][fidx(L, r, x)];
+            v += (real)at(R_T);
+            if (left) v += (real)at(R_TL);
+            if (right) v += (real)at(R_TR);
         }
     }
     return v;

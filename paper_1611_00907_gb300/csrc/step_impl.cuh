@@ -65,6 +65,8 @@ __device__ __forceinline__ int col_index(int l)
 {
     return l == 1 ? 0 : l == 2 ? 1 : l == T + 1 ? 2 : l == T + 2 ? 3 : -1;
 }
+// Tile of halo edge index ci (as edge_col) relative to this tile.
+__device__ __forceinline__ int edge_tile(int ci) { return ci == 0 ? -1 : ci == 3 ? 1 : 0; }
 
 // Issue the asynchronous loads of an interior tile's stored density and of
 // the partial sums its halo needs.
@@ -87,27 +89,30 @@ __device__ __forceinline__ void issue_rho_interior(const Lattice &L, int cur,
         cp_async<sizeof(rt)>(&s_rho[k], R + fi);
     }
     for (int p = threadIdx.x; p < SM::NRING; p += NT) {
-        int c, lx, ly;
+        int c, lx, ly, dbx = 0, dby = 0;  // receiving tile - this tile
         if (p < 4 * HR) {  // edge columns: class L or R, column-major storage
             const int ci = p / HR;
+            dbx = edge_tile(ci);
             ly = p % HR;
             lx = edge_col<TX>(ci);
             c = col_is_left(ci) ? R_L : R_R;
         } else if (p < 4 * HR + 4 * WR) {  // edge rows: class B or T
             const int q = p - 4 * HR, ri = q / WR;
+            dby = edge_tile(ri);
             lx = q % WR;
             ly = edge_col<TY>(ri);
             c = row_is_below(ri) ? R_B : R_T;
         } else {  // the 16 crossings: corner classes
             const int q = p - 4 * HR - 4 * WR, ci = q / 4, ri = q % 4;
+            dbx = edge_tile(ci);
+            dby = edge_tile(ri);
             lx = edge_col<TX>(ci);
             ly = edge_col<TY>(ri);
             c = row_is_below(ri) ? (col_is_left(ci) ? R_BL : R_BR)
                                  : (col_is_left(ci) ? R_TL : R_TR);
         }
         const int x = X0 + lx - 2, r = Y0 + ly - 2;
-        const long long idx =
-            (c == R_L || c == R_R) ? cidx(L, r, x) : fidx(L, r, x);
+        const long long idx = ring_index(L, c, X0 / TX + dbx, Y0 / TY + dby, r, x);
         cp_async<sizeof(rt)>(&s_ring[p], ring[c] + idx);
     }
 }
@@ -469,9 +474,7 @@ __device__ __forceinline__ void step_tile(const Lattice &L, int cur, int X0,
         const int x = INTERIOR ? X0 + ox : wrapi(X0 + ox, L.nx);
         const int rw = INTERIOR ? r : row_wrap(L, r);
         const int c = ring_class(ox, oy, wx, wy);
-        const long long idx =
-            (c == R_L || c == R_R) ? cidx(L, rw, x) : fidx(L, rw, x);
-        ring[c][idx] = (rho_t)s;
+        ring[c][ring_index(L, c, x / TX, rw / TY, rw, x)] = (rho_t)s;
     }
 }
 
@@ -622,27 +625,30 @@ __device__ __forceinline__ void step_tile_tma(const Lattice &L, int cur, int X0,
         using rt = rho_t;
         rt *const *ring = (rt *const *)L.ring[cur];
         for (int p = threadIdx.x; p < TS::NRING; p += NT) {
-            int c, lx, ly;
+            int c, lx, ly, dbx = 0, dby = 0;  // receiving tile - this tile
             if (p < 4 * HR) {
                 const int ci = p / HR;
+                dbx = edge_tile(ci);
                 ly = p % HR;
                 lx = edge_col<TX>(ci);
                 c = col_is_left(ci) ? R_L : R_R;
             } else if (p < 4 * HR + 4 * WR) {
                 const int q = p - 4 * HR, ri = q / WR;
+                dby = edge_tile(ri);
                 lx = q % WR;
                 ly = edge_col<TY>(ri);
                 c = row_is_below(ri) ? R_B : R_T;
             } else {
                 const int q = p - 4 * HR - 4 * WR, ci = q / 4, ri = q % 4;
+                dbx = edge_tile(ci);
+                dby = edge_tile(ri);
                 lx = edge_col<TX>(ci);
                 ly = edge_col<TY>(ri);
                 c = row_is_below(ri) ? (col_is_left(ci) ? R_BL : R_BR)
                                      : (col_is_left(ci) ? R_TL : R_TR);
             }
             const int x = X0 + lx - 2, r = Y0 + ly - 2;
-            const long long idx =
-                (c == R_L || c == R_R) ? cidx(L, r, x) : fidx(L, r, x);
+            const long long idx = ring_index(L, c, X0 / TX + dbx, Y0 / TY + dby, r, x);
             cp_async<sizeof(rt)>(&s_ring[p], ring[c] + idx);
         }
         cp_async_commit();
@@ -743,6 +749,9 @@ __device__ __forceinline__ void step_tile_tma(const Lattice &L, int cur, int X0,
     const int slot_c = TX + (lane == 31);        // exchange slot of a column
     const int xc = lane == 0 ? X0 - 1 : X0 + TX;  // ring column of the lane
     const int cls_c = lane == 0 ? R_R : R_L;
+    // this tile, and the tile of the ring column a lane feeds (classes L and
+    // R share one index layout)
+    const int bx = X0 / TX, by = Y0 / TY, bxc = lane == 0 ? bx - 1 : bx + 1;
     const bool col_lane = lane == 0 || lane == 31;
     pop_t *Arow = A + (long long)(Y0 + ly0) * L.pitch + X0 + lx;
 #pragma unroll
@@ -800,7 +809,7 @@ __device__ __forceinline__ void step_tile_tma(const Lattice &L, int cur, int X0,
                 first_c = done_c;
             } else {
                 Rn[(long long)(Y0 + ly - 1) * L.pitch + X0 + lx] = (rho_t)done;
-                if (col_lane) ring[cls_c][cidx(L, Y0 + ly - 1, xc)] = (rho_t)done_c;
+                if (col_lane) ring[cls_c][ring_index(L, R_L, bxc, by, Y0 + ly - 1, xc)] = (rho_t)done_c;
             }
             pend = same + up_prev;
             pend_c = same_c + up_prev_c;
@@ -826,25 +835,25 @@ __device__ __forceinline__ void step_tile_tma(const Lattice &L, int cur, int X0,
             top_c += s_down[(warp + 1) * XW + slot_c];
         }
         Rn[(long long)(Y0 + ly0 + PER - 1) * L.pitch + X0 + lx] = (rho_t)top;
-        if (col_lane) ring[cls_c][cidx(L, Y0 + ly0 + PER - 1, xc)] = (rho_t)top_c;
+        if (col_lane) ring[cls_c][ring_index(L, R_L, bxc, by, Y0 + ly0 + PER - 1, xc)] = (rho_t)top_c;
         // first row: add the warp below's last-row "up"
         if (warp > 0) {
             first += s_up[(warp - 1) * XW + lane];
             first_c += s_up[(warp - 1) * XW + slot_c];
         }
         Rn[(long long)(Y0 + ly0) * L.pitch + X0 + lx] = (rho_t)first;
-        if (col_lane) ring[cls_c][cidx(L, Y0 + ly0, xc)] = (rho_t)first_c;
+        if (col_lane) ring[cls_c][ring_index(L, R_L, bxc, by, Y0 + ly0, xc)] = (rho_t)first_c;
     }
     // ring rows below and above the tile, with their corners
     if (warp == 0) {
-        ring[R_T][fidx(L, Y0 - 1, X0 + lx)] = (rho_t)s_down[lane];
-        if (lane == 0) ring[R_TR][fidx(L, Y0 - 1, X0 - 1)] = (rho_t)s_down[TX];
-        if (lane == 31) ring[R_TL][fidx(L, Y0 - 1, X0 + TX)] = (rho_t)s_down[TX + 1];
+        ring[R_T][ring_index(L, R_T, bx, by - 1, Y0 - 1, X0 + lx)] = (rho_t)s_down[lane];
+        if (lane == 0) ring[R_TR][ring_index(L, R_TR, bx - 1, by - 1, Y0 - 1, X0 - 1)] = (rho_t)s_down[TX];
+        if (lane == 31) ring[R_TL][ring_index(L, R_TL, bx + 1, by - 1, Y0 - 1, X0 + TX)] = (rho_t)s_down[TX + 1];
     }
     if (warp == NW - 1) {
-        ring[R_B][fidx(L, Y0 + TY, X0 + lx)] = (rho_t)up_prev;
-        if (lane == 0) ring[R_BR][fidx(L, Y0 + TY, X0 - 1)] = (rho_t)up_prev_c;
-        if (lane == 31) ring[R_BL][fidx(L, Y0 + TY, X0 + TX)] = (rho_t)up_prev_c;
+        ring[R_B][ring_index(L, R_B, bx, by + 1, Y0 + TY, X0 + lx)] = (rho_t)up_prev;
+        if (lane == 0) ring[R_BR][ring_index(L, R_BR, bx - 1, by + 1, Y0 + TY, X0 - 1)] = (rho_t)up_prev_c;
+        if (lane == 31) ring[R_BL][ring_index(L, R_BL, bx + 1, by + 1, Y0 + TY, X0 + TX)] = (rho_t)up_prev_c;
     }
 }
 
@@ -1061,27 +1070,30 @@ __device__ __forceinline__ void step_tile_tma_pair(const Lattice &L, int cur, in
     {
         rho_t *const *ring = (rho_t *const *)L.ring[cur];
         for (int p = threadIdx.x; p < TS::NRING; p += NT) {
-            int c, lx, ly;
+            int c, lx, ly, dbx = 0, dby = 0;  // receiving tile - this tile
             if (p < 4 * HR) {
                 const int ci = p / HR;
+                dbx = edge_tile(ci);
                 ly = p % HR;
                 lx = edge_col<TX>(ci);
                 c = col_is_left(ci) ? R_L : R_R;
             } else if (p < 4 * HR + 4 * WR) {
                 const int q = p - 4 * HR, ri = q / WR;
+                dby = edge_tile(ri);
                 lx = q % WR;
                 ly = edge_col<TY>(ri);
                 c = row_is_below(ri) ? R_B : R_T;
             } else {
                 const int q = p - 4 * HR - 4 * WR, ci = q / 4, ri = q % 4;
+                dbx = edge_tile(ci);
+                dby = edge_tile(ri);
                 lx = edge_col<TX>(ci);
                 ly = edge_col<TY>(ri);
                 c = row_is_below(ri) ? (col_is_left(ci) ? R_BL : R_BR)
                                      : (col_is_left(ci) ? R_TL : R_TR);
             }
             const int x = X0 + lx - 2, r = Y0 + ly - 2;
-            const long long idx =
-                (c == R_L || c == R_R) ? cidx(L, r, x) : fidx(L, r, x);
+            const long long idx = ring_index(L, c, X0 / TX + dbx, Y0 / TY + dby, r, x);
             cp_async<sizeof(rho_t)>(&s_ring[p], ring[c] + idx);
         }
         cp_async_commit();
@@ -1167,6 +1179,9 @@ __device__ __forceinline__ void step_tile_tma_pair(const Lattice &L, int cur, in
     const int slot_c = TX + (lane == 31);        // exchange slot of a column
     const int xc = lane == 0 ? X0 - 1 : X0 + TX;  // ring column of the lane
     const int cls_c = lane == 0 ? R_R : R_L;
+    // this tile, and the tile of the ring column a lane feeds (classes L and
+    // R share one index layout)
+    const int bx = X0 / TX, by = Y0 / TY, bxc = lane == 0 ? bx - 1 : bx + 1;
     const bool col_lane = lane == 0 || lane == 31;
     float *Arow = A + (long long)(Y0 + ly0) * L.pitch + X0 + x0;
 #pragma unroll
@@ -1237,7 +1252,7 @@ __device__ __forceinline__ void step_tile_tma_pair(const Lattice &L, int cur, in
             } else {
                 *reinterpret_cast<float2 *>(Rn + (long long)(Y0 + ly - 1) * L.pitch +
                                             X0 + x0) = done;
-                if (col_lane) ring[cls_c][cidx(L, Y0 + ly - 1, xc)] = done_c;
+                if (col_lane) ring[cls_c][ring_index(L, R_L, bxc, by, Y0 + ly - 1, xc)] = done_c;
             }
             pend = padd(same, up_prev);
             pend_c = same_c + up_prev_c;
@@ -1261,25 +1276,25 @@ __device__ __forceinline__ void step_tile_tma_pair(const Lattice &L, int cur, in
         }
         *reinterpret_cast<float2 *>(Rn + (long long)(Y0 + ly0 + PER - 1) * L.pitch + X0 +
                                     x0) = top;
-        if (col_lane) ring[cls_c][cidx(L, Y0 + ly0 + PER - 1, xc)] = top_c;
+        if (col_lane) ring[cls_c][ring_index(L, R_L, bxc, by, Y0 + ly0 + PER - 1, xc)] = top_c;
         if (warp > 0) {
             first = padd(first, *reinterpret_cast<const float2 *>(s_up + (warp - 1) * XW + x0));
             first_c += s_up[(warp - 1) * XW + slot_c];
         }
         *reinterpret_cast<float2 *>(Rn + (long long)(Y0 + ly0) * L.pitch + X0 + x0) = first;
-        if (col_lane) ring[cls_c][cidx(L, Y0 + ly0, xc)] = first_c;
+        if (col_lane) ring[cls_c][ring_index(L, R_L, bxc, by, Y0 + ly0, xc)] = first_c;
     }
     // ring rows below and above the tile, with their corners
     if (warp == 0) {
-        *reinterpret_cast<float2 *>(ring[R_T] + fidx(L, Y0 - 1, X0 + x0)) =
+        *reinterpret_cast<float2 *>(ring[R_T] + ring_index(L, R_T, bx, by - 1, Y0 - 1, X0 + x0)) =
             *reinterpret_cast<const float2 *>(s_down + x0);
-        if (lane == 0) ring[R_TR][fidx(L, Y0 - 1, X0 - 1)] = s_down[TX];
-        if (lane == 31) ring[R_TL][fidx(L, Y0 - 1, X0 + TX)] = s_down[TX + 1];
+        if (lane == 0) ring[R_TR][ring_index(L, R_TR, bx - 1, by - 1, Y0 - 1, X0 - 1)] = s_down[TX];
+        if (lane == 31) ring[R_TL][ring_index(L, R_TL, bx + 1, by - 1, Y0 - 1, X0 + TX)] = s_down[TX + 1];
     }
     if (warp == NW - 1) {
-        *reinterpret_cast<float2 *>(ring[R_B] + fidx(L, Y0 + TY, X0 + x0)) = up_prev;
-        if (lane == 0) ring[R_BR][fidx(L, Y0 + TY, X0 - 1)] = up_prev_c;
-        if (lane == 31) ring[R_BL][fidx(L, Y0 + TY, X0 + TX)] = up_prev_c;
+        *reinterpret_cast<float2 *>(ring[R_B] + ring_index(L, R_B, bx, by + 1, Y0 + TY, X0 + x0)) = up_prev;
+        if (lane == 0) ring[R_BR][ring_index(L, R_BR, bx - 1, by + 1, Y0 + TY, X0 - 1)] = up_prev_c;
+        if (lane == 31) ring[R_BL][ring_index(L, R_BL, bx + 1, by + 1, Y0 + TY, X0 + TX)] = up_prev_c;
     }
 }
 
