@@ -243,8 +243,9 @@ def batch_specs(which):
     if which == "uneven":
         specs = inputs.uneven_batch(256)
     else:
+        # mu_s over mu_coex +- 0.25: the contact angle from about 0 to 180 deg
         _, _, mc = eos_coexistence("vdw", 9 / 49, 2 / 21, 1.0, 0.85)
-        specs = inputs.wetting_sweep(32, mu_coex=mc)
+        specs = inputs.wetting_sweep(32, mu_coex=mc, mu_span=0.5)
     fields = []
     for sp in specs:
         rv, rl, _ = eos_coexistence(sp["eos"], sp["a"], sp["b"], 1.0, sp["Tr"],
@@ -422,6 +423,21 @@ def measure_wetting_angles(steps):
     return out
 
 
+def measure_slab64(steps):
+    """The flat CS slab of the plain method (64 x 64 periodic, T/T_c 0.85,
+    kappa 0.5, tau 1, tanh width 4 at the Maxwell densities, FP64): bulk
+    densities after `steps` steps against the Maxwell construction."""
+    from paper_1611_00907_gb300 import eos_coexistence, inputs
+    from paper_1611_00907_gb300 import observables as obs
+    rv, rl, _ = eos_coexistence("cs", 1.0, 4.0, 1.0, 0.85)
+    spec = dict(nx=64, ny=64, eos="cs", a=1.0, b=4.0, Tr=0.85, tau=1.0, kappa=0.5)
+    ms, rhos, finite = _run_batch([spec], [inputs.slab(64, 64, rl, rv, 4.0)], "f64", steps)
+    l, v = obs.slab_bulk(rhos[0]) if finite[0] else (float("nan"),) * 2
+    return {"lattice": [64, 64], "steps": steps, "precision": "f64",
+            "rho_l": l, "rho_v": v, "maxwell": [rv, rl],
+            "rel_err_vs_maxwell": [v / rv - 1, l / rl - 1]}
+
+
 # Fig. 1: coexistence curves of flat interfaces against the Maxwell
 # construction (Sec. III, V): (label, EOS, a, b, omega, kappa, tau)
 FIG1_EOS = (("pr_water", "pr", 2 / 49, 2 / 21, 0.344, 0.01, 1.3),
@@ -506,11 +522,22 @@ def cpu_baseline(budget_s=15.0):
         L.step(5)
         steps += 5
     dt = time.perf_counter() - t
+    # the same oracle on one core, a shorter sample
     oracle.set_threads(1)
+    m = 128
+    L1 = oracle.Lattice(m, m, e, 1.0, 0.5)
+    L1.init_equilibrium(inputs.spinodal_noise(m, m, rc, 0.01, seed=1))
+    s1, t1 = 0, time.perf_counter()
+    while time.perf_counter() - t1 < budget_s / 5:
+        L1.step(5)
+        s1 += 5
+    dt1 = time.perf_counter() - t1
     return {"value": n * n * steps / dt / 1e6, "unit": "MLUPS",
             "cores": cores, "kind": "oracle",
             "sample": "%dx%d CS spinodal, %d steps, FP64 C oracle" % (
-                n, n, steps)}
+                n, n, steps),
+            "single_core_value": m * m * s1 / dt1 / 1e6,
+            "single_core_sample": "%dx%d, %d steps, 1 thread" % (m, m, s1)}
 
 
 def roofline(precision, ms_per_step, n_nodes, n_side=N_SIDE):
@@ -752,6 +779,7 @@ def main():
             3 * args.physics_steps // 2)
         physics["coexistence_curves"] = measure_coexistence_curves(
             args.physics_steps)
+        physics["slab_64"] = measure_slab64(args.physics_steps // 4)
 
     base = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:

@@ -57,11 +57,13 @@ def contact_angle(rho):
     (extrapolated from the first two fluid rows) and the apex height H
     above it (Sec. V):
     R = (4 H^2 + L^2) / (8 H), tan(theta) = L / (2 (R - H)).  A drop no
-    longer touching the wall gives 180."""
+    longer touching the wall gives 180, liquid covering the whole wall 0."""
     rho_l, rho_v = bulk_densities(rho)
     mid = 0.5 * (rho_l + rho_v)
     if not (rho[1] > mid).any():
         return 180.0 if (rho[1:-1] > mid).any() else float("nan")
+    if (rho[1] > mid).all():
+        return 0.0                     # a film over the whole wall
     cx = drop_column(rho)
     chords = []
     for row in (rho[1], rho[2]):

@@ -162,7 +162,8 @@ def build_dataset(n, nx, ny, steps, seed, stream=None):
         if not np.isfinite(rho).all():
             continue
         m = obs.measure(rho)
-        if all(np.isfinite(v) for v in m.values()) and m["theta"] < 179.0:
+        # caps only: no film (0) and no drop that left the wall (180)
+        if all(np.isfinite(v) for v in m.values()) and 0.0 < m["theta"] < 179.0:
             keep.append(c)
             meas.append(m)
     return keep, features(keep), targets(keep, meas)

@@ -84,3 +84,10 @@ def test_slab_bulk_reads_the_plateaus():
     rho = inputs.slab(16, 256, 0.3, 0.02, 4.0)
     l, v = obs.slab_bulk(rho)
     assert abs(l - 0.3) < 1e-9 and abs(v - 0.02) < 1e-9
+
+
+def test_film_over_the_wall_is_complete_wetting():
+    nx, ny = 128, 64
+    yy = np.mgrid[0:ny, 0:nx][0]
+    rho = np.where(yy < 10, 2.0, 0.05)
+    assert obs.contact_angle(rho) == 0.0
