@@ -438,6 +438,33 @@ def measure_slab64(steps):
             "rel_err_vs_maxwell": [v / rv - 1, l / rl - 1]}
 
 
+# Fig. 2 (Sec. V): the paper's printed (surface chemical potential, contact
+# angle) pairs for RKS at T/T_c 0.8, kappa 0.01, tau 1.3
+FIG2 = ((-0.23, 30.0), (-0.13, 60.0), (0.0, 105.0), (0.09, 135.0),
+        (0.15, 160.0), (0.18, 180.0))
+
+
+def measure_fig2(steps):
+    """Fig. 2 at the paper's size (500 x 200, walls, drop radius 50 on the
+    bottom wall), one FP64 batch of the six surface chemical potentials:
+    measured contact angle beside the printed one."""
+    from paper_1611_00907_gb300 import eos_coexistence, inputs
+    from paper_1611_00907_gb300 import observables as obs
+    a, b = 2 / 49, 2 / 21
+    rv, rl, _ = eos_coexistence("rks", a, b, 1.0, 0.8, 0.344)
+    specs = [dict(nx=500, ny=200, walls=True, eos="rks", a=a, b=b, Tr=0.8,
+                  omega=0.344, tau=1.3, kappa=0.01, mu_bottom=cp) for cp, _ in FIG2]
+    fields = [inputs.wall_drop(500, 200, 50, rl, rv, 2.0) for _ in FIG2]
+    ms, rhos, finite = _run_batch(specs, fields, "f64", steps)
+    rows = []
+    for (cp, printed), rho in zip(FIG2, rhos):
+        th = obs.contact_angle(rho) if rho is not None else float("nan")
+        rows.append({"mu_s": cp, "theta_printed": printed, "theta": th,
+                     "diff": th - printed})
+    return {"lattice": [500, 200], "steps": steps, "precision": "f64",
+            "seconds": ms * 1e-3, "rows": rows}
+
+
 # Fig. 1: coexistence curves of flat interfaces against the Maxwell
 # construction (Sec. III, V): (label, EOS, a, b, omega, kappa, tau)
 FIG1_EOS = (("pr_water", "pr", 2 / 49, 2 / 21, 0.344, 0.01, 1.3),
@@ -780,6 +807,7 @@ def main():
         physics["coexistence_curves"] = measure_coexistence_curves(
             args.physics_steps)
         physics["slab_64"] = measure_slab64(args.physics_steps // 4)
+        physics["fig2_contact_angles"] = measure_fig2(args.physics_steps)
 
     base = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
