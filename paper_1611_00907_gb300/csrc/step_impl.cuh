@@ -532,6 +532,98 @@ __device__ __forceinline__ bool tma_landed(unsigned long long *bar, int k, int *
     return false;
 }
 
+// Partial sums of an interior tile's halo edges, staged for the TMA paths.
+// In the compact ring layout each of the four halo edge columns is one
+// contiguous run of a class's column (rows Y0 - 4 .. Y0 + TY + 3) and each
+// of the four edge rows one run of a class's row (columns X0 - 4 ..
+// X0 + TX + 3), both 16-byte aligned, so thread 0 copies them whole with
+// cp.async.bulk on the density's mbarrier; the 16 corner entries come by
+// per-element cp.async.  Staged: [4][CL] columns (halo row ly at ly + 2),
+// [4][RL] rows (halo column lx at lx + 2), [16] corners (ci * 4 + ri).
+template <class rt, int TX, int TY>
+struct RingStage {
+    static constexpr int CL = TY + 8, RL = TX + 8;
+    static constexpr int NCOL = 4 * CL, NROW = 4 * RL, N = NCOL + NROW + 16;
+    static constexpr unsigned bulk_bytes = sizeof(rt) * (NCOL + NROW);
+    static_assert((CL * sizeof(rt)) % 16 == 0 && (RL * sizeof(rt)) % 16 == 0,
+                  "bulk copies are whole 16-byte units");
+};
+
+__device__ __forceinline__ void bulk_load(void *dst, const void *src, unsigned bytes,
+                                          unsigned long long *bar)
+{
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes"
+        " [%0], [%1], %2, [%3];\n" ::"r"(smem_addr(dst)),
+        "l"(reinterpret_cast<unsigned long long>(src)), "r"(bytes), "r"(smem_addr(bar))
+        : "memory");
+}
+
+// Thread 0 issues the eight bulk copies (the caller has added
+// RingStage::bulk_bytes to bar's expected transactions); threads 0..15 the
+// corner entries, committed as one cp.async group.
+template <class rt, int TX, int TY>
+__device__ __forceinline__ void stage_ring(const Lattice &L, int cur, int X0, int Y0,
+                                           rt *s_ring, unsigned long long *bar)
+{
+    using RS = RingStage<rt, TX, TY>;
+    rt *const *ring = (rt *const *)L.ring[cur];
+    const int bx = X0 / TX, by = Y0 / TY;
+    if (threadIdx.x == 0) {
+#pragma unroll
+        for (int ci = 0; ci < 4; ++ci) {
+            const int c = col_is_left(ci) ? R_L : R_R;
+            bulk_load(s_ring + ci * RS::CL,
+                      ring[c] + ring_index(L, c, bx + edge_tile(ci), by, Y0 - 4, X0),
+                      RS::CL * sizeof(rt), bar);
+        }
+#pragma unroll
+        for (int ri = 0; ri < 4; ++ri) {
+            const int c = row_is_below(ri) ? R_B : R_T;
+            bulk_load(s_ring + RS::NCOL + ri * RS::RL,
+                      ring[c] + ring_index(L, c, bx, by + edge_tile(ri), Y0, X0 - 4),
+                      RS::RL * sizeof(rt), bar);
+        }
+    }
+    if (threadIdx.x < 16) {
+        const int ci = threadIdx.x / 4, ri = threadIdx.x % 4;
+        const int c = row_is_below(ri) ? (col_is_left(ci) ? R_BL : R_BR)
+                                       : (col_is_left(ci) ? R_TL : R_TR);
+        cp_async<sizeof(rt)>(s_ring + RS::NCOL + RS::NROW + threadIdx.x,
+                             ring[c] + ring_index(L, c, bx + edge_tile(ci),
+                                                  by + edge_tile(ri), 0, 0));
+    }
+    cp_async_commit();
+}
+
+// Add the staged partial sums to the halo's tile-edge nodes of s_rho (rows
+// of pitch RP, halo node (lx, ly) at column lx + 2), in the order of
+// load_rho_stored.  Items 0 .. 4 HR - 1 take the four edge columns whole,
+// crossings with the edge rows included; the rest take the edge rows
+// without those crossings (halo columns 0, 3 .. TX, TX + 3).
+template <class real, int TX, int TY, int NT, int RP>
+__device__ __forceinline__ void combine_ring(real *s_rho, const real *s_ring)
+{
+    using RS = RingStage<real, TX, TY>;
+    constexpr int HR = TY + 4, NC = 4 * HR, NI = NC + 4 * TX;
+    for (int q = threadIdx.x; q < NI; q += NT) {
+        if (q < NC) {
+            const int ci = q / HR, ly = q - ci * HR, lx = edge_col<TX>(ci);
+            const int ri = col_index<TY>(ly);
+            real v = s_rho[ly * RP + lx + 2] + s_ring[ci * RS::CL + ly + 2];
+            if (ri >= 0)
+                v = (v + s_ring[RS::NCOL + ri * RS::RL + lx + 2]) +
+                    s_ring[RS::NCOL + RS::NROW + ci * 4 + ri];
+            s_rho[ly * RP + lx + 2] = v;
+        } else {
+            const int t = q - NC, ri = t / TX, k = t - ri * TX;
+            const int lx = k == 0 ? 0 : (k == TX - 1 ? TX + 3 : k + 2);
+            const int ly = edge_col<TY>(ri);
+            s_rho[ly * RP + lx + 2] += s_ring[RS::NCOL + ri * RS::RL + lx + 2];
+        }
+    }
+}
+
 // Shared memory of a TMA tile: the staged populations in their storage
 // type, then density, partial sums / exchange slots and mu in the
 // arithmetic type.
@@ -546,7 +638,7 @@ struct TmaSmem {
     static constexpr size_t PIN_BYTES = sizeof(pop_t) * 8 * PLANE;
     static constexpr int NRHO = (TY + 4) * RP;
     static constexpr int MP = TX + 2, MH = TY + 2;
-    static constexpr int NRING = StepSmem<real, TX, TY>::NRING;
+    static constexpr int NRING = RingStage<real, TX, TY>::N;
     static constexpr int NMU = MP * MH;
     static constexpr int NXCH = 2 * (STEP_THREADS / 32) * (TX + 2);
     static constexpr int NSHARE = NRING > NXCH ? NRING : NXCH;  // ring, then exchange
@@ -610,7 +702,7 @@ __device__ __forceinline__ void step_tile_tma(const Lattice &L, int cur, int X0,
     }
     __syncthreads();
     if (threadIdx.x == 0) {
-        mbar_expect_tx(&bar[0], TS::tx_rho);
+        mbar_expect_tx(&bar[0], TS::tx_rho + RingStage<real, TX, TY>::bulk_bytes);
         tma_load_2d(s_rho, &maps.rho[cur], X0 - 4, Y0 - 2, &bar[0]);
         mbar_expect_tx(&bar[1], TS::tx_pops);
 #pragma unroll
@@ -621,64 +713,14 @@ __device__ __forceinline__ void step_tile_tma(const Lattice &L, int cur, int X0,
                         X0 + pin_x0<PARITY, TS::PX>(i), y0, plane, &bar[1]);
         }
     }
-    {
-        using rt = rho_t;
-        rt *const *ring = (rt *const *)L.ring[cur];
-        for (int p = threadIdx.x; p < TS::NRING; p += NT) {
-            int c, lx, ly, dbx = 0, dby = 0;  // receiving tile - this tile
-            if (p < 4 * HR) {
-                const int ci = p / HR;
-                dbx = edge_tile(ci);
-                ly = p % HR;
-                lx = edge_col<TX>(ci);
-                c = col_is_left(ci) ? R_L : R_R;
-            } else if (p < 4 * HR + 4 * WR) {
-                const int q = p - 4 * HR, ri = q / WR;
-                dby = edge_tile(ri);
-                lx = q % WR;
-                ly = edge_col<TY>(ri);
-                c = row_is_below(ri) ? R_B : R_T;
-            } else {
-                const int q = p - 4 * HR - 4 * WR, ci = q / 4, ri = q % 4;
-                dbx = edge_tile(ci);
-                dby = edge_tile(ri);
-                lx = edge_col<TX>(ci);
-                ly = edge_col<TY>(ri);
-                c = row_is_below(ri) ? (col_is_left(ci) ? R_BL : R_BR)
-                                     : (col_is_left(ci) ? R_TL : R_TR);
-            }
-            const int x = X0 + lx - 2, r = Y0 + ly - 2;
-            const long long idx = ring_index(L, c, X0 / TX + dbx, Y0 / TY + dby, r, x);
-            cp_async<sizeof(rt)>(&s_ring[p], ring[c] + idx);
-        }
-        cp_async_commit();
-    }
+    stage_ring<real, TX, TY>(L, cur, X0, Y0, s_ring, &bar[0]);
     cp_async_wait_all();
     if (!tma_landed(bar, 0, L.err)) return;
 
     // 2. Partial sums into the halo's tile-edge nodes (order of
     //    load_rho_stored).  Halo (lx, ly) of the (TX + 4)-wide convention is
     //    staged row ly, column lx + 2.
-    for (int q = threadIdx.x; q < 4 * HR + 4 * WR; q += NT) {
-        int lx, ly;
-        if (q < 4 * HR) {
-            lx = edge_col<TX>(q / HR);
-            ly = q % HR;
-        } else {
-            const int t = q - 4 * HR;
-            lx = t % WR;
-            ly = edge_col<TY>(t / WR);
-            if (col_index<TX>(lx) >= 0) continue;
-        }
-        const int ci = col_index<TX>(lx), ri = col_index<TY>(ly);
-        real v = s_rho[ly * RP + lx + 2];
-        if (ci >= 0) v += s_ring[ci * HR + ly];
-        if (ri >= 0) {
-            v += s_ring[4 * HR + ri * WR + lx];
-            if (ci >= 0) v += s_ring[4 * HR + 4 * WR + ci * 4 + ri];
-        }
-        s_rho[ly * RP + lx + 2] = v;
-    }
+    combine_ring<real, TX, TY, NT, RP>(s_rho, s_ring);
     __syncthreads();
 
     // 3. mu at (a, b), a in [0, TX + 2) <-> x = X0 - 1 + a, b in [0, TY + 2)
@@ -1007,7 +1049,7 @@ struct TmaPairSmem {
     static constexpr int PLANE = TY * PP;
     static constexpr int NRHO = (TY + 4) * RP;
     static constexpr int MP = TX + 4, MH = TY + 2;  // mu of halo column a at a + 1
-    static constexpr int NRING = 4 * (TY + 4) + 4 * (TX + 4) + 16;
+    static constexpr int NRING = RingStage<float, TX, TY>::N;
     static constexpr int NMU = MP * MH;
     static constexpr int XW = TX + 2;              // exchange slots per warp
     static constexpr int NXCH = 2 * NW * XW;
@@ -1056,7 +1098,7 @@ __device__ __forceinline__ void step_tile_tma_pair(const Lattice &L, int cur, in
     }
     __syncthreads();
     if (threadIdx.x == 0) {
-        mbar_expect_tx(&bar[0], TS::tx_rho);
+        mbar_expect_tx(&bar[0], TS::tx_rho + RingStage<float, TX, TY>::bulk_bytes);
         tma_load_2d(s_rho, &maps.rho[cur], X0 - 4, Y0 - 2, &bar[0]);
         mbar_expect_tx(&bar[1], TS::tx_pops);
 #pragma unroll
@@ -1067,62 +1109,13 @@ __device__ __forceinline__ void step_tile_tma_pair(const Lattice &L, int cur, in
                         y0, plane, &bar[1]);
         }
     }
-    {
-        rho_t *const *ring = (rho_t *const *)L.ring[cur];
-        for (int p = threadIdx.x; p < TS::NRING; p += NT) {
-            int c, lx, ly, dbx = 0, dby = 0;  // receiving tile - this tile
-            if (p < 4 * HR) {
-                const int ci = p / HR;
-                dbx = edge_tile(ci);
-                ly = p % HR;
-                lx = edge_col<TX>(ci);
-                c = col_is_left(ci) ? R_L : R_R;
-            } else if (p < 4 * HR + 4 * WR) {
-                const int q = p - 4 * HR, ri = q / WR;
-                dby = edge_tile(ri);
-                lx = q % WR;
-                ly = edge_col<TY>(ri);
-                c = row_is_below(ri) ? R_B : R_T;
-            } else {
-                const int q = p - 4 * HR - 4 * WR, ci = q / 4, ri = q % 4;
-                dbx = edge_tile(ci);
-                dby = edge_tile(ri);
-                lx = edge_col<TX>(ci);
-                ly = edge_col<TY>(ri);
-                c = row_is_below(ri) ? (col_is_left(ci) ? R_BL : R_BR)
-                                     : (col_is_left(ci) ? R_TL : R_TR);
-            }
-            const int x = X0 + lx - 2, r = Y0 + ly - 2;
-            const long long idx = ring_index(L, c, X0 / TX + dbx, Y0 / TY + dby, r, x);
-            cp_async<sizeof(rho_t)>(&s_ring[p], ring[c] + idx);
-        }
-        cp_async_commit();
-    }
+    stage_ring<float, TX, TY>(L, cur, X0, Y0, s_ring, &bar[0]);
     cp_async_wait_all();
     if (!tma_landed(bar, 0, L.err)) return;
 
     // 2. Partial sums into the halo's tile-edge nodes (order of
     //    load_rho_stored); halo (lx, ly) is staged at row ly, column lx + 2.
-    for (int q = threadIdx.x; q < 4 * HR + 4 * WR; q += NT) {
-        int lx, ly;
-        if (q < 4 * HR) {
-            lx = edge_col<TX>(q / HR);
-            ly = q % HR;
-        } else {
-            const int t = q - 4 * HR;
-            lx = t % WR;
-            ly = edge_col<TY>(t / WR);
-            if (col_index<TX>(lx) >= 0) continue;
-        }
-        const int ci = col_index<TX>(lx), ri = col_index<TY>(ly);
-        float v = s_rho[ly * RP + lx + 2];
-        if (ci >= 0) v += s_ring[ci * HR + ly];
-        if (ri >= 0) {
-            v += s_ring[4 * HR + ri * WR + lx];
-            if (ci >= 0) v += s_ring[4 * HR + 4 * WR + ci * 4 + ri];
-        }
-        s_rho[ly * RP + lx + 2] = v;
-    }
+    combine_ring<float, TX, TY, NT, RP>(s_rho, s_ring);
     __syncthreads();
 
     // 3. mu at halo column a (x = X0 - 1 + a) and row b (r = Y0 - 1 + b),
