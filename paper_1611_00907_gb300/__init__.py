@@ -196,22 +196,43 @@ class Simulation:
         self._check(self._lib.lbm_eos_info(self._ctx, *[C.byref(x) for x in v]))
         return dict(zip(("T", "alpha", "Tc", "rhoc"), (x.value for x in v)))
 
-    def moments(self, device=False):
-        """dict of rho, vx, vy, mu [ny, nx] float64: numpy arrays, or CUDA
-        tensors when device=True."""
-        if device:
-            import torch
-            out = {k: torch.empty((self.ny, self.nx), dtype=torch.float64,
-                                  device="cuda:%d" % self.device)
-                   for k in ("rho", "vx", "vy", "mu")}
-            ptr = [out[k].data_ptr() for k in ("rho", "vx", "vy", "mu")]
-            self._check(self._lib.lbm_moments(self._ctx, *ptr, 1))
-            return out
-        out = {k: np.empty((self.ny, self.nx)) for k in ("rho", "vx", "vy",
-                                                          "mu")}
-        ptr = [out[k].ctypes.data for k in ("rho", "vx", "vy", "mu")]
-        self._check(self._lib.lbm_moments(self._ctx, *ptr, 0))
-        return out
+    def moments(self, device=False, fields=("rho", "vx", "vy", "mu"), out=None):
+        """dict of the requested fields among rho, vx, vy, mu [ny, nx] float64:
+        numpy arrays, or CUDA tensors when device=True.  Only the requested
+        fields are computed and copied.  out: optional dict of C-contiguous
+        float64 arrays [ny, nx] to write into (host arrays, e.g. views of
+        pinned memory, for device=False; CUDA tensors for device=True)."""
+        names = ("rho", "vx", "vy", "mu")
+        if any(k not in names for k in fields):
+            raise ValueError("fields must be among %s" % (names,))
+        out = dict(out or {})
+        ptr = []
+        for k in names:
+            if k not in fields:
+                ptr.append(None)
+                continue
+            a = out.get(k)
+            if a is None:
+                if device:
+                    import torch
+                    a = torch.empty((self.ny, self.nx), dtype=torch.float64,
+                                    device="cuda:%d" % self.device)
+                else:
+                    a = np.empty((self.ny, self.nx))
+                out[k] = a
+            if device:
+                ok = (tuple(a.shape) == (self.ny, self.nx) and a.is_cuda and
+                      a.is_contiguous() and str(a.dtype) == "torch.float64")
+                ptr.append(a.data_ptr() if ok else None)
+            else:
+                ok = (a.shape == (self.ny, self.nx) and a.dtype == np.float64
+                      and a.flags["C_CONTIGUOUS"] and a.flags["WRITEABLE"])
+                ptr.append(a.ctypes.data if ok else None)
+            if not ok:
+                raise ValueError("out[%r] must be a contiguous float64 [ny, nx] "
+                                 "%s array" % (k, "CUDA" if device else "host"))
+        self._check(self._lib.lbm_moments(self._ctx, *ptr, 1 if device else 0))
+        return {k: out[k] for k in names if k in fields}
 
     def populations(self):
         """Natural-order FP64 distributions [9, ny, nx] (numpy)."""

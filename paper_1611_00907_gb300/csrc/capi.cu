@@ -711,11 +711,7 @@ lbm_status lbm_moments(lbm_ctx *c, double *rho, double *vx, double *vy,
         CUDA_TRY(c, launch_macro(L, p, p, rho, vx, vy, mu, nullptr, nullptr,
                                  nullptr, c->stream));
         CUDA_TRY(c, cudaStreamSynchronize(c->stream));
-    {
-        lbm_status fs = check_kernel_flags(c);
-        if (fs != LBM_OK) return fs;
-    }
-        return LBM_OK;
+        return check_kernel_flags(c);
     }
     lbm_status s = ensure_tmp(c, 4 * field);
     if (s != LBM_OK) return s;

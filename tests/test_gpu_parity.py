@@ -372,3 +372,16 @@ def test_fp16_storage_tma_path(tile, monkeypatch):
     # half populations (eps 4.9e-4 on g_i) against the FP64 oracle
     for run in runs:
         assert _rel(run["rho"], want["rho"]) < 2e-3
+
+
+def test_moments_subset_into_caller_buffers():
+    sim, ref, rho = _setup("cs", 70, 21, True)
+    with sim:
+        sim.init(rho).step(3)
+        full = sim.moments()
+        buf = np.zeros((21, 70))
+        part = sim.moments(fields=("rho", "mu"), out={"rho": buf})
+        assert set(part) == {"rho", "mu"} and part["rho"] is buf
+        assert np.array_equal(buf, full["rho"]) and np.array_equal(part["mu"], full["mu"])
+        with pytest.raises(ValueError):
+            sim.moments(fields=("rho",), out={"rho": np.zeros((21, 70), np.float32)})
