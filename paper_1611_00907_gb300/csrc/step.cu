@@ -73,11 +73,11 @@ int step_shapes(int *tx, int *ty, int max)
 
 void step_default_shape(int prec, int *tx, int *ty)
 {
-    // fastest measured on GB300 for the 4096^2 workload in every precision
-    // (lbm_autotune picks per lattice)
-    (void)prec;
-    *tx = 32;
-    *ty = 32;
+    // fastest measured on GB300 for the 4096^2 workload (lbm_autotune picks
+    // per lattice): 32 x 32, and for FP16 storage the two-nodes-per-lane
+    // path's 64 x 16
+    *tx = prec == P_F16_OFF ? 64 : 32;
+    *ty = prec == P_F16_OFF ? 16 : 32;
 }
 
 void pt_shape(int prec, int *tx, int *ty)

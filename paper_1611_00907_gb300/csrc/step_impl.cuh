@@ -1041,12 +1041,32 @@ __device__ __forceinline__ void collide2(const float2 *f, float2 drho, float2 rh
                             padd(padd(fp[5], fp[6]), padd(fp[7], fp[8]))));
 }
 
-template <int TX, int TY, int NT>
+// Two adjacent stored populations (8- or 4-byte aligned) as a float pair.
+__device__ __forceinline__ float2 ld_pair(const float *p)
+{
+    return *reinterpret_cast<const float2 *>(p);
+}
+__device__ __forceinline__ float2 ld_pair(const __half *p)
+{
+    return __half22float2(*reinterpret_cast<const __half2 *>(p));
+}
+__device__ __forceinline__ void st_pair(float *p, float2 v)
+{
+    *reinterpret_cast<float2 *>(p) = v;
+}
+__device__ __forceinline__ void st_pair(__half *p, float2 v)
+{
+    *reinterpret_cast<__half2 *>(p) = __floats2half2_rn(v.x, v.y);
+}
+
+template <class pop_t, int TX, int TY, int NT>
 struct TmaPairSmem {
     static constexpr int NW = NT / 32;
+    static constexpr int PX = 16 / sizeof(pop_t);
     static constexpr int RP = TX + 8;              // density rows from x = X0 - 4
-    static constexpr int PP = TX + 4;              // population rows (pin_x0)
+    static constexpr int PP = TX + PX;             // population rows (pin_x0)
     static constexpr int PLANE = TY * PP;
+    static constexpr size_t PIN_BYTES = sizeof(pop_t) * 8 * PLANE;
     static constexpr int NRHO = (TY + 4) * RP;
     static constexpr int MP = TX + 4, MH = TY + 2;  // mu of halo column a at a + 1
     static constexpr int NRING = RingStage<float, TX, TY>::N;
@@ -1055,11 +1075,11 @@ struct TmaPairSmem {
     static constexpr int NXCH = 2 * NW * XW;
     static constexpr int NSHARE = NRING > NXCH ? NRING : NXCH;  // ring, then exchange
     static constexpr size_t bar_offset =
-        (sizeof(float) * (8 * PLANE + NRHO + NSHARE + NMU) + 15) / 16 * 16;
+        (PIN_BYTES + sizeof(float) * (NRHO + NSHARE + NMU) + 15) / 16 * 16;
     static constexpr size_t bytes = bar_offset + 16;
     static constexpr unsigned tx_rho = sizeof(float) * NRHO;
-    static constexpr unsigned tx_pops = sizeof(float) * 8 * PLANE;
-    static_assert((PLANE * sizeof(float)) % 128 == 0, "TMA destinations");
+    static constexpr unsigned tx_pops = PIN_BYTES;
+    static_assert((PLANE * sizeof(pop_t)) % 128 == 0, "TMA destinations");
     static_assert(NRHO % 2 == 0 && NSHARE % 2 == 0 && NMU % 2 == 0 && XW % 2 == 0 &&
                       PP % 2 == 0,
                   "pair-aligned sub-arrays");
@@ -1071,16 +1091,17 @@ __device__ __forceinline__ void step_tile_tma_pair(const Lattice &L, int cur, in
                                                    const TmaMaps &maps)
 {
     using rho_t = typename S::rho_t;
-    using TS = TmaPairSmem<TX, TY, NT>;
+    using pop_t = typename S::pop_t;
+    using TS = TmaPairSmem<pop_t, TX, TY, NT>;
     static_assert(TX == 64, "lanes map to x pairs");
-    static_assert(sizeof(typename S::pop_t) == 4 && sizeof(rho_t) == 4, "FP32 storage");
+    static_assert(sizeof(rho_t) == 4 && sizeof(typename S::real) == 4, "FP32 arithmetic");
     constexpr int NW = TS::NW, PER = TY / NW;
     static_assert(PER * NW == TY && PER >= 2, "warps own whole row blocks");
     constexpr int RP = TS::RP, PP = TS::PP, PLANE = TS::PLANE, MP = TS::MP, MH = TS::MH;
     constexpr int XW = TS::XW;
     constexpr int WR = TX + 4, HR = TY + 4;  // halo geometry of the ring staging
-    float *s_pin = reinterpret_cast<float *>(smem_raw);  // [8][TY][PP]
-    float *s_rho = s_pin + 8 * PLANE;                     // [TY + 4][RP]
+    pop_t *s_pin = reinterpret_cast<pop_t *>(smem_raw);             // [8][TY][PP]
+    float *s_rho = reinterpret_cast<float *>(smem_raw + TS::PIN_BYTES);  // [TY + 4][RP]
     float *s_ring = s_rho + TS::NRHO;
     float *s_mu = s_ring + TS::NSHARE;                    // [MH][MP]
     float *s_up = s_ring;                                 // [NW][XW], after step 2
@@ -1105,8 +1126,8 @@ __device__ __forceinline__ void step_tile_tma_pair(const Lattice &L, int cur, in
         for (int i = 1; i < 9; ++i) {
             const int plane = PARITY == 0 ? i - 1 : opp(i) - 1;
             const int y0 = PARITY == 0 ? Y0 : Y0 - ey(i);
-            tma_load_3d(s_pin + (i - 1) * PLANE, &maps.pops, X0 + pin_x0<PARITY, 4>(i),
-                        y0, plane, &bar[1]);
+            tma_load_3d(s_pin + (i - 1) * PLANE, &maps.pops,
+                        X0 + pin_x0<PARITY, TS::PX>(i), y0, plane, &bar[1]);
         }
     }
     stage_ring<float, TX, TY>(L, cur, X0, Y0, s_ring, &bar[0]);
@@ -1154,7 +1175,7 @@ __device__ __forceinline__ void step_tile_tma_pair(const Lattice &L, int cur, in
     //    the pair at columns x0, x0 + 1 of rows ly0 .. ly0 + PER - 1.
     const int x0 = 2 * lane, ly0 = warp * PER;
     const float2 tau = p2(K.tau), omega = p2(K.omega), third = p2(1.0f / 3.0f);
-    float *A = (float *)L.pops;
+    pop_t *A = (pop_t *)L.pops;
     rho_t *Rn = (rho_t *)L.rho[nxt];
     rho_t *const *ring = (rho_t *const *)L.ring[nxt];
     int woff[9];  // 32-bit: the TMA maps exist only when 8 planes fit
@@ -1176,7 +1197,7 @@ __device__ __forceinline__ void step_tile_tma_pair(const Lattice &L, int cur, in
     // R share one index layout)
     const int bx = X0 / TX, by = Y0 / TY, bxc = lane == 0 ? bx - 1 : bx + 1;
     const bool col_lane = lane == 0 || lane == 31;
-    float *Arow = A + (long long)(Y0 + ly0) * L.pitch + X0 + x0;
+    pop_t *Arow = A + (long long)(Y0 + ly0) * L.pitch + X0 + x0;
 #pragma unroll
     for (int k = 0; k < PER; ++k) {
         const int ly = ly0 + k;
@@ -1185,11 +1206,12 @@ __device__ __forceinline__ void step_tile_tma_pair(const Lattice &L, int cur, in
         float2 f[9];
 #pragma unroll
         for (int i = 1; i < 9; ++i) {
-            const float *src = s_pin + (i - 1) * PLANE + ly * PP + x0 + pin_col<PARITY, 4>(i);
+            const pop_t *src =
+                s_pin + (i - 1) * PLANE + ly * PP + x0 + pin_col<PARITY, TS::PX>(i);
             if (PARITY == 0 || ex(i) == 0)
-                f[i] = *reinterpret_cast<const float2 *>(src);
+                f[i] = ld_pair(src);
             else
-                f[i] = make_float2(src[0], src[1]);
+                f[i] = make_float2(ld_real(src), ld_real(src + 1));
         }
         const float2 drho = rm.c;
         const float2 rho = S::offset ? padd(drho, ref2) : drho;
@@ -1202,12 +1224,12 @@ __device__ __forceinline__ void step_tile_tma_pair(const Lattice &L, int cur, in
         collide2(f, drho, rho, Fx, Fy, tau, omega, fp);
 #pragma unroll
         for (int i = 1; i < 9; ++i) {
-            float *dst = Arow + woff[i];
+            pop_t *dst = Arow + woff[i];
             if (PARITY == 0 || ex(i) == 0) {
-                *reinterpret_cast<float2 *>(dst) = fp[i];
+                st_pair(dst, fp[i]);
             } else {
-                dst[0] = fp[i].x;
-                dst[1] = fp[i].y;
+                st_real(dst, fp[i].x);
+                st_real(dst + 1, fp[i].y);
             }
         }
         Arow += L.pitch;
@@ -1291,21 +1313,22 @@ __device__ __forceinline__ void step_tile_tma_pair(const Lattice &L, int cur, in
     }
 }
 
-// Whether a (precision, tile) pair has the two-nodes-per-lane TMA path, and
-// the CTA size of a shape: four rows per warp on that path.
+// Whether a (precision, tile) pair has the two-nodes-per-lane TMA path (FP32
+// arithmetic, FP32 or FP16 storage), and the CTA size of a shape: four rows
+// per warp on that path.
 template <class S>
-struct IsF32Storage {
+struct IsPairStorage {
     static constexpr bool value = sizeof(typename S::real) == 4 &&
-                                  sizeof(typename S::pop_t) == 4;
+                                  sizeof(typename S::rho_t) == 4;
 };
 template <class S, int TX, int TY>
 constexpr int step_threads()
 {
-    return (TX == 64 && IsF32Storage<S>::value) ? 8 * TY : STEP_THREADS;
+    return (TX == 64 && IsPairStorage<S>::value) ? 8 * TY : STEP_THREADS;
 }
 template <class S, int TX, int TY, int NT>
 struct HasTmaPair {
-    static constexpr bool value = TX == 64 && IsF32Storage<S>::value &&
+    static constexpr bool value = TX == 64 && IsPairStorage<S>::value &&
                                   TY % (NT / 32) == 0 && TY / (NT / 32) >= 2;
 };
 
@@ -1355,7 +1378,7 @@ static cudaError_t launch_shape(const Lattice &L, int parity, int cur,
     size_t smem_tma = 0;
     if constexpr (HasTma<S, TX, TY, NT>::value) smem_tma = TmaSmem<S, TX, TY>::bytes;
     if constexpr (HasTmaPair<S, TX, TY, NT>::value)
-        smem_tma = TmaPairSmem<TX, TY, NT>::bytes;
+        smem_tma = TmaPairSmem<typename S::pop_t, TX, TY, NT>::bytes;
     const size_t smem = smem_v4 > smem_tma ? smem_v4 : smem_tma;
     TmaMaps m{};
     if (maps && maps->valid && maps->tx == TX && maps->ty == TY) m = *maps;

@@ -344,7 +344,7 @@ def test_full_size_sampled_one_step(precision, tol):
         assert abs(m1 - m0) / m0 < (1e-13 if precision == "f64" else 1e-5)
 
 
-@pytest.mark.parametrize("tile", [(32, 16), (32, 24), (32, 32)])
+@pytest.mark.parametrize("tile", [(32, 16), (32, 24), (32, 32), (64, 16), (64, 32)])
 def test_fp16_storage_tma_path(tile, monkeypatch):
     # FP16 storage: interior tiles stage the half populations by TMA; the
     # same lattice with every tile on the general path (no tensor maps)
