@@ -25,6 +25,8 @@ struct lbm_batch {
     int tx = 32, ty = 32;
     Lattice *d_lats = nullptr;
     WorkItem *d_items = nullptr;
+    TmaMaps *d_maps = nullptr;  // per-lattice tensor maps, or null (no TMA)
+    int *d_counter = nullptr;   // work-item counters of the batched kernel
     int n_items = 0;
     long long t = 0;
     long long nodes = 0;
@@ -70,12 +72,17 @@ lbm_status rebuild(lbm_batch *b)
     drop_graph(b);
     std::vector<Lattice> lats;
     std::vector<WorkItem> items;
+    std::vector<TmaMaps> maps;
+    bool any_maps = false;
     for (size_t i = 0; i < b->inst.size(); ++i) {
         lbm_ctx *c = b->inst[i];
         c->L.tx = b->tx;
         c->L.ty = b->ty;
         ctx_refresh_maps(c);
         lats.push_back(c->L);
+        maps.push_back(c->maps);
+        if (!c->use_tma) maps.back().valid = 0;
+        any_maps = any_maps || maps.back().valid;
         if (!b->active[i]) continue;
         const Lattice &L = c->L;
         const int ntx = (L.nx + b->tx - 1) / b->tx, nty = (L.nyf + b->ty - 1) / b->ty;
@@ -88,8 +95,17 @@ lbm_status rebuild(lbm_batch *b)
     }
     cudaFree(b->d_lats);
     cudaFree(b->d_items);
+    cudaFree(b->d_maps);
     b->d_lats = nullptr;
     b->d_items = nullptr;
+    b->d_maps = nullptr;
+    if (!b->d_counter) BCUDA(b, cudaMalloc(&b->d_counter, 2 * sizeof(int)));
+    BCUDA(b, cudaMemset(b->d_counter, 0, 2 * sizeof(int)));
+    if (any_maps) {
+        BCUDA(b, cudaMalloc(&b->d_maps, maps.size() * sizeof(TmaMaps)));
+        BCUDA(b, cudaMemcpy(b->d_maps, maps.data(), maps.size() * sizeof(TmaMaps),
+                            cudaMemcpyHostToDevice));
+    }
     BCUDA(b, cudaMalloc(&b->d_lats, lats.size() * sizeof(Lattice)));
     BCUDA(b, cudaMalloc(&b->d_items, items.size() * sizeof(WorkItem)));
     BCUDA(b, cudaMemcpy(b->d_lats, lats.data(), lats.size() * sizeof(Lattice),
@@ -103,7 +119,8 @@ lbm_status rebuild(lbm_batch *b)
 lbm_status launch_one(lbm_batch *b)
 {
     const int p = (int)(b->t & 1);
-    BCUDA(b, launch_step_batch(b->d_lats, b->d_items, b->n_items, p, p,
+    BCUDA(b, launch_step_batch(b->d_lats, b->d_items, b->d_maps, b->d_counter,
+                               b->n_items, p, p,
                                b->precision, b->tx, b->ty, 0, b->stream));
     ++b->t;
     return LBM_OK;
@@ -116,7 +133,8 @@ lbm_status ensure_graph(lbm_batch *b)
     BCUDA(b, cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal));
     cudaError_t e = cudaSuccess;
     for (int k = 0; k < GRAPH_STEPS && e == cudaSuccess; ++k)
-        e = launch_step_batch(b->d_lats, b->d_items, b->n_items, k & 1, k & 1,
+        e = launch_step_batch(b->d_lats, b->d_items, b->d_maps, b->d_counter,
+                              b->n_items, k & 1, k & 1,
                               b->precision, b->tx, b->ty, 0, b->stream);
     cudaError_t e2 = cudaStreamEndCapture(b->stream, &g);
     if (e != cudaSuccess || e2 != cudaSuccess) {
@@ -413,6 +431,8 @@ void lbm_batch_destroy(lbm_batch *b)
     for (lbm_ctx *c : b->inst) lbm_destroy(c);
     cudaFree(b->d_lats);
     cudaFree(b->d_items);
+    cudaFree(b->d_maps);
+    cudaFree(b->d_counter);
     if (b->own_stream) cudaStreamDestroy(b->stream);
     delete b;
 }

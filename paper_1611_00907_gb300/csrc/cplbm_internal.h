@@ -155,9 +155,13 @@ struct WorkItem {
 // One step of every lattice of a batch in one launch: gridDim CTAs stride
 // over the work list.  All lattices share precision, tile shape and step
 // parity.  grid <= 0 picks one CTA per SM slot (occupancy-limited).
+// d_maps: per-lattice tensor maps in device memory (interior tiles of
+// 32-wide shapes take the TMA path), or nullptr.  d_counter: two ints, zero
+// before the first launch; the launches keep them so from then on.
 cudaError_t launch_step_batch(const Lattice *d_lats, const WorkItem *d_items,
-                              int n_items, int parity, int cur, int precision,
-                              int tx, int ty, int grid, cudaStream_t s);
+                              const TmaMaps *d_maps, int *d_counter, int n_items,
+                              int parity, int cur, int precision, int tx, int ty,
+                              int grid, cudaStream_t s);
 
 // fields.cu
 // Equilibrium initial state from double fields [ny][nx] on the device:

@@ -12,10 +12,10 @@ cudaError_t launch_step_f32(const Lattice &L, int parity, int cur,
 }
 
 cudaError_t launch_batch_f32(const Lattice *d_lats, const WorkItem *d_items,
-                             int n_items, int parity, int cur, int tx, int ty,
+                             const TmaMaps *d_maps, int *d_counter, int n_items, int parity, int cur, int tx, int ty,
                              int grid, cudaStream_t s)
 {
-    return launch_batch_t<SF32>(d_lats, d_items, n_items, parity, cur, tx, ty, grid, s);
+    return launch_batch_t<SF32>(d_lats, d_items, d_maps, d_counter, n_items, parity, cur, tx, ty, grid, s);
 }
 
 cudaError_t launch_pt_f32(const Lattice &L, int parity, int cur, cudaStream_t s)

@@ -516,18 +516,19 @@ __device__ __forceinline__ constexpr int pin_col(int i)
     return PARITY == 0 ? 0 : (ex(i) == 1 ? PX - 1 : (ex(i) == -1 ? 1 : 0));
 }
 
-// All threads: wait (bounded) for barrier k of the tile's copies (0: the
-// density halo, 1: the populations), then a block barrier.  false when any
-// thread gave up: the flag is raised, every copy of the tile is given
-// another bounded wait so none is left writing into this block's shared
-// memory, and the caller leaves the tile untouched.
-__device__ __forceinline__ bool tma_landed(unsigned long long *bar, int k, int *err)
+// All threads: wait (bounded) for phase `phase` of barrier k of the tile's
+// copies (0: the density halo and partial sums, 1: the populations), then a
+// block barrier.  false when any thread gave up: the flag is raised, every
+// copy of the tile is given another bounded wait so none is left writing
+// into this block's shared memory, and the caller leaves the tile untouched.
+__device__ __forceinline__ bool tma_landed(unsigned long long *bar, int k,
+                                           unsigned phase, int *err)
 {
-    const bool ok = mbar_wait(&bar[k], 0, 2000000000LL);  // ~1 s at 2 GHz
+    const bool ok = mbar_wait(&bar[k], phase, 2000000000LL);  // ~1 s at 2 GHz
     if (!__syncthreads_or(!ok)) return true;
     if (threadIdx.x == 0 && err) atomicOr(err, ERR_WAIT_TIMEOUT);
-    mbar_wait(&bar[0], 0, 2000000000LL);
-    mbar_wait(&bar[1], 0, 2000000000LL);
+    mbar_wait(&bar[0], phase, 2000000000LL);
+    mbar_wait(&bar[1], phase, 2000000000LL);
     __syncthreads();
     return false;
 }
@@ -669,9 +670,10 @@ __device__ __forceinline__ T lap_w(const T (&w)[3][3])
 }
 
 template <class S, int TX, int TY, int NT, int PARITY>
-__device__ __forceinline__ void step_tile_tma(const Lattice &L, int cur, int X0,
+__device__ __forceinline__ bool step_tile_tma(const Lattice &L, int cur, int X0,
                                               int Y0, unsigned char *smem_raw,
-                                              const TmaMaps &maps)
+                                              const TmaMaps &maps,
+                                              unsigned long long *bar, unsigned phase)
 {
     using real = typename S::real;
     using pop_t = typename S::pop_t;
@@ -689,18 +691,13 @@ __device__ __forceinline__ void step_tile_tma(const Lattice &L, int cur, int X0,
     real *s_mu = s_ring + TS::NSHARE;                    // [MH][MP]
     real *s_up = s_ring;                                 // [NW][XW], after step 2
     real *s_down = s_up + NW * XW;                       // [NW][XW]
-    unsigned long long *bar =
-        reinterpret_cast<unsigned long long *>(smem_raw + TS::bar_offset);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int nxt = cur ^ 1;
 
-    // 1. Loads.  Density halo and populations by TMA (thread 0), partial
-    //    sums by cp.async (all threads).
-    if (threadIdx.x == 0) {
-        mbar_init(&bar[0], 1);
-        mbar_init(&bar[1], 1);
-    }
-    __syncthreads();
+    // 1. Loads (bar: the caller's two initialised mbarriers, this tile
+    //    completing phase `phase` of each).  Density halo and populations by
+    //    TMA and the partial sums by bulk copies (thread 0), the corner sums
+    //    by cp.async.
     if (threadIdx.x == 0) {
         mbar_expect_tx(&bar[0], TS::tx_rho + RingStage<real, TX, TY>::bulk_bytes);
         tma_load_2d(s_rho, &maps.rho[cur], X0 - 4, Y0 - 2, &bar[0]);
@@ -715,7 +712,7 @@ __device__ __forceinline__ void step_tile_tma(const Lattice &L, int cur, int X0,
     }
     stage_ring<real, TX, TY>(L, cur, X0, Y0, s_ring, &bar[0]);
     cp_async_wait_all();
-    if (!tma_landed(bar, 0, L.err)) return;
+    if (!tma_landed(bar, 0, phase, L.err)) return false;
 
     // 2. Partial sums into the halo's tile-edge nodes (order of
     //    load_rho_stored).  Halo (lx, ly) of the (TX + 4)-wide convention is
@@ -758,7 +755,7 @@ __device__ __forceinline__ void step_tile_tma(const Lattice &L, int cur, int X0,
     }
     // the populations were in flight during steps 2 and 3; the barrier also
     // publishes s_mu
-    if (!tma_landed(bar, 1, L.err)) return;
+    if (!tma_landed(bar, 1, phase, L.err)) return false;
 
     // 4. Force, collision, in-place streaming and the register hand-over for
     //    the thread's PER nodes at rows ly0 .. ly0 + PER - 1, column lx.
@@ -897,6 +894,7 @@ __device__ __forceinline__ void step_tile_tma(const Lattice &L, int cur, int X0,
         if (lane == 0) ring[R_BR][ring_index(L, R_BR, bx - 1, by + 1, Y0 + TY, X0 - 1)] = (rho_t)up_prev_c;
         if (lane == 31) ring[R_BL][ring_index(L, R_BL, bx + 1, by + 1, Y0 + TY, X0 + TX)] = (rho_t)up_prev_c;
     }
+    return true;
 }
 
 // ---------------------------------------------------------------------------
@@ -1086,9 +1084,11 @@ struct TmaPairSmem {
 };
 
 template <class S, int TX, int TY, int NT, int PARITY>
-__device__ __forceinline__ void step_tile_tma_pair(const Lattice &L, int cur, int X0,
+__device__ __forceinline__ bool step_tile_tma_pair(const Lattice &L, int cur, int X0,
                                                    int Y0, unsigned char *smem_raw,
-                                                   const TmaMaps &maps)
+                                                   const TmaMaps &maps,
+                                                   unsigned long long *bar,
+                                                   unsigned phase)
 {
     using rho_t = typename S::rho_t;
     using pop_t = typename S::pop_t;
@@ -1106,18 +1106,10 @@ __device__ __forceinline__ void step_tile_tma_pair(const Lattice &L, int cur, in
     float *s_mu = s_ring + TS::NSHARE;                    // [MH][MP]
     float *s_up = s_ring;                                 // [NW][XW], after step 2
     float *s_down = s_up + NW * XW;                       // [NW][XW]
-    unsigned long long *bar =
-        reinterpret_cast<unsigned long long *>(smem_raw + TS::bar_offset);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int nxt = cur ^ 1;
 
-    // 1. Loads: density halo and populations by TMA (thread 0), partial sums
-    //    by cp.async (all threads).
-    if (threadIdx.x == 0) {
-        mbar_init(&bar[0], 1);
-        mbar_init(&bar[1], 1);
-    }
-    __syncthreads();
+    // 1. Loads (bar, phase: as step_tile_tma).
     if (threadIdx.x == 0) {
         mbar_expect_tx(&bar[0], TS::tx_rho + RingStage<float, TX, TY>::bulk_bytes);
         tma_load_2d(s_rho, &maps.rho[cur], X0 - 4, Y0 - 2, &bar[0]);
@@ -1132,7 +1124,7 @@ __device__ __forceinline__ void step_tile_tma_pair(const Lattice &L, int cur, in
     }
     stage_ring<float, TX, TY>(L, cur, X0, Y0, s_ring, &bar[0]);
     cp_async_wait_all();
-    if (!tma_landed(bar, 0, L.err)) return;
+    if (!tma_landed(bar, 0, phase, L.err)) return false;
 
     // 2. Partial sums into the halo's tile-edge nodes (order of
     //    load_rho_stored); halo (lx, ly) is staged at row ly, column lx + 2.
@@ -1169,7 +1161,7 @@ __device__ __forceinline__ void step_tile_tma_pair(const Lattice &L, int cur, in
     }
     // the populations were in flight during steps 2 and 3; the barrier also
     // publishes s_mu
-    if (!tma_landed(bar, 1, L.err)) return;
+    if (!tma_landed(bar, 1, phase, L.err)) return false;
 
     // 4. Force, collision, in-place streaming and the register hand-over for
     //    the pair at columns x0, x0 + 1 of rows ly0 .. ly0 + PER - 1.
@@ -1311,6 +1303,7 @@ __device__ __forceinline__ void step_tile_tma_pair(const Lattice &L, int cur, in
         if (lane == 0) ring[R_BR][ring_index(L, R_BR, bx - 1, by + 1, Y0 + TY, X0 - 1)] = up_prev_c;
         if (lane == 31) ring[R_BL][ring_index(L, R_BL, bx + 1, by + 1, Y0 + TY, X0 + TX)] = up_prev_c;
     }
+    return true;
 }
 
 // Whether a (precision, tile) pair has the two-nodes-per-lane TMA path (FP32
@@ -1350,15 +1343,19 @@ __global__ void __launch_bounds__(NT, HasTmaPair<S, TX, TY, NT>::value ? 512 / N
     const int by = PARITY ? gridDim.y - 1 - blockIdx.y : blockIdx.y;
     const int X0 = bx * TX, Y0 = by * TY;
     const bool interior = bx >= xlo && bx <= xhi && by >= ylo && by <= yhi;
-    if constexpr (HasTma<S, TX, TY, NT>::value) {
+    if constexpr (HasTma<S, TX, TY, NT>::value || HasTmaPair<S, TX, TY, NT>::value) {
         if (interior && maps.valid) {
-            step_tile_tma<S, TX, TY, NT, PARITY>(L, cur, X0, Y0, smem_raw, maps);
-            return;
-        }
-    }
-    if constexpr (HasTmaPair<S, TX, TY, NT>::value) {
-        if (interior && maps.valid) {
-            step_tile_tma_pair<S, TX, TY, NT, PARITY>(L, cur, X0, Y0, smem_raw, maps);
+            __shared__ __align__(8) unsigned long long bar[2];
+            if (threadIdx.x == 0) {
+                mbar_init(&bar[0], 1);
+                mbar_init(&bar[1], 1);
+            }
+            __syncthreads();
+            if constexpr (HasTma<S, TX, TY, NT>::value)
+                step_tile_tma<S, TX, TY, NT, PARITY>(L, cur, X0, Y0, smem_raw, maps, bar, 0);
+            else
+                step_tile_tma_pair<S, TX, TY, NT, PARITY>(L, cur, X0, Y0, smem_raw, maps,
+                                                          bar, 0);
             return;
         }
     }
@@ -1419,14 +1416,40 @@ static cudaError_t launch_shape(const Lattice &L, int parity, int cur,
 // that item's lattice, whose descriptor it first copies to shared memory.
 // ---------------------------------------------------------------------------
 template <class S, int TX, int TY, int NT, int PARITY>
-__global__ void __launch_bounds__(NT)
+__global__ void __launch_bounds__(NT, sizeof(typename S::real) == 8 ? 2 : 4)
     step_batch_kernel(const Lattice *__restrict__ lats,
-                      const WorkItem *__restrict__ items, int n_items, int cur)
+                      const WorkItem *__restrict__ items, int n_items, int cur,
+                      const TmaMaps *__restrict__ maps, int *counter)
 {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     __shared__ Lattice sL;
+    __shared__ int s_w;
+    // Work items are taken from counter[PARITY] as CTAs become free (a fixed
+    // share per CTA keeps the CTAs of an SM in lockstep, loading and
+    // computing all at once); this launch zeroes the other counter for the
+    // next step, which the stream order keeps from running before it.
+    if (blockIdx.x == 0 && threadIdx.x == 0) counter[PARITY ^ 1] = 0;
+    // TMA interior tiles (maps != nullptr: per-lattice tensor maps in global
+    // memory): the two mbarriers live outside the dynamic shared memory that
+    // general-path items reuse, are initialised once, and every TMA tile
+    // completes one phase of each.
+    __shared__ __align__(8) unsigned long long bar[2];
+    bool tma = HasTma<S, TX, TY, NT>::value && maps != nullptr;
+    unsigned phase = 0;
+    if (tma) {
+        if (threadIdx.x == 0) {
+            mbar_init(&bar[0], 1);
+            mbar_init(&bar[1], 1);
+        }
+        __syncthreads();
+    }
     static_assert(sizeof(Lattice) % sizeof(int) == 0, "descriptor copy");
-    for (int w = blockIdx.x; w < n_items; w += gridDim.x) {
+    int fenced = -1;  // lattice whose maps this CTA has fenced
+    for (;;) {
+        if (threadIdx.x == 0) s_w = atomicAdd(&counter[PARITY], 1);
+        __syncthreads();
+        const int w = s_w;
+        if (w >= n_items) break;
         // odd steps take the work list backwards (see step_kernel)
         const WorkItem it = items[PARITY ? n_items - 1 - w : w];
         {
@@ -1437,25 +1460,50 @@ __global__ void __launch_bounds__(NT)
                 dst[q] = src[q];
         }
         __syncthreads();
-        if (it.interior)
-            step_tile<S, TX, TY, NT, PARITY, true>(sL, cur, it.bx * TX,
-                                                   it.by * TY, smem_raw);
-        else
-            step_tile<S, TX, TY, NT, PARITY, false>(sL, cur, it.bx * TX,
-                                                    it.by * TY, smem_raw);
+        bool done = false;
+        if constexpr (HasTma<S, TX, TY, NT>::value) {
+            const TmaMaps &m = maps[it.inst];
+            if (tma && it.interior && m.valid && m.tx == TX && m.ty == TY) {
+                if (threadIdx.x == 0 && fenced != it.inst) {
+                    // the maps were written by the host: make the tensor-map
+                    // proxy see their current contents
+                    tensormap_acquire(&m.pops);
+                    tensormap_acquire(&m.rho[0]);
+                    tensormap_acquire(&m.rho[1]);
+                }
+                fenced = it.inst;
+                // a wait that gave up leaves the barriers in doubt: the rest
+                // of this CTA's items take the general path
+                tma = step_tile_tma<S, TX, TY, NT, PARITY>(sL, cur, it.bx * TX, it.by * TY,
+                                                           smem_raw, m, bar, phase);
+                phase ^= 1u;
+                done = true;
+            }
+        }
+        if (!done) {
+            if (it.interior)
+                step_tile<S, TX, TY, NT, PARITY, true>(sL, cur, it.bx * TX,
+                                                       it.by * TY, smem_raw);
+            else
+                step_tile<S, TX, TY, NT, PARITY, false>(sL, cur, it.bx * TX,
+                                                        it.by * TY, smem_raw);
+        }
         __syncthreads();  // smem and sL are reused by the next item
     }
 }
 
 template <class S, int TX, int TY>
 static cudaError_t launch_batch_shape(const Lattice *d_lats,
-                                      const WorkItem *d_items, int n_items,
-                                      int parity, int cur, int grid,
+                                      const WorkItem *d_items,
+                                      const TmaMaps *d_maps, int *d_counter,
+                                      int n_items, int parity, int cur, int grid,
                                       cudaStream_t s)
 {
     using real = typename S::real;
     constexpr int NT = STEP_THREADS;
-    const size_t smem = StepSmem<real, TX, TY>::bytes;
+    size_t smem = StepSmem<real, TX, TY>::bytes;
+    if constexpr (HasTma<S, TX, TY, NT>::value)
+        if (TmaSmem<S, TX, TY>::bytes > smem) smem = TmaSmem<S, TX, TY>::bytes;
     auto k0 = step_batch_kernel<S, TX, TY, NT, 0>;
     auto k1 = step_batch_kernel<S, TX, TY, NT, 1>;
     static int configured = -1, slots = 0;
@@ -1481,21 +1529,22 @@ static cudaError_t launch_batch_shape(const Lattice *d_lats,
     if (grid <= 0) grid = slots;
     if (grid > n_items) grid = n_items;
     if (parity == 0)
-        k0<<<grid, NT, smem, s>>>(d_lats, d_items, n_items, cur);
+        k0<<<grid, NT, smem, s>>>(d_lats, d_items, n_items, cur, d_maps, d_counter);
     else
-        k1<<<grid, NT, smem, s>>>(d_lats, d_items, n_items, cur);
+        k1<<<grid, NT, smem, s>>>(d_lats, d_items, n_items, cur, d_maps, d_counter);
     return cudaGetLastError();
 }
 
 template <class S>
 static cudaError_t launch_batch_t(const Lattice *d_lats, const WorkItem *d_items,
-                                  int n_items, int parity, int cur, int tx,
-                                  int ty, int grid, cudaStream_t s)
+                                  const TmaMaps *d_maps, int *d_counter,
+                                  int n_items, int parity, int cur, int tx, int ty,
+                                  int grid, cudaStream_t s)
 {
 #define CPLBM_CASE(a, b)                                                   \
     if (tx == a && ty == b)                                                \
-        return launch_batch_shape<S, a, b>(d_lats, d_items, n_items, parity, \
-                                           cur, grid, s);
+        return launch_batch_shape<S, a, b>(d_lats, d_items, d_maps, d_counter, \
+                                           n_items, parity, cur, grid, s);
     CPLBM_STEP_SHAPES(CPLBM_CASE)
 #undef CPLBM_CASE
     return cudaErrorInvalidValue;
