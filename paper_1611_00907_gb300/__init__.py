@@ -50,6 +50,20 @@ def eos_pressure(eos, a, b, R=1.0, Tr=0.85, omega=0.344, rho=None):
     return p
 
 
+def _default_device(device):
+    """device, or PyTorch's current CUDA device when None (0 without
+    PyTorch or CUDA): under torchrun each rank's set_device is followed."""
+    if device is not None:
+        return int(device)
+    try:
+        import torch
+        if torch.cuda.is_available():
+            return torch.cuda.current_device()
+    except ImportError:
+        pass
+    return 0
+
+
 def _is_torch(x):
     return type(x).__module__.startswith("torch")
 
@@ -84,11 +98,11 @@ class Simulation:
     def __init__(self, nx, ny, eos="cs", a=1.0, b=4.0, R=1.0, Tr=0.85,
                  omega=0.344, tau=1.0, kappa=0.5, walls=False,
                  precision="f64", rho_ref=0.0, mu_bottom=0.0, top_mode=0,
-                 mu_top=0.0, device=0, stream=None):
+                 mu_top=0.0, device=None, stream=None):
         self._lib = _lib.load()
         self.nx, self.ny, self.walls = int(nx), int(ny), bool(walls)
         self.precision = precision
-        self.device = int(device)
+        self.device = _default_device(device)
         if stream is None:
             try:
                 import torch
@@ -272,9 +286,9 @@ class Batch:
                     a=1.0, b=4.0, R=1.0, Tr=0.85, omega=0.344, mu_bottom=0.0,
                     top_mode=0, mu_top=0.0)
 
-    def __init__(self, instances, precision="f32", device=0, stream=None):
+    def __init__(self, instances, precision="f32", device=None, stream=None):
         self._lib = _lib.load()
-        self.device = int(device)
+        self.device = _default_device(device)
         self.specs = []
         arr = (_lib.LbmInstance * len(instances))()
         for k, spec in enumerate(instances):

@@ -45,12 +45,13 @@ class Mlp:
     """The network on one GPU.  X, T, Y are CUDA float32 tensors [B, nin] /
     [B, nout]; inputs and targets are standardised by the caller."""
 
-    def __init__(self, params=None, device=0, seed=0):
+    def __init__(self, params=None, device=None, seed=0):
         self._lib = _lib.load()
         p = np.ascontiguousarray(init_params(seed) if params is None else params,
                                  dtype=np.float32)
         h = C.c_void_p()
-        _lib.check_mlp(self._lib.lbm_mlp_create(int(device), p.ctypes.data,
+        from . import _default_device
+        _lib.check_mlp(self._lib.lbm_mlp_create(_default_device(device), p.ctypes.data,
                                                 C.byref(h)))
         self._m = h
 

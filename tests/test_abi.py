@@ -138,3 +138,13 @@ def test_library_pressure_matches_oracle(kind, a, b, Tr):
     assert np.abs(got - want).max() <= 1e-12 * np.abs(want).max()
     with pytest.raises(LbmError):
         eos_pressure(kind, a, b, 1.0, Tr, 0.344, [-0.1])
+
+
+def test_default_device_follows_torch():
+    # an explicit device wins; otherwise PyTorch's current CUDA device (so
+    # each torchrun rank uses its own GPU), 0 without CUDA
+    from paper_1611_00907_gb300 import _default_device
+    assert _default_device(3) == 3
+    torch = pytest.importorskip("torch")
+    want = torch.cuda.current_device() if torch.cuda.is_available() else 0
+    assert _default_device(None) == want
