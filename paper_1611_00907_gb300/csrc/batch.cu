@@ -86,12 +86,11 @@ lbm_status rebuild(lbm_batch *b)
         if (!b->active[i]) continue;
         const Lattice &L = c->L;
         const int ntx = (L.nx + b->tx - 1) / b->tx, nty = (L.nyf + b->ty - 1) / b->ty;
-        const int nfx = L.nx / b->tx, nfy = L.nyf / b->ty;
+        // seams = 0: the batched kernel takes seam tiles on the general path
+        // (step_batch_kernel)
         for (int by = 0; by < nty; ++by)
             for (int bx = 0; bx < ntx; ++bx)
-                items.push_back({(int)i, bx, by,
-                                 (bx >= 1 && bx <= nfx - 2 && by >= 1 &&
-                                  by <= nfy - 2) ? 1 : 0});
+                items.push_back({(int)i, bx, by, tile_kind(L, b->tx, b->ty, bx, by, 0)});
     }
     cudaFree(b->d_lats);
     cudaFree(b->d_items);

@@ -145,12 +145,40 @@ int step_shapes(int *tx, int *ty, int max);
 cudaError_t launch_step_pt(const Lattice &L, int parity, int cur, cudaStream_t s);
 void pt_shape(int prec, int *tx, int *ty);
 
+// Periodic edges whose tiles the TMA tile path may take (bit 0: left and
+// right, bit 1: bottom and top): the tiles along the edge are full and at
+// least three span the lattice, so the halo that wraps around the edge has
+// the layout of an interior halo.
+__host__ __device__ inline int seam_bits(const Lattice &L, int tx, int ty)
+{
+    int s = 0;
+    if (L.nx % tx == 0 && L.nx / tx >= 3) s |= 1;
+    if (!L.walls && L.nyf % ty == 0 && L.nyf / ty >= 3) s |= 2;
+    return s;
+}
+
+// Path class of tile (bx, by): TILE_INTERIOR when the tile and its eight
+// neighbours are full tiles and its halo neither wraps nor meets a wall;
+// TILE_SEAM when the same holds except that the halo wraps around a
+// periodic edge allowed by `seams` (seam_bits); TILE_GENERAL otherwise.
+enum { TILE_GENERAL = 0, TILE_SEAM = 1, TILE_INTERIOR = 2 };
+__host__ __device__ inline int tile_kind(const Lattice &L, int tx, int ty, int bx, int by,
+                                         int seams)
+{
+    const int nfx = L.nx / tx, nfy = L.nyf / ty;
+    const bool ix = bx >= 1 && bx <= nfx - 2, iy = by >= 1 && by <= nfy - 2;
+    if (ix && iy) return TILE_INTERIOR;
+    const bool sx = ix || ((seams & 1) && bx < nfx);
+    const bool sy = iy || ((seams & 2) && by < nfy);
+    return sx && sy ? TILE_SEAM : TILE_GENERAL;
+}
+
 // A tile of one lattice of a batch: the persistent batched step walks a
 // list of these (step.cu).
 struct WorkItem {
     int inst;      // index into the batch's Lattice array
     int bx, by;    // tile position
-    int interior;  // the tile and its neighbours are full, no wrap or wall
+    int kind;      // tile_kind of the tile
 };
 // One step of every lattice of a batch in one launch: gridDim CTAs stride
 // over the work list.  All lattices share precision, tile shape and step

@@ -597,6 +597,161 @@ __device__ __forceinline__ void stage_ring(const Lattice &L, int cur, int X0, in
     cp_async_commit();
 }
 
+// Tile b + d of a row or column of n tiles; across a periodic edge on seam
+// tiles.
+__device__ __forceinline__ int neighbour_tile(int b, int d, int n, bool seam)
+{
+    return seam ? wrapi(b + d, n) : b + d;
+}
+
+// Seam tiles (tile_kind): the halo wraps around a periodic edge, so the
+// partial sums are staged element by element with wrapped coordinates, in
+// the layout of stage_ring (column entry j <-> row Y0 - 4 + j, row entry j
+// <-> column X0 - 4 + j), by cp.async in one group.  At least three full
+// tiles span each wrapped direction, so the neighbour tiles are full and
+// distinct and one wrap step brings every coordinate into the lattice.
+template <class rt, int TX, int TY, int NT>
+__device__ __forceinline__ void stage_ring_wrapped(const Lattice &L, int cur, int X0,
+                                                   int Y0, rt *s_ring)
+{
+    using RS = RingStage<rt, TX, TY>;
+    rt *const *ring = (rt *const *)L.ring[cur];
+    const int bx = X0 / TX, by = Y0 / TY, ntx = L.nx / TX, nty = L.nyf / TY;
+    for (int p = threadIdx.x; p < RS::N; p += NT) {
+        long long idx;
+        int c;
+        if (p < RS::NCOL) {
+            const int ci = p / RS::CL, j = p - ci * RS::CL;
+            c = col_is_left(ci) ? R_L : R_R;
+            idx = ring_index(L, c, wrapi(bx + edge_tile(ci), ntx), 0,
+                             wrapi(Y0 - 4 + j, L.nyf), 0);
+        } else if (p < RS::NCOL + RS::NROW) {
+            const int q = p - RS::NCOL, ri = q / RS::RL, j = q - ri * RS::RL;
+            c = row_is_below(ri) ? R_B : R_T;
+            idx = ring_index(L, c, 0, wrapi(by + edge_tile(ri), nty), 0,
+                             wrapi(X0 - 4 + j, L.nx));
+        } else {
+            const int q = p - RS::NCOL - RS::NROW, ci = q / 4, ri = q % 4;
+            c = row_is_below(ri) ? (col_is_left(ci) ? R_BL : R_BR)
+                                 : (col_is_left(ci) ? R_TL : R_TR);
+            idx = ring_index(L, c, wrapi(bx + edge_tile(ci), ntx),
+                             wrapi(by + edge_tile(ri), nty), 0, 0);
+        }
+        cp_async<sizeof(rt)>(s_ring + p, ring[c] + idx);
+    }
+    cp_async_commit();
+}
+
+// Seam tiles: where the TMA boxes leave the lattice they fill zeros.  The
+// entries the step reads there are fetched from the wrapped nodes while the
+// boxes are in flight, into staging slots (seam_fix_load), and copied over
+// the zeros once the boxes have landed (seam_rho_apply, seam_pop_apply).
+//   density halo (rows of pitch RP from x = X0 - 4, y = Y0 - 2): the two
+//   halo columns or rows across the edge, columns X0 - 2 .. X0 + TX + 1;
+//   populations, odd steps (pin_x0 / pin_col layout): the three directions
+//   whose source x - e_i lies across the edge, at the edge column or row.
+// Slot t of each list is fixed by the enumeration below, so loading and
+// applying agree without storing positions.
+struct SeamEdges {
+    bool xl, xr, yb, yt;  // the tile touches the left / right / bottom / top edge
+};
+__device__ __forceinline__ SeamEdges seam_edges(const Lattice &L, int X0, int Y0, int TX,
+                                                int TY)
+{
+    return {X0 == 0, X0 + TX >= L.nx, Y0 == 0, Y0 + TY >= L.nyf};
+}
+template <int TX, int TY>
+struct SeamLists {
+    static constexpr int RHO_C = 2 * (TY + 4), RHO = RHO_C + 2 * (TX + 4);
+    static constexpr int POP_C = 3 * TY, POP = POP_C + 3 * TX;
+};
+// Density slot t: staged (ly, c); false when the slot is not used.
+template <int TX, int TY>
+__device__ __forceinline__ bool seam_rho_slot(const SeamEdges &e, int t, int &ly, int &c)
+{
+    using SL = SeamLists<TX, TY>;
+    if (t < SL::RHO_C) {
+        if (!e.xl && !e.xr) return false;
+        ly = t >> 1;
+        c = (e.xl ? 2 : TX + 4) + (t & 1);
+    } else {
+        if (!e.yb && !e.yt) return false;
+        const int q = t - SL::RHO_C, sel = q / (TX + 4);
+        ly = (e.yb ? 0 : TY + 2) + sel;
+        c = 2 + q - sel * (TX + 4);
+    }
+    return true;
+}
+// Population slot t: direction i at tile node (lx, ly).
+template <int TX, int TY>
+__device__ __forceinline__ bool seam_pop_slot(const SeamEdges &e, int t, int &i, int &lx,
+                                              int &ly)
+{
+    using SL = SeamLists<TX, TY>;
+    if (t < SL::POP_C) {
+        if (!e.xl && !e.xr) return false;
+        const int d = t / TY;
+        ly = t - d * TY;
+        lx = e.xl ? 0 : TX - 1;
+        // left edge: e_x = +1 reads x - 1 = -1; right edge: e_x = -1 reads x + 1 = nx
+        i = e.xl ? (d == 0 ? 1 : d == 1 ? 5 : 8) : (d == 0 ? 3 : d == 1 ? 6 : 7);
+    } else {
+        if (!e.yb && !e.yt) return false;
+        const int q = t - SL::POP_C, d = q / TX;
+        lx = q - d * TX;
+        ly = e.yb ? 0 : TY - 1;
+        i = e.yb ? (d == 0 ? 2 : d == 1 ? 5 : 6) : (d == 0 ? 4 : d == 1 ? 7 : 8);
+    }
+    return true;
+}
+template <class S, int TX, int TY, int NT, int PARITY>
+__device__ __forceinline__ void seam_fix_load(const Lattice &L, int cur, int X0, int Y0,
+                                              typename S::real *fix_rho,
+                                              typename S::pop_t *fix_pop)
+{
+    using rt = typename S::rho_t;
+    using pop_t = typename S::pop_t;
+    using SL = SeamLists<TX, TY>;
+    const SeamEdges e = seam_edges(L, X0, Y0, TX, TY);
+    const rt *R = (const rt *)L.rho[cur];
+    for (int t = threadIdx.x; t < SL::RHO; t += NT) {
+        int ly, c;
+        if (!seam_rho_slot<TX, TY>(e, t, ly, c)) continue;
+        const int x = wrapi(X0 - 4 + c, L.nx), r = wrapi(Y0 - 2 + ly, L.nyf);
+        fix_rho[t] = (typename S::real)R[(long long)r * L.pitch + x];
+    }
+    if (PARITY == 1) {
+        const pop_t *A = (const pop_t *)L.pops;
+        for (int t = threadIdx.x; t < SL::POP; t += NT) {
+            int i, lx, ly;
+            if (!seam_pop_slot<TX, TY>(e, t, i, lx, ly)) continue;
+            const int xs = wrapi(X0 + lx - ex(i), L.nx), rs = wrapi(Y0 + ly - ey(i), L.nyf);
+            fix_pop[t] = A[pidx(L, opp(i), rs, xs)];
+        }
+    }
+}
+template <class real, int TX, int TY, int NT, int RP>
+__device__ __forceinline__ void seam_rho_apply(const Lattice &L, int X0, int Y0,
+                                               const real *fix_rho, real *s_rho)
+{
+    const SeamEdges e = seam_edges(L, X0, Y0, TX, TY);
+    for (int t = threadIdx.x; t < SeamLists<TX, TY>::RHO; t += NT) {
+        int ly, c;
+        if (seam_rho_slot<TX, TY>(e, t, ly, c)) s_rho[ly * RP + c] = fix_rho[t];
+    }
+}
+template <class pop_t, int TX, int TY, int NT, int PLANE, int PP, int PX>
+__device__ __forceinline__ void seam_pop_apply(const Lattice &L, int X0, int Y0,
+                                               const pop_t *fix_pop, pop_t *s_pin)
+{
+    const SeamEdges e = seam_edges(L, X0, Y0, TX, TY);
+    for (int t = threadIdx.x; t < SeamLists<TX, TY>::POP; t += NT) {
+        int i, lx, ly;
+        if (seam_pop_slot<TX, TY>(e, t, i, lx, ly))
+            s_pin[(i - 1) * PLANE + ly * PP + lx + pin_col<1, PX>(i)] = fix_pop[t];
+    }
+}
+
 // Add the staged partial sums to the halo's tile-edge nodes of s_rho (rows
 // of pitch RP, halo node (lx, ly) at column lx + 2), in the order of
 // load_rho_stored.  Items 0 .. 4 HR - 1 take the four edge columns whole,
@@ -642,7 +797,12 @@ struct TmaSmem {
     static constexpr int NRING = RingStage<real, TX, TY>::N;
     static constexpr int NMU = MP * MH;
     static constexpr int NXCH = 2 * (STEP_THREADS / 32) * (TX + 2);
-    static constexpr int NSHARE = NRING > NXCH ? NRING : NXCH;  // ring, then exchange
+    // ring (and on seam tiles the staged population fix-ups after it), then
+    // the exchange slots
+    static constexpr int NFIXP = (SeamLists<TX, TY>::POP * sizeof(pop_t) + sizeof(real) - 1) /
+                                 sizeof(real);
+    static constexpr int NSHARE = NRING + NFIXP > NXCH ? NRING + NFIXP : NXCH;
+    static_assert(NMU >= SeamLists<TX, TY>::RHO, "density fix-ups staged in s_mu");
     static constexpr size_t bar_offset =
         (PIN_BYTES + sizeof(real) * (NRHO + NSHARE + NMU) + 15) / 16 * 16;
     static constexpr size_t bytes = bar_offset + 16;
@@ -669,7 +829,7 @@ __device__ __forceinline__ T lap_w(const T (&w)[3][3])
     return (T(4) * axial + diag - T(20) * w[1][1]) * T(1.0 / 6.0);
 }
 
-template <class S, int TX, int TY, int NT, int PARITY>
+template <class S, int TX, int TY, int NT, int PARITY, bool SEAM>
 __device__ __forceinline__ bool step_tile_tma(const Lattice &L, int cur, int X0,
                                               int Y0, unsigned char *smem_raw,
                                               const TmaMaps &maps,
@@ -693,13 +853,16 @@ __device__ __forceinline__ bool step_tile_tma(const Lattice &L, int cur, int X0,
     real *s_down = s_up + NW * XW;                       // [NW][XW]
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int nxt = cur ^ 1;
+    // SEAM: a seam tile (tile_kind), whose halo wraps around a periodic edge
+    constexpr bool seam = SEAM;
 
     // 1. Loads (bar: the caller's two initialised mbarriers, this tile
     //    completing phase `phase` of each).  Density halo and populations by
     //    TMA and the partial sums by bulk copies (thread 0), the corner sums
-    //    by cp.async.
+    //    by cp.async; on seam tiles all partial sums by cp.async, wrapped.
     if (threadIdx.x == 0) {
-        mbar_expect_tx(&bar[0], TS::tx_rho + RingStage<real, TX, TY>::bulk_bytes);
+        mbar_expect_tx(&bar[0],
+                       TS::tx_rho + (seam ? 0u : RingStage<real, TX, TY>::bulk_bytes));
         tma_load_2d(s_rho, &maps.rho[cur], X0 - 4, Y0 - 2, &bar[0]);
         mbar_expect_tx(&bar[1], TS::tx_pops);
 #pragma unroll
@@ -710,9 +873,19 @@ __device__ __forceinline__ bool step_tile_tma(const Lattice &L, int cur, int X0,
                         X0 + pin_x0<PARITY, TS::PX>(i), y0, plane, &bar[1]);
         }
     }
-    stage_ring<real, TX, TY>(L, cur, X0, Y0, s_ring, &bar[0]);
+    pop_t *fix_pop = reinterpret_cast<pop_t *>(s_ring + TS::NRING);
+    if (seam) {
+        stage_ring_wrapped<real, TX, TY, NT>(L, cur, X0, Y0, s_ring);
+        seam_fix_load<S, TX, TY, NT, PARITY>(L, cur, X0, Y0, s_mu, fix_pop);
+    } else {
+        stage_ring<real, TX, TY>(L, cur, X0, Y0, s_ring, &bar[0]);
+    }
     cp_async_wait_all();
     if (!tma_landed(bar, 0, phase, L.err)) return false;
+    if (seam) {
+        seam_rho_apply<real, TX, TY, NT, RP>(L, X0, Y0, s_mu, s_rho);
+        __syncthreads();
+    }
 
     // 2. Partial sums into the halo's tile-edge nodes (order of
     //    load_rho_stored).  Halo (lx, ly) of the (TX + 4)-wide convention is
@@ -756,6 +929,10 @@ __device__ __forceinline__ bool step_tile_tma(const Lattice &L, int cur, int X0,
     // the populations were in flight during steps 2 and 3; the barrier also
     // publishes s_mu
     if (!tma_landed(bar, 1, phase, L.err)) return false;
+    if (PARITY == 1 && seam) {
+        seam_pop_apply<pop_t, TX, TY, NT, PLANE, PP, TS::PX>(L, X0, Y0, fix_pop, s_pin);
+        __syncthreads();
+    }
 
     // 4. Force, collision, in-place streaming and the register hand-over for
     //    the thread's PER nodes at rows ly0 .. ly0 + PER - 1, column lx.
@@ -766,11 +943,18 @@ __device__ __forceinline__ bool step_tile_tma(const Lattice &L, int cur, int X0,
     pop_t *A = (pop_t *)L.pops;
     rho_t *Rn = (rho_t *)L.rho[nxt];
     rho_t *const *ring = (rho_t *const *)L.ring[nxt];
-    int woff[9];  // 32-bit: the TMA maps exist only when 8 planes fit
+    // 32-bit write offsets (the TMA maps exist only when 8 planes fit); on
+    // odd steps of seam tiles an x target across a periodic edge is brought
+    // back by nx (lanes 0 and 31), a row target by the lattice height (rows
+    // 0 and TY - 1, wrap_y below)
+    const int cxl = (PARITY == 1 && seam && X0 == 0 && lane == 0) ? L.nx : 0;
+    const int cxr = (PARITY == 1 && seam && X0 + TX >= L.nx && lane == TX - 1) ? -L.nx : 0;
+    int woff[9];
 #pragma unroll
     for (int i = 1; i < 9; ++i)
         woff[i] = PARITY == 0 ? (opp(i) - 1) * (int)L.plane
-                              : (i - 1) * (int)L.plane + ey(i) * L.pitch + ex(i);
+                              : (i - 1) * (int)L.plane + ey(i) * L.pitch + ex(i) +
+                                    (ex(i) < 0 ? cxl : ex(i) > 0 ? cxr : 0);
     const bool has_l = lane > 0, has_r = lane < 31;
     real wr[3][3], wm[3][3];
 #pragma unroll
@@ -790,7 +974,8 @@ __device__ __forceinline__ bool step_tile_tma(const Lattice &L, int cur, int X0,
     const int cls_c = lane == 0 ? R_R : R_L;
     // this tile, and the tile of the ring column a lane feeds (classes L and
     // R share one index layout)
-    const int bx = X0 / TX, by = Y0 / TY, bxc = lane == 0 ? bx - 1 : bx + 1;
+    const int bx = X0 / TX, by = Y0 / TY;
+    const int bxc = neighbour_tile(bx, lane == 0 ? -1 : 1, L.nx / TX, seam);
     const bool col_lane = lane == 0 || lane == 31;
     pop_t *Arow = A + (long long)(Y0 + ly0) * L.pitch + X0 + lx;
 #pragma unroll
@@ -814,8 +999,14 @@ __device__ __forceinline__ bool step_tile_tma(const Lattice &L, int cur, int X0,
         const real Fy = gry * real(1.0 / 3.0) - rho * gmy;
         real fp[9];
         collide<real>(f, drho, rho, Fx, Fy, tau, omega, fp);
+        {
+            const int wrap_y = L.nyf * L.pitch;
+            const int cyb = (PARITY == 1 && seam && Y0 == 0 && ly == 0) ? wrap_y : 0;
+            const int cyt = (PARITY == 1 && seam && Y0 + TY >= L.nyf && ly == TY - 1) ? -wrap_y : 0;
 #pragma unroll
-        for (int i = 1; i < 9; ++i) st_real(Arow + woff[i], fp[i]);
+            for (int i = 1; i < 9; ++i)
+                st_real(Arow + woff[i] + (ey(i) < 0 ? cyb : ey(i) > 0 ? cyt : 0), fp[i]);
+        }
         Arow += L.pitch;
 
         // lane-neighbour parts of the hand-over
@@ -884,15 +1075,19 @@ __device__ __forceinline__ bool step_tile_tma(const Lattice &L, int cur, int X0,
         if (col_lane) ring[cls_c][ring_index(L, R_L, bxc, by, Y0 + ly0, xc)] = (rho_t)first_c;
     }
     // ring rows below and above the tile, with their corners
+    const int bxl = neighbour_tile(bx, -1, L.nx / TX, seam);
+    const int bxr = neighbour_tile(bx, 1, L.nx / TX, seam);
     if (warp == 0) {
-        ring[R_T][ring_index(L, R_T, bx, by - 1, Y0 - 1, X0 + lx)] = (rho_t)s_down[lane];
-        if (lane == 0) ring[R_TR][ring_index(L, R_TR, bx - 1, by - 1, Y0 - 1, X0 - 1)] = (rho_t)s_down[TX];
-        if (lane == 31) ring[R_TL][ring_index(L, R_TL, bx + 1, by - 1, Y0 - 1, X0 + TX)] = (rho_t)s_down[TX + 1];
+        const int byb = neighbour_tile(by, -1, L.nyf / TY, seam);
+        ring[R_T][ring_index(L, R_T, bx, byb, Y0 - 1, X0 + lx)] = (rho_t)s_down[lane];
+        if (lane == 0) ring[R_TR][ring_index(L, R_TR, bxl, byb, Y0 - 1, X0 - 1)] = (rho_t)s_down[TX];
+        if (lane == 31) ring[R_TL][ring_index(L, R_TL, bxr, byb, Y0 - 1, X0 + TX)] = (rho_t)s_down[TX + 1];
     }
     if (warp == NW - 1) {
-        ring[R_B][ring_index(L, R_B, bx, by + 1, Y0 + TY, X0 + lx)] = (rho_t)up_prev;
-        if (lane == 0) ring[R_BR][ring_index(L, R_BR, bx - 1, by + 1, Y0 + TY, X0 - 1)] = (rho_t)up_prev_c;
-        if (lane == 31) ring[R_BL][ring_index(L, R_BL, bx + 1, by + 1, Y0 + TY, X0 + TX)] = (rho_t)up_prev_c;
+        const int byt = neighbour_tile(by, 1, L.nyf / TY, seam);
+        ring[R_B][ring_index(L, R_B, bx, byt, Y0 + TY, X0 + lx)] = (rho_t)up_prev;
+        if (lane == 0) ring[R_BR][ring_index(L, R_BR, bxl, byt, Y0 + TY, X0 - 1)] = (rho_t)up_prev_c;
+        if (lane == 31) ring[R_BL][ring_index(L, R_BL, bxr, byt, Y0 + TY, X0 + TX)] = (rho_t)up_prev_c;
     }
     return true;
 }
@@ -1071,7 +1266,10 @@ struct TmaPairSmem {
     static constexpr int NMU = MP * MH;
     static constexpr int XW = TX + 2;              // exchange slots per warp
     static constexpr int NXCH = 2 * NW * XW;
-    static constexpr int NSHARE = NRING > NXCH ? NRING : NXCH;  // ring, then exchange
+    // as TmaSmem
+    static constexpr int NFIXP = (SeamLists<TX, TY>::POP * sizeof(pop_t) + 3) / 4;
+    static constexpr int NSHARE = NRING + NFIXP > NXCH ? NRING + NFIXP : NXCH;
+    static_assert(NMU >= SeamLists<TX, TY>::RHO, "density fix-ups staged in s_mu");
     static constexpr size_t bar_offset =
         (PIN_BYTES + sizeof(float) * (NRHO + NSHARE + NMU) + 15) / 16 * 16;
     static constexpr size_t bytes = bar_offset + 16;
@@ -1083,7 +1281,7 @@ struct TmaPairSmem {
                   "pair-aligned sub-arrays");
 };
 
-template <class S, int TX, int TY, int NT, int PARITY>
+template <class S, int TX, int TY, int NT, int PARITY, bool SEAM>
 __device__ __forceinline__ bool step_tile_tma_pair(const Lattice &L, int cur, int X0,
                                                    int Y0, unsigned char *smem_raw,
                                                    const TmaMaps &maps,
@@ -1108,10 +1306,13 @@ __device__ __forceinline__ bool step_tile_tma_pair(const Lattice &L, int cur, in
     float *s_down = s_up + NW * XW;                       // [NW][XW]
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int nxt = cur ^ 1;
+    // SEAM: a seam tile (tile_kind), whose halo wraps around a periodic edge
+    constexpr bool seam = SEAM;
 
-    // 1. Loads (bar, phase: as step_tile_tma).
+    // 1. Loads (bar, phase, seam tiles: as step_tile_tma).
     if (threadIdx.x == 0) {
-        mbar_expect_tx(&bar[0], TS::tx_rho + RingStage<float, TX, TY>::bulk_bytes);
+        mbar_expect_tx(&bar[0],
+                       TS::tx_rho + (seam ? 0u : RingStage<float, TX, TY>::bulk_bytes));
         tma_load_2d(s_rho, &maps.rho[cur], X0 - 4, Y0 - 2, &bar[0]);
         mbar_expect_tx(&bar[1], TS::tx_pops);
 #pragma unroll
@@ -1122,9 +1323,19 @@ __device__ __forceinline__ bool step_tile_tma_pair(const Lattice &L, int cur, in
                         X0 + pin_x0<PARITY, TS::PX>(i), y0, plane, &bar[1]);
         }
     }
-    stage_ring<float, TX, TY>(L, cur, X0, Y0, s_ring, &bar[0]);
+    pop_t *fix_pop = reinterpret_cast<pop_t *>(s_ring + TS::NRING);
+    if (seam) {
+        stage_ring_wrapped<float, TX, TY, NT>(L, cur, X0, Y0, s_ring);
+        seam_fix_load<S, TX, TY, NT, PARITY>(L, cur, X0, Y0, s_mu, fix_pop);
+    } else {
+        stage_ring<float, TX, TY>(L, cur, X0, Y0, s_ring, &bar[0]);
+    }
     cp_async_wait_all();
     if (!tma_landed(bar, 0, phase, L.err)) return false;
+    if (seam) {
+        seam_rho_apply<float, TX, TY, NT, RP>(L, X0, Y0, s_mu, s_rho);
+        __syncthreads();
+    }
 
     // 2. Partial sums into the halo's tile-edge nodes (order of
     //    load_rho_stored); halo (lx, ly) is staged at row ly, column lx + 2.
@@ -1162,6 +1373,10 @@ __device__ __forceinline__ bool step_tile_tma_pair(const Lattice &L, int cur, in
     // the populations were in flight during steps 2 and 3; the barrier also
     // publishes s_mu
     if (!tma_landed(bar, 1, phase, L.err)) return false;
+    if (PARITY == 1 && seam) {
+        seam_pop_apply<pop_t, TX, TY, NT, PLANE, PP, TS::PX>(L, X0, Y0, fix_pop, s_pin);
+        __syncthreads();
+    }
 
     // 4. Force, collision, in-place streaming and the register hand-over for
     //    the pair at columns x0, x0 + 1 of rows ly0 .. ly0 + PER - 1.
@@ -1187,9 +1402,16 @@ __device__ __forceinline__ bool step_tile_tma_pair(const Lattice &L, int cur, in
     const int cls_c = lane == 0 ? R_R : R_L;
     // this tile, and the tile of the ring column a lane feeds (classes L and
     // R share one index layout)
-    const int bx = X0 / TX, by = Y0 / TY, bxc = lane == 0 ? bx - 1 : bx + 1;
+    const int bx = X0 / TX, by = Y0 / TY, ntx = L.nx / TX, nty = L.nyf / TY;
+    const int bxl = seam ? wrapi(bx - 1, ntx) : bx - 1, bxr = seam ? wrapi(bx + 1, ntx) : bx + 1;
+    const int byb = seam ? wrapi(by - 1, nty) : by - 1, byt = seam ? wrapi(by + 1, nty) : by + 1;
+    const int bxc = lane == 0 ? bxl : bxr;
     const bool col_lane = lane == 0 || lane == 31;
     pop_t *Arow = A + (long long)(Y0 + ly0) * L.pitch + X0 + x0;
+    // corrections of odd-step write offsets across the periodic edges
+    const int wrap_y = L.nyf * L.pitch;
+    const int cxl = (PARITY == 1 && seam && X0 == 0 && lane == 0) ? L.nx : 0;
+    const int cxr = (PARITY == 1 && seam && X0 + TX >= L.nx && lane == 31) ? -L.nx : 0;
 #pragma unroll
     for (int k = 0; k < PER; ++k) {
         const int ly = ly0 + k;
@@ -1214,14 +1436,21 @@ __device__ __forceinline__ bool step_tile_tma_pair(const Lattice &L, int cur, in
         const float2 Fy = psub(pmul(gry, third), pmul(rho, gmy));
         float2 fp[9];
         collide2(f, drho, rho, Fx, Fy, tau, omega, fp);
+        {
+            // odd steps on seam tiles: a target across a periodic edge is
+            // brought back by one lattice length (the x-shifted directions
+            // are stored one node at a time)
+            const int cyb = (PARITY == 1 && seam && Y0 == 0 && ly == 0) ? wrap_y : 0;
+            const int cyt = (PARITY == 1 && seam && Y0 + TY >= L.nyf && ly == TY - 1) ? -wrap_y : 0;
 #pragma unroll
-        for (int i = 1; i < 9; ++i) {
-            pop_t *dst = Arow + woff[i];
-            if (PARITY == 0 || ex(i) == 0) {
-                st_pair(dst, fp[i]);
-            } else {
-                st_real(dst, fp[i].x);
-                st_real(dst + 1, fp[i].y);
+            for (int i = 1; i < 9; ++i) {
+                pop_t *dst = Arow + woff[i] + (ey(i) < 0 ? cyb : ey(i) > 0 ? cyt : 0);
+                if (PARITY == 0 || ex(i) == 0) {
+                    st_pair(dst, fp[i]);
+                } else {
+                    st_real(dst + (ex(i) < 0 ? cxl : 0), fp[i].x);
+                    st_real(dst + 1 + (ex(i) > 0 ? cxr : 0), fp[i].y);
+                }
             }
         }
         Arow += L.pitch;
@@ -1293,15 +1522,15 @@ __device__ __forceinline__ bool step_tile_tma_pair(const Lattice &L, int cur, in
     }
     // ring rows below and above the tile, with their corners
     if (warp == 0) {
-        *reinterpret_cast<float2 *>(ring[R_T] + ring_index(L, R_T, bx, by - 1, Y0 - 1, X0 + x0)) =
+        *reinterpret_cast<float2 *>(ring[R_T] + ring_index(L, R_T, bx, byb, Y0 - 1, X0 + x0)) =
             *reinterpret_cast<const float2 *>(s_down + x0);
-        if (lane == 0) ring[R_TR][ring_index(L, R_TR, bx - 1, by - 1, Y0 - 1, X0 - 1)] = s_down[TX];
-        if (lane == 31) ring[R_TL][ring_index(L, R_TL, bx + 1, by - 1, Y0 - 1, X0 + TX)] = s_down[TX + 1];
+        if (lane == 0) ring[R_TR][ring_index(L, R_TR, bxl, byb, Y0 - 1, X0 - 1)] = s_down[TX];
+        if (lane == 31) ring[R_TL][ring_index(L, R_TL, bxr, byb, Y0 - 1, X0 + TX)] = s_down[TX + 1];
     }
     if (warp == NW - 1) {
-        *reinterpret_cast<float2 *>(ring[R_B] + ring_index(L, R_B, bx, by + 1, Y0 + TY, X0 + x0)) = up_prev;
-        if (lane == 0) ring[R_BR][ring_index(L, R_BR, bx - 1, by + 1, Y0 + TY, X0 - 1)] = up_prev_c;
-        if (lane == 31) ring[R_BL][ring_index(L, R_BL, bx + 1, by + 1, Y0 + TY, X0 + TX)] = up_prev_c;
+        *reinterpret_cast<float2 *>(ring[R_B] + ring_index(L, R_B, bx, byt, Y0 + TY, X0 + x0)) = up_prev;
+        if (lane == 0) ring[R_BR][ring_index(L, R_BR, bxl, byt, Y0 + TY, X0 - 1)] = up_prev_c;
+        if (lane == 31) ring[R_BL][ring_index(L, R_BL, bxr, byt, Y0 + TY, X0 + TX)] = up_prev_c;
     }
     return true;
 }
@@ -1333,8 +1562,7 @@ struct HasTma {
 
 template <class S, int TX, int TY, int NT, int PARITY>
 __global__ void __launch_bounds__(NT, HasTmaPair<S, TX, TY, NT>::value ? 512 / NT : 0)
-    step_kernel(const Lattice L, int cur, int xlo, int xhi, int ylo, int yhi,
-                const __grid_constant__ TmaMaps maps)
+    step_kernel(const Lattice L, int cur, int seams, const __grid_constant__ TmaMaps maps)
 {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     // Odd steps walk the tile grid backwards: the tiles a step writes last,
@@ -1342,20 +1570,33 @@ __global__ void __launch_bounds__(NT, HasTmaPair<S, TX, TY, NT>::value ? 512 / N
     const int bx = PARITY ? gridDim.x - 1 - blockIdx.x : blockIdx.x;
     const int by = PARITY ? gridDim.y - 1 - blockIdx.y : blockIdx.y;
     const int X0 = bx * TX, Y0 = by * TY;
-    const bool interior = bx >= xlo && bx <= xhi && by >= ylo && by <= yhi;
+    // seams: seam_bits of the lattice, for the kernels whose TMA path takes
+    // seam tiles (0 for the others)
+    const int kind = tile_kind(L, TX, TY, bx, by, seams);
+    const bool interior = kind == TILE_INTERIOR;
     if constexpr (HasTma<S, TX, TY, NT>::value || HasTmaPair<S, TX, TY, NT>::value) {
-        if (interior && maps.valid) {
+        if (kind != TILE_GENERAL && maps.valid) {
             __shared__ __align__(8) unsigned long long bar[2];
             if (threadIdx.x == 0) {
                 mbar_init(&bar[0], 1);
                 mbar_init(&bar[1], 1);
             }
             __syncthreads();
-            if constexpr (HasTma<S, TX, TY, NT>::value)
-                step_tile_tma<S, TX, TY, NT, PARITY>(L, cur, X0, Y0, smem_raw, maps, bar, 0);
-            else
-                step_tile_tma_pair<S, TX, TY, NT, PARITY>(L, cur, X0, Y0, smem_raw, maps,
-                                                          bar, 0);
+            if constexpr (HasTma<S, TX, TY, NT>::value) {
+                if (interior)
+                    step_tile_tma<S, TX, TY, NT, PARITY, false>(L, cur, X0, Y0, smem_raw,
+                                                                maps, bar, 0);
+                else
+                    step_tile_tma<S, TX, TY, NT, PARITY, true>(L, cur, X0, Y0, smem_raw,
+                                                               maps, bar, 0);
+            } else {
+                if (interior)
+                    step_tile_tma_pair<S, TX, TY, NT, PARITY, false>(L, cur, X0, Y0,
+                                                                     smem_raw, maps, bar, 0);
+                else
+                    step_tile_tma_pair<S, TX, TY, NT, PARITY, true>(L, cur, X0, Y0,
+                                                                    smem_raw, maps, bar, 0);
+            }
             return;
         }
     }
@@ -1394,15 +1635,16 @@ static cudaError_t launch_shape(const Lattice &L, int parity, int cur,
         if (e != cudaSuccess) return e;
         configured = dev;
     }
-    // Interior tiles: the tile and its eight neighbours are full tiles and
-    // the halo and ring need no wrap and meet no solid row.
+    // Tile classes (tile_kind): the 32-wide TMA path also takes the seam
+    // tiles of periodic edges.
     const int ntx = (L.nx + TX - 1) / TX, nty = (L.nyf + TY - 1) / TY;
-    const int nfx = L.nx / TX, nfy = L.nyf / TY;  // full tiles per direction
+    const int seams = HasTma<S, TX, TY, NT>::value || HasTmaPair<S, TX, TY, NT>::value
+                          ? seam_bits(L, TX, TY) : 0;
     dim3 grid(ntx, nty);
     if (parity == 0)
-        k0<<<grid, NT, smem, s>>>(L, cur, 1, nfx - 2, 1, nfy - 2, m);
+        k0<<<grid, NT, smem, s>>>(L, cur, seams, m);
     else
-        k1<<<grid, NT, smem, s>>>(L, cur, 1, nfx - 2, 1, nfy - 2, m);
+        k1<<<grid, NT, smem, s>>>(L, cur, seams, m);
     return cudaGetLastError();
 }
 
@@ -1463,7 +1705,7 @@ __global__ void __launch_bounds__(NT, sizeof(typename S::real) == 8 ? 2 : 4)
         bool done = false;
         if constexpr (HasTma<S, TX, TY, NT>::value) {
             const TmaMaps &m = maps[it.inst];
-            if (tma && it.interior && m.valid && m.tx == TX && m.ty == TY) {
+            if (tma && it.kind != TILE_GENERAL && m.valid && m.tx == TX && m.ty == TY) {
                 if (threadIdx.x == 0 && fenced != it.inst) {
                     // the maps were written by the host: make the tensor-map
                     // proxy see their current contents
@@ -1474,14 +1716,18 @@ __global__ void __launch_bounds__(NT, sizeof(typename S::real) == 8 ? 2 : 4)
                 fenced = it.inst;
                 // a wait that gave up leaves the barriers in doubt: the rest
                 // of this CTA's items take the general path
-                tma = step_tile_tma<S, TX, TY, NT, PARITY>(sL, cur, it.bx * TX, it.by * TY,
-                                                           smem_raw, m, bar, phase);
+                // interior tiles only: the seam variant would take the kernel
+                // past the 64 registers of four resident CTAs, and the spills
+                // cost the batch more than its seam tiles gain
+                tma = step_tile_tma<S, TX, TY, NT, PARITY, false>(sL, cur, it.bx * TX,
+                                                                  it.by * TY, smem_raw, m,
+                                                                  bar, phase);
                 phase ^= 1u;
                 done = true;
             }
         }
         if (!done) {
-            if (it.interior)
+            if (it.kind == TILE_INTERIOR)
                 step_tile<S, TX, TY, NT, PARITY, true>(sL, cur, it.bx * TX,
                                                        it.by * TY, smem_raw);
             else

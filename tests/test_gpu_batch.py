@@ -21,6 +21,8 @@ SPECS = [
          kappa=0.01),
     dict(nx=230, ny=140, eos="vdw", a=9 / 49, b=2 / 21, Tr=0.85, tau=1.0,
          kappa=0.01, walls=True),
+    # 3 x 3 tiles of 32 x 32: every tile but the centre wraps around an edge
+    dict(nx=96, ny=96, eos="cs", a=1.0, b=4.0, Tr=0.85, tau=1.0, kappa=0.5),
 ]
 
 

@@ -150,6 +150,67 @@ def _coexistence(case):
 # oracle: the density and populations carry FP32 rounding of a few ulp per
 # step, mu (~100x cancellation) and the velocity (small against the
 # populations it is summed from) proportionally more.
+# Seam tiles: full tiles whose halo wraps around a periodic edge (at least
+# three tiles across that edge) take the 32-wide TMA path, with the wrapped
+# parts of the halo, the partial sums and the odd-step populations loaded
+# element by element and the writes across the edge wrapped.
+SEAM_CASES = [
+    ((32, 32), False, (96, 96)),    # 3 x 3 tiles: all but the centre wrap
+    ((32, 16), False, (128, 48)),   # corners, left/right and bottom/top seams
+    ((32, 24), False, (96, 72)),
+    ((32, 16), True, (96, 50)),     # walls: left and right seams only
+    ((32, 32), False, (160, 100)),  # ragged rows: left and right seams only
+]
+
+
+@pytest.mark.parametrize("tile,walls,size", SEAM_CASES)
+def test_seam_tiles_fp64(tile, walls, size, oracle_threads):
+    nx, ny = size
+    sim, ref, rho = _setup("cs", nx, ny, walls)
+    with sim:
+        sim.set_tile(*tile)
+        sim.init(rho)
+        ref.init_equilibrium(rho)
+        # both parities of the in-place pattern; the TMA path adds the
+        # density hand-over in another order than the oracle, and near
+        # coexistence mu (~2e-3 here) is the difference of terms ~50x its
+        # size, so one last-bit density difference shows as ~1e-13 in mu
+        for _ in range(2):
+            sim.step(1)
+            ref.step(1)
+            _compare(sim, ref, 1e-12)
+        sim.step(198)
+        ref.step(198)
+        _compare(sim, ref, 1e-11)
+
+
+@pytest.mark.parametrize("tile,walls,size", SEAM_CASES[:2] + SEAM_CASES[3:4] + [
+    ((64, 16), False, (192, 48)),   # two nodes per lane: 3 x 3 tiles
+    ((64, 32), True, (192, 98)),
+])
+@pytest.mark.parametrize("precision", ["f32", "f32_offset"])
+def test_seam_tiles_fp32(tile, walls, size, precision, monkeypatch):
+    # against the oracle (tolerance as test_every_tile_shape) and against the
+    # same lattice with every tile on the general path
+    nx, ny = size
+    ref_rho = 0.5 * sum(_coexistence("cs")) if precision == "f32_offset" else 0.0
+    runs = []
+    for no_tma in (False, True):
+        if no_tma:
+            monkeypatch.setenv("CPLBM_NO_TMA", "1")
+        sim, ref, rho = _setup("cs", nx, ny, walls, precision=precision,
+                               rho_ref=ref_rho)
+        with sim:
+            sim.set_tile(*tile)
+            sim.init(rho).step(60)
+            runs.append(sim.moments())
+    ref.init_equilibrium(rho).step(60)
+    want = ref.moments()
+    for k in ("rho", "mu", "vx", "vy"):
+        assert _rel(runs[0][k], want[k]) < 1e-4, (k, _rel(runs[0][k], want[k]))
+        assert _rel(runs[0][k], runs[1][k]) < 1e-4, (k, _rel(runs[0][k], runs[1][k]))
+
+
 @pytest.mark.parametrize("case", list(EOS_CASES))
 @pytest.mark.parametrize("precision", ["f32", "f32_offset"])
 @pytest.mark.parametrize("tile,walls", [((64, 16), False), ((64, 32), True),
@@ -345,7 +406,8 @@ def test_full_size_sampled_one_step(precision, tol):
 
 
 @pytest.mark.parametrize("tile", [(32, 16), (32, 24), (32, 32), (64, 16), (64, 32)])
-def test_fp16_storage_tma_path(tile, monkeypatch):
+@pytest.mark.parametrize("size", [(330, 200), (192, 96)])  # 192 x 96: seam tiles
+def test_fp16_storage_tma_path(tile, size, monkeypatch):
     # FP16 storage: interior tiles stage the half populations by TMA; the
     # same lattice with every tile on the general path (no tensor maps)
     # does the same FP32 arithmetic on the same half inputs.  The two paths
@@ -357,7 +419,7 @@ def test_fp16_storage_tma_path(tile, monkeypatch):
     for no_tma in (False, True):
         if no_tma:
             monkeypatch.setenv("CPLBM_NO_TMA", "1")
-        sim, ref, rho = _setup("cs", 330, 200, False, precision="f16_offset",
+        sim, ref, rho = _setup("cs", *size, False, precision="f16_offset",
                                rho_ref=0.5 * (rv + rl))
         with sim:
             sim.set_tile(*tile)
