@@ -107,9 +107,10 @@ lbm_status lbm_set_wall_mu(lbm_ctx *ctx, double mu_bottom, int top_mode,
                            double mu_top);
 
 /* Tile shape of the fused step kernel: tx x ty fluid nodes per CTA, one of
- * 32x16, 32x24, 32x32, 64x16 (LBM_ERR_ARG otherwise).  The shape changes
- * speed only, not results.  May be called at any time; the default depends
- * on the precision. */
+ * 32x16, 32x24, 32x32, 64x16, 64x32 (LBM_ERR_ARG otherwise).  The shape
+ * changes speed, and in FP32 arithmetic the rounding order of some sums,
+ * not the method.  May be called at any time.  Default: 64x16 (two nodes
+ * per lane) for FP32 arithmetic, 32x32 for FP64. */
 lbm_status lbm_set_tile(lbm_ctx *ctx, int tx, int ty);
 lbm_status lbm_get_tile(const lbm_ctx *ctx, int *tx, int *ty);
 
@@ -218,8 +219,9 @@ lbm_status lbm_batch_moments(lbm_batch *b, int index, double *rho, double *vx,
 lbm_status lbm_batch_populations(lbm_batch *b, int index, double *f,
                                  int on_device);
 lbm_status lbm_batch_reduce(lbm_batch *b, int index, double out[4]);
-/* Tile shape of the batched kernel (as lbm_set_tile), or the fastest one
- * measured over nsteps steps with the state restored afterwards. */
+/* Tile shape of the batched kernel (as lbm_set_tile; default 32x32, the
+ * width its TMA path takes), or the fastest one measured over nsteps steps
+ * with the state restored afterwards. */
 lbm_status lbm_batch_set_tile(lbm_batch *b, int tx, int ty);
 lbm_status lbm_batch_autotune(lbm_batch *b, int nsteps, int *tx, int *ty);
 /* Lattice count, total nodes, steps taken, tile shape (any may be NULL). */

@@ -202,7 +202,9 @@ lbm_status lbm_batch_create(const lbm_instance *inst, int count, int precision,
         }
         b->own_stream = true;
     }
-    step_default_shape(precision, &b->tx, &b->ty);
+    // the batched kernel's TMA path is the 32-wide one
+    b->tx = 32;
+    b->ty = 32;
     for (int i = 0; i < count && st == LBM_OK; ++i) {
         const lbm_instance &q = inst[i];
         lbm_config cfg{q.nx, q.ny, q.walls, q.tau, q.kappa, q.rho_ref, precision,

@@ -76,10 +76,10 @@ int step_shapes(int *tx, int *ty, int max)
 void step_default_shape(int prec, int *tx, int *ty)
 {
     // fastest measured on GB300 for the 4096^2 workload (lbm_autotune picks
-    // per lattice): 32 x 32, and for FP16 storage the two-nodes-per-lane
-    // path's 64 x 16
-    *tx = prec == P_F16_OFF ? 64 : 32;
-    *ty = prec == P_F16_OFF ? 16 : 32;
+    // per lattice): the two-nodes-per-lane path's 64 x 16 for FP32
+    // arithmetic (FP32, FP32-offset and FP16 storage), 32 x 32 for FP64
+    *tx = prec == P_F64 ? 32 : 64;
+    *ty = prec == P_F64 ? 32 : 16;
 }
 
 void pt_shape(int prec, int *tx, int *ty)

@@ -1560,8 +1560,11 @@ struct HasTma {
     static constexpr bool value = TX == 32 && (TY % (NT / 32)) == 0;
 };
 
+// Pair-path kernels ask for 640 / NT resident CTAs: five of 128 threads
+// (96 registers, no spills), which FP16 storage's shared memory allows
+// (100 -> 108 GLUPS at 4096^2, 64 x 16); FP32 storage's fits four.
 template <class S, int TX, int TY, int NT, int PARITY>
-__global__ void __launch_bounds__(NT, HasTmaPair<S, TX, TY, NT>::value ? 512 / NT : 0)
+__global__ void __launch_bounds__(NT, HasTmaPair<S, TX, TY, NT>::value ? 640 / NT : 0)
     step_kernel(const Lattice L, int cur, int seams, const __grid_constant__ TmaMaps maps)
 {
     extern __shared__ __align__(128) unsigned char smem_raw[];
