@@ -1560,11 +1560,19 @@ struct HasTma {
     static constexpr bool value = TX == 32 && (TY % (NT / 32)) == 0;
 };
 
-// Pair-path kernels ask for 640 / NT resident CTAs: five of 128 threads
-// (96 registers, no spills), which FP16 storage's shared memory allows
-// (100 -> 108 GLUPS at 4096^2, 64 x 16); FP32 storage's fits four.
+// Resident CTAs a pair-path kernel asks for (__launch_bounds__): 640 / NT,
+// five of 128 threads at 96 registers; six for FP16 storage at 64 x 16
+// (80 registers), whose TMA path needs 31 KB of shared memory, so six fit
+// when a launch has no general tile (launch_shape).
+template <class S, int TX, int TY, int NT>
+constexpr int pair_min_ctas()
+{
+    return sizeof(typename S::pop_t) == 2 && NT == 128 ? 6 : 640 / NT;
+}
+
 template <class S, int TX, int TY, int NT, int PARITY>
-__global__ void __launch_bounds__(NT, HasTmaPair<S, TX, TY, NT>::value ? 640 / NT : 0)
+__global__ void __launch_bounds__(NT, HasTmaPair<S, TX, TY, NT>::value
+                                          ? pair_min_ctas<S, TX, TY, NT>() : 0)
     step_kernel(const Lattice L, int cur, int seams, const __grid_constant__ TmaMaps maps)
 {
     extern __shared__ __align__(128) unsigned char smem_raw[];
@@ -1620,7 +1628,7 @@ static cudaError_t launch_shape(const Lattice &L, int parity, int cur,
     if constexpr (HasTma<S, TX, TY, NT>::value) smem_tma = TmaSmem<S, TX, TY>::bytes;
     if constexpr (HasTmaPair<S, TX, TY, NT>::value)
         smem_tma = TmaPairSmem<typename S::pop_t, TX, TY, NT>::bytes;
-    const size_t smem = smem_v4 > smem_tma ? smem_v4 : smem_tma;
+    const size_t smem_max = smem_v4 > smem_tma ? smem_v4 : smem_tma;
     TmaMaps m{};
     if (maps && maps->valid && maps->tx == TX && maps->ty == TY) m = *maps;
     auto k0 = step_kernel<S, TX, TY, NT, 0>;
@@ -1631,18 +1639,23 @@ static cudaError_t launch_shape(const Lattice &L, int parity, int cur,
     if (e != cudaSuccess) return e;
     if (configured != dev) {
         e = cudaFuncSetAttribute(k0, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)smem);
+                                 (int)smem_max);
         if (e == cudaSuccess)
             e = cudaFuncSetAttribute(
-                k1, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+                k1, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_max);
         if (e != cudaSuccess) return e;
         configured = dev;
     }
-    // Tile classes (tile_kind): the 32-wide TMA path also takes the seam
-    // tiles of periodic edges.
+    // Tile classes (tile_kind): the TMA paths also take the seam tiles of
+    // periodic edges.
     const int ntx = (L.nx + TX - 1) / TX, nty = (L.nyf + TY - 1) / TY;
     const int seams = HasTma<S, TX, TY, NT>::value || HasTmaPair<S, TX, TY, NT>::value
                           ? seam_bits(L, TX, TY) : 0;
+    // When both periodic directions are seams and the maps are valid, every
+    // tile is interior or seam and takes the TMA path (step_kernel has no
+    // general fallback on it), so the launch needs only that path's shared
+    // memory, and more CTAs fit.
+    const size_t smem = (seams == 3 && m.valid && smem_tma > 0) ? smem_tma : smem_max;
     dim3 grid(ntx, nty);
     if (parity == 0)
         k0<<<grid, NT, smem, s>>>(L, cur, seams, m);
