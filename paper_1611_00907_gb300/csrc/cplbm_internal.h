@@ -157,16 +157,22 @@ __host__ __device__ inline int seam_bits(const Lattice &L, int tx, int ty)
     return s;
 }
 
-// Path class of tile (bx, by): TILE_INTERIOR when the tile and its eight
-// neighbours are full tiles and its halo neither wraps nor meets a wall;
-// TILE_SEAM when the same holds except that the halo wraps around a
-// periodic edge allowed by `seams` (seam_bits); TILE_GENERAL otherwise.
+// Path class of tile (bx, by): TILE_INTERIOR when the tile is full, its
+// halo neither wraps nor meets a wall, and its halo's tile edges sit where
+// they sit between full tiles: every neighbour is full, except that the
+// last (ragged) tile of a row or column may be the right or top neighbour
+// when it is at least 4 nodes wide (its far edge then lies beyond the
+// 2-node halo, and the halo's staged rows and columns stay inside the
+// arrays); TILE_SEAM when the same holds except that the halo wraps around
+// a periodic edge allowed by `seams` (seam_bits); TILE_GENERAL otherwise.
 enum { TILE_GENERAL = 0, TILE_SEAM = 1, TILE_INTERIOR = 2 };
 __host__ __device__ inline int tile_kind(const Lattice &L, int tx, int ty, int bx, int by,
                                          int seams)
 {
     const int nfx = L.nx / tx, nfy = L.nyf / ty;
-    const bool ix = bx >= 1 && bx <= nfx - 2, iy = by >= 1 && by <= nfy - 2;
+    const int xhi = L.nx - nfx * tx >= 4 ? nfx - 1 : nfx - 2;
+    const int yhi = L.nyf - nfy * ty >= 4 ? nfy - 1 : nfy - 2;
+    const bool ix = bx >= 1 && bx <= xhi, iy = by >= 1 && by <= yhi;
     if (ix && iy) return TILE_INTERIOR;
     const bool sx = ix || ((seams & 1) && bx < nfx);
     const bool sy = iy || ((seams & 2) && by < nfy);

@@ -597,11 +597,14 @@ __device__ __forceinline__ void stage_ring(const Lattice &L, int cur, int X0, in
     cp_async_commit();
 }
 
-// Tile b + d of a row or column of n tiles; across a periodic edge on seam
-// tiles.
-__device__ __forceinline__ int neighbour_tile(int b, int d, int n, bool seam)
+// Tile of the neighbour d (-1, 0, 1) of the tile starting at coordinate c0
+// (size T) along a lattice direction of n nodes: the tile of node c0 - 1,
+// c0 or c0 + T, wrapped around the periodic edge on seam tiles.  Taken from
+// the node, so a ragged last tile counts as the tile it is.
+__device__ __forceinline__ int neighbour_tile(int c0, int d, int T, int n, bool seam)
 {
-    return seam ? wrapi(b + d, n) : b + d;
+    const int c = d < 0 ? c0 - 1 : (d > 0 ? c0 + T : c0);
+    return (seam ? wrapi(c, n) : c) / T;
 }
 
 // Seam tiles (tile_kind): the halo wraps around a periodic edge, so the
@@ -616,26 +619,25 @@ __device__ __forceinline__ void stage_ring_wrapped(const Lattice &L, int cur, in
 {
     using RS = RingStage<rt, TX, TY>;
     rt *const *ring = (rt *const *)L.ring[cur];
-    const int bx = X0 / TX, by = Y0 / TY, ntx = L.nx / TX, nty = L.nyf / TY;
     for (int p = threadIdx.x; p < RS::N; p += NT) {
         long long idx;
         int c;
         if (p < RS::NCOL) {
             const int ci = p / RS::CL, j = p - ci * RS::CL;
             c = col_is_left(ci) ? R_L : R_R;
-            idx = ring_index(L, c, wrapi(bx + edge_tile(ci), ntx), 0,
+            idx = ring_index(L, c, neighbour_tile(X0, edge_tile(ci), TX, L.nx, true), 0,
                              wrapi(Y0 - 4 + j, L.nyf), 0);
         } else if (p < RS::NCOL + RS::NROW) {
             const int q = p - RS::NCOL, ri = q / RS::RL, j = q - ri * RS::RL;
             c = row_is_below(ri) ? R_B : R_T;
-            idx = ring_index(L, c, 0, wrapi(by + edge_tile(ri), nty), 0,
+            idx = ring_index(L, c, 0, neighbour_tile(Y0, edge_tile(ri), TY, L.nyf, true), 0,
                              wrapi(X0 - 4 + j, L.nx));
         } else {
             const int q = p - RS::NCOL - RS::NROW, ci = q / 4, ri = q % 4;
             c = row_is_below(ri) ? (col_is_left(ci) ? R_BL : R_BR)
                                  : (col_is_left(ci) ? R_TL : R_TR);
-            idx = ring_index(L, c, wrapi(bx + edge_tile(ci), ntx),
-                             wrapi(by + edge_tile(ri), nty), 0, 0);
+            idx = ring_index(L, c, neighbour_tile(X0, edge_tile(ci), TX, L.nx, true),
+                             neighbour_tile(Y0, edge_tile(ri), TY, L.nyf, true), 0, 0);
         }
         cp_async<sizeof(rt)>(s_ring + p, ring[c] + idx);
     }
@@ -975,7 +977,7 @@ __device__ __forceinline__ bool step_tile_tma(const Lattice &L, int cur, int X0,
     // this tile, and the tile of the ring column a lane feeds (classes L and
     // R share one index layout)
     const int bx = X0 / TX, by = Y0 / TY;
-    const int bxc = neighbour_tile(bx, lane == 0 ? -1 : 1, L.nx / TX, seam);
+    const int bxc = neighbour_tile(X0, lane == 0 ? -1 : 1, TX, L.nx, seam);
     const bool col_lane = lane == 0 || lane == 31;
     pop_t *Arow = A + (long long)(Y0 + ly0) * L.pitch + X0 + lx;
 #pragma unroll
@@ -1075,16 +1077,16 @@ __device__ __forceinline__ bool step_tile_tma(const Lattice &L, int cur, int X0,
         if (col_lane) ring[cls_c][ring_index(L, R_L, bxc, by, Y0 + ly0, xc)] = (rho_t)first_c;
     }
     // ring rows below and above the tile, with their corners
-    const int bxl = neighbour_tile(bx, -1, L.nx / TX, seam);
-    const int bxr = neighbour_tile(bx, 1, L.nx / TX, seam);
+    const int bxl = neighbour_tile(X0, -1, TX, L.nx, seam);
+    const int bxr = neighbour_tile(X0, 1, TX, L.nx, seam);
     if (warp == 0) {
-        const int byb = neighbour_tile(by, -1, L.nyf / TY, seam);
+        const int byb = neighbour_tile(Y0, -1, TY, L.nyf, seam);
         ring[R_T][ring_index(L, R_T, bx, byb, Y0 - 1, X0 + lx)] = (rho_t)s_down[lane];
         if (lane == 0) ring[R_TR][ring_index(L, R_TR, bxl, byb, Y0 - 1, X0 - 1)] = (rho_t)s_down[TX];
         if (lane == 31) ring[R_TL][ring_index(L, R_TL, bxr, byb, Y0 - 1, X0 + TX)] = (rho_t)s_down[TX + 1];
     }
     if (warp == NW - 1) {
-        const int byt = neighbour_tile(by, 1, L.nyf / TY, seam);
+        const int byt = neighbour_tile(Y0, 1, TY, L.nyf, seam);
         ring[R_B][ring_index(L, R_B, bx, byt, Y0 + TY, X0 + lx)] = (rho_t)up_prev;
         if (lane == 0) ring[R_BR][ring_index(L, R_BR, bxl, byt, Y0 + TY, X0 - 1)] = (rho_t)up_prev_c;
         if (lane == 31) ring[R_BL][ring_index(L, R_BL, bxr, byt, Y0 + TY, X0 + TX)] = (rho_t)up_prev_c;
@@ -1402,9 +1404,9 @@ __device__ __forceinline__ bool step_tile_tma_pair(const Lattice &L, int cur, in
     const int cls_c = lane == 0 ? R_R : R_L;
     // this tile, and the tile of the ring column a lane feeds (classes L and
     // R share one index layout)
-    const int bx = X0 / TX, by = Y0 / TY, ntx = L.nx / TX, nty = L.nyf / TY;
-    const int bxl = seam ? wrapi(bx - 1, ntx) : bx - 1, bxr = seam ? wrapi(bx + 1, ntx) : bx + 1;
-    const int byb = seam ? wrapi(by - 1, nty) : by - 1, byt = seam ? wrapi(by + 1, nty) : by + 1;
+    const int bx = X0 / TX, by = Y0 / TY;
+    const int bxl = neighbour_tile(X0, -1, TX, L.nx, seam), bxr = neighbour_tile(X0, 1, TX, L.nx, seam);
+    const int byb = neighbour_tile(Y0, -1, TY, L.nyf, seam), byt = neighbour_tile(Y0, 1, TY, L.nyf, seam);
     const int bxc = lane == 0 ? bxl : bxr;
     const bool col_lane = lane == 0 || lane == 31;
     pop_t *Arow = A + (long long)(Y0 + ly0) * L.pitch + X0 + x0;

@@ -184,14 +184,44 @@ def test_seam_tiles_fp64(tile, walls, size, oracle_threads):
         _compare(sim, ref, 1e-11)
 
 
+# A full tile whose right or top neighbour is the ragged last tile of its
+# row or column takes the interior paths when that tile is at least 4 nodes
+# wide (remainder 4 here; remainder 3 keeps the general path).
+RAGGED_NEIGHBOUR_CASES = [
+    ((32, 32), False, (100, 100)),   # remainders 4 and 4
+    ((32, 16), True, (99, 54)),      # x remainder 3, 52 fluid rows: remainder 4
+    ((32, 24), True, (134, 77)),     # remainders 6 and 3
+]
+
+
+@pytest.mark.parametrize("tile,walls,size", RAGGED_NEIGHBOUR_CASES)
+def test_ragged_neighbour_tiles_fp64(tile, walls, size, oracle_threads):
+    nx, ny = size
+    sim, ref, rho = _setup("cs", nx, ny, walls)
+    with sim:
+        sim.set_tile(*tile)
+        sim.init(rho)
+        ref.init_equilibrium(rho)
+        for _ in range(2):      # both parities; tolerance as test_seam_tiles_fp64
+            sim.step(1)
+            ref.step(1)
+            _compare(sim, ref, 1e-12)
+        sim.step(198)
+        ref.step(198)
+        _compare(sim, ref, 1e-11)
+
+
 @pytest.mark.parametrize("tile,walls,size", SEAM_CASES[:2] + SEAM_CASES[3:4] + [
     ((64, 16), False, (192, 48)),   # two nodes per lane: 3 x 3 tiles
     ((64, 32), True, (192, 98)),
+    ((64, 16), False, (196, 52)),   # ragged right and top neighbours (remainders 4)
+    ((32, 32), True, (100, 102)),
 ])
 @pytest.mark.parametrize("precision", ["f32", "f32_offset"])
 def test_seam_tiles_fp32(tile, walls, size, precision, monkeypatch):
-    # against the oracle (tolerance as test_every_tile_shape) and against the
-    # same lattice with every tile on the general path
+    # seam and ragged-neighbour tiles, against the oracle (tolerance as
+    # test_every_tile_shape) and against the same lattice with every tile on
+    # the general path
     nx, ny = size
     ref_rho = 0.5 * sum(_coexistence("cs")) if precision == "f32_offset" else 0.0
     runs = []
