@@ -146,14 +146,16 @@ cudaError_t launch_step_pt(const Lattice &L, int parity, int cur, cudaStream_t s
 void pt_shape(int prec, int *tx, int *ty);
 
 // Periodic edges whose tiles the TMA tile path may take (bit 0: left and
-// right, bit 1: bottom and top): the tiles along the edge are full and at
-// least three span the lattice, so the halo that wraps around the edge has
-// the layout of an interior halo.
+// right, bit 1: bottom and top): at least three full tiles span the
+// lattice, and the last tile across the edge is full or at least 4 nodes
+// wide, so the halo that wraps around the edge has the layout of an
+// interior halo (the ragged tile itself stays on the general path).
 __host__ __device__ inline int seam_bits(const Lattice &L, int tx, int ty)
 {
     int s = 0;
-    if (L.nx % tx == 0 && L.nx / tx >= 3) s |= 1;
-    if (!L.walls && L.nyf % ty == 0 && L.nyf / ty >= 3) s |= 2;
+    const int rx = L.nx % tx, ry = L.nyf % ty;
+    if (L.nx / tx >= 3 && (rx == 0 || rx >= 4)) s |= 1;
+    if (!L.walls && L.nyf / ty >= 3 && (ry == 0 || ry >= 4)) s |= 2;
     return s;
 }
 

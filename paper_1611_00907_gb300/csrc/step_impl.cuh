@@ -1653,11 +1653,12 @@ static cudaError_t launch_shape(const Lattice &L, int parity, int cur,
     const int ntx = (L.nx + TX - 1) / TX, nty = (L.nyf + TY - 1) / TY;
     const int seams = HasTma<S, TX, TY, NT>::value || HasTmaPair<S, TX, TY, NT>::value
                           ? seam_bits(L, TX, TY) : 0;
-    // When both periodic directions are seams and the maps are valid, every
-    // tile is interior or seam and takes the TMA path (step_kernel has no
-    // general fallback on it), so the launch needs only that path's shared
-    // memory, and more CTAs fit.
-    const size_t smem = (seams == 3 && m.valid && smem_tma > 0) ? smem_tma : smem_max;
+    // When both periodic directions are seams over full tiles only and the
+    // maps are valid, every tile is interior or seam and takes the TMA path
+    // (step_kernel has no general fallback on it), so the launch needs only
+    // that path's shared memory, and more CTAs fit.
+    const bool all_tma = seams == 3 && L.nx % TX == 0 && L.nyf % TY == 0 && m.valid;
+    const size_t smem = (all_tma && smem_tma > 0) ? smem_tma : smem_max;
     dim3 grid(ntx, nty);
     if (parity == 0)
         k0<<<grid, NT, smem, s>>>(L, cur, seams, m);
