@@ -7,8 +7,9 @@ liquid and vapour densities, interface width and contact angle.  It is
 trained on converged runs of the method itself (batched lattices), and a
 new case then starts from a circular-cap drop with the predicted angle,
 densities and width instead of the plain half-disc at the Maxwell
-densities.  The plain cold start stays the fallback and the judge: both
-are run to convergence and their observables compared.
+densities.  The plain cold start stays the fallback and the measure of
+the warm start's error: both are run to convergence and their
+observables compared.
 """
 import math
 

@@ -2,7 +2,7 @@
 converged batched runs of the method, predicts held-out cases' contact
 angle; runs started from its prediction converge in fewer steps than the
 plain half-disc start and reach the same observables (the cold start is
-the judge)."""
+the reference for the error)."""
 import numpy as np
 import pytest
 
