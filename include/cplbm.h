@@ -305,6 +305,20 @@ lbm_status lbm_eos_pressure(int eos, double a, double b, double R,
                             double T_over_Tc, double omega, const double *rho,
                             double *p, size_t n);
 
+/* Path class of every tile of the fused step for an nx x ny lattice (ny
+ * counts the two solid rows when walls != 0) at tile shape tx x ty, one of
+ * the compiled shapes: kinds[by * ntx + bx] = 2 for an interior tile (the
+ * TMA or cp.async interior path), 1 for a seam tile (its halo wraps around
+ * a periodic edge; the TMA paths only), 0 for a general tile, with ntx =
+ * ceil(nx / tx), nty = ceil(fluid rows / ty) and max >= ntx * nty entries
+ * in kinds (a host array).  seams != 0 gives the classes of a single
+ * lattice whose shape has a TMA path; seams == 0 those of a batch, or of a
+ * shape without one (seam tiles general).  Host-only, no device work; for
+ * choosing lattice sizes and for tests.  LBM_ERR_ARG on a bad size, shape
+ * or a short array. */
+lbm_status lbm_tile_kinds(int nx, int ny, int walls, int tx, int ty, int seams,
+                          int *kinds, size_t max);
+
 /* Release the context and its device memory.  NULL is ignored. */
 void lbm_destroy(lbm_ctx *ctx);
 

@@ -13,7 +13,7 @@ from . import _lib
 from ._lib import EOS, PRECISION, LbmError, check
 
 __all__ = ["Simulation", "Batch", "LbmError", "eos_critical",
-           "eos_coexistence", "eos_pressure", "EOS", "PRECISION"]
+           "eos_coexistence", "eos_pressure", "tile_kinds", "EOS", "PRECISION"]
 
 
 def eos_critical(eos, a, b, R=1.0):
@@ -48,6 +48,20 @@ def eos_pressure(eos, a, b, R=1.0, Tr=0.85, omega=0.344, rho=None):
                                float(omega), r.ctypes.data, p.ctypes.data,
                                r.size))
     return p
+
+
+def tile_kinds(nx, ny, walls=False, tile=(32, 32), seams=True):
+    """Path class of every tile of the fused step, [nty][ntx]: 2 interior,
+    1 seam (halo wraps a periodic edge; TMA paths), 0 general.  seams=False
+    gives a batch's classes.  From the library; no device work."""
+    lib = _lib.load()
+    tx, ty = tile
+    nyf = ny - 2 if walls else ny
+    ntx, nty = -(-nx // tx), -(-nyf // ty)
+    out = np.zeros((max(nty, 1), max(ntx, 1)), dtype=np.int32)
+    check(lib.lbm_tile_kinds(int(nx), int(ny), int(bool(walls)), int(tx), int(ty),
+                             int(bool(seams)), out.ctypes.data, out.size))
+    return out
 
 
 def _default_device(device):

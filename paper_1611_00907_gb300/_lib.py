@@ -67,6 +67,8 @@ SIGNATURES = {
                              C.c_double, C.c_double, _dp, _dp, _dp], C.c_int),
     "lbm_eos_pressure": ([C.c_int, C.c_double, C.c_double, C.c_double,
                           C.c_double, C.c_double, _vp, _vp, C.c_size_t], C.c_int),
+    "lbm_tile_kinds": ([C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int,
+                        _vp, C.c_size_t], C.c_int),
     "lbm_step_noalloc": ([C.POINTER(LbmConfig), C.c_int, C.c_double,
                           C.c_double, C.c_double, C.c_double, C.c_double,
                           C.c_double, C.c_int, C.c_double, _vp, C.c_int],

@@ -424,6 +424,33 @@ lbm_status lbm_eos_pressure(int eos, double a, double b, double R,
     return LBM_OK;
 }
 
+lbm_status lbm_tile_kinds(int nx, int ny, int walls, int tx, int ty, int seams,
+                          int *kinds, size_t max)
+{
+    if (!kinds) return fail(nullptr, LBM_ERR_ARG, "null array");
+    if (nx < 5 || ny < (walls ? 7 : 5))
+        return fail(nullptr, LBM_ERR_ARG, "lattice %d x %d too small", nx, ny);
+    int sx[16], sy[16];
+    const int ns = step_shapes(sx, sy, 16);
+    bool known = false;
+    for (int k = 0; k < ns && k < 16; ++k) known = known || (sx[k] == tx && sy[k] == ty);
+    if (!known) return fail(nullptr, LBM_ERR_ARG, "no step kernel for tile %d x %d", tx, ty);
+    Lattice L{};
+    L.nx = nx;
+    L.ny = ny;
+    L.walls = walls ? 1 : 0;
+    L.nyf = walls ? ny - 2 : ny;
+    const int ntx = (nx + tx - 1) / tx, nty = (L.nyf + ty - 1) / ty;
+    if ((size_t)ntx * nty > max)
+        return fail(nullptr, LBM_ERR_ARG, "kinds holds %zu entries, %d x %d needed", max, ntx,
+                    nty);
+    const int sb = seams ? seam_bits(L, tx, ty) : 0;
+    for (int by = 0; by < nty; ++by)
+        for (int bx = 0; bx < ntx; ++bx)
+            kinds[(size_t)by * ntx + bx] = tile_kind(L, tx, ty, bx, by, sb);
+    return LBM_OK;
+}
+
 lbm_status lbm_set_eos(lbm_ctx *c, int eos, double a, double b, double R,
                        double T_over_Tc, double omega)
 {
