@@ -69,11 +69,20 @@ def hbm_peak():
     return FALLBACK_HBM_GBS, "fallback"
 
 
+def kernel_code(text):
+    """Source text without comments and with whitespace collapsed: what the
+    compiler sees of the kernel, so that editing a comment does not void
+    counters measured on the code."""
+    text = re.sub(r"/\*.*?\*/", " ", text, flags=re.S)
+    text = re.sub(r"//[^\n]*", " ", text)
+    return " ".join(text.split())
+
+
 def kernel_hash():
     h = hashlib.sha256()
     for rel in KERNEL_SOURCES:
-        with open(os.path.join(ROOT, rel), "rb") as fh:
-            h.update(fh.read())
+        with open(os.path.join(ROOT, rel)) as fh:
+            h.update(kernel_code(fh.read()).encode())
     return h.hexdigest()[:16]
 
 

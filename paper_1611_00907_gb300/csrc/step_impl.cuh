@@ -28,11 +28,14 @@
 // The chemical potential is computed while the populations are in flight.
 //
 // Two code paths share this structure.  Tiles whose halo and ring touch no
-// domain edge and whose neighbours are full tiles (nearly all of a large
-// lattice) take the interior path: constant address offsets, no periodic
-// wrap, no wall tests, asynchronous density loads.  All other tiles take
-// the general path.  Both add the same terms in the same order, so a node's
-// values do not depend on which path a tile took.
+// domain edge and whose neighbours' edges sit where full tiles' would
+// (tile_kind; nearly all of a large lattice) take the interior path:
+// constant address offsets, no periodic wrap, no wall tests, asynchronous
+// density loads.  All other tiles take the general path.  Both add the same
+// terms in the same order, so a node's values do not depend on which path
+// a tile took.  The TMA paths further below take the interior tiles and,
+// in a variant, the tiles whose halo wraps around a periodic edge; they
+// sum the density hand-over in registers, in another order.
 #pragma once
 #include "device_common.cuh"
 
