@@ -92,6 +92,19 @@ lbm_status rebuild(lbm_batch *b)
             for (int bx = 0; bx < ntx; ++bx)
                 items.push_back({(int)i, bx, by, tile_kind(L, b->tx, b->ty, bx, by, 0)});
     }
+    // General tiles cost a few interior tiles each.  CTAs take items in list
+    // order, backwards on odd steps, so the general tiles go in the middle,
+    // between two halves of the others: in either direction a step ends on
+    // short items and the CTAs finish close together.
+    {
+        std::vector<WorkItem> gen, rest;
+        for (const WorkItem &it : items) (it.kind == TILE_GENERAL ? gen : rest).push_back(it);
+        const size_t h = rest.size() / 2;
+        items.clear();
+        items.insert(items.end(), rest.begin(), rest.begin() + h);
+        items.insert(items.end(), gen.begin(), gen.end());
+        items.insert(items.end(), rest.begin() + h, rest.end());
+    }
     cudaFree(b->d_lats);
     cudaFree(b->d_items);
     cudaFree(b->d_maps);
