@@ -614,8 +614,10 @@ __device__ __forceinline__ int neighbour_tile(int c0, int d, int T, int n, bool 
 // partial sums are staged element by element with wrapped coordinates, in
 // the layout of stage_ring (column entry j <-> row Y0 - 4 + j, row entry j
 // <-> column X0 - 4 + j), by cp.async in one group.  At least three full
-// tiles span each wrapped direction, so the neighbour tiles are full and
-// distinct and one wrap step brings every coordinate into the lattice.
+// tiles span each wrapped direction and its last tile is full or at least
+// 4 nodes wide (seam_bits), so the neighbour tiles are distinct, their near
+// edges sit where a full tile's would, and one wrap step brings every
+// coordinate into the lattice.
 template <class rt, int TX, int TY, int NT>
 __device__ __forceinline__ void stage_ring_wrapped(const Lattice &L, int cur, int X0,
                                                    int Y0, rt *s_ring)
