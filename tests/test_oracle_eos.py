@@ -9,7 +9,8 @@ facts that do not come from the oracle's own formulas:
   Z_c = 3/8; Redlich-Kwong family Z_c = 1/3 and b rho_c = 2^(1/3) - 1;
   Peng-Robinson textbook constants Omega_a = 0.45724, Omega_b = 0.07780,
   Z_c = 0.3074; Carnahan-Starling-van der Waals Z_c = 0.3590;
-* alpha(T_c) = 1 for PR and RKS.
+* alpha(T_c) = 1 for PR and RKS, and alpha(T) reproduces the definition of
+  the acentric factor omega (vapour pressure at T_r = 0.7).
 """
 import math
 
@@ -124,10 +125,34 @@ def test_alpha_is_one_at_critical_and_decreases_with_temperature():
             assert thermo.alpha_of(kind, 0.8, omega) > 1.0
             assert thermo.alpha_of(kind, 1.2, omega) < 1.0
     assert thermo.alpha_of("vdw", 0.7, 0.3) == 1.0
-    # PR, omega = 0.344: m = 0.37464 + 1.54226 w - 0.26992 w^2 (Eq. 22 text)
-    m = 0.37464 + 1.54226 * 0.344 - 0.26992 * 0.344 ** 2
-    assert thermo.alpha_of("pr", 0.81, 0.344) == pytest.approx(
-        (1 + m * 0.1) ** 2, rel=1e-15)
+
+
+# Largest |omega recovered - omega| allowed: the Soave correlation was built to
+# reproduce the acentric-factor definition at T_r = 0.7 (a few 1e-4 here); the
+# Peng-Robinson one was fitted to whole vapour-pressure curves and misses it by
+# up to ~4e-3 over 0 <= omega <= 0.5.  A dropped or sign-flipped omega^2 term,
+# the other EOS's coefficients, (1 - T_r) for (1 - sqrt(T_r)) or a missing
+# square each miss by 0.03 or more.
+_OMEGA_TOL = {"rks": 1e-3, "pr": 6e-3}
+
+
+@pytest.mark.parametrize("kind", ["pr", "rks"])
+@pytest.mark.parametrize("omega", [0.0, 0.011, 0.2, 0.344, 0.5])
+def test_alpha_reproduces_the_acentric_factor(kind, omega):
+    """alpha(T) of RKS (text under Eq. 19) and PR (text under Eq. 22) against
+    the definition of the acentric factor (Pitzer, 1955), which neither
+    correlation contains: omega = -1 - log10(p_sat / p_c) at T_r = 0.7.
+    Soave (1972) and Peng and Robinson (1976) chose m(omega) so that their
+    EOS reproduce measured vapour pressures, and with them this definition.
+    p_sat is the Maxwell pressure at 0.7 T_c and p_c the printed p0 at the
+    critical point, both from the oracle's pinned solvers; alpha is the only
+    omega-dependent input."""
+    a, b = 2 / 49, 2 / 21
+    Tc, rc = thermo.critical_point(kind, a, b)
+    p_c = float(oracle.Eos(kind, a, b, 1.0, Tc, 1.0).p0(rc))
+    _, _, _, p_sat = thermo.maxwell(_eos(kind, a, b, Tr=0.7, omega=omega))
+    recovered = -1.0 - math.log10(p_sat / p_c)
+    assert abs(recovered - omega) < _OMEGA_TOL[kind], (recovered, omega)
 
 
 def test_critical_point_scales_with_parameters():

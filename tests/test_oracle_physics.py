@@ -11,6 +11,9 @@ theory fix about converged states.
 * Fig. 2: the paper's printed (CP, theta) pairs for RKS (tests/golden).
 * Galilean invariance (Sec. II): a slab given a uniform velocity keeps its
   profile and is carried by that velocity.
+* Reported velocity v = u + F/(2 rho) (Sec. II, the forcing of ref. [36]):
+  a converged flat interface carries no mass flux, so v vanishes to the
+  discretisation error while u = sum f e / rho does not.
 """
 import math
 import os
@@ -167,3 +170,37 @@ def test_fig2_contact_angles_rks_remaining(row, oracle_threads):
     L.step(6000)
     got = ob.contact_angle(L.moments()["rho"], rl, rv)[0]
     assert got == pytest.approx(theta, abs=6.0 if theta < 150 else 21.0)
+
+
+@pytest.mark.parametrize("walls", [False, True])
+def test_reported_velocity_vanishes_at_a_flat_interface(walls, oracle_threads):
+    """The velocity the oracle reports is v = u + F/(2 rho) (Sec. II, after
+    Eq. 14), with u = sum_i f_i e_i / rho the bare first moment.  In a
+    converged one-dimensional state the mass flux between rows vanishes;
+    that flux is the mean of the moments before (rho u) and after (rho u + F)
+    the collision, i.e. rho v, so v is zero to the discretisation error while
+    u = -F/(2 rho) is of the size of the force.  Here |u| reaches 0.07 and
+    |v| stays below 5e-6 (periodic slab) or 2.1e-4 (a film on a wall, where
+    bounce-back adds its own error).  A half force with the wrong sign gives
+    |v| = 2|u|, a whole force |v| = |u|, no force |v| = |u|."""
+    e = thermo.make_eos("cs", 1.0, 4.0, 1.0, 0.85)
+    rv, rl, mc, _ = thermo.maxwell(e)
+    nx, ny = 4, 64
+    if walls:
+        y = np.arange(ny)[:, None] + np.zeros((1, nx))
+        rho = (rl + rv) / 2 + (rl - rv) / 2 * np.tanh(2 * (20 - y) / 4)
+    else:
+        rho = inputs.slab(nx, ny, rl, rv, 4.0)
+    L = oracle.Lattice(nx, ny, e, 1.0, 0.5, walls=walls, mu_bottom=mc + 0.01)
+    L.init_equilibrium(rho).step(10000)
+    m = L.moments()
+    fl = L.fluid_rows()
+    f = L.f[:, fl]
+    ux = (f * oracle.EX[:, None, None]).sum(0) / m["rho"][fl]
+    uy = (f * oracle.EY[:, None, None]).sum(0) / m["rho"][fl]
+    u_max = max(np.abs(ux).max(), np.abs(uy).max())
+    v_max = max(np.abs(m["vx"][fl]).max(), np.abs(m["vy"][fl]).max())
+    assert u_max > 0.05
+    assert v_max < (1e-2 if walls else 1e-3) * u_max, (v_max, u_max)
+    if walls:   # solid rows report no velocity
+        assert not m["vx"][0].any() and not m["vy"][-1].any()
