@@ -360,7 +360,8 @@ LAPLACE_T = ((0.7, 1.5), (0.8, 1.0), (0.9, 1.0))
 def measure_laplace(steps):
     """Static CS drops (a 1, b 4, kappa 0.5) of radii 16 .. 80 in 256^2
     periodic boxes at three temperatures, one batch per storage (FP32 offset,
-    FP64): Laplace pressure jump against 1 / R per temperature."""
+    FP64): Laplace pressure jump against 1 / R per temperature, its slope
+    against the flat-interface tension sigma of Eq. 1."""
     from paper_1611_00907_gb300 import eos_coexistence, eos_pressure, inputs
     from paper_1611_00907_gb300 import observables as obs
     radii = inputs.ring_radii(16, 80, 8)
@@ -393,8 +394,14 @@ def measure_laplace(steps):
                     rhos[k], lambda v: eos_pressure("cs", 1.0, 4.0, 1.0, Tr, 0.344, v))
                 pts.append((1.0 / R, dp))
             fit = obs.line_fit(*zip(*pts)) if len(pts) >= 3 else (None,) * 3
+            # the 2-D Laplace law: slope = sigma of square-gradient theory
+            sigma = obs.surface_tension(
+                lambda v: eos_pressure("cs", 1.0, 4.0, 1.0, Tr, 0.344, v), rv, rl, 0.5)
             res["T%.1f" % Tr] = {"slope": fit[0], "intercept": fit[1],
-                                 "r2": fit[2], "inv_R_dp": pts,
+                                 "r2": fit[2], "sigma": sigma,
+                                 "slope_over_sigma": (fit[0] / sigma
+                                                      if fit[0] is not None else None),
+                                 "inv_R_dp": pts,
                                  "evaporated_initial_radii": gone}
         out[prec] = res
     out["slope_rel_diff_f32_offset_vs_f64"] = {

@@ -91,12 +91,18 @@ def measure(rho):
 
 
 def periodic_drop_bulk(rho):
-    """(rho_in, rho_out) of a drop centred in a periodic box: mean of the
-    interior plateau (within 2 % of the density range of the maximum) and
-    median of the box's edge rows and columns, the points farthest from the
-    drop."""
-    lo, hi = float(rho.min()), float(rho.max())
-    rho_in = float(rho[rho >= hi - 0.02 * (hi - lo)].mean())
+    """(rho_in, rho_out) of a static drop in a periodic box: the density at
+    the drop's centre - the mean of the 3 x 3 nodes around the density
+    maximum, where the bulk pressure of a static drop peaks and its profile
+    is flat - and the median of the box's edge rows and columns, the points
+    farthest from a centred drop.  (A mean over a band of the largest
+    densities takes in the top of the interface profile and biases rho_in
+    low; the pressure jump of a large drop is too small to afford that.)"""
+    ny, nx = rho.shape
+    jy, jx = np.unravel_index(int(np.argmax(rho)), rho.shape)
+    rows = (np.arange(-1, 2) + jy) % ny
+    cols = (np.arange(-1, 2) + jx) % nx
+    rho_in = float(rho[np.ix_(rows, cols)].mean())
     edge = np.concatenate([rho[0], rho[-1], rho[:, 0], rho[:, -1]])
     return rho_in, float(np.median(edge))
 
@@ -115,6 +121,29 @@ def laplace_jump(rho, pressure):
     rho_in, rho_out = periodic_drop_bulk(rho)
     p_in, p_out = pressure(np.array([rho_in, rho_out]))
     return float(p_in - p_out), equimolar_radius(rho, rho_in, rho_out)
+
+
+def surface_tension(pressure, rho_v, rho_l, kappa, nodes=64):
+    """Tension of a flat interface in the square-gradient theory of Eq. 1:
+    sigma = integral over [rho_v, rho_l] of sqrt(2 kappa w(rho)), w the
+    excess grand-potential density.  With psi from the bulk pressure (Eq. 15)
+    and Eq. 3, d(w / rho) / drho = (p0(rho) - p_c) / rho^2 and w(rho_v) = 0,
+    so w(rho) = rho * integral from rho_v to rho of (p0(s) - p_c) / s^2 ds,
+    p_c = p0(rho_v): only the bulk pressure is needed.  pressure maps an
+    array of densities to p0 (the library's EOS); rho_v, rho_l are the
+    coexisting densities.  Gauss-Legendre quadrature of `nodes` points,
+    inner and outer."""
+    x, wq = np.polynomial.legendre.leggauss(nodes)
+    p_c = float(np.asarray(pressure(np.array([rho_v])))[0])
+
+    def w_of(r):
+        s = rho_v + (r - rho_v) * 0.5 * (x + 1.0)
+        g = (np.asarray(pressure(s)) - p_c) / (s * s)
+        return r * 0.5 * (r - rho_v) * float((wq * g).sum())
+
+    r_out = rho_v + (rho_l - rho_v) * 0.5 * (x + 1.0)
+    vals = np.array([math.sqrt(2.0 * kappa * max(w_of(r), 0.0)) for r in r_out])
+    return 0.5 * (rho_l - rho_v) * float((wq * vals).sum())
 
 
 def line_fit(x, y):

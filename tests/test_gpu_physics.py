@@ -166,3 +166,30 @@ def test_fig2_at_the_papers_size():
             assert theta == 180.0
         else:
             assert abs(theta - printed) < 4.0, (cp, theta, printed)
+
+
+def test_laplace_slope_matches_sigma_with_the_library_measurement():
+    """The 2-D Laplace law Delta p = sigma / R (Sec. III) on the GPU: three
+    static CS drops (T/T_c 0.85, kappa 0.5, 128^2, FP64), measured with the
+    library-side observables the benchmark uses (pressure jump from the
+    density at the drop's centre and far away, equimolar radius), against
+    the square-gradient tension of Eq. 1.  On the oracle the same case gives
+    slope / sigma = 0.996."""
+    from paper_1611_00907_gb300 import eos_coexistence, eos_pressure
+    from paper_1611_00907_gb300 import observables as pob
+    Tr = 0.85
+    rv, rl, _ = eos_coexistence("cs", 1.0, 4.0, 1.0, Tr)
+
+    def p0(v):
+        return eos_pressure("cs", 1.0, 4.0, 1.0, Tr, 0.344, v)
+
+    sigma = pob.surface_tension(p0, rv, rl, 0.5)
+    pts = []
+    for r in (16, 24, 32):
+        with Simulation(128, 128, **CS, precision="f64") as sim:
+            sim.init(inputs.drop(128, 128, r, rl, rv, 4.0)).step(6000)
+            dp, R = pob.laplace_jump(sim.moments(fields=("rho",))["rho"], p0)
+        assert abs(dp * R / sigma - 1) < 0.08, (r, dp * R / sigma)
+        pts.append((1.0 / R, dp))
+    slope, _, r2 = pob.line_fit(*zip(*pts))
+    assert abs(slope / sigma - 1) < 0.03 and r2 > 0.99, (slope / sigma, r2)

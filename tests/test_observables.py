@@ -65,8 +65,8 @@ def test_equimolar_radius_and_jump_of_a_disc():
         d = R - np.hypot(xx - n / 2 + 0.5, yy - n / 2 + 0.5)
         rho = inputs.tanh_profile(d, 0.3, 0.02, 4.0)
         rin, rout = obs.periodic_drop_bulk(rho)
-        # the plateau band (2 % of the range) takes in the profile's tail
-        assert abs(rin - 0.3) < 1e-3 and abs(rout - 0.02) < 1e-9
+        # the centre of a disc of radius >= 20 is bulk to tanh(10) = 1 - 4e-9
+        assert abs(rin - 0.3) < 1e-8 and abs(rout - 0.02) < 1e-9
         # a symmetric tanh profile puts the excess mass's edge at d = 0 up
         # to a curvature correction of order W^2 / R
         assert abs(obs.equimolar_radius(rho, rin, rout) - R) < 3.0 / R
@@ -91,3 +91,26 @@ def test_film_over_the_wall_is_complete_wetting():
     yy = np.mgrid[0:ny, 0:nx][0]
     rho = np.where(yy < 10, 2.0, 0.05)
     assert obs.contact_angle(rho) == 0.0
+
+
+def test_centre_density_follows_a_drifted_drop():
+    n = 128
+    yy, xx = np.mgrid[0:n, 0:n]
+    # a drop whose centre sits across the periodic corner
+    d = 20.0 - np.hypot((xx + 10) % n - 10.3, (yy + 10) % n - 7.6)
+    rho = inputs.tanh_profile(d, 0.3, 0.02, 4.0)
+    rin, rout = obs.periodic_drop_bulk(rho)
+    assert abs(rin - 0.3) < 1e-8 and abs(rout - 0.02) < 1e-9
+
+
+@pytest.mark.parametrize("Tr", [0.7, 0.85, 0.9])
+def test_surface_tension_from_the_bulk_pressure_matches_the_oracle(Tr):
+    """The product's sigma (bulk pressure only, through the library's EOS)
+    against the oracle's (the printed psi, Eq. 1)."""
+    from oracle import thermo
+    from paper_1611_00907_gb300 import eos_coexistence, eos_pressure
+    rv, rl, _ = eos_coexistence("cs", 1.0, 4.0, 1.0, Tr)
+    got = obs.surface_tension(
+        lambda v: eos_pressure("cs", 1.0, 4.0, 1.0, Tr, 0.344, v), rv, rl, 0.5)
+    want = thermo.surface_tension(thermo.make_eos("cs", 1.0, 4.0, 1.0, Tr), 0.5)
+    assert got == pytest.approx(want, rel=1e-7)
