@@ -275,13 +275,18 @@ const char *lbm_mlp_last_error(const lbm_mlp *m);
  * The call allocates nothing: the density buffers a context would own live
  * in one fixed device array of LBM_NOALLOC_SCRATCH_BYTES, which every GPU
  * that loads the library holds until the process exits.  A lattice needs
- * 8 * (2 nx nyf + 16 nx ceil32(nyf)) bytes of it, nyf = ny - 2 with walls,
- * else ny (256 x 256 periodic fits exactly); larger lattices are rejected
- * with LBM_ERR_ARG.  The first call on a device looks up the array's device
- * address (cudaGetSymbolAddress); make that first call before any stream
- * capture.  All calls share the array and each clears what must start at
- * zero: calls that overlap on the GPU race on it and must be serialised by
- * the caller.  Errors are reported through lbm_last_error(NULL). */
+ * two density fields (8 nx nyf bytes each, nyf = ny - 2 with walls, else ny)
+ * and two generations of the partial sums that cross tile edges, about
+ * 1.2 nx nyf bytes each (the sizes a context allocates), each part rounded
+ * up to 256 bytes: about 19.2 bytes a node, so 702 x 702 periodic is the
+ * largest square that fits; larger lattices are rejected with LBM_ERR_ARG
+ * and a message naming the bytes needed.  The first call on a device (and
+ * the first after a device reset, which makes a new context) looks up the
+ * array's device address (cudaGetSymbolAddress) and caches it with the
+ * context's ID; make that first call before any stream capture.  All calls
+ * share the array and each clears what must start at zero: calls that
+ * overlap on the GPU race on it and must be serialised by the caller.
+ * Errors are reported through lbm_last_error(NULL) of the calling thread. */
 #define LBM_NOALLOC_SCRATCH_BYTES (18u * 65536u * 8u)
 lbm_status lbm_step_noalloc(const lbm_config *cfg, int eos, double a,
                             double b, double R, double T_over_Tc,
@@ -322,9 +327,37 @@ lbm_status lbm_tile_kinds(int nx, int ny, int walls, int tx, int ty, int seams,
 /* Release the context and its device memory.  NULL is ignored. */
 void lbm_destroy(lbm_ctx *ctx);
 
-/* Message of the last error on ctx (or of the last failed lbm_create or
- * lbm_eos_critical when ctx is NULL).  Never NULL. */
+/* Message of the last error on ctx (or, when ctx is NULL, of the last
+ * failed call without a context made by the calling thread: lbm_create,
+ * the host EOS helpers, lbm_step_noalloc).  Never NULL. */
 const char *lbm_last_error(const lbm_ctx *ctx);
+
+/* ------------------------------------------------------------------------
+ * Test hooks: host-side fault injection.  They make the library's own
+ * failure paths run without any fault on the GPU; they are not needed for
+ * normal use.
+ * ------------------------------------------------------------------------ */
+
+/* Limit, in SM clock cycles, of the step kernels' first wait for a tile's
+ * staged data (the TMA paths).  Default about 2e9 (one second at 2 GHz);
+ * cycles < 0 restores it; 0 gives up at once, without polling.  A
+ * tile whose wait gives up waits (with the default limit) for its copies
+ * still in flight, leaves its nodes untouched and raises a flag that the
+ * next synchronising call on ctx (lbm_moments, lbm_reduce,
+ * lbm_get_populations) reports as LBM_ERR_CUDA with a message naming the
+ * timeout; the flag is then cleared.  The lattice is
+ * then inconsistent: re-initialise it (lbm_init or lbm_set_state). */
+lbm_status lbm_test_set_wait_cycles(lbm_ctx *ctx, long long cycles);
+
+/* Make the device allocation after the next `after` ones (counted over the
+ * whole library and every thread) fail as if the device were out of
+ * memory; after < 0 disarms a pending failure.  The call that meets the
+ * failure returns LBM_ERR_OOM and frees whatever it had allocated. */
+void lbm_test_fail_device_alloc(int after);
+
+/* Device allocations the library currently holds (contexts, batches,
+ * networks and their staging buffers), for leak checks. */
+long long lbm_test_device_allocs(void);
 
 #ifdef __cplusplus
 }

@@ -69,6 +69,9 @@ SIGNATURES = {
                           C.c_double, C.c_double, _vp, _vp, C.c_size_t], C.c_int),
     "lbm_tile_kinds": ([C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int,
                         _vp, C.c_size_t], C.c_int),
+    "lbm_test_set_wait_cycles": ([_ctx, C.c_longlong], C.c_int),
+    "lbm_test_fail_device_alloc": ([C.c_int], None),
+    "lbm_test_device_allocs": ([], C.c_longlong),
     "lbm_step_noalloc": ([C.POINTER(LbmConfig), C.c_int, C.c_double,
                           C.c_double, C.c_double, C.c_double, C.c_double,
                           C.c_double, C.c_int, C.c_double, _vp, C.c_int],

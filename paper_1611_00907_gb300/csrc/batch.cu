@@ -105,21 +105,21 @@ lbm_status rebuild(lbm_batch *b)
         items.insert(items.end(), gen.begin(), gen.end());
         items.insert(items.end(), rest.begin() + h, rest.end());
     }
-    cudaFree(b->d_lats);
-    cudaFree(b->d_items);
-    cudaFree(b->d_maps);
+    dev_free(b->d_lats);
+    dev_free(b->d_items);
+    dev_free(b->d_maps);
     b->d_lats = nullptr;
     b->d_items = nullptr;
     b->d_maps = nullptr;
-    if (!b->d_counter) BCUDA(b, cudaMalloc(&b->d_counter, 2 * sizeof(int)));
+    if (!b->d_counter) BCUDA(b, dev_alloc((void **)&b->d_counter, 2 * sizeof(int)));
     BCUDA(b, cudaMemset(b->d_counter, 0, 2 * sizeof(int)));
     if (any_maps) {
-        BCUDA(b, cudaMalloc(&b->d_maps, maps.size() * sizeof(TmaMaps)));
+        BCUDA(b, dev_alloc((void **)&b->d_maps, maps.size() * sizeof(TmaMaps)));
         BCUDA(b, cudaMemcpy(b->d_maps, maps.data(), maps.size() * sizeof(TmaMaps),
                             cudaMemcpyHostToDevice));
     }
-    BCUDA(b, cudaMalloc(&b->d_lats, lats.size() * sizeof(Lattice)));
-    BCUDA(b, cudaMalloc(&b->d_items, items.size() * sizeof(WorkItem)));
+    BCUDA(b, dev_alloc((void **)&b->d_lats, lats.size() * sizeof(Lattice)));
+    BCUDA(b, dev_alloc((void **)&b->d_items, items.size() * sizeof(WorkItem)));
     BCUDA(b, cudaMemcpy(b->d_lats, lats.data(), lats.size() * sizeof(Lattice),
                         cudaMemcpyHostToDevice));
     BCUDA(b, cudaMemcpy(b->d_items, items.data(), items.size() * sizeof(WorkItem),
@@ -366,7 +366,7 @@ lbm_status lbm_batch_autotune(lbm_batch *b, int nsteps, int *tx, int *ty)
     std::vector<char *> snaps(b->inst.size(), nullptr);
     lbm_status st = LBM_OK;
     for (size_t i = 0; i < b->inst.size() && st == LBM_OK; ++i) {
-        cudaError_t e = cudaMalloc(&snaps[i], ctx_state_bytes(b->inst[i]));
+        cudaError_t e = dev_alloc((void **)&snaps[i], ctx_state_bytes(b->inst[i]));
         if (e != cudaSuccess) st = bfail(b, LBM_ERR_OOM, "autotune snapshot");
         else st = ctx_snapshot(b->inst[i], snaps[i], true);
     }
@@ -418,7 +418,7 @@ lbm_status lbm_batch_autotune(lbm_batch *b, int nsteps, int *tx, int *ty)
     }
     if (e0) cudaEventDestroy(e0);
     if (e1) cudaEventDestroy(e1);
-    for (char *p : snaps) cudaFree(p);
+    for (char *p : snaps) dev_free(p);
     if (st != LBM_OK) return st;
     if (tx) *tx = b->tx;
     if (ty) *ty = b->ty;
@@ -443,10 +443,10 @@ void lbm_batch_destroy(lbm_batch *b)
     cudaSetDevice(b->device);
     drop_graph(b);
     for (lbm_ctx *c : b->inst) lbm_destroy(c);
-    cudaFree(b->d_lats);
-    cudaFree(b->d_items);
-    cudaFree(b->d_maps);
-    cudaFree(b->d_counter);
+    dev_free(b->d_lats);
+    dev_free(b->d_items);
+    dev_free(b->d_maps);
+    dev_free(b->d_counter);
     if (b->own_stream) cudaStreamDestroy(b->stream);
     delete b;
 }

@@ -5,6 +5,7 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <atomic>
 #include <new>
 #include <string>
 
@@ -16,6 +17,34 @@ using namespace cplbm;
 #include "context.h"
 
 static thread_local std::string g_err;
+
+namespace cplbm {
+namespace {
+// Device allocations the library holds, and the countdown of the test hook
+// lbm_test_fail_device_alloc (negative: disarmed).
+std::atomic<long long> g_live_allocs{0};
+std::atomic<int> g_fail_countdown{-1};
+}  // namespace
+
+cudaError_t dev_alloc(void **p, size_t bytes)
+{
+    *p = nullptr;
+    int n = g_fail_countdown.load();
+    while (n >= 0 && !g_fail_countdown.compare_exchange_weak(n, n - 1)) {
+    }
+    if (n == 0) return cudaErrorMemoryAllocation;  // the injected failure
+    cudaError_t e = cudaMalloc(p, bytes);
+    if (e == cudaSuccess) ++g_live_allocs;
+    else *p = nullptr;
+    return e;
+}
+
+void dev_free(void *p)
+{
+    if (!p) return;
+    if (cudaFree(p) == cudaSuccess) --g_live_allocs;
+}
+}  // namespace cplbm
 
 namespace {
 
@@ -196,24 +225,12 @@ bool coexistence(int kind, double a, double b, double R, double Tr,
 lbm_status ensure_tmp(lbm_ctx *c, size_t bytes)
 {
     if (c->tmp_bytes >= bytes) return LBM_OK;
-    if (c->d_tmp) cudaFree(c->d_tmp);
+    dev_free(c->d_tmp);
     c->d_tmp = nullptr;
     c->tmp_bytes = 0;
-    CUDA_TRY(c, cudaMalloc(&c->d_tmp, bytes));
+    CUDA_TRY(c, dev_alloc((void **)&c->d_tmp, bytes));
     c->tmp_bytes = bytes;
     return LBM_OK;
-}
-
-// Elements of the compact partial-sum buffer of class c (ring_index): one
-// column per tile column (L, R), one row per tile row (B, T), one entry per
-// tile (corners), counted for the smallest compiled tile, 32 x 16, so that
-// every tile shape fits.
-size_t ring_elems(const Lattice &L, int c)
-{
-    const size_t ncx = ((size_t)L.nx + 31) / 32, ncy = ((size_t)L.nyf + 15) / 16;
-    if (c == R_L || c == R_R) return ncx * L.nyf_pad;
-    if (c == R_B || c == R_T) return ncy * L.pitch;
-    return ncy * ncx;
 }
 
 // Queue the zeroing of both generations of partial sums.
@@ -231,16 +248,16 @@ cudaError_t clear_rings(const Lattice &L, cudaStream_t s)
 void free_all(lbm_ctx *c)
 {
     Lattice &L = c->L;
-    cudaFree(L.pops);
+    dev_free(L.pops);
     for (int k = 0; k < 2; ++k) {
-        cudaFree(L.rho[k]);
-        for (int r = 0; r < R_COUNT; ++r) cudaFree(L.ring[k][r]);
+        dev_free(L.rho[k]);
+        for (int r = 0; r < R_COUNT; ++r) dev_free(L.ring[k][r]);
     }
-    cudaFree(c->d_red);
-    cudaFree(c->d_bad);
-    cudaFree(c->d_prev);
-    cudaFree(c->d_tmp);
-    cudaFree(c->d_err);
+    dev_free(c->d_red);
+    dev_free(c->d_bad);
+    dev_free(c->d_prev);
+    dev_free(c->d_tmp);
+    dev_free(c->d_err);
 }
 
 // Tensor maps for the current tile shape (the TMA path is skipped when they
@@ -342,10 +359,10 @@ lbm_status lbm_create(const lbm_config *cfg, lbm_ctx **out)
     lbm_status st = LBM_OK;
     auto alloc = [&](void **p, size_t bytes) {
         if (st != LBM_OK) return;
-        cudaError_t ea = cudaMalloc(p, bytes);
+        cudaError_t ea = dev_alloc(p, bytes);
         if (ea != cudaSuccess) {
             *p = nullptr;
-            st = fail(nullptr, LBM_ERR_OOM, "cudaMalloc(%zu): %s", bytes,
+            st = fail(nullptr, LBM_ERR_OOM, "device allocation of %zu bytes: %s", bytes,
                       cudaGetErrorString(ea));
         }
     };
@@ -366,6 +383,7 @@ lbm_status lbm_create(const lbm_config *cfg, lbm_ctx **out)
         return st;
     }
     L.err = c->d_err;
+    L.wait_cycles = WAIT_CYCLES_DEFAULT;
     const char *no_tma = getenv("CPLBM_NO_TMA");
     c->use_tma = !(no_tma && no_tma[0] == '1');
     refresh_maps(c);
@@ -558,7 +576,7 @@ lbm_status lbm_autotune(lbm_ctx *c, int nsteps, int *best_tx, int *best_ty)
     const size_t bytes = 8 * (size_t)L.plane * pop_bytes(L.precision) +
                          (size_t)L.plane * rho_bytes(L.precision);
     char *snap = nullptr;
-    CUDA_TRY(c, cudaMalloc(&snap, bytes));
+    CUDA_TRY(c, dev_alloc((void **)&snap, bytes));
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     int tx[16], ty[16];
     const int n = step_shapes(tx, ty, 16);
@@ -602,7 +620,7 @@ lbm_status lbm_autotune(lbm_ctx *c, int nsteps, int *best_tx, int *best_ty)
     }
     if (e0) cudaEventDestroy(e0);
     if (e1) cudaEventDestroy(e1);
-    cudaFree(snap);
+    dev_free(snap);
     if (st != LBM_OK) return st;
     if (e != cudaSuccess)
         return fail(c, LBM_ERR_CUDA, "autotune: %s", cudaGetErrorString(e));
@@ -886,6 +904,17 @@ void lbm_destroy(lbm_ctx *c)
     free_all(c);
     delete c;
 }
+
+lbm_status lbm_test_set_wait_cycles(lbm_ctx *c, long long cycles)
+{
+    if (!c) return fail(nullptr, LBM_ERR_ARG, "null context");
+    c->L.wait_cycles = cycles < 0 ? WAIT_CYCLES_DEFAULT : cycles;
+    return LBM_OK;
+}
+
+void lbm_test_fail_device_alloc(int after) { g_fail_countdown = after < 0 ? -1 : after; }
+
+long long lbm_test_device_allocs(void) { return g_live_allocs.load(); }
 
 const char *lbm_last_error(const lbm_ctx *c)
 {

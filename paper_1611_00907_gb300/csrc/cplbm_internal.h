@@ -86,6 +86,8 @@ struct Lattice {
     int top_mode;
     int precision;
     int *err;            // device flag: a bounded wait in a kernel gave up
+    long long wait_cycles;  // SM clocks a tile waits for its staged data
+                            // before it gives up (WAIT_CYCLES_DEFAULT)
     Consts<float> cf;    // tau .. mu_top and eos as float (set_consts)
     Consts<double> cd;   // ... and as double
 };
@@ -120,6 +122,29 @@ bool build_tma_maps(const Lattice &L, TmaMaps *m, char *err, size_t errlen);
 
 // Bits of Lattice::err.
 enum { ERR_WAIT_TIMEOUT = 1 };
+// Limit of the step kernels' first wait for a tile's staged data: about a
+// second at the 2 GHz SM clock, far beyond any copy's latency.  A wait
+// that reaches it raises ERR_WAIT_TIMEOUT, drains the tile's copies (with
+// this same long limit, whatever Lattice::wait_cycles says) and leaves the
+// tile untouched.
+constexpr long long WAIT_CYCLES_DEFAULT = 2000000000LL;
+
+// Entries of partial-sum class c (R_L .. R_TR) of one generation: one
+// column per 32-wide tile column (L, R), one row per 16-high tile row
+// (B, T), one entry per such tile (corners); see ring_index.
+inline size_t ring_elems(const Lattice &L, int c)
+{
+    const size_t ncx = ((size_t)L.nx + 31) / 32, ncy = ((size_t)L.nyf + 15) / 16;
+    if (c == R_L || c == R_R) return ncx * L.nyf_pad;
+    if (c == R_B || c == R_T) return ncy * L.pitch;
+    return ncy * ncx;
+}
+
+// Every device allocation of the library goes through these two (capi.cu),
+// which count the live allocations and can be told to fail one on purpose
+// (lbm_test_fail_device_alloc): the host-side fault injection of the tests.
+cudaError_t dev_alloc(void **p, size_t bytes);
+void dev_free(void *p);
 
 // Sizes of the storage types per precision.
 inline size_t pop_bytes(int prec)

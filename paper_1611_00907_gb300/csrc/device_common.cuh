@@ -180,14 +180,15 @@ __device__ __forceinline__ void mbar_expect_tx(unsigned long long *bar, unsigned
                  "r"(bytes)
                  : "memory");
 }
-// Wait for phase `parity` of the barrier for at most max_cycles SM clocks;
-// false when the limit was reached.
+// Wait for phase `parity` of the barrier: poll while fewer than max_cycles
+// SM clocks have passed; false when the limit was reached (max_cycles <= 0:
+// at once, without polling).
 __device__ __forceinline__ bool mbar_wait(unsigned long long *bar, unsigned parity,
                                           long long max_cycles)
 {
     const unsigned a = smem_addr(bar);
     const long long t0 = clock64();
-    while (true) {
+    while (clock64() - t0 < max_cycles) {
         unsigned done;
         asm volatile(
             "{\n .reg .pred p;\n"
@@ -197,8 +198,8 @@ __device__ __forceinline__ bool mbar_wait(unsigned long long *bar, unsigned pari
             : "r"(a), "r"(parity)
             : "memory");
         if (done) return true;
-        if (clock64() - t0 > max_cycles) return false;
     }
+    return false;
 }
 // Order later tensor-map-proxy reads of the 128-byte map at p after
 // generic-proxy writes to it (maps kept in global memory).

@@ -20,6 +20,7 @@
 #include <string>
 
 #include "../../include/cplbm.h"
+#include "cplbm_internal.h"  // dev_alloc / dev_free
 
 namespace cplbm_mlp {
 
@@ -295,6 +296,8 @@ __global__ void mlp_adam_kernel(float *p, float *grad, float *m, float *v,
 }  // namespace cplbm_mlp
 
 using namespace cplbm_mlp;
+using cplbm::dev_alloc;
+using cplbm::dev_free;
 
 struct lbm_mlp {
     float *p = nullptr, *grad = nullptr, *m = nullptr, *v = nullptr;
@@ -357,13 +360,13 @@ lbm_status lbm_mlp_create(int device, const float *init, lbm_mlp **out)
     m->device = device;
     cudaError_t e = cudaSetDevice(device);
     const size_t fb = NPARAM * sizeof(float);
-    if (e == cudaSuccess) e = cudaMalloc(&m->p, fb);
-    if (e == cudaSuccess) e = cudaMalloc(&m->grad, fb);
-    if (e == cudaSuccess) e = cudaMalloc(&m->m, fb);
-    if (e == cudaSuccess) e = cudaMalloc(&m->v, fb);
-    if (e == cudaSuccess) e = cudaMalloc(&m->loss, sizeof(float));
-    if (e == cudaSuccess) e = cudaMalloc(&m->wt, NW * sizeof(__nv_bfloat16));
-    if (e == cudaSuccess) e = cudaMalloc(&m->w, NW * sizeof(__nv_bfloat16));
+    if (e == cudaSuccess) e = dev_alloc((void **)&m->p, fb);
+    if (e == cudaSuccess) e = dev_alloc((void **)&m->grad, fb);
+    if (e == cudaSuccess) e = dev_alloc((void **)&m->m, fb);
+    if (e == cudaSuccess) e = dev_alloc((void **)&m->v, fb);
+    if (e == cudaSuccess) e = dev_alloc((void **)&m->loss, sizeof(float));
+    if (e == cudaSuccess) e = dev_alloc((void **)&m->wt, NW * sizeof(__nv_bfloat16));
+    if (e == cudaSuccess) e = dev_alloc((void **)&m->w, NW * sizeof(__nv_bfloat16));
     if (e == cudaSuccess) e = cudaMemcpy(m->p, init, fb, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemset(m->grad, 0, fb);
     if (e == cudaSuccess) e = cudaMemset(m->m, 0, fb);
@@ -444,13 +447,13 @@ lbm_status lbm_mlp_get_params(lbm_mlp *m, float *out)
 void lbm_mlp_destroy(lbm_mlp *m)
 {
     if (!m) return;
-    cudaFree(m->p);
-    cudaFree(m->grad);
-    cudaFree(m->m);
-    cudaFree(m->v);
-    cudaFree(m->loss);
-    cudaFree(m->wt);
-    cudaFree(m->w);
+    dev_free(m->p);
+    dev_free(m->grad);
+    dev_free(m->m);
+    dev_free(m->v);
+    dev_free(m->loss);
+    dev_free(m->wt);
+    dev_free(m->w);
     delete m;
 }
 

@@ -17,6 +17,8 @@
 #include <cstdio>
 #include <mutex>
 
+#include <cudaTypedefs.h>
+
 #include "../../include/cplbm.h"
 #include "device_common.cuh"
 
@@ -29,23 +31,84 @@ constexpr size_t kScratchDoubles = LBM_NOALLOC_SCRATCH_BYTES / sizeof(double);
 static __device__ __align__(256) double g_noalloc_scratch[kScratchDoubles];
 
 // In host code the name g_noalloc_scratch is only a stand-in for the device
-// array, not its address: the address is looked up once per device, with
-// that device current, and cached here.
+// array, not its address.  The address is looked up with the device current
+// and cached per device together with the unique ID of the CUDA context it
+// belongs to: after a device reset the primary context is a new one, the
+// module is loaded again at a new address, and the next call looks it up
+// again.  Where the driver cannot report a context ID, every call looks the
+// address up.
 constexpr int kMaxDevices = 64;
+struct ScratchAddr {
+    bool valid;
+    unsigned long long ctx_id;
+    double *ptr;
+};
 std::mutex g_setup_mutex;
-double *g_scratch_ptr[kMaxDevices] = {};
+ScratchAddr g_scratch_addr[kMaxDevices] = {};
+
+bool current_context_id(unsigned long long *id)
+{
+    static PFN_cuCtxGetCurrent_v4000 get_current = nullptr;
+    static PFN_cuCtxGetId_v12000 get_id = nullptr;
+    static bool tried = false;
+    if (!tried) {
+        tried = true;
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &p, 4000,
+                                             cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            get_current = reinterpret_cast<PFN_cuCtxGetCurrent_v4000>(p);
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &p, 12000,
+                                             cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            get_id = reinterpret_cast<PFN_cuCtxGetId_v12000>(p);
+    }
+    CUcontext ctx = nullptr;
+    return get_current && get_id && get_current(&ctx) == CUDA_SUCCESS && ctx &&
+           get_id(ctx, id) == CUDA_SUCCESS;
+}
 
 cudaError_t scratch_on_current_device(int device, double **out)
 {
     std::lock_guard<std::mutex> lock(g_setup_mutex);
-    if (!g_scratch_ptr[device]) {
+    unsigned long long id = 0;
+    const bool have_id = current_context_id(&id);
+    ScratchAddr &a = g_scratch_addr[device];
+    if (!(have_id && a.valid && a.ctx_id == id)) {
         void *p = nullptr;
         cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
         if (e != cudaSuccess) return e;
-        g_scratch_ptr[device] = static_cast<double *>(p);
+        a.ptr = static_cast<double *>(p);
+        a.ctx_id = id;
+        a.valid = have_id;
     }
-    *out = g_scratch_ptr[device];
+    *out = a.ptr;
     return cudaSuccess;
+}
+
+// Offsets of the parts carved from the scratch array, in doubles, each part
+// starting on a 256-byte boundary: the two density generations, then both
+// generations of the eight partial-sum classes at the sizes a context would
+// allocate for them (ring_elems).
+constexpr size_t kAlign = 256 / sizeof(double);
+inline size_t round_up(size_t n) { return (n + kAlign - 1) / kAlign * kAlign; }
+size_t scratch_layout(const Lattice &L, size_t *rho_off, size_t ring_off[2][R_COUNT],
+                      size_t *ring_begin)
+{
+    const size_t field = round_up((size_t)L.nyf * L.nx);
+    size_t off = 0;
+    for (int k = 0; k < 2; ++k) {
+        rho_off[k] = off;
+        off += field;
+    }
+    *ring_begin = off;
+    for (int k = 0; k < 2; ++k)
+        for (int c = 0; c < R_COUNT; ++c) {
+            ring_off[k][c] = off;
+            off += round_up(ring_elems(L, c));
+        }
+    return off;
 }
 
 // rho = sum_i f_i at every fluid node, from natural-order populations.
@@ -126,8 +189,8 @@ extern "C" lbm_status lbm_step_noalloc(
     // starting at the first fluid row
     L.plane = (long long)cfg->nx * cfg->ny;
     const size_t field = (size_t)L.nyf * L.nx;
-    const size_t ring = (size_t)L.nx * L.nyf_pad;  // >= field
-    const size_t need = 2 * field + 2 * R_COUNT * ring;
+    size_t rho_off[2], ring_off[2][R_COUNT], ring_begin;
+    const size_t need = scratch_layout(L, rho_off, ring_off, &ring_begin);
     if (need > kScratchDoubles)
         return fail_msg(LBM_ERR_ARG,
                         "lattice %d x %d needs %zu bytes of scratch; the "
@@ -151,6 +214,7 @@ extern "C" lbm_status lbm_step_noalloc(
     L.top_mode = top_mode;
     L.mu_top = mu_top;
     L.precision = P_F64;
+    L.wait_cycles = WAIT_CYCLES_DEFAULT;  // no TMA path here; set for completeness
     set_consts(L);
     step_default_shape(P_F64, &L.tx, &L.ty);
 
@@ -167,16 +231,15 @@ extern "C" lbm_status lbm_step_noalloc(
         return fail_msg(LBM_ERR_CUDA, "cudaGetSymbolAddress: %s",
                         cudaGetErrorString(e));
     L.pops = f + L.plane + (long long)L.walls * L.nx;
-    L.rho[0] = scratch;
-    L.rho[1] = scratch + field;
-    for (int k = 0; k < 2; ++k)
-        for (int c = 0; c < R_COUNT; ++c)
-            L.ring[k][c] = scratch + 2 * field + (size_t)(k * R_COUNT + c) * ring;
+    for (int k = 0; k < 2; ++k) {
+        L.rho[k] = scratch + rho_off[k];
+        for (int c = 0; c < R_COUNT; ++c) L.ring[k][c] = scratch + ring_off[k][c];
+    }
 
     cudaStream_t s = (cudaStream_t)cfg->stream;
     // the partial sums are read for tile-edge nodes from the first step on
     // and must start at zero; the last call left its own values there
-    e = cudaMemsetAsync(L.ring[0][0], 0, 2 * R_COUNT * ring * sizeof(double), s);
+    e = cudaMemsetAsync(scratch + ring_begin, 0, (need - ring_begin) * sizeof(double), s);
     if (e != cudaSuccess)
         return fail_msg(LBM_ERR_CUDA, "cudaMemsetAsync: %s", cudaGetErrorString(e));
     const unsigned blocks = (unsigned)((field + 255) / 256);

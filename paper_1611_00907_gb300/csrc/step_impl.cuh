@@ -524,14 +524,16 @@ __device__ __forceinline__ constexpr int pin_col(int i)
 // block barrier.  false when any thread gave up: the flag is raised, every
 // copy of the tile is given another bounded wait so none is left writing
 // into this block's shared memory, and the caller leaves the tile untouched.
+// `limit` bounds the first wait (Lattice::wait_cycles); the drain waits keep
+// the long default so that no copy lands after the block has moved on.
 __device__ __forceinline__ bool tma_landed(unsigned long long *bar, int k,
-                                           unsigned phase, int *err)
+                                           unsigned phase, int *err, long long limit)
 {
-    const bool ok = mbar_wait(&bar[k], phase, 2000000000LL);  // ~1 s at 2 GHz
+    const bool ok = mbar_wait(&bar[k], phase, limit);
     if (!__syncthreads_or(!ok)) return true;
     if (threadIdx.x == 0 && err) atomicOr(err, ERR_WAIT_TIMEOUT);
-    mbar_wait(&bar[0], phase, 2000000000LL);
-    mbar_wait(&bar[1], phase, 2000000000LL);
+    mbar_wait(&bar[0], phase, WAIT_CYCLES_DEFAULT);
+    mbar_wait(&bar[1], phase, WAIT_CYCLES_DEFAULT);
     __syncthreads();
     return false;
 }
@@ -888,7 +890,7 @@ __device__ __forceinline__ bool step_tile_tma(const Lattice &L, int cur, int X0,
         stage_ring<real, TX, TY>(L, cur, X0, Y0, s_ring, &bar[0]);
     }
     cp_async_wait_all();
-    if (!tma_landed(bar, 0, phase, L.err)) return false;
+    if (!tma_landed(bar, 0, phase, L.err, L.wait_cycles)) return false;
     if (seam) {
         seam_rho_apply<real, TX, TY, NT, RP>(L, X0, Y0, s_mu, s_rho);
         __syncthreads();
@@ -935,7 +937,7 @@ __device__ __forceinline__ bool step_tile_tma(const Lattice &L, int cur, int X0,
     }
     // the populations were in flight during steps 2 and 3; the barrier also
     // publishes s_mu
-    if (!tma_landed(bar, 1, phase, L.err)) return false;
+    if (!tma_landed(bar, 1, phase, L.err, L.wait_cycles)) return false;
     if (PARITY == 1 && seam) {
         seam_pop_apply<pop_t, TX, TY, NT, PLANE, PP, TS::PX>(L, X0, Y0, fix_pop, s_pin);
         __syncthreads();
@@ -1338,7 +1340,7 @@ __device__ __forceinline__ bool step_tile_tma_pair(const Lattice &L, int cur, in
         stage_ring<float, TX, TY>(L, cur, X0, Y0, s_ring, &bar[0]);
     }
     cp_async_wait_all();
-    if (!tma_landed(bar, 0, phase, L.err)) return false;
+    if (!tma_landed(bar, 0, phase, L.err, L.wait_cycles)) return false;
     if (seam) {
         seam_rho_apply<float, TX, TY, NT, RP>(L, X0, Y0, s_mu, s_rho);
         __syncthreads();
@@ -1379,7 +1381,7 @@ __device__ __forceinline__ bool step_tile_tma_pair(const Lattice &L, int cur, in
     }
     // the populations were in flight during steps 2 and 3; the barrier also
     // publishes s_mu
-    if (!tma_landed(bar, 1, phase, L.err)) return false;
+    if (!tma_landed(bar, 1, phase, L.err, L.wait_cycles)) return false;
     if (PARITY == 1 && seam) {
         seam_pop_apply<pop_t, TX, TY, NT, PLANE, PP, TS::PX>(L, X0, Y0, fix_pop, s_pin);
         __syncthreads();

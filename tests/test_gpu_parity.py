@@ -352,6 +352,86 @@ def test_mass_conservation_and_reduce():
         assert d2 == 0.0           # no step since the last call
 
 
+def _oracle_reduction(ref, rho_prev):
+    """(mass, rho v_x, rho v_y, max |rho - rho_prev|) over the fluid nodes of
+    the oracle's state, with v = u + F/(2 rho) as the oracle reports it, and
+    the sums of magnitudes that bound each sum's rounding."""
+    m = ref.moments()
+    fl = ref.fluid_rows()
+    r, px, py = m["rho"][fl], (m["rho"] * m["vx"])[fl], (m["rho"] * m["vy"])[fl]
+    want = (r.sum(), px.sum(), py.sum(), np.abs(r - rho_prev[fl]).max())
+    scale = (np.abs(r).sum(), np.abs(px).sum(), np.abs(py).sum())
+    return want, scale, m["rho"]
+
+
+@pytest.mark.parametrize("walls", [False, True])
+@pytest.mark.parametrize("precision,tol", [("f64", 1e-12), ("f32", 2e-5)])
+def test_reduction_matches_oracle(walls, precision, tol):
+    """The FP64 reductions of lbm_reduce (mass, momentum sum rho v with the
+    reported velocity of Sec. II, and the convergence measure max |rho_t -
+    rho_t'| since the previous call) against the same quantities of the
+    oracle's state, from a moving drop so that momentum is not round-off."""
+    sim, ref, rho = _setup("cs", 131, 37, walls, precision=precision)
+    ny, nx = rho.shape
+    ux, uy = np.full((ny, nx), 0.02), np.full((ny, nx), -0.01)
+    if walls:
+        uy[:] = 0.0
+    with sim:
+        sim.init(rho, ux, uy)
+        ref.init_equilibrium(rho, ux, uy)
+        prev = ref.moments()["rho"]
+        got = sim.reduce()
+        want, scale, _ = _oracle_reduction(ref, prev)
+        t0 = 1e-13 if precision == "f64" else tol   # FP32 stores a rounded state
+        for k in range(3):
+            assert abs(got[k] - want[k]) <= t0 * scale[k], (k, got, want)
+        assert got[3] == 0.0
+        for n in (1, 40, 161):
+            sim.step(n)
+            ref.step(n)
+            got = sim.reduce()
+            want, scale, prev = _oracle_reduction(ref, prev)
+            for k in range(3):
+                assert abs(got[k] - want[k]) <= tol * scale[k], (n, k, got, want)
+            assert want[3] > 1e-6
+            # FP32 densities carry their own storage rounding: absolute bound
+            dtol = 1e-12 * want[3] if precision == "f64" else 3e-5 * rho.max()
+            assert abs(got[3] - want[3]) <= dtol, (n, got[3], want[3])
+
+
+def test_diverging_lattice_reports_numeric_error():
+    """A lattice the scheme cannot hold (van der Waals with kappa = 0.5: its
+    density range makes the square-gradient term linearly unstable; the
+    oracle goes non-finite within three steps) makes lbm_reduce return
+    LBM_ERR_NUMERIC with the count of bad nodes, instead of a value.  The
+    failure is the run's own arithmetic; no index depends on a density, so
+    nothing is read or written out of place."""
+    import ctypes as C
+    from paper_1611_00907_gb300 import _lib
+    kind, a, b, Tr = "vdw", 9 / 49, 2 / 21, 0.85
+    e = thermo.make_eos(kind, a, b, 1.0, Tr)
+    rv, rl, _, _ = thermo.maxwell(e)
+    nx, ny = 70, 21
+    rho = inputs.drop(nx, ny, 6, rl, rv, 2.0)
+    ref = oracle.Lattice(nx, ny, e, 1.0, 0.5).init_equilibrium(rho).step(20)
+    assert not np.isfinite(ref.density()).all()
+    with Simulation(nx, ny, kind, a, b, 1.0, Tr, tau=1.0, kappa=0.5) as sim:
+        sim.init(rho)
+        sim.reduce()                       # finite initial state: OK
+        sim.step(20)
+        out = (C.c_double * 4)()
+        st = sim._lib.lbm_reduce(sim._ctx, out)
+        assert st == _lib.LBM_ERR_NUMERIC
+        assert b"non-finite" in sim._lib.lbm_last_error(sim._ctx)
+        with pytest.raises(LbmError) as ei:
+            sim.reduce()
+        assert ei.value.status == _lib.LBM_ERR_NUMERIC
+        # the context stays usable: a uniform state runs and reduces again
+        flat = np.full((ny, nx), rv)
+        sim.init(flat).step(2)
+        assert sim.reduce()[0] == pytest.approx(flat.sum(), rel=1e-13)
+
+
 def test_checkpoint_resume_is_bitwise():
     sim, _, rho = _setup("cs", 131, 37, True)
     with sim:

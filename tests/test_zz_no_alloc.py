@@ -26,7 +26,8 @@ def _config(nx, ny, walls, stream, tau=1.0, kappa=0.5):
                           C.c_void_p(stream), 0)
 
 
-@pytest.mark.parametrize("walls,size", [(False, (70, 21)), (True, (131, 37))])
+@pytest.mark.parametrize("walls,size", [(False, (70, 21)), (True, (131, 37)),
+                                        (True, (512, 384)), (False, (702, 702))])
 def test_noalloc_matches_context_step_on_two_calls(walls, size):
     torch = pytest.importorskip("torch")
     nx, ny = size
@@ -63,7 +64,8 @@ def test_noalloc_matches_context_step_on_two_calls(walls, size):
 
 def test_noalloc_rejects_oversized_and_odd_requests():
     lib = _lib.load()
-    cfg = _config(512, 512, False, None)
+    # 702 x 702 periodic is the largest square the fixed array holds
+    cfg = _config(703, 703, False, None)
     dummy = C.c_void_p(16)   # never dereferenced: checks come first
     st = lib.lbm_step_noalloc(C.byref(cfg), 1, 1.0, 4.0, 1.0, 0.85, 0.344,
                               0.0, 0, 0.0, dummy, 2)
