@@ -293,13 +293,39 @@ def measure_batch(which, precision, steps, warmup, sequential=True):
             ms = t0.elapsed_time(t1)
             out["value"] = nodes * steps / (ms * 1e-3) / 1e6
             out["ms_per_step"] = ms / steps
-            finite = 0
-            for k in range(len(specs)):
-                try:
-                    finite += math.isfinite(b.reduce(k)[0])
-                except LbmError:   # non-finite values on that lattice
-                    pass
-            out["finite_fraction"] = finite / len(specs)
+            def finite_flags():
+                flags = []
+                for k in range(len(specs)):
+                    try:
+                        flags.append(math.isfinite(b.reduce(k)[0]))
+                    except LbmError:   # non-finite values on that lattice
+                        flags.append(False)
+                return flags
+
+            ok = finite_flags()
+            out["finite_fraction"] = sum(ok) / len(specs)
+            if not all(ok):
+                # A sweep drops the lattices its parameters cannot hold:
+                # take them out of the launch (the batch has run an even
+                # number of steps) and time the ones that stay finite.
+                if (warmup + steps) % 2:
+                    b.step(1)
+                for k, good in enumerate(ok):
+                    if not good:
+                        b.set_active(k, False)
+                live = sum(sp["nx"] * sp["ny"] for sp, good in zip(specs, ok) if good)
+                torch.cuda.synchronize()
+                t0.record(stream)
+                b.step(steps)
+                t1.record(stream)
+                torch.cuda.synchronize()
+                ms2 = t0.elapsed_time(t1)
+                still = finite_flags()
+                out["finite_only"] = {
+                    "value": live * steps / (ms2 * 1e-3) / 1e6,
+                    "instances": sum(ok), "nodes": live,
+                    "ms_per_step": ms2 / steps,
+                    "still_finite": sum(s and g for s, g in zip(still, ok)) / max(1, sum(ok))}
         if sequential:
             sims = []
             for sp, f in zip(specs, fields):

@@ -86,11 +86,12 @@ lbm_status rebuild(lbm_batch *b)
         if (!b->active[i]) continue;
         const Lattice &L = c->L;
         const int ntx = (L.nx + b->tx - 1) / b->tx, nty = (L.nyf + b->ty - 1) / b->ty;
-        // seams = 0: the batched kernel takes seam tiles on the general path
-        // (step_batch_kernel)
+        // edge tiles (periodic seams, wall rows) take the TMA path of the
+        // 32-wide shapes too (step_batch_kernel)
+        const int seams = b->tx == 32 ? seam_bits(L, b->tx, b->ty) : 0;
         for (int by = 0; by < nty; ++by)
             for (int bx = 0; bx < ntx; ++bx)
-                items.push_back({(int)i, bx, by, tile_kind(L, b->tx, b->ty, bx, by, 0)});
+                items.push_back({(int)i, bx, by, tile_kind(L, b->tx, b->ty, bx, by, seams)});
     }
     // General tiles cost a few interior tiles each.  CTAs take items in list
     // order, backwards on odd steps, so the general tiles go in the middle,

@@ -170,17 +170,22 @@ int step_shapes(int *tx, int *ty, int max);
 cudaError_t launch_step_pt(const Lattice &L, int parity, int cur, cudaStream_t s);
 void pt_shape(int prec, int *tx, int *ty);
 
-// Periodic edges whose tiles the TMA tile path may take (bit 0: left and
-// right, bit 1: bottom and top): at least three full tiles span the
-// lattice, and the last tile across the edge is full or at least 4 nodes
-// wide, so the halo that wraps around the edge has the layout of an
-// interior halo (the ragged tile itself stays on the general path).
+// Edge tiles the TMA tile paths may take (bit 0: periodic left and right,
+// bit 1: periodic bottom and top, bit 2: the bottom and top wall rows).
+// Periodic edges: at least three full tiles span the lattice, and the last
+// tile across the edge is full or at least 4 nodes wide, so the halo that
+// wraps around the edge has the layout of an interior halo (the ragged tile
+// itself stays on the general path).  Walls: at least two tile rows, the
+// bottom one full and the one above it full or at least 4 rows high, so the
+// bottom wall tile's halo above sees interior tile edges; the top wall
+// tile may be ragged down to two rows (tile_kind).
 __host__ __device__ inline int seam_bits(const Lattice &L, int tx, int ty)
 {
     int s = 0;
-    const int rx = L.nx % tx, ry = L.nyf % ty;
+    const int rx = L.nx % tx, ry = L.nyf % ty, nfy = L.nyf / ty;
     if (L.nx / tx >= 3 && (rx == 0 || rx >= 4)) s |= 1;
-    if (!L.walls && L.nyf / ty >= 3 && (ry == 0 || ry >= 4)) s |= 2;
+    if (!L.walls && nfy >= 3 && (ry == 0 || ry >= 4)) s |= 2;
+    if (L.walls && (nfy >= 2 || (nfy == 1 && ry >= 4))) s |= 4;
     return s;
 }
 
@@ -190,8 +195,14 @@ __host__ __device__ inline int seam_bits(const Lattice &L, int tx, int ty)
 // last (ragged) tile of a row or column may be the right or top neighbour
 // when it is at least 4 nodes wide (its far edge then lies beyond the
 // 2-node halo, and the halo's staged rows and columns stay inside the
-// arrays); TILE_SEAM when the same holds except that the halo wraps around
-// a periodic edge allowed by `seams` (seam_bits); TILE_GENERAL otherwise.
+// arrays); TILE_SEAM (an edge tile of the TMA paths) when the same holds
+// along each direction except that the halo wraps around a periodic edge
+// allowed by `seams`, or the tile is a bottom or top wall tile allowed by
+// `seams` (seam_bits); TILE_GENERAL otherwise.  A top wall tile of one
+// fluid row stays general: that row is then also the tile's bottom edge,
+// which holds partial sums from the tile below, and the Eq. 28 average of
+// the halo's outermost columns reads it one column beyond the halo, where
+// the TMA paths add no partial sums.
 enum { TILE_GENERAL = 0, TILE_SEAM = 1, TILE_INTERIOR = 2 };
 __host__ __device__ inline int tile_kind(const Lattice &L, int tx, int ty, int bx, int by,
                                          int seams)
@@ -201,8 +212,10 @@ __host__ __device__ inline int tile_kind(const Lattice &L, int tx, int ty, int b
     const int yhi = L.nyf - nfy * ty >= 4 ? nfy - 1 : nfy - 2;
     const bool ix = bx >= 1 && bx <= xhi, iy = by >= 1 && by <= yhi;
     if (ix && iy) return TILE_INTERIOR;
+    const int nty = (L.nyf + ty - 1) / ty;
+    const bool wall = (seams & 4) && (by == 0 || (by == nty - 1 && L.nyf - by * ty >= 2));
     const bool sx = ix || ((seams & 1) && bx < nfx);
-    const bool sy = iy || ((seams & 2) && by < nfy);
+    const bool sy = iy || ((seams & 2) && by < nfy) || wall;
     return sx && sy ? TILE_SEAM : TILE_GENERAL;
 }
 

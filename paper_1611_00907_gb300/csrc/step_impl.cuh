@@ -612,66 +612,92 @@ __device__ __forceinline__ int neighbour_tile(int c0, int d, int T, int n, bool 
     return (seam ? wrapi(c, n) : c) / T;
 }
 
-// Seam tiles (tile_kind): the halo wraps around a periodic edge, so the
-// partial sums are staged element by element with wrapped coordinates, in
+// Edge tiles (tile_kind TILE_SEAM): the halo wraps around a periodic edge
+// or meets a wall, so the partial sums are staged element by element, in
 // the layout of stage_ring (column entry j <-> row Y0 - 4 + j, row entry j
-// <-> column X0 - 4 + j), by cp.async in one group.  At least three full
-// tiles span each wrapped direction and its last tile is full or at least
-// 4 nodes wide (seam_bits), so the neighbour tiles are distinct, their near
-// edges sit where a full tile's would, and one wrap step brings every
-// coordinate into the lattice.
+// <-> column X0 - 4 + j), by cp.async in one group.  Across a periodic edge
+// the coordinates wrap: at least three full tiles span each wrapped
+// direction and its last tile is full or at least 4 nodes wide (seam_bits),
+// so the neighbour tiles are distinct, their near edges sit where a full
+// tile's would, and one wrap step brings every coordinate into the lattice.
+// With walls, entries of rows outside the fluid and of tile rows beyond a
+// wall (below a bottom wall tile: edge rows 0 and 1; above a top wall
+// tile: 2 and 3) have no writer and are staged as zeros.
 template <class rt, int TX, int TY, int NT>
 __device__ __forceinline__ void stage_ring_wrapped(const Lattice &L, int cur, int X0,
                                                    int Y0, rt *s_ring)
 {
     using RS = RingStage<rt, TX, TY>;
     rt *const *ring = (rt *const *)L.ring[cur];
+    const bool walls = L.walls != 0;
+    const bool wb = walls && Y0 == 0, wt = walls && Y0 + TY >= L.nyf;
     for (int p = threadIdx.x; p < RS::N; p += NT) {
-        long long idx;
-        int c;
+        long long idx = 0;
+        int c = 0;
+        bool valid = true;
         if (p < RS::NCOL) {
             const int ci = p / RS::CL, j = p - ci * RS::CL;
+            const int r = Y0 - 4 + j;
             c = col_is_left(ci) ? R_L : R_R;
+            valid = !walls || (r >= 0 && r < L.nyf);
             idx = ring_index(L, c, neighbour_tile(X0, edge_tile(ci), TX, L.nx, true), 0,
-                             wrapi(Y0 - 4 + j, L.nyf), 0);
+                             walls ? r : wrapi(r, L.nyf), 0);
         } else if (p < RS::NCOL + RS::NROW) {
             const int q = p - RS::NCOL, ri = q / RS::RL, j = q - ri * RS::RL;
             c = row_is_below(ri) ? R_B : R_T;
-            idx = ring_index(L, c, 0, neighbour_tile(Y0, edge_tile(ri), TY, L.nyf, true), 0,
+            valid = !(wb && ri <= 1) && !(wt && ri >= 2);
+            idx = ring_index(L, c, 0,
+                             neighbour_tile(Y0, edge_tile(ri), TY, L.nyf, !walls), 0,
                              wrapi(X0 - 4 + j, L.nx));
         } else {
             const int q = p - RS::NCOL - RS::NROW, ci = q / 4, ri = q % 4;
             c = row_is_below(ri) ? (col_is_left(ci) ? R_BL : R_BR)
                                  : (col_is_left(ci) ? R_TL : R_TR);
+            valid = !(wb && ri <= 1) && !(wt && ri >= 2);
             idx = ring_index(L, c, neighbour_tile(X0, edge_tile(ci), TX, L.nx, true),
-                             neighbour_tile(Y0, edge_tile(ri), TY, L.nyf, true), 0, 0);
+                             neighbour_tile(Y0, edge_tile(ri), TY, L.nyf, !walls), 0, 0);
         }
-        cp_async<sizeof(rt)>(s_ring + p, ring[c] + idx);
+        if (valid) cp_async<sizeof(rt)>(s_ring + p, ring[c] + idx);
+        else s_ring[p] = rt(0);
     }
     cp_async_commit();
 }
 
-// Seam tiles: where the TMA boxes leave the lattice they fill zeros.  The
-// entries the step reads there are fetched from the wrapped nodes while the
-// boxes are in flight, into staging slots (seam_fix_load), and copied over
-// the zeros once the boxes have landed (seam_rho_apply, seam_pop_apply).
+// Edge tiles: where the TMA boxes leave the lattice they fill zeros.  The
+// entries the step reads there are fetched from the lattice while the boxes
+// are in flight, into staging slots (seam_fix_load), and copied over the
+// zeros once the boxes have landed (seam_rho_apply, seam_pop_apply).
 //   density halo (rows of pitch RP from x = X0 - 4, y = Y0 - 2): the two
-//   halo columns or rows across the edge, columns X0 - 2 .. X0 + TX + 1;
+//   halo columns or rows across a periodic edge, columns X0 - 2 .. X0 + TX
+//   + 1 (with walls, only rows of the fluid); on a wall tile at a periodic
+//   x edge also the wall-adjacent row's density one column further out,
+//   which the Eq. 28 average of the outermost halo column needs;
 //   populations, odd steps (pin_x0 / pin_col layout): the three directions
-//   whose source x - e_i lies across the edge, at the edge column or row.
+//   whose source x - e_i lies across a periodic edge, at the edge column or
+//   row, and on a wall tile the three directions whose source lies in the
+//   solid row, at the wall-adjacent row (halfway bounce-back: read from the
+//   node's own slot i); all taken with aa_read_index.
 // Slot t of each list is fixed by the enumeration below, so loading and
 // applying agree without storing positions.
 struct SeamEdges {
-    bool xl, xr, yb, yt;  // the tile touches the left / right / bottom / top edge
+    bool xl, xr, yb, yt;  // the tile's halo wraps the left / right / bottom / top edge
+    bool wb, wt;          // the tile meets the bottom / top wall
+    int hy;               // fluid rows of the tile (below TY only on a ragged top wall tile)
+    int vlo, vhi;         // staged density rows holding fluid nodes: [vlo, vhi)
 };
 __device__ __forceinline__ SeamEdges seam_edges(const Lattice &L, int X0, int Y0, int TX,
                                                 int TY)
 {
-    return {X0 == 0, X0 + TX >= L.nx, Y0 == 0, Y0 + TY >= L.nyf};
+    const bool w = L.walls != 0;
+    const bool wb = w && Y0 == 0, wt = w && Y0 + TY >= L.nyf;
+    const int hy = wt ? L.nyf - Y0 : TY;
+    return {X0 == 0, X0 + TX >= L.nx, !w && Y0 == 0, !w && Y0 + TY >= L.nyf,
+            wb,     wt,              hy,  wb ? 2 : 0,  wt ? hy + 2 : TY + 4};
 }
 template <int TX, int TY>
 struct SeamLists {
-    static constexpr int RHO_C = 2 * (TY + 4), RHO = RHO_C + 2 * (TX + 4);
+    static constexpr int RHO_C = 2 * (TY + 4), RHO_R = RHO_C + 2 * (TX + 4);
+    static constexpr int RHO = RHO_R + 4;
     static constexpr int POP_C = 3 * TY, POP = POP_C + 3 * TX;
 };
 // Density slot t: staged (ly, c); false when the slot is not used.
@@ -683,12 +709,20 @@ __device__ __forceinline__ bool seam_rho_slot(const SeamEdges &e, int t, int &ly
         if (!e.xl && !e.xr) return false;
         ly = t >> 1;
         c = (e.xl ? 2 : TX + 4) + (t & 1);
-    } else {
+        return ly >= e.vlo && ly < e.vhi;
+    }
+    if (t < SL::RHO_R) {
         if (!e.yb && !e.yt) return false;
         const int q = t - SL::RHO_C, sel = q / (TX + 4);
         ly = (e.yb ? 0 : TY + 2) + sel;
         c = 2 + q - sel * (TX + 4);
+        return true;
     }
+    // wall rows at a periodic x edge: t = base + 2 * top + right
+    const int k = t - SL::RHO_R, top = k >> 1, right = k & 1;
+    if (!(top ? e.wt : e.wb) || !(right ? e.xr : e.xl)) return false;
+    ly = top ? e.hy + 1 : 2;
+    c = right ? TX + 6 : 1;
     return true;
 }
 // Population slot t: direction i at tile node (lx, ly).
@@ -704,13 +738,14 @@ __device__ __forceinline__ bool seam_pop_slot(const SeamEdges &e, int t, int &i,
         lx = e.xl ? 0 : TX - 1;
         // left edge: e_x = +1 reads x - 1 = -1; right edge: e_x = -1 reads x + 1 = nx
         i = e.xl ? (d == 0 ? 1 : d == 1 ? 5 : 8) : (d == 0 ? 3 : d == 1 ? 6 : 7);
-    } else {
-        if (!e.yb && !e.yt) return false;
-        const int q = t - SL::POP_C, d = q / TX;
-        lx = q - d * TX;
-        ly = e.yb ? 0 : TY - 1;
-        i = e.yb ? (d == 0 ? 2 : d == 1 ? 5 : 6) : (d == 0 ? 4 : d == 1 ? 7 : 8);
+        return ly < e.hy;
     }
+    const bool bottom = e.yb || e.wb;
+    if (!bottom && !e.yt && !e.wt) return false;
+    const int q = t - SL::POP_C, d = q / TX;
+    lx = q - d * TX;
+    ly = bottom ? 0 : e.hy - 1;
+    i = bottom ? (d == 0 ? 2 : d == 1 ? 5 : 6) : (d == 0 ? 4 : d == 1 ? 7 : 8);
     return true;
 }
 template <class S, int TX, int TY, int NT, int PARITY>
@@ -726,6 +761,7 @@ __device__ __forceinline__ void seam_fix_load(const Lattice &L, int cur, int X0,
     for (int t = threadIdx.x; t < SL::RHO; t += NT) {
         int ly, c;
         if (!seam_rho_slot<TX, TY>(e, t, ly, c)) continue;
+        // fluid rows only: with walls the row needs no wrap
         const int x = wrapi(X0 - 4 + c, L.nx), r = wrapi(Y0 - 2 + ly, L.nyf);
         fix_rho[t] = (typename S::real)R[(long long)r * L.pitch + x];
     }
@@ -734,8 +770,7 @@ __device__ __forceinline__ void seam_fix_load(const Lattice &L, int cur, int X0,
         for (int t = threadIdx.x; t < SL::POP; t += NT) {
             int i, lx, ly;
             if (!seam_pop_slot<TX, TY>(e, t, i, lx, ly)) continue;
-            const int xs = wrapi(X0 + lx - ex(i), L.nx), rs = wrapi(Y0 + ly - ey(i), L.nyf);
-            fix_pop[t] = A[pidx(L, opp(i), rs, xs)];
+            fix_pop[t] = A[aa_read_index(L, 1, i, Y0 + ly, X0 + lx)];
         }
     }
 }
@@ -759,6 +794,58 @@ __device__ __forceinline__ void seam_pop_apply(const Lattice &L, int X0, int Y0,
         if (seam_pop_slot<TX, TY>(e, t, i, lx, ly))
             s_pin[(i - 1) * PLANE + ly * PP + lx + pin_col<1, PX>(i)] = fix_pop[t];
     }
+}
+
+// Edge tiles at a wall: the solid row's density by Eq. 28 from the
+// wall-adjacent fluid row (both after the partial sums were added), at
+// staged columns 2 .. TX + 5 (x = X0 - 2 .. X0 + TX + 1), in the order of
+// load_rho_tile; the top solid row mirrors it (staged row hy + 2 from hy +
+// 1).  Ends with a block barrier when the tile meets a wall (CTA-uniform).
+template <class real, int TX, int NT, int RP>
+__device__ __forceinline__ void wall_rho_rows(const SeamEdges &e, real *s_rho)
+{
+    if (!e.wb && !e.wt) return;
+    constexpr int W = TX + 4;
+    for (int t = threadIdx.x; t < 2 * W; t += NT) {
+        const int top = t >= W;
+        if (!(top ? e.wt : e.wb)) continue;
+        const int c = 2 + t - top * W;
+        const real *src = s_rho + (top ? e.hy + 1 : 2) * RP + c;
+        s_rho[(top ? e.hy + 2 : 1) * RP + c] =
+            real(2.0 / 3.0) * src[0] + real(1.0 / 6.0) * src[-1] + real(1.0 / 6.0) * src[1];
+    }
+    __syncthreads();
+}
+
+// mu of halo row b (r = Y0 - 1 + b) of an edge tile when that row is not a
+// fluid row: mu_s on the bottom solid row (Sec. IV); on the top solid row
+// the value of its fluid neighbour below (Sec. V, top_mode 0: computed here
+// from the staged density, as mu_tile does) or mu_top; zero beyond a ragged
+// top wall tile (never read).  false for fluid rows.  c: staged density
+// index of the halo node.
+template <class S, int RP>
+__device__ __forceinline__ bool wall_mu(const Lattice &L, const SeamEdges &e, int b, int c,
+                                        const typename S::real *s_rho, typename S::real &m)
+{
+    using real = typename S::real;
+    const Consts<real> &K = consts<real>(L);
+    if (e.wb && b == 0) {
+        m = K.mu_bottom;
+        return true;
+    }
+    if (e.wt && b >= e.hy + 1) {
+        if (b > e.hy + 1) {
+            m = real(0);
+        } else if (L.top_mode == 0) {
+            const int cb = c - RP;  // fluid neighbour below (row nyf - 1)
+            const real ref = S::offset ? K.rho_ref : real(0);
+            m = mu_bulk(K.eos, s_rho[cb] + ref) - K.kappa * lap9<real, RP>(s_rho, cb);
+        } else {
+            m = K.mu_top;
+        }
+        return true;
+    }
+    return false;
 }
 
 // Add the staged partial sums to the halo's tile-edge nodes of s_rho (rows
@@ -852,7 +939,6 @@ __device__ __forceinline__ bool step_tile_tma(const Lattice &L, int cur, int X0,
     constexpr int NW = NT / 32, PER = TY / NW;
     static_assert(PER * NW == TY && PER >= 2, "warps own whole row blocks");
     constexpr int RP = TS::RP, PP = TS::PP, PLANE = TS::PLANE, MP = TS::MP, MH = TS::MH;
-    constexpr int WR = TX + 4, HR = TY + 4;  // halo geometry of the ring staging
     constexpr int XW = TX + 2;               // exchange slots per warp
     pop_t *s_pin = reinterpret_cast<pop_t *>(smem_raw);            // [8][TY][PP]
     real *s_rho = reinterpret_cast<real *>(smem_raw + TS::PIN_BYTES);  // [TY + 4][RP]
@@ -901,11 +987,15 @@ __device__ __forceinline__ bool step_tile_tma(const Lattice &L, int cur, int X0,
     //    staged row ly, column lx + 2.
     combine_ring<real, TX, TY, NT, RP>(s_rho, s_ring);
     __syncthreads();
+    // edge tiles at a wall: the solid row's density (Eq. 28)
+    const SeamEdges edge = seam_edges(L, X0, Y0, TX, TY);
+    if (seam) wall_rho_rows<real, TX, NT, RP>(edge, s_rho);
 
     // 3. mu at (a, b), a in [0, TX + 2) <-> x = X0 - 1 + a, b in [0, TY + 2)
     //    <-> r = Y0 - 1 + b; its density sits at staged (b + 1, a + 3).
     //    Columns 1..TX: lane a - 1, each warp a run of consecutive rows with
-    //    a rolling 3 x 3 window; columns 0 and TX + 1 separately.
+    //    a rolling 3 x 3 window; columns 0 and TX + 1 separately.  Solid
+    //    rows of wall tiles take the surface values (wall_mu).
     {
         const Consts<real> &K = consts<real>(L);
         const EosT<real> &eos = K.eos;
@@ -921,7 +1011,10 @@ __device__ __forceinline__ bool step_tile_tma(const Lattice &L, int cur, int X0,
         for (int b = b0; b < b1; ++b) {
 #pragma unroll
             for (int d = 0; d < 3; ++d) w[2][d] = s_rho[(b + 2) * RP + a + 2 + d];
-            s_mu[b * MP + a] = mu_bulk(eos, w[1][1] + ref) - kappa * lap_w(w);
+            real m;
+            if (!(seam && wall_mu<S, RP>(L, edge, b, (b + 1) * RP + a + 3, s_rho, m)))
+                m = mu_bulk(eos, w[1][1] + ref) - kappa * lap_w(w);
+            s_mu[b * MP + a] = m;
 #pragma unroll
             for (int d = 0; d < 3; ++d) {
                 w[0][d] = w[1][d];
@@ -931,8 +1024,10 @@ __device__ __forceinline__ bool step_tile_tma(const Lattice &L, int cur, int X0,
         for (int t = threadIdx.x; t < 2 * MH; t += NT) {
             const int ae = (t & 1) ? TX + 1 : 0, b = t >> 1;
             const int c = (b + 1) * RP + ae + 3;
-            s_mu[b * MP + ae] =
-                mu_bulk(eos, s_rho[c] + ref) - kappa * lap9<real, RP>(s_rho, c);
+            real m;
+            if (!(seam && wall_mu<S, RP>(L, edge, b, c, s_rho, m)))
+                m = mu_bulk(eos, s_rho[c] + ref) - kappa * lap9<real, RP>(s_rho, c);
+            s_mu[b * MP + ae] = m;
         }
     }
     // the populations were in flight during steps 2 and 3; the barrier also
@@ -964,6 +1059,9 @@ __device__ __forceinline__ bool step_tile_tma(const Lattice &L, int cur, int X0,
         woff[i] = PARITY == 0 ? (opp(i) - 1) * (int)L.plane
                               : (i - 1) * (int)L.plane + ey(i) * L.pitch + ex(i) +
                                     (ex(i) < 0 ? cxl : ex(i) > 0 ? cxr : 0);
+    // wall tiles: rows 0 .. hy - 1 hold fluid (hy < TY on a ragged top wall
+    // tile; the rows above it are not updated and contribute nothing)
+    const int hy = seam ? edge.hy : TY;
     const bool has_l = lane > 0, has_r = lane < 31;
     real wr[3][3], wm[3][3];
 #pragma unroll
@@ -995,44 +1093,64 @@ __device__ __forceinline__ bool step_tile_tma(const Lattice &L, int cur, int X0,
             wr[2][d] = s_rho[(ly + 3) * RP + lx + 3 + d];
             wm[2][d] = s_mu[(ly + 2) * MP + lx + d];
         }
-        real f[9];
-#pragma unroll
-        for (int i = 1; i < 9; ++i)
-            f[i] = ld_real(s_pin + (i - 1) * PLANE + ly * PP + lx + pin_col<PARITY, TS::PX>(i));
-        const real drho = wr[1][1];
-        const real rho = drho + rho_ref;
-        real gmx, gmy, grx, gry;
-        grad_w(wm, gmx, gmy);
-        grad_w(wr, grx, gry);
-        const real Fx = grx * real(1.0 / 3.0) - rho * gmx;
-        const real Fy = gry * real(1.0 / 3.0) - rho * gmy;
-        real fp[9];
-        collide<real>(f, drho, rho, Fx, Fy, tau, omega, fp);
-        {
-            const int wrap_y = L.nyf * L.pitch;
-            const int cyb = (PARITY == 1 && seam && Y0 == 0 && ly == 0) ? wrap_y : 0;
-            const int cyt = (PARITY == 1 && seam && Y0 + TY >= L.nyf && ly == TY - 1) ? -wrap_y : 0;
+        real same = real(0), up = real(0), down = real(0);
+        real same_c = real(0), up_c = real(0), down_c = real(0);
+        if (!seam || ly < hy) {  // warp-uniform
+            real f[9];
 #pragma unroll
             for (int i = 1; i < 9; ++i)
-                st_real(Arow + woff[i] + (ey(i) < 0 ? cyb : ey(i) > 0 ? cyt : 0), fp[i]);
+                f[i] = ld_real(s_pin + (i - 1) * PLANE + ly * PP + lx + pin_col<PARITY, TS::PX>(i));
+            const real drho = wr[1][1];
+            const real rho = drho + rho_ref;
+            real gmx, gmy, grx, gry;
+            grad_w(wm, gmx, gmy);
+            grad_w(wr, grx, gry);
+            const real Fx = grx * real(1.0 / 3.0) - rho * gmx;
+            const real Fy = gry * real(1.0 / 3.0) - rho * gmy;
+            real fp[9];
+            collide<real>(f, drho, rho, Fx, Fy, tau, omega, fp);
+            // wall rows (halfway bounce-back, Sec. IV): what leaves into the
+            // solid row comes back to the node
+            const bool wall_b = seam && edge.wb && ly == 0;
+            const bool wall_t = seam && edge.wt && ly == hy - 1;
+            {
+                const int wrap_y = L.nyf * L.pitch;
+                const int cyb = (PARITY == 1 && seam && edge.yb && ly == 0) ? wrap_y : 0;
+                const int cyt = (PARITY == 1 && seam && edge.yt && ly == TY - 1) ? -wrap_y : 0;
+#pragma unroll
+                for (int i = 1; i < 9; ++i) {
+                    // odd steps: a population heading into a solid row goes
+                    // to the node's own slot opp(i)
+                    const bool into_wall = PARITY == 1 && ((ey(i) < 0 && wall_b) ||
+                                                           (ey(i) > 0 && wall_t));
+                    const int o = into_wall ? (opp(i) - 1) * (int)L.plane
+                                            : woff[i] + (ey(i) < 0 ? cyb : ey(i) > 0 ? cyt : 0);
+                    st_real(Arow + o, fp[i]);
+                }
+            }
+
+            // lane-neighbour parts of the hand-over
+            const real f1l = __shfl_up_sync(0xffffffffu, fp[1], 1);
+            const real f5l = __shfl_up_sync(0xffffffffu, fp[5], 1);
+            const real f8l = __shfl_up_sync(0xffffffffu, fp[8], 1);
+            const real f3r = __shfl_down_sync(0xffffffffu, fp[3], 1);
+            const real f6r = __shfl_down_sync(0xffffffffu, fp[6], 1);
+            const real f7r = __shfl_down_sync(0xffffffffu, fp[7], 1);
+            same = fp[0] + (has_l ? f1l : real(0)) + (has_r ? f3r : real(0));
+            up = fp[2] + (has_l ? f5l : real(0)) + (has_r ? f6r : real(0));
+            down = fp[4] + (has_l ? f8l : real(0)) + (has_r ? f7r : real(0));
+            if (wall_b) same += (fp[4] + fp[7]) + fp[8];
+            if (wall_t) same += (fp[2] + fp[5]) + fp[6];
+            // ring columns: lane 0 feeds x = X0 - 1 (f*_3; f*_6 up; f*_7
+            // down), lane 31 feeds x = X0 + TX (f*_1; f*_5 up; f*_8 down)
+            same_c = lane == 0 ? fp[3] : fp[1];
+            up_c = lane == 0 ? fp[6] : fp[5];
+            down_c = lane == 0 ? fp[7] : fp[8];
         }
         Arow += L.pitch;
-
-        // lane-neighbour parts of the hand-over
-        const real f1l = __shfl_up_sync(0xffffffffu, fp[1], 1);
-        const real f5l = __shfl_up_sync(0xffffffffu, fp[5], 1);
-        const real f8l = __shfl_up_sync(0xffffffffu, fp[8], 1);
-        const real f3r = __shfl_down_sync(0xffffffffu, fp[3], 1);
-        const real f6r = __shfl_down_sync(0xffffffffu, fp[6], 1);
-        const real f7r = __shfl_down_sync(0xffffffffu, fp[7], 1);
-        const real same = fp[0] + (has_l ? f1l : real(0)) + (has_r ? f3r : real(0));
-        const real up = fp[2] + (has_l ? f5l : real(0)) + (has_r ? f6r : real(0));
-        const real down = fp[4] + (has_l ? f8l : real(0)) + (has_r ? f7r : real(0));
-        // ring columns: lane 0 feeds x = X0 - 1 (f*_3; f*_6 up; f*_7 down),
-        // lane 31 feeds x = X0 + TX (f*_1; f*_5 up; f*_8 down)
-        const real same_c = lane == 0 ? fp[3] : fp[1];
-        const real up_c = lane == 0 ? fp[6] : fp[5];
-        const real down_c = lane == 0 ? fp[7] : fp[8];
+        // rows of the lattice this warp may write (all but those above a
+        // ragged top wall tile's fluid)
+        const bool row_ok = !seam || ly - 1 < hy;
         if (k == 0) {
             // this row's "down" belongs to the warp below (or the ring row
             // under the tile)
@@ -1046,7 +1164,7 @@ __device__ __forceinline__ bool step_tile_tma(const Lattice &L, int cur, int X0,
             if (k == 1) {
                 first = done;
                 first_c = done_c;
-            } else {
+            } else if (row_ok) {
                 Rn[(long long)(Y0 + ly - 1) * L.pitch + X0 + lx] = (rho_t)done;
                 if (col_lane) ring[cls_c][ring_index(L, R_L, bxc, by, Y0 + ly - 1, xc)] = (rho_t)done_c;
             }
@@ -1073,26 +1191,31 @@ __device__ __forceinline__ bool step_tile_tma(const Lattice &L, int cur, int X0,
             top += s_down[(warp + 1) * XW + lane];
             top_c += s_down[(warp + 1) * XW + slot_c];
         }
-        Rn[(long long)(Y0 + ly0 + PER - 1) * L.pitch + X0 + lx] = (rho_t)top;
-        if (col_lane) ring[cls_c][ring_index(L, R_L, bxc, by, Y0 + ly0 + PER - 1, xc)] = (rho_t)top_c;
+        if (!seam || ly0 + PER - 1 < hy) {
+            Rn[(long long)(Y0 + ly0 + PER - 1) * L.pitch + X0 + lx] = (rho_t)top;
+            if (col_lane) ring[cls_c][ring_index(L, R_L, bxc, by, Y0 + ly0 + PER - 1, xc)] = (rho_t)top_c;
+        }
         // first row: add the warp below's last-row "up"
         if (warp > 0) {
             first += s_up[(warp - 1) * XW + lane];
             first_c += s_up[(warp - 1) * XW + slot_c];
         }
-        Rn[(long long)(Y0 + ly0) * L.pitch + X0 + lx] = (rho_t)first;
-        if (col_lane) ring[cls_c][ring_index(L, R_L, bxc, by, Y0 + ly0, xc)] = (rho_t)first_c;
+        if (!seam || ly0 < hy) {
+            Rn[(long long)(Y0 + ly0) * L.pitch + X0 + lx] = (rho_t)first;
+            if (col_lane) ring[cls_c][ring_index(L, R_L, bxc, by, Y0 + ly0, xc)] = (rho_t)first_c;
+        }
     }
-    // ring rows below and above the tile, with their corners
+    // ring rows below and above the tile, with their corners (none across a
+    // wall)
     const int bxl = neighbour_tile(X0, -1, TX, L.nx, seam);
     const int bxr = neighbour_tile(X0, 1, TX, L.nx, seam);
-    if (warp == 0) {
+    if (warp == 0 && !(seam && edge.wb)) {
         const int byb = neighbour_tile(Y0, -1, TY, L.nyf, seam);
         ring[R_T][ring_index(L, R_T, bx, byb, Y0 - 1, X0 + lx)] = (rho_t)s_down[lane];
         if (lane == 0) ring[R_TR][ring_index(L, R_TR, bxl, byb, Y0 - 1, X0 - 1)] = (rho_t)s_down[TX];
         if (lane == 31) ring[R_TL][ring_index(L, R_TL, bxr, byb, Y0 - 1, X0 + TX)] = (rho_t)s_down[TX + 1];
     }
-    if (warp == NW - 1) {
+    if (warp == NW - 1 && !(seam && edge.wt)) {
         const int byt = neighbour_tile(Y0, 1, TY, L.nyf, seam);
         ring[R_B][ring_index(L, R_B, bx, byt, Y0 + TY, X0 + lx)] = (rho_t)up_prev;
         if (lane == 0) ring[R_BR][ring_index(L, R_BR, bxl, byt, Y0 + TY, X0 - 1)] = (rho_t)up_prev_c;
@@ -1306,7 +1429,6 @@ __device__ __forceinline__ bool step_tile_tma_pair(const Lattice &L, int cur, in
     static_assert(PER * NW == TY && PER >= 2, "warps own whole row blocks");
     constexpr int RP = TS::RP, PP = TS::PP, PLANE = TS::PLANE, MP = TS::MP, MH = TS::MH;
     constexpr int XW = TS::XW;
-    constexpr int WR = TX + 4, HR = TY + 4;  // halo geometry of the ring staging
     pop_t *s_pin = reinterpret_cast<pop_t *>(smem_raw);             // [8][TY][PP]
     float *s_rho = reinterpret_cast<float *>(smem_raw + TS::PIN_BYTES);  // [TY + 4][RP]
     float *s_ring = s_rho + TS::NRHO;
@@ -1350,6 +1472,9 @@ __device__ __forceinline__ bool step_tile_tma_pair(const Lattice &L, int cur, in
     //    load_rho_stored); halo (lx, ly) is staged at row ly, column lx + 2.
     combine_ring<float, TX, TY, NT, RP>(s_rho, s_ring);
     __syncthreads();
+    // edge tiles at a wall: the solid row's density (Eq. 28)
+    const SeamEdges edge = seam_edges(L, X0, Y0, TX, TY);
+    if (seam) wall_rho_rows<float, TX, NT, RP>(edge, s_rho);
 
     // 3. mu at halo column a (x = X0 - 1 + a) and row b (r = Y0 - 1 + b),
     //    stored at s_mu[b][a + 1]; its density is staged at (b + 1, a + 3).
@@ -1366,17 +1491,26 @@ __device__ __forceinline__ bool step_tile_tma_pair(const Lattice &L, int cur, in
         Row2 d = row2(s_rho, b0 * RP + c0), m = row2(s_rho, (b0 + 1) * RP + c0);
         for (int b = b0; b < b1; ++b) {
             const Row2 u = row2(s_rho, (b + 2) * RP + c0);
-            const float2 rho = S::offset ? padd(m.c, ref2) : m.c;
-            *reinterpret_cast<float2 *>(s_mu + b * MP + 2 * lane + 2) =
-                pfma(mkappa, lap2(u, m, d), mu_bulk2(eos, rho));
+            float2 mp;
+            if (seam && ((edge.wb && b == 0) || (edge.wt && b >= edge.hy + 1))) {
+                // solid rows of wall tiles: surface values (wall_mu)
+                wall_mu<S, RP>(L, edge, b, (b + 1) * RP + c0, s_rho, mp.x);
+                wall_mu<S, RP>(L, edge, b, (b + 1) * RP + c0 + 1, s_rho, mp.y);
+            } else {
+                const float2 rho = S::offset ? padd(m.c, ref2) : m.c;
+                mp = pfma(mkappa, lap2(u, m, d), mu_bulk2(eos, rho));
+            }
+            *reinterpret_cast<float2 *>(s_mu + b * MP + 2 * lane + 2) = mp;
             d = m;
             m = u;
         }
         for (int t = threadIdx.x; t < 2 * MH; t += NT) {
             const int ae = (t & 1) ? TX + 1 : 0, b = t >> 1;
             const int c = (b + 1) * RP + ae + 3;
-            s_mu[b * MP + ae + 1] =
-                mu_bulk(eos, s_rho[c] + ref) - K.kappa * lap9<float, RP>(s_rho, c);
+            float mv;
+            if (!(seam && wall_mu<S, RP>(L, edge, b, c, s_rho, mv)))
+                mv = mu_bulk(eos, s_rho[c] + ref) - K.kappa * lap9<float, RP>(s_rho, c);
+            s_mu[b * MP + ae + 1] = mv;
         }
     }
     // the populations were in flight during steps 2 and 3; the barrier also
@@ -1399,6 +1533,8 @@ __device__ __forceinline__ bool step_tile_tma_pair(const Lattice &L, int cur, in
     for (int i = 1; i < 9; ++i)
         woff[i] = PARITY == 0 ? (opp(i) - 1) * (int)L.plane
                               : (i - 1) * (int)L.plane + ey(i) * L.pitch + ex(i);
+    // wall tiles: rows 0 .. hy - 1 hold fluid (as step_tile_tma)
+    const int hy = seam ? edge.hy : TY;
     const bool has_l = lane > 0, has_r = lane < 31;
     // windows: density of tile row ly at staged row ly + 2, column x0 + 4;
     // mu of tile row ly at s_mu row ly + 1, column x0 + 2
@@ -1426,63 +1562,78 @@ __device__ __forceinline__ bool step_tile_tma_pair(const Lattice &L, int cur, in
         const int ly = ly0 + k;
         const Row2 ru = row2(s_rho, (ly + 3) * RP + x0 + 4);
         const Row2 mu = row2(s_mu, (ly + 2) * MP + x0 + 2);
-        float2 f[9];
-#pragma unroll
-        for (int i = 1; i < 9; ++i) {
-            const pop_t *src =
-                s_pin + (i - 1) * PLANE + ly * PP + x0 + pin_col<PARITY, TS::PX>(i);
-            if (PARITY == 0 || ex(i) == 0)
-                f[i] = ld_pair(src);
-            else
-                f[i] = make_float2(ld_real(src), ld_real(src + 1));
-        }
-        const float2 drho = rm.c;
-        const float2 rho = S::offset ? padd(drho, ref2) : drho;
-        float2 grx, gry, gmx, gmy;
-        grad2(ru, rm, rd, grx, gry);
-        grad2(mu, mm, md, gmx, gmy);
-        const float2 Fx = psub(pmul(grx, third), pmul(rho, gmx));
-        const float2 Fy = psub(pmul(gry, third), pmul(rho, gmy));
-        float2 fp[9];
-        collide2(f, drho, rho, Fx, Fy, tau, omega, fp);
-        {
-            // odd steps on seam tiles: a target across a periodic edge is
-            // brought back by one lattice length (the x-shifted directions
-            // are stored one node at a time)
-            const int cyb = (PARITY == 1 && seam && Y0 == 0 && ly == 0) ? wrap_y : 0;
-            const int cyt = (PARITY == 1 && seam && Y0 + TY >= L.nyf && ly == TY - 1) ? -wrap_y : 0;
+        float2 same = p2(0.0f), up = p2(0.0f), down = p2(0.0f);
+        float same_c = 0.0f, up_c = 0.0f, down_c = 0.0f;
+        if (!seam || ly < hy) {  // warp-uniform
+            float2 f[9];
 #pragma unroll
             for (int i = 1; i < 9; ++i) {
-                pop_t *dst = Arow + woff[i] + (ey(i) < 0 ? cyb : ey(i) > 0 ? cyt : 0);
-                if (PARITY == 0 || ex(i) == 0) {
-                    st_pair(dst, fp[i]);
-                } else {
-                    st_real(dst + (ex(i) < 0 ? cxl : 0), fp[i].x);
-                    st_real(dst + 1 + (ex(i) > 0 ? cxr : 0), fp[i].y);
+                const pop_t *src =
+                    s_pin + (i - 1) * PLANE + ly * PP + x0 + pin_col<PARITY, TS::PX>(i);
+                if (PARITY == 0 || ex(i) == 0)
+                    f[i] = ld_pair(src);
+                else
+                    f[i] = make_float2(ld_real(src), ld_real(src + 1));
+            }
+            const float2 drho = rm.c;
+            const float2 rho = S::offset ? padd(drho, ref2) : drho;
+            float2 grx, gry, gmx, gmy;
+            grad2(ru, rm, rd, grx, gry);
+            grad2(mu, mm, md, gmx, gmy);
+            const float2 Fx = psub(pmul(grx, third), pmul(rho, gmx));
+            const float2 Fy = psub(pmul(gry, third), pmul(rho, gmy));
+            float2 fp[9];
+            collide2(f, drho, rho, Fx, Fy, tau, omega, fp);
+            // wall rows (halfway bounce-back, Sec. IV)
+            const bool wall_b = seam && edge.wb && ly == 0;
+            const bool wall_t = seam && edge.wt && ly == hy - 1;
+            {
+                // odd steps on seam tiles: a target across a periodic edge is
+                // brought back by one lattice length (the x-shifted directions
+                // are stored one node at a time); a population heading into a
+                // solid row goes to the node's own slot opp(i)
+                const int cyb = (PARITY == 1 && seam && edge.yb && ly == 0) ? wrap_y : 0;
+                const int cyt = (PARITY == 1 && seam && edge.yt && ly == TY - 1) ? -wrap_y : 0;
+#pragma unroll
+                for (int i = 1; i < 9; ++i) {
+                    const bool into_wall = PARITY == 1 && ((ey(i) < 0 && wall_b) ||
+                                                           (ey(i) > 0 && wall_t));
+                    pop_t *dst = into_wall ? Arow + (opp(i) - 1) * (int)L.plane
+                                           : Arow + woff[i] + (ey(i) < 0 ? cyb : ey(i) > 0 ? cyt : 0);
+                    if (PARITY == 0 || ex(i) == 0 || into_wall) {
+                        st_pair(dst, fp[i]);
+                    } else {
+                        st_real(dst + (ex(i) < 0 ? cxl : 0), fp[i].x);
+                        st_real(dst + 1 + (ex(i) > 0 ? cxr : 0), fp[i].y);
+                    }
                 }
             }
+
+            // lane-neighbour parts of the hand-over
+            const float f1l = __shfl_up_sync(0xffffffffu, fp[1].y, 1);
+            const float f5l = __shfl_up_sync(0xffffffffu, fp[5].y, 1);
+            const float f8l = __shfl_up_sync(0xffffffffu, fp[8].y, 1);
+            const float f3r = __shfl_down_sync(0xffffffffu, fp[3].x, 1);
+            const float f6r = __shfl_down_sync(0xffffffffu, fp[6].x, 1);
+            const float f7r = __shfl_down_sync(0xffffffffu, fp[7].x, 1);
+            same = make_float2((fp[0].x + (has_l ? f1l : 0.0f)) + fp[3].y,
+                               (fp[0].y + fp[1].x) + (has_r ? f3r : 0.0f));
+            up = make_float2((fp[2].x + (has_l ? f5l : 0.0f)) + fp[6].y,
+                             (fp[2].y + fp[5].x) + (has_r ? f6r : 0.0f));
+            down = make_float2((fp[4].x + (has_l ? f8l : 0.0f)) + fp[7].y,
+                               (fp[4].y + fp[8].x) + (has_r ? f7r : 0.0f));
+            // what leaves into a solid row comes back to the node
+            if (wall_b) same = padd(same, padd(padd(fp[4], fp[7]), fp[8]));
+            if (wall_t) same = padd(same, padd(padd(fp[2], fp[5]), fp[6]));
+            // ring columns: lane 0 feeds x = X0 - 1 (f*_3; f*_6 up; f*_7 down)
+            // from its first node, lane 31 feeds x = X0 + TX (f*_1; f*_5 up;
+            // f*_8 down) from its second
+            same_c = lane == 0 ? fp[3].x : fp[1].y;
+            up_c = lane == 0 ? fp[6].x : fp[5].y;
+            down_c = lane == 0 ? fp[7].x : fp[8].y;
         }
         Arow += L.pitch;
-
-        // lane-neighbour parts of the hand-over
-        const float f1l = __shfl_up_sync(0xffffffffu, fp[1].y, 1);
-        const float f5l = __shfl_up_sync(0xffffffffu, fp[5].y, 1);
-        const float f8l = __shfl_up_sync(0xffffffffu, fp[8].y, 1);
-        const float f3r = __shfl_down_sync(0xffffffffu, fp[3].x, 1);
-        const float f6r = __shfl_down_sync(0xffffffffu, fp[6].x, 1);
-        const float f7r = __shfl_down_sync(0xffffffffu, fp[7].x, 1);
-        const float2 same = make_float2((fp[0].x + (has_l ? f1l : 0.0f)) + fp[3].y,
-                                        (fp[0].y + fp[1].x) + (has_r ? f3r : 0.0f));
-        const float2 up = make_float2((fp[2].x + (has_l ? f5l : 0.0f)) + fp[6].y,
-                                      (fp[2].y + fp[5].x) + (has_r ? f6r : 0.0f));
-        const float2 down = make_float2((fp[4].x + (has_l ? f8l : 0.0f)) + fp[7].y,
-                                        (fp[4].y + fp[8].x) + (has_r ? f7r : 0.0f));
-        // ring columns: lane 0 feeds x = X0 - 1 (f*_3; f*_6 up; f*_7 down) from
-        // its first node, lane 31 feeds x = X0 + TX (f*_1; f*_5 up; f*_8 down)
-        // from its second
-        const float same_c = lane == 0 ? fp[3].x : fp[1].y;
-        const float up_c = lane == 0 ? fp[6].x : fp[5].y;
-        const float down_c = lane == 0 ? fp[7].x : fp[8].y;
+        const bool row_ok = !seam || ly - 1 < hy;
         if (k == 0) {
             *reinterpret_cast<float2 *>(s_down + warp * XW + x0) = down;
             if (col_lane) s_down[warp * XW + slot_c] = down_c;
@@ -1494,7 +1645,7 @@ __device__ __forceinline__ bool step_tile_tma_pair(const Lattice &L, int cur, in
             if (k == 1) {
                 first = done;
                 first_c = done_c;
-            } else {
+            } else if (row_ok) {
                 *reinterpret_cast<float2 *>(Rn + (long long)(Y0 + ly - 1) * L.pitch +
                                             X0 + x0) = done;
                 if (col_lane) ring[cls_c][ring_index(L, R_L, bxc, by, Y0 + ly - 1, xc)] = done_c;
@@ -1519,24 +1670,29 @@ __device__ __forceinline__ bool step_tile_tma_pair(const Lattice &L, int cur, in
             top = padd(top, *reinterpret_cast<const float2 *>(s_down + (warp + 1) * XW + x0));
             top_c += s_down[(warp + 1) * XW + slot_c];
         }
-        *reinterpret_cast<float2 *>(Rn + (long long)(Y0 + ly0 + PER - 1) * L.pitch + X0 +
-                                    x0) = top;
-        if (col_lane) ring[cls_c][ring_index(L, R_L, bxc, by, Y0 + ly0 + PER - 1, xc)] = top_c;
+        if (!seam || ly0 + PER - 1 < hy) {
+            *reinterpret_cast<float2 *>(Rn + (long long)(Y0 + ly0 + PER - 1) * L.pitch + X0 +
+                                        x0) = top;
+            if (col_lane) ring[cls_c][ring_index(L, R_L, bxc, by, Y0 + ly0 + PER - 1, xc)] = top_c;
+        }
         if (warp > 0) {
             first = padd(first, *reinterpret_cast<const float2 *>(s_up + (warp - 1) * XW + x0));
             first_c += s_up[(warp - 1) * XW + slot_c];
         }
-        *reinterpret_cast<float2 *>(Rn + (long long)(Y0 + ly0) * L.pitch + X0 + x0) = first;
-        if (col_lane) ring[cls_c][ring_index(L, R_L, bxc, by, Y0 + ly0, xc)] = first_c;
+        if (!seam || ly0 < hy) {
+            *reinterpret_cast<float2 *>(Rn + (long long)(Y0 + ly0) * L.pitch + X0 + x0) = first;
+            if (col_lane) ring[cls_c][ring_index(L, R_L, bxc, by, Y0 + ly0, xc)] = first_c;
+        }
     }
-    // ring rows below and above the tile, with their corners
-    if (warp == 0) {
+    // ring rows below and above the tile, with their corners (none across a
+    // wall)
+    if (warp == 0 && !(seam && edge.wb)) {
         *reinterpret_cast<float2 *>(ring[R_T] + ring_index(L, R_T, bx, byb, Y0 - 1, X0 + x0)) =
             *reinterpret_cast<const float2 *>(s_down + x0);
         if (lane == 0) ring[R_TR][ring_index(L, R_TR, bxl, byb, Y0 - 1, X0 - 1)] = s_down[TX];
         if (lane == 31) ring[R_TL][ring_index(L, R_TL, bxr, byb, Y0 - 1, X0 + TX)] = s_down[TX + 1];
     }
-    if (warp == NW - 1) {
+    if (warp == NW - 1 && !(seam && edge.wt)) {
         *reinterpret_cast<float2 *>(ring[R_B] + ring_index(L, R_B, bx, byt, Y0 + TY, X0 + x0)) = up_prev;
         if (lane == 0) ring[R_BR][ring_index(L, R_BR, bxl, byt, Y0 + TY, X0 - 1)] = up_prev_c;
         if (lane == 31) ring[R_BL][ring_index(L, R_BL, bxr, byt, Y0 + TY, X0 + TX)] = up_prev_c;
@@ -1660,11 +1816,16 @@ static cudaError_t launch_shape(const Lattice &L, int parity, int cur,
     const int ntx = (L.nx + TX - 1) / TX, nty = (L.nyf + TY - 1) / TY;
     const int seams = HasTma<S, TX, TY, NT>::value || HasTmaPair<S, TX, TY, NT>::value
                           ? seam_bits(L, TX, TY) : 0;
-    // When both periodic directions are seams over full tiles only and the
-    // maps are valid, every tile is interior or seam and takes the TMA path
-    // (step_kernel has no general fallback on it), so the launch needs only
-    // that path's shared memory, and more CTAs fit.
-    const bool all_tma = seams == 3 && L.nx % TX == 0 && L.nyf % TY == 0 && m.valid;
+    // When every tile is interior or an edge tile and the maps are valid,
+    // every tile takes the TMA path (step_kernel has no general fallback on
+    // it), so the launch needs only that path's shared memory, and more CTAs
+    // fit: x periodic seams over full tiles, and in y either periodic seams
+    // over full tiles or walls whose top tile is full or at least 4 rows
+    // high (otherwise the tile below it is general).
+    const int ry = L.nyf % TY;
+    const bool all_tma = m.valid && (seams & 1) && L.nx % TX == 0 &&
+                         (L.walls ? ((seams & 4) && (ry == 0 || ry >= 4))
+                                  : ((seams & 2) && ry == 0));
     const size_t smem = (all_tma && smem_tma > 0) ? smem_tma : smem_max;
     dim3 grid(ntx, nty);
     if (parity == 0)
@@ -1742,12 +1903,14 @@ __global__ void __launch_bounds__(NT, sizeof(typename S::real) == 8 ? 2 : 4)
                 fenced = it.inst;
                 // a wait that gave up leaves the barriers in doubt: the rest
                 // of this CTA's items take the general path
-                // interior tiles only: the seam variant would take the kernel
-                // past the 64 registers of four resident CTAs, and the spills
-                // cost the batch more than its seam tiles gain
-                tma = step_tile_tma<S, TX, TY, NT, PARITY, false>(sL, cur, it.bx * TX,
-                                                                  it.by * TY, smem_raw, m,
-                                                                  bar, phase);
+                if (it.kind == TILE_INTERIOR)
+                    tma = step_tile_tma<S, TX, TY, NT, PARITY, false>(sL, cur, it.bx * TX,
+                                                                      it.by * TY, smem_raw, m,
+                                                                      bar, phase);
+                else
+                    tma = step_tile_tma<S, TX, TY, NT, PARITY, true>(sL, cur, it.bx * TX,
+                                                                     it.by * TY, smem_raw, m,
+                                                                     bar, phase);
                 phase ^= 1u;
                 done = true;
             }

@@ -13,7 +13,7 @@ import pytest
 
 import oracle
 from oracle import thermo
-from paper_1611_00907_gb300 import LbmError, Simulation, inputs
+from paper_1611_00907_gb300 import LbmError, Simulation, inputs, tile_kinds
 
 pytestmark = pytest.mark.gpu
 
@@ -239,6 +239,74 @@ def test_seam_tiles_fp32(tile, walls, size, precision, monkeypatch):
     for k in ("rho", "mu", "vx", "vy"):
         assert _rel(runs[0][k], want[k]) < 1e-4, (k, _rel(runs[0][k], want[k]))
         assert _rel(runs[0][k], runs[1][k]) < 1e-4, (k, _rel(runs[0][k], runs[1][k]))
+
+
+# Wall tiles: with walls the bottom and top tile rows take the TMA paths as
+# edge tiles (the top one may be ragged, down to one fluid row): the Eq. 28
+# density row after the partial sums, the surface chemical potential rows,
+# odd-step reads and writes through the node's own slots at the wall, the
+# bounce-back in the register hand-over, and no partial sums across a wall.
+WALL_CASES = [
+    ((32, 32), (128, 66)),    # 64 fluid rows: full top tile
+    ((32, 16), (128, 51)),    # one-row top wall tile: general path beside TMA tiles
+    ((32, 16), (128, 52)),    # two rows
+    ((32, 24), (96, 53)),     # three rows (the tile below it general)
+    ((32, 32), (160, 38)),    # two tile rows, top 4 rows high
+    ((32, 16), (100, 60)),    # ragged last column (general) beside wall tiles
+]
+
+
+@pytest.mark.parametrize("tile,size", WALL_CASES)
+@pytest.mark.parametrize("case,top_mode", [("cs", 0), ("cs", 1), ("rks", 0)])
+def test_wall_tiles_fp64(tile, size, case, top_mode, oracle_threads):
+    nx, ny = size
+    kinds = np.asarray(tile_kinds(nx, ny, True, tile))
+    assert (kinds[[0, -1]] > 0).sum() >= 4     # wall rows on the TMA paths
+    sim, ref, rho = _setup(case, nx, ny, True, top_mode=top_mode,
+                           mu_top=0.004 if case == "cs" else -0.05)
+    with sim:
+        sim.set_tile(*tile)
+        sim.init(rho)
+        ref.init_equilibrium(rho)
+        for _ in range(2):      # both parities; tolerance as test_seam_tiles_fp64
+            sim.step(1)
+            ref.step(1)
+            _compare(sim, ref, 1e-12)
+        sim.step(198)
+        ref.step(198)
+        _compare(sim, ref, 1e-11)
+
+
+@pytest.mark.parametrize("tile,size", WALL_CASES[:3] + [
+    ((64, 16), (192, 66)),    # two nodes per lane: full top tile
+    ((64, 16), (192, 53)),    # three-row top tile
+    ((64, 32), (192, 100)),   # two-row top tile
+    ((64, 16), (256, 39)),    # two tile rows, every tile on the TMA path
+])
+@pytest.mark.parametrize("precision", ["f32", "f32_offset", "f16_offset"])
+def test_wall_tiles_reduced_precision(tile, size, precision, monkeypatch):
+    # against the oracle and against the same lattice with every tile on the
+    # general path (FP16 storage: its rounding of ~5e-4 per population
+    # shows in the density at ~1e-3 after 60 steps; rho only)
+    nx, ny = size
+    ref_rho = 0.5 * sum(_coexistence("cs")) if precision != "f32" else 0.0
+    runs = []
+    for no_tma in (False, True):
+        if no_tma:
+            monkeypatch.setenv("CPLBM_NO_TMA", "1")
+        sim, ref, rho = _setup("cs", nx, ny, True, precision=precision,
+                               rho_ref=ref_rho)
+        with sim:
+            sim.set_tile(*tile)
+            sim.init(rho).step(60)
+            runs.append(sim.moments())
+    ref.init_equilibrium(rho).step(60)
+    want = ref.moments()
+    keys, tol = (("rho",), 2e-3) if precision == "f16_offset" else (
+        ("rho", "mu", "vx", "vy"), 1e-4)
+    for k in keys:
+        assert _rel(runs[0][k], want[k]) < tol, (k, _rel(runs[0][k], want[k]))
+        assert _rel(runs[0][k], runs[1][k]) < tol, (k, _rel(runs[0][k], runs[1][k]))
 
 
 @pytest.mark.parametrize("case", list(EOS_CASES))

@@ -73,14 +73,21 @@ def rule_kind(g, tx, ty, bx, by, seams):
     """The classification as cplbm.h and cplbm_internal.h state it."""
     nfx, nfy = g.nx // tx, g.nyf // ty
     rx, ry = g.nx - nfx * tx, g.nyf - nfy * ty
+    nty = -(-g.nyf // ty)
     sx = seams and nfx >= 3 and (rx == 0 or rx >= 4)
     sy = seams and not g.walls and nfy >= 3 and (ry == 0 or ry >= 4)
+    # wall tiles: two tile rows at least, the one above the bottom tile
+    # full or at least 4 rows high
+    sw = seams and g.walls and (nfy >= 2 or (nfy == 1 and ry >= 4))
     xhi = nfx - 1 if rx >= 4 else nfx - 2
     yhi = nfy - 1 if ry >= 4 else nfy - 2
     ix, iy = 1 <= bx <= xhi, 1 <= by <= yhi
     if ix and iy:
         return 2
-    if (ix or (sx and bx < nfx)) and (iy or (sy and by < nfy)):
+    # a one-row top wall tile stays general (its only row is also a tile
+    # bottom edge, read by the Eq. 28 average beyond the combined halo)
+    wall = sw and (by == 0 or (by == nty - 1 and g.nyf - by * ty >= 2))
+    if (ix or (sx and bx < nfx)) and (iy or (sy and by < nfy) or wall):
         return 1
     return 0
 
@@ -98,17 +105,33 @@ def pin_col(px, i):   # odd steps
     return px - 1 if EX[i] == 1 else (1 if EX[i] == -1 else 0)
 
 
+def aa_read_source(g, i, r, x):
+    """(plane, row, column) an odd step reads f_i of fluid node (x, r) from
+    (aa_read_index): slot opp(i) of x - e_i, or with a solid source row the
+    node's own slot i (halfway bounce-back); x and, without walls, y wrap."""
+    rs = r - EY[i]
+    if g.walls and not 0 <= rs < g.nyf:
+        return i, r, x
+    return OPP[i], wrap(rs, g.nyf), wrap(x - EX[i], g.nx)
+
+
 def check_tile(g, tx, ty, bx, by, seam):
     x0, y0 = bx * tx, by * ty
     nx, nyf = g.nx, g.nyf
-    assert x0 + tx <= nx and y0 + ty <= nyf, "TMA tiles are full"
-    # the four (or, wrapped, more distant) neighbour tiles across the halo
-    # are full or at least 4 nodes wide
+    wb = g.walls and y0 == 0
+    wt = g.walls and y0 + ty >= nyf
+    hy = nyf - y0 if wt else ty          # fluid rows of the tile
+    assert x0 + tx <= nx, "TMA tiles are full in x"
+    assert y0 + ty <= nyf or wt, "only a top wall tile may be ragged"
+    assert hy >= 1 and not (wb and wt)
+    # the neighbour tiles across the halo are full or at least 4 nodes wide
     for c in (x0 - 1, x0 + tx):
         if seam or 0 <= c < nx:
             t = wrap(c, nx) // tx
             assert min(tx, nx - t * tx) >= 4
     for c in (y0 - 1, y0 + ty):
+        if g.walls and not 0 <= c < nyf:
+            continue                      # beyond a wall: no tile
         if seam or 0 <= c < nyf:
             t = wrap(c, nyf) // ty
             assert min(ty, nyf - t * ty) >= 4
@@ -125,86 +148,139 @@ def check_tile(g, tx, ty, bx, by, seam):
             i0 = g.ring_index(c, bx, by + edge_tile(ri), y0, x0 - 4)
             assert 0 <= i0 and i0 + rl <= g.ring_elems(c)
         return
-    # seam tiles: partial sums staged element by element, wrapped
+    # edge tiles: partial sums staged element by element, wrapped across
+    # periodic edges; with walls only fluid rows and existing tile rows
     for ci in range(4):
         c = R_L if ci & 1 else R_R
         t = neighbour_tile(x0, edge_tile(ci), tx, nx, True)
         for j in range(cl):
-            assert 0 <= g.ring_index(c, t, 0, wrap(y0 - 4 + j, nyf), 0) < g.ring_elems(c)
+            r = y0 - 4 + j
+            if g.walls and not 0 <= r < nyf:
+                continue
+            assert 0 <= g.ring_index(c, t, 0, wrap(r, nyf), 0) < g.ring_elems(c)
     for ri in range(4):
+        if (wb and ri <= 1) or (wt and ri >= 2):
+            continue
         c = R_B if ri & 1 else R_T
-        t = neighbour_tile(y0, edge_tile(ri), ty, nyf, True)
+        t = neighbour_tile(y0, edge_tile(ri), ty, nyf, not g.walls)
+        if g.walls:   # the tile row of the halo node, no wrap
+            assert t == by + (-1 if ri == 0 else 1 if ri == 3 else 0)
         for j in range(rl):
             assert 0 <= g.ring_index(c, 0, t, 0, wrap(x0 - 4 + j, nx)) < g.ring_elems(c)
-    xl, xr, yb, yt = x0 == 0, x0 + tx >= nx, y0 == 0, y0 + ty >= nyf
-    # density fix-ups (seam_rho_slot) cover every zero-filled entry read
+    xl, xr = x0 == 0, x0 + tx >= nx
+    yb, yt = not g.walls and y0 == 0, not g.walls and y0 + ty >= nyf
+    vlo, vhi = (2 if wb else 0), (hy + 2 if wt else ty + 4)
+    # density fix-ups (seam_rho_slot) cover every zero-filled entry read:
+    # the fluid rows of the halo and the sources of the Eq. 28 rows
     fixed = set()
-    for t in range(2 * (ty + 4) + 2 * (tx + 4)):
+    for t in range(2 * (ty + 4) + 2 * (tx + 4) + 4):
         if t < 2 * (ty + 4):
             if not (xl or xr):
                 continue
             ly, c = t >> 1, (2 if xl else tx + 4) + (t & 1)
-        else:
+            if not vlo <= ly < vhi:
+                continue
+        elif t < 2 * (ty + 4) + 2 * (tx + 4):
             if not (yb or yt):
                 continue
             q = t - 2 * (ty + 4)
             sel = q // (tx + 4)
             ly, c = (0 if yb else ty + 2) + sel, 2 + q - sel * (tx + 4)
-        x, r = wrap(x0 - 4 + c, nx), wrap(y0 - 2 + ly, nyf)
-        assert 0 <= x < nx and 0 <= r < nyf
+        else:
+            k = t - 2 * (ty + 4) - 2 * (tx + 4)
+            top, right = k >> 1, k & 1
+            if not ((wt if top else wb) and (xr if right else xl)):
+                continue
+            ly, c = (hy + 1 if top else 2), (tx + 6 if right else 1)
+        x, r = wrap(x0 - 4 + c, nx), y0 - 2 + ly
+        assert 0 <= x < nx
+        assert 0 <= r < nyf if g.walls else True
         fixed.add((ly, c))
-    for ly in range(ty + 4):
-        for c in range(2, tx + 6):
-            if not (0 <= x0 - 4 + c < nx and 0 <= y0 - 2 + ly < nyf):
-                assert (ly, c) in fixed
-    # odd-step population fix-ups (seam_pop_slot) cover every source across
-    # an edge; only boundary nodes can have one
-    fixed = set()
+    read = {(ly, c) for ly in range(vlo, vhi) for c in range(2, tx + 6)}
+    if wb:
+        read |= {(2, c) for c in range(1, tx + 7)}
+    if wt:
+        read |= {(hy + 1, c) for c in range(1, tx + 7)}
+    for ly, c in read:
+        x, r = x0 - 4 + c, y0 - 2 + ly
+        assert not (g.walls and not 0 <= r < nyf), "a solid row is read as stored"
+        if not (0 <= x < nx and 0 <= r < nyf):
+            assert (ly, c) in fixed, (ly, c)
+        # entries outside the halo (columns 1 and tx + 6, read only by the
+        # Eq. 28 average) get no partial sums: the node there must hold its
+        # whole density, i.e. sit on no edge of its own tile that receives
+        # partial sums (load_rho_stored)
+        if c in (1, tx + 6):
+            xs, rr = wrap(x, nx), r
+            tx0 = xs // tx * tx
+            wxx = min(tx, nx - tx0)
+            ty0 = rr // ty * ty
+            wyy = min(ty, nyf - ty0)
+            lxx, lyy = xs - tx0, rr - ty0
+            edge = lxx in (0, wxx - 1) or \
+                (lyy == 0 and not (g.walls and rr == 0)) or \
+                (lyy == wyy - 1 and not (g.walls and rr == nyf - 1))
+            assert not edge, ("Eq. 28 source needs partial sums", ly, c)
+    # odd-step population fix-ups (seam_pop_slot) cover every source the
+    # TMA box cannot deliver: across a periodic edge, or in a solid row
+    fixed = {}
     for t in range(3 * ty + 3 * tx):
         if t < 3 * ty:
             if not (xl or xr):
                 continue
             d, ly = t // ty, t % ty
+            if ly >= hy:
+                continue
             lx = 0 if xl else tx - 1
             i = ([1, 5, 8] if xl else [3, 6, 7])[d]
         else:
-            if not (yb or yt):
+            bottom = yb or wb
+            if not (bottom or yt or wt):
                 continue
             q = t - 3 * ty
             d, lx = q // tx, q % tx
-            ly = 0 if yb else ty - 1
-            i = ([2, 5, 6] if yb else [4, 7, 8])[d]
-        xs, rs = wrap(x0 + lx - EX[i], nx), wrap(y0 + ly - EY[i], nyf)
-        assert 0 <= xs < nx and 0 <= rs < nyf
-        fixed.add((i, ly, lx))
-    border = {(lx, ly) for lx in (0, tx - 1) for ly in range(ty)} | \
-             {(lx, ly) for ly in (0, ty - 1) for lx in range(tx)}
-    for lx, ly in border:
-        for i in range(1, 9):
-            if not (0 <= x0 + lx - EX[i] < nx and 0 <= y0 + ly - EY[i] < nyf):
-                assert (i, ly, lx) in fixed
-            # the staged column matches the box's start
-            px = 4
-            start = x0 - px if EX[i] == 1 else x0
-            assert start + lx + pin_col(px, i) == x0 + lx - EX[i]
-        # odd-step writes: the offset correction (lanes 0 / TX-1, rows 0 /
-        # TY-1 at an edge) brings every target back into the lattice
-        for i in range(1, 9):
-            x, r = x0 + lx + EX[i], y0 + ly + EY[i]
-            if EX[i] < 0 and xl and lx == 0:
-                x += nx
-            if EX[i] > 0 and xr and lx == tx - 1:
-                x -= nx
-            if EY[i] < 0 and yb and ly == 0:
-                r += nyf
-            if EY[i] > 0 and yt and ly == ty - 1:
-                r -= nyf
-            assert 0 <= x < nx and 0 <= r < nyf
+            ly = 0 if bottom else hy - 1
+            i = ([2, 5, 6] if bottom else [4, 7, 8])[d]
+        src = aa_read_source(g, i, y0 + ly, x0 + lx)
+        assert 0 <= src[1] < nyf and 0 <= src[2] < nx
+        # two slots that name one node and direction fetch the same source
+        assert fixed.setdefault((i, ly, lx), src) == src
+    for ly in range(hy):
+        for lx in range(tx):
+            for i in range(1, 9):
+                x, r = x0 + lx, y0 + ly
+                plane, rs, xs = aa_read_source(g, i, r, x)
+                # the TMA box of direction i delivers slot opp(i) at row r -
+                # e_y, column x - e_x, inside the lattice only
+                boxed = plane == OPP[i] and rs == r - EY[i] and xs == x - EX[i]
+                if not boxed:
+                    assert (i, ly, lx) in fixed, (i, ly, lx)
+                # the staged column matches the box's start
+                px = 4
+                start = x0 - px if EX[i] == 1 else x0
+                assert start + lx + pin_col(px, i) == x0 + lx - EX[i]
+                # odd-step writes: into a solid row -> own slot opp(i);
+                # across a periodic edge -> corrected back into the lattice
+                xt, rt = x + EX[i], r + EY[i]
+                if g.walls and not 0 <= rt < nyf:
+                    assert (wb and ly == 0 and EY[i] < 0) or (wt and ly == hy - 1 and EY[i] > 0)
+                    continue
+                if EX[i] < 0 and xl and lx == 0:
+                    xt += nx
+                if EX[i] > 0 and xr and lx == tx - 1:
+                    xt -= nx
+                if EY[i] < 0 and yb and ly == 0:
+                    rt += nyf
+                if EY[i] > 0 and yt and ly == ty - 1:
+                    rt -= nyf
+                assert 0 <= xt < nx and 0 <= rt < nyf
     # hand-over: neighbour tiles are the tiles of the neighbour nodes
     for d in (-1, 1):
         t = neighbour_tile(x0, d, tx, nx, True)
         assert t == wrap(x0 - 1 if d < 0 else x0 + tx, nx) // tx
         assert 0 <= g.ring_index(R_L, t, 0, nyf - 1, 0) < g.ring_elems(R_L)
+        if (d < 0 and wb) or (d > 0 and wt):
+            continue                      # no ring row across a wall
         t = neighbour_tile(y0, d, ty, nyf, True)
         assert t == wrap(y0 - 1 if d < 0 else y0 + ty, nyf) // ty
         assert 0 <= g.ring_index(R_T, 0, t, 0, nx - 1) < g.ring_elems(R_T)
@@ -214,7 +290,11 @@ def _lattices():
     fixed = [(96, 96, False), (128, 48, False), (96, 50, True), (224, 165, False),
              (160, 100, False), (100, 100, False), (99, 54, True), (134, 77, True),
              (196, 52, False), (192, 98, True), (1000, 1000, False), (500, 200, True),
-             (70, 21, False), (5, 5, False), (131, 37, True), (4096, 4096, False)]
+             (70, 21, False), (5, 5, False), (131, 37, True), (4096, 4096, False),
+             # walls: top wall tiles 1 (general), 2, 3, 4 and 16 rows high;
+             # two tile rows
+             (128, 51, True), (128, 52, True), (128, 53, True), (128, 38, True),
+             (192, 66, True), (96, 22, True), (96, 38, True), (512, 256, True)]
     rng = random.Random(1611)
     extra = [(rng.choice([32, 64, 96, 128, 160, 192, 224, 256]) + rng.choice([0, 0, 1, 3, 4, 5, 20]),
               rng.randint(7, 300), rng.random() < 0.5) for _ in range(60)]
@@ -234,28 +314,41 @@ def test_library_classes_follow_the_stated_rules(seams):
 
 
 def test_index_arithmetic_of_tma_tiles():
-    checked = 0
+    checked = wall_tiles = ragged_tops = 0
     for nx, ny, walls in _lattices():
-        if nx * ny > 300 * 300:
+        if nx * ny > 520 * 260:
             continue
         g = Geometry(nx, ny, walls)
         for tx, ty in SHAPES:
             kinds = tile_kinds(nx, ny, walls, (tx, ty), True)
+            nty = kinds.shape[0]
             for by, bx in zip(*np.nonzero(kinds)):
                 check_tile(g, tx, ty, int(bx), int(by), kinds[by, bx] == 1)
                 checked += 1
-    assert checked > 2000
+                if walls and by in (0, nty - 1):
+                    wall_tiles += 1
+                    ragged_tops += by == nty - 1 and g.nyf % ty != 0
+    assert checked > 2000 and wall_tiles > 300 and ragged_tops > 100
 
 
 def test_small_shared_memory_launch_has_no_general_tile():
-    # launch_shape asks only for the TMA path's shared memory when both
-    # periodic directions are seams over full tiles
+    # launch_shape asks only for the TMA path's shared memory when x is
+    # periodic seams over full tiles and y either the same or walls with a
+    # top tile full or at least 4 rows high
+    seen = 0
     for nx, ny, walls in _lattices():
         for tx, ty in SHAPES:
             g = Geometry(nx, ny, walls)
-            if not walls and nx % tx == 0 and g.nyf % ty == 0 and \
-                    nx // tx >= 3 and g.nyf // ty >= 3:
+            nfy, ry = g.nyf // ty, g.nyf % ty
+            x_ok = nx % tx == 0 and nx // tx >= 3
+            if walls:
+                y_ok = (nfy >= 2 or (nfy == 1 and ry >= 4)) and (ry == 0 or ry >= 4)
+            else:
+                y_ok = ry == 0 and nfy >= 3
+            if x_ok and y_ok:
                 assert tile_kinds(nx, ny, walls, (tx, ty), True).min() >= 1
+                seen += walls
+    assert seen > 0
 
 
 def test_tile_kinds_rejects_bad_arguments():
