@@ -622,14 +622,15 @@ __device__ __forceinline__ int neighbour_tile(int c0, int d, int T, int n, bool 
 // tile's would, and one wrap step brings every coordinate into the lattice.
 // With walls, entries of rows outside the fluid and of tile rows beyond a
 // wall (below a bottom wall tile: edge rows 0 and 1; above a top wall
-// tile: 2 and 3) have no writer and are staged as zeros.
-template <class rt, int TX, int TY, int NT>
+// tile: 2 and 3) have no writer and are staged as zeros.  WALLS: the
+// variant that handles walled lattices (false: periodic ones only).
+template <class rt, int TX, int TY, int NT, bool WALLS>
 __device__ __forceinline__ void stage_ring_wrapped(const Lattice &L, int cur, int X0,
                                                    int Y0, rt *s_ring)
 {
     using RS = RingStage<rt, TX, TY>;
     rt *const *ring = (rt *const *)L.ring[cur];
-    const bool walls = L.walls != 0;
+    const bool walls = WALLS && L.walls != 0;
     const bool wb = walls && Y0 == 0, wt = walls && Y0 + TY >= L.nyf;
     for (int p = threadIdx.x; p < RS::N; p += NT) {
         long long idx = 0;
@@ -685,10 +686,11 @@ struct SeamEdges {
     int hy;               // fluid rows of the tile (below TY only on a ragged top wall tile)
     int vlo, vhi;         // staged density rows holding fluid nodes: [vlo, vhi)
 };
+template <bool WALLS>
 __device__ __forceinline__ SeamEdges seam_edges(const Lattice &L, int X0, int Y0, int TX,
                                                 int TY)
 {
-    const bool w = L.walls != 0;
+    const bool w = WALLS && L.walls != 0;
     const bool wb = w && Y0 == 0, wt = w && Y0 + TY >= L.nyf;
     const int hy = wt ? L.nyf - Y0 : TY;
     return {X0 == 0, X0 + TX >= L.nx, !w && Y0 == 0, !w && Y0 + TY >= L.nyf,
@@ -748,7 +750,7 @@ __device__ __forceinline__ bool seam_pop_slot(const SeamEdges &e, int t, int &i,
     i = bottom ? (d == 0 ? 2 : d == 1 ? 5 : 6) : (d == 0 ? 4 : d == 1 ? 7 : 8);
     return true;
 }
-template <class S, int TX, int TY, int NT, int PARITY>
+template <class S, int TX, int TY, int NT, int PARITY, bool WALLS>
 __device__ __forceinline__ void seam_fix_load(const Lattice &L, int cur, int X0, int Y0,
                                               typename S::real *fix_rho,
                                               typename S::pop_t *fix_pop)
@@ -756,7 +758,7 @@ __device__ __forceinline__ void seam_fix_load(const Lattice &L, int cur, int X0,
     using rt = typename S::rho_t;
     using pop_t = typename S::pop_t;
     using SL = SeamLists<TX, TY>;
-    const SeamEdges e = seam_edges(L, X0, Y0, TX, TY);
+    const SeamEdges e = seam_edges<WALLS>(L, X0, Y0, TX, TY);
     const rt *R = (const rt *)L.rho[cur];
     for (int t = threadIdx.x; t < SL::RHO; t += NT) {
         int ly, c;
@@ -770,25 +772,27 @@ __device__ __forceinline__ void seam_fix_load(const Lattice &L, int cur, int X0,
         for (int t = threadIdx.x; t < SL::POP; t += NT) {
             int i, lx, ly;
             if (!seam_pop_slot<TX, TY>(e, t, i, lx, ly)) continue;
-            fix_pop[t] = A[aa_read_index(L, 1, i, Y0 + ly, X0 + lx)];
+            fix_pop[t] = WALLS ? A[aa_read_index(L, 1, i, Y0 + ly, X0 + lx)]
+                               : A[pidx(L, opp(i), wrapi(Y0 + ly - ey(i), L.nyf),
+                                        wrapi(X0 + lx - ex(i), L.nx))];
         }
     }
 }
-template <class real, int TX, int TY, int NT, int RP>
+template <class real, int TX, int TY, int NT, int RP, bool WALLS>
 __device__ __forceinline__ void seam_rho_apply(const Lattice &L, int X0, int Y0,
                                                const real *fix_rho, real *s_rho)
 {
-    const SeamEdges e = seam_edges(L, X0, Y0, TX, TY);
+    const SeamEdges e = seam_edges<WALLS>(L, X0, Y0, TX, TY);
     for (int t = threadIdx.x; t < SeamLists<TX, TY>::RHO; t += NT) {
         int ly, c;
         if (seam_rho_slot<TX, TY>(e, t, ly, c)) s_rho[ly * RP + c] = fix_rho[t];
     }
 }
-template <class pop_t, int TX, int TY, int NT, int PLANE, int PP, int PX>
+template <class pop_t, int TX, int TY, int NT, int PLANE, int PP, int PX, bool WALLS>
 __device__ __forceinline__ void seam_pop_apply(const Lattice &L, int X0, int Y0,
                                                const pop_t *fix_pop, pop_t *s_pin)
 {
-    const SeamEdges e = seam_edges(L, X0, Y0, TX, TY);
+    const SeamEdges e = seam_edges<WALLS>(L, X0, Y0, TX, TY);
     for (int t = threadIdx.x; t < SeamLists<TX, TY>::POP; t += NT) {
         int i, lx, ly;
         if (seam_pop_slot<TX, TY>(e, t, i, lx, ly))
@@ -925,7 +929,7 @@ __device__ __forceinline__ T lap_w(const T (&w)[3][3])
     return (T(4) * axial + diag - T(20) * w[1][1]) * T(1.0 / 6.0);
 }
 
-template <class S, int TX, int TY, int NT, int PARITY, bool SEAM>
+template <class S, int TX, int TY, int NT, int PARITY, int EDGE>
 __device__ __forceinline__ bool step_tile_tma(const Lattice &L, int cur, int X0,
                                               int Y0, unsigned char *smem_raw,
                                               const TmaMaps &maps,
@@ -948,8 +952,10 @@ __device__ __forceinline__ bool step_tile_tma(const Lattice &L, int cur, int X0,
     real *s_down = s_up + NW * XW;                       // [NW][XW]
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int nxt = cur ^ 1;
-    // SEAM: a seam tile (tile_kind), whose halo wraps around a periodic edge
-    constexpr bool seam = SEAM;
+    // EDGE: 0 interior tile; an edge tile (tile_kind TILE_SEAM), whose halo
+    // wraps around a periodic edge, of a periodic lattice (1) or of any
+    // lattice, walls included (2)
+    constexpr bool seam = EDGE != 0, walls_ok = EDGE == 2;
 
     // 1. Loads (bar: the caller's two initialised mbarriers, this tile
     //    completing phase `phase` of each).  Density halo and populations by
@@ -970,15 +976,15 @@ __device__ __forceinline__ bool step_tile_tma(const Lattice &L, int cur, int X0,
     }
     pop_t *fix_pop = reinterpret_cast<pop_t *>(s_ring + TS::NRING);
     if (seam) {
-        stage_ring_wrapped<real, TX, TY, NT>(L, cur, X0, Y0, s_ring);
-        seam_fix_load<S, TX, TY, NT, PARITY>(L, cur, X0, Y0, s_mu, fix_pop);
+        stage_ring_wrapped<real, TX, TY, NT, walls_ok>(L, cur, X0, Y0, s_ring);
+        seam_fix_load<S, TX, TY, NT, PARITY, walls_ok>(L, cur, X0, Y0, s_mu, fix_pop);
     } else {
         stage_ring<real, TX, TY>(L, cur, X0, Y0, s_ring, &bar[0]);
     }
     cp_async_wait_all();
     if (!tma_landed(bar, 0, phase, L.err, L.wait_cycles)) return false;
     if (seam) {
-        seam_rho_apply<real, TX, TY, NT, RP>(L, X0, Y0, s_mu, s_rho);
+        seam_rho_apply<real, TX, TY, NT, RP, walls_ok>(L, X0, Y0, s_mu, s_rho);
         __syncthreads();
     }
 
@@ -988,8 +994,8 @@ __device__ __forceinline__ bool step_tile_tma(const Lattice &L, int cur, int X0,
     combine_ring<real, TX, TY, NT, RP>(s_rho, s_ring);
     __syncthreads();
     // edge tiles at a wall: the solid row's density (Eq. 28)
-    const SeamEdges edge = seam_edges(L, X0, Y0, TX, TY);
-    if (seam) wall_rho_rows<real, TX, NT, RP>(edge, s_rho);
+    const SeamEdges edge = seam_edges<walls_ok>(L, X0, Y0, TX, TY);
+    if (walls_ok) wall_rho_rows<real, TX, NT, RP>(edge, s_rho);
 
     // 3. mu at (a, b), a in [0, TX + 2) <-> x = X0 - 1 + a, b in [0, TY + 2)
     //    <-> r = Y0 - 1 + b; its density sits at staged (b + 1, a + 3).
@@ -1012,7 +1018,7 @@ __device__ __forceinline__ bool step_tile_tma(const Lattice &L, int cur, int X0,
 #pragma unroll
             for (int d = 0; d < 3; ++d) w[2][d] = s_rho[(b + 2) * RP + a + 2 + d];
             real m;
-            if (!(seam && wall_mu<S, RP>(L, edge, b, (b + 1) * RP + a + 3, s_rho, m)))
+            if (!(walls_ok && wall_mu<S, RP>(L, edge, b, (b + 1) * RP + a + 3, s_rho, m)))
                 m = mu_bulk(eos, w[1][1] + ref) - kappa * lap_w(w);
             s_mu[b * MP + a] = m;
 #pragma unroll
@@ -1025,7 +1031,7 @@ __device__ __forceinline__ bool step_tile_tma(const Lattice &L, int cur, int X0,
             const int ae = (t & 1) ? TX + 1 : 0, b = t >> 1;
             const int c = (b + 1) * RP + ae + 3;
             real m;
-            if (!(seam && wall_mu<S, RP>(L, edge, b, c, s_rho, m)))
+            if (!(walls_ok && wall_mu<S, RP>(L, edge, b, c, s_rho, m)))
                 m = mu_bulk(eos, s_rho[c] + ref) - kappa * lap9<real, RP>(s_rho, c);
             s_mu[b * MP + ae] = m;
         }
@@ -1034,7 +1040,7 @@ __device__ __forceinline__ bool step_tile_tma(const Lattice &L, int cur, int X0,
     // publishes s_mu
     if (!tma_landed(bar, 1, phase, L.err, L.wait_cycles)) return false;
     if (PARITY == 1 && seam) {
-        seam_pop_apply<pop_t, TX, TY, NT, PLANE, PP, TS::PX>(L, X0, Y0, fix_pop, s_pin);
+        seam_pop_apply<pop_t, TX, TY, NT, PLANE, PP, TS::PX, walls_ok>(L, X0, Y0, fix_pop, s_pin);
         __syncthreads();
     }
 
@@ -1061,7 +1067,7 @@ __device__ __forceinline__ bool step_tile_tma(const Lattice &L, int cur, int X0,
                                     (ex(i) < 0 ? cxl : ex(i) > 0 ? cxr : 0);
     // wall tiles: rows 0 .. hy - 1 hold fluid (hy < TY on a ragged top wall
     // tile; the rows above it are not updated and contribute nothing)
-    const int hy = seam ? edge.hy : TY;
+    const int hy = walls_ok ? edge.hy : TY;
     const bool has_l = lane > 0, has_r = lane < 31;
     real wr[3][3], wm[3][3];
 #pragma unroll
@@ -1095,7 +1101,7 @@ __device__ __forceinline__ bool step_tile_tma(const Lattice &L, int cur, int X0,
         }
         real same = real(0), up = real(0), down = real(0);
         real same_c = real(0), up_c = real(0), down_c = real(0);
-        if (!seam || ly < hy) {  // warp-uniform
+        if (!walls_ok || ly < hy) {  // warp-uniform
             real f[9];
 #pragma unroll
             for (int i = 1; i < 9; ++i)
@@ -1111,8 +1117,8 @@ __device__ __forceinline__ bool step_tile_tma(const Lattice &L, int cur, int X0,
             collide<real>(f, drho, rho, Fx, Fy, tau, omega, fp);
             // wall rows (halfway bounce-back, Sec. IV): what leaves into the
             // solid row comes back to the node
-            const bool wall_b = seam && edge.wb && ly == 0;
-            const bool wall_t = seam && edge.wt && ly == hy - 1;
+            const bool wall_b = walls_ok && edge.wb && ly == 0;
+            const bool wall_t = walls_ok && edge.wt && ly == hy - 1;
             {
                 const int wrap_y = L.nyf * L.pitch;
                 const int cyb = (PARITY == 1 && seam && edge.yb && ly == 0) ? wrap_y : 0;
@@ -1150,7 +1156,7 @@ __device__ __forceinline__ bool step_tile_tma(const Lattice &L, int cur, int X0,
         Arow += L.pitch;
         // rows of the lattice this warp may write (all but those above a
         // ragged top wall tile's fluid)
-        const bool row_ok = !seam || ly - 1 < hy;
+        const bool row_ok = !walls_ok || ly - 1 < hy;
         if (k == 0) {
             // this row's "down" belongs to the warp below (or the ring row
             // under the tile)
@@ -1191,7 +1197,7 @@ __device__ __forceinline__ bool step_tile_tma(const Lattice &L, int cur, int X0,
             top += s_down[(warp + 1) * XW + lane];
             top_c += s_down[(warp + 1) * XW + slot_c];
         }
-        if (!seam || ly0 + PER - 1 < hy) {
+        if (!walls_ok || ly0 + PER - 1 < hy) {
             Rn[(long long)(Y0 + ly0 + PER - 1) * L.pitch + X0 + lx] = (rho_t)top;
             if (col_lane) ring[cls_c][ring_index(L, R_L, bxc, by, Y0 + ly0 + PER - 1, xc)] = (rho_t)top_c;
         }
@@ -1200,7 +1206,7 @@ __device__ __forceinline__ bool step_tile_tma(const Lattice &L, int cur, int X0,
             first += s_up[(warp - 1) * XW + lane];
             first_c += s_up[(warp - 1) * XW + slot_c];
         }
-        if (!seam || ly0 < hy) {
+        if (!walls_ok || ly0 < hy) {
             Rn[(long long)(Y0 + ly0) * L.pitch + X0 + lx] = (rho_t)first;
             if (col_lane) ring[cls_c][ring_index(L, R_L, bxc, by, Y0 + ly0, xc)] = (rho_t)first_c;
         }
@@ -1209,13 +1215,13 @@ __device__ __forceinline__ bool step_tile_tma(const Lattice &L, int cur, int X0,
     // wall)
     const int bxl = neighbour_tile(X0, -1, TX, L.nx, seam);
     const int bxr = neighbour_tile(X0, 1, TX, L.nx, seam);
-    if (warp == 0 && !(seam && edge.wb)) {
+    if (warp == 0 && !(walls_ok && edge.wb)) {
         const int byb = neighbour_tile(Y0, -1, TY, L.nyf, seam);
         ring[R_T][ring_index(L, R_T, bx, byb, Y0 - 1, X0 + lx)] = (rho_t)s_down[lane];
         if (lane == 0) ring[R_TR][ring_index(L, R_TR, bxl, byb, Y0 - 1, X0 - 1)] = (rho_t)s_down[TX];
         if (lane == 31) ring[R_TL][ring_index(L, R_TL, bxr, byb, Y0 - 1, X0 + TX)] = (rho_t)s_down[TX + 1];
     }
-    if (warp == NW - 1 && !(seam && edge.wt)) {
+    if (warp == NW - 1 && !(walls_ok && edge.wt)) {
         const int byt = neighbour_tile(Y0, 1, TY, L.nyf, seam);
         ring[R_B][ring_index(L, R_B, bx, byt, Y0 + TY, X0 + lx)] = (rho_t)up_prev;
         if (lane == 0) ring[R_BR][ring_index(L, R_BR, bxl, byt, Y0 + TY, X0 - 1)] = (rho_t)up_prev_c;
@@ -1413,7 +1419,7 @@ struct TmaPairSmem {
                   "pair-aligned sub-arrays");
 };
 
-template <class S, int TX, int TY, int NT, int PARITY, bool SEAM>
+template <class S, int TX, int TY, int NT, int PARITY, int EDGE>
 __device__ __forceinline__ bool step_tile_tma_pair(const Lattice &L, int cur, int X0,
                                                    int Y0, unsigned char *smem_raw,
                                                    const TmaMaps &maps,
@@ -1437,8 +1443,10 @@ __device__ __forceinline__ bool step_tile_tma_pair(const Lattice &L, int cur, in
     float *s_down = s_up + NW * XW;                       // [NW][XW]
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int nxt = cur ^ 1;
-    // SEAM: a seam tile (tile_kind), whose halo wraps around a periodic edge
-    constexpr bool seam = SEAM;
+    // EDGE: 0 interior tile; an edge tile (tile_kind TILE_SEAM), whose halo
+    // wraps around a periodic edge, of a periodic lattice (1) or of any
+    // lattice, walls included (2)
+    constexpr bool seam = EDGE != 0, walls_ok = EDGE == 2;
 
     // 1. Loads (bar, phase, seam tiles: as step_tile_tma).
     if (threadIdx.x == 0) {
@@ -1456,15 +1464,15 @@ __device__ __forceinline__ bool step_tile_tma_pair(const Lattice &L, int cur, in
     }
     pop_t *fix_pop = reinterpret_cast<pop_t *>(s_ring + TS::NRING);
     if (seam) {
-        stage_ring_wrapped<float, TX, TY, NT>(L, cur, X0, Y0, s_ring);
-        seam_fix_load<S, TX, TY, NT, PARITY>(L, cur, X0, Y0, s_mu, fix_pop);
+        stage_ring_wrapped<float, TX, TY, NT, walls_ok>(L, cur, X0, Y0, s_ring);
+        seam_fix_load<S, TX, TY, NT, PARITY, walls_ok>(L, cur, X0, Y0, s_mu, fix_pop);
     } else {
         stage_ring<float, TX, TY>(L, cur, X0, Y0, s_ring, &bar[0]);
     }
     cp_async_wait_all();
     if (!tma_landed(bar, 0, phase, L.err, L.wait_cycles)) return false;
     if (seam) {
-        seam_rho_apply<float, TX, TY, NT, RP>(L, X0, Y0, s_mu, s_rho);
+        seam_rho_apply<float, TX, TY, NT, RP, walls_ok>(L, X0, Y0, s_mu, s_rho);
         __syncthreads();
     }
 
@@ -1473,8 +1481,8 @@ __device__ __forceinline__ bool step_tile_tma_pair(const Lattice &L, int cur, in
     combine_ring<float, TX, TY, NT, RP>(s_rho, s_ring);
     __syncthreads();
     // edge tiles at a wall: the solid row's density (Eq. 28)
-    const SeamEdges edge = seam_edges(L, X0, Y0, TX, TY);
-    if (seam) wall_rho_rows<float, TX, NT, RP>(edge, s_rho);
+    const SeamEdges edge = seam_edges<walls_ok>(L, X0, Y0, TX, TY);
+    if (walls_ok) wall_rho_rows<float, TX, NT, RP>(edge, s_rho);
 
     // 3. mu at halo column a (x = X0 - 1 + a) and row b (r = Y0 - 1 + b),
     //    stored at s_mu[b][a + 1]; its density is staged at (b + 1, a + 3).
@@ -1492,7 +1500,7 @@ __device__ __forceinline__ bool step_tile_tma_pair(const Lattice &L, int cur, in
         for (int b = b0; b < b1; ++b) {
             const Row2 u = row2(s_rho, (b + 2) * RP + c0);
             float2 mp;
-            if (seam && ((edge.wb && b == 0) || (edge.wt && b >= edge.hy + 1))) {
+            if (walls_ok && ((edge.wb && b == 0) || (edge.wt && b >= edge.hy + 1))) {
                 // solid rows of wall tiles: surface values (wall_mu)
                 wall_mu<S, RP>(L, edge, b, (b + 1) * RP + c0, s_rho, mp.x);
                 wall_mu<S, RP>(L, edge, b, (b + 1) * RP + c0 + 1, s_rho, mp.y);
@@ -1508,7 +1516,7 @@ __device__ __forceinline__ bool step_tile_tma_pair(const Lattice &L, int cur, in
             const int ae = (t & 1) ? TX + 1 : 0, b = t >> 1;
             const int c = (b + 1) * RP + ae + 3;
             float mv;
-            if (!(seam && wall_mu<S, RP>(L, edge, b, c, s_rho, mv)))
+            if (!(walls_ok && wall_mu<S, RP>(L, edge, b, c, s_rho, mv)))
                 mv = mu_bulk(eos, s_rho[c] + ref) - K.kappa * lap9<float, RP>(s_rho, c);
             s_mu[b * MP + ae + 1] = mv;
         }
@@ -1517,7 +1525,7 @@ __device__ __forceinline__ bool step_tile_tma_pair(const Lattice &L, int cur, in
     // publishes s_mu
     if (!tma_landed(bar, 1, phase, L.err, L.wait_cycles)) return false;
     if (PARITY == 1 && seam) {
-        seam_pop_apply<pop_t, TX, TY, NT, PLANE, PP, TS::PX>(L, X0, Y0, fix_pop, s_pin);
+        seam_pop_apply<pop_t, TX, TY, NT, PLANE, PP, TS::PX, walls_ok>(L, X0, Y0, fix_pop, s_pin);
         __syncthreads();
     }
 
@@ -1534,7 +1542,7 @@ __device__ __forceinline__ bool step_tile_tma_pair(const Lattice &L, int cur, in
         woff[i] = PARITY == 0 ? (opp(i) - 1) * (int)L.plane
                               : (i - 1) * (int)L.plane + ey(i) * L.pitch + ex(i);
     // wall tiles: rows 0 .. hy - 1 hold fluid (as step_tile_tma)
-    const int hy = seam ? edge.hy : TY;
+    const int hy = walls_ok ? edge.hy : TY;
     const bool has_l = lane > 0, has_r = lane < 31;
     // windows: density of tile row ly at staged row ly + 2, column x0 + 4;
     // mu of tile row ly at s_mu row ly + 1, column x0 + 2
@@ -1564,7 +1572,7 @@ __device__ __forceinline__ bool step_tile_tma_pair(const Lattice &L, int cur, in
         const Row2 mu = row2(s_mu, (ly + 2) * MP + x0 + 2);
         float2 same = p2(0.0f), up = p2(0.0f), down = p2(0.0f);
         float same_c = 0.0f, up_c = 0.0f, down_c = 0.0f;
-        if (!seam || ly < hy) {  // warp-uniform
+        if (!walls_ok || ly < hy) {  // warp-uniform
             float2 f[9];
 #pragma unroll
             for (int i = 1; i < 9; ++i) {
@@ -1585,8 +1593,8 @@ __device__ __forceinline__ bool step_tile_tma_pair(const Lattice &L, int cur, in
             float2 fp[9];
             collide2(f, drho, rho, Fx, Fy, tau, omega, fp);
             // wall rows (halfway bounce-back, Sec. IV)
-            const bool wall_b = seam && edge.wb && ly == 0;
-            const bool wall_t = seam && edge.wt && ly == hy - 1;
+            const bool wall_b = walls_ok && edge.wb && ly == 0;
+            const bool wall_t = walls_ok && edge.wt && ly == hy - 1;
             {
                 // odd steps on seam tiles: a target across a periodic edge is
                 // brought back by one lattice length (the x-shifted directions
@@ -1633,7 +1641,7 @@ __device__ __forceinline__ bool step_tile_tma_pair(const Lattice &L, int cur, in
             down_c = lane == 0 ? fp[7].x : fp[8].y;
         }
         Arow += L.pitch;
-        const bool row_ok = !seam || ly - 1 < hy;
+        const bool row_ok = !walls_ok || ly - 1 < hy;
         if (k == 0) {
             *reinterpret_cast<float2 *>(s_down + warp * XW + x0) = down;
             if (col_lane) s_down[warp * XW + slot_c] = down_c;
@@ -1670,7 +1678,7 @@ __device__ __forceinline__ bool step_tile_tma_pair(const Lattice &L, int cur, in
             top = padd(top, *reinterpret_cast<const float2 *>(s_down + (warp + 1) * XW + x0));
             top_c += s_down[(warp + 1) * XW + slot_c];
         }
-        if (!seam || ly0 + PER - 1 < hy) {
+        if (!walls_ok || ly0 + PER - 1 < hy) {
             *reinterpret_cast<float2 *>(Rn + (long long)(Y0 + ly0 + PER - 1) * L.pitch + X0 +
                                         x0) = top;
             if (col_lane) ring[cls_c][ring_index(L, R_L, bxc, by, Y0 + ly0 + PER - 1, xc)] = top_c;
@@ -1679,20 +1687,20 @@ __device__ __forceinline__ bool step_tile_tma_pair(const Lattice &L, int cur, in
             first = padd(first, *reinterpret_cast<const float2 *>(s_up + (warp - 1) * XW + x0));
             first_c += s_up[(warp - 1) * XW + slot_c];
         }
-        if (!seam || ly0 < hy) {
+        if (!walls_ok || ly0 < hy) {
             *reinterpret_cast<float2 *>(Rn + (long long)(Y0 + ly0) * L.pitch + X0 + x0) = first;
             if (col_lane) ring[cls_c][ring_index(L, R_L, bxc, by, Y0 + ly0, xc)] = first_c;
         }
     }
     // ring rows below and above the tile, with their corners (none across a
     // wall)
-    if (warp == 0 && !(seam && edge.wb)) {
+    if (warp == 0 && !(walls_ok && edge.wb)) {
         *reinterpret_cast<float2 *>(ring[R_T] + ring_index(L, R_T, bx, byb, Y0 - 1, X0 + x0)) =
             *reinterpret_cast<const float2 *>(s_down + x0);
         if (lane == 0) ring[R_TR][ring_index(L, R_TR, bxl, byb, Y0 - 1, X0 - 1)] = s_down[TX];
         if (lane == 31) ring[R_TL][ring_index(L, R_TL, bxr, byb, Y0 - 1, X0 + TX)] = s_down[TX + 1];
     }
-    if (warp == NW - 1 && !(seam && edge.wt)) {
+    if (warp == NW - 1 && !(walls_ok && edge.wt)) {
         *reinterpret_cast<float2 *>(ring[R_B] + ring_index(L, R_B, bx, byt, Y0 + TY, X0 + x0)) = up_prev;
         if (lane == 0) ring[R_BR][ring_index(L, R_BR, bxl, byt, Y0 + TY, X0 - 1)] = up_prev_c;
         if (lane == 31) ring[R_BL][ring_index(L, R_BL, bxr, byt, Y0 + TY, X0 + TX)] = up_prev_c;
@@ -1735,7 +1743,10 @@ constexpr int pair_min_ctas()
     return sizeof(typename S::pop_t) == 2 && NT == 128 ? 6 : 640 / NT;
 }
 
-template <class S, int TX, int TY, int NT, int PARITY>
+// WALLS: the kernel of walled lattices, whose edge tiles include the wall
+// rows; periodic lattices take the variant without the wall code, so that it
+// does not weigh on the code the interior tiles run.
+template <class S, int TX, int TY, int NT, int PARITY, bool WALLS>
 __global__ void __launch_bounds__(NT, HasTmaPair<S, TX, TY, NT>::value
                                           ? pair_min_ctas<S, TX, TY, NT>() : 0)
     step_kernel(const Lattice L, int cur, int seams, const __grid_constant__ TmaMaps maps)
@@ -1760,18 +1771,18 @@ __global__ void __launch_bounds__(NT, HasTmaPair<S, TX, TY, NT>::value
             __syncthreads();
             if constexpr (HasTma<S, TX, TY, NT>::value) {
                 if (interior)
-                    step_tile_tma<S, TX, TY, NT, PARITY, false>(L, cur, X0, Y0, smem_raw,
-                                                                maps, bar, 0);
+                    step_tile_tma<S, TX, TY, NT, PARITY, 0>(L, cur, X0, Y0, smem_raw,
+                                                            maps, bar, 0);
                 else
-                    step_tile_tma<S, TX, TY, NT, PARITY, true>(L, cur, X0, Y0, smem_raw,
-                                                               maps, bar, 0);
+                    step_tile_tma<S, TX, TY, NT, PARITY, WALLS ? 2 : 1>(L, cur, X0, Y0,
+                                                                        smem_raw, maps, bar, 0);
             } else {
                 if (interior)
-                    step_tile_tma_pair<S, TX, TY, NT, PARITY, false>(L, cur, X0, Y0,
-                                                                     smem_raw, maps, bar, 0);
+                    step_tile_tma_pair<S, TX, TY, NT, PARITY, 0>(L, cur, X0, Y0,
+                                                                 smem_raw, maps, bar, 0);
                 else
-                    step_tile_tma_pair<S, TX, TY, NT, PARITY, true>(L, cur, X0, Y0,
-                                                                    smem_raw, maps, bar, 0);
+                    step_tile_tma_pair<S, TX, TY, NT, PARITY, WALLS ? 2 : 1>(
+                        L, cur, X0, Y0, smem_raw, maps, bar, 0);
             }
             return;
         }
@@ -1796,18 +1807,20 @@ static cudaError_t launch_shape(const Lattice &L, int parity, int cur,
     const size_t smem_max = smem_v4 > smem_tma ? smem_v4 : smem_tma;
     TmaMaps m{};
     if (maps && maps->valid && maps->tx == TX && maps->ty == TY) m = *maps;
-    auto k0 = step_kernel<S, TX, TY, NT, 0>;
-    auto k1 = step_kernel<S, TX, TY, NT, 1>;
-    static int configured = -1;  // device the attribute was set on
+    // kernels of periodic (index 0) and walled (1) lattices, by parity
+    void (*const kern[2][2])(const Lattice, int, int, const TmaMaps) = {
+        {step_kernel<S, TX, TY, NT, 0, false>, step_kernel<S, TX, TY, NT, 1, false>},
+        {step_kernel<S, TX, TY, NT, 0, true>, step_kernel<S, TX, TY, NT, 1, true>}};
+    static int configured = -1;  // device the attributes were set on
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
     if (configured != dev) {
-        e = cudaFuncSetAttribute(k0, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)smem_max);
-        if (e == cudaSuccess)
-            e = cudaFuncSetAttribute(
-                k1, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_max);
+        for (int w = 0; w < 2 && e == cudaSuccess; ++w)
+            for (int p = 0; p < 2 && e == cudaSuccess; ++p)
+                e = cudaFuncSetAttribute(kern[w][p],
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem_max);
         if (e != cudaSuccess) return e;
         configured = dev;
     }
@@ -1828,10 +1841,7 @@ static cudaError_t launch_shape(const Lattice &L, int parity, int cur,
                                   : ((seams & 2) && ry == 0));
     const size_t smem = (all_tma && smem_tma > 0) ? smem_tma : smem_max;
     dim3 grid(ntx, nty);
-    if (parity == 0)
-        k0<<<grid, NT, smem, s>>>(L, cur, seams, m);
-    else
-        k1<<<grid, NT, smem, s>>>(L, cur, seams, m);
+    kern[L.walls ? 1 : 0][parity & 1]<<<grid, NT, smem, s>>>(L, cur, seams, m);
     return cudaGetLastError();
 }
 
@@ -1903,14 +1913,16 @@ __global__ void __launch_bounds__(NT, sizeof(typename S::real) == 8 ? 2 : 4)
                 fenced = it.inst;
                 // a wait that gave up leaves the barriers in doubt: the rest
                 // of this CTA's items take the general path
+                // lattices of a batch may or may not have walls: edge tiles
+                // take the variant that handles both
                 if (it.kind == TILE_INTERIOR)
-                    tma = step_tile_tma<S, TX, TY, NT, PARITY, false>(sL, cur, it.bx * TX,
-                                                                      it.by * TY, smem_raw, m,
-                                                                      bar, phase);
+                    tma = step_tile_tma<S, TX, TY, NT, PARITY, 0>(sL, cur, it.bx * TX,
+                                                                  it.by * TY, smem_raw, m,
+                                                                  bar, phase);
                 else
-                    tma = step_tile_tma<S, TX, TY, NT, PARITY, true>(sL, cur, it.bx * TX,
-                                                                     it.by * TY, smem_raw, m,
-                                                                     bar, phase);
+                    tma = step_tile_tma<S, TX, TY, NT, PARITY, 2>(sL, cur, it.bx * TX,
+                                                                  it.by * TY, smem_raw, m,
+                                                                  bar, phase);
                 phase ^= 1u;
                 done = true;
             }
