@@ -40,17 +40,39 @@ KERNEL_SOURCES = ["paper_1611_00907_gb300/csrc/step_impl.cuh",
                   "paper_1611_00907_gb300/csrc/cplbm_internal.h"]
 
 
-def workload_config(n=N_SIDE):
+def workload_config(n=N_SIDE, ny=None, walls=False):
+    if walls:
+        ny = ny or n
+        return {"workload": "cs_wall_drop_%dx%d" % (n, ny), "nx": n, "ny": ny,
+                "eos": "carnahan-starling a=1 b=4 R=1", "T_over_Tc": 0.85,
+                "kappa": 0.5, "tau": 1.0,
+                "init": "half disc r = min(nx, ny)/4 on the bottom wall, Maxwell "
+                        "densities, tanh width 4; mu_s = mu_coex + 0.01",
+                "boundary": "solid rows y=0 and y=ny-1, x periodic",
+                "l2": "working set > L2 (no flush)" if n * ny > 4 * 1024 * 1024
+                      else "working set in L2"}
     return {"workload": "cs_spinodal_%dx%d" % (n, n), "nx": n, "ny": n,
             "eos": "carnahan-starling a=1 b=4 R=1", "T_over_Tc": 0.85,
             "kappa": 0.5, "tau": 1.0, "init": "rho_c(1+0.01*U[-1,1)), seed 1",
             "boundary": "periodic", "l2": "working set > L2 (no flush)"}
 
 
-def initial_rho(n=N_SIDE):
-    from paper_1611_00907_gb300 import eos_critical, inputs
+def initial_rho(n=N_SIDE, ny=None, walls=False):
+    """The bench lattice: the spinodal workload, or (walls) a drop on the
+    bottom wall of an n x ny lattice with solid bottom and top rows."""
+    from paper_1611_00907_gb300 import eos_coexistence, eos_critical, inputs
+    if walls:
+        ny = ny or n
+        rv, rl, _ = eos_coexistence("cs", 1.0, 4.0, 1.0, 0.85)
+        return inputs.wall_drop(n, ny, min(n, ny) / 4, rl, rv, 4.0)
     _, rc = eos_critical("cs", 1.0, 4.0, 1.0)
     return inputs.spinodal_noise(n, n, rc, 0.01, seed=1)
+
+
+def wall_mu():
+    """Surface chemical potential of the walled bench lattice."""
+    from paper_1611_00907_gb300 import eos_coexistence
+    return eos_coexistence("cs", 1.0, 4.0, 1.0, 0.85)[2] + 0.01
 
 
 # ---------------------------------------------------------------------------
@@ -185,18 +207,19 @@ def time_steps(sim, steps, warmup):
 
 
 def measure_gpu(precision, steps, warmup, rho, tile=None, no_tma=False,
-                force_model=None):
+                force_model=None, walls=False):
     import torch
     from paper_1611_00907_gb300 import Simulation
-    n = rho.shape[0]
+    ny, nx = rho.shape
     rho_dev = torch.tensor(rho, device="cuda")
     old = os.environ.get("CPLBM_NO_TMA")
     if no_tma:
         os.environ["CPLBM_NO_TMA"] = "1"
     try:
-        sim = Simulation(n, n, precision=precision,
+        wall_args = dict(walls=True, mu_bottom=wall_mu()) if walls else {}
+        sim = Simulation(nx, ny, precision=precision,
                          rho_ref=0.15 if "offset" in precision else 0.0,
-                         **EOS_ARGS)
+                         **EOS_ARGS, **wall_args)
     finally:
         if no_tma:
             if old is None:
@@ -608,10 +631,11 @@ def cpu_baseline(budget_s=15.0):
             "single_core_sample": "%dx%d, %d steps, 1 thread" % (m, m, s1)}
 
 
-def roofline(precision, ms_per_step, n_nodes, n_side=N_SIDE):
+def roofline(precision, ms_per_step, n_nodes, n_side=N_SIDE, walls=False):
     peak, src = hbm_peak()
     achieved = BYTES_PER_LU[precision] * n_nodes / (ms_per_step * 1e-3) / 1e9
-    traffic = recorded_traffic(precision, n_side)
+    # the recorded counters are of the periodic spinodal workload
+    traffic = None if walls else recorded_traffic(precision, n_side)
     return {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak,
             "unit": "GB/s", "frac": round(achieved / peak, 4),
             "traffic": traffic, "peak_source": src,
@@ -750,6 +774,14 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--n", type=int, default=N_SIDE,
                     help="lattice side (profiling runs use smaller cases)")
+    ap.add_argument("--walls", action="store_true",
+                    help="time a walled lattice (a drop on the bottom wall) "
+                         "instead of the spinodal workload")
+    ap.add_argument("--ny", type=int, default=None,
+                    help="lattice height with --walls, solid rows included "
+                         "(default: --n)")
+    ap.add_argument("--batches", default="uneven,wetting,wetting_f16",
+                    help="batched workloads to time (comma list)")
     ap.add_argument("--tile", default=None,
                     help="step tile shape TXxTY (default: the library's)")
     ap.add_argument("--batch-steps", type=int, default=100,
@@ -764,6 +796,10 @@ def main():
                          "1.5x as many (0: skip both)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
+    if args.walls:
+        # the end-to-end and pressure-tensor legs are defined on the periodic
+        # spinodal workload
+        args.no_e2e, args.pt_steps = True, 0
     rank, world = dist_setup()
     if args.impl == "reference":
         return run_reference(args, rank, world)
@@ -774,20 +810,22 @@ def main():
         return 1
     import __graft_entry__
     __graft_entry__.build()
-    rho = initial_rho(args.n)
+    rho = initial_rho(args.n, args.ny, args.walls)
     n_nodes = rho.size
     tile = tuple(int(v) for v in args.tile.split("x")) if args.tile else None
 
     barrier(world)
     with ClockSampler(int(os.environ.get("LOCAL_RANK", "0"))) as clocks:
-        ms = measure_gpu(args.precision, args.steps, args.warmup, rho, tile)
+        ms = measure_gpu(args.precision, args.steps, args.warmup, rho, tile,
+                         walls=args.walls)
     ms = max_over_ranks(ms, world)
     ms_step = ms / args.steps
     value = world * n_nodes * args.steps / (ms * 1e-3) / 1e6
 
     fp64 = None
     if args.fp64_steps > 0:
-        fp64_ms = measure_gpu("f64", args.fp64_steps, 3, rho) / args.fp64_steps
+        fp64_ms = measure_gpu("f64", args.fp64_steps, 3, rho,
+                              walls=args.walls) / args.fp64_steps
         fp64_ms = max_over_ranks(fp64_ms, world)
         fp64 = {"value": world * n_nodes / (fp64_ms * 1e-3) / 1e6,
                 "unit": "MLUPS", "ms_per_step": fp64_ms,
@@ -798,12 +836,13 @@ def main():
     # lattice
     fp16 = None
     if args.fp16_steps > 0:
-        f16_ms = measure_gpu("f16_offset", args.fp16_steps, 3, rho) / args.fp16_steps
+        f16_ms = measure_gpu("f16_offset", args.fp16_steps, 3, rho,
+                             walls=args.walls) / args.fp16_steps
         f16_ms = max_over_ranks(f16_ms, world)
         fp16 = {"value": world * n_nodes / (f16_ms * 1e-3) / 1e6,
                 "unit": "MLUPS", "ms_per_step": f16_ms,
                 "steps": args.fp16_steps,
-                "roofline": roofline("f16_offset", f16_ms, n_nodes, args.n)}
+                "roofline": roofline("f16_offset", f16_ms, n_nodes, args.n, args.walls)}
 
     e2e = None
     if not args.no_e2e:
@@ -828,11 +867,14 @@ def main():
                         "steps": k}
 
     batches = {}
-    if args.batch_steps > 0:
+    legs = set(args.batches.split(",")) if args.batch_steps > 0 else set()
+    if "uneven" in legs:
         batches["batch_uneven"] = measure_batch("uneven", "f32",
                                                 args.batch_steps, 4)
+    if "wetting" in legs:
         batches["batch_wetting"] = measure_batch("wetting", "f32",
                                                  args.batch_steps, 4)
+    if "wetting_f16" in legs:
         batches["batch_wetting_f16"] = measure_batch(
             "wetting", "f16_offset", args.batch_steps, 4, sequential=False)
 
@@ -860,8 +902,9 @@ def main():
                 "ms_per_step": ms_step, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None,
                 "dtype": args.precision, "data": "synthetic",
-                "config": workload_config(args.n),
-                "roofline": roofline(args.precision, ms_step, n_nodes, args.n),
+                "config": workload_config(args.n, args.ny, args.walls),
+                "roofline": roofline(args.precision, ms_step, n_nodes, args.n,
+                                     args.walls),
                 "fp64": fp64, "fp16_offset": fp16, "e2e": e2e,
                 "cpu_baseline": base,
                 "gpu_launches": args.steps, "clocks": clocks.summary()}

@@ -86,25 +86,33 @@ lbm_status rebuild(lbm_batch *b)
         if (!b->active[i]) continue;
         const Lattice &L = c->L;
         const int ntx = (L.nx + b->tx - 1) / b->tx, nty = (L.nyf + b->ty - 1) / b->ty;
-        // edge tiles (periodic seams, wall rows) take the TMA path of the
-        // 32-wide shapes too (step_batch_kernel)
-        const int seams = b->tx == 32 ? seam_bits(L, b->tx, b->ty) : 0;
+        // edge tiles (periodic seams, wall rows) take the TMA paths too: the
+        // 32-wide one, and for FP32 arithmetic the 64-wide pair path
+        // (step_batch_kernel)
+        const bool tma_shape = b->tx == 32 || (b->tx == 64 && b->precision != LBM_F64);
+        const int seams = tma_shape ? seam_bits(L, b->tx, b->ty) : 0;
         for (int by = 0; by < nty; ++by)
             for (int bx = 0; bx < ntx; ++bx)
                 items.push_back({(int)i, bx, by, tile_kind(L, b->tx, b->ty, bx, by, seams)});
     }
-    // General tiles cost a few interior tiles each.  CTAs take items in list
-    // order, backwards on odd steps, so the general tiles go in the middle,
-    // between two halves of the others: in either direction a step ends on
-    // short items and the CTAs finish close together.
+    // General tiles cost a few interior tiles each, edge tiles (seams,
+    // walls) somewhat more than one.  CTAs take items in list order,
+    // backwards on odd steps: the interior tiles go in two halves at the
+    // ends, so that in either direction a step ends on short items and the
+    // CTAs finish close together, and the edge and general tiles between
+    // them, each class in one run, so that the CTAs of an SM mostly run the
+    // same code path at a time (the batched kernel holds three large ones
+    // and the instruction cache does not hold them all).
     {
-        std::vector<WorkItem> gen, rest;
-        for (const WorkItem &it : items) (it.kind == TILE_GENERAL ? gen : rest).push_back(it);
-        const size_t h = rest.size() / 2;
+        std::vector<WorkItem> gen, edge, inner;
+        for (const WorkItem &it : items)
+            (it.kind == TILE_GENERAL ? gen : it.kind == TILE_SEAM ? edge : inner).push_back(it);
+        const size_t h = inner.size() / 2;
         items.clear();
-        items.insert(items.end(), rest.begin(), rest.begin() + h);
+        items.insert(items.end(), inner.begin(), inner.begin() + h);
+        items.insert(items.end(), edge.begin(), edge.end());
         items.insert(items.end(), gen.begin(), gen.end());
-        items.insert(items.end(), rest.begin() + h, rest.end());
+        items.insert(items.end(), inner.begin() + h, inner.end());
     }
     dev_free(b->d_lats);
     dev_free(b->d_items);
@@ -216,7 +224,7 @@ lbm_status lbm_batch_create(const lbm_instance *inst, int count, int precision,
         }
         b->own_stream = true;
     }
-    // the batched kernel's TMA path is the 32-wide one
+    // the default shape (lbm_batch_autotune picks among all of them)
     b->tx = 32;
     b->ty = 32;
     for (int i = 0; i < count && st == LBM_OK; ++i) {

@@ -1855,7 +1855,9 @@ static cudaError_t launch_shape(const Lattice &L, int parity, int cur,
 // that item's lattice, whose descriptor it first copies to shared memory.
 // ---------------------------------------------------------------------------
 template <class S, int TX, int TY, int NT, int PARITY>
-__global__ void __launch_bounds__(NT, sizeof(typename S::real) == 8 ? 2 : 4)
+__global__ void __launch_bounds__(NT, HasTmaPair<S, TX, TY, NT>::value
+                                          ? pair_min_ctas<S, TX, TY, NT>()
+                                          : (sizeof(typename S::real) == 8 ? 2 : 4))
     step_batch_kernel(const Lattice *__restrict__ lats,
                       const WorkItem *__restrict__ items, int n_items, int cur,
                       const TmaMaps *__restrict__ maps, int *counter)
@@ -1873,7 +1875,8 @@ __global__ void __launch_bounds__(NT, sizeof(typename S::real) == 8 ? 2 : 4)
     // general-path items reuse, are initialised once, and every TMA tile
     // completes one phase of each.
     __shared__ __align__(8) unsigned long long bar[2];
-    bool tma = HasTma<S, TX, TY, NT>::value && maps != nullptr;
+    bool tma = (HasTma<S, TX, TY, NT>::value || HasTmaPair<S, TX, TY, NT>::value) &&
+               maps != nullptr;
     unsigned phase = 0;
     if (tma) {
         if (threadIdx.x == 0) {
@@ -1900,7 +1903,7 @@ __global__ void __launch_bounds__(NT, sizeof(typename S::real) == 8 ? 2 : 4)
         }
         __syncthreads();
         bool done = false;
-        if constexpr (HasTma<S, TX, TY, NT>::value) {
+        if constexpr (HasTma<S, TX, TY, NT>::value || HasTmaPair<S, TX, TY, NT>::value) {
             const TmaMaps &m = maps[it.inst];
             if (tma && it.kind != TILE_GENERAL && m.valid && m.tx == TX && m.ty == TY) {
                 if (threadIdx.x == 0 && fenced != it.inst) {
@@ -1915,14 +1918,21 @@ __global__ void __launch_bounds__(NT, sizeof(typename S::real) == 8 ? 2 : 4)
                 // of this CTA's items take the general path
                 // lattices of a batch may or may not have walls: edge tiles
                 // take the variant that handles both
-                if (it.kind == TILE_INTERIOR)
-                    tma = step_tile_tma<S, TX, TY, NT, PARITY, 0>(sL, cur, it.bx * TX,
-                                                                  it.by * TY, smem_raw, m,
-                                                                  bar, phase);
-                else
-                    tma = step_tile_tma<S, TX, TY, NT, PARITY, 2>(sL, cur, it.bx * TX,
-                                                                  it.by * TY, smem_raw, m,
-                                                                  bar, phase);
+                if constexpr (HasTma<S, TX, TY, NT>::value) {
+                    if (it.kind == TILE_INTERIOR)
+                        tma = step_tile_tma<S, TX, TY, NT, PARITY, 0>(
+                            sL, cur, it.bx * TX, it.by * TY, smem_raw, m, bar, phase);
+                    else
+                        tma = step_tile_tma<S, TX, TY, NT, PARITY, 2>(
+                            sL, cur, it.bx * TX, it.by * TY, smem_raw, m, bar, phase);
+                } else {  // two nodes per lane (64-wide FP32-arithmetic shapes)
+                    if (it.kind == TILE_INTERIOR)
+                        tma = step_tile_tma_pair<S, TX, TY, NT, PARITY, 0>(
+                            sL, cur, it.bx * TX, it.by * TY, smem_raw, m, bar, phase);
+                    else
+                        tma = step_tile_tma_pair<S, TX, TY, NT, PARITY, 2>(
+                            sL, cur, it.bx * TX, it.by * TY, smem_raw, m, bar, phase);
+                }
                 phase ^= 1u;
                 done = true;
             }
@@ -1947,10 +1957,13 @@ static cudaError_t launch_batch_shape(const Lattice *d_lats,
                                       cudaStream_t s)
 {
     using real = typename S::real;
-    constexpr int NT = STEP_THREADS;
+    constexpr int NT = step_threads<S, TX, TY>();
     size_t smem = StepSmem<real, TX, TY>::bytes;
     if constexpr (HasTma<S, TX, TY, NT>::value)
         if (TmaSmem<S, TX, TY>::bytes > smem) smem = TmaSmem<S, TX, TY>::bytes;
+    if constexpr (HasTmaPair<S, TX, TY, NT>::value)
+        if (TmaPairSmem<typename S::pop_t, TX, TY, NT>::bytes > smem)
+            smem = TmaPairSmem<typename S::pop_t, TX, TY, NT>::bytes;
     auto k0 = step_batch_kernel<S, TX, TY, NT, 0>;
     auto k1 = step_batch_kernel<S, TX, TY, NT, 1>;
     static int configured = -1, slots = 0;

@@ -26,9 +26,9 @@ SPECS = [
 ]
 
 
-def _instances():
+def _instances(specs=None):
     out = []
-    for s in SPECS:
+    for s in (SPECS if specs is None else specs):
         e = thermo.make_eos(s["eos"], s["a"], s["b"], 1.0, s["Tr"], 0.344)
         rv, rl, mc, _ = thermo.maxwell(e)
         d = {k: v for k, v in s.items() if k != "mu_delta"}
@@ -151,3 +151,56 @@ def test_inactive_lattices_keep_their_state(oracle_threads):
             got = b.moments(k)
             for key in ("rho", "mu", "vx", "vy"):
                 assert _rel(got[key], ref.moments()[key]) < 1e-12, (k, key)
+
+
+# Lattices whose 64-wide tiles include interior, periodic-seam and wall tiles
+# (three or more full 64-wide tiles across), plus the heterogeneous set.
+PAIR_SPECS = [
+    dict(nx=192, ny=66, eos="cs", a=1.0, b=4.0, Tr=0.85, tau=1.0, kappa=0.5,
+         walls=True, mu_delta=0.01),
+    dict(nx=256, ny=128, eos="cs", a=1.0, b=4.0, Tr=0.85, tau=1.0, kappa=0.5),
+    dict(nx=200, ny=100, eos="rks", a=2 / 49, b=2 / 21, Tr=0.8, tau=1.3,
+         kappa=0.01, walls=True, mu_delta=-0.05),
+]
+
+
+@pytest.mark.parametrize("tile", [(32, 16), (32, 24), (32, 32), (64, 16), (64, 32)])
+@pytest.mark.parametrize("precision", ["f32", "f32_offset", "f16_offset"])
+def test_batch_tile_shapes_reduced_precision(tile, precision):
+    """Every tile shape of the batched kernel in FP32 arithmetic (the
+    64-wide shapes on the two-nodes-per-lane TMA path, edge tiles
+    included): each lattice against the FP64 oracle and against its own
+    single-lattice run at the same shape."""
+    inst = _instances(SPECS + PAIR_SPECS)
+    for d, e, rho in inst:
+        rv, rl, _, _ = thermo.maxwell(e)
+        d["rho_ref"] = 0.5 * (rv + rl) if precision != "f32" else 0.0
+    with Batch([d for d, _, _ in inst], precision=precision) as b:
+        b.set_tile(*tile)
+        for k, (_, _, rho) in enumerate(inst):
+            b.init(k, rho)
+        b.step(40)
+        for k, (d, e, rho) in enumerate(inst):
+            ref = oracle.Lattice(d["nx"], d["ny"], e, d["tau"], d["kappa"],
+                                 walls=d.get("walls", False),
+                                 mu_bottom=d["mu_bottom"])
+            ref.init_equilibrium(rho).step(40)
+            kw = {x: d[x] for x in ("eos", "a", "b", "tau", "kappa", "walls",
+                                    "mu_bottom", "rho_ref") if x in d}
+            with Simulation(d["nx"], d["ny"], Tr=d["Tr"], precision=precision,
+                            **kw) as sim:
+                sim.set_tile(*tile)
+                sim.init(rho).step(40)
+                one = sim.moments()
+            got, want = b.moments(k), ref.moments()
+            if precision == "f16_offset":
+                # half-precision populations: density only, ~1e-3 after 40 steps
+                assert _rel(got["rho"], want["rho"]) < 2e-3, (k, "rho")
+                assert _rel(got["rho"], one["rho"]) < 2e-3, (k, "rho")
+                continue
+            # the velocity is a small difference of populations of size rho/9:
+            # its FP32 rounding relative to max |v| reaches ~1e-4 on the RKS
+            # lattice (density ratio ~30)
+            for key, tol in (("rho", 1e-4), ("mu", 1e-4), ("vx", 3e-4), ("vy", 3e-4)):
+                assert _rel(got[key], want[key]) < tol, (k, key)
+            assert _rel(got["rho"], one["rho"]) < 1e-5, k
