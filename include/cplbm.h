@@ -250,6 +250,15 @@ lbm_status lbm_mlp_create(int device, const float *init, lbm_mlp **out);
  * squared error of the last step's forward pass. */
 lbm_status lbm_mlp_train(lbm_mlp *m, const float *X, int nin, const float *T,
                          int nout, int B, int iters, float lr, float *loss);
+/* The full-batch gradient of the loss of lbm_mlp_train (mean squared
+ * error of the first nout outputs against T) with respect to the FP32
+ * parameters, from one forward and backward pass of the training kernels
+ * (BF16 weights, activations and layer deltas, FP32 accumulation); the
+ * parameters and the optimiser state are left unchanged.  X, T as for
+ * lbm_mlp_train (device); grad: host array of lbm_mlp_param_count()
+ * values; *loss (may be NULL) receives the mean squared error. */
+lbm_status lbm_mlp_gradient(lbm_mlp *m, const float *X, int nin, const float *T,
+                            int nout, int B, float *grad, float *loss);
 /* Y [B][nout] = the network's first nout outputs for X [B][nin] (device). */
 lbm_status lbm_mlp_predict(lbm_mlp *m, const float *X, int nin, float *Y,
                            int nout, int B);

@@ -98,6 +98,8 @@ SIGNATURES = {
     "lbm_mlp_train": ([_ctx, _vp, C.c_int, _vp, C.c_int, C.c_int, C.c_int,
                        C.c_float, C.POINTER(C.c_float)], C.c_int),
     "lbm_mlp_predict": ([_ctx, _vp, C.c_int, _vp, C.c_int, C.c_int], C.c_int),
+    "lbm_mlp_gradient": ([_ctx, _vp, C.c_int, _vp, C.c_int, C.c_int, _vp,
+                          C.POINTER(C.c_float)], C.c_int),
     "lbm_mlp_get_params": ([_ctx, _vp], C.c_int),
     "lbm_mlp_destroy": ([_ctx], None),
     "lbm_mlp_last_error": ([_ctx], C.c_char_p),

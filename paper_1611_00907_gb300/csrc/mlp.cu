@@ -420,6 +420,32 @@ lbm_status lbm_mlp_train(lbm_mlp *m, const float *X, int nin, const float *T,
     return LBM_OK;
 }
 
+lbm_status lbm_mlp_gradient(lbm_mlp *m, const float *X, int nin, const float *T,
+                            int nout, int B, float *grad, float *loss_out)
+{
+    if (!m) return LBM_ERR_ARG;
+    if (!X || !T || !grad || B <= 0 || nin < 1 || nin > DIN || nout < 1 || nout > DOUT)
+        return mfail(m, LBM_ERR_ARG, "bad gradient arguments", cudaSuccess);
+    MCUDA(m, cudaSetDevice(m->device), "cudaSetDevice");
+    lbm_status st = smem_attr(m);
+    if (st != LBM_OK) return st;
+    // the training pass without the optimiser step: the accumulated full-batch
+    // gradient is copied out and the accumulator cleared again
+    MCUDA(m, cudaMemsetAsync(m->grad, 0, NPARAM * sizeof(float)), "memset");
+    MCUDA(m, cudaMemsetAsync(m->loss, 0, sizeof(float)), "memset");
+    mlp_train_kernel<<<(B + SAMPLES - 1) / SAMPLES, THREADS, sizeof(Smem)>>>(
+        params_of(m), X, nin, T, nout, B, m->grad, m->loss);
+    MCUDA(m, cudaGetLastError(), "mlp gradient launch");
+    float loss = 0.f;
+    MCUDA(m, cudaMemcpy(grad, m->grad, NPARAM * sizeof(float), cudaMemcpyDeviceToHost),
+          "gradient copy");
+    MCUDA(m, cudaMemcpy(&loss, m->loss, sizeof(float), cudaMemcpyDeviceToHost),
+          "loss copy");
+    MCUDA(m, cudaMemset(m->grad, 0, NPARAM * sizeof(float)), "memset");
+    if (loss_out) *loss_out = loss / (float)(B * nout);
+    return LBM_OK;
+}
+
 lbm_status lbm_mlp_predict(lbm_mlp *m, const float *X, int nin, float *Y,
                            int nout, int B)
 {

@@ -73,6 +73,17 @@ class Mlp:
             X.shape[0], int(iters), float(lr), C.byref(loss)), self._m)
         return loss.value
 
+    def gradient(self, X, T):
+        """Full-batch gradient of the training loss at the current
+        parameters (FP32 numpy array of param_count() values) and the
+        loss; the network is not updated."""
+        g = np.empty(param_count(), dtype=np.float32)
+        loss = C.c_float()
+        _lib.check_mlp(self._lib.lbm_mlp_gradient(
+            self._m, X.data_ptr(), X.shape[1], T.data_ptr(), T.shape[1],
+            X.shape[0], g.ctypes.data, C.byref(loss)), self._m)
+        return g, loss.value
+
     def predict(self, X, nout):
         import torch
         Y = torch.empty((X.shape[0], nout), dtype=torch.float32,

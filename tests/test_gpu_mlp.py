@@ -49,6 +49,32 @@ def ref_grad(p, X, T):
     return g
 
 
+def ref_grad_bf16(p, X, T):
+    """ref_grad with the layer deltas rounded to BF16 where the training
+    kernel rounds them (the output delta for the weight gradients of the
+    last layer and for the products with W^T; the inner deltas after the
+    tanh derivative); the last layer's bias gradient takes the unrounded
+    output delta, as the kernel does."""
+    ws, bs = mlp.layout()
+    B, nout = T.shape
+    y, acts = ref_forward(p, X, nout)
+    g = np.zeros_like(p, dtype=np.float64)
+    d = np.zeros((B, 16))
+    d[:, :nout] = (2 * (y - T) / (B * nout)).astype(np.float32)
+    g[bs[3]] = d.sum(axis=0)
+    d = bf16(d.astype(np.float32)).astype(np.float64)
+    for l in range(3, -1, -1):
+        sl, (k, n) = ws[l]
+        g[sl] = (acts[l].astype(np.float64).T @ d).ravel()
+        if l == 0:
+            break
+        W = bf16(p[sl].reshape(k, n)).astype(np.float64)
+        d = (d @ W.T) * (1 - acts[l].astype(np.float64) ** 2)
+        d = bf16(d.astype(np.float32)).astype(np.float64)
+        g[bs[l - 1]] = d.sum(axis=0)
+    return g
+
+
 def _data(B=512, nin=8, nout=4, seed=0):
     rng = np.random.default_rng(seed)
     X = rng.uniform(-1, 1, (B, nin)).astype(np.float32)
@@ -104,3 +130,38 @@ def test_training_reduces_loss():
         net.close()
     assert last < 0.1 * first
     assert np.mean((pred - T) ** 2) < 0.2 * np.mean(T ** 2)
+
+
+def test_gradient_matches_reference_elementwise():
+    """The full-batch gradient of the training kernels, element by element,
+    against the NumPy model with the same BF16 rounding points.  What is
+    left is FP32 against FP64 accumulation and the rare layer delta whose
+    BF16 rounding flips with it: measured on GB300 (two seeds) at most
+    5e-5 (weights) and 1.9e-4 (biases) of each block's largest entry, norms
+    within 1.7e-4.  The bounds below leave a factor of three to six; the
+    model without the delta rounding (ref_grad) is 2.5e-4 to 5e-4 (weights)
+    and 1.8e-3 to 3.5e-3 (inner biases) away in norm, so the test also tells
+    the rounding points apart."""
+    torch = pytest.importorskip("torch")
+    X, T = _data(1000, seed=7)       # not a multiple of the 64-sample CTA
+    p = mlp.init_params(7)
+    net = mlp.Mlp(p)
+    try:
+        g, loss = net.gradient(torch.tensor(X, device="cuda"),
+                               torch.tensor(T, device="cuda"))
+        p_after = net.params()
+    finally:
+        net.close()
+    assert np.array_equal(p_after, p)          # no update
+    want, plain = ref_grad_bf16(p, X, T), ref_grad(p, X, T)
+    y, _ = ref_forward(p, X, T.shape[1])
+    assert loss == pytest.approx(np.mean((y - T) ** 2), rel=1e-4)
+    ws, bs = mlp.layout()
+    blocks = [(w, 3e-4, 1.5e-4) for w, _ in ws] + [(b, 6e-4, 6e-4) for b in bs]
+    for k, (sl, max_tol, norm_tol) in enumerate(blocks):
+        got, ref = g[sl].astype(np.float64), want[sl]
+        rel = np.abs(got - ref) / np.abs(ref).max()
+        assert rel.max() < max_tol, (k, rel.max())
+        assert np.linalg.norm(got - ref) < norm_tol * np.linalg.norm(ref), k
+        if k != 7:   # the output bias takes the unrounded delta in both models
+            assert np.linalg.norm(got - plain[sl]) > norm_tol * np.linalg.norm(ref), k
