@@ -735,7 +735,7 @@ lbm_status lbm_step(lbm_ctx *c, int nsteps)
     for (int k = 0; k < nsteps; ++k) {
         const int p = (int)(c->t & 1);
         if (c->force_model == 1)
-            CUDA_TRY(c, launch_step_pt(c->L, p, p, c->stream));
+            CUDA_TRY(c, launch_step_pt(c->L, p, p, c->stream, &c->maps));
         else
             CUDA_TRY(c, launch_step(c->L, p, p, c->stream, &c->maps));
         ++c->t;

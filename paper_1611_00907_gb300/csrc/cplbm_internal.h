@@ -167,7 +167,10 @@ int step_shapes(int *tx, int *ty, int max);
 
 // Baseline step with the pressure-tensor force (Eq. 5): FP32 (tile 32x32)
 // and FP64 (32x16), periodic lattices; pt_shape gives the tile it needs.
-cudaError_t launch_step_pt(const Lattice &L, int parity, int cur, cudaStream_t s);
+// maps: the TMA maps of that tile (interior and seam tiles take the TMA
+// path), or nullptr for the general path only.
+cudaError_t launch_step_pt(const Lattice &L, int parity, int cur, cudaStream_t s,
+                           const TmaMaps *maps = nullptr);
 void pt_shape(int prec, int *tx, int *ty);
 
 // Edge tiles the TMA tile paths may take (bit 0: periodic left and right,

@@ -18,8 +18,10 @@ CPLBM_PREC_DECL(f32)
 CPLBM_PREC_DECL(f32off)
 CPLBM_PREC_DECL(f16off)
 #undef CPLBM_PREC_DECL
-cudaError_t launch_pt_f64(const Lattice &L, int parity, int cur, cudaStream_t s);
-cudaError_t launch_pt_f32(const Lattice &L, int parity, int cur, cudaStream_t s);
+cudaError_t launch_pt_f64(const Lattice &L, int parity, int cur, cudaStream_t s,
+                          const TmaMaps *maps);
+cudaError_t launch_pt_f32(const Lattice &L, int parity, int cur, cudaStream_t s,
+                          const TmaMaps *maps);
 
 template <class T>
 static void fill_consts(Consts<T> &k, const Lattice &L)
@@ -88,13 +90,14 @@ void pt_shape(int prec, int *tx, int *ty)
     *ty = prec == P_F64 ? 16 : 32;
 }
 
-cudaError_t launch_step_pt(const Lattice &L, int parity, int cur, cudaStream_t s)
+cudaError_t launch_step_pt(const Lattice &L, int parity, int cur, cudaStream_t s,
+                           const TmaMaps *maps)
 {
     if (L.walls) return cudaErrorInvalidValue;
     if (L.precision == P_F64 && L.tx == 32 && L.ty == 16)
-        return launch_pt_f64(L, parity, cur, s);
+        return launch_pt_f64(L, parity, cur, s, maps);
     if (L.precision == P_F32 && L.tx == 32 && L.ty == 32)
-        return launch_pt_f32(L, parity, cur, s);
+        return launch_pt_f32(L, parity, cur, s, maps);
     return cudaErrorInvalidValue;
 }
 

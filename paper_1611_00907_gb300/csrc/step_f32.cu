@@ -12,9 +12,10 @@ cudaError_t launch_step_f32(const Lattice &L, int parity, int cur,
 }
 
 
-cudaError_t launch_pt_f32(const Lattice &L, int parity, int cur, cudaStream_t s)
+cudaError_t launch_pt_f32(const Lattice &L, int parity, int cur, cudaStream_t s,
+                          const TmaMaps *maps)
 {
-    return launch_pt_shape<SF32, 32, 32>(L, parity, cur, s);
+    return launch_pt_shape<SF32, 32, 32>(L, parity, cur, s, maps);
 }
 
 }  // namespace cplbm

@@ -883,7 +883,7 @@ __device__ __forceinline__ void combine_ring(real *s_rho, const real *s_ring)
 // Shared memory of a TMA tile: the staged populations in their storage
 // type, then density, partial sums / exchange slots and mu in the
 // arithmetic type.
-template <class S, int TX, int TY>
+template <class S, int TX, int TY, int NP = 1>
 struct TmaSmem {
     using real = typename S::real;
     using pop_t = typename S::pop_t;
@@ -895,14 +895,14 @@ struct TmaSmem {
     static constexpr int NRHO = (TY + 4) * RP;
     static constexpr int MP = TX + 2, MH = TY + 2;
     static constexpr int NRING = RingStage<real, TX, TY>::N;
-    static constexpr int NMU = MP * MH;
+    static constexpr int NMU = NP * MP * MH;  // mu, or (NP = 3) the tensor of Eq. 9
     static constexpr int NXCH = 2 * (STEP_THREADS / 32) * (TX + 2);
     // ring (and on seam tiles the staged population fix-ups after it), then
     // the exchange slots
     static constexpr int NFIXP = (SeamLists<TX, TY>::POP * sizeof(pop_t) + sizeof(real) - 1) /
                                  sizeof(real);
     static constexpr int NSHARE = NRING + NFIXP > NXCH ? NRING + NFIXP : NXCH;
-    static_assert(NMU >= SeamLists<TX, TY>::RHO, "density fix-ups staged in s_mu");
+    static_assert(MP * MH >= SeamLists<TX, TY>::RHO, "density fix-ups staged in s_mu");
     static constexpr size_t bar_offset =
         (PIN_BYTES + sizeof(real) * (NRHO + NSHARE + NMU) + 15) / 16 * 16;
     static constexpr size_t bytes = bar_offset + 16;
@@ -929,7 +929,9 @@ __device__ __forceinline__ T lap_w(const T (&w)[3][3])
     return (T(4) * axial + diag - T(20) * w[1][1]) * T(1.0 / 6.0);
 }
 
-template <class S, int TX, int TY, int NT, int PARITY, int EDGE>
+// PT: the baseline force of Eq. 5 (the pressure tensor of Eq. 9 in three
+// planes where the chemical potential would be; periodic lattices only).
+template <class S, int TX, int TY, int NT, int PARITY, int EDGE, bool PT = false>
 __device__ __forceinline__ bool step_tile_tma(const Lattice &L, int cur, int X0,
                                               int Y0, unsigned char *smem_raw,
                                               const TmaMaps &maps,
@@ -938,8 +940,9 @@ __device__ __forceinline__ bool step_tile_tma(const Lattice &L, int cur, int X0,
     using real = typename S::real;
     using pop_t = typename S::pop_t;
     using rho_t = typename S::rho_t;
-    using TS = TmaSmem<S, TX, TY>;
+    using TS = TmaSmem<S, TX, TY, PT ? 3 : 1>;
     static_assert(TX == 32, "lanes map to x");
+    static_assert(!PT || EDGE != 2, "the pressure-tensor force has no wall rule");
     constexpr int NW = NT / 32, PER = TY / NW;
     static_assert(PER * NW == TY && PER >= 2, "warps own whole row blocks");
     constexpr int RP = TS::RP, PP = TS::PP, PLANE = TS::PLANE, MP = TS::MP, MH = TS::MH;
@@ -1001,8 +1004,28 @@ __device__ __forceinline__ bool step_tile_tma(const Lattice &L, int cur, int X0,
     //    <-> r = Y0 - 1 + b; its density sits at staged (b + 1, a + 3).
     //    Columns 1..TX: lane a - 1, each warp a run of consecutive rows with
     //    a rolling 3 x 3 window; columns 0 and TX + 1 separately.  Solid
-    //    rows of wall tiles take the surface values (wall_mu).
-    {
+    //    rows of wall tiles take the surface values (wall_mu).  The
+    //    pressure-tensor baseline (PT) fills the three planes of Eq. 9
+    //    instead, in the arithmetic of pt_tile.
+    if constexpr (PT) {
+        const Consts<real> &K = consts<real>(L);
+        const real kappa = K.kappa;
+        const real ref = S::offset ? K.rho_ref : real(0);
+        constexpr int N = MP * MH;
+        for (int k = threadIdx.x; k < N; k += NT) {
+            const int a = k % MP, b = k / MP;
+            const int c = (b + 1) * RP + a + 3;
+            const real rho = s_rho[c] + ref;
+            real gx, gy;
+            grad9<real, RP>(s_rho, c, gx, gy);
+            const real lap = lap9<real, RP>(s_rho, c);
+            const real iso = p0_bulk(K.eos, rho) - kappa * rho * lap -
+                             real(0.5) * kappa * (gx * gx + gy * gy);
+            s_mu[k] = iso + kappa * gx * gx;
+            s_mu[N + k] = kappa * gx * gy;
+            s_mu[2 * N + k] = iso + kappa * gy * gy;
+        }
+    } else {
         const Consts<real> &K = consts<real>(L);
         const EosT<real> &eos = K.eos;
         const real kappa = K.kappa;
@@ -1109,10 +1132,23 @@ __device__ __forceinline__ bool step_tile_tma(const Lattice &L, int cur, int X0,
             const real drho = wr[1][1];
             const real rho = drho + rho_ref;
             real gmx, gmy, grx, gry;
-            grad_w(wm, gmx, gmy);
             grad_w(wr, grx, gry);
-            const real Fx = grx * real(1.0 / 3.0) - rho * gmx;
-            const real Fy = gry * real(1.0 / 3.0) - rho * gmy;
+            real Fx, Fy;
+            if constexpr (PT) {
+                // Eq. 5: F = -div(P) + grad(cs^2 rho), as step_tile
+                constexpr int N = MP * MH;
+                const int cm = (ly + 1) * MP + lx + 1;
+                real pxx_x, pxx_y, pxy_x, pxy_y, pyy_x, pyy_y;
+                grad9<real, MP>(s_mu, cm, pxx_x, pxx_y);
+                grad9<real, MP>(s_mu + N, cm, pxy_x, pxy_y);
+                grad9<real, MP>(s_mu + 2 * N, cm, pyy_x, pyy_y);
+                Fx = grx * real(1.0 / 3.0) - (pxx_x + pxy_y);
+                Fy = gry * real(1.0 / 3.0) - (pxy_x + pyy_y);
+            } else {
+                grad_w(wm, gmx, gmy);
+                Fx = grx * real(1.0 / 3.0) - rho * gmx;
+                Fy = gry * real(1.0 / 3.0) - rho * gmy;
+            }
             real fp[9];
             collide<real>(f, drho, rho, Fx, Fy, tau, omega, fp);
             // wall rows (halfway bounce-back, Sec. IV): what leaves into the
@@ -2013,17 +2049,37 @@ static cudaError_t launch_batch_t(const Lattice *d_lats, const WorkItem *d_items
 
 // ---------------------------------------------------------------------------
 // Baseline: the same step with the pressure-tensor force (Eq. 5, Eq. 9),
-// the form the method avoids, for measuring what avoiding it saves.  The
-// general tile paths only (no TMA), periodic lattices, FP32 and FP64.
+// the form the method avoids, for measuring what avoiding it saves.
+// Periodic lattices, FP32 and FP64, on the same tile paths as the step
+// kernel: TMA for interior and periodic-seam tiles (32-wide shapes), the
+// general path for the rest.
 // ---------------------------------------------------------------------------
 template <class S, int TX, int TY, int NT, int PARITY>
 __global__ void __launch_bounds__(NT)
-    step_pt_kernel(const Lattice L, int cur, int xlo, int xhi, int ylo, int yhi)
+    step_pt_kernel(const Lattice L, int cur, int seams, const __grid_constant__ TmaMaps maps)
 {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     const int bx = PARITY ? gridDim.x - 1 - blockIdx.x : blockIdx.x;  // as step_kernel
     const int by = PARITY ? gridDim.y - 1 - blockIdx.y : blockIdx.y;
-    const bool interior = bx >= xlo && bx <= xhi && by >= ylo && by <= yhi;
+    const int kind = tile_kind(L, TX, TY, bx, by, seams);
+    const bool interior = kind == TILE_INTERIOR;
+    if constexpr (HasTma<S, TX, TY, NT>::value) {
+        if (kind != TILE_GENERAL && maps.valid) {
+            __shared__ __align__(8) unsigned long long bar[2];
+            if (threadIdx.x == 0) {
+                mbar_init(&bar[0], 1);
+                mbar_init(&bar[1], 1);
+            }
+            __syncthreads();
+            if (interior)
+                step_tile_tma<S, TX, TY, NT, PARITY, 0, true>(L, cur, bx * TX, by * TY,
+                                                              smem_raw, maps, bar, 0);
+            else
+                step_tile_tma<S, TX, TY, NT, PARITY, 1, true>(L, cur, bx * TX, by * TY,
+                                                              smem_raw, maps, bar, 0);
+            return;
+        }
+    }
     if (interior)
         step_tile<S, TX, TY, NT, PARITY, true, true>(L, cur, bx * TX, by * TY,
                                                      smem_raw);
@@ -2034,12 +2090,16 @@ __global__ void __launch_bounds__(NT)
 
 template <class S, int TX, int TY>
 static cudaError_t launch_pt_shape(const Lattice &L, int parity, int cur,
-                                   cudaStream_t s)
+                                   cudaStream_t s, const TmaMaps *maps)
 {
     using real = typename S::real;
     using SM = StepSmem<real, TX, TY>;
     constexpr int NT = STEP_THREADS;
-    const size_t smem = SM::bytes + 2 * sizeof(real) * SM::WM * SM::HM;
+    size_t smem = SM::bytes + 2 * sizeof(real) * SM::WM * SM::HM;
+    if constexpr (HasTma<S, TX, TY, NT>::value)
+        if (TmaSmem<S, TX, TY, 3>::bytes > smem) smem = TmaSmem<S, TX, TY, 3>::bytes;
+    TmaMaps m{};
+    if (maps && maps->valid && maps->tx == TX && maps->ty == TY) m = *maps;
     auto k0 = step_pt_kernel<S, TX, TY, NT, 0>;
     auto k1 = step_pt_kernel<S, TX, TY, NT, 1>;
     static int configured = -1;
@@ -2056,12 +2116,12 @@ static cudaError_t launch_pt_shape(const Lattice &L, int parity, int cur,
         configured = dev;
     }
     const int ntx = (L.nx + TX - 1) / TX, nty = (L.nyf + TY - 1) / TY;
-    const int nfx = L.nx / TX, nfy = L.nyf / TY;
+    const int seams = HasTma<S, TX, TY, NT>::value ? seam_bits(L, TX, TY) : 0;
     dim3 grid(ntx, nty);
     if (parity == 0)
-        k0<<<grid, NT, smem, s>>>(L, cur, 1, nfx - 2, 1, nfy - 2);
+        k0<<<grid, NT, smem, s>>>(L, cur, seams, m);
     else
-        k1<<<grid, NT, smem, s>>>(L, cur, 1, nfx - 2, 1, nfy - 2);
+        k1<<<grid, NT, smem, s>>>(L, cur, seams, m);
     return cudaGetLastError();
 }
 

@@ -1,5 +1,7 @@
 """The pressure-tensor baseline (Eq. 5 with Eq. 9) on the GPU against the
-oracle's pressure-tensor step, and its argument checks."""
+oracle's pressure-tensor step, and its argument checks.  Interior and
+periodic-seam tiles take the TMA tile path, as in the chemical-potential
+step; 224 x 165 and 96 x 96 have both (and general tiles in the first)."""
 import numpy as np
 import pytest
 
@@ -24,7 +26,7 @@ def _rel(a, b):
     return np.abs(a - b).max() / np.abs(b).max()
 
 
-@pytest.mark.parametrize("size", [(70, 21), (224, 165), (5, 5)])
+@pytest.mark.parametrize("size", [(70, 21), (224, 165), (96, 96), (5, 5)])
 @pytest.mark.parametrize("steps", [1, 2, 200])
 def test_pressure_tensor_step_matches_oracle_fp64(size, steps, oracle_threads):
     sim, ref, rho = _case(*size, "f64")
@@ -37,13 +39,22 @@ def test_pressure_tensor_step_matches_oracle_fp64(size, steps, oracle_threads):
             assert _rel(f[i], ref.f[i]) < 1e-12, i
 
 
-def test_pressure_tensor_fp32(oracle_threads):
-    sim, ref, rho = _case(224, 165, "f32")
-    with sim:
-        sim.set_force_model("pressure_tensor")
-        sim.init(rho).step(50)
-        ref.init_equilibrium(rho).step_pressure_tensor(50)
-        assert _rel(sim.moments()["rho"], ref.moments()["rho"]) < 1e-5
+@pytest.mark.parametrize("size", [(224, 165), (96, 96)])
+def test_pressure_tensor_fp32(size, oracle_threads, monkeypatch):
+    # against the oracle, and against the same lattice on the general path
+    runs = []
+    for no_tma in (False, True):
+        if no_tma:
+            monkeypatch.setenv("CPLBM_NO_TMA", "1")
+        sim, ref, rho = _case(*size, "f32")
+        with sim:
+            sim.set_force_model("pressure_tensor")
+            sim.init(rho).step(50)
+            runs.append(sim.moments()["rho"])
+    ref.init_equilibrium(rho).step_pressure_tensor(50)
+    want = ref.moments()["rho"]
+    assert _rel(runs[0], want) < 1e-5
+    assert _rel(runs[0], runs[1]) < 1e-5
 
 
 def test_pressure_tensor_arguments():
