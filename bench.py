@@ -583,8 +583,11 @@ def measure_warmstart(full):
     t_train = time.perf_counter() - t0
     try:
         with torch.cuda.stream(stream):
+            # convergence: the drop has settled (contact angle and bulk
+            # densities steady between checks), read every 500 (250) steps
             r = ws.compare(model, ws.sample_cases(neval, seed=99), nx, ny,
-                           max_steps, check_every=200, tol=1e-5, stream=stream)
+                           max_steps, check_every=500 if full else 250,
+                           stream=stream, settle=ws.SETTLE)
     finally:
         model.close()
     r.update(training_runs=ntrain, training_kept=len(cases),

@@ -376,11 +376,16 @@ class Batch:
                                                    1 if active else 0))
         return self
 
-    def moments(self, index):
+    def moments(self, index, fields=("rho", "vx", "vy", "mu")):
+        """dict of the requested fields among rho, vx, vy, mu of lattice
+        `index` (numpy [ny, nx]); only those are computed and copied."""
         d = self.specs[index]
         shape = (int(d["ny"]), int(d["nx"]))
-        out = {k: np.empty(shape) for k in ("rho", "vx", "vy", "mu")}
-        ptr = [out[k].ctypes.data for k in ("rho", "vx", "vy", "mu")]
+        names = ("rho", "vx", "vy", "mu")
+        if any(k not in names for k in fields):
+            raise ValueError("fields must be among %s" % (names,))
+        out = {k: np.empty(shape) for k in names if k in fields}
+        ptr = [out[k].ctypes.data if k in out else None for k in names]
         self._check(self._lib.lbm_batch_moments(self._b, int(index), *ptr, 0))
         return out
 

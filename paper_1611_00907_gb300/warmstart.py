@@ -11,6 +11,7 @@ densities.  The plain cold start stays the fallback and the measure of
 the warm start's error: both are run to convergence and their
 observables compared.
 """
+import json
 import math
 
 import numpy as np
@@ -105,19 +106,48 @@ def warm_field(case, pred, nx, ny):
     return inputs.tanh_profile(d, rl, rv, W)
 
 
+# A settled drop (the convergence test of the sweep comparison): between two
+# checks its contact angle moves by less than theta_deg and its bulk
+# densities by less than the relative rho_l, rho_v, `repeats` checks in a
+# row.  A film over the wall (0 degrees) or a drop that left it (180) counts
+# on its densities alone.
+SETTLE = dict(theta_deg=0.05, rho_l=1e-5, rho_v=1e-4, repeats=2)
+
+
+def _settled(prev, cur, settle):
+    if prev is None:
+        return False
+    th0, th1 = prev["theta"], cur["theta"]
+    if np.isfinite(th0) and np.isfinite(th1):
+        if abs(th1 - th0) >= settle["theta_deg"]:
+            return False
+    elif np.isfinite(th0) != np.isfinite(th1):
+        return False
+    return (abs(cur["rho_l"] / prev["rho_l"] - 1) < settle["rho_l"] and
+            abs(cur["rho_v"] / prev["rho_v"] - 1) < settle["rho_v"])
+
+
 def run_batch(cases, fields, nx, ny, max_steps, check_every=200, tol=1e-6,
-              precision="f32", stream=None):
-    """Run every case from its field until max |rho change| over
-    check_every steps (even) stays below tol * rho_l, or max_steps; a case
-    that has converged (or gone non-finite) leaves the batched launch.
-    Returns the per-case convergence step (max_steps if never), the final
-    fields, the device milliseconds until the last case converged, and the
-    steps run."""
+              precision="f32", stream=None, settle=None):
+    """Run every case from its field until it has converged, or max_steps;
+    a case that has converged (or gone non-finite) leaves the batched launch.
+    Convergence: with settle None, max |rho change| over check_every steps
+    (even) below tol * rho_l (the library's FP64 reduction); with a settle
+    dict (SETTLE), the drop has settled: its contact angle and bulk
+    densities, measured on the density read back every check_every steps,
+    stop moving (_settled).  Returns the per-case convergence step (max_steps
+    if never), the final fields, the device milliseconds of stepping until
+    the last case converged (the host's checks between the blocks of steps
+    not included), and the steps run."""
     import torch
     specs = [_spec(c, nx, ny) for c in cases]
     conv = np.full(len(cases), max_steps, dtype=np.int64)
     done = np.zeros(len(cases), dtype=bool)
+    prev = [None] * len(cases)
+    calm = np.zeros(len(cases), dtype=np.int64)
     steps = 0
+    ms = 0.0
+    st = stream if stream else torch.cuda.current_stream()
     ev0 = torch.cuda.Event(enable_timing=True)
     ev1 = torch.cuda.Event(enable_timing=True)
     with Batch(specs, precision=precision,
@@ -127,9 +157,12 @@ def run_batch(cases, fields, nx, ny, max_steps, check_every=200, tol=1e-6,
         for k in range(len(cases)):
             b.reduce(k)
         torch.cuda.synchronize()
-        ev0.record(stream if stream else torch.cuda.current_stream())
         while steps < max_steps and not done.all():
+            ev0.record(st)
             b.step(check_every)
+            ev1.record(st)
+            ev1.synchronize()
+            ms += ev0.elapsed_time(ev1)
             steps += check_every
             for k in range(len(cases)):
                 if done[k]:
@@ -140,14 +173,18 @@ def run_batch(cases, fields, nx, ny, max_steps, check_every=200, tol=1e-6,
                     done[k] = True            # non-finite: never converges
                     b.set_active(k, False)
                     continue
-                if d < tol * cases[k]["rho_l"]:
+                if settle is None:
+                    ok = d < tol * cases[k]["rho_l"]
+                else:
+                    m = obs.measure(b.moments(k, fields=("rho",))["rho"])
+                    calm[k] = calm[k] + 1 if _settled(prev[k], m, settle) else 0
+                    prev[k] = m
+                    ok = calm[k] >= settle["repeats"]
+                if ok:
                     done[k] = True
                     conv[k] = steps
                     b.set_active(k, False)
-        ev1.record(stream if stream else torch.cuda.current_stream())
-        torch.cuda.synchronize()
-        ms = ev0.elapsed_time(ev1)
-        final = [b.moments(k)["rho"] for k in range(len(cases))]
+        final = [b.moments(k, fields=("rho",))["rho"] for k in range(len(cases))]
     return conv, final, ms, steps
 
 
@@ -199,17 +236,17 @@ def _stat(values, fn):
 
 
 def compare(model, cases, nx, ny, max_steps, check_every=200, tol=1e-6,
-            stream=None):
-    """Cold and warm starts of the same cases run to convergence: step
-    counts, device time to the last converged case, and, over the cases
-    both starts converged on, the warm start's observable errors against
-    the cold start's result."""
+            stream=None, settle=None):
+    """Cold and warm starts of the same cases run to convergence (run_batch's
+    test, by tol or by settle): step counts, device time of stepping to the
+    last converged case, and, over the cases both starts converged on, the
+    warm start's observable errors against the cold start's result."""
     preds = model.predict(cases)
     cold = run_batch(cases, [cold_field(c, nx, ny) for c in cases], nx, ny,
-                     max_steps, check_every, tol, stream=stream)
+                     max_steps, check_every, tol, stream=stream, settle=settle)
     warm = run_batch(cases, [warm_field(c, p, nx, ny) for c, p in
                              zip(cases, preds)], nx, ny, max_steps,
-                     check_every, tol, stream=stream)
+                     check_every, tol, stream=stream, settle=settle)
     both = (cold[0] < max_steps) & (warm[0] < max_steps)
     err = {"rho_l": [], "rho_v": [], "theta": []}
     for k, (rc, rw) in enumerate(zip(cold[1], warm[1])):
@@ -226,14 +263,22 @@ def compare(model, cases, nx, ny, max_steps, check_every=200, tol=1e-6,
             if np.isfinite(t):
                 pred_err.append(abs(p["theta"] - t))
     return dict(
-        cases=len(cases), nx=nx, ny=ny, tol=tol, check_every=check_every,
+        cases=len(cases), nx=nx, ny=ny, check_every=check_every,
+        convergence=("settled drop: " + json.dumps(settle)) if settle else
+        "max |rho change| over check_every steps < %g rho_l" % tol,
         max_steps=max_steps,
+        capped_cold=int((cold[0] >= max_steps).sum()),
+        capped_warm=int((warm[0] >= max_steps).sum()),
         cold_steps_mean=float(cold[0].mean()), warm_steps_mean=float(warm[0].mean()),
         both_converged=int(both.sum()),
         cold_steps_median_both=float(np.median(cold[0][both])) if both.any() else None,
         warm_steps_median_both=float(np.median(warm[0][both])) if both.any() else None,
         step_ratio_median_both=float(np.median(warm[0][both] / cold[0][both]))
         if both.any() else None,
+        # lattice-steps to convergence summed over the cases both starts
+        # converged on: the work the warm start saves there
+        cold_steps_sum_both=int(cold[0][both].sum()),
+        warm_steps_sum_both=int(warm[0][both].sum()),
         cold_ms=cold[2], warm_ms=warm[2],
         cold_converged=float((cold[0] < max_steps).mean()),
         warm_converged=float((warm[0] < max_steps).mean()),
