@@ -289,7 +289,7 @@ def batch_specs(which):
 
 
 def measure_batch(which, precision, steps, warmup, sequential=True):
-    """One persistent launch per step over every lattice (graph-replayed),
+    """One launch per step over every lattice's tiles (graph-replayed),
     and the same lattices stepped one by one, each its own launch."""
     import math
     import torch
@@ -305,6 +305,7 @@ def measure_batch(which, precision, steps, warmup, sequential=True):
             for k, f in enumerate(fields):
                 b.init(k, f)
             out["tile"] = list(b.autotune(6))
+            out["items_per_cta"] = b.items_per_cta
             b.step(warmup)
             torch.cuda.synchronize()
             t0 = torch.cuda.Event(enable_timing=True)

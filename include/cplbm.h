@@ -178,7 +178,7 @@ lbm_status lbm_eos_critical(int eos, double a, double b, double R,
 /* ------------------------------------------------------------------------
  * Batches: many independent lattices (different sizes, EOS, temperatures,
  * relaxation times, wall chemical potentials; one precision) advanced
- * together by one persistent kernel launch per step over all their tiles,
+ * together by one kernel launch per step over all their tiles,
  * with blocks of 16 steps replayed from a captured CUDA graph.  Every
  * lattice follows the same update as lbm_step.  Lattice i is addressed by
  * its index in the array given to lbm_batch_create.
@@ -219,11 +219,20 @@ lbm_status lbm_batch_moments(lbm_batch *b, int index, double *rho, double *vx,
 lbm_status lbm_batch_populations(lbm_batch *b, int index, double *f,
                                  int on_device);
 lbm_status lbm_batch_reduce(lbm_batch *b, int index, double out[4]);
-/* Tile shape of the batched kernel (as lbm_set_tile; default 32x32, the
- * width its TMA path takes), or the fastest one measured over nsteps steps
- * with the state restored afterwards. */
+/* Tile shape of the batched kernel (as lbm_set_tile; default 32x32), or
+ * the fastest configuration measured over nsteps steps (every tile shape
+ * with 1, 2 and 4 work items per CTA, see lbm_batch_schedule) with the
+ * state restored afterwards; *tx, *ty receive the shape kept. */
 lbm_status lbm_batch_set_tile(lbm_batch *b, int tx, int ty);
 lbm_status lbm_batch_autotune(lbm_batch *b, int nsteps, int *tx, int *ty);
+/* Work items (tiles) per CTA of the batched kernel: each CTA takes that
+ * many consecutive tiles of the work list, which mostly belong to one
+ * lattice, so its descriptor is loaded once for them; more items per CTA
+ * save that set-up, fewer balance the end of a step better.  Speed only,
+ * results are unchanged.  items_per_cta in 1 .. 64 sets it (default 1),
+ * <= 0 leaves it; *current (may be NULL) receives the value in use.
+ * LBM_ERR_ARG above 64. */
+lbm_status lbm_batch_schedule(lbm_batch *b, int items_per_cta, int *current);
 /* Lattice count, total nodes, steps taken, tile shape (any may be NULL). */
 lbm_status lbm_batch_info(const lbm_batch *b, int *count, long long *nodes,
                           long long *steps, int *tx, int *ty);

@@ -288,8 +288,8 @@ class Simulation:
 
 
 class Batch:
-    """Many independent lattices advanced together (one persistent kernel
-    launch per step, blocks of steps replayed from a CUDA graph).
+    """Many independent lattices advanced together (one kernel launch per
+    step over all their tiles, blocks of steps replayed from a CUDA graph).
 
     instances: list of dicts with keys nx, ny and optionally walls, tau,
     kappa, rho_ref, eos, a, b, R, Tr, omega, mu_bottom, top_mode, mu_top
@@ -404,6 +404,17 @@ class Batch:
     def set_tile(self, tx, ty):
         self._check(self._lib.lbm_batch_set_tile(self._b, int(tx), int(ty)))
         return self
+
+    @property
+    def items_per_cta(self):
+        """Work items (tiles) each CTA of the batched kernel takes."""
+        cur = C.c_int()
+        self._check(self._lib.lbm_batch_schedule(self._b, 0, C.byref(cur)))
+        return cur.value
+
+    @items_per_cta.setter
+    def items_per_cta(self, k):
+        self._check(self._lib.lbm_batch_schedule(self._b, int(k), None))
 
     def autotune(self, nsteps=10):
         tx, ty = C.c_int(), C.c_int()

@@ -88,6 +88,7 @@ SIGNATURES = {
     "lbm_batch_set_tile": ([_ctx, C.c_int, C.c_int], C.c_int),
     "lbm_batch_autotune": ([_ctx, C.c_int, C.POINTER(C.c_int),
                             C.POINTER(C.c_int)], C.c_int),
+    "lbm_batch_schedule": ([_ctx, C.c_int, C.POINTER(C.c_int)], C.c_int),
     "lbm_batch_info": ([_ctx, C.POINTER(C.c_int), C.POINTER(C.c_longlong),
                         C.POINTER(C.c_longlong), C.POINTER(C.c_int),
                         C.POINTER(C.c_int)], C.c_int),

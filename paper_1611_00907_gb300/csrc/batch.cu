@@ -1,9 +1,9 @@
 // Batched lattices (lbm_batch_* in include/cplbm.h): many independent
 // lattices of different sizes, EOS, temperatures, relaxation times and wall
-// chemical potentials advanced together, one persistent kernel launch per
-// step over a work list of tiles, with blocks of steps replayed from a
-// captured CUDA graph.  Each lattice is a full context (its own device
-// state), so the per-lattice calls (moments, reductions) are the
+// chemical potentials advanced together, one kernel launch per step over a
+// work list of tiles (a few consecutive tiles per CTA), with blocks of steps
+// replayed from a captured CUDA graph.  Each lattice is a full context (its
+// own device state), so the per-lattice calls (moments, reductions) are the
 // single-lattice ones.
 #include <cmath>
 #include <cstdarg>
@@ -26,7 +26,7 @@ struct lbm_batch {
     Lattice *d_lats = nullptr;
     WorkItem *d_items = nullptr;
     TmaMaps *d_maps = nullptr;  // per-lattice tensor maps, or null (no TMA)
-    int *d_counter = nullptr;   // work-item counters of the batched kernel
+    int per_cta = 1;            // work items per CTA of the batched kernel
     int n_items = 0;
     long long t = 0;
     long long nodes = 0;
@@ -120,8 +120,6 @@ lbm_status rebuild(lbm_batch *b)
     b->d_lats = nullptr;
     b->d_items = nullptr;
     b->d_maps = nullptr;
-    if (!b->d_counter) BCUDA(b, dev_alloc((void **)&b->d_counter, 2 * sizeof(int)));
-    BCUDA(b, cudaMemset(b->d_counter, 0, 2 * sizeof(int)));
     if (any_maps) {
         BCUDA(b, dev_alloc((void **)&b->d_maps, maps.size() * sizeof(TmaMaps)));
         BCUDA(b, cudaMemcpy(b->d_maps, maps.data(), maps.size() * sizeof(TmaMaps),
@@ -140,9 +138,8 @@ lbm_status rebuild(lbm_batch *b)
 lbm_status launch_one(lbm_batch *b)
 {
     const int p = (int)(b->t & 1);
-    BCUDA(b, launch_step_batch(b->d_lats, b->d_items, b->d_maps, b->d_counter,
-                               b->n_items, p, p,
-                               b->precision, b->tx, b->ty, 0, b->stream));
+    BCUDA(b, launch_step_batch(b->d_lats, b->d_items, b->d_maps, b->n_items, p, p,
+                               b->precision, b->tx, b->ty, b->per_cta, b->stream));
     ++b->t;
     return LBM_OK;
 }
@@ -154,9 +151,8 @@ lbm_status ensure_graph(lbm_batch *b)
     BCUDA(b, cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal));
     cudaError_t e = cudaSuccess;
     for (int k = 0; k < GRAPH_STEPS && e == cudaSuccess; ++k)
-        e = launch_step_batch(b->d_lats, b->d_items, b->d_maps, b->d_counter,
-                              b->n_items, k & 1, k & 1,
-                              b->precision, b->tx, b->ty, 0, b->stream);
+        e = launch_step_batch(b->d_lats, b->d_items, b->d_maps, b->n_items, k & 1, k & 1,
+                              b->precision, b->tx, b->ty, b->per_cta, b->stream);
     cudaError_t e2 = cudaStreamEndCapture(b->stream, &g);
     if (e != cudaSuccess || e2 != cudaSuccess) {
         if (g) cudaGraphDestroy(g);
@@ -363,6 +359,20 @@ lbm_status lbm_batch_set_tile(lbm_batch *b, int tx, int ty)
     return rebuild(b);
 }
 
+lbm_status lbm_batch_schedule(lbm_batch *b, int items_per_cta, int *current)
+{
+    if (!b) return LBM_ERR_ARG;
+    if (items_per_cta > 64)
+        return bfail(b, LBM_ERR_ARG, "items per CTA must be 1 .. 64 (got %d)",
+                     items_per_cta);
+    if (items_per_cta > 0 && items_per_cta != b->per_cta) {
+        b->per_cta = items_per_cta;
+        drop_graph(b);  // the captured launches carry the old grid
+    }
+    if (current) *current = b->per_cta;
+    return LBM_OK;
+}
+
 lbm_status lbm_batch_autotune(lbm_batch *b, int nsteps, int *tx, int *ty)
 {
     if (!b) return LBM_ERR_ARG;
@@ -390,9 +400,12 @@ lbm_status lbm_batch_autotune(lbm_batch *b, int nsteps, int *tx, int *ty)
     if (st == LBM_OK && (cudaEventCreate(&e0) != cudaSuccess ||
                          cudaEventCreate(&e1) != cudaSuccess))
         st = bfail(b, LBM_ERR_CUDA, "event create");
+    // configurations: every tile shape with 1, 2 or 4 work items per CTA
+    const int per[3] = {1, 2, 4};
     auto restore = [&](int k) -> lbm_status {
-        b->tx = sx[k];
-        b->ty = sy[k];
+        b->tx = sx[k / 3];
+        b->ty = sy[k / 3];
+        b->per_cta = per[k % 3];
         lbm_status s2 = rebuild(b);
         for (size_t i = 0; i < b->inst.size() && s2 == LBM_OK; ++i)
             s2 = ctx_snapshot(b->inst[i], snaps[i], false);
@@ -400,8 +413,8 @@ lbm_status lbm_batch_autotune(lbm_batch *b, int nsteps, int *tx, int *ty)
         for (size_t i = 0; i < b->inst.size(); ++i) b->inst[i]->t = tsave[i];
         return s2;
     };
-    for (int k = 0; k < n && st == LBM_OK; ++k) {
-        if (!step_shape_supported(b->precision, sx[k], sy[k])) continue;
+    for (int k = 0; k < 3 * n && st == LBM_OK; ++k) {
+        if (!step_shape_supported(b->precision, sx[k / 3], sy[k / 3])) continue;
         st = restore(k);
         for (int w = 0; w < 2 && st == LBM_OK; ++w) st = launch_one(b);
         if (st != LBM_OK) break;
@@ -455,7 +468,6 @@ void lbm_batch_destroy(lbm_batch *b)
     dev_free(b->d_lats);
     dev_free(b->d_items);
     dev_free(b->d_maps);
-    dev_free(b->d_counter);
     if (b->own_stream) cudaStreamDestroy(b->stream);
     delete b;
 }

@@ -222,23 +222,22 @@ __host__ __device__ inline int tile_kind(const Lattice &L, int tx, int ty, int b
     return sx && sy ? TILE_SEAM : TILE_GENERAL;
 }
 
-// A tile of one lattice of a batch: the persistent batched step walks a
-// list of these (step.cu).
+// A tile of one lattice of a batch: the batched step walks a list of these
+// (step.cu).
 struct WorkItem {
     int inst;      // index into the batch's Lattice array
     int bx, by;    // tile position
     int kind;      // tile_kind of the tile
 };
-// One step of every lattice of a batch in one launch: gridDim CTAs stride
-// over the work list.  All lattices share precision, tile shape and step
-// parity.  grid <= 0 picks one CTA per SM slot (occupancy-limited).
-// d_maps: per-lattice tensor maps in device memory (interior tiles of
-// 32-wide shapes take the TMA path), or nullptr.  d_counter: two ints, zero
-// before the first launch; the launches keep them so from then on.
+// One step of every lattice of a batch in one launch: each CTA takes
+// per_cta consecutive items of the work list.  All lattices share
+// precision, tile shape and step parity.  d_maps: per-lattice tensor maps
+// in device memory (interior and edge tiles of the shapes with a TMA path),
+// or nullptr.
 cudaError_t launch_step_batch(const Lattice *d_lats, const WorkItem *d_items,
-                              const TmaMaps *d_maps, int *d_counter, int n_items,
-                              int parity, int cur, int precision, int tx, int ty,
-                              int grid, cudaStream_t s);
+                              const TmaMaps *d_maps, int n_items, int parity,
+                              int cur, int precision, int tx, int ty, int per_cta,
+                              cudaStream_t s);
 
 // fields.cu
 // Equilibrium initial state from double fields [ny][nx] on the device:

@@ -9,10 +9,9 @@ namespace cplbm {
                                   cudaStream_t s, const TmaMaps *maps);        \
     cudaError_t launch_batch_##tag(const Lattice *d_lats,                      \
                                    const WorkItem *d_items,                   \
-                                   const TmaMaps *d_maps, int *d_counter,     \
-                                   int n_items,                               \
+                                   const TmaMaps *d_maps, int n_items,        \
                                    int parity, int cur, int tx, int ty,       \
-                                   int grid, cudaStream_t s);
+                                   int per_cta, cudaStream_t s);
 CPLBM_PREC_DECL(f64)
 CPLBM_PREC_DECL(f32)
 CPLBM_PREC_DECL(f32off)
@@ -102,18 +101,17 @@ cudaError_t launch_step_pt(const Lattice &L, int parity, int cur, cudaStream_t s
 }
 
 cudaError_t launch_step_batch(const Lattice *d_lats, const WorkItem *d_items,
-                              const TmaMaps *d_maps, int *d_counter, int n_items,
-                              int parity,
-                              int cur, int precision, int tx, int ty, int grid,
+                              const TmaMaps *d_maps, int n_items, int parity,
+                              int cur, int precision, int tx, int ty, int per_cta,
                               cudaStream_t s)
 {
     switch (precision) {
-    case P_F64: return launch_batch_f64(d_lats, d_items, d_maps, d_counter, n_items, parity, cur, tx, ty, grid, s);
-    case P_F32: return launch_batch_f32(d_lats, d_items, d_maps, d_counter, n_items, parity, cur, tx, ty, grid, s);
+    case P_F64: return launch_batch_f64(d_lats, d_items, d_maps, n_items, parity, cur, tx, ty, per_cta, s);
+    case P_F32: return launch_batch_f32(d_lats, d_items, d_maps, n_items, parity, cur, tx, ty, per_cta, s);
     case P_F32_OFF:
-        return launch_batch_f32off(d_lats, d_items, d_maps, d_counter, n_items, parity, cur, tx, ty, grid, s);
+        return launch_batch_f32off(d_lats, d_items, d_maps, n_items, parity, cur, tx, ty, per_cta, s);
     case P_F16_OFF:
-        return launch_batch_f16off(d_lats, d_items, d_maps, d_counter, n_items, parity, cur, tx, ty, grid, s);
+        return launch_batch_f16off(d_lats, d_items, d_maps, n_items, parity, cur, tx, ty, per_cta, s);
     }
     return cudaErrorInvalidValue;
 }

@@ -1886,9 +1886,13 @@ static cudaError_t launch_shape(const Lattice &L, int parity, int cur,
 
 // ---------------------------------------------------------------------------
 // Batched step: many independent lattices of different sizes and physics in
-// one persistent launch.  Each CTA takes work items blockIdx.x,
-// blockIdx.x + gridDim.x, ... and runs the general or interior tile path on
-// that item's lattice, whose descriptor it first copies to shared memory.
+// one launch.  Each CTA takes `per_cta` consecutive work items (tiles of the
+// work list, in list order, backwards on odd steps as step_kernel walks its
+// grid); the hardware hands out the CTAs as others finish, so there is no
+// work counter and no per-item wait on one.  Consecutive items mostly belong
+// to one lattice: its descriptor is copied to shared memory and its tensor
+// maps are fenced once per CTA, and per_cta (lbm_batch_autotune) trades that
+// saving against the balance of the last CTAs.
 // ---------------------------------------------------------------------------
 template <class S, int TX, int TY, int NT, int PARITY>
 __global__ void __launch_bounds__(NT, HasTmaPair<S, TX, TY, NT>::value
@@ -1896,78 +1900,72 @@ __global__ void __launch_bounds__(NT, HasTmaPair<S, TX, TY, NT>::value
                                           : (sizeof(typename S::real) == 8 ? 2 : 4))
     step_batch_kernel(const Lattice *__restrict__ lats,
                       const WorkItem *__restrict__ items, int n_items, int cur,
-                      const TmaMaps *__restrict__ maps, int *counter)
+                      const TmaMaps *__restrict__ maps, int per_cta)
 {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     __shared__ Lattice sL;
-    __shared__ int s_w;
-    // Work items are taken from counter[PARITY] as CTAs become free (a fixed
-    // share per CTA keeps the CTAs of an SM in lockstep, loading and
-    // computing all at once); this launch zeroes the other counter for the
-    // next step, which the stream order keeps from running before it.
-    if (blockIdx.x == 0 && threadIdx.x == 0) counter[PARITY ^ 1] = 0;
-    // TMA interior tiles (maps != nullptr: per-lattice tensor maps in global
-    // memory): the two mbarriers live outside the dynamic shared memory that
-    // general-path items reuse, are initialised once, and every TMA tile
-    // completes one phase of each.
     __shared__ __align__(8) unsigned long long bar[2];
-    bool tma = (HasTma<S, TX, TY, NT>::value || HasTmaPair<S, TX, TY, NT>::value) &&
-               maps != nullptr;
-    unsigned phase = 0;
-    if (tma) {
-        if (threadIdx.x == 0) {
-            mbar_init(&bar[0], 1);
-            mbar_init(&bar[1], 1);
-        }
-        __syncthreads();
-    }
     static_assert(sizeof(Lattice) % sizeof(int) == 0, "descriptor copy");
-    int fenced = -1;  // lattice whose maps this CTA has fenced
-    for (;;) {
-        if (threadIdx.x == 0) s_w = atomicAdd(&counter[PARITY], 1);
-        __syncthreads();
-        const int w = s_w;
-        if (w >= n_items) break;
-        // odd steps take the work list backwards (see step_kernel)
+    constexpr bool kTma = HasTma<S, TX, TY, NT>::value || HasTmaPair<S, TX, TY, NT>::value;
+    int inst = -1;         // lattice whose descriptor sL holds
+    int fenced = -1;       // lattice whose maps this CTA has fenced
+    bool bars = false;     // mbarriers initialised
+    unsigned phase = 0;    // next phase of the mbarriers
+    bool tma_ok = true;    // a wait that gave up sends the rest to the general path
+    const int w0 = (int)blockIdx.x * per_cta;
+    for (int j = 0; j < per_cta && w0 + j < n_items; ++j) {
+        const int w = w0 + j;
         const WorkItem it = items[PARITY ? n_items - 1 - w : w];
-        {
+        const TmaMaps *m = maps ? &maps[it.inst] : nullptr;
+        bool use_tma = false;
+        if constexpr (kTma) {
+            use_tma = tma_ok && m && it.kind != TILE_GENERAL && m->valid &&
+                      m->tx == TX && m->ty == TY;
+            if (use_tma && threadIdx.x == 0) {
+                if (!bars) {
+                    mbar_init(&bar[0], 1);
+                    mbar_init(&bar[1], 1);
+                }
+                if (fenced != it.inst) {
+                    // the maps were written by the host: make the tensor-map
+                    // proxy see the current contents of the two this step
+                    // reads (while the other threads copy the descriptor)
+                    tensormap_acquire(&m->pops);
+                    tensormap_acquire(&m->rho[cur]);
+                }
+            }
+            if (use_tma) {
+                bars = true;
+                fenced = it.inst;
+            }
+        }
+        if (it.inst != inst) {
             const int *src = reinterpret_cast<const int *>(lats + it.inst);
             int *dst = reinterpret_cast<int *>(&sL);
-            for (int q = threadIdx.x; q < (int)(sizeof(Lattice) / sizeof(int));
-                 q += NT)
+            for (int q = threadIdx.x; q < (int)(sizeof(Lattice) / sizeof(int)); q += NT)
                 dst[q] = src[q];
+            inst = it.inst;
         }
         __syncthreads();
         bool done = false;
-        if constexpr (HasTma<S, TX, TY, NT>::value || HasTmaPair<S, TX, TY, NT>::value) {
-            const TmaMaps &m = maps[it.inst];
-            if (tma && it.kind != TILE_GENERAL && m.valid && m.tx == TX && m.ty == TY) {
-                if (threadIdx.x == 0 && fenced != it.inst) {
-                    // the maps were written by the host: make the tensor-map
-                    // proxy see their current contents
-                    tensormap_acquire(&m.pops);
-                    tensormap_acquire(&m.rho[0]);
-                    tensormap_acquire(&m.rho[1]);
-                }
-                fenced = it.inst;
-                // a wait that gave up leaves the barriers in doubt: the rest
-                // of this CTA's items take the general path
+        if constexpr (kTma) {
+            if (use_tma) {
                 // lattices of a batch may or may not have walls: edge tiles
                 // take the variant that handles both
                 if constexpr (HasTma<S, TX, TY, NT>::value) {
                     if (it.kind == TILE_INTERIOR)
-                        tma = step_tile_tma<S, TX, TY, NT, PARITY, 0>(
-                            sL, cur, it.bx * TX, it.by * TY, smem_raw, m, bar, phase);
+                        tma_ok = step_tile_tma<S, TX, TY, NT, PARITY, 0>(
+                            sL, cur, it.bx * TX, it.by * TY, smem_raw, *m, bar, phase);
                     else
-                        tma = step_tile_tma<S, TX, TY, NT, PARITY, 2>(
-                            sL, cur, it.bx * TX, it.by * TY, smem_raw, m, bar, phase);
+                        tma_ok = step_tile_tma<S, TX, TY, NT, PARITY, 2>(
+                            sL, cur, it.bx * TX, it.by * TY, smem_raw, *m, bar, phase);
                 } else {  // two nodes per lane (64-wide FP32-arithmetic shapes)
                     if (it.kind == TILE_INTERIOR)
-                        tma = step_tile_tma_pair<S, TX, TY, NT, PARITY, 0>(
-                            sL, cur, it.bx * TX, it.by * TY, smem_raw, m, bar, phase);
+                        tma_ok = step_tile_tma_pair<S, TX, TY, NT, PARITY, 0>(
+                            sL, cur, it.bx * TX, it.by * TY, smem_raw, *m, bar, phase);
                     else
-                        tma = step_tile_tma_pair<S, TX, TY, NT, PARITY, 2>(
-                            sL, cur, it.bx * TX, it.by * TY, smem_raw, m, bar, phase);
+                        tma_ok = step_tile_tma_pair<S, TX, TY, NT, PARITY, 2>(
+                            sL, cur, it.bx * TX, it.by * TY, smem_raw, *m, bar, phase);
                 }
                 phase ^= 1u;
                 done = true;
@@ -1975,11 +1973,11 @@ __global__ void __launch_bounds__(NT, HasTmaPair<S, TX, TY, NT>::value
         }
         if (!done) {
             if (it.kind == TILE_INTERIOR)
-                step_tile<S, TX, TY, NT, PARITY, true>(sL, cur, it.bx * TX,
-                                                       it.by * TY, smem_raw);
+                step_tile<S, TX, TY, NT, PARITY, true>(sL, cur, it.bx * TX, it.by * TY,
+                                                       smem_raw);
             else
-                step_tile<S, TX, TY, NT, PARITY, false>(sL, cur, it.bx * TX,
-                                                        it.by * TY, smem_raw);
+                step_tile<S, TX, TY, NT, PARITY, false>(sL, cur, it.bx * TX, it.by * TY,
+                                                        smem_raw);
         }
         __syncthreads();  // smem and sL are reused by the next item
     }
@@ -1988,9 +1986,8 @@ __global__ void __launch_bounds__(NT, HasTmaPair<S, TX, TY, NT>::value
 template <class S, int TX, int TY>
 static cudaError_t launch_batch_shape(const Lattice *d_lats,
                                       const WorkItem *d_items,
-                                      const TmaMaps *d_maps, int *d_counter,
-                                      int n_items, int parity, int cur, int grid,
-                                      cudaStream_t s)
+                                      const TmaMaps *d_maps, int n_items, int parity,
+                                      int cur, int per_cta, cudaStream_t s)
 {
     using real = typename S::real;
     constexpr int NT = step_threads<S, TX, TY>();
@@ -2002,7 +1999,7 @@ static cudaError_t launch_batch_shape(const Lattice *d_lats,
             smem = TmaPairSmem<typename S::pop_t, TX, TY, NT>::bytes;
     auto k0 = step_batch_kernel<S, TX, TY, NT, 0>;
     auto k1 = step_batch_kernel<S, TX, TY, NT, 1>;
-    static int configured = -1, slots = 0;
+    static int configured = -1;
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
@@ -2012,35 +2009,28 @@ static cudaError_t launch_batch_shape(const Lattice *d_lats,
         if (e == cudaSuccess)
             e = cudaFuncSetAttribute(
                 k1, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        int per_sm = 0, sms = 0;
-        if (e == cudaSuccess)
-            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k0, NT, smem);
-        if (e == cudaSuccess)
-            e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
         if (e != cudaSuccess) return e;
-        slots = (per_sm > 0 ? per_sm : 1) * sms;
         configured = dev;
     }
     if (n_items <= 0) return cudaSuccess;
-    if (grid <= 0) grid = slots;
-    if (grid > n_items) grid = n_items;
+    if (per_cta < 1) per_cta = 1;
+    const int grid = (n_items + per_cta - 1) / per_cta;
     if (parity == 0)
-        k0<<<grid, NT, smem, s>>>(d_lats, d_items, n_items, cur, d_maps, d_counter);
+        k0<<<grid, NT, smem, s>>>(d_lats, d_items, n_items, cur, d_maps, per_cta);
     else
-        k1<<<grid, NT, smem, s>>>(d_lats, d_items, n_items, cur, d_maps, d_counter);
+        k1<<<grid, NT, smem, s>>>(d_lats, d_items, n_items, cur, d_maps, per_cta);
     return cudaGetLastError();
 }
 
 template <class S>
 static cudaError_t launch_batch_t(const Lattice *d_lats, const WorkItem *d_items,
-                                  const TmaMaps *d_maps, int *d_counter,
-                                  int n_items, int parity, int cur, int tx, int ty,
-                                  int grid, cudaStream_t s)
+                                  const TmaMaps *d_maps, int n_items, int parity,
+                                  int cur, int tx, int ty, int per_cta, cudaStream_t s)
 {
-#define CPLBM_CASE(a, b)                                                   \
-    if (tx == a && ty == b)                                                \
-        return launch_batch_shape<S, a, b>(d_lats, d_items, d_maps, d_counter, \
-                                           n_items, parity, cur, grid, s);
+#define CPLBM_CASE(a, b)                                                        \
+    if (tx == a && ty == b)                                                     \
+        return launch_batch_shape<S, a, b>(d_lats, d_items, d_maps, n_items,    \
+                                           parity, cur, per_cta, s);
     CPLBM_STEP_SHAPES(CPLBM_CASE)
 #undef CPLBM_CASE
     return cudaErrorInvalidValue;

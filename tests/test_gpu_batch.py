@@ -47,9 +47,12 @@ def _rel(got, want):
 
 
 @pytest.mark.parametrize("steps", [37, 1])
-def test_batch_matches_oracle_per_lattice(steps, oracle_threads):
+@pytest.mark.parametrize("per_cta", [1, 3])
+def test_batch_matches_oracle_per_lattice(steps, per_cta, oracle_threads):
     inst = _instances()
     with Batch([d for d, _, _ in inst], precision="f64") as b:
+        b.items_per_cta = per_cta          # CTAs spanning lattice boundaries
+        assert b.items_per_cta == per_cta
         for k, (_, _, rho) in enumerate(inst):
             b.init(k, rho)
         b.step(steps)          # odd: graph blocks of 16 plus single steps
@@ -101,6 +104,16 @@ def test_batch_autotune_keeps_state_and_reduce_conserves_mass():
         b.step(40)
         for k in range(len(inst)):
             assert abs(b.reduce(k)[0] - m0[k]) / m0[k] < 1e-13
+
+
+def test_batch_schedule_arguments():
+    inst = _instances()
+    with Batch([d for d, _, _ in inst], precision="f32") as b:
+        assert b.items_per_cta == 1
+        b.items_per_cta = 64
+        with pytest.raises(LbmError):
+            b.items_per_cta = 65
+        assert b.items_per_cta == 64
 
 
 def test_batch_rejects_init_at_odd_step_and_bad_index():
@@ -166,7 +179,8 @@ PAIR_SPECS = [
 
 @pytest.mark.parametrize("tile", [(32, 16), (32, 24), (32, 32), (64, 16), (64, 32)])
 @pytest.mark.parametrize("precision", ["f32", "f32_offset", "f16_offset"])
-def test_batch_tile_shapes_reduced_precision(tile, precision):
+@pytest.mark.parametrize("per_cta", [1, 4])
+def test_batch_tile_shapes_reduced_precision(tile, precision, per_cta):
     """Every tile shape of the batched kernel in FP32 arithmetic (the
     64-wide shapes on the two-nodes-per-lane TMA path, edge tiles
     included): each lattice against the FP64 oracle and against its own
@@ -177,6 +191,7 @@ def test_batch_tile_shapes_reduced_precision(tile, precision):
         d["rho_ref"] = 0.5 * (rv + rl) if precision != "f32" else 0.0
     with Batch([d for d, _, _ in inst], precision=precision) as b:
         b.set_tile(*tile)
+        b.items_per_cta = per_cta
         for k, (_, _, rho) in enumerate(inst):
             b.init(k, rho)
         b.step(40)
