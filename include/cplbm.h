@@ -221,17 +221,24 @@ lbm_status lbm_batch_populations(lbm_batch *b, int index, double *f,
 lbm_status lbm_batch_reduce(lbm_batch *b, int index, double out[4]);
 /* Tile shape of the batched kernel (as lbm_set_tile; default 32x32), or
  * the fastest configuration measured over nsteps steps (every tile shape
- * with 1, 2 and 4 work items per CTA, see lbm_batch_schedule) with the
- * state restored afterwards; *tx, *ty receive the shape kept. */
+ * with each schedule of lbm_batch_schedule: 0 when some group of lattices
+ * qualifies, 1, 2 and 4) with the state restored afterwards; *tx, *ty
+ * receive the shape kept. */
 lbm_status lbm_batch_set_tile(lbm_batch *b, int tx, int ty);
 lbm_status lbm_batch_autotune(lbm_batch *b, int nsteps, int *tx, int *ty);
-/* Work items (tiles) per CTA of the batched kernel: each CTA takes that
- * many consecutive tiles of the work list, which mostly belong to one
- * lattice, so its descriptor is loaded once for them; more items per CTA
- * save that set-up, fewer balance the end of a step better.  Speed only,
- * results are unchanged.  items_per_cta in 1 .. 64 sets it (default 1),
- * <= 0 leaves it; *current (may be NULL) receives the value in use.
- * LBM_ERR_ARG above 64. */
+/* Schedule of the batched kernel.  The lattices go to the GPU in groups of
+ * 32 (by index), one launch per group and step; the groups run on parallel
+ * branches of the captured graph.  items_per_cta in 1 .. 64: each CTA takes
+ * that many consecutive tiles of the group's work list, which mostly belong
+ * to one lattice, so its descriptor is loaded once for them; more items per
+ * CTA save that set-up, fewer balance the end of a step better.  0 (the
+ * default): a group whose active lattices share nx, ny and walls and whose
+ * every tile takes a TMA path (a sweep of physical parameters on one
+ * geometry) is launched as a grid of one row of tiles per lattice, with the
+ * descriptors passed as a kernel parameter and no work list; the other
+ * groups take one item per CTA.  Speed only, results are unchanged.  -1
+ * leaves the setting; *current (may be NULL) receives the value in use.
+ * LBM_ERR_ARG outside -1 .. 64. */
 lbm_status lbm_batch_schedule(lbm_batch *b, int items_per_cta, int *current);
 /* Lattice count, total nodes, steps taken, tile shape (any may be NULL). */
 lbm_status lbm_batch_info(const lbm_batch *b, int *count, long long *nodes,

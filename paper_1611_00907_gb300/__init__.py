@@ -407,9 +407,10 @@ class Batch:
 
     @property
     def items_per_cta(self):
-        """Work items (tiles) each CTA of the batched kernel takes."""
+        """Work items (tiles) each CTA of the batched kernel takes; 0: one
+        grid row per lattice for groups of one geometry (lbm_batch_schedule)."""
         cur = C.c_int()
-        self._check(self._lib.lbm_batch_schedule(self._b, 0, C.byref(cur)))
+        self._check(self._lib.lbm_batch_schedule(self._b, -1, C.byref(cur)))
         return cur.value
 
     @items_per_cta.setter

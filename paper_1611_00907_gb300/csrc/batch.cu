@@ -8,6 +8,8 @@
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
+#include <cstring>
+#include <memory>
 #include <new>
 #include <string>
 #include <vector>
@@ -15,6 +17,24 @@
 #include "context.h"
 
 using namespace cplbm;
+
+namespace {
+
+// The lattices [inst0, inst0 + BATCH_LAUNCH_LATTICES) of a batch: one
+// launch per step over their segment of the work list.
+struct Group {
+    int inst0 = 0;
+    int item0 = 0, n_items = 0;    // segment of the device work list
+    bool tma_only = false;         // no item takes the general path
+    std::unique_ptr<BatchMaps> maps[2];  // by the density buffer a step reads
+    // active lattices of one geometry, every tile on a TMA path: the
+    // grid-per-lattice launch (step_uniform_kernel) can take the group
+    std::unique_ptr<UniformGroup> uniform[2];
+    int n_uniform = 0, ntx = 0, nty = 0, seams = 0;
+    bool walls = false;
+};
+
+}  // namespace
 
 struct lbm_batch {
     std::vector<lbm_ctx *> inst;
@@ -25,9 +45,17 @@ struct lbm_batch {
     int tx = 32, ty = 32;
     Lattice *d_lats = nullptr;
     WorkItem *d_items = nullptr;
-    TmaMaps *d_maps = nullptr;  // per-lattice tensor maps, or null (no TMA)
-    int per_cta = 1;            // work items per CTA of the batched kernel
-    int n_items = 0;
+    // work items per CTA of the batched kernel; 0: a grid row per lattice
+    // for the groups of one geometry (lbm_batch_schedule), one item per CTA
+    // for the others
+    int per_cta = 0;
+    int n_items = 0;            // all groups
+    std::vector<Group> groups;
+    // graph branches: the groups after the first run on their own streams
+    // inside the captured graph (their lattices are independent)
+    std::vector<cudaStream_t> aux;
+    std::vector<cudaEvent_t> joins;
+    cudaEvent_t fork = nullptr;
     long long t = 0;
     long long nodes = 0;
     cudaGraphExec_t exec = nullptr;  // GRAPH_STEPS steps from an even step
@@ -66,80 +94,172 @@ void drop_graph(lbm_batch *b)
 }
 
 // Apply the batch tile shape to every lattice and rebuild the device copies
-// of the descriptors and the work list.
+// of the descriptors, the work list and the groups' tensor maps.
 lbm_status rebuild(lbm_batch *b)
 {
     drop_graph(b);
+    const int n = (int)b->inst.size();
     std::vector<Lattice> lats;
     std::vector<WorkItem> items;
-    std::vector<TmaMaps> maps;
-    bool any_maps = false;
-    for (size_t i = 0; i < b->inst.size(); ++i) {
-        lbm_ctx *c = b->inst[i];
-        c->L.tx = b->tx;
-        c->L.ty = b->ty;
-        ctx_refresh_maps(c);
-        lats.push_back(c->L);
-        maps.push_back(c->maps);
-        if (!c->use_tma) maps.back().valid = 0;
-        any_maps = any_maps || maps.back().valid;
-        if (!b->active[i]) continue;
-        const Lattice &L = c->L;
-        const int ntx = (L.nx + b->tx - 1) / b->tx, nty = (L.nyf + b->ty - 1) / b->ty;
-        // edge tiles (periodic seams, wall rows) take the TMA paths too: the
-        // 32-wide one, and for FP32 arithmetic the 64-wide pair path
-        // (step_batch_kernel)
-        const bool tma_shape = b->tx == 32 || (b->tx == 64 && b->precision != LBM_F64);
-        const int seams = tma_shape ? seam_bits(L, b->tx, b->ty) : 0;
-        for (int by = 0; by < nty; ++by)
-            for (int bx = 0; bx < ntx; ++bx)
-                items.push_back({(int)i, bx, by, tile_kind(L, b->tx, b->ty, bx, by, seams)});
-    }
-    // General tiles cost a few interior tiles each, edge tiles (seams,
-    // walls) somewhat more than one.  CTAs take items in list order,
-    // backwards on odd steps: the interior tiles go in two halves at the
-    // ends, so that in either direction a step ends on short items and the
-    // CTAs finish close together, and the edge and general tiles between
-    // them, each class in one run, so that the CTAs of an SM mostly run the
-    // same code path at a time (the batched kernel holds three large ones
-    // and the instruction cache does not hold them all).
-    {
+    // edge tiles (periodic seams, wall rows) take the TMA paths too: the
+    // 32-wide one, and for FP32 arithmetic the 64-wide pair path
+    // (step_batch_kernel); FP64 64-wide tiles have no TMA path
+    const bool tma_shape = b->tx == 32 || (b->tx == 64 && b->precision != LBM_F64);
+    b->groups.clear();
+    for (int g0 = 0; g0 < n; g0 += BATCH_LAUNCH_LATTICES) {
+        Group grp;
+        grp.inst0 = g0;
+        grp.item0 = (int)items.size();
+        for (int p = 0; p < 2; ++p) {
+            grp.maps[p].reset(new (std::nothrow) BatchMaps);
+            if (!grp.maps[p]) return bfail(b, LBM_ERR_OOM, "host allocation failed");
+            std::memset(grp.maps[p].get(), 0, sizeof(BatchMaps));
+        }
         std::vector<WorkItem> gen, edge, inner;
-        for (const WorkItem &it : items)
-            (it.kind == TILE_GENERAL ? gen : it.kind == TILE_SEAM ? edge : inner).push_back(it);
+        for (int i = g0; i < n && i < g0 + BATCH_LAUNCH_LATTICES; ++i) {
+            lbm_ctx *c = b->inst[i];
+            c->L.tx = b->tx;
+            c->L.ty = b->ty;
+            ctx_refresh_maps(c);
+            lats.push_back(c->L);
+            const bool maps_ok = tma_shape && c->use_tma && c->maps.valid;
+            if (maps_ok)
+                for (int p = 0; p < 2; ++p) {
+                    grp.maps[p]->pops[i - g0] = c->maps.pops;
+                    grp.maps[p]->rho[i - g0] = c->maps.rho[p];
+                }
+            if (!b->active[i]) continue;
+            const Lattice &L = c->L;
+            const int ntx = (L.nx + b->tx - 1) / b->tx, nty = (L.nyf + b->ty - 1) / b->ty;
+            const int seams = tma_shape ? seam_bits(L, b->tx, b->ty) : 0;
+            const int no_tma = maps_ok ? 0 : ITEM_NO_TMA;
+            for (int by = 0; by < nty; ++by)
+                for (int bx = 0; bx < ntx; ++bx) {
+                    const int kind = tile_kind(L, b->tx, b->ty, bx, by, seams);
+                    (kind == TILE_GENERAL ? gen : kind == TILE_SEAM ? edge : inner)
+                        .push_back({i, bx, by, kind | no_tma});
+                }
+        }
+        // General tiles cost a few interior tiles each, edge tiles (seams,
+        // walls) somewhat more than one.  CTAs take items in list order,
+        // backwards on odd steps: the interior tiles go in two halves at the
+        // ends, so that in either direction a step ends on short items and
+        // the CTAs finish close together, and the edge and general tiles
+        // between them, each class in one run, so that the CTAs of an SM
+        // mostly run the same code path at a time (the batched kernel holds
+        // three large ones and the instruction cache does not hold them all).
         const size_t h = inner.size() / 2;
-        items.clear();
         items.insert(items.end(), inner.begin(), inner.begin() + h);
         items.insert(items.end(), edge.begin(), edge.end());
         items.insert(items.end(), gen.begin(), gen.end());
         items.insert(items.end(), inner.begin() + h, inner.end());
+        grp.n_items = (int)items.size() - grp.item0;
+        grp.tma_only = tma_shape;
+        for (int k = grp.item0; k < (int)items.size(); ++k)
+            if ((items[k].kind & 3) == TILE_GENERAL || (items[k].kind & ITEM_NO_TMA))
+                grp.tma_only = false;
+        // one geometry among the active lattices: the grid-per-lattice launch
+        int first = -1;
+        bool same = grp.tma_only && grp.n_items > 0;
+        for (int i = g0; same && i < n && i < g0 + BATCH_LAUNCH_LATTICES; ++i) {
+            if (!b->active[i]) continue;
+            const Lattice &L = b->inst[i]->L;
+            if (first < 0) first = i;
+            const Lattice &F = b->inst[first]->L;
+            same = L.nx == F.nx && L.ny == F.ny && L.walls == F.walls;
+        }
+        if (same && first >= 0) {
+            const Lattice &F = b->inst[first]->L;
+            grp.ntx = (F.nx + b->tx - 1) / b->tx;
+            grp.nty = (F.nyf + b->ty - 1) / b->ty;
+            grp.seams = seam_bits(F, b->tx, b->ty);
+            grp.walls = F.walls != 0;
+            for (int p = 0; p < 2; ++p) {
+                grp.uniform[p].reset(new (std::nothrow) UniformGroup);
+                if (!grp.uniform[p]) return bfail(b, LBM_ERR_OOM, "host allocation failed");
+                std::memset(grp.uniform[p].get(), 0, sizeof(UniformGroup));
+            }
+            int k = 0;
+            for (int i = g0; i < n && i < g0 + BATCH_LAUNCH_LATTICES; ++i) {
+                if (!b->active[i]) continue;
+                const lbm_ctx *c = b->inst[i];
+                for (int p = 0; p < 2; ++p) {
+                    grp.uniform[p]->pops[k] = c->maps.pops;
+                    grp.uniform[p]->rho[k] = c->maps.rho[p];
+                    grp.uniform[p]->L[k] = c->L;
+                }
+                ++k;
+            }
+            grp.n_uniform = k;
+        }
+        b->groups.push_back(std::move(grp));
     }
     dev_free(b->d_lats);
     dev_free(b->d_items);
-    dev_free(b->d_maps);
     b->d_lats = nullptr;
     b->d_items = nullptr;
-    b->d_maps = nullptr;
-    if (any_maps) {
-        BCUDA(b, dev_alloc((void **)&b->d_maps, maps.size() * sizeof(TmaMaps)));
-        BCUDA(b, cudaMemcpy(b->d_maps, maps.data(), maps.size() * sizeof(TmaMaps),
-                            cudaMemcpyHostToDevice));
-    }
     BCUDA(b, dev_alloc((void **)&b->d_lats, lats.size() * sizeof(Lattice)));
-    BCUDA(b, dev_alloc((void **)&b->d_items, items.size() * sizeof(WorkItem)));
+    BCUDA(b, dev_alloc((void **)&b->d_items, (items.size() + 1) * sizeof(WorkItem)));
     BCUDA(b, cudaMemcpy(b->d_lats, lats.data(), lats.size() * sizeof(Lattice),
                         cudaMemcpyHostToDevice));
-    BCUDA(b, cudaMemcpy(b->d_items, items.data(), items.size() * sizeof(WorkItem),
-                        cudaMemcpyHostToDevice));
+    if (!items.empty())
+        BCUDA(b, cudaMemcpy(b->d_items, items.data(), items.size() * sizeof(WorkItem),
+                            cudaMemcpyHostToDevice));
     b->n_items = (int)items.size();
+    // one stream and join event per group after the first, for the graph
+    while (b->aux.size() + 1 < b->groups.size()) {
+        cudaStream_t st = nullptr;
+        cudaEvent_t ev = nullptr;
+        BCUDA(b, cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
+        b->aux.push_back(st);
+        BCUDA(b, cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+        b->joins.push_back(ev);
+    }
+    if (!b->fork && b->groups.size() > 1)
+        BCUDA(b, cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming));
     return LBM_OK;
+}
+
+BatchList work_list(const lbm_batch *b, const Group &g, int cur)
+{
+    BatchList w;
+    w.lats = b->d_lats;
+    w.items = b->d_items + g.item0;
+    w.n_items = g.n_items;
+    w.per_cta = b->per_cta > 0 ? b->per_cta : 1;
+    w.tma_only = g.tma_only;
+    w.inst0 = g.inst0;
+    w.maps = g.maps[cur].get();
+    if (b->per_cta == 0 && g.n_uniform > 0) {
+        w.uniform = g.uniform[cur].get();
+        w.n_uniform = g.n_uniform;
+        w.ntx = g.ntx;
+        w.nty = g.nty;
+        w.seams = g.seams;
+        w.walls = g.walls;
+    }
+    return w;
+}
+
+// One step of every group; group k on streams[k] (the batch stream for the
+// direct launches).
+cudaError_t launch_groups(const lbm_batch *b, int p, const cudaStream_t *streams)
+{
+    for (size_t k = 0; k < b->groups.size(); ++k) {
+        const Group &g = b->groups[k];
+        if (g.n_items == 0) continue;
+        cudaError_t e = launch_step_batch(work_list(b, g, p), p, p, b->precision, b->tx,
+                                          b->ty, streams[k]);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
 }
 
 lbm_status launch_one(lbm_batch *b)
 {
     const int p = (int)(b->t & 1);
-    BCUDA(b, launch_step_batch(b->d_lats, b->d_items, b->d_maps, b->n_items, p, p,
-                               b->precision, b->tx, b->ty, b->per_cta, b->stream));
+    std::vector<cudaStream_t> streams(b->groups.size(), b->stream);
+    BCUDA(b, launch_groups(b, p, streams.data()));
     ++b->t;
     return LBM_OK;
 }
@@ -147,12 +267,22 @@ lbm_status launch_one(lbm_batch *b)
 lbm_status ensure_graph(lbm_batch *b)
 {
     if (b->exec) return LBM_OK;
+    std::vector<cudaStream_t> streams(b->groups.size(), b->stream);
+    for (size_t k = 1; k < b->groups.size(); ++k) streams[k] = b->aux[k - 1];
     cudaGraph_t g = nullptr;
     BCUDA(b, cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal));
     cudaError_t e = cudaSuccess;
+    if (b->groups.size() > 1) {  // fork: the branches start after the batch stream
+        e = cudaEventRecord(b->fork, b->stream);
+        for (size_t k = 1; k < b->groups.size() && e == cudaSuccess; ++k)
+            e = cudaStreamWaitEvent(streams[k], b->fork, 0);
+    }
     for (int k = 0; k < GRAPH_STEPS && e == cudaSuccess; ++k)
-        e = launch_step_batch(b->d_lats, b->d_items, b->d_maps, b->n_items, k & 1, k & 1,
-                              b->precision, b->tx, b->ty, b->per_cta, b->stream);
+        e = launch_groups(b, k & 1, streams.data());
+    for (size_t k = 1; k < b->groups.size() && e == cudaSuccess; ++k) {  // join
+        e = cudaEventRecord(b->joins[k - 1], streams[k]);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(b->stream, b->joins[k - 1], 0);
+    }
     cudaError_t e2 = cudaStreamEndCapture(b->stream, &g);
     if (e != cudaSuccess || e2 != cudaSuccess) {
         if (g) cudaGraphDestroy(g);
@@ -362,10 +492,10 @@ lbm_status lbm_batch_set_tile(lbm_batch *b, int tx, int ty)
 lbm_status lbm_batch_schedule(lbm_batch *b, int items_per_cta, int *current)
 {
     if (!b) return LBM_ERR_ARG;
-    if (items_per_cta > 64)
-        return bfail(b, LBM_ERR_ARG, "items per CTA must be 1 .. 64 (got %d)",
-                     items_per_cta);
-    if (items_per_cta > 0 && items_per_cta != b->per_cta) {
+    if (items_per_cta < -1 || items_per_cta > BATCH_MAX_PER_CTA)
+        return bfail(b, LBM_ERR_ARG, "items per CTA must be 0 .. %d, or -1 (got %d)",
+                     BATCH_MAX_PER_CTA, items_per_cta);
+    if (items_per_cta >= 0 && items_per_cta != b->per_cta) {
         b->per_cta = items_per_cta;
         drop_graph(b);  // the captured launches carry the old grid
     }
@@ -400,12 +530,13 @@ lbm_status lbm_batch_autotune(lbm_batch *b, int nsteps, int *tx, int *ty)
     if (st == LBM_OK && (cudaEventCreate(&e0) != cudaSuccess ||
                          cudaEventCreate(&e1) != cudaSuccess))
         st = bfail(b, LBM_ERR_CUDA, "event create");
-    // configurations: every tile shape with 1, 2 or 4 work items per CTA
-    const int per[3] = {1, 2, 4};
+    // configurations: every tile shape with a grid row per lattice (groups of
+    // one geometry) or 1, 2 or 4 work items per CTA
+    const int per[4] = {0, 1, 2, 4};
     auto restore = [&](int k) -> lbm_status {
-        b->tx = sx[k / 3];
-        b->ty = sy[k / 3];
-        b->per_cta = per[k % 3];
+        b->tx = sx[k / 4];
+        b->ty = sy[k / 4];
+        b->per_cta = per[k % 4];
         lbm_status s2 = rebuild(b);
         for (size_t i = 0; i < b->inst.size() && s2 == LBM_OK; ++i)
             s2 = ctx_snapshot(b->inst[i], snaps[i], false);
@@ -413,9 +544,15 @@ lbm_status lbm_batch_autotune(lbm_batch *b, int nsteps, int *tx, int *ty)
         for (size_t i = 0; i < b->inst.size(); ++i) b->inst[i]->t = tsave[i];
         return s2;
     };
-    for (int k = 0; k < 3 * n && st == LBM_OK; ++k) {
-        if (!step_shape_supported(b->precision, sx[k / 3], sy[k / 3])) continue;
+    for (int k = 0; k < 4 * n && st == LBM_OK; ++k) {
+        if (!step_shape_supported(b->precision, sx[k / 4], sy[k / 4])) continue;
         st = restore(k);
+        if (st != LBM_OK) break;
+        if (per[k % 4] == 0) {  // the same launches as one item per CTA otherwise
+            bool any = false;
+            for (const Group &g : b->groups) any = any || g.n_uniform > 0;
+            if (!any) continue;
+        }
         for (int w = 0; w < 2 && st == LBM_OK; ++w) st = launch_one(b);
         if (st != LBM_OK) break;
         if (cudaEventRecord(e0, b->stream) != cudaSuccess) {
@@ -467,7 +604,9 @@ void lbm_batch_destroy(lbm_batch *b)
     for (lbm_ctx *c : b->inst) lbm_destroy(c);
     dev_free(b->d_lats);
     dev_free(b->d_items);
-    dev_free(b->d_maps);
+    for (cudaStream_t st : b->aux) cudaStreamDestroy(st);
+    for (cudaEvent_t ev : b->joins) cudaEventDestroy(ev);
+    if (b->fork) cudaEventDestroy(b->fork);
     if (b->own_stream) cudaStreamDestroy(b->stream);
     delete b;
 }

@@ -227,17 +227,51 @@ __host__ __device__ inline int tile_kind(const Lattice &L, int tx, int ty, int b
 struct WorkItem {
     int inst;      // index into the batch's Lattice array
     int bx, by;    // tile position
-    int kind;      // tile_kind of the tile
+    int kind;      // tile_kind of the tile, | ITEM_NO_TMA when the lattice
+                   // has no usable tensor maps
 };
-// One step of every lattice of a batch in one launch: each CTA takes
+enum { ITEM_NO_TMA = 4 };
+// Most work items one CTA of the batched step takes (lbm_batch_schedule).
+constexpr int BATCH_MAX_PER_CTA = 64;
+// Tensor maps of the lattices of one batched launch, a kernel parameter:
+// for lattice inst0 + k, the population map and the map of the density
+// buffer the step reads.  Batches of more lattices take one launch per
+// group of BATCH_LAUNCH_LATTICES.
+constexpr int BATCH_LAUNCH_LATTICES = 32;
+struct BatchMaps {
+    CUtensorMap pops[BATCH_LAUNCH_LATTICES];
+    CUtensorMap rho[BATCH_LAUNCH_LATTICES];
+};
+// A group of lattices of one geometry (nx, ny, walls; the physics may
+// differ) whose every tile takes a TMA path, as one kernel parameter of
+// 24 KB: descriptors and the maps of the step's density buffer.  Lattice k
+// of the launch is grid row k.
+struct UniformGroup {
+    CUtensorMap pops[BATCH_LAUNCH_LATTICES];
+    CUtensorMap rho[BATCH_LAUNCH_LATTICES];
+    Lattice L[BATCH_LAUNCH_LATTICES];
+};
+// One launch of a batch's work list (batch.cu builds it).
+struct BatchList {
+    const Lattice *lats = nullptr;    // device: descriptors of all lattices
+    const WorkItem *items = nullptr;  // device: tiles of this launch's lattices
+    int n_items = 0;
+    int per_cta = 1;                  // consecutive items per CTA
+    bool tma_only = false;            // every item takes a TMA path
+    int inst0 = 0;                    // first lattice of this launch
+    const BatchMaps *maps = nullptr;  // host: their maps for the step's density
+    // Set for a group of one geometry (instead of the work list): the
+    // launch is one grid row of ntx * nty tiles per lattice.
+    const UniformGroup *uniform = nullptr;  // host
+    int n_uniform = 0, ntx = 0, nty = 0, seams = 0;
+    bool walls = false;
+};
+// One step of a group of lattices of a batch in one launch: each CTA takes
 // per_cta consecutive items of the work list.  All lattices share
-// precision, tile shape and step parity.  d_maps: per-lattice tensor maps
-// in device memory (interior and edge tiles of the shapes with a TMA path),
-// or nullptr.
-cudaError_t launch_step_batch(const Lattice *d_lats, const WorkItem *d_items,
-                              const TmaMaps *d_maps, int n_items, int parity,
-                              int cur, int precision, int tx, int ty, int per_cta,
-                              cudaStream_t s);
+// precision, tile shape and step parity.  With tma_only the kernel holds
+// no general tile path (fewer registers live, less shared memory).
+cudaError_t launch_step_batch(const BatchList &w, int parity, int cur, int precision,
+                              int tx, int ty, cudaStream_t s);
 
 // fields.cu
 // Equilibrium initial state from double fields [ny][nx] on the device:

@@ -201,14 +201,6 @@ __device__ __forceinline__ bool mbar_wait(unsigned long long *bar, unsigned pari
     }
     return false;
 }
-// Order later tensor-map-proxy reads of the 128-byte map at p after
-// generic-proxy writes to it (maps kept in global memory).
-__device__ __forceinline__ void tensormap_acquire(const void *p)
-{
-    asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;\n" ::"l"(
-                     reinterpret_cast<unsigned long long>(p))
-                 : "memory");
-}
 __device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *map,
                                             int x, int y, unsigned long long *bar)
 {

@@ -7,11 +7,8 @@ namespace cplbm {
 #define CPLBM_PREC_DECL(tag)                                                   \
     cudaError_t launch_step_##tag(const Lattice &L, int parity, int cur,       \
                                   cudaStream_t s, const TmaMaps *maps);        \
-    cudaError_t launch_batch_##tag(const Lattice *d_lats,                      \
-                                   const WorkItem *d_items,                   \
-                                   const TmaMaps *d_maps, int n_items,        \
-                                   int parity, int cur, int tx, int ty,       \
-                                   int per_cta, cudaStream_t s);
+    cudaError_t launch_batch_##tag(const BatchList &w, int parity, int cur,   \
+                                   int tx, int ty, cudaStream_t s);
 CPLBM_PREC_DECL(f64)
 CPLBM_PREC_DECL(f32)
 CPLBM_PREC_DECL(f32off)
@@ -100,18 +97,14 @@ cudaError_t launch_step_pt(const Lattice &L, int parity, int cur, cudaStream_t s
     return cudaErrorInvalidValue;
 }
 
-cudaError_t launch_step_batch(const Lattice *d_lats, const WorkItem *d_items,
-                              const TmaMaps *d_maps, int n_items, int parity,
-                              int cur, int precision, int tx, int ty, int per_cta,
-                              cudaStream_t s)
+cudaError_t launch_step_batch(const BatchList &w, int parity, int cur, int precision,
+                              int tx, int ty, cudaStream_t s)
 {
     switch (precision) {
-    case P_F64: return launch_batch_f64(d_lats, d_items, d_maps, n_items, parity, cur, tx, ty, per_cta, s);
-    case P_F32: return launch_batch_f32(d_lats, d_items, d_maps, n_items, parity, cur, tx, ty, per_cta, s);
-    case P_F32_OFF:
-        return launch_batch_f32off(d_lats, d_items, d_maps, n_items, parity, cur, tx, ty, per_cta, s);
-    case P_F16_OFF:
-        return launch_batch_f16off(d_lats, d_items, d_maps, n_items, parity, cur, tx, ty, per_cta, s);
+    case P_F64: return launch_batch_f64(w, parity, cur, tx, ty, s);
+    case P_F32: return launch_batch_f32(w, parity, cur, tx, ty, s);
+    case P_F32_OFF: return launch_batch_f32off(w, parity, cur, tx, ty, s);
+    case P_F16_OFF: return launch_batch_f16off(w, parity, cur, tx, ty, s);
     }
     return cudaErrorInvalidValue;
 }

@@ -5,12 +5,10 @@
 
 namespace cplbm {
 
-cudaError_t launch_batch_f32off(const Lattice *d_lats, const WorkItem *d_items,
-                             const TmaMaps *d_maps, int n_items, int parity, int cur,
-                             int tx, int ty, int per_cta, cudaStream_t s)
+cudaError_t launch_batch_f32off(const BatchList &w, int parity, int cur, int tx,
+                                int ty, cudaStream_t s)
 {
-    return launch_batch_t<SF32Off>(d_lats, d_items, d_maps, n_items, parity, cur, tx, ty,
-                              per_cta, s);
+    return launch_batch_t<SF32Off>(w, parity, cur, tx, ty, s);
 }
 
 }  // namespace cplbm

@@ -883,6 +883,14 @@ __device__ __forceinline__ void combine_ring(real *s_rho, const real *s_ring)
 // Shared memory of a TMA tile: the staged populations in their storage
 // type, then density, partial sums / exchange slots and mu in the
 // arithmetic type.
+// The two tensor maps one tile's TMA loads read: the populations and the
+// density buffer of this step.  Addresses in kernel-parameter space (the
+// maps are __grid_constant__ arguments of the launching kernel).
+struct TileMaps {
+    const CUtensorMap *pops;
+    const CUtensorMap *rho;
+};
+
 template <class S, int TX, int TY, int NP = 1>
 struct TmaSmem {
     using real = typename S::real;
@@ -934,7 +942,7 @@ __device__ __forceinline__ T lap_w(const T (&w)[3][3])
 template <class S, int TX, int TY, int NT, int PARITY, int EDGE, bool PT = false>
 __device__ __forceinline__ bool step_tile_tma(const Lattice &L, int cur, int X0,
                                               int Y0, unsigned char *smem_raw,
-                                              const TmaMaps &maps,
+                                              TileMaps maps,
                                               unsigned long long *bar, unsigned phase)
 {
     using real = typename S::real;
@@ -967,13 +975,13 @@ __device__ __forceinline__ bool step_tile_tma(const Lattice &L, int cur, int X0,
     if (threadIdx.x == 0) {
         mbar_expect_tx(&bar[0],
                        TS::tx_rho + (seam ? 0u : RingStage<real, TX, TY>::bulk_bytes));
-        tma_load_2d(s_rho, &maps.rho[cur], X0 - 4, Y0 - 2, &bar[0]);
+        tma_load_2d(s_rho, maps.rho, X0 - 4, Y0 - 2, &bar[0]);
         mbar_expect_tx(&bar[1], TS::tx_pops);
 #pragma unroll
         for (int i = 1; i < 9; ++i) {
             const int plane = PARITY == 0 ? i - 1 : opp(i) - 1;
             const int y0 = PARITY == 0 ? Y0 : Y0 - ey(i);
-            tma_load_3d(s_pin + (i - 1) * PLANE, &maps.pops,
+            tma_load_3d(s_pin + (i - 1) * PLANE, maps.pops,
                         X0 + pin_x0<PARITY, TS::PX>(i), y0, plane, &bar[1]);
         }
     }
@@ -1458,7 +1466,7 @@ struct TmaPairSmem {
 template <class S, int TX, int TY, int NT, int PARITY, int EDGE>
 __device__ __forceinline__ bool step_tile_tma_pair(const Lattice &L, int cur, int X0,
                                                    int Y0, unsigned char *smem_raw,
-                                                   const TmaMaps &maps,
+                                                   TileMaps maps,
                                                    unsigned long long *bar,
                                                    unsigned phase)
 {
@@ -1488,13 +1496,13 @@ __device__ __forceinline__ bool step_tile_tma_pair(const Lattice &L, int cur, in
     if (threadIdx.x == 0) {
         mbar_expect_tx(&bar[0],
                        TS::tx_rho + (seam ? 0u : RingStage<float, TX, TY>::bulk_bytes));
-        tma_load_2d(s_rho, &maps.rho[cur], X0 - 4, Y0 - 2, &bar[0]);
+        tma_load_2d(s_rho, maps.rho, X0 - 4, Y0 - 2, &bar[0]);
         mbar_expect_tx(&bar[1], TS::tx_pops);
 #pragma unroll
         for (int i = 1; i < 9; ++i) {
             const int plane = PARITY == 0 ? i - 1 : opp(i) - 1;
             const int y0 = PARITY == 0 ? Y0 : Y0 - ey(i);
-            tma_load_3d(s_pin + (i - 1) * PLANE, &maps.pops,
+            tma_load_3d(s_pin + (i - 1) * PLANE, maps.pops,
                         X0 + pin_x0<PARITY, TS::PX>(i), y0, plane, &bar[1]);
         }
     }
@@ -1805,20 +1813,21 @@ __global__ void __launch_bounds__(NT, HasTmaPair<S, TX, TY, NT>::value
                 mbar_init(&bar[1], 1);
             }
             __syncthreads();
+            const TileMaps tm{&maps.pops, &maps.rho[cur]};
             if constexpr (HasTma<S, TX, TY, NT>::value) {
                 if (interior)
                     step_tile_tma<S, TX, TY, NT, PARITY, 0>(L, cur, X0, Y0, smem_raw,
-                                                            maps, bar, 0);
+                                                            tm, bar, 0);
                 else
                     step_tile_tma<S, TX, TY, NT, PARITY, WALLS ? 2 : 1>(L, cur, X0, Y0,
-                                                                        smem_raw, maps, bar, 0);
+                                                                        smem_raw, tm, bar, 0);
             } else {
                 if (interior)
                     step_tile_tma_pair<S, TX, TY, NT, PARITY, 0>(L, cur, X0, Y0,
-                                                                 smem_raw, maps, bar, 0);
+                                                                 smem_raw, tm, bar, 0);
                 else
                     step_tile_tma_pair<S, TX, TY, NT, PARITY, WALLS ? 2 : 1>(
-                        L, cur, X0, Y0, smem_raw, maps, bar, 0);
+                        L, cur, X0, Y0, smem_raw, tm, bar, 0);
             }
             return;
         }
@@ -1885,152 +1894,221 @@ static cudaError_t launch_shape(const Lattice &L, int parity, int cur,
 #define CPLBM_STEP_SHAPES(X) X(32, 16) X(32, 24) X(32, 32) X(64, 16) X(64, 32)
 
 // ---------------------------------------------------------------------------
+// Batched step of lattices of one geometry: step_kernel's tile grid,
+// flattened into grid x, with one grid row per lattice.  The descriptors and
+// tensor maps come as the kernel parameter (UniformGroup), so a CTA starts
+// its copies with no global read before them, and the tile class follows
+// from the tile position as in step_kernel.  Only for groups whose every
+// tile takes a TMA path; WALLS as for step_kernel.
+// ---------------------------------------------------------------------------
+template <class S, int TX, int TY, int NT, int PARITY, bool WALLS>
+__global__ void __launch_bounds__(NT, HasTmaPair<S, TX, TY, NT>::value
+                                          ? pair_min_ctas<S, TX, TY, NT>() : 0)
+    step_uniform_kernel(int cur, int seams, int ntx, int nty,
+                        const __grid_constant__ UniformGroup G)
+{
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    __shared__ __align__(8) unsigned long long bar[2];
+    // lattice by lattice, each in tile-grid order; odd steps walk the order
+    // backwards (step_kernel)
+    const int c = PARITY ? (int)gridDim.x - 1 - (int)blockIdx.x : (int)blockIdx.x;
+    const int per = ntx * nty;  // tiles per lattice
+    const int k = c / per;
+    const int t = c - k * per;
+    const int by = t / ntx, bx = t - by * ntx;
+    const Lattice &L = G.L[k];
+    const int X0 = bx * TX, Y0 = by * TY;
+    const bool interior = tile_kind(L, TX, TY, bx, by, seams) == TILE_INTERIOR;
+    if (threadIdx.x == 0) {
+        mbar_init(&bar[0], 1);
+        mbar_init(&bar[1], 1);
+    }
+    __syncthreads();
+    const TileMaps tm{&G.pops[k], &G.rho[k]};
+    if constexpr (HasTma<S, TX, TY, NT>::value) {
+        if (interior)
+            step_tile_tma<S, TX, TY, NT, PARITY, 0>(L, cur, X0, Y0, smem_raw, tm, bar, 0);
+        else
+            step_tile_tma<S, TX, TY, NT, PARITY, WALLS ? 2 : 1>(L, cur, X0, Y0, smem_raw,
+                                                                tm, bar, 0);
+    } else {
+        if (interior)
+            step_tile_tma_pair<S, TX, TY, NT, PARITY, 0>(L, cur, X0, Y0, smem_raw, tm, bar,
+                                                         0);
+        else
+            step_tile_tma_pair<S, TX, TY, NT, PARITY, WALLS ? 2 : 1>(L, cur, X0, Y0,
+                                                                     smem_raw, tm, bar, 0);
+    }
+}
+
+// ---------------------------------------------------------------------------
 // Batched step: many independent lattices of different sizes and physics in
 // one launch.  Each CTA takes `per_cta` consecutive work items (tiles of the
 // work list, in list order, backwards on odd steps as step_kernel walks its
 // grid); the hardware hands out the CTAs as others finish, so there is no
-// work counter and no per-item wait on one.  Consecutive items mostly belong
-// to one lattice: its descriptor is copied to shared memory and its tensor
-// maps are fenced once per CTA, and per_cta (lbm_batch_autotune) trades that
-// saving against the balance of the last CTAs.
+// work counter and no per-item wait on one.  The CTA stages its items in
+// shared memory with one load, so no tile waits on a global read of the
+// next item.  Consecutive items mostly belong to one lattice: its
+// descriptor is copied to shared memory once per CTA, and per_cta
+// (lbm_batch_autotune) trades that saving against the balance of the last
+// CTAs.  The tensor maps come as a kernel parameter (BatchMaps, up to
+// BATCH_LAUNCH_LATTICES lattices from inst0 on): a map in global memory,
+// written by the host, would need a proxy fence and a fetch in every CTA
+// before its first copy, which cost a sixth of the step time at one item
+// per CTA.  Little state lives across the tile bodies (the
+// item index, the mbarrier phase, the wait status).  GEN = false compiles
+// the kernel without the general tile path, for work lists whose every item
+// takes a TMA path: the general body is what makes the compiler spill, and
+// its shared memory is the larger one for the FP16 storage.  Without it, a
+// wait that gives up leaves the CTA's remaining tiles as they were (the
+// error flag is raised), as step_kernel does.
 // ---------------------------------------------------------------------------
-template <class S, int TX, int TY, int NT, int PARITY>
+template <class S, int TX, int TY, int NT, int PARITY, bool GEN>
 __global__ void __launch_bounds__(NT, HasTmaPair<S, TX, TY, NT>::value
                                           ? pair_min_ctas<S, TX, TY, NT>()
                                           : (sizeof(typename S::real) == 8 ? 2 : 4))
     step_batch_kernel(const Lattice *__restrict__ lats,
                       const WorkItem *__restrict__ items, int n_items, int cur,
-                      const TmaMaps *__restrict__ maps, int per_cta)
+                      int per_cta, int inst0, const __grid_constant__ BatchMaps maps)
 {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     __shared__ Lattice sL;
     __shared__ __align__(8) unsigned long long bar[2];
+    __shared__ int4 s_items[BATCH_MAX_PER_CTA];
     static_assert(sizeof(Lattice) % sizeof(int) == 0, "descriptor copy");
+    static_assert(sizeof(WorkItem) == sizeof(int4), "work item staging");
     constexpr bool kTma = HasTma<S, TX, TY, NT>::value || HasTmaPair<S, TX, TY, NT>::value;
-    int inst = -1;         // lattice whose descriptor sL holds
-    int fenced = -1;       // lattice whose maps this CTA has fenced
-    bool bars = false;     // mbarriers initialised
+    const int w0 = (int)blockIdx.x * per_cta;
+    const int cnt = min(per_cta, n_items - w0);
+    for (int q = threadIdx.x; q < cnt; q += NT)
+        s_items[q] = reinterpret_cast<const int4 *>(items)[PARITY ? n_items - 1 - (w0 + q)
+                                                                   : w0 + q];
+    if (kTma && threadIdx.x == 0) {
+        mbar_init(&bar[0], 1);
+        mbar_init(&bar[1], 1);
+    }
+    __syncthreads();
     unsigned phase = 0;    // next phase of the mbarriers
     bool tma_ok = true;    // a wait that gave up sends the rest to the general path
-    const int w0 = (int)blockIdx.x * per_cta;
-    for (int j = 0; j < per_cta && w0 + j < n_items; ++j) {
-        const int w = w0 + j;
-        const WorkItem it = items[PARITY ? n_items - 1 - w : w];
-        const TmaMaps *m = maps ? &maps[it.inst] : nullptr;
-        bool use_tma = false;
-        if constexpr (kTma) {
-            use_tma = tma_ok && m && it.kind != TILE_GENERAL && m->valid &&
-                      m->tx == TX && m->ty == TY;
-            if (use_tma && threadIdx.x == 0) {
-                if (!bars) {
-                    mbar_init(&bar[0], 1);
-                    mbar_init(&bar[1], 1);
-                }
-                if (fenced != it.inst) {
-                    // the maps were written by the host: make the tensor-map
-                    // proxy see the current contents of the two this step
-                    // reads (while the other threads copy the descriptor)
-                    tensormap_acquire(&m->pops);
-                    tensormap_acquire(&m->rho[cur]);
-                }
-            }
-            if (use_tma) {
-                bars = true;
-                fenced = it.inst;
-            }
-        }
-        if (it.inst != inst) {
-            const int *src = reinterpret_cast<const int *>(lats + it.inst);
+    for (int j = 0; j < cnt; ++j) {
+        const int4 it = s_items[j];   // (inst, bx, by, kind)
+        if (j == 0 || s_items[j - 1].x != it.x) {
+            const int *src = reinterpret_cast<const int *>(lats + it.x);
             int *dst = reinterpret_cast<int *>(&sL);
             for (int q = threadIdx.x; q < (int)(sizeof(Lattice) / sizeof(int)); q += NT)
                 dst[q] = src[q];
-            inst = it.inst;
         }
         __syncthreads();
+        const int kind = it.w & 3;
+        const int x0 = it.y * TX, y0 = it.z * TY;
         bool done = false;
         if constexpr (kTma) {
-            if (use_tma) {
+            if (tma_ok && kind != TILE_GENERAL && !(it.w & ITEM_NO_TMA)) {
+                const TileMaps m{&maps.pops[it.x - inst0], &maps.rho[it.x - inst0]};
                 // lattices of a batch may or may not have walls: edge tiles
                 // take the variant that handles both
                 if constexpr (HasTma<S, TX, TY, NT>::value) {
-                    if (it.kind == TILE_INTERIOR)
+                    if (kind == TILE_INTERIOR)
                         tma_ok = step_tile_tma<S, TX, TY, NT, PARITY, 0>(
-                            sL, cur, it.bx * TX, it.by * TY, smem_raw, *m, bar, phase);
+                            sL, cur, x0, y0, smem_raw, m, bar, phase);
                     else
                         tma_ok = step_tile_tma<S, TX, TY, NT, PARITY, 2>(
-                            sL, cur, it.bx * TX, it.by * TY, smem_raw, *m, bar, phase);
+                            sL, cur, x0, y0, smem_raw, m, bar, phase);
                 } else {  // two nodes per lane (64-wide FP32-arithmetic shapes)
-                    if (it.kind == TILE_INTERIOR)
+                    if (kind == TILE_INTERIOR)
                         tma_ok = step_tile_tma_pair<S, TX, TY, NT, PARITY, 0>(
-                            sL, cur, it.bx * TX, it.by * TY, smem_raw, *m, bar, phase);
+                            sL, cur, x0, y0, smem_raw, m, bar, phase);
                     else
                         tma_ok = step_tile_tma_pair<S, TX, TY, NT, PARITY, 2>(
-                            sL, cur, it.bx * TX, it.by * TY, smem_raw, *m, bar, phase);
+                            sL, cur, x0, y0, smem_raw, m, bar, phase);
                 }
                 phase ^= 1u;
                 done = true;
             }
         }
-        if (!done) {
-            if (it.kind == TILE_INTERIOR)
-                step_tile<S, TX, TY, NT, PARITY, true>(sL, cur, it.bx * TX, it.by * TY,
-                                                       smem_raw);
-            else
-                step_tile<S, TX, TY, NT, PARITY, false>(sL, cur, it.bx * TX, it.by * TY,
-                                                        smem_raw);
+        if constexpr (GEN) {
+            if (!done) {
+                if (kind == TILE_INTERIOR)
+                    step_tile<S, TX, TY, NT, PARITY, true>(sL, cur, x0, y0, smem_raw);
+                else
+                    step_tile<S, TX, TY, NT, PARITY, false>(sL, cur, x0, y0, smem_raw);
+            }
+        } else {
+            (void)done;
         }
         __syncthreads();  // smem and sL are reused by the next item
     }
 }
 
 template <class S, int TX, int TY>
-static cudaError_t launch_batch_shape(const Lattice *d_lats,
-                                      const WorkItem *d_items,
-                                      const TmaMaps *d_maps, int n_items, int parity,
-                                      int cur, int per_cta, cudaStream_t s)
+static cudaError_t launch_batch_shape(const BatchList &w, int parity, int cur,
+                                      cudaStream_t s)
 {
     using real = typename S::real;
     constexpr int NT = step_threads<S, TX, TY>();
-    size_t smem = StepSmem<real, TX, TY>::bytes;
-    if constexpr (HasTma<S, TX, TY, NT>::value)
-        if (TmaSmem<S, TX, TY>::bytes > smem) smem = TmaSmem<S, TX, TY>::bytes;
+    constexpr bool kTma = HasTma<S, TX, TY, NT>::value || HasTmaPair<S, TX, TY, NT>::value;
+    size_t smem_tma = 0;
+    if constexpr (HasTma<S, TX, TY, NT>::value) smem_tma = TmaSmem<S, TX, TY>::bytes;
     if constexpr (HasTmaPair<S, TX, TY, NT>::value)
-        if (TmaPairSmem<typename S::pop_t, TX, TY, NT>::bytes > smem)
-            smem = TmaPairSmem<typename S::pop_t, TX, TY, NT>::bytes;
-    auto k0 = step_batch_kernel<S, TX, TY, NT, 0>;
-    auto k1 = step_batch_kernel<S, TX, TY, NT, 1>;
+        smem_tma = TmaPairSmem<typename S::pop_t, TX, TY, NT>::bytes;
+    const size_t smem_gen = StepSmem<real, TX, TY>::bytes > smem_tma
+                                ? StepSmem<real, TX, TY>::bytes : smem_tma;
+    // [general path compiled in][parity]
+    void (*kern[2][2])(const Lattice *, const WorkItem *, int, int, int, int,
+                       const BatchMaps) = {
+        {step_batch_kernel<S, TX, TY, NT, 0, !kTma>, step_batch_kernel<S, TX, TY, NT, 1, !kTma>},
+        {step_batch_kernel<S, TX, TY, NT, 0, true>, step_batch_kernel<S, TX, TY, NT, 1, true>}};
     static int configured = -1;
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
     if (configured != dev) {
-        e = cudaFuncSetAttribute(k0, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)smem);
-        if (e == cudaSuccess)
-            e = cudaFuncSetAttribute(
-                k1, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        for (int g = 0; g < 2 && e == cudaSuccess; ++g)
+            for (int p = 0; p < 2 && e == cudaSuccess; ++p)
+                e = cudaFuncSetAttribute(kern[g][p], cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)(g || !kTma ? smem_gen : smem_tma));
         if (e != cudaSuccess) return e;
         configured = dev;
     }
-    if (n_items <= 0) return cudaSuccess;
-    if (per_cta < 1) per_cta = 1;
-    const int grid = (n_items + per_cta - 1) / per_cta;
-    if (parity == 0)
-        k0<<<grid, NT, smem, s>>>(d_lats, d_items, n_items, cur, d_maps, per_cta);
-    else
-        k1<<<grid, NT, smem, s>>>(d_lats, d_items, n_items, cur, d_maps, per_cta);
+    if constexpr (kTma) {
+        if (w.uniform) {
+            void (*uk[2][2])(int, int, int, int, const UniformGroup) = {
+                {step_uniform_kernel<S, TX, TY, NT, 0, false>,
+                 step_uniform_kernel<S, TX, TY, NT, 1, false>},
+                {step_uniform_kernel<S, TX, TY, NT, 0, true>,
+                 step_uniform_kernel<S, TX, TY, NT, 1, true>}};
+            static int uconfigured = -1;
+            if (uconfigured != dev) {
+                for (int q = 0; q < 4 && e == cudaSuccess; ++q)
+                    e = cudaFuncSetAttribute(uk[q >> 1][q & 1],
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)smem_tma);
+                if (e != cudaSuccess) return e;
+                uconfigured = dev;
+            }
+            if (w.n_uniform <= 0) return cudaSuccess;
+            const int grid = w.ntx * w.nty * w.n_uniform;
+            uk[w.walls ? 1 : 0][parity & 1]<<<grid, NT, smem_tma, s>>>(cur, w.seams, w.ntx,
+                                                                       w.nty, *w.uniform);
+            return cudaGetLastError();
+        }
+    }
+    if (w.n_items <= 0) return cudaSuccess;
+    const int per_cta = w.per_cta < 1 ? 1 : w.per_cta;
+    const int grid = (w.n_items + per_cta - 1) / per_cta;
+    const int g = (kTma && w.tma_only) ? 0 : 1;
+    const size_t smem = g || !kTma ? smem_gen : smem_tma;
+    kern[g][parity & 1]<<<grid, NT, smem, s>>>(w.lats, w.items, w.n_items, cur, per_cta,
+                                               w.inst0, *w.maps);
     return cudaGetLastError();
 }
 
 template <class S>
-static cudaError_t launch_batch_t(const Lattice *d_lats, const WorkItem *d_items,
-                                  const TmaMaps *d_maps, int n_items, int parity,
-                                  int cur, int tx, int ty, int per_cta, cudaStream_t s)
+static cudaError_t launch_batch_t(const BatchList &w, int parity, int cur, int tx, int ty,
+                                  cudaStream_t s)
 {
 #define CPLBM_CASE(a, b)                                                        \
-    if (tx == a && ty == b)                                                     \
-        return launch_batch_shape<S, a, b>(d_lats, d_items, d_maps, n_items,    \
-                                           parity, cur, per_cta, s);
+    if (tx == a && ty == b) return launch_batch_shape<S, a, b>(w, parity, cur, s);
     CPLBM_STEP_SHAPES(CPLBM_CASE)
 #undef CPLBM_CASE
     return cudaErrorInvalidValue;
@@ -2061,12 +2139,13 @@ __global__ void __launch_bounds__(NT)
                 mbar_init(&bar[1], 1);
             }
             __syncthreads();
+            const TileMaps tm{&maps.pops, &maps.rho[cur]};
             if (interior)
                 step_tile_tma<S, TX, TY, NT, PARITY, 0, true>(L, cur, bx * TX, by * TY,
-                                                              smem_raw, maps, bar, 0);
+                                                              smem_raw, tm, bar, 0);
             else
                 step_tile_tma<S, TX, TY, NT, PARITY, 1, true>(L, cur, bx * TX, by * TY,
-                                                              smem_raw, maps, bar, 0);
+                                                              smem_raw, tm, bar, 0);
             return;
         }
     }

@@ -1,4 +1,4 @@
-"""Batched lattices (one persistent launch per step over every lattice's
+"""Batched lattices (one launch per step over every lattice's
 tiles, blocks of steps from a CUDA graph) against the FP64 oracle and the
 single-lattice path, lattice by lattice."""
 import numpy as np
@@ -109,11 +109,14 @@ def test_batch_autotune_keeps_state_and_reduce_conserves_mass():
 def test_batch_schedule_arguments():
     inst = _instances()
     with Batch([d for d, _, _ in inst], precision="f32") as b:
-        assert b.items_per_cta == 1
+        assert b.items_per_cta == 0
         b.items_per_cta = 64
-        with pytest.raises(LbmError):
-            b.items_per_cta = 65
+        for bad in (65, -2):
+            with pytest.raises(LbmError):
+                b.items_per_cta = bad
         assert b.items_per_cta == 64
+        b.items_per_cta = 0
+        assert b.items_per_cta == 0
 
 
 def test_batch_rejects_init_at_odd_step_and_bad_index():
@@ -219,3 +222,128 @@ def test_batch_tile_shapes_reduced_precision(tile, precision, per_cta):
             for key, tol in (("rho", 1e-4), ("mu", 1e-4), ("vx", 3e-4), ("vy", 3e-4)):
                 assert _rel(got[key], want[key]) < tol, (k, key)
             assert _rel(got["rho"], one["rho"]) < 1e-5, k
+
+
+# Lattices whose tiles all take a TMA path (full tiles, periodic seams or
+# walls, at least three 64-wide tiles across): the batched kernel is then
+# launched without its general tile path.
+TMA_SPECS = [
+    PAIR_SPECS[0], PAIR_SPECS[1],
+    dict(nx=192, ny=98, eos="rks", a=2 / 49, b=2 / 21, Tr=0.8, tau=1.3,
+         kappa=0.01, walls=True, mu_delta=-0.05),
+    dict(nx=192, ny=96, eos="pr", a=2 / 49, b=2 / 21, Tr=0.85, tau=1.3,
+         kappa=0.01),
+]
+
+
+@pytest.mark.parametrize("tile", [(32, 16), (32, 32), (64, 16), (64, 32)])
+@pytest.mark.parametrize("precision", ["f64", "f32", "f16_offset"])
+@pytest.mark.parametrize("per_cta", [1, 3])
+def test_batch_tma_only_work_list(tile, precision, per_cta):
+    """A work list without general tiles (the kernel variant compiled
+    without the general path) against the FP64 oracle, lattice by lattice,
+    over both in-place parities."""
+    from paper_1611_00907_gb300 import tile_kinds
+    if precision == "f64" and tile[0] == 64:
+        pytest.skip("FP64 64-wide tiles have no TMA path")
+    inst = _instances(TMA_SPECS)
+    for d, e, rho in inst:
+        assert (np.asarray(tile_kinds(d["nx"], d["ny"], d.get("walls", False),
+                                      tile, True)) > 0).all()
+        rv, rl, _, _ = thermo.maxwell(e)
+        d["rho_ref"] = 0.5 * (rv + rl) if precision == "f16_offset" else 0.0
+    with Batch([d for d, _, _ in inst], precision=precision) as b:
+        b.set_tile(*tile)
+        b.items_per_cta = per_cta
+        for k, (_, _, rho) in enumerate(inst):
+            b.init(k, rho)
+        b.step(21)
+        for k, (d, e, rho) in enumerate(inst):
+            ref = oracle.Lattice(d["nx"], d["ny"], e, d["tau"], d["kappa"],
+                                 walls=d.get("walls", False),
+                                 mu_bottom=d["mu_bottom"])
+            ref.init_equilibrium(rho).step(21)
+            got, want = b.moments(k), ref.moments()
+            if precision == "f16_offset":
+                assert _rel(got["rho"], want["rho"]) < 2e-3, (k, "rho")
+                continue
+            tols = ((("rho", 1e-12), ("mu", 1e-12), ("vx", 1e-12), ("vy", 1e-12))
+                    if precision == "f64" else
+                    (("rho", 1e-4), ("mu", 1e-4), ("vx", 3e-4), ("vy", 3e-4)))
+            for key, tol in tols:
+                assert _rel(got[key], want[key]) < tol, (k, key)
+
+
+def test_batch_of_more_lattices_than_one_launch_takes():
+    """A batch larger than one launch's group of lattices (their tensor maps
+    travel as a kernel parameter): the groups run as separate launches, on
+    parallel branches of the captured graph, and every lattice still
+    follows the oracle."""
+    base = dict(nx=64, ny=32, eos="cs", a=1.0, b=4.0, Tr=0.85, tau=1.0, kappa=0.5)
+    specs = [dict(base, tau=0.8 + 0.004 * k) for k in range(70)]
+    specs[3] = dict(specs[3], nx=70, ny=21)          # ragged: general tiles
+    specs[66] = dict(specs[66], walls=True, ny=34, mu_delta=0.02)
+    inst = _instances(specs)
+    with Batch([d for d, _, _ in inst], precision="f64") as b:
+        for k, (_, _, rho) in enumerate(inst):
+            b.init(k, rho)
+        b.step(17)
+        for k in (0, 3, 63, 64, 66, 69):
+            d, e, rho = inst[k]
+            ref = oracle.Lattice(d["nx"], d["ny"], e, d["tau"], d["kappa"],
+                                 walls=d.get("walls", False),
+                                 mu_bottom=d["mu_bottom"])
+            ref.init_equilibrium(rho).step(17)
+            got, want = b.moments(k), ref.moments()
+            for key in ("rho", "mu", "vx", "vy"):
+                assert _rel(got[key], want[key]) < 1e-12, (k, key)
+
+
+# Sweeps on one geometry (the wetting study's shape): the grid-per-lattice
+# launch, physics differing lattice by lattice.
+SWEEPS = {
+    "walls": [dict(nx=192, ny=66, eos="cs", a=1.0, b=4.0, Tr=0.85, tau=tau,
+                   kappa=0.5, walls=True, mu_delta=md)
+              for tau, md in ((1.0, -0.02), (0.9, 0.0), (1.2, 0.015), (1.0, 0.03))],
+    "periodic": [dict(nx=256, ny=128, eos="cs", a=1.0, b=4.0, Tr=tr, tau=1.0,
+                      kappa=0.5) for tr in (0.8, 0.85, 0.9)],
+}
+
+
+@pytest.mark.parametrize("sweep", ["walls", "periodic"])
+@pytest.mark.parametrize("tile", [(32, 16), (32, 32), (64, 16), (64, 32)])
+@pytest.mark.parametrize("precision", ["f64", "f32", "f16_offset"])
+def test_batch_grid_per_lattice_on_one_geometry(sweep, tile, precision):
+    """The grid-per-lattice launch (descriptors as a kernel parameter)
+    against the FP64 oracle, lattice by lattice, over both in-place
+    parities; a lattice taken out of the launch half-way keeps its state
+    and the grid rows of the others move up."""
+    if precision == "f64" and tile[0] == 64:
+        pytest.skip("FP64 64-wide tiles have no TMA path")
+    inst = _instances(SWEEPS[sweep])
+    for d, e, rho in inst:
+        rv, rl, _, _ = thermo.maxwell(e)
+        d["rho_ref"] = 0.5 * (rv + rl) if precision == "f16_offset" else 0.0
+    with Batch([d for d, _, _ in inst], precision=precision) as b:
+        b.set_tile(*tile)
+        b.items_per_cta = 0
+        for k, (_, _, rho) in enumerate(inst):
+            b.init(k, rho)
+        b.step(6)
+        b.set_active(1, False)
+        b.step(17)
+        for k, (d, e, rho) in enumerate(inst):
+            n = 6 if k == 1 else 23
+            ref = oracle.Lattice(d["nx"], d["ny"], e, d["tau"], d["kappa"],
+                                 walls=d.get("walls", False),
+                                 mu_bottom=d["mu_bottom"])
+            ref.init_equilibrium(rho).step(n)
+            got, want = b.moments(k), ref.moments()
+            if precision == "f16_offset":
+                assert _rel(got["rho"], want["rho"]) < 2e-3, (k, "rho")
+                continue
+            tols = ((("rho", 1e-12), ("mu", 1e-12), ("vx", 1e-12), ("vy", 1e-12))
+                    if precision == "f64" else
+                    (("rho", 1e-4), ("mu", 1e-4), ("vx", 3e-4), ("vy", 3e-4)))
+            for key, tol in tols:
+                assert _rel(got[key], want[key]) < tol, (k, key)
