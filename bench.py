@@ -288,7 +288,7 @@ def batch_specs(which):
     return [{k: v for k, v in sp.items() if k in keep} for sp in specs], fields
 
 
-def measure_batch(which, precision, steps, warmup, sequential=True):
+def measure_batch(which, precision, steps, warmup, sequential=True, config=None):
     """One launch per step over every lattice's tiles (graph-replayed),
     and the same lattices stepped one by one, each its own launch."""
     import math
@@ -304,7 +304,13 @@ def measure_batch(which, precision, steps, warmup, sequential=True):
                    stream=stream.cuda_stream) as b:
             for k, f in enumerate(fields):
                 b.init(k, f)
-            out["tile"] = list(b.autotune(6))
+            if config is None:
+                out["tile"] = list(b.autotune(6))
+            else:  # a fixed configuration (profiling runs)
+                b.set_tile(*config[0])
+                b.items_per_cta = config[1]
+                out["tile"] = list(config[0])
+                out["autotuned"] = False
             out["items_per_cta"] = b.items_per_cta
             b.step(warmup)
             torch.cuda.synchronize()
@@ -788,6 +794,9 @@ def main():
                     help="batched workloads to time (comma list)")
     ap.add_argument("--tile", default=None,
                     help="step tile shape TXxTY (default: the library's)")
+    ap.add_argument("--batch-config", default=None,
+                    help="TXxTY:SCHEDULE for the batched legs instead of "
+                         "the autotuner (profiling runs), e.g. 64x32:0")
     ap.add_argument("--batch-steps", type=int, default=100,
                     help="steps of the batched workloads (0: skip them)")
     ap.add_argument("--pt-steps", type=int, default=200,
@@ -874,15 +883,20 @@ def main():
 
     batches = {}
     legs = set(args.batches.split(",")) if args.batch_steps > 0 else set()
+    bcfg = None
+    if args.batch_config:
+        shape, sched = args.batch_config.split(":")
+        bcfg = (tuple(int(v) for v in shape.split("x")), int(sched))
     if "uneven" in legs:
         batches["batch_uneven"] = measure_batch("uneven", "f32",
-                                                args.batch_steps, 4)
+                                                args.batch_steps, 4, config=bcfg)
     if "wetting" in legs:
         batches["batch_wetting"] = measure_batch("wetting", "f32",
-                                                 args.batch_steps, 4)
+                                                 args.batch_steps, 4, config=bcfg)
     if "wetting_f16" in legs:
         batches["batch_wetting_f16"] = measure_batch(
-            "wetting", "f16_offset", args.batch_steps, 4, sequential=False)
+            "wetting", "f16_offset", args.batch_steps, 4, sequential=False,
+            config=bcfg)
 
     warm = None
     if args.warmstart != "off" and rank == 0:
