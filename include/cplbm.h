@@ -384,6 +384,14 @@ void lbm_test_fail_device_alloc(int after);
  * networks and their staging buffers), for leak checks. */
 long long lbm_test_device_allocs(void);
 
+/* The FP64 natural logarithm and reciprocal the FP64 step evaluates the EOS
+ * and the collision with (a table-driven logarithm and a Newton-refined
+ * reciprocal, each within a few ulp of log(x) and 1/x), applied on the
+ * current device to the n host values x into the host arrays log_out and
+ * rcp_out; for accuracy tests.  Synchronous.  LBM_ERR_ARG on a NULL buffer
+ * or n < 0; errors go to lbm_last_error(NULL). */
+lbm_status lbm_test_fp64_math(const double *x, int n, double *log_out, double *rcp_out);
+
 #ifdef __cplusplus
 }
 #endif

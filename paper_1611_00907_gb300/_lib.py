@@ -72,6 +72,7 @@ SIGNATURES = {
     "lbm_test_set_wait_cycles": ([_ctx, C.c_longlong], C.c_int),
     "lbm_test_fail_device_alloc": ([C.c_int], None),
     "lbm_test_device_allocs": ([], C.c_longlong),
+    "lbm_test_fp64_math": ([C.c_void_p, C.c_int, C.c_void_p, C.c_void_p], C.c_int),
     "lbm_step_noalloc": ([C.POINTER(LbmConfig), C.c_int, C.c_double,
                           C.c_double, C.c_double, C.c_double, C.c_double,
                           C.c_double, C.c_int, C.c_double, _vp, C.c_int],

@@ -916,6 +916,27 @@ void lbm_test_fail_device_alloc(int after) { g_fail_countdown = after < 0 ? -1 :
 
 long long lbm_test_device_allocs(void) { return g_live_allocs.load(); }
 
+lbm_status lbm_test_fp64_math(const double *x, int n, double *log_out, double *rcp_out)
+{
+    if (!x || !log_out || !rcp_out || n < 0)
+        return fail(nullptr, LBM_ERR_ARG, "null buffer or negative count");
+    if (n == 0) return LBM_OK;
+    const size_t bytes = (size_t)n * sizeof(double);
+    double *d = nullptr;
+    cudaError_t e = dev_alloc((void **)&d, 3 * bytes);
+    if (e != cudaSuccess)
+        return fail(nullptr, e == cudaErrorMemoryAllocation ? LBM_ERR_OOM : LBM_ERR_CUDA,
+                    "device allocation: %s", cudaGetErrorString(e));
+    e = cudaMemcpy(d, x, bytes, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = launch_fp64_math(d, n, d + n, d + 2 * (size_t)n, 0);
+    if (e == cudaSuccess) e = cudaMemcpy(log_out, d + n, bytes, cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess) e = cudaMemcpy(rcp_out, d + 2 * (size_t)n, bytes, cudaMemcpyDeviceToHost);
+    dev_free(d);
+    if (e != cudaSuccess)
+        return fail(nullptr, LBM_ERR_CUDA, "fp64 math: %s", cudaGetErrorString(e));
+    return LBM_OK;
+}
+
 const char *lbm_last_error(const lbm_ctx *c)
 {
     return c ? c->err.c_str() : g_err.c_str();

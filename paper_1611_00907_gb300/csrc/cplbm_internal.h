@@ -274,6 +274,10 @@ cudaError_t launch_step_batch(const BatchList &w, int parity, int cur, int preci
                               int tx, int ty, cudaStream_t s);
 
 // fields.cu
+// The FP64 logarithm and reciprocal of the step kernels (log_tab, rcp_nr)
+// on n device values, into lg and rc (device).
+cudaError_t launch_fp64_math(const double *x, int n, double *lg, double *rc,
+                             cudaStream_t s);
 // Equilibrium initial state from double fields [ny][nx] on the device:
 // fills pops (parity 0 order) and rho[0]/ring[0]; counts invalid densities
 // into *bad (device int, zeroed by the caller).

@@ -8,6 +8,7 @@
 #include <cuda_runtime.h>
 
 #include "cplbm_internal.h"
+#include "log_table.h"
 
 namespace cplbm {
 
@@ -70,13 +71,66 @@ __device__ __forceinline__ void st_real(__half *p, float v) { *p = __float2half_
 // Bulk chemical potential psi'(rho): Eq. 18 (vdW), Eq. 21 (RK/RKS), Eq. 24
 // (PR), Eq. 27 (CS) without the -kappa lap(rho) term.
 // ---------------------------------------------------------------------------
+// FP64 reciprocal: the hardware's approximate reciprocal (PTX
+// rcp.approx.ftz.f64) refined by two Newton-Raphson steps r <- r + r (1 -
+// x r), each of which doubles the number of correct bits.  Within one ulp of
+// 1/x for normal x with a normal reciprocal (measured: the correctly
+// rounded value on 800 000 log-uniform samples), not guaranteed correctly
+// rounded as IEEE division is, at a fraction of its FP64-pipe instructions
+// (the GB300 FP64 pipe bounds the FP64 step).  Zero, infinite and NaN x give
+// NaN.
+__device__ __forceinline__ double rcp_nr(double x)
+{
+    double r;
+    asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(r) : "d"(x));
+    r = fma(r, fma(-x, r, 1.0), r);
+    return fma(r, fma(-x, r, 1.0), r);
+}
+
+// FP64 natural logarithm after Tang's table-driven method (P. T. P. Tang,
+// ACM TOMS 16(4), 1990).  x = 2^m y with y in [1, 2); F = 1 + j/128 the
+// breakpoint next to y, f = y - F (exact, |f| <= 2^-8), r = f/F from the
+// tabulated 1/F; ln x = m ln 2 + ln F + ln(1 + r), the last by its Taylor
+// series through r^7 (the rest is below 2^-59 of r).  ln 2 and ln F are
+// tabulated as hi + lo with hi a multiple of 2^-32, so m ln2_hi + lnF_hi is
+// exact: just below 1 the two cancel almost entirely, and only the small
+// terms carry rounding errors.  For x in [1 - 2^-9, 1) (m = -1, j = 128) the
+// series takes r = x - 1 directly.  Within about two ulp for positive
+// normal x; zero, negative, subnormal, infinite and NaN x go to log().
+__device__ __forceinline__ double log_tab(double x)
+{
+    const int hi = __double2hiint(x);
+    if ((unsigned)(hi - 0x00100000) >= 0x7FE00000u) return log(x);
+    int m = (hi >> 20) - 1023;
+    const int mant = hi & 0x000FFFFF;        // top 20 bits of the significand
+    int j = (mant + (1 << 12)) >> 13;        // nearest multiple of 1/128: 0 .. 128
+    double y = __hiloint2double(mant | 0x3FF00000, __double2loint(x));
+    if (m == -1 && j == LOG_TABLE_N) {       // x in [1 - 2^-9, 1)
+        y = x;
+        m = 0;
+        j = 0;
+    }
+    const double F = __hiloint2double(0x3FF00000 + (j << 13), 0);
+    const double2 t = __ldg(&kLogTable[j]);  // {1/F, hi of ln F}
+    const double r = (y - F) * t.x;
+    double q = fma(r, 1.0 / 7.0, -1.0 / 6.0);
+    q = fma(q, r, 1.0 / 5.0);
+    q = fma(q, r, -1.0 / 4.0);
+    q = fma(q, r, 1.0 / 3.0);
+    q = fma(q, r, -0.5);
+    const double p = fma(r * r, q, r);       // ln(1 + r)
+    const double dm = (double)m;
+    return fma(dm, LN2_HI, t.y) + (fma(dm, LN2_LO, __ldg(&kLogTableLo[j])) + p);
+}
+
 // Division and logarithm of the arithmetic type: the FP32 kernels use the
 // fast hardware forms (__fdividef, __logf), whose few-ulp errors sit far
-// below the FP32 storage error; FP64 keeps IEEE division and log().
+// below the FP32 storage error; FP64 the reciprocal and logarithm above,
+// within one or two ulp of IEEE division and log().
 __device__ __forceinline__ float fdiv(float a, float b) { return __fdividef(a, b); }
-__device__ __forceinline__ double fdiv(double a, double b) { return a / b; }
+__device__ __forceinline__ double fdiv(double a, double b) { return a * rcp_nr(b); }
 __device__ __forceinline__ float flog(float x) { return __logf(x); }
-__device__ __forceinline__ double flog(double x) { return log(x); }
+__device__ __forceinline__ double flog(double x) { return log_tab(x); }
 
 template <class T>
 __device__ __forceinline__ T mu_bulk(const EosT<T> &e, T rho)

@@ -287,4 +287,24 @@ cudaError_t launch_gather_rho(const Lattice &L, int cur, void *dst,
     CPLBM_DISPATCH(L.precision, launch_gather_t<S>(L, cur, dst, s))
 }
 
+// The FP64 logarithm and reciprocal of the step kernels on n values
+// (lbm_test_fp64_math).
+__global__ void fp64_math_kernel(const double *__restrict__ x, int n,
+                                 double *__restrict__ lg, double *__restrict__ rc)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) {
+        lg[i] = log_tab(x[i]);
+        rc[i] = rcp_nr(x[i]);
+    }
+}
+
+cudaError_t launch_fp64_math(const double *x, int n, double *lg, double *rc,
+                             cudaStream_t s)
+{
+    if (n <= 0) return cudaSuccess;
+    fp64_math_kernel<<<(n + 255) / 256, 256, 0, s>>>(x, n, lg, rc);
+    return cudaGetLastError();
+}
+
 }  // namespace cplbm
