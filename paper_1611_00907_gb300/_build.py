@@ -65,7 +65,8 @@ def build(force: bool = False, verbose: bool = False) -> str:
         for _, err in results:
             sys.stderr.write(err)
     tmp = LIB + ".tmp%d" % os.getpid()
-    cmd = [cc, *ARCH, "-shared", "-o", tmp] + [o for o, _ in results]
+    # -ldl: NVTX (csrc/trace.h) looks up a profiler's library at run time
+    cmd = [cc, *ARCH, "-shared", "-o", tmp] + [o for o, _ in results] + ["-ldl"]
     res = subprocess.run(cmd, capture_output=True, text=True)
     if res.returncode != 0:
         raise RuntimeError("nvcc link failed:\n%s" % res.stderr)

@@ -15,6 +15,7 @@
 #include <vector>
 
 #include "context.h"
+#include "trace.h"
 
 using namespace cplbm;
 
@@ -383,6 +384,7 @@ lbm_status lbm_batch_create(const lbm_instance *inst, int count, int precision,
 lbm_status lbm_batch_init(lbm_batch *b, int index, const double *rho,
                           const double *ux, const double *uy, int on_device)
 {
+    CPLBM_TRACE("lbm_batch_init");
     if (!b) return LBM_ERR_ARG;
     lbm_status st = check_index(b, index);
     if (st != LBM_OK) return st;
@@ -397,6 +399,7 @@ lbm_status lbm_batch_init(lbm_batch *b, int index, const double *rho,
 
 lbm_status lbm_batch_step(lbm_batch *b, int nsteps)
 {
+    CPLBM_TRACE("lbm_batch_step");
     if (!b) return LBM_ERR_ARG;
     if (nsteps < 0) return bfail(b, LBM_ERR_ARG, "nsteps must be >= 0");
     for (size_t i = 0; i < b->inst.size(); ++i)
@@ -448,6 +451,7 @@ lbm_status lbm_batch_set_active(lbm_batch *b, int index, int active)
 lbm_status lbm_batch_moments(lbm_batch *b, int index, double *rho, double *vx,
                              double *vy, double *mu, int on_device)
 {
+    CPLBM_TRACE("lbm_batch_moments");
     if (!b) return LBM_ERR_ARG;
     lbm_status st = check_index(b, index);
     if (st != LBM_OK) return st;
@@ -466,6 +470,7 @@ lbm_status lbm_batch_populations(lbm_batch *b, int index, double *f, int on_devi
 
 lbm_status lbm_batch_reduce(lbm_batch *b, int index, double out[4])
 {
+    CPLBM_TRACE("lbm_batch_reduce");
     if (!b) return LBM_ERR_ARG;
     lbm_status st = check_index(b, index);
     if (st != LBM_OK) return st;
@@ -475,6 +480,7 @@ lbm_status lbm_batch_reduce(lbm_batch *b, int index, double out[4])
 
 lbm_status lbm_batch_set_tile(lbm_batch *b, int tx, int ty)
 {
+    CPLBM_TRACE("lbm_batch_set_tile");
     if (!b) return LBM_ERR_ARG;
     if (!step_shape_supported(b->precision, tx, ty))
         return bfail(b, LBM_ERR_ARG, "no step kernel for tile %d x %d", tx, ty);
@@ -505,6 +511,7 @@ lbm_status lbm_batch_schedule(lbm_batch *b, int items_per_cta, int *current)
 
 lbm_status lbm_batch_autotune(lbm_batch *b, int nsteps, int *tx, int *ty)
 {
+    CPLBM_TRACE("lbm_batch_autotune");
     if (!b) return LBM_ERR_ARG;
     for (size_t i = 0; i < b->inst.size(); ++i)
         if (!b->inst[i]->initialized)

@@ -11,6 +11,7 @@
 
 #include "../../include/cplbm.h"
 #include "cplbm_internal.h"
+#include "trace.h"
 
 using namespace cplbm;
 
@@ -512,6 +513,7 @@ lbm_status lbm_eos_info(const lbm_ctx *c, double *T, double *alpha,
 
 lbm_status lbm_set_tile(lbm_ctx *c, int tx, int ty)
 {
+    CPLBM_TRACE("lbm_set_tile");
     if (!c) return fail(nullptr, LBM_ERR_ARG, "null context");
     if (!step_shape_supported(c->L.precision, tx, ty))
         return fail(c, LBM_ERR_ARG, "no step kernel for tile %d x %d", tx, ty);
@@ -567,6 +569,7 @@ lbm_status snapshot(lbm_ctx *c, char *snap, bool save)
 
 lbm_status lbm_autotune(lbm_ctx *c, int nsteps, int *best_tx, int *best_ty)
 {
+    CPLBM_TRACE("lbm_autotune");
     if (!c) return fail(nullptr, LBM_ERR_ARG, "null context");
     if (!c->initialized) return fail(c, LBM_ERR_STATE, "lbm_init must come first");
     if (nsteps < 2) nsteps = 2;
@@ -677,6 +680,7 @@ lbm_status lbm_set_wall_mu(lbm_ctx *c, double mu_bottom, int top_mode,
 lbm_status lbm_init(lbm_ctx *c, const double *rho, const double *ux,
                     const double *uy, int on_device)
 {
+    CPLBM_TRACE("lbm_init");
     if (!c) return fail(nullptr, LBM_ERR_ARG, "null context");
     if (!rho) return fail(c, LBM_ERR_ARG, "rho is required");
     if (!c->eos_set) return fail(c, LBM_ERR_STATE, "lbm_set_eos must come first");
@@ -728,6 +732,7 @@ lbm_status lbm_init(lbm_ctx *c, const double *rho, const double *ux,
 
 lbm_status lbm_step(lbm_ctx *c, int nsteps)
 {
+    CPLBM_TRACE("lbm_step");
     if (!c) return fail(nullptr, LBM_ERR_ARG, "null context");
     if (nsteps < 0) return fail(c, LBM_ERR_ARG, "nsteps must be >= 0");
     if (!c->initialized) return fail(c, LBM_ERR_STATE, "lbm_init must come first");
@@ -746,6 +751,7 @@ lbm_status lbm_step(lbm_ctx *c, int nsteps)
 lbm_status lbm_moments(lbm_ctx *c, double *rho, double *vx, double *vy,
                        double *mu, int on_device)
 {
+    CPLBM_TRACE("lbm_moments");
     if (!c) return fail(nullptr, LBM_ERR_ARG, "null context");
     if (!c->initialized) return fail(c, LBM_ERR_STATE, "lbm_init must come first");
     CUDA_TRY(c, cudaSetDevice(c->device));
@@ -779,6 +785,7 @@ lbm_status lbm_moments(lbm_ctx *c, double *rho, double *vx, double *vy,
 
 lbm_status lbm_get_populations(lbm_ctx *c, double *f, int on_device)
 {
+    CPLBM_TRACE("lbm_get_populations");
     if (!c) return fail(nullptr, LBM_ERR_ARG, "null context");
     if (!f) return fail(c, LBM_ERR_ARG, "null output");
     if (!c->initialized) return fail(c, LBM_ERR_STATE, "lbm_init must come first");
@@ -806,6 +813,7 @@ lbm_status lbm_get_populations(lbm_ctx *c, double *f, int on_device)
 
 lbm_status lbm_reduce(lbm_ctx *c, double out[4])
 {
+    CPLBM_TRACE("lbm_reduce");
     if (!c) return fail(nullptr, LBM_ERR_ARG, "null context");
     if (!out) return fail(c, LBM_ERR_ARG, "null output");
     if (!c->initialized) return fail(c, LBM_ERR_STATE, "lbm_init must come first");
@@ -843,6 +851,7 @@ size_t lbm_state_size(const lbm_ctx *c)
 
 lbm_status lbm_get_state(lbm_ctx *c, void *buf, size_t bytes)
 {
+    CPLBM_TRACE("lbm_get_state");
     if (!c) return fail(nullptr, LBM_ERR_ARG, "null context");
     if (!buf || bytes < lbm_state_size(c))
         return fail(c, LBM_ERR_ARG, "buffer smaller than lbm_state_size()");
@@ -870,6 +879,7 @@ lbm_status lbm_get_state(lbm_ctx *c, void *buf, size_t bytes)
 
 lbm_status lbm_set_state(lbm_ctx *c, const void *buf, size_t bytes)
 {
+    CPLBM_TRACE("lbm_set_state");
     if (!c) return fail(nullptr, LBM_ERR_ARG, "null context");
     if (!buf || bytes < lbm_state_size(c))
         return fail(c, LBM_ERR_ARG, "buffer smaller than lbm_state_size()");

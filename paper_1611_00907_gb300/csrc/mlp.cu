@@ -21,6 +21,7 @@
 
 #include "../../include/cplbm.h"
 #include "cplbm_internal.h"  // dev_alloc / dev_free
+#include "trace.h"
 
 namespace cplbm_mlp {
 
@@ -391,6 +392,7 @@ lbm_status lbm_mlp_create(int device, const float *init, lbm_mlp **out)
 lbm_status lbm_mlp_train(lbm_mlp *m, const float *X, int nin, const float *T,
                          int nout, int B, int iters, float lr, float *loss_out)
 {
+    CPLBM_TRACE("lbm_mlp_train");
     if (!m) return LBM_ERR_ARG;
     if (!X || !T || B <= 0 || nin < 1 || nin > DIN || nout < 1 || nout > DOUT ||
         iters < 0 || !(lr >= 0))
@@ -423,6 +425,7 @@ lbm_status lbm_mlp_train(lbm_mlp *m, const float *X, int nin, const float *T,
 lbm_status lbm_mlp_gradient(lbm_mlp *m, const float *X, int nin, const float *T,
                             int nout, int B, float *grad, float *loss_out)
 {
+    CPLBM_TRACE("lbm_mlp_gradient");
     if (!m) return LBM_ERR_ARG;
     if (!X || !T || !grad || B <= 0 || nin < 1 || nin > DIN || nout < 1 || nout > DOUT)
         return mfail(m, LBM_ERR_ARG, "bad gradient arguments", cudaSuccess);
@@ -449,6 +452,7 @@ lbm_status lbm_mlp_gradient(lbm_mlp *m, const float *X, int nin, const float *T,
 lbm_status lbm_mlp_predict(lbm_mlp *m, const float *X, int nin, float *Y,
                            int nout, int B)
 {
+    CPLBM_TRACE("lbm_mlp_predict");
     if (!m) return LBM_ERR_ARG;
     if (!X || !Y || B <= 0 || nin < 1 || nin > DIN || nout < 1 || nout > DOUT)
         return mfail(m, LBM_ERR_ARG, "bad prediction arguments", cudaSuccess);
