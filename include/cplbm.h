@@ -384,6 +384,15 @@ void lbm_test_fail_device_alloc(int after);
  * networks and their staging buffers), for leak checks. */
 long long lbm_test_device_allocs(void);
 
+/* Bounds-checked debug build only (libcplbm_checked.so, CPLBM_CHECK_BOUNDS):
+ * make the device checks treat each density buffer of ctx as rho_bytes long
+ * (0 .. its real size), so that in-bounds accesses beyond that count as out
+ * of bounds: they are skipped and the next synchronising call reports
+ * LBM_ERR_CUDA naming an access outside its buffer.  A negative control of
+ * the checks that makes no real out-of-bounds access.  LBM_ERR_STATE in the
+ * product build; LBM_ERR_ARG outside that range. */
+lbm_status lbm_test_shrink_bounds(lbm_ctx *ctx, long long rho_bytes);
+
 /* The FP64 natural logarithm and reciprocal the FP64 step evaluates the EOS
  * and the collision with (a table-driven logarithm and a Newton-refined
  * reciprocal, each within a few ulp of log(x) and 1/x), applied on the

@@ -1,14 +1,19 @@
 """ctypes declarations of the C ABI in include/cplbm.h.
 
 Loading fails loudly when libcplbm.so has not been built: there is no CPU
-fallback anywhere in this package.
+fallback anywhere in this package.  CPLBM_LIBRARY_VARIANT=checked in the
+environment loads the bounds-checked debug build (libcplbm_checked.so,
+`python -m paper_1611_00907_gb300._build --checked`) instead.
 """
 import ctypes as C
 import os
 import re
 
 HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(HERE, "libcplbm.so")
+_VARIANT = os.environ.get("CPLBM_LIBRARY_VARIANT", "")
+if _VARIANT not in ("", "checked"):
+    raise ImportError("CPLBM_LIBRARY_VARIANT must be unset or 'checked'")
+LIB_PATH = os.path.join(HERE, "libcplbm_checked.so" if _VARIANT else "libcplbm.so")
 HEADER = os.path.join(os.path.dirname(HERE), "include", "cplbm.h")
 
 LBM_OK, LBM_ERR_ARG, LBM_ERR_CUDA, LBM_ERR_OOM, LBM_ERR_NUMERIC, \
@@ -73,6 +78,7 @@ SIGNATURES = {
     "lbm_test_fail_device_alloc": ([C.c_int], None),
     "lbm_test_device_allocs": ([], C.c_longlong),
     "lbm_test_fp64_math": ([C.c_void_p, C.c_int, C.c_void_p, C.c_void_p], C.c_int),
+    "lbm_test_shrink_bounds": ([_ctx, C.c_longlong], C.c_int),
     "lbm_step_noalloc": ([C.POINTER(LbmConfig), C.c_int, C.c_double,
                           C.c_double, C.c_double, C.c_double, C.c_double,
                           C.c_double, C.c_int, C.c_double, _vp, C.c_int],
@@ -125,9 +131,11 @@ def load():
     if _lib is None:
         if not os.path.exists(LIB_PATH):
             raise ImportError(
-                "libcplbm.so is not built (expected at %s); run "
-                "`python -c 'import __graft_entry__ as g; g.build()'`"
-                % LIB_PATH)
+                "%s is not built (expected at %s); run "
+                "`python -c 'import __graft_entry__ as g; g.build()'`%s"
+                % (os.path.basename(LIB_PATH), LIB_PATH,
+                   " and `python -m paper_1611_00907_gb300._build --checked`"
+                   if _VARIANT else ""))
         lib = C.CDLL(LIB_PATH)
         for name, (args, res) in SIGNATURES.items():
             fn = getattr(lib, name)

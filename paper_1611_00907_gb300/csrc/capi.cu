@@ -277,6 +277,9 @@ lbm_status check_kernel_flags(lbm_ctx *c)
     CUDA_TRY(c, cudaMemcpy(&flags, c->d_err, sizeof(int), cudaMemcpyDeviceToHost));
     if (flags) {
         CUDA_TRY(c, cudaMemset(c->d_err, 0, sizeof(int)));
+        if (flags & ERR_BOUNDS)
+            return fail(c, LBM_ERR_CUDA, "a kernel accessed memory outside its buffer "
+                        "(bounds-checked build; flags %d); the access was skipped", flags);
         return fail(c, LBM_ERR_CUDA, "a step kernel's wait for its data timed out "
                     "(flags %d); the affected tiles were not updated", flags);
     }
@@ -368,6 +371,9 @@ lbm_status lbm_create(const lbm_config *cfg, lbm_ctx **out)
         }
     };
     alloc(&L.pops, 8 * (size_t)L.plane * pb);
+#ifdef CPLBM_CHECK_BOUNDS
+    set_bounds(L, 8 * L.plane * (long long)pb, L.plane * (long long)rb);
+#endif
     for (int k = 0; k < 2; ++k) {
         alloc(&L.rho[k], (size_t)L.plane * rb);
         for (int r = 0; r < R_COUNT; ++r) alloc(&L.ring[k][r], ring_elems(L, r) * rb);
@@ -925,6 +931,20 @@ lbm_status lbm_test_set_wait_cycles(lbm_ctx *c, long long cycles)
 void lbm_test_fail_device_alloc(int after) { g_fail_countdown = after < 0 ? -1 : after; }
 
 long long lbm_test_device_allocs(void) { return g_live_allocs.load(); }
+
+lbm_status lbm_test_shrink_bounds(lbm_ctx *c, long long rho_bytes)
+{
+    if (!c) return fail(nullptr, LBM_ERR_ARG, "null context");
+#ifdef CPLBM_CHECK_BOUNDS
+    if (rho_bytes < 0 || rho_bytes > c->L.b_rho)
+        return fail(c, LBM_ERR_ARG, "extent must be 0 .. %lld bytes", c->L.b_rho);
+    c->L.b_rho = rho_bytes;
+    return LBM_OK;
+#else
+    (void)rho_bytes;
+    return fail(c, LBM_ERR_STATE, "bounds checks exist in the checked build only");
+#endif
+}
 
 lbm_status lbm_test_fp64_math(const double *x, int n, double *log_out, double *rcp_out)
 {

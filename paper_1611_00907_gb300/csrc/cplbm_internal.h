@@ -90,6 +90,11 @@ struct Lattice {
                             // before it gives up (WAIT_CYCLES_DEFAULT)
     Consts<float> cf;    // tau .. mu_top and eos as float (set_consts)
     Consts<double> cd;   // ... and as double
+#ifdef CPLBM_CHECK_BOUNDS
+    // bounds-checked build: bytes of pops, of each density buffer and of
+    // each partial-sum class (set_bounds)
+    long long b_pops, b_rho, b_ring[R_COUNT];
+#endif
 };
 
 // Refresh L.cf and L.cd from the double fields; call after any change of
@@ -120,8 +125,9 @@ struct TmaMaps {
 // (with a message) when the layout does not allow TMA.
 bool build_tma_maps(const Lattice &L, TmaMaps *m, char *err, size_t errlen);
 
-// Bits of Lattice::err.
-enum { ERR_WAIT_TIMEOUT = 1 };
+// Bits of Lattice::err.  ERR_BOUNDS: a global access outside its buffer,
+// caught (and skipped) by the bounds-checked build.
+enum { ERR_WAIT_TIMEOUT = 1, ERR_BOUNDS = 2 };
 // Limit of the step kernels' first wait for a tile's staged data: about a
 // second at the 2 GHz SM clock, far beyond any copy's latency.  A wait
 // that reaches it raises ERR_WAIT_TIMEOUT, drains the tile's copies (with
@@ -152,6 +158,19 @@ inline size_t pop_bytes(int prec)
     return prec == P_F64 ? 8 : prec == P_F16_OFF ? 2 : 4;
 }
 inline size_t rho_bytes(int prec) { return prec == P_F64 ? 8 : 4; }
+
+#ifdef CPLBM_CHECK_BOUNDS
+// Bounds-checked build: record the extents the device checks compare with;
+// pops_bytes counts from L.pops to the end of the population storage,
+// rho_buf_bytes is the size of each density buffer.
+inline void set_bounds(Lattice &L, long long pops_bytes, long long rho_buf_bytes)
+{
+    const long long rb = (long long)rho_bytes(L.precision);
+    L.b_pops = pops_bytes;
+    L.b_rho = rho_buf_bytes;
+    for (int c = 0; c < R_COUNT; ++c) L.b_ring[c] = (long long)ring_elems(L, c) * rb;
+}
+#endif
 
 // Launchers (step.cu).  `cur` selects rho[cur] / ring[cur] as the current
 // density and `parity` the AA phase of the step being taken.

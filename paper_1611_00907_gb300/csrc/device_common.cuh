@@ -68,6 +68,37 @@ __device__ __forceinline__ void st_real(float *p, float v) { *p = v; }
 __device__ __forceinline__ void st_real(__half *p, float v) { *p = __float2half_rn(v); }
 
 // ---------------------------------------------------------------------------
+// Bounds-checked build (CPLBM_CHECK_BOUNDS; a debug build that stands in for
+// a memory checker): the global accesses of the step and field kernels are
+// checked against the buffer they belong to first; an access outside it
+// raises ERR_BOUNDS in L.err and is skipped (a load reads zero, a copy
+// leaves its destination as it was).  TMA loads need no check: the tensor
+// map bounds them.  In the normal build every check is the constant true,
+// its arguments are not evaluated, and the accesses compile as before.
+// n: elements accessed from p on.
+// ---------------------------------------------------------------------------
+#ifdef CPLBM_CHECK_BOUNDS
+__device__ __forceinline__ bool in_buffer(const Lattice &L, const void *base, long long bytes,
+                                          const void *p, long long size)
+{
+    const long long off = (const char *)p - (const char *)base;
+    if (off >= 0 && off + size <= bytes) return true;
+    if (L.err) atomicOr(L.err, ERR_BOUNDS);
+    return false;
+}
+#define CPLBM_IN_POPS(L, p, n) \
+    ::cplbm::in_buffer(L, (L).pops, (L).b_pops, p, (long long)(n) * sizeof(*(p)))
+#define CPLBM_IN_RHO(L, k, p, n) \
+    ::cplbm::in_buffer(L, (L).rho[k], (L).b_rho, p, (long long)(n) * sizeof(*(p)))
+#define CPLBM_IN_RING(L, k, c, p, n) \
+    ::cplbm::in_buffer(L, (L).ring[k][c], (L).b_ring[c], p, (long long)(n) * sizeof(*(p)))
+#else
+#define CPLBM_IN_POPS(L, p, n) true
+#define CPLBM_IN_RHO(L, k, p, n) true
+#define CPLBM_IN_RING(L, k, c, p, n) true
+#endif
+
+// ---------------------------------------------------------------------------
 // Bulk chemical potential psi'(rho): Eq. 18 (vdW), Eq. 21 (RK/RKS), Eq. 24
 // (PR), Eq. 27 (CS) without the -kappa lap(rho) term.
 // ---------------------------------------------------------------------------
@@ -355,7 +386,8 @@ __device__ __forceinline__ typename S::real load_rho_stored(const Lattice &L,
     using rt = typename S::rho_t;
     using real = typename S::real;
     const rt *R = (const rt *)L.rho[cur];
-    real v = (real)R[fidx(L, r, x)];
+    const rt *rp = R + fidx(L, r, x);
+    real v = CPLBM_IN_RHO(L, cur, rp, 1) ? (real)*rp : real(0);
     const int bx = x / L.tx, by = r / L.ty;
     const int lx = x - bx * L.tx, ly = r - by * L.ty;
     const int wx = min(L.tx, L.nx - bx * L.tx);
@@ -365,7 +397,10 @@ __device__ __forceinline__ typename S::real load_rho_stored(const Lattice &L,
     const bool above = ly == wy - 1 && !(L.walls && r == L.nyf - 1);
     if (left | right | below | above) {
         rt *const *ring = (rt *const *)L.ring[cur];
-        auto at = [&](int c) { return ring[c][ring_index(L, c, bx, by, r, x)]; };
+        auto at = [&](int c) {
+            const rt *q = ring[c] + ring_index(L, c, bx, by, r, x);
+            return CPLBM_IN_RING(L, cur, c, q, 1) ? *q : rt(0);
+        };
         if (left) v += (real)at(R_L);
         if (right) v += (real)at(R_R);
         if (below) {

@@ -33,10 +33,11 @@ __global__ void init_kernel(const Lattice L, const double *rho_in,
         const double eu = ex(i) * ux + ey(i) * uy;
         const double feq =
             wgt<double>(i) * rho * (1.0 + 3.0 * eu + 4.5 * eu * eu - usq);
-        st_real(A + pidx(L, i, r, x),
-                (typename S::real)(feq - wgt<double>(i) * ref));
+        pop_t *p = A + pidx(L, i, r, x);
+        if (CPLBM_IN_POPS(L, p, 1)) st_real(p, (typename S::real)(feq - wgt<double>(i) * ref));
     }
-    ((rho_t *)L.rho[0])[fidx(L, r, x)] = (rho_t)(rho - ref);
+    rho_t *q = (rho_t *)L.rho[0] + fidx(L, r, x);
+    if (CPLBM_IN_RHO(L, 0, q, 1)) *q = (rho_t)(rho - ref);
 }
 
 // ---------------------------------------------------------------------------
@@ -84,8 +85,10 @@ __global__ void macro_kernel(const Lattice L, int parity, int cur,
         const int cr = (ly + 2) * WR + lx + 2, cm = (ly + 1) * WM + lx + 1;
         real f[9];
 #pragma unroll
-        for (int i = 1; i < 9; ++i)
-            f[i] = ld_real(A + aa_read_index(L, parity, i, r, x));
+        for (int i = 1; i < 9; ++i) {
+            const pop_t *p = A + aa_read_index(L, parity, i, r, x);
+            f[i] = CPLBM_IN_POPS(L, p, 1) ? ld_real(p) : real(0);
+        }
         const real rho = s_rho[cr] + rho_ref;
         real gmx, gmy, grx, gry;
         grad9<real, WM>(s_mu, cm, gmx, gmy);
@@ -181,7 +184,8 @@ __global__ void populations_kernel(const Lattice L, int parity, int cur,
     const pop_t *A = (const pop_t *)L.pops;
     double sum = 0.0;
     for (int i = 1; i < 9; ++i) {
-        const double v = (double)ld_real(A + aa_read_index(L, parity, i, r, x)) +
+        const pop_t *p = A + aa_read_index(L, parity, i, r, x);
+        const double v = (CPLBM_IN_POPS(L, p, 1) ? (double)ld_real(p) : 0.0) +
                          wgt<double>(i) * ref;
         f[i * N + g] = v;
         sum += v;

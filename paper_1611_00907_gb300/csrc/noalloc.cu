@@ -235,6 +235,12 @@ extern "C" lbm_status lbm_step_noalloc(
         L.rho[k] = scratch + rho_off[k];
         for (int c = 0; c < R_COUNT; ++c) L.ring[k][c] = scratch + ring_off[k][c];
     }
+#ifdef CPLBM_CHECK_BOUNDS
+    // f holds 9 planes of nx * ny values; no error flag here, so an access
+    // outside its buffer is skipped without a report
+    set_bounds(L, (8 * L.plane - (long long)L.walls * L.nx) * (long long)sizeof(double),
+               (long long)field * (long long)sizeof(double));
+#endif
 
     cudaStream_t s = (cudaStream_t)cfg->stream;
     // the partial sums are read for tile-edge nodes from the first step on

@@ -89,7 +89,7 @@ __device__ __forceinline__ void issue_rho_interior(const Lattice &L, int cur,
     for (int k = threadIdx.x; k < WR * HR; k += NT) {
         const int lx = k % WR, ly = k / WR;
         const long long fi = (long long)(Y0 + ly - 2) * L.pitch + X0 + lx - 2;
-        cp_async<sizeof(rt)>(&s_rho[k], R + fi);
+        if (CPLBM_IN_RHO(L, cur, R + fi, 1)) cp_async<sizeof(rt)>(&s_rho[k], R + fi);
     }
     for (int p = threadIdx.x; p < SM::NRING; p += NT) {
         int c, lx, ly, dbx = 0, dby = 0;  // receiving tile - this tile
@@ -116,7 +116,8 @@ __device__ __forceinline__ void issue_rho_interior(const Lattice &L, int cur,
         }
         const int x = X0 + lx - 2, r = Y0 + ly - 2;
         const long long idx = ring_index(L, c, X0 / TX + dbx, Y0 / TY + dby, r, x);
-        cp_async<sizeof(rt)>(&s_ring[p], ring[c] + idx);
+        if (CPLBM_IN_RING(L, cur, c, ring[c] + idx, 1))
+            cp_async<sizeof(rt)>(&s_ring[p], ring[c] + idx);
     }
 }
 
@@ -358,7 +359,8 @@ __device__ __forceinline__ void step_tile(const Lattice &L, int cur, int X0,
                 const pop_t *src = INTERIOR
                     ? A + base + roff[i]
                     : A + aa_read_index(L, PARITY, i, r, x);
-                cp_async<sizeof(pop_t)>(&s_post[post_idx<TX, TY>(i, ly, lx)], src);
+                if (CPLBM_IN_POPS(L, src, 1))
+                    cp_async<sizeof(pop_t)>(&s_post[post_idx<TX, TY>(i, ly, lx)], src);
             }
         }
         cp_async_commit();
@@ -398,13 +400,13 @@ __device__ __forceinline__ void step_tile(const Lattice &L, int cur, int X0,
         if constexpr (ASYNC) {
 #pragma unroll
             for (int i = 1; i < 9; ++i) f[i] = s_post[post_idx<TX, TY>(i, ly, lx)];
-        } else if (INTERIOR) {
-#pragma unroll
-            for (int i = 1; i < 9; ++i) f[i] = ld_real(A + base + roff[i]);
         } else {
 #pragma unroll
-            for (int i = 1; i < 9; ++i)
-                f[i] = ld_real(A + aa_read_index(L, PARITY, i, r, x));
+            for (int i = 1; i < 9; ++i) {
+                const pop_t *src = INTERIOR ? A + base + roff[i]
+                                            : A + aa_read_index(L, PARITY, i, r, x);
+                f[i] = CPLBM_IN_POPS(L, src, 1) ? ld_real(src) : real(0);
+            }
         }
         const int cr = (ly + 2) * WR + lx + 2, cm = (ly + 1) * WM + lx + 1;
         const real drho = s_rho[cr];
@@ -432,13 +434,11 @@ __device__ __forceinline__ void step_tile(const Lattice &L, int cur, int X0,
         self0[k] = fp[0];
 #pragma unroll
         for (int i = 1; i < 9; ++i) s_post[post_idx<TX, TY>(i, ly, lx)] = fp[i];
-        if (INTERIOR) {
 #pragma unroll
-            for (int i = 1; i < 9; ++i) st_real(A + base + woff[i], fp[i]);
-        } else {
-#pragma unroll
-            for (int i = 1; i < 9; ++i)
-                st_real(A + aa_write_index(L, PARITY, i, r, x), fp[i]);
+        for (int i = 1; i < 9; ++i) {
+            pop_t *dst = INTERIOR ? A + base + woff[i]
+                                  : A + aa_write_index(L, PARITY, i, r, x);
+            if (CPLBM_IN_POPS(L, dst, 1)) st_real(dst, fp[i]);
         }
     }
     __syncthreads();
@@ -463,7 +463,8 @@ __device__ __forceinline__ void step_tile(const Lattice &L, int cur, int X0,
             s = handover_sum<real, TX, TY>(L, s_post, lx, ly, wx, wy, r, true,
                                            self0[k]);
         }
-        Rn[(long long)r * L.pitch + X0 + lx] = (rho_t)s;
+        rho_t *q = Rn + (long long)r * L.pitch + X0 + lx;
+        if (CPLBM_IN_RHO(L, nxt, q, 1)) *q = (rho_t)s;
     }
     // Ring around the tile: partial sums for the neighbouring tiles.
     const int nring = 2 * (wx + wy) + 4;
@@ -477,7 +478,8 @@ __device__ __forceinline__ void step_tile(const Lattice &L, int cur, int X0,
         const int x = INTERIOR ? X0 + ox : wrapi(X0 + ox, L.nx);
         const int rw = INTERIOR ? r : row_wrap(L, r);
         const int c = ring_class(ox, oy, wx, wy);
-        ring[c][ring_index(L, c, x / TX, rw / TY, rw, x)] = (rho_t)s;
+        rho_t *q = ring[c] + ring_index(L, c, x / TX, rw / TY, rw, x);
+        if (CPLBM_IN_RING(L, nxt, c, q, 1)) *q = (rho_t)s;
     }
 }
 
@@ -555,6 +557,23 @@ struct RingStage {
                   "bulk copies are whole 16-byte units");
 };
 
+// Stores of the density hand-over into generation `gen` (element type T,
+// value type V: one element or a packed pair), checked in the
+// bounds-checked build.
+template <class T, class V>
+__device__ __forceinline__ void put_rho(const Lattice &L, int gen, T *R, long long idx, V v)
+{
+    T *q = R + idx;
+    if (CPLBM_IN_RHO(L, gen, q, sizeof(V) / sizeof(T))) *reinterpret_cast<V *>(q) = v;
+}
+template <class T, class V>
+__device__ __forceinline__ void put_ring(const Lattice &L, int gen, T *const *ring, int c,
+                                         long long idx, V v)
+{
+    T *q = ring[c] + idx;
+    if (CPLBM_IN_RING(L, gen, c, q, sizeof(V) / sizeof(T))) *reinterpret_cast<V *>(q) = v;
+}
+
 __device__ __forceinline__ void bulk_load(void *dst, const void *src, unsigned bytes,
                                           unsigned long long *bar)
 {
@@ -579,25 +598,27 @@ __device__ __forceinline__ void stage_ring(const Lattice &L, int cur, int X0, in
 #pragma unroll
         for (int ci = 0; ci < 4; ++ci) {
             const int c = col_is_left(ci) ? R_L : R_R;
-            bulk_load(s_ring + ci * RS::CL,
-                      ring[c] + ring_index(L, c, bx + edge_tile(ci), by, Y0 - 4, X0),
-                      RS::CL * sizeof(rt), bar);
+            const rt *src = ring[c] + ring_index(L, c, bx + edge_tile(ci), by, Y0 - 4, X0);
+            // a skipped copy leaves its bytes owed to bar: the bounded wait
+            // then gives up and reports it too
+            if (CPLBM_IN_RING(L, cur, c, src, RS::CL))
+                bulk_load(s_ring + ci * RS::CL, src, RS::CL * sizeof(rt), bar);
         }
 #pragma unroll
         for (int ri = 0; ri < 4; ++ri) {
             const int c = row_is_below(ri) ? R_B : R_T;
-            bulk_load(s_ring + RS::NCOL + ri * RS::RL,
-                      ring[c] + ring_index(L, c, bx, by + edge_tile(ri), Y0, X0 - 4),
-                      RS::RL * sizeof(rt), bar);
+            const rt *src = ring[c] + ring_index(L, c, bx, by + edge_tile(ri), Y0, X0 - 4);
+            if (CPLBM_IN_RING(L, cur, c, src, RS::RL))
+                bulk_load(s_ring + RS::NCOL + ri * RS::RL, src, RS::RL * sizeof(rt), bar);
         }
     }
     if (threadIdx.x < 16) {
         const int ci = threadIdx.x / 4, ri = threadIdx.x % 4;
         const int c = row_is_below(ri) ? (col_is_left(ci) ? R_BL : R_BR)
                                        : (col_is_left(ci) ? R_TL : R_TR);
-        cp_async<sizeof(rt)>(s_ring + RS::NCOL + RS::NROW + threadIdx.x,
-                             ring[c] + ring_index(L, c, bx + edge_tile(ci),
-                                                  by + edge_tile(ri), 0, 0));
+        const rt *src = ring[c] + ring_index(L, c, bx + edge_tile(ci), by + edge_tile(ri), 0, 0);
+        if (CPLBM_IN_RING(L, cur, c, src, 1))
+            cp_async<sizeof(rt)>(s_ring + RS::NCOL + RS::NROW + threadIdx.x, src);
     }
     cp_async_commit();
 }
@@ -658,7 +679,8 @@ __device__ __forceinline__ void stage_ring_wrapped(const Lattice &L, int cur, in
             idx = ring_index(L, c, neighbour_tile(X0, edge_tile(ci), TX, L.nx, true),
                              neighbour_tile(Y0, edge_tile(ri), TY, L.nyf, !walls), 0, 0);
         }
-        if (valid) cp_async<sizeof(rt)>(s_ring + p, ring[c] + idx);
+        if (valid && CPLBM_IN_RING(L, cur, c, ring[c] + idx, 1))
+            cp_async<sizeof(rt)>(s_ring + p, ring[c] + idx);
         else s_ring[p] = rt(0);
     }
     cp_async_commit();
@@ -765,16 +787,18 @@ __device__ __forceinline__ void seam_fix_load(const Lattice &L, int cur, int X0,
         if (!seam_rho_slot<TX, TY>(e, t, ly, c)) continue;
         // fluid rows only: with walls the row needs no wrap
         const int x = wrapi(X0 - 4 + c, L.nx), r = wrapi(Y0 - 2 + ly, L.nyf);
-        fix_rho[t] = (typename S::real)R[(long long)r * L.pitch + x];
+        const rt *q = R + (long long)r * L.pitch + x;
+        fix_rho[t] = CPLBM_IN_RHO(L, cur, q, 1) ? (typename S::real)*q : typename S::real(0);
     }
     if (PARITY == 1) {
         const pop_t *A = (const pop_t *)L.pops;
         for (int t = threadIdx.x; t < SL::POP; t += NT) {
             int i, lx, ly;
             if (!seam_pop_slot<TX, TY>(e, t, i, lx, ly)) continue;
-            fix_pop[t] = WALLS ? A[aa_read_index(L, 1, i, Y0 + ly, X0 + lx)]
-                               : A[pidx(L, opp(i), wrapi(Y0 + ly - ey(i), L.nyf),
-                                        wrapi(X0 + lx - ex(i), L.nx))];
+            const pop_t *q = WALLS ? A + aa_read_index(L, 1, i, Y0 + ly, X0 + lx)
+                                   : A + pidx(L, opp(i), wrapi(Y0 + ly - ey(i), L.nyf),
+                                              wrapi(X0 + lx - ex(i), L.nx));
+            fix_pop[t] = CPLBM_IN_POPS(L, q, 1) ? *q : pop_t(0);
         }
     }
 }
@@ -1175,7 +1199,7 @@ __device__ __forceinline__ bool step_tile_tma(const Lattice &L, int cur, int X0,
                                                            (ey(i) > 0 && wall_t));
                     const int o = into_wall ? (opp(i) - 1) * (int)L.plane
                                             : woff[i] + (ey(i) < 0 ? cyb : ey(i) > 0 ? cyt : 0);
-                    st_real(Arow + o, fp[i]);
+                    if (CPLBM_IN_POPS(L, Arow + o, 1)) st_real(Arow + o, fp[i]);
                 }
             }
 
@@ -1215,8 +1239,8 @@ __device__ __forceinline__ bool step_tile_tma(const Lattice &L, int cur, int X0,
                 first = done;
                 first_c = done_c;
             } else if (row_ok) {
-                Rn[(long long)(Y0 + ly - 1) * L.pitch + X0 + lx] = (rho_t)done;
-                if (col_lane) ring[cls_c][ring_index(L, R_L, bxc, by, Y0 + ly - 1, xc)] = (rho_t)done_c;
+                put_rho(L, nxt, Rn, (long long)(Y0 + ly - 1) * L.pitch + X0 + lx, (rho_t)done);
+                if (col_lane) put_ring(L, nxt, ring, cls_c, ring_index(L, R_L, bxc, by, Y0 + ly - 1, xc), (rho_t)done_c);
             }
             pend = same + up_prev;
             pend_c = same_c + up_prev_c;
@@ -1242,8 +1266,8 @@ __device__ __forceinline__ bool step_tile_tma(const Lattice &L, int cur, int X0,
             top_c += s_down[(warp + 1) * XW + slot_c];
         }
         if (!walls_ok || ly0 + PER - 1 < hy) {
-            Rn[(long long)(Y0 + ly0 + PER - 1) * L.pitch + X0 + lx] = (rho_t)top;
-            if (col_lane) ring[cls_c][ring_index(L, R_L, bxc, by, Y0 + ly0 + PER - 1, xc)] = (rho_t)top_c;
+            put_rho(L, nxt, Rn, (long long)(Y0 + ly0 + PER - 1) * L.pitch + X0 + lx, (rho_t)top);
+            if (col_lane) put_ring(L, nxt, ring, cls_c, ring_index(L, R_L, bxc, by, Y0 + ly0 + PER - 1, xc), (rho_t)top_c);
         }
         // first row: add the warp below's last-row "up"
         if (warp > 0) {
@@ -1251,8 +1275,8 @@ __device__ __forceinline__ bool step_tile_tma(const Lattice &L, int cur, int X0,
             first_c += s_up[(warp - 1) * XW + slot_c];
         }
         if (!walls_ok || ly0 < hy) {
-            Rn[(long long)(Y0 + ly0) * L.pitch + X0 + lx] = (rho_t)first;
-            if (col_lane) ring[cls_c][ring_index(L, R_L, bxc, by, Y0 + ly0, xc)] = (rho_t)first_c;
+            put_rho(L, nxt, Rn, (long long)(Y0 + ly0) * L.pitch + X0 + lx, (rho_t)first);
+            if (col_lane) put_ring(L, nxt, ring, cls_c, ring_index(L, R_L, bxc, by, Y0 + ly0, xc), (rho_t)first_c);
         }
     }
     // ring rows below and above the tile, with their corners (none across a
@@ -1261,15 +1285,15 @@ __device__ __forceinline__ bool step_tile_tma(const Lattice &L, int cur, int X0,
     const int bxr = neighbour_tile(X0, 1, TX, L.nx, seam);
     if (warp == 0 && !(walls_ok && edge.wb)) {
         const int byb = neighbour_tile(Y0, -1, TY, L.nyf, seam);
-        ring[R_T][ring_index(L, R_T, bx, byb, Y0 - 1, X0 + lx)] = (rho_t)s_down[lane];
-        if (lane == 0) ring[R_TR][ring_index(L, R_TR, bxl, byb, Y0 - 1, X0 - 1)] = (rho_t)s_down[TX];
-        if (lane == 31) ring[R_TL][ring_index(L, R_TL, bxr, byb, Y0 - 1, X0 + TX)] = (rho_t)s_down[TX + 1];
+        put_ring(L, nxt, ring, R_T, ring_index(L, R_T, bx, byb, Y0 - 1, X0 + lx), (rho_t)s_down[lane]);
+        if (lane == 0) put_ring(L, nxt, ring, R_TR, ring_index(L, R_TR, bxl, byb, Y0 - 1, X0 - 1), (rho_t)s_down[TX]);
+        if (lane == 31) put_ring(L, nxt, ring, R_TL, ring_index(L, R_TL, bxr, byb, Y0 - 1, X0 + TX), (rho_t)s_down[TX + 1]);
     }
     if (warp == NW - 1 && !(walls_ok && edge.wt)) {
         const int byt = neighbour_tile(Y0, 1, TY, L.nyf, seam);
-        ring[R_B][ring_index(L, R_B, bx, byt, Y0 + TY, X0 + lx)] = (rho_t)up_prev;
-        if (lane == 0) ring[R_BR][ring_index(L, R_BR, bxl, byt, Y0 + TY, X0 - 1)] = (rho_t)up_prev_c;
-        if (lane == 31) ring[R_BL][ring_index(L, R_BL, bxr, byt, Y0 + TY, X0 + TX)] = (rho_t)up_prev_c;
+        put_ring(L, nxt, ring, R_B, ring_index(L, R_B, bx, byt, Y0 + TY, X0 + lx), (rho_t)up_prev);
+        if (lane == 0) put_ring(L, nxt, ring, R_BR, ring_index(L, R_BR, bxl, byt, Y0 + TY, X0 - 1), (rho_t)up_prev_c);
+        if (lane == 31) put_ring(L, nxt, ring, R_BL, ring_index(L, R_BL, bxr, byt, Y0 + TY, X0 + TX), (rho_t)up_prev_c);
     }
     return true;
 }
@@ -1653,10 +1677,11 @@ __device__ __forceinline__ bool step_tile_tma_pair(const Lattice &L, int cur, in
                     pop_t *dst = into_wall ? Arow + (opp(i) - 1) * (int)L.plane
                                            : Arow + woff[i] + (ey(i) < 0 ? cyb : ey(i) > 0 ? cyt : 0);
                     if (PARITY == 0 || ex(i) == 0 || into_wall) {
-                        st_pair(dst, fp[i]);
+                        if (CPLBM_IN_POPS(L, dst, 2)) st_pair(dst, fp[i]);
                     } else {
-                        st_real(dst + (ex(i) < 0 ? cxl : 0), fp[i].x);
-                        st_real(dst + 1 + (ex(i) > 0 ? cxr : 0), fp[i].y);
+                        pop_t *d0 = dst + (ex(i) < 0 ? cxl : 0), *d1 = dst + 1 + (ex(i) > 0 ? cxr : 0);
+                        if (CPLBM_IN_POPS(L, d0, 1)) st_real(d0, fp[i].x);
+                        if (CPLBM_IN_POPS(L, d1, 1)) st_real(d1, fp[i].y);
                     }
                 }
             }
@@ -1698,9 +1723,8 @@ __device__ __forceinline__ bool step_tile_tma_pair(const Lattice &L, int cur, in
                 first = done;
                 first_c = done_c;
             } else if (row_ok) {
-                *reinterpret_cast<float2 *>(Rn + (long long)(Y0 + ly - 1) * L.pitch +
-                                            X0 + x0) = done;
-                if (col_lane) ring[cls_c][ring_index(L, R_L, bxc, by, Y0 + ly - 1, xc)] = done_c;
+                put_rho(L, nxt, Rn, (long long)(Y0 + ly - 1) * L.pitch + X0 + x0, done);
+                if (col_lane) put_ring(L, nxt, ring, cls_c, ring_index(L, R_L, bxc, by, Y0 + ly - 1, xc), done_c);
             }
             pend = padd(same, up_prev);
             pend_c = same_c + up_prev_c;
@@ -1723,31 +1747,29 @@ __device__ __forceinline__ bool step_tile_tma_pair(const Lattice &L, int cur, in
             top_c += s_down[(warp + 1) * XW + slot_c];
         }
         if (!walls_ok || ly0 + PER - 1 < hy) {
-            *reinterpret_cast<float2 *>(Rn + (long long)(Y0 + ly0 + PER - 1) * L.pitch + X0 +
-                                        x0) = top;
-            if (col_lane) ring[cls_c][ring_index(L, R_L, bxc, by, Y0 + ly0 + PER - 1, xc)] = top_c;
+            put_rho(L, nxt, Rn, (long long)(Y0 + ly0 + PER - 1) * L.pitch + X0 + x0, top);
+            if (col_lane) put_ring(L, nxt, ring, cls_c, ring_index(L, R_L, bxc, by, Y0 + ly0 + PER - 1, xc), top_c);
         }
         if (warp > 0) {
             first = padd(first, *reinterpret_cast<const float2 *>(s_up + (warp - 1) * XW + x0));
             first_c += s_up[(warp - 1) * XW + slot_c];
         }
         if (!walls_ok || ly0 < hy) {
-            *reinterpret_cast<float2 *>(Rn + (long long)(Y0 + ly0) * L.pitch + X0 + x0) = first;
-            if (col_lane) ring[cls_c][ring_index(L, R_L, bxc, by, Y0 + ly0, xc)] = first_c;
+            put_rho(L, nxt, Rn, (long long)(Y0 + ly0) * L.pitch + X0 + x0, first);
+            if (col_lane) put_ring(L, nxt, ring, cls_c, ring_index(L, R_L, bxc, by, Y0 + ly0, xc), first_c);
         }
     }
     // ring rows below and above the tile, with their corners (none across a
     // wall)
     if (warp == 0 && !(walls_ok && edge.wb)) {
-        *reinterpret_cast<float2 *>(ring[R_T] + ring_index(L, R_T, bx, byb, Y0 - 1, X0 + x0)) =
-            *reinterpret_cast<const float2 *>(s_down + x0);
-        if (lane == 0) ring[R_TR][ring_index(L, R_TR, bxl, byb, Y0 - 1, X0 - 1)] = s_down[TX];
-        if (lane == 31) ring[R_TL][ring_index(L, R_TL, bxr, byb, Y0 - 1, X0 + TX)] = s_down[TX + 1];
+        put_ring(L, nxt, ring, R_T, ring_index(L, R_T, bx, byb, Y0 - 1, X0 + x0), *reinterpret_cast<const float2 *>(s_down + x0));
+        if (lane == 0) put_ring(L, nxt, ring, R_TR, ring_index(L, R_TR, bxl, byb, Y0 - 1, X0 - 1), s_down[TX]);
+        if (lane == 31) put_ring(L, nxt, ring, R_TL, ring_index(L, R_TL, bxr, byb, Y0 - 1, X0 + TX), s_down[TX + 1]);
     }
     if (warp == NW - 1 && !(walls_ok && edge.wt)) {
-        *reinterpret_cast<float2 *>(ring[R_B] + ring_index(L, R_B, bx, byt, Y0 + TY, X0 + x0)) = up_prev;
-        if (lane == 0) ring[R_BR][ring_index(L, R_BR, bxl, byt, Y0 + TY, X0 - 1)] = up_prev_c;
-        if (lane == 31) ring[R_BL][ring_index(L, R_BL, bxr, byt, Y0 + TY, X0 + TX)] = up_prev_c;
+        put_ring(L, nxt, ring, R_B, ring_index(L, R_B, bx, byt, Y0 + TY, X0 + x0), up_prev);
+        if (lane == 0) put_ring(L, nxt, ring, R_BR, ring_index(L, R_BR, bxl, byt, Y0 + TY, X0 - 1), up_prev_c);
+        if (lane == 31) put_ring(L, nxt, ring, R_BL, ring_index(L, R_BL, bxr, byt, Y0 + TY, X0 + TX), up_prev_c);
     }
     return true;
 }
