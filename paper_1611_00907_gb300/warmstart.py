@@ -91,10 +91,14 @@ def cold_field(case, nx, ny):
     return inputs.wall_drop(nx, ny, r, case["rho_l"], case["rho_v"], width)
 
 
-def warm_field(case, pred, nx, ny):
-    """A circular cap of the same area meeting the wall at the predicted
-    angle, with the predicted bulk densities and interface width."""
+def warm_field(case, pred, nx, ny, mass=None):
+    """A circular cap meeting the wall at the predicted angle, with the
+    predicted bulk densities and interface width: of the case's area, or,
+    with `mass`, of the area that gives the fluid rows that total density
+    (mass_matched_area)."""
     th = math.radians(min(max(pred["theta"], 5.0), 175.0))
+    if mass is not None:
+        case = dict(case, area=mass_matched_area(case, pred, nx, ny, mass))
     area = case["area"] * nx * (ny - 2)
     R = math.sqrt(area / (th - math.sin(th) * math.cos(th)))
     yy, xx = np.mgrid[0:ny, 0:nx].astype(np.float64)
@@ -104,6 +108,26 @@ def warm_field(case, pred, nx, ny):
     rv = max(pred["rho_v"], 1e-6)
     W = min(max(pred["width"], 1.0), 12.0)
     return inputs.tanh_profile(d, rl, rv, W)
+
+
+def fluid_mass(rho):
+    """Total density of the fluid rows (rows 0 and ny - 1 are solid)."""
+    return float(np.asarray(rho)[1:-1].sum())
+
+
+def mass_matched_area(case, pred, nx, ny, mass, iters=4):
+    """Area fraction of the warm cap whose fluid rows hold `mass` (the cold
+    start's): the same system, with the same total mass, as the cold start,
+    so that both relax to one equilibrium.  Mass grows with the cap's area at
+    the rate rho_l - rho_v per node; a few corrections settle the tanh
+    profile's share."""
+    rl = pred["rho_l"] if pred["rho_l"] > pred["rho_v"] else case["rho_l"]
+    rv = max(pred["rho_v"], 1e-6)
+    c = dict(case)
+    for _ in range(iters):
+        m = fluid_mass(warm_field(c, pred, nx, ny))
+        c["area"] += (mass - m) / ((rl - rv) * nx * (ny - 2))
+    return c["area"]
 
 
 # A settled drop (the convergence test of the sweep comparison): between two
@@ -244,8 +268,9 @@ def compare(model, cases, nx, ny, max_steps, check_every=200, tol=1e-6,
     preds = model.predict(cases)
     cold = run_batch(cases, [cold_field(c, nx, ny) for c in cases], nx, ny,
                      max_steps, check_every, tol, stream=stream, settle=settle)
-    warm = run_batch(cases, [warm_field(c, p, nx, ny) for c, p in
-                             zip(cases, preds)], nx, ny, max_steps,
+    # the warm cap holds the cold start's mass: the same system
+    warm = run_batch(cases, [warm_field(c, p, nx, ny, mass=fluid_mass(cold_field(c, nx, ny)))
+                             for c, p in zip(cases, preds)], nx, ny, max_steps,
                      check_every, tol, stream=stream, settle=settle)
     both = (cold[0] < max_steps) & (warm[0] < max_steps)
     err = {"rho_l": [], "rho_v": [], "theta": []}

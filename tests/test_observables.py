@@ -114,3 +114,24 @@ def test_surface_tension_from_the_bulk_pressure_matches_the_oracle(Tr):
         lambda v: eos_pressure("cs", 1.0, 4.0, 1.0, Tr, 0.344, v), rv, rl, 0.5)
     want = thermo.surface_tension(thermo.make_eos("cs", 1.0, 4.0, 1.0, Tr), 0.5)
     assert got == pytest.approx(want, rel=1e-7)
+
+
+@pytest.mark.parametrize("theta", [30, 90, 150])
+def test_warm_cap_holds_the_requested_mass(theta):
+    """The mass-matched warm cap carries exactly the total density asked for
+    (the cold start's), whatever its angle and densities, and without a
+    target keeps the case's area."""
+    nx, ny = 256, 128
+    case = dict(CASE, area=0.1)
+    cold = inputs.wall_drop(nx, ny, math.sqrt(2 * 0.1 * nx * (ny - 2) / math.pi),
+                            2.0, 0.05, 4.0)
+    M = ws.fluid_mass(cold)
+    pred = dict(theta=theta, rho_l=1.97, rho_v=0.058, width=3.0)
+    rho = ws.warm_field(case, pred, nx, ny, mass=M)
+    assert abs(ws.fluid_mass(rho) / M - 1) < 1e-6
+    # the cap grows when the case's area at these densities holds too little
+    # mass, and shrinks when it holds too much
+    plain = ws.warm_field(case, pred, nx, ny)
+    grew = (rho[1:-1] > 1.0).sum() > (plain[1:-1] > 1.0).sum()
+    assert grew == (ws.fluid_mass(plain) < M)
+    assert abs(ws.fluid_mass(ws.warm_field(case, pred, nx, ny, mass=1.05 * M)) / (1.05 * M) - 1) < 1e-6
