@@ -1971,7 +1971,8 @@ __global__ void __launch_bounds__(NT, HasTmaPair<S, TX, TY, NT>::value
 // work counter and no per-item wait on one.  The CTA stages its items in
 // shared memory with one load, so no tile waits on a global read of the
 // next item.  Consecutive items mostly belong to one lattice: its
-// descriptor is copied to shared memory once per CTA, and per_cta
+// descriptor is copied to shared memory when the CTA's lattice changes, not
+// per item, and per_cta
 // (lbm_batch_autotune) trades that saving against the balance of the last
 // CTAs.  The tensor maps come as a kernel parameter (BatchMaps, up to
 // BATCH_LAUNCH_LATTICES lattices from inst0 on): a map in global memory,
