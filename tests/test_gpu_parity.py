@@ -614,36 +614,14 @@ def test_fp16_storage_tma_path(tile, size, monkeypatch):
         assert _rel(run["rho"], want["rho"]) < 2e-3
 
 
-EPS_HALF = 2.0 ** -11  # unit roundoff of IEEE binary16 (round to nearest)
-
-
 @pytest.mark.parametrize("tile", [(32, 16), (32, 32), (64, 16), (64, 32)])
 @pytest.mark.parametrize("size", [(330, 200), (192, 96)])   # 192 x 96: seam tiles
 @pytest.mark.parametrize("steps", [20, 21])                 # both in-place parities
 def test_fp16_storage_against_the_oracle(tile, size, steps):
     """Density, chemical potential and reported velocity of the FP16-offset
-    storage against the FP64 oracle, within bounds that follow from the
-    half-precision unit roundoff u.
-
-    Every step stores each moving population once, as g_i = f_i - w_i rho_ref
-    in half: an error of at most u |g_i| <= u w_i A, A = max |f_i / w_i -
-    rho_ref|.  A node's density sums eight such values, sum w_i = 5/9: one
-    step adds at most (5/9) u A.  The roundings of successive steps are
-    independent, and density and momentum are conserved, so each step's
-    error spreads over the lattice (over ~t nodes after t steps) instead of
-    piling up at one node: a node collects sum_t 1/t ~ 1 + ln n of one step's
-    variance, K(n) = sqrt(1 + ln n), and
-        d_rho <= (5/9) u A K(n).
-    mu = psi'(rho) - kappa lap(rho) (Eq. 8): the spread error passes through
-    psi'', the last step's fresh error through the Laplacian's stencil, whose
-    weights sum to 40/6 in magnitude:
-        d_mu <= max|psi''| d_rho + kappa (40/6) (5/9) u A.
-    v = (sum_i f_i e_i)/rho + F/(2 rho), F = -rho grad mu + c_s^2 grad rho
-    (Eq. 12, Sec. II): the momentum takes sum_i w_i |e_ix| u A = u A / 3 per
-    step, spread as the density's; grad mu / 2 takes d_mu; c_s^2 grad rho /
-    (2 rho) takes d_rho / (3 rho):
-        d_v <= (u A K(n) / 3 + d_rho / 3) / rho_min + d_mu.
-    A factor 2 covers the propagation through collision and streaming."""
+    storage against the FP64 oracle, within the bounds that follow from the
+    half-precision unit roundoff (derived in tests/fp16_bounds.py)."""
+    from fp16_bounds import check, run_with_bounds
     kind, a, b, Tr, kappa, tau = EOS_CASES["cs"]
     e = thermo.make_eos(kind, a, b, 1.0, Tr, 0.344)
     rv, rl = _coexistence("cs")
@@ -654,24 +632,8 @@ def test_fp16_storage_against_the_oracle(tile, size, steps):
         sim.set_tile(*tile)
         sim.init(rho).step(steps)
         got = sim.moments()
-    ref.init_equilibrium(rho)
-    A = 0.0
-    for n in range(steps + 1):
-        if n:
-            ref.step(1)
-        A = max(A, float(np.abs(ref.f[1:] / oracle.W[1:, None, None] - rho_ref).max()))
-    want = ref.moments()
-    grid = np.linspace(want["rho"].min(), want["rho"].max(), 2001)
-    psi2 = np.abs(thermo.dp0_drho(kind, a, b, 1.0, e.T, e.alpha, grid) / grid).max()
-    K = np.sqrt(1 + np.log(steps))
-    d_rho = (5 / 9) * EPS_HALF * A * K
-    d_mu = psi2 * d_rho + kappa * (40 / 6) * (5 / 9) * EPS_HALF * A
-    d_v = (EPS_HALF * A * K / 3 + d_rho / 3) / want["rho"].min() + d_mu
-    for key, bound in (("rho", d_rho), ("mu", d_mu), ("vx", d_v), ("vy", d_v)):
-        err = np.abs(got[key] - want[key]).max()
-        assert err <= 2 * bound, (key, err, bound)
-        # the bounds must mean something: well below the field's own size
-        assert 2 * bound < 0.2 * np.abs(want[key]).max(), (key, bound)
+    want, bounds = run_with_bounds(ref, rho, steps, rho_ref, e, kappa)
+    check(got, want, bounds, (tile, size, steps))
 
 
 def test_moments_subset_into_caller_buffers():
