@@ -47,9 +47,13 @@ def _cfg(**kw):
 
 
 @pytest.mark.parametrize("bad", [dict(tau=0.5), dict(tau=float("nan")),
-                                 dict(nx=4), dict(ny=3), dict(walls=2),
-                                 dict(kappa=-1.0), dict(precision=7),
-                                 dict(walls=1, ny=6)])
+                                 dict(tau=float("inf")), dict(nx=4), dict(ny=3),
+                                 dict(walls=2), dict(kappa=-1.0),
+                                 dict(kappa=float("nan")), dict(precision=7),
+                                 dict(precision=-1), dict(walls=1, ny=6),
+                                 dict(rho_ref=float("inf")),
+                                 # the largest lattice: 2^31 nodes
+                                 dict(nx=65536, ny=32769)])
 def test_create_rejects_invalid_configuration(lib, bad):
     ctx = C.c_void_p()
     cfg = _cfg(**bad)
@@ -57,6 +61,19 @@ def test_create_rejects_invalid_configuration(lib, bad):
     assert st == _lib.LBM_ERR_ARG
     assert ctx.value is None
     assert lib.lbm_last_error(None)
+
+
+def test_batch_create_rejects_empty_and_bad_precision(lib):
+    b = C.c_void_p()
+    inst = (_lib.LbmInstance * 1)()
+    assert lib.lbm_batch_create(inst, 0, 1, None, 0, C.byref(b)) == _lib.LBM_ERR_ARG
+    assert lib.lbm_batch_create(inst, 1, 9, None, 0, C.byref(b)) == _lib.LBM_ERR_ARG
+    assert lib.lbm_batch_create(None, 1, 1, None, 0, C.byref(b)) == _lib.LBM_ERR_ARG
+    assert b.value is None
+    assert lib.lbm_batch_last_error(None)
+    assert lib.lbm_batch_step(None, 1) == _lib.LBM_ERR_ARG
+    assert lib.lbm_batch_schedule(None, 1, None) == _lib.LBM_ERR_ARG
+    lib.lbm_batch_destroy(None)
 
 
 def test_null_arguments_are_errors_not_crashes(lib):
