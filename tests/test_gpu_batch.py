@@ -352,3 +352,33 @@ def test_batch_grid_per_lattice_on_one_geometry(sweep, tile, precision):
                     (("rho", 1e-4), ("mu", 1e-4), ("vx", 3e-4), ("vy", 3e-4)))
             for key, tol in tols:
                 assert _rel(got[key], want[key]) < tol, (k, key)
+
+
+def test_batch_with_no_lattice_in_the_launch_and_zero_steps():
+    """Degenerate schedules: zero steps change nothing; with every lattice
+    out of the launch a step launches nothing and only counts; back in, the
+    lattices continue from where they stopped."""
+    inst = _instances(SPECS[:3])
+    with Batch([d for d, _, _ in inst], precision="f64") as b:
+        for k, (_, _, rho) in enumerate(inst):
+            b.init(k, rho)
+        b.step(0)
+        b.step(4)
+        before = [b.populations(k) for k in range(len(inst))]
+        for k in range(len(inst)):
+            b.set_active(k, False)
+        b.step(6)
+        b.step(0)
+        assert b.info()["steps"] == 10
+        for k in range(len(inst)):
+            assert np.array_equal(b.populations(k), before[k])
+            b.set_active(k, True)
+        b.step(3)
+        for k, (d, e, rho) in enumerate(inst):
+            ref = oracle.Lattice(d["nx"], d["ny"], e, d["tau"], d["kappa"],
+                                 walls=d.get("walls", False),
+                                 mu_bottom=d["mu_bottom"])
+            ref.init_equilibrium(rho).step(7)
+            got = b.moments(k)
+            for key in ("rho", "mu", "vx", "vy"):
+                assert _rel(got[key], ref.moments()[key]) < 1e-12, (k, key)
