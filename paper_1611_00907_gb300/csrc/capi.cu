@@ -248,6 +248,10 @@ cudaError_t clear_rings(const Lattice &L, cudaStream_t s)
 
 void free_all(lbm_ctx *c)
 {
+    if (c->graph) cudaGraphExecDestroy(c->graph);
+    if (c->capture_stream) cudaStreamDestroy(c->capture_stream);
+    c->graph = nullptr;
+    c->capture_stream = nullptr;
     Lattice &L = c->L;
     dev_free(L.pops);
     for (int k = 0; k < 2; ++k) {
@@ -291,6 +295,67 @@ struct StateHeader {
     int nx, ny, walls, precision;
     long long t;
 };
+
+// Steps replayed per CUDA graph launch (from an even step: both in-place
+// parities in turn).
+constexpr int STEP_GRAPH_STEPS = 16;
+
+cudaError_t launch_one_step(lbm_ctx *c, cudaStream_t s)
+{
+    const int p = (int)(c->t & 1);
+    return c->force_model == 1 ? launch_step_pt(c->L, p, p, s, &c->maps)
+                               : launch_step(c->L, p, p, s, &c->maps);
+}
+
+// The graph of STEP_GRAPH_STEPS steps from an even step, captured on a
+// private stream (the caller's may be the legacy stream, which cannot
+// capture) and launched on the caller's.  Its kernels carry the lattice
+// descriptor and tensor maps by value: a change of tile shape, physics,
+// force model or wait limit since the capture makes a new one.  Returns
+// false (direct launches) when capture is not possible.
+bool step_graph(lbm_ctx *c)
+{
+    if (c->graph_failed) return false;
+    // the caller capturing on its stream: direct launches join its graph
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (c->stream && (cudaStreamIsCapturing(c->stream, &cs) != cudaSuccess ||
+                      cs != cudaStreamCaptureStatusNone))
+        return false;
+    if (c->graph && std::memcmp(&c->graph_L, &c->L, sizeof(Lattice)) == 0 &&
+        std::memcmp(&c->graph_maps, &c->maps, sizeof(TmaMaps)) == 0 &&
+        c->graph_force == c->force_model)
+        return true;
+    if (c->graph) cudaGraphExecDestroy(c->graph);
+    c->graph = nullptr;
+    if (!c->capture_stream &&
+        cudaStreamCreateWithFlags(&c->capture_stream, cudaStreamNonBlocking) != cudaSuccess) {
+        c->capture_stream = nullptr;
+        c->graph_failed = true;
+        return false;
+    }
+    const long long t0 = c->t;
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaStreamBeginCapture(c->capture_stream, cudaStreamCaptureModeThreadLocal);
+    const bool capturing = e == cudaSuccess;
+    for (int k = 0; k < STEP_GRAPH_STEPS && e == cudaSuccess; ++k, ++c->t)
+        e = launch_one_step(c, c->capture_stream);
+    c->t = t0;
+    const cudaError_t e2 = capturing ? cudaStreamEndCapture(c->capture_stream, &g) : cudaSuccess;
+    if (e == cudaSuccess && e2 == cudaSuccess)
+        e = cudaGraphInstantiate(&c->graph, g, 0);
+    if (g) cudaGraphDestroy(g);
+    if (e != cudaSuccess || e2 != cudaSuccess) {
+        cudaGetLastError();  // the direct launches report their own errors
+        c->graph = nullptr;
+        c->graph_failed = true;
+        return false;
+    }
+    // byte copies: the comparison above covers padding bytes too
+    std::memcpy(&c->graph_L, &c->L, sizeof(Lattice));
+    std::memcpy(&c->graph_maps, &c->maps, sizeof(TmaMaps));
+    c->graph_force = c->force_model;
+    return true;
+}
 
 }  // namespace
 
@@ -743,12 +808,19 @@ lbm_status lbm_step(lbm_ctx *c, int nsteps)
     if (nsteps < 0) return fail(c, LBM_ERR_ARG, "nsteps must be >= 0");
     if (!c->initialized) return fail(c, LBM_ERR_STATE, "lbm_init must come first");
     CUDA_TRY(c, cudaSetDevice(c->device));
-    for (int k = 0; k < nsteps; ++k) {
-        const int p = (int)(c->t & 1);
-        if (c->force_model == 1)
-            CUDA_TRY(c, launch_step_pt(c->L, p, p, c->stream, &c->maps));
-        else
-            CUDA_TRY(c, launch_step(c->L, p, p, c->stream, &c->maps));
+    int left = nsteps;
+    if (left > 0 && (c->t & 1)) {  // graphs start on an even step
+        CUDA_TRY(c, launch_one_step(c, c->stream));
+        ++c->t;
+        --left;
+    }
+    while (left >= STEP_GRAPH_STEPS && step_graph(c)) {
+        CUDA_TRY(c, cudaGraphLaunch(c->graph, c->stream));
+        c->t += STEP_GRAPH_STEPS;
+        left -= STEP_GRAPH_STEPS;
+    }
+    for (; left > 0; --left) {
+        CUDA_TRY(c, launch_one_step(c, c->stream));
         ++c->t;
     }
     return LBM_OK;

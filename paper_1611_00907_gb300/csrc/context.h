@@ -24,6 +24,15 @@ struct lbm_ctx {
     cplbm::TmaMaps maps{};            // tensor maps of the TMA interior path
     bool use_tma = true;
     int force_model = 0;       // 0 chemical potential (Eq. 12), 1 Eq. 5
+    // lbm_step replays blocks of steps from a captured CUDA graph (capi.cu,
+    // step_graph): the graph, the stream it was captured on, and the launch
+    // parameters it holds, compared before each replay
+    cudaGraphExec_t graph = nullptr;
+    cudaStream_t capture_stream = nullptr;
+    cplbm::Lattice graph_L{};
+    cplbm::TmaMaps graph_maps{};
+    int graph_force = -1;
+    bool graph_failed = false;  // capture refused: direct launches only
     std::string err;
 };
 

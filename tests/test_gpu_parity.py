@@ -647,3 +647,72 @@ def test_moments_subset_into_caller_buffers():
         assert np.array_equal(buf, full["rho"]) and np.array_equal(part["mu"], full["mu"])
         with pytest.raises(ValueError):
             sim.moments(fields=("rho",), out={"rho": np.zeros((21, 70), np.float32)})
+
+
+@pytest.mark.parametrize("own_stream", [False, True])
+def test_step_graphs_follow_every_change(own_stream):
+    """lbm_step replays blocks of 16 steps from a captured CUDA graph whose
+    kernels hold the lattice's parameters: a change of tile shape, wall
+    chemical potential or wait limit between calls must reach the replayed
+    steps (the graph is captured again), on the legacy stream and on a
+    stream of the caller's, and odd step counts fall back to single
+    launches in between."""
+    import torch
+    nx, ny = 192, 66
+    kind, a, b, Tr, kappa, tau = EOS_CASES["cs"]
+    e = thermo.make_eos(kind, a, b, 1.0, Tr, 0.344)
+    rv, rl, mc, _ = thermo.maxwell(e)
+    rho = inputs.wall_drop(nx, ny, 24, rl, rv, 4.0)
+    stream = torch.cuda.Stream() if own_stream else None
+    sim = Simulation(nx, ny, kind, a, b, 1.0, Tr, omega=0.344, tau=tau, kappa=kappa,
+                     walls=True, precision="f64", mu_bottom=mc + 0.01,
+                     stream=stream.cuda_stream if stream else None)
+    ref = oracle.Lattice(nx, ny, e, tau, kappa, walls=True, mu_bottom=mc + 0.01)
+    lib = _lib_module().load()
+    with sim:
+        sim.init(rho)
+        ref.init_equilibrium(rho)
+        sim.step(37)                      # graphs, then single launches
+        ref.step(37)
+        sim.set_tile(64, 32)
+        sim.step(33)                      # one single launch, then graphs
+        ref.step(33)
+        sim.set_wall_mu(mc - 0.02)
+        ref.mu_bottom = mc - 0.02
+        sim.step(32)
+        ref.step(32)
+        assert lib.lbm_test_set_wait_cycles(sim._ctx, 1 << 40) == 0
+        sim.step(16)
+        ref.step(16)
+        _compare(sim, ref, 1e-11)
+
+
+def test_steps_inside_a_callers_graph_capture():
+    """A caller capturing lbm_step into its own CUDA graph gets every step
+    in it (the library does not capture a graph of its own meanwhile)."""
+    import torch
+    sim, ref, rho = _setup("cs", 128, 64, False)
+    stream = torch.cuda.Stream()
+    sim.close()
+    kind, a, b, Tr, kappa, tau = EOS_CASES["cs"]
+    sim = Simulation(128, 64, kind, a, b, 1.0, Tr, omega=0.344, tau=tau, kappa=kappa,
+                     precision="f64", stream=stream.cuda_stream)
+    with sim:
+        sim.init(rho).step(2)             # kernel attributes set outside the capture
+        sim.init(rho)
+        torch.cuda.synchronize()
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g, stream=stream):
+            sim.step(32)                  # captured into g: 32 kernel launches
+        for _ in range(3):
+            g.replay()
+        torch.cuda.synchronize()
+        ref.init_equilibrium(rho).step(3 * 32)
+        # the capture itself advanced the lattice's step count by 32 without
+        # running anything: the replays did the stepping
+        _compare(sim, ref, 1e-11)
+
+
+def _lib_module():
+    from paper_1611_00907_gb300 import _lib
+    return _lib
