@@ -382,3 +382,37 @@ def test_batch_with_no_lattice_in_the_launch_and_zero_steps():
             got = b.moments(k)
             for key in ("rho", "mu", "vx", "vy"):
                 assert _rel(got[key], ref.moments()[key]) < 1e-12, (k, key)
+
+
+@pytest.mark.parametrize("precision", ["f32", "f16_offset"])
+def test_autotune_over_both_schedules_keeps_the_state(precision):
+    """A batch of one geometry: the autotuner times the grid-per-lattice
+    launch beside the work list at every tile shape, keeps the fastest and
+    leaves every lattice's state and step count as they were; the batch then
+    follows the oracle."""
+    inst = _instances(SWEEPS["walls"])
+    for d, e, rho in inst:
+        rv, rl, _, _ = thermo.maxwell(e)
+        d["rho_ref"] = 0.5 * (rv + rl)
+    with Batch([d for d, _, _ in inst], precision=precision) as b:
+        for k, (_, _, rho) in enumerate(inst):
+            b.init(k, rho)
+        b.step(6)
+        before = [b.populations(k) for k in range(len(inst))]
+        shape = b.autotune(4)
+        assert shape == b.info()["tile"] and b.info()["steps"] == 6
+        assert b.items_per_cta in (0, 1, 2, 4)
+        for k in range(len(inst)):
+            assert np.array_equal(b.populations(k), before[k])
+        b.step(17)
+        for k, (d, e, rho) in enumerate(inst):
+            ref = oracle.Lattice(d["nx"], d["ny"], e, d["tau"], d["kappa"],
+                                 walls=True, mu_bottom=d["mu_bottom"])
+            got = b.moments(k)
+            if precision == "f16_offset":
+                want, bounds = run_with_bounds(ref, rho, 23, d["rho_ref"], e, d["kappa"])
+                check(got, want, bounds, (k, shape), meaningful=("rho", "mu"))
+            else:
+                want = ref.init_equilibrium(rho).step(23).moments()
+                for key, tol in (("rho", 1e-4), ("mu", 1e-4), ("vx", 3e-4), ("vy", 3e-4)):
+                    assert _rel(got[key], want[key]) < tol, (k, key)
