@@ -135,7 +135,13 @@ lbm_status lbm_set_force_model(lbm_ctx *ctx, int model);
 lbm_status lbm_init(lbm_ctx *ctx, const double *rho, const double *ux,
                     const double *uy, int on_device);
 
-/* Queue nsteps (>= 0) time steps.  Returns without waiting for the GPU. */
+/* Queue nsteps (>= 0) time steps (Sec. II: density, Eq. 8, Eq. 12, the
+ * BGK collision of Eq. 13-14 and streaming, with the wall rule of Sec. IV)
+ * on the context's stream.  Returns without waiting for the GPU.  Blocks of
+ * 16 steps replay a CUDA graph captured on a private stream at the first
+ * such call (and again after any change of tile shape, physics, force
+ * model or wait limit); while the context's stream is being captured by
+ * the caller, every step is a plain launch that joins the caller's graph. */
 lbm_status lbm_step(lbm_ctx *ctx, int nsteps);
 
 /* Macroscopic fields of the current state: rho (solid rows: Eq. 28), the
