@@ -865,18 +865,20 @@ def main():
 
     # The paper's efficiency claim (Sec. II, VI): the chemical-potential force
     # against the pressure-tensor force it replaces, same lattice and tile,
-    # on the TMA tile paths the product runs and on the general paths.
+    # on the TMA tile paths the product runs and on the general paths: FP32
+    # at the default tile (two nodes per lane) and at 32 x 32, FP64 at 32 x 16.
     pt = None
     if args.pt_steps > 0:
         pt = {}
-        for prec, tile in (("f32", (32, 32)), ("f64", (32, 16))):
+        for key, prec, tile in (("f32", "f32", (64, 16)), ("f32_32x32", "f32", (32, 32)),
+                                ("f64", "f64", (32, 16))):
             k = args.pt_steps if prec == "f32" else max(2, args.pt_steps // 10)
-            pt[prec] = {"tile": list(tile), "steps": k}
+            pt[key] = {"tile": list(tile), "steps": k}
             for path, no_tma in (("tma", False), ("general", True)):
                 cp_ms = measure_gpu(prec, k, 3, rho, tile, no_tma=no_tma) / k
-                pt_ms = measure_gpu(prec, k, 3, rho, None, no_tma=no_tma,
+                pt_ms = measure_gpu(prec, k, 3, rho, tile, no_tma=no_tma,
                                     force_model="pressure_tensor") / k
-                pt[prec][path] = {
+                pt[key][path] = {
                     "chemical_potential_mlups": n_nodes / (cp_ms * 1e-3) / 1e6,
                     "pressure_tensor_mlups": n_nodes / (pt_ms * 1e-3) / 1e6,
                     "speedup": pt_ms / cp_ms}

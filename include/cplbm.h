@@ -115,7 +115,8 @@ lbm_status lbm_set_tile(lbm_ctx *ctx, int tx, int ty);
 lbm_status lbm_get_tile(const lbm_ctx *ctx, int *tx, int *ty);
 
 /* Time nsteps (rounded up to an even count >= 2) steps of each compiled
- * tile shape on the context's own lattice, keep the fastest, and restore
+ * tile shape of the force model in use (lbm_set_force_model) on the
+ * context's own lattice, keep the fastest, and restore
  * the state exactly as it was (the step counter included).  Allocates one
  * temporary copy of the state.  *tx, *ty (may be NULL) receive the shape. */
 lbm_status lbm_autotune(lbm_ctx *ctx, int nsteps, int *tx, int *ty);
@@ -124,8 +125,12 @@ lbm_status lbm_autotune(lbm_ctx *ctx, int nsteps, int *tx, int *ty);
  * Eq. 12.  1: the pressure-tensor force it replaces, F = -div(P) +
  * grad(cs^2 rho) with P of Eq. 9 (Eq. 5), same stencils - a baseline for
  * measuring the cost the method avoids; periodic lattices, LBM_F64 or
- * LBM_F32, fixed tile shape (set by this call).  lbm_moments reports v and
- * mu with the chemical-potential definitions in both models. */
+ * LBM_F32.  Model 1 has kernels for tiles 64x16 (FP32, set by this call;
+ * the same two-nodes-per-lane path as the default step) and 32x32 (FP32),
+ * and 32x16 (FP64, set by this call); lbm_set_tile refuses other shapes
+ * while it is in use, and lbm_autotune times its step over those shapes.
+ * lbm_moments reports v and mu with the chemical-potential definitions in
+ * both models. */
 lbm_status lbm_set_force_model(lbm_ctx *ctx, int model);
 
 /* Set the state to equilibrium populations f_i = f_i^eq(rho, u) (Eq. 14)

@@ -588,13 +588,9 @@ lbm_status lbm_set_tile(lbm_ctx *c, int tx, int ty)
     if (!c) return fail(nullptr, LBM_ERR_ARG, "null context");
     if (!step_shape_supported(c->L.precision, tx, ty))
         return fail(c, LBM_ERR_ARG, "no step kernel for tile %d x %d", tx, ty);
-    if (c->force_model == 1) {
-        int px, py;
-        pt_shape(c->L.precision, &px, &py);
-        if (tx != px || ty != py)
-            return fail(c, LBM_ERR_ARG, "the pressure-tensor baseline runs on "
-                        "tiles %d x %d only", px, py);
-    }
+    if (c->force_model == 1 && !pt_shape_supported(c->L.precision, tx, ty))
+        return fail(c, LBM_ERR_ARG, "the pressure-tensor baseline has no "
+                    "kernel for tile %d x %d", tx, ty);
     if (c->initialized && (tx != c->L.tx || ty != c->L.ty)) {
         // The tile grid defines how the current density is split between
         // rho and the partial sums: gather it whole before switching.
@@ -662,19 +658,19 @@ lbm_status lbm_autotune(lbm_ctx *c, int nsteps, int *best_tx, int *best_ty)
     if (st == LBM_OK) e = cudaEventCreate(&e0);
     if (st == LBM_OK && e == cudaSuccess) e = cudaEventCreate(&e1);
     for (int k = 0; k < n && st == LBM_OK && e == cudaSuccess; ++k) {
+        // the shapes of the force model in use, timed with its step
         if (!step_shape_supported(L.precision, tx[k], ty[k])) continue;
+        if (c->force_model == 1 && !pt_shape_supported(L.precision, tx[k], ty[k])) continue;
         L.tx = tx[k];
         L.ty = ty[k];
         refresh_maps(c);
         st = snapshot(c, snap, false);
         c->t = t0;
         for (int w = 0; w < 2 && e == cudaSuccess; ++w, ++c->t)
-            e = launch_step(L, (int)(c->t & 1), (int)(c->t & 1), c->stream,
-                            &c->maps);
+            e = launch_one_step(c, c->stream);
         if (e == cudaSuccess) e = cudaEventRecord(e0, c->stream);
         for (int s = 0; s < nsteps && e == cudaSuccess; ++s, ++c->t)
-            e = launch_step(L, (int)(c->t & 1), (int)(c->t & 1), c->stream,
-                            &c->maps);
+            e = launch_one_step(c, c->stream);
         if (e == cudaSuccess) e = cudaEventRecord(e1, c->stream);
         if (e == cudaSuccess) e = cudaEventSynchronize(e1);
         float ms = 0.f;

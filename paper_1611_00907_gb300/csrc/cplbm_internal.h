@@ -184,13 +184,15 @@ void step_default_shape(int prec, int *tx, int *ty);
 // `max` pairs.
 int step_shapes(int *tx, int *ty, int max);
 
-// Baseline step with the pressure-tensor force (Eq. 5): FP32 (tile 32x32)
-// and FP64 (32x16), periodic lattices; pt_shape gives the tile it needs.
+// Baseline step with the pressure-tensor force (Eq. 5): FP32 (tiles 64x16,
+// two nodes per lane, and 32x32) and FP64 (32x16), periodic lattices;
+// pt_shape gives the default tile, pt_shape_supported the others.
 // maps: the TMA maps of that tile (interior and seam tiles take the TMA
 // path), or nullptr for the general path only.
 cudaError_t launch_step_pt(const Lattice &L, int parity, int cur, cudaStream_t s,
                            const TmaMaps *maps = nullptr);
 void pt_shape(int prec, int *tx, int *ty);
+bool pt_shape_supported(int prec, int tx, int ty);
 
 // Edge tiles the TMA tile paths may take (bit 0: periodic left and right,
 // bit 1: periodic bottom and top, bit 2: the bottom and top wall rows).

@@ -82,19 +82,24 @@ void step_default_shape(int prec, int *tx, int *ty)
 
 void pt_shape(int prec, int *tx, int *ty)
 {
-    *tx = 32;
-    *ty = prec == P_F64 ? 16 : 32;
+    // FP32: the step's default tile (two nodes per lane)
+    *tx = prec == P_F64 ? 32 : 64;
+    *ty = 16;
+}
+
+bool pt_shape_supported(int prec, int tx, int ty)
+{
+    if (prec == P_F64) return tx == 32 && ty == 16;
+    if (prec == P_F32) return (tx == 64 && ty == 16) || (tx == 32 && ty == 32);
+    return false;
 }
 
 cudaError_t launch_step_pt(const Lattice &L, int parity, int cur, cudaStream_t s,
                            const TmaMaps *maps)
 {
-    if (L.walls) return cudaErrorInvalidValue;
-    if (L.precision == P_F64 && L.tx == 32 && L.ty == 16)
-        return launch_pt_f64(L, parity, cur, s, maps);
-    if (L.precision == P_F32 && L.tx == 32 && L.ty == 32)
-        return launch_pt_f32(L, parity, cur, s, maps);
-    return cudaErrorInvalidValue;
+    if (L.walls || !pt_shape_supported(L.precision, L.tx, L.ty)) return cudaErrorInvalidValue;
+    if (L.precision == P_F64) return launch_pt_f64(L, parity, cur, s, maps);
+    return launch_pt_f32(L, parity, cur, s, maps);
 }
 
 cudaError_t launch_step_batch(const BatchList &w, int parity, int cur, int precision,

@@ -15,6 +15,7 @@ cudaError_t launch_step_f32(const Lattice &L, int parity, int cur,
 cudaError_t launch_pt_f32(const Lattice &L, int parity, int cur, cudaStream_t s,
                           const TmaMaps *maps)
 {
+    if (L.tx == 64 && L.ty == 16) return launch_pt_shape<SF32, 64, 16>(L, parity, cur, s, maps);
     return launch_pt_shape<SF32, 32, 32>(L, parity, cur, s, maps);
 }
 

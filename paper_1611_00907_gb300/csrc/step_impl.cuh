@@ -1396,6 +1396,29 @@ __device__ __forceinline__ float2 mu_bulk2(const EosT<float> &e, float2 rho)
     }
 }
 
+// p0_bulk on a pair of densities (the pressure-tensor baseline).
+__device__ __forceinline__ float2 p0_bulk2(const EosT<float> &e, float2 rho)
+{
+    const float2 one = p2(1.0f), ma = p2(-e.a);
+    const float2 br = pmul(p2(e.b), rho), rrt = pmul(rho, p2(e.RT));
+    switch (e.kind) {
+    case EOS_VDW:
+        return pfma(pmul(ma, rho), rho, pdiv(rrt, psub(one, br)));
+    case EOS_CS: {
+        const float2 h = pmul(p2(e.quarter_b), rho), q = psub(one, h), h2 = pmul(h, h);
+        const float2 num = pmul(rrt, psub(padd(padd(one, h), h2), pmul(h2, h)));
+        return pfma(pmul(ma, rho), rho, pdiv(num, pmul(pmul(q, q), q)));
+    }
+    case EOS_PR: {
+        const float2 den = psub(pfma(p2(2.0f), br, one), pmul(br, br));
+        return psub(pdiv(rrt, psub(one, br)), pdiv(pmul(pmul(p2(e.aalpha), rho), rho), den));
+    }
+    default:  // EOS_RKS
+        return psub(pdiv(rrt, psub(one, br)),
+                    pdiv(pmul(pmul(p2(e.aalpha), rho), rho), padd(one, br)));
+    }
+}
+
 // collide() on a pair of nodes.
 __device__ __forceinline__ void collide2(const float2 *f, float2 drho, float2 rho,
                                          float2 Fx, float2 Fy, float2 tau,
@@ -1458,7 +1481,7 @@ __device__ __forceinline__ void st_pair(__half *p, float2 v)
     *reinterpret_cast<__half2 *>(p) = __floats2half2_rn(v.x, v.y);
 }
 
-template <class pop_t, int TX, int TY, int NT>
+template <class pop_t, int TX, int TY, int NT, int NP = 1>
 struct TmaPairSmem {
     static constexpr int NW = NT / 32;
     static constexpr int PX = 16 / sizeof(pop_t);
@@ -1469,7 +1492,7 @@ struct TmaPairSmem {
     static constexpr int NRHO = (TY + 4) * RP;
     static constexpr int MP = TX + 4, MH = TY + 2;  // mu of halo column a at a + 1
     static constexpr int NRING = RingStage<float, TX, TY>::N;
-    static constexpr int NMU = MP * MH;
+    static constexpr int NMU = NP * MP * MH;        // mu, or (NP = 3) the tensor of Eq. 9
     static constexpr int XW = TX + 2;              // exchange slots per warp
     static constexpr int NXCH = 2 * NW * XW;
     // as TmaSmem
@@ -1487,7 +1510,8 @@ struct TmaPairSmem {
                   "pair-aligned sub-arrays");
 };
 
-template <class S, int TX, int TY, int NT, int PARITY, int EDGE>
+// PT: the baseline force of Eq. 5, as for step_tile_tma.
+template <class S, int TX, int TY, int NT, int PARITY, int EDGE, bool PT = false>
 __device__ __forceinline__ bool step_tile_tma_pair(const Lattice &L, int cur, int X0,
                                                    int Y0, unsigned char *smem_raw,
                                                    TileMaps maps,
@@ -1496,9 +1520,10 @@ __device__ __forceinline__ bool step_tile_tma_pair(const Lattice &L, int cur, in
 {
     using rho_t = typename S::rho_t;
     using pop_t = typename S::pop_t;
-    using TS = TmaPairSmem<pop_t, TX, TY, NT>;
+    using TS = TmaPairSmem<pop_t, TX, TY, NT, PT ? 3 : 1>;
     static_assert(TX == 64, "lanes map to x pairs");
     static_assert(sizeof(rho_t) == 4 && sizeof(typename S::real) == 4, "FP32 arithmetic");
+    static_assert(!PT || EDGE != 2, "the pressure-tensor force has no wall rule");
     constexpr int NW = TS::NW, PER = TY / NW;
     static_assert(PER * NW == TY && PER >= 2, "warps own whole row blocks");
     constexpr int RP = TS::RP, PP = TS::PP, PLANE = TS::PLANE, MP = TS::MP, MH = TS::MH;
@@ -1559,7 +1584,46 @@ __device__ __forceinline__ bool step_tile_tma_pair(const Lattice &L, int cur, in
     const Consts<float> &K = consts<float>(L);
     const float ref = S::offset ? K.rho_ref : 0.0f;
     const float2 ref2 = p2(ref);
-    {
+    constexpr int NP1 = MP * MH;  // one plane of s_mu
+    if constexpr (PT) {
+        // the tensor of Eq. 9 in three planes (xx, xy, yy), in the
+        // arithmetic of pt_tile, with the window walk of the mu branch
+        const EosT<float> &eos = K.eos;
+        const float kappa = K.kappa;
+        const float2 kap = p2(kappa), mkap = p2(-kappa), mhkap = p2(-0.5f * kappa);
+        const int b0 = (warp * MH) / NW, b1 = ((warp + 1) * MH) / NW;
+        const int c0 = 2 * lane + 4;
+        Row2 d = row2(s_rho, b0 * RP + c0), m = row2(s_rho, (b0 + 1) * RP + c0);
+        for (int b = b0; b < b1; ++b) {
+            const Row2 u = row2(s_rho, (b + 2) * RP + c0);
+            const float2 rho = S::offset ? padd(m.c, ref2) : m.c;
+            float2 gx, gy;
+            grad2(u, m, d, gx, gy);
+            const float2 lap = lap2(u, m, d);
+            const float2 iso = pfma(mhkap, pfma(gx, gx, pmul(gy, gy)),
+                                    pfma(pmul(mkap, rho), lap, p0_bulk2(eos, rho)));
+            float *o = s_mu + b * MP + 2 * lane + 2;
+            *reinterpret_cast<float2 *>(o) = pfma(pmul(kap, gx), gx, iso);
+            *reinterpret_cast<float2 *>(o + NP1) = pmul(pmul(kap, gx), gy);
+            *reinterpret_cast<float2 *>(o + 2 * NP1) = pfma(pmul(kap, gy), gy, iso);
+            d = m;
+            m = u;
+        }
+        for (int t = threadIdx.x; t < 2 * MH; t += NT) {
+            const int ae = (t & 1) ? TX + 1 : 0, b = t >> 1;
+            const int c = (b + 1) * RP + ae + 3;
+            const float rho = s_rho[c] + ref;
+            float gx, gy;
+            grad9<float, RP>(s_rho, c, gx, gy);
+            const float lap = lap9<float, RP>(s_rho, c);
+            const float iso = p0_bulk(eos, rho) - kappa * rho * lap -
+                              0.5f * kappa * (gx * gx + gy * gy);
+            float *o = s_mu + b * MP + ae + 1;
+            o[0] = iso + kappa * gx * gx;
+            o[NP1] = kappa * gx * gy;
+            o[2 * NP1] = iso + kappa * gy * gy;
+        }
+    } else {
         const EosT<float> &eos = K.eos;
         const float2 mkappa = p2(-K.kappa);
         const int b0 = (warp * MH) / NW, b1 = ((warp + 1) * MH) / NW;
@@ -1616,6 +1680,14 @@ __device__ __forceinline__ bool step_tile_tma_pair(const Lattice &L, int cur, in
     // mu of tile row ly at s_mu row ly + 1, column x0 + 2
     Row2 rd = row2(s_rho, (ly0 + 1) * RP + x0 + 4), rm = row2(s_rho, (ly0 + 2) * RP + x0 + 4);
     Row2 md = row2(s_mu, ly0 * MP + x0 + 2), mm = row2(s_mu, (ly0 + 1) * MP + x0 + 2);
+    // PT: md / mm hold P_xx; the windows of P_xy and P_yy
+    Row2 xyd{}, xym{}, yyd{}, yym{};
+    if constexpr (PT) {
+        xyd = row2(s_mu + NP1, ly0 * MP + x0 + 2);
+        xym = row2(s_mu + NP1, (ly0 + 1) * MP + x0 + 2);
+        yyd = row2(s_mu + 2 * NP1, ly0 * MP + x0 + 2);
+        yym = row2(s_mu + 2 * NP1, (ly0 + 1) * MP + x0 + 2);
+    }
     float2 pend = p2(0.0f), up_prev = p2(0.0f), first = p2(0.0f);
     float pend_c = 0.0f, up_prev_c = 0.0f, first_c = 0.0f;
     const int slot_c = TX + (lane == 31);        // exchange slot of a column
@@ -1638,6 +1710,11 @@ __device__ __forceinline__ bool step_tile_tma_pair(const Lattice &L, int cur, in
         const int ly = ly0 + k;
         const Row2 ru = row2(s_rho, (ly + 3) * RP + x0 + 4);
         const Row2 mu = row2(s_mu, (ly + 2) * MP + x0 + 2);
+        Row2 xyu{}, yyu{};
+        if constexpr (PT) {
+            xyu = row2(s_mu + NP1, (ly + 2) * MP + x0 + 2);
+            yyu = row2(s_mu + 2 * NP1, (ly + 2) * MP + x0 + 2);
+        }
         float2 same = p2(0.0f), up = p2(0.0f), down = p2(0.0f);
         float same_c = 0.0f, up_c = 0.0f, down_c = 0.0f;
         if (!walls_ok || ly < hy) {  // warp-uniform
@@ -1653,11 +1730,20 @@ __device__ __forceinline__ bool step_tile_tma_pair(const Lattice &L, int cur, in
             }
             const float2 drho = rm.c;
             const float2 rho = S::offset ? padd(drho, ref2) : drho;
-            float2 grx, gry, gmx, gmy;
+            float2 grx, gry, gmx, gmy, Fx, Fy;
             grad2(ru, rm, rd, grx, gry);
             grad2(mu, mm, md, gmx, gmy);
-            const float2 Fx = psub(pmul(grx, third), pmul(rho, gmx));
-            const float2 Fy = psub(pmul(gry, third), pmul(rho, gmy));
+            if constexpr (PT) {
+                // Eq. 5: F = -div(P) + grad(cs^2 rho)
+                float2 xy_x, xy_y, yy_x, yy_y;
+                grad2(xyu, xym, xyd, xy_x, xy_y);
+                grad2(yyu, yym, yyd, yy_x, yy_y);
+                Fx = psub(pmul(grx, third), padd(gmx, xy_y));
+                Fy = psub(pmul(gry, third), padd(xy_x, yy_y));
+            } else {
+                Fx = psub(pmul(grx, third), pmul(rho, gmx));
+                Fy = psub(pmul(gry, third), pmul(rho, gmy));
+            }
             float2 fp[9];
             collide2(f, drho, rho, Fx, Fy, tau, omega, fp);
             // wall rows (halfway bounce-back, Sec. IV)
@@ -1735,6 +1821,12 @@ __device__ __forceinline__ bool step_tile_tma_pair(const Lattice &L, int cur, in
         rm = ru;
         md = mm;
         mm = mu;
+        if constexpr (PT) {
+            xyd = xym;
+            xym = xyu;
+            yyd = yym;
+            yym = yyu;
+        }
     }
     *reinterpret_cast<float2 *>(s_up + warp * XW + x0) = up_prev;
     if (col_lane) s_up[warp * XW + slot_c] = up_prev_c;
@@ -2142,11 +2234,20 @@ static cudaError_t launch_batch_t(const BatchList &w, int parity, int cur, int t
 // Baseline: the same step with the pressure-tensor force (Eq. 5, Eq. 9),
 // the form the method avoids, for measuring what avoiding it saves.
 // Periodic lattices, FP32 and FP64, on the same tile paths as the step
-// kernel: TMA for interior and periodic-seam tiles (32-wide shapes), the
-// general path for the rest.
+// kernel: TMA for interior and periodic-seam tiles (32-wide shapes, and the
+// two-nodes-per-lane path of 64-wide FP32 shapes), the general path for the
+// rest.
 // ---------------------------------------------------------------------------
+// Resident CTAs a pressure-tensor kernel asks for: three on the pair path,
+// whose three tensor planes take the tile's shared memory to ~58 KB.
+template <class S, int TX, int TY, int NT>
+constexpr int pt_min_ctas()
+{
+    return HasTmaPair<S, TX, TY, NT>::value ? 3 : 0;
+}
+
 template <class S, int TX, int TY, int NT, int PARITY>
-__global__ void __launch_bounds__(NT)
+__global__ void __launch_bounds__(NT, pt_min_ctas<S, TX, TY, NT>())
     step_pt_kernel(const Lattice L, int cur, int seams, const __grid_constant__ TmaMaps maps)
 {
     extern __shared__ __align__(128) unsigned char smem_raw[];
@@ -2154,7 +2255,7 @@ __global__ void __launch_bounds__(NT)
     const int by = PARITY ? gridDim.y - 1 - blockIdx.y : blockIdx.y;
     const int kind = tile_kind(L, TX, TY, bx, by, seams);
     const bool interior = kind == TILE_INTERIOR;
-    if constexpr (HasTma<S, TX, TY, NT>::value) {
+    if constexpr (HasTma<S, TX, TY, NT>::value || HasTmaPair<S, TX, TY, NT>::value) {
         if (kind != TILE_GENERAL && maps.valid) {
             __shared__ __align__(8) unsigned long long bar[2];
             if (threadIdx.x == 0) {
@@ -2163,12 +2264,21 @@ __global__ void __launch_bounds__(NT)
             }
             __syncthreads();
             const TileMaps tm{&maps.pops, &maps.rho[cur]};
-            if (interior)
-                step_tile_tma<S, TX, TY, NT, PARITY, 0, true>(L, cur, bx * TX, by * TY,
-                                                              smem_raw, tm, bar, 0);
-            else
-                step_tile_tma<S, TX, TY, NT, PARITY, 1, true>(L, cur, bx * TX, by * TY,
-                                                              smem_raw, tm, bar, 0);
+            if constexpr (HasTma<S, TX, TY, NT>::value) {
+                if (interior)
+                    step_tile_tma<S, TX, TY, NT, PARITY, 0, true>(L, cur, bx * TX, by * TY,
+                                                                  smem_raw, tm, bar, 0);
+                else
+                    step_tile_tma<S, TX, TY, NT, PARITY, 1, true>(L, cur, bx * TX, by * TY,
+                                                                  smem_raw, tm, bar, 0);
+            } else {
+                if (interior)
+                    step_tile_tma_pair<S, TX, TY, NT, PARITY, 0, true>(
+                        L, cur, bx * TX, by * TY, smem_raw, tm, bar, 0);
+                else
+                    step_tile_tma_pair<S, TX, TY, NT, PARITY, 1, true>(
+                        L, cur, bx * TX, by * TY, smem_raw, tm, bar, 0);
+            }
             return;
         }
     }
@@ -2186,10 +2296,14 @@ static cudaError_t launch_pt_shape(const Lattice &L, int parity, int cur,
 {
     using real = typename S::real;
     using SM = StepSmem<real, TX, TY>;
-    constexpr int NT = STEP_THREADS;
+    constexpr int NT = step_threads<S, TX, TY>();
     size_t smem = SM::bytes + 2 * sizeof(real) * SM::WM * SM::HM;
     if constexpr (HasTma<S, TX, TY, NT>::value)
         if (TmaSmem<S, TX, TY, 3>::bytes > smem) smem = TmaSmem<S, TX, TY, 3>::bytes;
+    if constexpr (HasTmaPair<S, TX, TY, NT>::value) {
+        using PS = TmaPairSmem<typename S::pop_t, TX, TY, NT, 3>;
+        if (PS::bytes > smem) smem = PS::bytes;
+    }
     TmaMaps m{};
     if (maps && maps->valid && maps->tx == TX && maps->ty == TY) m = *maps;
     auto k0 = step_pt_kernel<S, TX, TY, NT, 0>;
@@ -2208,7 +2322,8 @@ static cudaError_t launch_pt_shape(const Lattice &L, int parity, int cur,
         configured = dev;
     }
     const int ntx = (L.nx + TX - 1) / TX, nty = (L.nyf + TY - 1) / TY;
-    const int seams = HasTma<S, TX, TY, NT>::value ? seam_bits(L, TX, TY) : 0;
+    const int seams = HasTma<S, TX, TY, NT>::value || HasTmaPair<S, TX, TY, NT>::value
+                          ? seam_bits(L, TX, TY) : 0;
     dim3 grid(ntx, nty);
     if (parity == 0)
         k0<<<grid, NT, smem, s>>>(L, cur, seams, m);
