@@ -349,14 +349,16 @@ lbm_status lbm_eos_pressure(int eos, double a, double b, double R,
 /* Path class of every tile of the fused step for an nx x ny lattice (ny
  * counts the two solid rows when walls != 0) at tile shape tx x ty, one of
  * the compiled shapes: kinds[by * ntx + bx] = 2 for an interior tile (the
- * TMA or cp.async interior path), 1 for a seam tile (its halo wraps around
- * a periodic edge; the TMA paths only), 0 for a general tile, with ntx =
- * ceil(nx / tx), nty = ceil(fluid rows / ty) and max >= ntx * nty entries
- * in kinds (a host array).  seams != 0 gives the classes of a single
- * lattice whose shape has a TMA path; seams == 0 those of a batch, or of a
- * shape without one (seam tiles general).  Host-only, no device work; for
- * choosing lattice sizes and for tests.  LBM_ERR_ARG on a bad size, shape
- * or a short array. */
+ * TMA or cp.async interior path), 1 for an edge tile (the TMA paths only:
+ * its halo wraps around a periodic edge or meets a wall, or, on 32-wide
+ * shapes, it is the ragged last tile, at least 4 nodes wide, of a periodic
+ * direction), 0 for a general tile, with ntx = ceil(nx / tx), nty =
+ * ceil(fluid rows / ty) and max >= ntx * nty entries in kinds (a host
+ * array).  seams != 0 gives the classes of a lattice (single or in a
+ * batch) whose shape has a TMA path; seams == 0 those of a shape without
+ * one (edge tiles general).  Host-only, no device work; for choosing
+ * lattice sizes and for tests.  LBM_ERR_ARG on a bad size, shape or a
+ * short array. */
 lbm_status lbm_tile_kinds(int nx, int ny, int walls, int tx, int ty, int seams,
                           int *kinds, size_t max);
 

@@ -195,14 +195,17 @@ void pt_shape(int prec, int *tx, int *ty);
 bool pt_shape_supported(int prec, int tx, int ty);
 
 // Edge tiles the TMA tile paths may take (bit 0: periodic left and right,
-// bit 1: periodic bottom and top, bit 2: the bottom and top wall rows).
-// Periodic edges: at least three full tiles span the lattice, and the last
-// tile across the edge is full or at least 4 nodes wide, so the halo that
-// wraps around the edge has the layout of an interior halo (the ragged tile
-// itself stays on the general path).  Walls: at least two tile rows, the
-// bottom one full and the one above it full or at least 4 rows high, so the
-// bottom wall tile's halo above sees interior tile edges; the top wall
-// tile may be ragged down to two rows (tile_kind).
+// bit 1: periodic bottom and top, bit 2: the bottom and top wall rows, bit
+// 3: the ragged last tile of a periodic direction).  Periodic edges: at
+// least three full tiles span the lattice, and the last tile across the
+// edge is full or at least 4 nodes wide, so the halo that wraps around the
+// edge has the layout of an interior halo.  That ragged last tile takes the
+// TMA path too on 32-wide tiles (bit 3), whose tile function places the
+// right and top tile edges at the tile's own width and height; the
+// two-nodes-per-lane path leaves it to the general path.  Walls: at least
+// two tile rows, the bottom one full and the one above it full or at least
+// 4 rows high, so the bottom wall tile's halo above sees interior tile
+// edges; the top wall tile may be ragged down to two rows (tile_kind).
 __host__ __device__ inline int seam_bits(const Lattice &L, int tx, int ty)
 {
     int s = 0;
@@ -210,6 +213,7 @@ __host__ __device__ inline int seam_bits(const Lattice &L, int tx, int ty)
     if (L.nx / tx >= 3 && (rx == 0 || rx >= 4)) s |= 1;
     if (!L.walls && nfy >= 3 && (ry == 0 || ry >= 4)) s |= 2;
     if (L.walls && (nfy >= 2 || (nfy == 1 && ry >= 4))) s |= 4;
+    if (tx == 32) s |= 8;
     return s;
 }
 
@@ -221,8 +225,9 @@ __host__ __device__ inline int seam_bits(const Lattice &L, int tx, int ty)
 // 2-node halo, and the halo's staged rows and columns stay inside the
 // arrays); TILE_SEAM (an edge tile of the TMA paths) when the same holds
 // along each direction except that the halo wraps around a periodic edge
-// allowed by `seams`, or the tile is a bottom or top wall tile allowed by
-// `seams` (seam_bits); TILE_GENERAL otherwise.  A top wall tile of one
+// allowed by `seams` (the ragged last tile there too when `seams` allows
+// it), or the tile is a bottom or top wall tile allowed by `seams`
+// (seam_bits); TILE_GENERAL otherwise.  A top wall tile of one
 // fluid row stays general: that row is then also the tile's bottom edge,
 // which holds partial sums from the tile below, and the Eq. 28 average of
 // the halo's outermost columns reads it one column beyond the halo, where
@@ -238,8 +243,9 @@ __host__ __device__ inline int tile_kind(const Lattice &L, int tx, int ty, int b
     if (ix && iy) return TILE_INTERIOR;
     const int nty = (L.nyf + ty - 1) / ty;
     const bool wall = (seams & 4) && (by == 0 || (by == nty - 1 && L.nyf - by * ty >= 2));
-    const bool sx = ix || ((seams & 1) && bx < nfx);
-    const bool sy = iy || ((seams & 2) && by < nfy) || wall;
+    const bool ragged = (seams & 8) != 0;
+    const bool sx = ix || ((seams & 1) && (bx < nfx || ragged));
+    const bool sy = iy || ((seams & 2) && (by < nfy || ragged)) || wall;
     return sx && sy ? TILE_SEAM : TILE_GENERAL;
 }
 

@@ -61,6 +61,16 @@ __device__ __forceinline__ int edge_col(int ci)
 {
     return ci == 0 ? 1 : ci == 1 ? 2 : ci == 2 ? T + 1 : T + 2;
 }
+// The same for an edge tile of width (height) w: a ragged last tile has
+// its far edge at column (row) w + 1 and the next tile's near edge at w + 2.
+__device__ __forceinline__ int edge_col(int ci, int w)
+{
+    return ci == 0 ? 1 : ci == 1 ? 2 : ci == 2 ? w + 1 : w + 2;
+}
+__device__ __forceinline__ int col_index(int l, int w)
+{
+    return l == 1 ? 0 : l == 2 ? 1 : l == w + 1 ? 2 : l == w + 2 ? 3 : -1;
+}
 __device__ __forceinline__ bool col_is_left(int ci) { return ci & 1; }
 __device__ __forceinline__ bool row_is_below(int ri) { return ri & 1; }
 template <int T>
@@ -691,8 +701,9 @@ __device__ __forceinline__ void stage_ring_wrapped(const Lattice &L, int cur, in
 // are in flight, into staging slots (seam_fix_load), and copied over the
 // zeros once the boxes have landed (seam_rho_apply, seam_pop_apply).
 //   density halo (rows of pitch RP from x = X0 - 4, y = Y0 - 2): the two
-//   halo columns or rows across a periodic edge, columns X0 - 2 .. X0 + TX
-//   + 1 (with walls, only rows of the fluid); on a wall tile at a periodic
+//   halo columns or rows across a periodic edge, the right and top ones
+//   after the tile's own width hx and height hy (SeamEdges), columns X0 - 2
+//   .. X0 + TX + 1 (with walls, only rows of the fluid); on a wall tile at a periodic
 //   x edge also the wall-adjacent row's density one column further out,
 //   which the Eq. 28 average of the outermost halo column needs;
 //   populations, odd steps (pin_x0 / pin_col layout): the three directions
@@ -705,7 +716,8 @@ __device__ __forceinline__ void stage_ring_wrapped(const Lattice &L, int cur, in
 struct SeamEdges {
     bool xl, xr, yb, yt;  // the tile's halo wraps the left / right / bottom / top edge
     bool wb, wt;          // the tile meets the bottom / top wall
-    int hy;               // fluid rows of the tile (below TY only on a ragged top wall tile)
+    int hx, hy;           // columns and fluid rows of the tile (below TX, TY only
+                          // on the ragged last tile of a direction)
     int vlo, vhi;         // staged density rows holding fluid nodes: [vlo, vhi)
 };
 template <bool WALLS>
@@ -714,9 +726,9 @@ __device__ __forceinline__ SeamEdges seam_edges(const Lattice &L, int X0, int Y0
 {
     const bool w = WALLS && L.walls != 0;
     const bool wb = w && Y0 == 0, wt = w && Y0 + TY >= L.nyf;
-    const int hy = wt ? L.nyf - Y0 : TY;
+    const int hx = min(TX, L.nx - X0), hy = min(TY, L.nyf - Y0);
     return {X0 == 0, X0 + TX >= L.nx, !w && Y0 == 0, !w && Y0 + TY >= L.nyf,
-            wb,     wt,              hy,  wb ? 2 : 0,  wt ? hy + 2 : TY + 4};
+            wb,     wt,              hx, hy,  wb ? 2 : 0,  wt ? hy + 2 : TY + 4};
 }
 template <int TX, int TY>
 struct SeamLists {
@@ -732,13 +744,13 @@ __device__ __forceinline__ bool seam_rho_slot(const SeamEdges &e, int t, int &ly
     if (t < SL::RHO_C) {
         if (!e.xl && !e.xr) return false;
         ly = t >> 1;
-        c = (e.xl ? 2 : TX + 4) + (t & 1);
+        c = (e.xl ? 2 : e.hx + 4) + (t & 1);
         return ly >= e.vlo && ly < e.vhi;
     }
     if (t < SL::RHO_R) {
         if (!e.yb && !e.yt) return false;
         const int q = t - SL::RHO_C, sel = q / (TX + 4);
-        ly = (e.yb ? 0 : TY + 2) + sel;
+        ly = (e.yb ? 0 : e.hy + 2) + sel;
         c = 2 + q - sel * (TX + 4);
         return true;
     }
@@ -746,7 +758,7 @@ __device__ __forceinline__ bool seam_rho_slot(const SeamEdges &e, int t, int &ly
     const int k = t - SL::RHO_R, top = k >> 1, right = k & 1;
     if (!(top ? e.wt : e.wb) || !(right ? e.xr : e.xl)) return false;
     ly = top ? e.hy + 1 : 2;
-    c = right ? TX + 6 : 1;
+    c = right ? e.hx + 6 : 1;
     return true;
 }
 // Population slot t: direction i at tile node (lx, ly).
@@ -759,7 +771,7 @@ __device__ __forceinline__ bool seam_pop_slot(const SeamEdges &e, int t, int &i,
         if (!e.xl && !e.xr) return false;
         const int d = t / TY;
         ly = t - d * TY;
-        lx = e.xl ? 0 : TX - 1;
+        lx = e.xl ? 0 : e.hx - 1;
         // left edge: e_x = +1 reads x - 1 = -1; right edge: e_x = -1 reads x + 1 = nx
         i = e.xl ? (d == 0 ? 1 : d == 1 ? 5 : 8) : (d == 0 ? 3 : d == 1 ? 6 : 7);
         return ly < e.hy;
@@ -770,7 +782,7 @@ __device__ __forceinline__ bool seam_pop_slot(const SeamEdges &e, int t, int &i,
     lx = q - d * TX;
     ly = bottom ? 0 : e.hy - 1;
     i = bottom ? (d == 0 ? 2 : d == 1 ? 5 : 6) : (d == 0 ? 4 : d == 1 ? 7 : 8);
-    return true;
+    return lx < e.hx;
 }
 template <class S, int TX, int TY, int NT, int PARITY, bool WALLS>
 __device__ __forceinline__ void seam_fix_load(const Lattice &L, int cur, int X0, int Y0,
@@ -880,16 +892,19 @@ __device__ __forceinline__ bool wall_mu(const Lattice &L, const SeamEdges &e, in
 // of pitch RP, halo node (lx, ly) at column lx + 2), in the order of
 // load_rho_stored.  Items 0 .. 4 HR - 1 take the four edge columns whole,
 // crossings with the edge rows included; the rest take the edge rows
-// without those crossings (halo columns 0, 3 .. TX, TX + 3).
+// without those crossings (halo columns 0, 3 .. hx, hx + 3).  hx, hy: the
+// tile's width and height (TX, TY but on a ragged last tile, whose halo
+// ends at column hx + 3 and row hy + 3; what lies beyond is not read).
 template <class real, int TX, int TY, int NT, int RP>
-__device__ __forceinline__ void combine_ring(real *s_rho, const real *s_ring)
+__device__ __forceinline__ void combine_ring(real *s_rho, const real *s_ring, int hx,
+                                             int hy)
 {
     using RS = RingStage<real, TX, TY>;
     constexpr int HR = TY + 4, NC = 4 * HR, NI = NC + 4 * TX;
     for (int q = threadIdx.x; q < NI; q += NT) {
         if (q < NC) {
-            const int ci = q / HR, ly = q - ci * HR, lx = edge_col<TX>(ci);
-            const int ri = col_index<TY>(ly);
+            const int ci = q / HR, ly = q - ci * HR, lx = edge_col(ci, hx);
+            const int ri = col_index(ly, hy);
             real v = s_rho[ly * RP + lx + 2] + s_ring[ci * RS::CL + ly + 2];
             if (ri >= 0)
                 v = (v + s_ring[RS::NCOL + ri * RS::RL + lx + 2]) +
@@ -897,8 +912,9 @@ __device__ __forceinline__ void combine_ring(real *s_rho, const real *s_ring)
             s_rho[ly * RP + lx + 2] = v;
         } else {
             const int t = q - NC, ri = t / TX, k = t - ri * TX;
-            const int lx = k == 0 ? 0 : (k == TX - 1 ? TX + 3 : k + 2);
-            const int ly = edge_col<TY>(ri);
+            if (k >= hx) continue;
+            const int lx = k == 0 ? 0 : (k == hx - 1 ? hx + 3 : k + 2);
+            const int ly = edge_col(ri, hy);
             s_rho[ly * RP + lx + 2] += s_ring[RS::NCOL + ri * RS::RL + lx + 2];
         }
     }
@@ -1025,11 +1041,16 @@ __device__ __forceinline__ bool step_tile_tma(const Lattice &L, int cur, int X0,
 
     // 2. Partial sums into the halo's tile-edge nodes (order of
     //    load_rho_stored).  Halo (lx, ly) of the (TX + 4)-wide convention is
-    //    staged row ly, column lx + 2.
-    combine_ring<real, TX, TY, NT, RP>(s_rho, s_ring);
+    //    staged row ly, column lx + 2.  Edge tiles may be the ragged last
+    //    tile of a periodic direction: hx columns, hy rows (its right and
+    //    top edges, the wrap and the partial sums across them sit there);
+    //    lanes at hx and beyond and rows at hy and beyond compute but store
+    //    nothing.
+    const SeamEdges edge = seam_edges<walls_ok>(L, X0, Y0, TX, TY);
+    const int hx = seam ? edge.hx : TX, hy = seam ? edge.hy : TY;
+    combine_ring<real, TX, TY, NT, RP>(s_rho, s_ring, hx, hy);
     __syncthreads();
     // edge tiles at a wall: the solid row's density (Eq. 28)
-    const SeamEdges edge = seam_edges<walls_ok>(L, X0, Y0, TX, TY);
     if (walls_ok) wall_rho_rows<real, TX, NT, RP>(edge, s_rho);
 
     // 3. mu at (a, b), a in [0, TX + 2) <-> x = X0 - 1 + a, b in [0, TY + 2)
@@ -1110,20 +1131,22 @@ __device__ __forceinline__ bool step_tile_tma(const Lattice &L, int cur, int X0,
     rho_t *const *ring = (rho_t *const *)L.ring[nxt];
     // 32-bit write offsets (the TMA maps exist only when 8 planes fit); on
     // odd steps of seam tiles an x target across a periodic edge is brought
-    // back by nx (lanes 0 and 31), a row target by the lattice height (rows
-    // 0 and TY - 1, wrap_y below)
+    // back by nx (lanes 0 and hx - 1), a row target by the lattice height
+    // (rows 0 and hy - 1, wrap_y below)
+    const int lr = hx - 1;  // lane of the tile's last column
     const int cxl = (PARITY == 1 && seam && X0 == 0 && lane == 0) ? L.nx : 0;
-    const int cxr = (PARITY == 1 && seam && X0 + TX >= L.nx && lane == TX - 1) ? -L.nx : 0;
+    const int cxr = (PARITY == 1 && seam && X0 + TX >= L.nx && lane == lr) ? -L.nx : 0;
     int woff[9];
 #pragma unroll
     for (int i = 1; i < 9; ++i)
         woff[i] = PARITY == 0 ? (opp(i) - 1) * (int)L.plane
                               : (i - 1) * (int)L.plane + ey(i) * L.pitch + ex(i) +
                                     (ex(i) < 0 ? cxl : ex(i) > 0 ? cxr : 0);
-    // wall tiles: rows 0 .. hy - 1 hold fluid (hy < TY on a ragged top wall
-    // tile; the rows above it are not updated and contribute nothing)
-    const int hy = walls_ok ? edge.hy : TY;
-    const bool has_l = lane > 0, has_r = lane < 31;
+    // rows 0 .. hy - 1 and columns 0 .. hx - 1 are the tile's (below TY, TX
+    // on a ragged last tile, and on a ragged top wall tile rows hy and up are
+    // not fluid); the others are not updated and contribute nothing
+    const bool has_l = lane > 0, has_r = lane < lr;
+    const bool lane_ok = lane < hx;
     real wr[3][3], wm[3][3];
 #pragma unroll
     for (int j = 0; j < 2; ++j)
@@ -1134,17 +1157,19 @@ __device__ __forceinline__ bool step_tile_tma(const Lattice &L, int cur, int X0,
         }
     // Rolling hand-over.  pend: row k - 1 without its "down" part;
     // first: row 0 of the warp without the warp below's "up"; *_c: the same
-    // for the ring column a lane 0 / lane 31 feeds.
+    // for the ring column a lane 0 / lane hx - 1 feeds; up_top: the "up" of
+    // the tile's last row hy - 1, for the ring row above the tile.
     real pend = real(0), up_prev = real(0), first = real(0);
     real pend_c = real(0), up_prev_c = real(0), first_c = real(0);
-    const int slot_c = TX + (lane == 31);        // exchange slot of a column
-    const int xc = lane == 0 ? X0 - 1 : X0 + TX;  // ring column of the lane
+    real up_top = real(0), up_top_c = real(0);
+    const int slot_c = TX + (lane == lr);         // exchange slot of a column
+    const int xc = lane == 0 ? X0 - 1 : X0 + hx;  // ring column of the lane
     const int cls_c = lane == 0 ? R_R : R_L;
     // this tile, and the tile of the ring column a lane feeds (classes L and
     // R share one index layout)
     const int bx = X0 / TX, by = Y0 / TY;
     const int bxc = neighbour_tile(X0, lane == 0 ? -1 : 1, TX, L.nx, seam);
-    const bool col_lane = lane == 0 || lane == 31;
+    const bool col_lane = lane == 0 || lane == lr;
     pop_t *Arow = A + (long long)(Y0 + ly0) * L.pitch + X0 + lx;
 #pragma unroll
     for (int k = 0; k < PER; ++k) {
@@ -1156,7 +1181,7 @@ __device__ __forceinline__ bool step_tile_tma(const Lattice &L, int cur, int X0,
         }
         real same = real(0), up = real(0), down = real(0);
         real same_c = real(0), up_c = real(0), down_c = real(0);
-        if (!walls_ok || ly < hy) {  // warp-uniform
+        if (!seam || ly < hy) {  // warp-uniform
             real f[9];
 #pragma unroll
             for (int i = 1; i < 9; ++i)
@@ -1190,7 +1215,7 @@ __device__ __forceinline__ bool step_tile_tma(const Lattice &L, int cur, int X0,
             {
                 const int wrap_y = L.nyf * L.pitch;
                 const int cyb = (PARITY == 1 && seam && edge.yb && ly == 0) ? wrap_y : 0;
-                const int cyt = (PARITY == 1 && seam && edge.yt && ly == TY - 1) ? -wrap_y : 0;
+                const int cyt = (PARITY == 1 && seam && edge.yt && ly == hy - 1) ? -wrap_y : 0;
 #pragma unroll
                 for (int i = 1; i < 9; ++i) {
                     // odd steps: a population heading into a solid row goes
@@ -1199,7 +1224,8 @@ __device__ __forceinline__ bool step_tile_tma(const Lattice &L, int cur, int X0,
                                                            (ey(i) > 0 && wall_t));
                     const int o = into_wall ? (opp(i) - 1) * (int)L.plane
                                             : woff[i] + (ey(i) < 0 ? cyb : ey(i) > 0 ? cyt : 0);
-                    if (CPLBM_IN_POPS(L, Arow + o, 1)) st_real(Arow + o, fp[i]);
+                    if ((!seam || lane_ok) && CPLBM_IN_POPS(L, Arow + o, 1))
+                        st_real(Arow + o, fp[i]);
                 }
             }
 
@@ -1216,15 +1242,20 @@ __device__ __forceinline__ bool step_tile_tma(const Lattice &L, int cur, int X0,
             if (wall_b) same += (fp[4] + fp[7]) + fp[8];
             if (wall_t) same += (fp[2] + fp[5]) + fp[6];
             // ring columns: lane 0 feeds x = X0 - 1 (f*_3; f*_6 up; f*_7
-            // down), lane 31 feeds x = X0 + TX (f*_1; f*_5 up; f*_8 down)
+            // down), lane hx - 1 feeds x = X0 + hx (f*_1; f*_5 up; f*_8 down)
             same_c = lane == 0 ? fp[3] : fp[1];
             up_c = lane == 0 ? fp[6] : fp[5];
             down_c = lane == 0 ? fp[7] : fp[8];
         }
+        if (seam && ly == hy - 1) {
+            up_top = up;
+            up_top_c = up_c;
+        }
         Arow += L.pitch;
-        // rows of the lattice this warp may write (all but those above a
-        // ragged top wall tile's fluid)
-        const bool row_ok = !walls_ok || ly - 1 < hy;
+        // rows of the lattice this warp may write (the tile's rows
+        // 0 .. hy - 1) and its lanes that hold a node of the tile
+        const bool row_ok = !seam || ly - 1 < hy;
+        const bool put_ok = !seam || lane_ok;
         if (k == 0) {
             // this row's "down" belongs to the warp below (or the ring row
             // under the tile)
@@ -1239,7 +1270,7 @@ __device__ __forceinline__ bool step_tile_tma(const Lattice &L, int cur, int X0,
                 first = done;
                 first_c = done_c;
             } else if (row_ok) {
-                put_rho(L, nxt, Rn, (long long)(Y0 + ly - 1) * L.pitch + X0 + lx, (rho_t)done);
+                if (put_ok) put_rho(L, nxt, Rn, (long long)(Y0 + ly - 1) * L.pitch + X0 + lx, (rho_t)done);
                 if (col_lane) put_ring(L, nxt, ring, cls_c, ring_index(L, R_L, bxc, by, Y0 + ly - 1, xc), (rho_t)done_c);
             }
             pend = same + up_prev;
@@ -1265,8 +1296,9 @@ __device__ __forceinline__ bool step_tile_tma(const Lattice &L, int cur, int X0,
             top += s_down[(warp + 1) * XW + lane];
             top_c += s_down[(warp + 1) * XW + slot_c];
         }
-        if (!walls_ok || ly0 + PER - 1 < hy) {
-            put_rho(L, nxt, Rn, (long long)(Y0 + ly0 + PER - 1) * L.pitch + X0 + lx, (rho_t)top);
+        if (!seam || ly0 + PER - 1 < hy) {
+            if (!seam || lane_ok)
+                put_rho(L, nxt, Rn, (long long)(Y0 + ly0 + PER - 1) * L.pitch + X0 + lx, (rho_t)top);
             if (col_lane) put_ring(L, nxt, ring, cls_c, ring_index(L, R_L, bxc, by, Y0 + ly0 + PER - 1, xc), (rho_t)top_c);
         }
         // first row: add the warp below's last-row "up"
@@ -1274,26 +1306,31 @@ __device__ __forceinline__ bool step_tile_tma(const Lattice &L, int cur, int X0,
             first += s_up[(warp - 1) * XW + lane];
             first_c += s_up[(warp - 1) * XW + slot_c];
         }
-        if (!walls_ok || ly0 < hy) {
-            put_rho(L, nxt, Rn, (long long)(Y0 + ly0) * L.pitch + X0 + lx, (rho_t)first);
+        if (!seam || ly0 < hy) {
+            if (!seam || lane_ok)
+                put_rho(L, nxt, Rn, (long long)(Y0 + ly0) * L.pitch + X0 + lx, (rho_t)first);
             if (col_lane) put_ring(L, nxt, ring, cls_c, ring_index(L, R_L, bxc, by, Y0 + ly0, xc), (rho_t)first_c);
         }
     }
     // ring rows below and above the tile, with their corners (none across a
-    // wall)
+    // wall); the row above takes the "up" of the tile's last row hy - 1 (the
+    // last row of the last warp but on a ragged last tile)
     const int bxl = neighbour_tile(X0, -1, TX, L.nx, seam);
     const int bxr = neighbour_tile(X0, 1, TX, L.nx, seam);
     if (warp == 0 && !(walls_ok && edge.wb)) {
         const int byb = neighbour_tile(Y0, -1, TY, L.nyf, seam);
-        put_ring(L, nxt, ring, R_T, ring_index(L, R_T, bx, byb, Y0 - 1, X0 + lx), (rho_t)s_down[lane]);
+        if (!seam || lane_ok)
+            put_ring(L, nxt, ring, R_T, ring_index(L, R_T, bx, byb, Y0 - 1, X0 + lx), (rho_t)s_down[lane]);
         if (lane == 0) put_ring(L, nxt, ring, R_TR, ring_index(L, R_TR, bxl, byb, Y0 - 1, X0 - 1), (rho_t)s_down[TX]);
-        if (lane == 31) put_ring(L, nxt, ring, R_TL, ring_index(L, R_TL, bxr, byb, Y0 - 1, X0 + TX), (rho_t)s_down[TX + 1]);
+        if (lane == lr) put_ring(L, nxt, ring, R_TL, ring_index(L, R_TL, bxr, byb, Y0 - 1, X0 + hx), (rho_t)s_down[TX + 1]);
     }
-    if (warp == NW - 1 && !(walls_ok && edge.wt)) {
+    const real upt = seam ? up_top : up_prev, upt_c = seam ? up_top_c : up_prev_c;
+    if (warp == (hy - 1) / PER && !(walls_ok && edge.wt)) {
         const int byt = neighbour_tile(Y0, 1, TY, L.nyf, seam);
-        put_ring(L, nxt, ring, R_B, ring_index(L, R_B, bx, byt, Y0 + TY, X0 + lx), (rho_t)up_prev);
-        if (lane == 0) put_ring(L, nxt, ring, R_BR, ring_index(L, R_BR, bxl, byt, Y0 + TY, X0 - 1), (rho_t)up_prev_c);
-        if (lane == 31) put_ring(L, nxt, ring, R_BL, ring_index(L, R_BL, bxr, byt, Y0 + TY, X0 + TX), (rho_t)up_prev_c);
+        if (!seam || lane_ok)
+            put_ring(L, nxt, ring, R_B, ring_index(L, R_B, bx, byt, Y0 + hy, X0 + lx), (rho_t)upt);
+        if (lane == 0) put_ring(L, nxt, ring, R_BR, ring_index(L, R_BR, bxl, byt, Y0 + hy, X0 - 1), (rho_t)upt_c);
+        if (lane == lr) put_ring(L, nxt, ring, R_BL, ring_index(L, R_BL, bxr, byt, Y0 + hy, X0 + hx), (rho_t)upt_c);
     }
     return true;
 }
@@ -1571,7 +1608,7 @@ __device__ __forceinline__ bool step_tile_tma_pair(const Lattice &L, int cur, in
 
     // 2. Partial sums into the halo's tile-edge nodes (order of
     //    load_rho_stored); halo (lx, ly) is staged at row ly, column lx + 2.
-    combine_ring<float, TX, TY, NT, RP>(s_rho, s_ring);
+    combine_ring<float, TX, TY, NT, RP>(s_rho, s_ring, TX, TY);
     __syncthreads();
     // edge tiles at a wall: the solid row's density (Eq. 28)
     const SeamEdges edge = seam_edges<walls_ok>(L, X0, Y0, TX, TY);

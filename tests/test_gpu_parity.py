@@ -186,7 +186,7 @@ def test_seam_tiles_fp64(tile, walls, size, oracle_threads):
 
 # A full tile whose right or top neighbour is the ragged last tile of its
 # row or column takes the interior paths when that tile is at least 4 nodes
-# wide (remainder 4 here; remainder 3 keeps the general path).
+# wide (remainder 4 here; remainder 3 keeps the general path for both).
 RAGGED_NEIGHBOUR_CASES = [
     ((32, 32), False, (100, 100)),   # remainders 4 and 4
     ((32, 16), True, (99, 54)),      # x remainder 3, 52 fluid rows: remainder 4
@@ -197,6 +197,48 @@ RAGGED_NEIGHBOUR_CASES = [
 @pytest.mark.parametrize("tile,walls,size", RAGGED_NEIGHBOUR_CASES)
 def test_ragged_neighbour_tiles_fp64(tile, walls, size, oracle_threads):
     nx, ny = size
+    sim, ref, rho = _setup("cs", nx, ny, walls)
+    with sim:
+        sim.set_tile(*tile)
+        sim.init(rho)
+        ref.init_equilibrium(rho)
+        for _ in range(2):      # both parities; tolerance as test_seam_tiles_fp64
+            sim.step(1)
+            ref.step(1)
+            _compare(sim, ref, 1e-12)
+        sim.step(198)
+        ref.step(198)
+        _compare(sim, ref, 1e-11)
+
+
+# The ragged last tile of a periodic direction (at least 4 nodes) takes the
+# 32-wide TMA path itself: its right and top edges, the wrap across them and
+# the partial sums there sit at its own width and height, and the lanes and
+# rows beyond them store nothing.
+RAGGED_TMA_CASES = [
+    ((32, 32), False, (100, 100)),   # remainders 4 and 4: the narrowest
+    ((32, 16), False, (230, 140)),   # remainders 6 and 12
+    ((32, 24), False, (133, 120)),   # x remainder 5, y full
+    ((32, 32), False, (128, 115)),   # x full, y remainder 19
+    ((32, 24), True, (134, 77)),     # walls: x remainder 6, top wall tile ragged
+    ((32, 16), True, (230, 140)),
+]
+
+
+@pytest.mark.parametrize("tile,walls,size", RAGGED_TMA_CASES)
+def test_ragged_last_tiles_take_tma_fp64(tile, walls, size, oracle_threads):
+    nx, ny = size
+    # the ragged last tile of every tile row (column) with TMA tiles is one
+    # (a row under a top wall tile of fewer than 4 rows is general whole)
+    kinds = np.asarray(tile_kinds(nx, ny, walls, tile))
+    tx, ty = tile
+    nyf = ny - 2 if walls else ny
+    if nx % tx:
+        rows = (kinds[:, :-1] != 0).any(axis=1)
+        assert rows.sum() >= 2 and (kinds[rows, -1] == 1).all()
+    if not walls and nyf % ty:
+        cols = (kinds[:-1, :] != 0).any(axis=0)
+        assert cols.sum() >= 2 and (kinds[-1, cols] == 1).all()
     sim, ref, rho = _setup("cs", nx, ny, walls)
     with sim:
         sim.set_tile(*tile)

@@ -14,6 +14,9 @@ wrapped writes and the neighbour tiles of the density hand-over):
   across a periodic edge) is replaced from the wrapped node;
 * every neighbour tile the hand-over writes to is the tile that holds the
   neighbour node;
+* every halo node the step reads gets exactly the partial sums (class and
+  owning tile) that load_rho_stored adds for that node, no more and no fewer,
+  from the staged entries that combine_ring adds at that position;
 * the launch that asks only for the TMA path's shared memory has no general
   tile.
 
@@ -87,7 +90,9 @@ def rule_kind(g, tx, ty, bx, by, seams):
     # a one-row top wall tile stays general (its only row is also a tile
     # bottom edge, read by the Eq. 28 average beyond the combined halo)
     wall = sw and (by == 0 or (by == nty - 1 and g.nyf - by * ty >= 2))
-    if (ix or (sx and bx < nfx)) and (iy or (sy and by < nfy) or wall):
+    # the ragged last tile of a periodic direction: TMA on 32-wide tiles
+    ragged = seams and tx == 32
+    if (ix or (sx and (bx < nfx or ragged))) and (iy or (sy and (by < nfy or ragged)) or wall):
         return 1
     return 0
 
@@ -115,14 +120,105 @@ def aa_read_source(g, i, r, x):
     return OPP[i], wrap(rs, g.nyf), wrap(x - EX[i], g.nx)
 
 
+def edge_pos(ci, w):
+    """Halo column (row) of edge index ci of a tile w wide (high)."""
+    return (1, 2, w + 1, w + 2)[ci]
+
+
+def combine_model(tx, ty, hx, hy):
+    """Staged (row, column) -> the staged entries combine_ring adds there:
+    ('col', ci, j), ('row', ri, j), ('corner', ci, ri)."""
+    add = {}
+    for ci in range(4):
+        lx = edge_pos(ci, hx)
+        for ly in range(ty + 4):
+            e = [("col", ci, ly + 2)]
+            if ly in (1, 2, hy + 1, hy + 2):
+                ri = (1, 2, hy + 1, hy + 2).index(ly)
+                e += [("row", ri, lx + 2), ("corner", ci, ri)]
+            add.setdefault((ly, lx + 2), []).extend(e)
+    for ri in range(4):
+        ly = edge_pos(ri, hy)
+        for k in range(hx):
+            lx = 0 if k == 0 else (hx + 3 if k == hx - 1 else k + 2)
+            add.setdefault((ly, lx + 2), []).append(("row", ri, lx + 2))
+    return add
+
+
+def check_combine(g, tx, ty, bx, by, hx, hy, seam):
+    """Every halo node the tile reads gets, from the staged entries
+    combine_ring adds at its position, exactly the partial sums
+    load_rho_stored adds for it (class and owning tile; entries staged as
+    zeros, with no writer, count as absent)."""
+    x0, y0 = bx * tx, by * ty
+    nx, nyf = g.nx, g.nyf
+    wb = g.walls and y0 == 0
+    wt = g.walls and y0 + ty >= nyf
+    vlo, vhi = (2 if wb else 0), (hy + 2 if wt else ty + 4)
+
+    def resolve(entry):
+        kind, a, b = entry
+        if kind == "col":
+            r = y0 - 4 + b
+            if g.walls and not 0 <= r < nyf:
+                return None
+            t = neighbour_tile(x0, edge_tile(a), tx, nx, True)
+            return (R_L if a & 1 else R_R, t, wrap(r, nyf))
+        ri = a if kind == "row" else b
+        if (wb and ri <= 1) or (wt and ri >= 2):
+            return None
+        ty_ = neighbour_tile(y0, edge_tile(ri), ty, nyf, not g.walls)
+        if kind == "row":
+            return (R_B if ri & 1 else R_T, ty_, wrap(x0 - 4 + b, nx))
+        ci = a
+        tx_ = neighbour_tile(x0, edge_tile(ci), tx, nx, True)
+        left, below = ci & 1, ri & 1   # col_is_left, row_is_below
+        c = (R_BL if left else R_BR) if below else (R_TL if left else R_TR)
+        return (c, tx_, ty_)
+
+    model = combine_model(tx, ty, hx, hy)
+    for ly in range(vlo, min(vhi, hy + 4)):
+        for c in range(2, hx + 6):
+            xs, r = wrap(x0 - 4 + c, nx), y0 - 2 + ly
+            rs = r if g.walls else wrap(r, nyf)
+            tbx, tby = xs // tx, rs // ty
+            wx, wy = min(tx, nx - tbx * tx), min(ty, nyf - tby * ty)
+            lxn, lyn = xs - tbx * tx, rs - tby * ty
+            left, right = lxn == 0, lxn == wx - 1
+            below = lyn == 0 and not (g.walls and rs == 0)
+            above = lyn == wy - 1 and not (g.walls and rs == nyf - 1)
+            want = []
+            if left:
+                want.append((R_L, tbx, rs))
+            if right:
+                want.append((R_R, tbx, rs))
+            if below:
+                want.append((R_B, tby, xs))
+                if left:
+                    want.append((R_BL, tbx, tby))
+                if right:
+                    want.append((R_BR, tbx, tby))
+            if above:
+                want.append((R_T, tby, xs))
+                if left:
+                    want.append((R_TL, tbx, tby))
+                if right:
+                    want.append((R_TR, tbx, tby))
+            got = [e for e in map(resolve, model.get((ly, c), [])) if e is not None]
+            assert sorted(got) == sorted(want), (g.nx, g.ny, g.walls, tx, ty, bx, by,
+                                                 ly, c, got, want)
+
+
 def check_tile(g, tx, ty, bx, by, seam):
     x0, y0 = bx * tx, by * ty
     nx, nyf = g.nx, g.nyf
     wb = g.walls and y0 == 0
     wt = g.walls and y0 + ty >= nyf
-    hy = nyf - y0 if wt else ty          # fluid rows of the tile
-    assert x0 + tx <= nx, "TMA tiles are full in x"
-    assert y0 + ty <= nyf or wt, "only a top wall tile may be ragged"
+    hx, hy = min(tx, nx - x0), min(ty, nyf - y0)   # columns and fluid rows of the tile
+    if tx != 32:
+        assert hx == tx, "two-nodes-per-lane TMA tiles are full in x"
+        assert hy == ty or wt, "only a top wall tile may be ragged"
+    assert hx >= 4 and (hy >= 4 or wt), "a ragged last tile is at least 4 wide"
     assert hy >= 1 and not (wb and wt)
     # the neighbour tiles across the halo are full or at least 4 nodes wide
     for c in (x0 - 1, x0 + tx):
@@ -135,6 +231,7 @@ def check_tile(g, tx, ty, bx, by, seam):
         if seam or 0 <= c < nyf:
             t = wrap(c, nyf) // ty
             assert min(ty, nyf - t * ty) >= 4
+    check_combine(g, tx, ty, bx, by, hx, hy, seam)
     cl, rl = ty + 8, tx + 8
     if not seam:
         assert x0 >= 2 and x0 + tx + 1 < nx and y0 >= 2 and y0 + ty + 1 < nyf
@@ -177,7 +274,7 @@ def check_tile(g, tx, ty, bx, by, seam):
         if t < 2 * (ty + 4):
             if not (xl or xr):
                 continue
-            ly, c = t >> 1, (2 if xl else tx + 4) + (t & 1)
+            ly, c = t >> 1, (2 if xl else hx + 4) + (t & 1)
             if not vlo <= ly < vhi:
                 continue
         elif t < 2 * (ty + 4) + 2 * (tx + 4):
@@ -185,22 +282,23 @@ def check_tile(g, tx, ty, bx, by, seam):
                 continue
             q = t - 2 * (ty + 4)
             sel = q // (tx + 4)
-            ly, c = (0 if yb else ty + 2) + sel, 2 + q - sel * (tx + 4)
+            ly, c = (0 if yb else hy + 2) + sel, 2 + q - sel * (tx + 4)
         else:
             k = t - 2 * (ty + 4) - 2 * (tx + 4)
             top, right = k >> 1, k & 1
             if not ((wt if top else wb) and (xr if right else xl)):
                 continue
-            ly, c = (hy + 1 if top else 2), (tx + 6 if right else 1)
+            ly, c = (hy + 1 if top else 2), (hx + 6 if right else 1)
         x, r = wrap(x0 - 4 + c, nx), y0 - 2 + ly
         assert 0 <= x < nx
         assert 0 <= r < nyf if g.walls else True
         fixed.add((ly, c))
-    read = {(ly, c) for ly in range(vlo, vhi) for c in range(2, tx + 6)}
+    # the halo of the tile's own nodes: columns 2 .. hx + 5, rows up to hy + 3
+    read = {(ly, c) for ly in range(vlo, min(vhi, hy + 4)) for c in range(2, hx + 6)}
     if wb:
-        read |= {(2, c) for c in range(1, tx + 7)}
+        read |= {(2, c) for c in range(1, hx + 7)}
     if wt:
-        read |= {(hy + 1, c) for c in range(1, tx + 7)}
+        read |= {(hy + 1, c) for c in range(1, hx + 7)}
     for ly, c in read:
         x, r = x0 - 4 + c, y0 - 2 + ly
         assert not (g.walls and not 0 <= r < nyf), "a solid row is read as stored"
@@ -210,7 +308,7 @@ def check_tile(g, tx, ty, bx, by, seam):
         # Eq. 28 average) get no partial sums: the node there must hold its
         # whole density, i.e. sit on no edge of its own tile that receives
         # partial sums (load_rho_stored)
-        if c in (1, tx + 6):
+        if c in (1, hx + 6):
             xs, rr = wrap(x, nx), r
             tx0 = xs // tx * tx
             wxx = min(tx, nx - tx0)
@@ -231,7 +329,7 @@ def check_tile(g, tx, ty, bx, by, seam):
             d, ly = t // ty, t % ty
             if ly >= hy:
                 continue
-            lx = 0 if xl else tx - 1
+            lx = 0 if xl else hx - 1
             i = ([1, 5, 8] if xl else [3, 6, 7])[d]
         else:
             bottom = yb or wb
@@ -239,6 +337,8 @@ def check_tile(g, tx, ty, bx, by, seam):
                 continue
             q = t - 3 * ty
             d, lx = q // tx, q % tx
+            if lx >= hx:
+                continue
             ly = 0 if bottom else hy - 1
             i = ([2, 5, 6] if bottom else [4, 7, 8])[d]
         src = aa_read_source(g, i, y0 + ly, x0 + lx)
@@ -246,7 +346,7 @@ def check_tile(g, tx, ty, bx, by, seam):
         # two slots that name one node and direction fetch the same source
         assert fixed.setdefault((i, ly, lx), src) == src
     for ly in range(hy):
-        for lx in range(tx):
+        for lx in range(hx):
             for i in range(1, 9):
                 x, r = x0 + lx, y0 + ly
                 plane, rs, xs = aa_read_source(g, i, r, x)
@@ -267,11 +367,11 @@ def check_tile(g, tx, ty, bx, by, seam):
                     continue
                 if EX[i] < 0 and xl and lx == 0:
                     xt += nx
-                if EX[i] > 0 and xr and lx == tx - 1:
+                if EX[i] > 0 and xr and lx == hx - 1:
                     xt -= nx
                 if EY[i] < 0 and yb and ly == 0:
                     rt += nyf
-                if EY[i] > 0 and yt and ly == ty - 1:
+                if EY[i] > 0 and yt and ly == hy - 1:
                     rt -= nyf
                 assert 0 <= xt < nx and 0 <= rt < nyf
     # hand-over: neighbour tiles are the tiles of the neighbour nodes
@@ -314,7 +414,7 @@ def test_library_classes_follow_the_stated_rules(seams):
 
 
 def test_index_arithmetic_of_tma_tiles():
-    checked = wall_tiles = ragged_tops = 0
+    checked = wall_tiles = ragged_tops = ragged_x = ragged_y = 0
     for nx, ny, walls in _lattices():
         if nx * ny > 520 * 260:
             continue
@@ -328,7 +428,10 @@ def test_index_arithmetic_of_tma_tiles():
                 if walls and by in (0, nty - 1):
                     wall_tiles += 1
                     ragged_tops += by == nty - 1 and g.nyf % ty != 0
+                ragged_x += (bx + 1) * tx > nx
+                ragged_y += not walls and (by + 1) * ty > g.nyf
     assert checked > 2000 and wall_tiles > 300 and ragged_tops > 100
+    assert ragged_x > 100 and ragged_y > 100, (ragged_x, ragged_y)
 
 
 def test_small_shared_memory_launch_has_no_general_tile():
