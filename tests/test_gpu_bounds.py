@@ -24,10 +24,12 @@ TILES = [(32, 16), (32, 24), (32, 32), (64, 16), (64, 32)]
 # (nx, ny, walls): odd and ragged sizes, seam tiles (three or more full
 # tiles across), one-node-wide last tiles, walls with ragged top tiles,
 # ragged last tiles of periodic directions on the 32-wide TMA path (230 x
-# 140; 100 x 100: 4 nodes, the narrowest it takes)
+# 140; 100 x 100: 4 nodes, the narrowest it takes; 229 x 141 and 197 x 66:
+# odd widths)
 SIZES = [(9, 7, False), (70, 21, False), (131, 37, False), (65, 17, False),
          (192, 96, False), (256, 128, False), (230, 140, False), (100, 100, False),
-         (9, 9, True), (131, 37, True), (96, 50, True), (192, 66, True), (230, 140, True)]
+         (229, 141, False), (9, 9, True), (131, 37, True), (96, 50, True), (192, 66, True),
+         (230, 140, True), (197, 66, True)]
 
 
 def _child():

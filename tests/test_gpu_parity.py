@@ -253,6 +253,45 @@ def test_ragged_last_tiles_take_tma_fp64(tile, walls, size, oracle_threads):
         _compare(sim, ref, 1e-11)
 
 
+# Lattices with ragged last tiles in FP32 arithmetic: on the 32-wide path
+# they take the TMA path (odd widths included); on the two-nodes-per-lane
+# path they stay general beside TMA neighbours.  Against the oracle
+# (tolerance as test_every_tile_shape) and against the same lattice on the
+# general path.
+RAGGED_FP32_CASES = [
+    ((32, 24), False, (133, 120)),   # x remainder 5
+    ((32, 16), False, (229, 141)),   # remainders 5 and 13
+    ((32, 16), True, (197, 66)),     # walls: x remainder 5
+    ((64, 16), False, (229, 141)),   # remainders 37 and 13: general ragged tiles
+    ((64, 32), True, (197, 66)),     # walls, x remainder 5
+]
+
+
+@pytest.mark.parametrize("tile,walls,size", RAGGED_FP32_CASES)
+@pytest.mark.parametrize("precision", ["f32", "f32_offset"])
+def test_ragged_lattices_fp32(tile, walls, size, precision, monkeypatch):
+    nx, ny = size
+    kinds = np.asarray(tile_kinds(nx, ny, walls, tile))
+    if tile[0] == 32:
+        assert (kinds[1:-1, -1] == 1).all() and kinds.min() >= 1
+    ref_rho = 0.5 * sum(_coexistence("cs")) if precision == "f32_offset" else 0.0
+    runs = []
+    for no_tma in (False, True):
+        if no_tma:
+            monkeypatch.setenv("CPLBM_NO_TMA", "1")
+        sim, ref, rho = _setup("cs", nx, ny, walls, precision=precision,
+                               rho_ref=ref_rho)
+        with sim:
+            sim.set_tile(*tile)
+            sim.init(rho).step(61)
+            runs.append(sim.moments())
+    ref.init_equilibrium(rho).step(61)
+    want = ref.moments()
+    for k in ("rho", "mu", "vx", "vy"):
+        assert _rel(runs[0][k], want[k]) < 1e-4, (k, _rel(runs[0][k], want[k]))
+        assert _rel(runs[0][k], runs[1][k]) < 1e-4, (k, _rel(runs[0][k], runs[1][k]))
+
+
 @pytest.mark.parametrize("tile,walls,size", SEAM_CASES[:2] + SEAM_CASES[3:4] + [
     ((64, 16), False, (192, 48)),   # two nodes per lane: 3 x 3 tiles
     ((64, 32), True, (192, 98)),
@@ -657,7 +696,9 @@ def test_fp16_storage_tma_path(tile, size, monkeypatch):
 
 
 @pytest.mark.parametrize("tile", [(32, 16), (32, 32), (64, 16), (64, 32)])
-@pytest.mark.parametrize("size", [(330, 200), (192, 96)])   # 192 x 96: seam tiles
+# 192 x 96: seam tiles; 330 x 200 and 229 x 141: ragged last tiles (even and
+# odd widths; TMA on 32-wide tiles, general on 64-wide ones)
+@pytest.mark.parametrize("size", [(330, 200), (192, 96), (229, 141)])
 @pytest.mark.parametrize("steps", [20, 21])                 # both in-place parities
 def test_fp16_storage_against_the_oracle(tile, size, steps):
     """Density, chemical potential and reported velocity of the FP16-offset
